@@ -1,0 +1,388 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each checks a closed form, an
+exact invariant, a textbook special case, an independent scalar root or
+quadrature, or a finite-difference derivative.  (Paper: arXiv:1910.12578,
+section 2, Eq. 1 and Eq. sdc:general.)
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1910_12578_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([int(t) for t in line.split()])
+    return rows
+
+
+# ---------------------------------------------------------------- quadrature
+def test_quadrature_weights_golden():
+    """Trapezoid and Simpson node-to-node weights (section 2)."""
+    for M, m, l, num, den in _read_golden("quadrature_weights.txt"):
+        q = O.quad_weights(M)
+        assert q[m, l] == pytest.approx(num / den, abs=1e-15)
+
+
+@pytest.mark.parametrize("M", [2, 3])
+def test_quadrature_exact_on_polynomials(M):
+    """The weights integrate 1, t, ..., t^(M-1) exactly on each sub-interval."""
+    q = O.quad_weights(M)
+    tau = [0.0, 1.0] if M == 2 else [0.0, 0.5, 1.0]
+    for p in range(M):
+        for m in range(M - 1):
+            exact = (tau[m + 1] ** (p + 1) - tau[m] ** (p + 1)) / (p + 1)
+            got = sum(q[m, l] * tau[l] ** p for l in range(M))
+            assert got == pytest.approx(exact, abs=1e-15)
+    # Simpson: the two halves add up to 1/6, 2/3, 1/6
+    if M == 3:
+        assert q.sum(0) == pytest.approx([1 / 6, 2 / 3, 1 / 6], abs=1e-15)
+
+
+# ---------------------------------------------------------------- helpers
+def uniform_1d(net, nx=4, rho=1.0, u=0.0, T=1.0, X=None, M=2, K=2, gamma=5.0 / 3.0, limiter=1):
+    P = W.Problem(dim=1, n=(nx, 1, 1), dx=(1.0 / nx, 1.0, 1.0), gamma=gamma, net=net,
+                  n_nodes=M, n_iters=K, limiter=limiter)
+    X = X if X is not None else [1.0] + [0.0] * (net.nspec - 1)
+    ones = np.ones(nx)
+    U = W.conserved_from(gamma, rho * ones, [u * ones], T * ones, [x * ones for x in X])
+    return P, U.reshape(P.nvar, 1, 1, nx)
+
+
+def custom_chain(a, nu, Q):
+    """Alpha chain with hand-picked constants (same structure as the seeded one)."""
+    nspec = len(a) + 1
+    rng = np.random.default_rng(0)
+    net = W.alpha_chain(nspec, rng)
+    net.a = np.array(a, dtype=float)
+    net.nu = np.array(nu, dtype=float)
+    net.Q = np.array(Q, dtype=float)
+    return net
+
+
+# ---------------------------------------------------------------- HLLC
+@pytest.mark.parametrize("dim", [1, 3])
+def test_hllc_consistency(dim):
+    """F(q, q) equals the physical Euler flux (consistency of the Riemann solver)."""
+    rng = np.random.default_rng(1)
+    net = W.alpha_chain(4, rng)
+    P = W.Problem(dim=dim, n=(4, 4 if dim == 3 else 1, 4 if dim == 3 else 1), dx=(0.25,) * 3,
+                  gamma=1.4, net=net)
+    o = O.Oracle(P)
+    for _ in range(20):
+        rho = rng.uniform(0.5, 2.0)
+        u = rng.uniform(-2, 2, dim)
+        p = rng.uniform(0.2, 3.0)
+        X = rng.dirichlet(np.ones(net.nspec))
+        q = np.concatenate([[rho], u, [p], X])
+        for d in range(dim):
+            F = o.hllc(d, q, q)
+            E = p / (P.gamma - 1) + 0.5 * rho * np.dot(u, u)
+            mom = rho * u[d] * u
+            mom[d] += p
+            exact = np.concatenate([[rho * u[d]], mom, [(E + p) * u[d]], rho * u[d] * X])
+            assert np.allclose(F, exact, rtol=1e-13, atol=1e-13)
+
+
+def test_hllc_resolves_contact():
+    """An isolated contact (equal u and p) gives the upwind-side flux exactly."""
+    net = W.decay_network()
+    P = W.Problem(dim=1, n=(4, 1, 1), dx=(0.25, 1, 1), gamma=5 / 3, net=net)
+    o = O.Oracle(P)
+    u, p = 0.3, 1.2
+    qL = np.array([1.0, u, p, 0.7, 0.3])
+    qR = np.array([0.25, u, p, 0.2, 0.8])
+    F = o.hllc(0, qL, qR)
+    E = p / (P.gamma - 1) + 0.5 * 1.0 * u * u
+    assert F[0] == pytest.approx(1.0 * u, rel=1e-14)
+    assert F[1] == pytest.approx(1.0 * u * u + p, rel=1e-14)
+    assert F[2] == pytest.approx((E + p) * u, rel=1e-14)
+    assert F[3:] == pytest.approx(1.0 * u * qL[3:], rel=1e-14)
+
+
+# ---------------------------------------------------------------- Jacobian
+@pytest.mark.parametrize("which", ["decay", "chain7", "chain13"])
+def test_jacobian_matches_finite_differences(which):
+    """Analytic dR/dw against a 4th-order central difference of R itself."""
+    rng = np.random.default_rng(2)
+    if which == "decay":
+        net = W.decay_network()
+    else:
+        net = W.alpha_chain(7 if which == "chain7" else 13, rng)
+    P = W.Problem(dim=3, n=(2, 2, 2), dx=(0.5,) * 3, gamma=5 / 3, net=net)
+    o = O.Oracle(P)
+    n = net.nspec + 1
+    for _ in range(5):
+        rho = rng.uniform(0.5, 2.0)
+        mom = rng.uniform(-0.3, 0.3, 3)
+        X = rng.dirichlet(np.ones(net.nspec))
+        T = rng.uniform(0.6, 1.5)
+        rhoE = rho * T / (P.gamma - 1) + 0.5 * np.dot(mom, mom) / rho
+        w = np.concatenate([[rhoE], rho * X])
+        R, J = o.rates(rho, mom, w)
+        Jfd = np.zeros((n, n))
+        for c in range(n):
+            h = 1e-4 * max(abs(w[c]), 1e-3)
+            e = np.zeros(n); e[c] = h
+            f = lambda s: o.rates(rho, mom, w + s * e, jac=False)
+            Jfd[:, c] = (-f(2) + 8 * f(1) - 8 * f(-1) + f(-2)) / (12 * h)
+        scale = np.abs(J).max()
+        assert np.abs(J - Jfd).max() <= 1e-7 * scale + 1e-12
+
+
+# ---------------------------------------------------------------- linear equation
+@pytest.mark.parametrize("row", _read_golden("amplification.txt"))
+def test_amplification_factor_closed_forms(row):
+    """A -> B with Q = 0 and no flow is y' = -k y with k fixed; one SDC step
+    multiplies X_A by the closed-form g(z) of the sweep (hand derivation)."""
+    M, K, num, den = row
+    net = W.decay_network(Q=0.0)
+    T = 1.0
+    k = 1e3 * math.exp(-10.0 / T)
+    P, U = uniform_1d(net, T=T, M=M, K=(K if K > 0 else 60))
+    P.newton_rtol = 1e-14
+    o = O.Oracle(P)
+    dt = 0.1 / k                    # z = -k dt = -1/10
+    U1, st = o.step(U, dt)
+    g = U1[3, 0, 0, :] / U[3, 0, 0, :]
+    assert np.all(np.abs(g - num / den) <= 2e-15)
+    # mass fraction sum and energy untouched
+    assert np.allclose(U1[3] + U1[4], U[0], rtol=0, atol=1e-15)
+    assert np.array_equal(U1[2], U[2])
+
+
+def test_sweep_is_backward_euler_limit_for_stiff_decay():
+    """K=1, M=2 is backward Euler: for z -> -inf the factor tends to 0 like 1/(1-z)."""
+    net = W.decay_network(Q=0.0)
+    P, U = uniform_1d(net, T=1.0, M=2, K=1)
+    o = O.Oracle(P)
+    k = 1e3 * math.exp(-10.0)
+    for z in [-10.0, -1e3, -1e6]:
+        U1, _ = o.step(U, -z / k)
+        assert U1[3, 0, 0, 0] / U[3, 0, 0, 0] == pytest.approx(1 / (1 - z), rel=1e-13)
+
+
+# ---------------------------------------------------------------- order of accuracy
+def _run_to(P, U, t_final, nsteps):
+    o = O.Oracle(P)
+    dt = t_final / nsteps
+    V = U.copy()
+    for _ in range(nsteps):
+        V, _ = o.step(V, dt)
+    return V
+
+
+@pytest.mark.parametrize("M,K,order", [(2, 1, 1), (2, 2, 2), (3, 1, 1), (3, 2, 2), (3, 3, 3), (3, 4, 4)])
+def test_order_decay_with_heating(M, K, order):
+    """Section 2: each iteration raises the order by one up to the order of the
+    integral (2 with the trapezoid, 4 with Simpson).  Spatially uniform state,
+    so A = 0 exactly; the T-dependent A -> B with Q = 1 is nonlinear."""
+    net = W.decay_network(Q=1.0)
+    P, U = uniform_1d(net, T=2.0, M=M, K=K)
+    P.newton_rtol = 1e-14
+    ref = _run_to(P, U, 0.3, 2048)
+    errs = []
+    for ns in (32, 64, 128):
+        V = _run_to(P, U, 0.3, ns)
+        errs.append(abs(V[3, 0, 0, 0] - ref[3, 0, 0, 0]))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[-1] == pytest.approx(order, abs=0.35), (errs, rates)
+
+
+@pytest.mark.parametrize("M,K,order", [(2, 2, 2), (3, 3, 3), (3, 4, 4)])
+def test_order_alpha_chain(M, K, order):
+    """Same order test on a 5-species alpha chain with moderate rates."""
+    net = custom_chain(a=[1.5, 3.0, 2.0, 1.0], nu=[6.0, 8.0, 5.0, 7.0], Q=[1.0, 0.8, 0.6, 0.5])
+    P, U = uniform_1d(net, T=1.0, M=M, K=K)
+    P.newton_rtol = 1e-14
+    ref = _run_to(P, U, 0.4, 2048)
+    errs = []
+    for ns in (32, 64, 128):
+        V = _run_to(P, U, 0.4, ns)
+        errs.append(np.abs(V[2:] - ref[2:]).max())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[-1] == pytest.approx(order, abs=0.35), (errs, rates)
+
+
+def test_decay_with_heating_matches_quadrature_reference():
+    """A -> B with Q = 1 and no flow reduces to the scalar ODE
+    dX/dt = -k(T0 + (gamma-1) Q (1 - X)) X; its exact time to reach X is
+    t(X) = int_X^1 dX' / (k(T(X')) X'), computed by adaptive quadrature."""
+    from scipy.integrate import quad
+    from scipy.optimize import brentq
+    gamma, T0, Q, tf = 5 / 3, 2.0, 1.0, 0.3
+    k = lambda X: 1e3 * math.exp(-10.0 / (T0 + (gamma - 1) * Q * (1 - X)))
+    t_of = lambda X: quad(lambda s: 1.0 / (k(s) * s), X, 1.0, epsabs=1e-14, epsrel=1e-14, limit=400)[0]
+    X_exact = brentq(lambda X: t_of(X) - tf, 1e-12, 1.0, xtol=1e-15, rtol=1e-15)
+    net = W.decay_network(Q=Q)
+    errs = []
+    for ns in (64, 128, 256):
+        P, U = uniform_1d(net, T=T0, M=2, K=2)
+        P.newton_rtol = 1e-14
+        V = _run_to(P, U, tf, ns)
+        errs.append(abs(V[3, 0, 0, 0] - X_exact))
+    assert errs[-1] < 1e-5
+    assert math.log2(errs[0] / errs[1]) == pytest.approx(2.0, abs=0.3)
+    assert math.log2(errs[1] / errs[2]) == pytest.approx(2.0, abs=0.3)
+
+
+# ---------------------------------------------------------------- Newton
+def test_newton_matches_bisection_root():
+    """One zone, A -> B, Q = 1, no flow: mass and total energy reduce the
+    implicit update to f(X) = X + dt k(T(X)) X - X_rhs = 0, solved by bisection."""
+    gamma, Q = 5 / 3, 1.0
+    net = W.decay_network(Q=Q)
+    P, _ = uniform_1d(net)
+    o = O.Oracle(P)
+    rng = np.random.default_rng(3)
+    for _ in range(10):
+        XA = rng.uniform(0.2, 1.0)
+        T = rng.uniform(1.0, 3.0)
+        E = T / (gamma - 1)
+        dt = 10 ** rng.uniform(-3, 0)
+        rhs = np.array([E, XA, 1 - XA])
+        w, status, it = o.newton_zone(1.0, [0.0], rhs, dt, rhs.copy())
+        assert status == O.NEWTON_OK
+        f = lambda X: X + dt * 1e3 * math.exp(-10.0 / ((gamma - 1) * (E + Q * (XA - X)))) * X - XA
+        lo, hi = 0.0, XA
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if f(mid) > 0:
+                hi = mid
+            else:
+                lo = mid
+        assert w[1] == pytest.approx(0.5 * (lo + hi), rel=1e-12, abs=1e-15)
+        assert w[0] == pytest.approx(E + Q * (XA - w[1]), rel=1e-13)
+
+
+def test_newton_reports_status():
+    """maxit = 1 cannot converge: the zone reports ORC_NEWTON_MAXIT."""
+    net = W.decay_network(Q=1.0)
+    P, _ = uniform_1d(net)
+    P.newton_maxit = 1
+    o = O.Oracle(P)
+    w, status, it = o.newton_zone(1.0, [0.0], np.array([3.0, 1.0, 0.0]), 1.0, np.array([3.0, 1.0, 0.0]))
+    assert status == O.NEWTON_MAXIT and it == 1
+
+
+# ---------------------------------------------------------------- conservation / symmetry
+def test_conservation_3d_hot_spot():
+    """Mass, momentum, sum X = 1 per zone and total energy including the
+    binding energy released by the network are conserved to round-off."""
+    P, U = W.config_box(n=12, nspec=7, seed=0, T0=0.5, amp=2.0)
+    o = O.Oracle(P)
+    b = P.net.binding()
+    mass = np.asarray(P.net.mass)
+
+    def totals(V):
+        rho = V[0]
+        Y = V[5:] / mass[:, None, None, None] / rho
+        e_tot = (V[4] - rho * np.tensordot(b, Y, axes=1)).sum()
+        return V[0].sum(), V[1:4].sum(axis=(1, 2, 3)), e_tot
+
+    m0, p0, e0 = totals(U)
+    V = U.copy()
+    for _ in range(3):
+        V, st = o.step(V, o.cfl_dt(V))
+        assert st.n_fail == 0
+    m1, p1, e1 = totals(V)
+    assert abs(m1 - m0) <= 1e-13 * abs(m0)
+    assert np.all(np.abs(p1 - p0) <= 1e-13 * abs(m0))
+    assert abs(e1 - e0) <= 1e-12 * abs(e0)
+    assert np.abs(V[5:].sum(0) - V[0]).max() <= 1e-13
+    # the network really burned something
+    assert V[6].max() > 1e-3
+
+
+def _translation_problem(nx, limiter=1):
+    net = W.decay_network()
+    net.a = np.array([0.0])  # R = 0
+    P = W.Problem(dim=1, n=(nx, 1, 1), dx=(1.0 / nx, 1, 1), gamma=1.4, net=net, n_nodes=2, n_iters=2,
+                  limiter=limiter)
+    x = (np.arange(nx) + 0.5) / nx
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * x)
+    U = W.conserved_from(P.gamma, rho, [0.1 * np.ones(nx)], 1.0 / rho, [np.ones(nx), np.zeros(nx)])
+    return P, U.reshape(P.nvar, 1, 1, nx), x
+
+
+def test_translation_keeps_velocity_and_pressure_uniform():
+    """R = 0: a density profile advected at uniform u and p keeps u and p
+    uniform to round-off (HLLC resolves the contact, S* = u)."""
+    P, U, x = _translation_problem(64)
+    o = O.Oracle(P)
+    V = U.copy()
+    for _ in range(20):
+        V, _ = o.step(V, o.cfl_dt(V))
+    u = V[1] / V[0]
+    p = (P.gamma - 1) * (V[2] - 0.5 * V[1] ** 2 / V[0])
+    assert np.abs(u - 0.1).max() < 1e-13
+    assert np.abs(p - 1.0).max() < 1e-13
+
+
+def test_shift_by_one_zone_is_bitwise():
+    """Shifting the initial data by one zone shifts the result by one zone, bitwise."""
+    P, U, x = _translation_problem(32)
+    o = O.Oracle(P)
+    dt = o.cfl_dt(U)
+    V, _ = o.step(U, dt)
+    Us = np.roll(U, 1, axis=-1)
+    Vs, _ = o.step(Us, dt)
+    assert np.array_equal(np.roll(V, 1, axis=-1), Vs)
+    # 3D hot spot, shift along y
+    P3, U3 = W.config_box(n=8, nspec=7, seed=1, T0=0.5)
+    o3 = O.Oracle(P3)
+    dt3 = o3.cfl_dt(U3)
+    V3, _ = o3.step(U3, dt3)
+    V3s, _ = o3.step(np.roll(U3, 1, axis=2), dt3)
+    assert np.array_equal(np.roll(V3, 1, axis=2), V3s)
+
+
+@pytest.mark.parametrize("limiter,order", [(0, 2.0)])
+def test_translation_converges(limiter, order):
+    """R = 0, smooth profile, unlimited PLM: the L1 error against the exactly
+    translated profile (cell averages) falls at second order."""
+    errs = []
+    for nx in (32, 64, 128):
+        P, U, x = _translation_problem(nx, limiter=limiter)
+        o = O.Oracle(P)
+        t, tf = 0.0, 1.0
+        V = U.copy()
+        c = math.sqrt(1.4 * 1.0 / 0.8) + 0.1
+        nsteps = int(math.ceil(tf / (0.4 / nx / c)))
+        dt = tf / nsteps
+        for _ in range(nsteps):
+            V, _ = o.step(V, dt)
+        h = 1.0 / nx
+        xl = np.arange(nx) * h - 0.1 * tf
+        exact = 1.0 + 0.2 * (np.cos(2 * np.pi * xl) - np.cos(2 * np.pi * (xl + h))) / (2 * np.pi * h)
+        errs.append(np.abs(V[0, 0, 0] - exact).mean())
+    r = math.log2(errs[1] / errs[2])
+    assert r == pytest.approx(order, abs=0.25), errs
+
+
+def test_mirror_symmetry():
+    """x -> -x with u -> -u gives the mirrored result to round-off."""
+    P, U = W.config_box(n=8, nspec=7, seed=2, T0=0.5)
+    o = O.Oracle(P)
+    dt = o.cfl_dt(U)
+    V, _ = o.step(U, dt)
+    Um = U[:, :, :, ::-1].copy()
+    Um[1] *= -1
+    Vm, _ = o.step(Um, dt)
+    Vm = Vm[:, :, :, ::-1].copy()
+    Vm[1] *= -1
+    scale = np.abs(V).reshape(P.nvar, -1).max(1)[:, None, None, None] + 1e-300
+    assert np.abs(V - Vm).max() / 1.0 <= 1e-12 * np.abs(V).max()
+    assert np.all(np.abs(V - Vm) <= 1e-12 * scale + 1e-14)
