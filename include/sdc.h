@@ -1,0 +1,163 @@
+/*
+ * sdc.h -- C ABI of libsdc: the data-parallel hot path of the spectral
+ * deferred correction (SDC) coupling of hydrodynamics and reactions of
+ * arXiv:1910.12578 (Castro), section 2, on one NVIDIA GB300 (sm_103a).
+ *
+ * The method (section 2):
+ *   Eq. 1            U_t = A(U) + R(U): A is the divergence of the
+ *                    hydrodynamic fluxes, R the reactive sources.
+ *   Eq. sdc:general  from temporal node m to m+1, iteration k -> k+1,
+ *     U^{m+1,(k+1)} = U^{m,(k+1)} + dt_m [A^{m,(k+1)} - A^{m,(k)}]
+ *                   + dt_m [R^{m+1,(k+1)} - R^{m+1,(k)}]
+ *                   + int_{t^m}^{t^{m+1}} (A^{(k)} + R^{(k)}) dt
+ *   with zone averages, explicit in A and implicit in R (an implicit
+ *   equation for the new state), the integral built from the previous
+ *   iteration at every node: trapezoid rule (2 Gauss-Lobatto nodes) or
+ *   Simpson's rule (3 Gauss-Lobatto nodes).
+ *
+ * Conventions used by every call:
+ *   - Conserved fields, in this order: rho, rho*u_0..rho*u_{dim-1}, rho*E,
+ *     rho*X_0..rho*X_{nspec-1};  nvar = 2 + dim + nspec.
+ *   - Reactive fields (the unknowns of the implicit update and the layout of
+ *     every R array): rho*E, rho*X_0..rho*X_{nspec-1};  n = nspec + 1.
+ *   - Arrays are FP64, field-major and x fastest.  Several boxes are
+ *     concatenated in the order given to sdc_init_box:
+ *         U[f * Ntot + off_b + i + n0*(j + n1*k)],  Ntot = sum of box zones.
+ *   - Every box is periodic on itself; its 2-zone halo is formed on chip
+ *     from its own interior (no ghost storage in memory).
+ *   - All array arguments are DEVICE pointers owned by the caller, 16-byte
+ *     aligned.  The library owns only its workspace (inside the context).
+ *   - Work is enqueued on the CUDA stream given to sdc_init_box (borrowed,
+ *     not owned).  Calls that return host-visible results (stats, dt) wait
+ *     for that stream; the others return after enqueueing.
+ *   - Every call returns a status and never aborts, traps or exits.
+ *   - Not thread safe per context; one GPU (the current device at
+ *     sdc_init_box) per context.
+ */
+#ifndef SDC_H
+#define SDC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sdc_ctx sdc_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    SDC_OK = 0,
+    SDC_ERR_INVALID_ARG = 1,   /* a bad size, pointer, network or parameter */
+    SDC_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
+    SDC_ERR_OOM = 3,           /* workspace allocation failed */
+    SDC_ERR_NEWTON_NOCONV = 4, /* some zones did not converge (best iterate kept) */
+    SDC_ERR_NONPHYSICAL = 5,   /* a zone had no admissible Newton step */
+    SDC_ERR_TIMEOUT = 6        /* a bounded device wait gave up */
+} sdc_status;
+
+typedef enum { SDC_PREC_FP64 = 0, SDC_PREC_FP32_JAC = 1 } sdc_precision;
+
+/* rate laws of the network: r_j = a_j rho^(o_j-1) f_j(T) prod_reactants Y^cnt,
+   Y_i = X_i / mass_i, o_j = total reactant count */
+enum { SDC_RATE_POWER = 0 /* f = T^nu */, SDC_RATE_ARRHENIUS = 1 /* f = exp(-nu/T) */ };
+
+/* per-zone Newton outcome (zone_status arrays) */
+enum { SDC_ZONE_OK = 0, SDC_ZONE_MAXIT = 1, SDC_ZONE_NONPHYSICAL = 2, SDC_ZONE_SINGULAR = 3 };
+
+#define SDC_MAX_SPEC 16
+#define SDC_MAX_REAC 16
+
+/* one periodic box: dim in {1,2,3}, zones per axis (unused axes = 1), widths */
+typedef struct {
+    int dim;
+    int n[3];
+    double dx[3];
+} sdc_box;
+
+/* reaction network (host pointers, copied by sdc_init_box).
+   R(rho X_i) = rho mass_i sum_j s_ij r_j,  R(rho E) = rho sum_j Q_j r_j,
+   s_ij = (prod_j == i) - (reactant multiplicities of i in reaction j). */
+typedef struct {
+    int nspec, nreac, rate_law;
+    const double* mass;   /* [nspec] species mass numbers            */
+    const double* a;      /* [nreac] rate prefactors                 */
+    const double* nu;     /* [nreac] exponent (power) or activation  */
+    const double* Q;      /* [nreac] energy released per unit rate   */
+    const int* reac;      /* [2*nreac] reactant species, -1 = none    */
+    const int* cnt;       /* [2*nreac] reactant multiplicities        */
+    const int* prod;      /* [nreac] product species                  */
+} sdc_network;
+
+typedef struct {
+    double gamma;          /* gamma-law gas, p = rho T                      */
+    int n_nodes;           /* M: 2 (trapezoid) or 3 (Simpson)               */
+    int n_iters;           /* K: SDC iterations per step, >= 1              */
+    int limiter;           /* 1 = MC limited PLM, 0 = unlimited centred PLM */
+    sdc_precision prec;    /* Newton linear algebra precision               */
+    double newton_rtol;    /* scaled Newton update that ends the solve      */
+    int newton_maxit;      /* iteration cap per zone solve                  */
+} sdc_params;
+
+typedef struct {
+    long long newton_iters_total; /* sum over zone solves of the iterations   */
+    long long newton_solves;      /* zone solves                              */
+    long long n_fail;             /* zone solves not converged                */
+    long long hist[64];           /* hist[i]: solves with i iterations (63 = 63+) */
+} sdc_stats;
+
+/* Create a context for nbox boxes with one network and one parameter set,
+   allocate its device workspace and upload the network.
+   Errors: SDC_ERR_INVALID_ARG (nbox < 1, bad dims, nspec > SDC_MAX_SPEC,
+   nreac > SDC_MAX_REAC, species index out of range, n_nodes not 2/3,
+   n_iters < 1, gamma <= 1), SDC_ERR_OOM, SDC_ERR_CUDA.  *out is NULL on error. */
+sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net,
+                        const sdc_params* prm, void* cuda_stream, sdc_ctx** out);
+
+/* A(U): advective term, the divergence of the HLLC fluxes of a method-of-lines
+   PLM reconstruction (MC limiter) of the primitive variables
+   (paper section 2, Eq. 1: "the divergence of the hydrodynamic fluxes").
+   U, A: [nvar][Ntot] device arrays; A may not alias U. */
+sdc_status sdc_advective_term(sdc_ctx* ctx, const double* U, double* A);
+
+/* Node-to-node integral of Eq. sdc:general from node m to m+1 (0 <= m < M-1):
+   I = sum_l q_{m,l} dt (A_l + R_l), q the trapezoid / Simpson weights.
+   A_nodes: [M][nvar][Ntot], R_nodes: [M][n][Ntot] (R enters the reactive
+   fields only), I: [nvar][Ntot]. */
+sdc_status sdc_node_integral(sdc_ctx* ctx, const double* A_nodes, const double* R_nodes,
+                             double dt, int m, double* I);
+
+/* Implicit reaction update of Eq. sdc:general at every zone:
+   solve  w - dt_m R(w; rho, rho u) = rhs_w  for the reactive fields w, with
+   rho and rho*u taken from rhs (R has no mass or momentum component), by
+   Newton iteration on the analytic Jacobian I - dt_m dR/dw (dense LU with
+   partial pivoting) globalised by pseudo-transient continuation.
+   rhs: [nvar][Ntot].  U_inout: [nvar][Ntot], the guess on entry (its mass
+   fractions and specific energy are carried to the density of rhs), the
+   solution on exit.  R_out: [n][Ntot] = R(solution).  zone_status, zone_iters:
+   [Ntot] or NULL.  stats: NULL (asynchronous) or filled after a wait.
+   Returns SDC_ERR_NEWTON_NOCONV when stats is given and some zone failed. */
+sdc_status sdc_react_newton(sdc_ctx* ctx, const double* rhs, double dt_m, double* U_inout,
+                            double* R_out, int* zone_status, int* zone_iters, sdc_stats* stats);
+
+/* One SDC time step of size dt, in place on U ([nvar][Ntot]): every node starts
+   at U^n, then K iterations of the node-to-node sweep of Eq. sdc:general;
+   U^{n+1} = U^{M-1,(K)}.  Replays a CUDA graph captured at the first call for
+   this U pointer.  stats: NULL (asynchronous) or filled after a wait;
+   returns SDC_ERR_NEWTON_NOCONV when stats is given and some zone failed. */
+sdc_status sdc_step(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats);
+
+/* CFL time step: dt = cfl / max over zones of sum_d (|u_d| + c) / dx_d.
+   Waits for the stream; *dt_out is a host pointer. */
+sdc_status sdc_cfl_dt(sdc_ctx* ctx, const double* U, double cfl, double* dt_out);
+
+/* Sizes of the context: total zones, nvar, n (reactive fields). */
+sdc_status sdc_sizes(const sdc_ctx* ctx, long long* ntot, int* nvar, int* nreactive);
+
+/* Release the context and its workspace (NULL is allowed). */
+void sdc_destroy(sdc_ctx* ctx);
+
+/* Static description of a status code. */
+const char* sdc_status_string(sdc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDC_H */

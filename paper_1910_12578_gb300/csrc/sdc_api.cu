@@ -1,0 +1,497 @@
+// sdc_api.cu -- C ABI of libsdc (declared in include/sdc.h): context set-up,
+// the SDC step driver of Eq. sdc:general (paper section 2) captured as a CUDA
+// graph, and the small elementwise kernels of the path.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/sdc.h"
+#include "sdc_launch.h"
+
+using namespace sdcd;
+
+namespace {
+
+constexpr int EW_BLOCK = 256;
+
+__global__ void set_scalar_kernel(double* p, double v) { *p = v; }
+
+// rhs at node 0 (A at node 0 never changes within a step, so its correction is zero):
+//   rhs = U^0 - dtm R^{1,(k)} + sum_l (q_l dt) (A_l + R_l)^{(k)}
+__global__ void rhs_node0_kernel(int nvar, int dim, long long N, const double* __restrict__ U0,
+                                 RhsArgs ra) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)nvar * N) return;
+    const int f = (int)(i / N);
+    const long long z = i - (long long)f * N;
+    const double dt = *ra.dt;
+    const double dtm = dt * ra.dtm_frac;
+    const bool reactive = f >= 1 + dim;
+    const int r = f - 1 - dim;
+    double v = U0[i];
+    if (reactive) v -= dtm * ra.Rnext[r * N + z];
+    double I = 0.0;
+    for (int l = 0; l < ra.M; l++) {
+        double src = ra.Aold[l][i];
+        if (reactive) src += ra.Rold[l][r * N + z];
+        I += (ra.qw[l] * dt) * src;
+    }
+    ra.rhs[i] = v + I;
+}
+
+// I = sum_l (q_l dt) (A_l + R_l)
+__global__ void node_integral_kernel(int nvar, int dim, int M, long long N, const double* __restrict__ A,
+                                     const double* __restrict__ R, double q0, double q1, double q2, double dt,
+                                     double* __restrict__ I) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)nvar * N) return;
+    const int f = (int)(i / N);
+    const long long z = i - (long long)f * N;
+    const int n = nvar - 1 - dim;
+    const bool reactive = f >= 1 + dim;
+    const int r = f - 1 - dim;
+    const double q[3] = {q0, q1, q2};
+    double s = 0.0;
+    for (int l = 0; l < M; l++) {
+        double src = A[(long long)l * nvar * N + i];
+        if (reactive) src += R[(long long)l * n * N + r * N + z];
+        s += (q[l] * dt) * src;
+    }
+    I[i] = s;
+}
+
+// max over zones of sum_d (|u_d| + c) / dx_d; non-negative doubles order like
+// their bit patterns, so the maximum is an unsigned integer atomicMax
+__global__ void cfl_kernel(NetParams P, int dim, int nbox, long long N, const BoxDev* __restrict__ boxes,
+                           const double* __restrict__ U, unsigned long long* __restrict__ out) {
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (z < N) {
+        int lo = 0, hi = nbox - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (boxes[mid].off <= z) lo = mid; else hi = mid - 1;
+        }
+        const BoxDev b = boxes[lo];
+        const double rho = U[z];
+        const double ir = 1.0 / rho;
+        double u[3], ke = 0.0;
+        for (int d = 0; d < dim; d++) {
+            u[d] = U[(1 + d) * N + z] * ir;
+            ke += 0.5 * rho * u[d] * u[d];
+        }
+        const double p = P.gm1 * (U[(1 + dim) * N + z] - ke);
+        const double c = sqrt(P.gamma * p * ir);
+        for (int d = 0; d < dim; d++) s += (fabs(u[d]) + c) * b.idx[d];
+        if (!(s >= 0.0)) s = INFINITY;  // a NaN state gives no usable step
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(s));
+}
+
+inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
+
+}  // namespace
+
+struct sdc_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;      // borrowed
+    cudaStream_t cap_stream = nullptr;  // owned: graph capture
+    int nbox = 0, dim = 0, nspec = 0, nvar = 0, nw = 0;
+    long long Ntot = 0;
+    NetParams P;
+    NewtonCfg cfg;
+    int M = 0, K = 0, limiter = 1, prec = 0;
+    double tau[3] = {0, 0, 0};
+    double q[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    BoxDev* d_boxes = nullptr;
+    TileDev* d_tiles = nullptr;
+    int ntiles = 0;
+    double* d_dt = nullptr;
+    double* node_ws[2] = {nullptr, nullptr};  // node 0 (copy of U^n), node 1 when M = 3
+    double* A0 = nullptr;                     // A at node 0 (fixed within a step)
+    double* R0 = nullptr;
+    double* Ag[2][3] = {{nullptr}};           // two generations of A at nodes 1..M-1
+    double* Rg[2][3] = {{nullptr}};
+    double* rhs = nullptr;
+    DevStats* d_stats = nullptr;
+    unsigned long long* d_smax = nullptr;
+    std::vector<void*> allocs;
+    cudaGraphExec_t gexec = nullptr;
+    double* gU = nullptr;
+};
+
+namespace {
+
+sdc_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return SDC_OK;
+    if (e == cudaErrorMemoryAllocation) return SDC_ERR_OOM;
+    return SDC_ERR_CUDA;
+}
+
+#define SDC_TRY(x)                                   \
+    do {                                             \
+        cudaError_t e_ = (x);                        \
+        if (e_ != cudaSuccess) return cuda_status(e_); \
+    } while (0)
+
+cudaError_t ctx_alloc(sdc_ctx* c, void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) c->allocs.push_back(*p);
+    return e;
+}
+
+bool is_alpha_chain(const sdc_network* net) {
+    if (net->nreac != net->nspec - 1 || net->nspec < 3) return false;
+    for (int j = 0; j < net->nreac; j++) {
+        const int* r = net->reac + 2 * j;
+        const int* c = net->cnt + 2 * j;
+        if (j == 0) {
+            if (!(r[0] == 0 && c[0] == 3 && r[1] < 0 && net->prod[0] == 1)) return false;
+        } else {
+            if (!(r[0] == j && c[0] == 1 && r[1] == 0 && c[1] == 1 && net->prod[j] == j + 1)) return false;
+        }
+    }
+    return true;
+}
+
+void weights(int M, double tau[3], double q[2][3]) {
+    // integrals of the Lagrange basis through the Gauss-Lobatto nodes over
+    // each sub-interval, in units of the step: trapezoid / Simpson halves
+    if (M == 2) {
+        tau[0] = 0.0; tau[1] = 1.0;
+        q[0][0] = 0.5; q[0][1] = 0.5; q[0][2] = 0.0;
+    } else {
+        tau[0] = 0.0; tau[1] = 0.5; tau[2] = 1.0;
+        q[0][0] = 5.0 / 24.0; q[0][1] = 1.0 / 3.0; q[0][2] = -1.0 / 24.0;
+        q[1][0] = -1.0 / 24.0; q[1][1] = 1.0 / 3.0; q[1][2] = 5.0 / 24.0;
+    }
+}
+
+RhsArgs rhs_args(const sdc_ctx* c, const double* const* Aold, const double* const* Rold, int m) {
+    RhsArgs ra;
+    for (int l = 0; l < 3; l++) {
+        ra.Aold[l] = l < c->M ? Aold[l] : nullptr;
+        ra.Rold[l] = l < c->M ? Rold[l] : nullptr;
+        ra.qw[l] = c->q[m][l];
+    }
+    ra.Rnext = Rold[m + 1];
+    ra.Aold_m = Aold[m];
+    ra.rhs = c->rhs;
+    ra.dt = c->d_dt;
+    ra.dtm_frac = c->tau[m + 1] - c->tau[m];
+    ra.M = c->M;
+    return ra;
+}
+
+// Enqueue one SDC step on stream st (dt already in c->d_dt); U is node M-1.
+cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st) {
+    const long long N = c->Ntot;
+    const size_t ubytes = sizeof(double) * c->nvar * N;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->d_stats, 0, sizeof(DevStats), st)) != cudaSuccess) return e;
+    double* node[3] = {c->node_ws[0], c->M == 3 ? c->node_ws[1] : U, U};
+    if ((e = cudaMemcpyAsync(node[0], U, ubytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+    RhsArgs none = rhs_args(c, (const double* const*)c->Ag[0], (const double* const*)c->Rg[0], 0);
+    if ((e = launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles, c->ntiles, node[0], c->A0,
+                            STENCIL_A, none, st)) != cudaSuccess)
+        return e;
+    if ((e = launch_reaction_source(c->P, N, c->dim, node[0], c->R0, st)) != cudaSuccess) return e;
+    const double* Aold[3] = {c->A0, c->A0, c->A0};
+    const double* Rold[3] = {c->R0, c->R0, c->R0};
+    for (int k = 0; k < c->K; k++) {
+        const int g = k & 1;
+        double* Anew[3] = {c->A0, c->Ag[g][1], c->Ag[g][2]};
+        double* Rnew[3] = {c->R0, c->Rg[g][1], c->Rg[g][2]};
+        for (int m = 0; m < c->M - 1; m++) {
+            RhsArgs ra = rhs_args(c, Aold, Rold, m);
+            if (m == 0) {
+                rhs_node0_kernel<<<grid_for((long long)c->nvar * N, EW_BLOCK), EW_BLOCK, 0, st>>>(
+                    c->nvar, c->dim, N, node[0], ra);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            } else {
+                if ((e = launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles, c->ntiles, node[m],
+                                        Anew[m], STENCIL_A_RHS, ra, st)) != cudaSuccess)
+                    return e;
+            }
+            const double* guess = (k == 0) ? node[0] : node[m + 1];
+            if ((e = launch_newton(c->P, c->cfg, c->prec, N, c->dim, c->rhs, guess, node[m + 1], Rnew[m + 1], c->d_dt,
+                                   c->tau[m + 1] - c->tau[m], 0.0, nullptr, nullptr, c->d_stats, st)) != cudaSuccess)
+                return e;
+        }
+        if (k < c->K - 1) {
+            if ((e = launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles, c->ntiles, node[c->M - 1],
+                                    Anew[c->M - 1], STENCIL_A, none, st)) != cudaSuccess)
+                return e;
+        }
+        for (int l = 1; l < c->M; l++) {
+            Aold[l] = Anew[l];
+            Rold[l] = Rnew[l];
+        }
+    }
+    return cudaSuccess;
+}
+
+void stats_to_host(const DevStats& d, sdc_stats* s) {
+    s->newton_iters_total = (long long)d.iters_total;
+    s->newton_solves = (long long)d.solves;
+    s->n_fail = (long long)d.fails;
+    for (int i = 0; i < 64; i++) s->hist[i] = (long long)d.hist[i];
+}
+
+sdc_status read_stats(sdc_ctx* c, sdc_stats* stats) {
+    DevStats h;
+    SDC_TRY(cudaMemcpyAsync(&h, c->d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream));
+    SDC_TRY(cudaStreamSynchronize(c->stream));
+    stats_to_host(h, stats);
+    return stats->n_fail ? SDC_ERR_NEWTON_NOCONV : SDC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sdc_status_string(sdc_status s) {
+    switch (s) {
+        case SDC_OK: return "ok";
+        case SDC_ERR_INVALID_ARG: return "invalid argument";
+        case SDC_ERR_CUDA: return "CUDA error";
+        case SDC_ERR_OOM: return "out of device memory";
+        case SDC_ERR_NEWTON_NOCONV: return "Newton iteration did not converge in some zones";
+        case SDC_ERR_NONPHYSICAL: return "no admissible Newton step in some zones";
+        case SDC_ERR_TIMEOUT: return "bounded device wait expired";
+    }
+    return "unknown status";
+}
+
+void sdc_destroy(sdc_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (void* p : ctx->allocs) cudaFree(p);
+    delete ctx;
+}
+
+sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, const sdc_params* prm,
+                        void* cuda_stream, sdc_ctx** out) {
+    if (!out) return SDC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!boxes || nbox < 1 || !net || !prm) return SDC_ERR_INVALID_ARG;
+    const int dim = boxes[0].dim;
+    if (dim != 1 && dim != 3) return SDC_ERR_INVALID_ARG;
+    long long Ntot = 0;
+    for (int b = 0; b < nbox; b++) {
+        if (boxes[b].dim != dim) return SDC_ERR_INVALID_ARG;
+        for (int d = 0; d < 3; d++) {
+            if (boxes[b].n[d] < 1) return SDC_ERR_INVALID_ARG;
+            if (d >= dim && boxes[b].n[d] != 1) return SDC_ERR_INVALID_ARG;
+            if (d < dim && !(boxes[b].dx[d] > 0.0)) return SDC_ERR_INVALID_ARG;
+        }
+        Ntot += (long long)boxes[b].n[0] * boxes[b].n[1] * boxes[b].n[2];
+    }
+    if (net->nspec < 1 || net->nspec > SDC_MAX_SPEC || net->nreac < 1 || net->nreac > SDC_MAX_REAC)
+        return SDC_ERR_INVALID_ARG;
+    if (!net->mass || !net->a || !net->nu || !net->Q || !net->reac || !net->cnt || !net->prod)
+        return SDC_ERR_INVALID_ARG;
+    if (net->rate_law != SDC_RATE_POWER && net->rate_law != SDC_RATE_ARRHENIUS) return SDC_ERR_INVALID_ARG;
+    for (int j = 0; j < net->nreac; j++) {
+        for (int s = 0; s < 2; s++) {
+            const int sp = net->reac[2 * j + s];
+            if (sp >= net->nspec || sp < -1) return SDC_ERR_INVALID_ARG;
+            if (sp >= 0 && (net->cnt[2 * j + s] < 1 || net->cnt[2 * j + s] > 3)) return SDC_ERR_INVALID_ARG;
+        }
+        if (net->reac[2 * j] < 0) return SDC_ERR_INVALID_ARG;
+        if (net->reac[2 * j] == net->reac[2 * j + 1]) return SDC_ERR_INVALID_ARG;
+        if (net->prod[j] < 0 || net->prod[j] >= net->nspec) return SDC_ERR_INVALID_ARG;
+    }
+    if (!(prm->gamma > 1.0) || (prm->n_nodes != 2 && prm->n_nodes != 3) || prm->n_iters < 1 ||
+        prm->newton_maxit < 1 || !(prm->newton_rtol > 0.0) ||
+        (prm->prec != SDC_PREC_FP64 && prm->prec != SDC_PREC_FP32_JAC))
+        return SDC_ERR_INVALID_ARG;
+    const int topo = is_alpha_chain(net) ? TOPO_CHAIN : TOPO_GENERIC;
+    int topo_used = topo;
+    if (!newton_supported(net->nspec, topo_used)) {
+        topo_used = TOPO_GENERIC;
+        if (!newton_supported(net->nspec, topo_used)) return SDC_ERR_INVALID_ARG;
+    }
+    // the per-thread rate arrays hold nspec - 1 reactions
+    if (net->nreac > net->nspec - 1) return SDC_ERR_INVALID_ARG;
+    if (!stencil_supported(dim, net->nspec)) return SDC_ERR_INVALID_ARG;
+
+    sdc_ctx* c = new (std::nothrow) sdc_ctx();
+    if (!c) return SDC_ERR_OOM;
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&c->device);
+    c->nbox = nbox;
+    c->dim = dim;
+    c->nspec = net->nspec;
+    c->nvar = 2 + dim + net->nspec;
+    c->nw = net->nspec + 1;
+    c->Ntot = Ntot;
+    c->M = prm->n_nodes;
+    c->K = prm->n_iters;
+    c->limiter = prm->limiter ? 1 : 0;
+    c->prec = prm->prec;
+    c->cfg.rtol = prm->newton_rtol;
+    c->cfg.maxit = prm->newton_maxit;
+    weights(c->M, c->tau, c->q);
+    NetParams& P = c->P;
+    memset(&P, 0, sizeof(P));
+    P.nspec = net->nspec;
+    P.nreac = net->nreac;
+    P.law = net->rate_law;
+    P.topo = topo_used;
+    P.gamma = prm->gamma;
+    P.gm1 = prm->gamma - 1.0;
+    for (int i = 0; i < net->nspec; i++) P.mass[i] = net->mass[i];
+    for (int j = 0; j < net->nreac; j++) {
+        P.a[j] = net->a[j];
+        P.nu[j] = net->nu[j];
+        P.Q[j] = net->Q[j];
+        P.r0[j] = net->reac[2 * j];
+        P.c0[j] = net->cnt[2 * j];
+        P.r1[j] = net->reac[2 * j + 1];
+        P.c1[j] = net->reac[2 * j + 1] >= 0 ? net->cnt[2 * j + 1] : 0;
+        P.prod[j] = net->prod[j];
+        P.order[j] = P.c0[j] + P.c1[j];
+    }
+
+    // boxes and stencil tiles
+    std::vector<BoxDev> hb(nbox);
+    std::vector<TileDev> ht;
+    int tl[3];
+    stencil_tile(dim, tl);
+    long long off = 0;
+    for (int b = 0; b < nbox; b++) {
+        hb[b].off = off;
+        for (int d = 0; d < 3; d++) {
+            hb[b].n[d] = boxes[b].n[d];
+            hb[b].idx[d] = d < dim ? 1.0 / boxes[b].dx[d] : 0.0;
+        }
+        off += (long long)boxes[b].n[0] * boxes[b].n[1] * boxes[b].n[2];
+        for (int z = 0; z < boxes[b].n[2]; z += tl[2])
+            for (int y = 0; y < boxes[b].n[1]; y += tl[1])
+                for (int x = 0; x < boxes[b].n[0]; x += tl[0]) ht.push_back(TileDev{b, {x, y, z}});
+    }
+    c->ntiles = (int)ht.size();
+
+    sdc_status st = SDC_OK;
+    auto fail = [&](cudaError_t e) {
+        sdc_destroy(c);
+        return cuda_status(e);
+    };
+    cudaError_t e;
+    if ((e = stencil_prepare(dim, net->nspec)) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+    if ((e = ctx_alloc(c, (void**)&c->d_boxes, sizeof(BoxDev) * nbox)) != cudaSuccess) return fail(e);
+    if ((e = ctx_alloc(c, (void**)&c->d_tiles, sizeof(TileDev) * ht.size())) != cudaSuccess) return fail(e);
+    if ((e = ctx_alloc(c, (void**)&c->d_dt, sizeof(double))) != cudaSuccess) return fail(e);
+    if ((e = ctx_alloc(c, (void**)&c->d_stats, sizeof(DevStats))) != cudaSuccess) return fail(e);
+    if ((e = ctx_alloc(c, (void**)&c->d_smax, sizeof(unsigned long long))) != cudaSuccess) return fail(e);
+    const size_t ub = sizeof(double) * c->nvar * Ntot, rb = sizeof(double) * c->nw * Ntot;
+    if ((e = ctx_alloc(c, (void**)&c->node_ws[0], ub)) != cudaSuccess) return fail(e);
+    if (c->M == 3 && (e = ctx_alloc(c, (void**)&c->node_ws[1], ub)) != cudaSuccess) return fail(e);
+    if ((e = ctx_alloc(c, (void**)&c->A0, ub)) != cudaSuccess) return fail(e);
+    if ((e = ctx_alloc(c, (void**)&c->R0, rb)) != cudaSuccess) return fail(e);
+    if ((e = ctx_alloc(c, (void**)&c->rhs, ub)) != cudaSuccess) return fail(e);
+    for (int g = 0; g < 2; g++)
+        for (int m = 1; m < c->M; m++) {
+            if ((e = ctx_alloc(c, (void**)&c->Ag[g][m], ub)) != cudaSuccess) return fail(e);
+            if ((e = ctx_alloc(c, (void**)&c->Rg[g][m], rb)) != cudaSuccess) return fail(e);
+        }
+    if ((e = cudaMemcpy(c->d_boxes, hb.data(), sizeof(BoxDev) * nbox, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaMemcpy(c->d_tiles, ht.data(), sizeof(TileDev) * ht.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaMemset(c->d_stats, 0, sizeof(DevStats))) != cudaSuccess) return fail(e);
+    (void)st;
+    *out = c;
+    return SDC_OK;
+}
+
+sdc_status sdc_sizes(const sdc_ctx* ctx, long long* ntot, int* nvar, int* nreactive) {
+    if (!ctx) return SDC_ERR_INVALID_ARG;
+    if (ntot) *ntot = ctx->Ntot;
+    if (nvar) *nvar = ctx->nvar;
+    if (nreactive) *nreactive = ctx->nw;
+    return SDC_OK;
+}
+
+sdc_status sdc_advective_term(sdc_ctx* ctx, const double* U, double* A) {
+    if (!ctx || !U || !A || U == A) return SDC_ERR_INVALID_ARG;
+    RhsArgs none;
+    memset(&none, 0, sizeof(none));
+    SDC_TRY(launch_stencil(ctx->P, ctx->dim, ctx->limiter, ctx->Ntot, ctx->d_boxes, ctx->d_tiles, ctx->ntiles, U, A,
+                           STENCIL_A, none, ctx->stream));
+    return SDC_OK;
+}
+
+sdc_status sdc_node_integral(sdc_ctx* ctx, const double* A_nodes, const double* R_nodes, double dt, int m,
+                             double* I) {
+    if (!ctx || !A_nodes || !R_nodes || !I || m < 0 || m >= ctx->M - 1) return SDC_ERR_INVALID_ARG;
+    const long long n = (long long)ctx->nvar * ctx->Ntot;
+    node_integral_kernel<<<grid_for(n, EW_BLOCK), EW_BLOCK, 0, ctx->stream>>>(
+        ctx->nvar, ctx->dim, ctx->M, ctx->Ntot, A_nodes, R_nodes, ctx->q[m][0], ctx->q[m][1], ctx->q[m][2], dt, I);
+    SDC_TRY(cudaGetLastError());
+    return SDC_OK;
+}
+
+sdc_status sdc_react_newton(sdc_ctx* ctx, const double* rhs, double dt_m, double* U_inout, double* R_out,
+                            int* zone_status, int* zone_iters, sdc_stats* stats) {
+    if (!ctx || !rhs || !U_inout || !R_out || rhs == U_inout) return SDC_ERR_INVALID_ARG;
+    if (stats) SDC_TRY(cudaMemsetAsync(ctx->d_stats, 0, sizeof(DevStats), ctx->stream));
+    SDC_TRY(launch_newton(ctx->P, ctx->cfg, ctx->prec, ctx->Ntot, ctx->dim, rhs, U_inout, U_inout, R_out, nullptr,
+                          1.0, dt_m, zone_status, zone_iters, ctx->d_stats, ctx->stream));
+    if (stats) return read_stats(ctx, stats);
+    return SDC_OK;
+}
+
+sdc_status sdc_step(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats) {
+    if (!ctx || !U || !(dt > 0.0)) return SDC_ERR_INVALID_ARG;
+    if (!ctx->gexec || ctx->gU != U) {
+        if (ctx->gexec) {
+            cudaGraphExecDestroy(ctx->gexec);
+            ctx->gexec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        SDC_TRY(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue_step(ctx, U, ctx->cap_stream);
+        cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_status(e != cudaSuccess ? e : e2);
+        }
+        e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            ctx->gexec = nullptr;
+            return cuda_status(e);
+        }
+        ctx->gU = U;
+    }
+    set_scalar_kernel<<<1, 1, 0, ctx->stream>>>(ctx->d_dt, dt);
+    SDC_TRY(cudaGetLastError());
+    SDC_TRY(cudaGraphLaunch(ctx->gexec, ctx->stream));
+    if (stats) return read_stats(ctx, stats);
+    return SDC_OK;
+}
+
+sdc_status sdc_cfl_dt(sdc_ctx* ctx, const double* U, double cfl, double* dt_out) {
+    if (!ctx || !U || !dt_out || !(cfl > 0.0)) return SDC_ERR_INVALID_ARG;
+    SDC_TRY(cudaMemsetAsync(ctx->d_smax, 0, sizeof(unsigned long long), ctx->stream));
+    cfl_kernel<<<grid_for(ctx->Ntot, EW_BLOCK), EW_BLOCK, 0, ctx->stream>>>(ctx->P, ctx->dim, ctx->nbox, ctx->Ntot,
+                                                                           ctx->d_boxes, U, ctx->d_smax);
+    SDC_TRY(cudaGetLastError());
+    unsigned long long bits = 0;
+    SDC_TRY(cudaMemcpyAsync(&bits, ctx->d_smax, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream));
+    SDC_TRY(cudaStreamSynchronize(ctx->stream));
+    double smax;
+    memcpy(&smax, &bits, sizeof(smax));
+    if (!(smax > 0.0) || !(smax < INFINITY)) return SDC_ERR_NONPHYSICAL;
+    *dt_out = cfl / smax;
+    return SDC_OK;
+}
+
+}  // extern "C"

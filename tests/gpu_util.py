@@ -1,0 +1,61 @@
+"""Helpers shared by the GPU parity tests (tests only)."""
+import numpy as np
+
+import oracle as O
+
+
+def rel_err(gpu, orc, nvar, dim, species_floor=1e-6):
+    """Per-field relative infinity-norm error; species fields are taken
+    relative to max(|rho X_i|_inf, species_floor * |rho|_inf)."""
+    g = np.asarray(gpu).reshape(nvar, -1)
+    o = np.asarray(orc).reshape(nvar, -1)
+    rho_max = np.abs(o[0]).max()
+    out = []
+    for f in range(nvar):
+        den = np.abs(o[f]).max()
+        if f >= 2 + dim:
+            den = max(den, species_floor * rho_max)
+        den = max(den, 1e-300)
+        out.append(np.abs(g[f] - o[f]).max() / den)
+    return np.array(out)
+
+
+def rel_err_R(gpu, orc, n, scale):
+    g = np.asarray(gpu).reshape(n, -1)
+    o = np.asarray(orc).reshape(n, -1)
+    return np.array([np.abs(g[r] - o[r]).max() / max(np.abs(o[r]).max(), scale) for r in range(n)])
+
+
+def oracle_sweep_inputs(o, U, dt, k_iters=1, m_target=None):
+    """Run the oracle sweep in Python from its building blocks and return the
+    (rhs, guess, dt_m) seen by the Newton solve at the last (k, m) visited."""
+    P = o.P
+    M = P.n_nodes
+    dim = P.dim
+    tau = [0.0, 1.0] if M == 2 else [0.0, 0.5, 1.0]
+    Un = [U.copy() for _ in range(M)]
+    A0 = o.advective(U)
+    R0 = o.reaction_source(U)
+    Aold = [A0] * M
+    Rold = [R0] * M
+    last = None
+    for k in range(k_iters):
+        Anew = [A0] + [None] * (M - 1)
+        Rnew = [R0] + [None] * (M - 1)
+        for m in range(M - 1):
+            dtm = dt * (tau[m + 1] - tau[m])
+            Anew[m] = A0 if m == 0 else o.advective(Un[m])
+            I = o.node_integral(Aold, Rold, dt, m)
+            rhs = Un[m] + dtm * (Anew[m] - Aold[m])
+            rhs[1 + dim:] -= dtm * Rold[m + 1]
+            rhs = rhs + I
+            last = (rhs.copy(), Un[m + 1].copy(), dtm)
+            if m_target is not None and m == m_target and k == k_iters - 1:
+                return last
+            Unew, Rn, zs, zi, st = o.react_newton(rhs, dtm, Un[m + 1])
+            Un[m + 1] = Unew
+            Rnew[m + 1] = Rn
+        if k < k_iters - 1:
+            Anew[M - 1] = o.advective(Un[M - 1])
+        Aold, Rold = Anew, Rnew
+    return last

@@ -1,0 +1,205 @@
+"""GPU (libsdc, sm_103a) against the FP64 CPU oracle, element by element, on
+the same seeded inputs, through the C ABI.
+
+Tolerances: FP64 path 1e-12 relative per field (species relative to
+max(|rho X_i|_inf, 1e-6 |rho|_inf)); FP32-Jacobian path 1e-9.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1910_12578_gb300 import workloads as W
+
+from gpu_util import oracle_sweep_inputs, rel_err, rel_err_R
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-9
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1910_12578_gb300 import build
+    build.build()
+    return torch
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def problems():
+    out = {}
+    P, U = W.config_1d()
+    out["1d"] = (P, U)
+    P, U = W.config_box(n=16, nspec=7, seed=0, T0=0.5)
+    out["box16"] = (P, U)
+    P, U = W.config_box(n=16, nspec=7, seed=1, T0=0.5)
+    P.n = (24, 16, 12)   # ragged box: not a multiple of the 8x8x4 tile along y? (16 yes, 12 partial)
+    P.dx = (1 / 24, 1 / 16, 1 / 12)
+    out["ragged"] = (P, W.hot_spot_state(P, 2.0, T0=0.5))
+    return out
+
+
+PROBS = problems()
+
+
+@pytest.mark.parametrize("name", ["1d", "box16", "ragged"])
+def test_advective_term_parity(torch_cuda, name):
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = PROBS[name]
+    o = O.Oracle(P)
+    A_orc = o.advective(U)
+    ctx = sdc.Context(P)
+    Ud = dev(torch, U)
+    Ad = torch.empty_like(Ud)
+    ctx.advective_term(Ud, Ad)
+    torch.cuda.synchronize()
+    A_gpu = Ad.cpu().numpy()
+    scale = np.abs(A_orc).reshape(P.nvar, -1).max(1)
+    err = np.abs(A_gpu - A_orc).reshape(P.nvar, -1).max(1) / np.maximum(scale, 1e-12 * scale.max())
+    assert err.max() <= TOL64, err
+
+
+@pytest.mark.parametrize("name", ["1d", "box16"])
+def test_node_integral_parity(torch_cuda, name):
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = PROBS[name]
+    o = O.Oracle(P)
+    rng = np.random.default_rng(5)
+    M = P.n_nodes
+    A = [rng.standard_normal(U.shape) for _ in range(M)]
+    R = [rng.standard_normal((P.net.nspec + 1,) + U.shape[1:]) for _ in range(M)]
+    ctx = sdc.Context(P)
+    Ad = dev(torch, np.stack(A))
+    Rd = dev(torch, np.stack(R))
+    for m in range(M - 1):
+        I_orc = o.node_integral(A, R, 0.01, m)
+        Id = torch.empty(U.shape, dtype=torch.float64, device="cuda")
+        ctx.node_integral(Ad, Rd, 0.01, m, Id)
+        torch.cuda.synchronize()
+        assert np.abs(Id.cpu().numpy() - I_orc).max() <= 1e-15 * np.abs(I_orc).max()
+
+
+@pytest.mark.parametrize("name,k_iters,prec", [("1d", 1, 0), ("1d", 2, 0), ("box16", 1, 0), ("box16", 2, 0),
+                                               ("box16", 2, 1), ("ragged", 2, 0)])
+def test_react_newton_parity(torch_cuda, name, k_iters, prec):
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = PROBS[name]
+    o = O.Oracle(P)
+    dt = o.cfl_dt(U)
+    rhs, guess, dtm = oracle_sweep_inputs(o, U, dt, k_iters=k_iters)
+    Uo, Ro, zs_o, zi_o, st_o = o.react_newton(rhs, dtm, guess)
+    ctx = sdc.Context(P, prec=prec)
+    rd = dev(torch, rhs)
+    Ud = dev(torch, guess)
+    Rd = torch.empty((P.net.nspec + 1,) + U.shape[1:], dtype=torch.float64, device="cuda")
+    zs = torch.empty(U.shape[1:], dtype=torch.int32, device="cuda")
+    zi = torch.empty(U.shape[1:], dtype=torch.int32, device="cuda")
+    st = ctx.react_newton(rd, dtm, Ud, Rd, zs, zi)
+    torch.cuda.synchronize()
+    tol = TOL64 if prec == 0 else TOL32
+    e = rel_err(Ud.cpu().numpy(), Uo, P.nvar, P.dim)
+    assert e.max() <= tol, e
+    eR = rel_err_R(Rd.cpu().numpy(), Ro, P.net.nspec + 1, 1e-6 * np.abs(Ro).max())
+    assert eR.max() <= (1e-9 if prec == 0 else 1e-6), eR
+    assert np.array_equal(zs.cpu().numpy(), zs_o) or prec == 1
+    assert st.n_fail == st_o.n_fail or prec == 1
+    assert st.newton_solves == P.nzones
+    if prec == 0:
+        # iteration counts agree except where a stop test sat on the threshold
+        assert np.mean(zi.cpu().numpy() == zi_o) > 0.99
+
+
+@pytest.mark.parametrize("name,nsteps,prec", [("1d", 10, 0), ("box16", 2, 0), ("box16", 1, 1), ("ragged", 1, 0)])
+def test_step_parity(torch_cuda, name, nsteps, prec):
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = PROBS[name]
+    o = O.Oracle(P)
+    Uo, dts, sts = o.run(U, nsteps)
+    ctx = sdc.Context(P, prec=prec)
+    Ud = dev(torch, U)
+    fails = 0
+    for dt in dts:
+        st = ctx.step(Ud, dt)
+        fails += st.n_fail
+    torch.cuda.synchronize()
+    tol = TOL64 if prec == 0 else TOL32
+    e = rel_err(Ud.cpu().numpy(), Uo, P.nvar, P.dim)
+    assert e.max() <= tol, e
+    assert fails == sum(s.n_fail for s in sts) or prec == 1
+
+
+def test_step_is_deterministic(torch_cuda):
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = PROBS["box16"]
+    outs = []
+    for _ in range(2):
+        ctx = sdc.Context(P)
+        Ud = dev(torch, U)
+        ctx.step(Ud, 1e-3)
+        ctx.step(Ud, 1e-3)
+        outs.append(Ud.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_cfl_dt_matches_oracle(torch_cuda):
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    for name in ["1d", "box16", "ragged"]:
+        P, U = PROBS[name]
+        o = O.Oracle(P)
+        ctx = sdc.Context(P)
+        assert ctx.cfl_dt(dev(torch, U), 0.5) == pytest.approx(o.cfl_dt(U, 0.5), rel=1e-14)
+
+
+def test_batched_boxes_match_per_box_oracle(torch_cuda):
+    """Ragged boxes in one context: each box equals the oracle run on it alone."""
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    net, boxes = W.batched_boxes(nbox=4, nspec=7, seed=3, edges=(8, 16, 24))
+    Ps = [b[0] for b in boxes]
+    for P in Ps:
+        P.n_iters = 2
+    Ucat = np.concatenate([b[1].reshape(P.nvar, -1) for P, b in zip(Ps, boxes)], axis=1)
+    dt = min(O.Oracle(P).cfl_dt(b[1]) for P, b in zip(Ps, boxes))
+    ctx = sdc.Context(Ps)
+    Ud = dev(torch, Ucat)
+    ctx.step(Ud, dt)
+    torch.cuda.synchronize()
+    G = Ud.cpu().numpy()
+    off = 0
+    for P, b in zip(Ps, boxes):
+        Uo, _ = O.Oracle(P).step(b[1], dt)
+        nz = P.nzones
+        e = rel_err(G[:, off:off + nz], Uo.reshape(P.nvar, -1), P.nvar, P.dim)
+        assert e.max() <= TOL64, e
+        off += nz
+
+
+def test_full_size_config_step_parity(torch_cuda):
+    """64^3, 7 species, 3 Gauss-Lobatto nodes, 3 iterations: one full step at
+    the size the benchmark times, every zone compared with the oracle."""
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = W.config_box(n=64, nspec=7, seed=1, T0=0.5)
+    o = O.Oracle(P)
+    dt = o.cfl_dt(U)
+    Uo, st_o = o.step(U, dt)
+    for prec, tol in ((0, TOL64), (1, TOL32)):
+        ctx = sdc.Context(P, prec=prec)
+        Ud = dev(torch, U)
+        st = ctx.step(Ud, dt)
+        torch.cuda.synchronize()
+        e = rel_err(Ud.cpu().numpy(), Uo, P.nvar, P.dim)
+        assert e.max() <= tol, (prec, e)
+        assert st.newton_solves == st_o.newton_solves
