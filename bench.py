@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""Throughput of the SDC hydro + reaction hot path on GB300.
+
+Metric: zone-node-iterations/s = zones x (M-1) x K per SDC step / time, one
+unit being one zone's node m -> m+1 update in one SDC iteration (advective term,
+right-hand side and implicit reaction solve).  A step is one sdc_step (CUDA
+graph) over the whole box from the same seeded initial state.
+
+Default workload: 64^3 periodic box, 7-species alpha chain, 3 Gauss-Lobatto
+nodes, 3 SDC iterations, FP64.  Inputs are resident in HBM when the timed
+region starts; L2 is flushed (256 MB write) before every timed step.
+
+Usage:
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|fp32jac]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+Under torchrun each rank runs its own box (independent problems, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1910_12578_gb300 import workloads as W  # noqa: E402
+
+METRIC = "zone-node-iterations/s on 1 GB300 at stated FP64-oracle error; % of roofline"
+UNIT = "zone-node-iterations/s"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--config", choices=["box64", "box256"], default="box64")
+    p.add_argument("--prec", choices=["fp64", "fp32jac"], default="fp64")
+    p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload(name, seed):
+    if name == "box64":
+        P, U = W.config_box(n=64, nspec=7, n_nodes=3, n_iters=3, seed=seed, T0=0.5)
+        desc = ("64^3 periodic box, 7-species alpha chain (seeded), hot spot 2x over T0=0.5, "
+                "3 Gauss-Lobatto nodes, 3 SDC iterations, CFL 0.5")
+    else:
+        P, U = W.config_box(n=256, nspec=13, n_nodes=3, n_iters=4, seed=seed, T0=0.5)
+        desc = ("256^3 periodic box, 13-species alpha chain (seeded), hot spot 2x over T0=0.5, "
+                "3 Gauss-Lobatto nodes, 4 SDC iterations, CFL 0.5")
+    return P, U, desc
+
+
+def units_per_step(P):
+    return P.nzones * (P.n_nodes - 1) * P.n_iters
+
+
+def newton_flops_per_iter(nspec):
+    """Algorithmic flops of one Newton / pseudo-time iteration of one zone
+    (alpha chain, n = nspec + 1 unknowns, nspec - 1 reactions):
+      state evaluation  9 (n_r) + 3 nspec + 5 n   (rate constants and their T
+                                                  derivative, sources, residual, norm)
+      Jacobian / matrix 14 n_r + n
+      LU, partial pivot 2n^3/3 - n^2/2 - n/6 + n  (multiply-add = 2, n reciprocals)
+      two triangular solves 2 n^2 - n
+      update and tests  3 n
+    The transcendental calls (1 log, n_r exp per evaluation) are not counted."""
+    n, nr = nspec + 1, nspec - 1
+    ev = 9 * nr + 3 * nspec + 5 * n
+    jac = 14 * nr + n
+    lu = 2 * n ** 3 / 3 - n ** 2 / 2 - n / 6 + n
+    sol = 2 * n ** 2 - n
+    return ev, jac + lu + sol, 3 * n
+
+
+def stencil_bytes_per_zone(P, rhs_mode):
+    nv, n, M = P.nvar, P.net.nspec + 1, P.n_nodes
+    if not rhs_mode:
+        return 8 * 2 * nv                               # read U, write A
+    return 8 * ((1 + 1 + 1 + M + 1) * nv + (M + 1) * n)  # U, A new, A old m, A old l, rhs; R old l, R next
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """The FP64 CPU oracle, as it stands, on the host cores: each step is one
+    full SDC step of the same workload."""
+    ws, rank, _ = dist()
+    if rank != 0:
+        return 0
+    import oracle as O
+    P, U, desc = workload(args.config, args.seed)
+    if args.config == "box256":
+        # bounded sample: a 64^3 box with the same network and parameters
+        P, U = W.config_box(n=64, nspec=13, n_nodes=3, n_iters=4, seed=args.seed, T0=0.5)
+        desc += " (sample: 64^3 box, same network)"
+    o = O.Oracle(P)
+    dt = o.cfl_dt(U)
+    for _ in range(args.warmup):
+        o.step(U, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(U, dt)
+    el = time.perf_counter() - t0
+    v = units_per_step(P) * args.steps / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "zones": P.nzones, "nspec": P.net.nspec, "nodes": P.n_nodes,
+                       "iters": P.n_iters, "seed": args.seed},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d full SDC steps of the workload, OpenMP over zones" % args.steps},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_and_error(P, U, dt, gpu_out, target_s=10.0, max_steps=4):
+    """The oracle as it stands on the host cores (bounded sample: whole SDC steps
+    of the workload until ~10 s of CPU work), plus the error of the GPU step
+    against it (this leg is the only one that runs the oracle)."""
+    import numpy as np
+    import oracle as O
+    o = O.Oracle(P)
+    t0 = time.perf_counter()
+    Uo, _ = o.step(U, dt)
+    steps = 1
+    while time.perf_counter() - t0 < target_s and steps < max_steps:
+        o.step(U, dt)
+        steps += 1
+    el = time.perf_counter() - t0
+    g = gpu_out.reshape(P.nvar, -1)
+    r = Uo.reshape(P.nvar, -1)
+    rho_max = np.abs(r[0]).max()
+    errs = {}
+    names = ["rho"] + ["mom%d" % d for d in range(P.dim)] + ["rhoE"] + ["X%d" % i for i in range(P.net.nspec)]
+    for f in range(P.nvar):
+        den = np.abs(r[f]).max()
+        if f >= 2 + P.dim:
+            den = max(den, 1e-6 * rho_max)
+        errs[names[f]] = float(np.abs(g[f] - r[f]).max() / max(den, 1e-300))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return ({"value": units_per_step(P) * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+             "sample": "%d full SDC step(s) of the workload from the initial state, OpenMP over zones" % steps},
+            {"max_rel": max(errs.values()), "per_field": errs})
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1910_12578_gb300 import build as B
+    from paper_1910_12578_gb300 import sdc
+
+    ws, rank, local = dist()
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if not os.path.exists(sdc.LIB_PATH):
+        B.build()
+    P, U, desc = workload(args.config, args.seed + rank)
+    prec = sdc.PREC_FP64 if args.prec == "fp64" else sdc.PREC_FP32_JAC
+    ctx = sdc.Context(P, prec=prec)
+    U0 = torch.from_numpy(U).cuda()
+    Ud = torch.empty_like(U0)
+    dt = ctx.cfl_dt(U0, P.cfl)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    units = units_per_step(P)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # warm-up (also captures the graph)
+    for _ in range(max(args.warmup, 1)):
+        Ud.copy_(U0)
+        ctx.step(Ud, dt, stats=False)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, each from the same initial state, L2 flushed before each
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    for i, (a, b) in enumerate(evs):
+        Ud.copy_(U0)
+        flush.fill_(i & 0xFF)
+        a.record()
+        ctx.step(Ud, dt, stats=False)
+        b.record()
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = units * args.steps * ws / (total_ms * 1e-3)
+
+    # ---- end to end through the public API with host buffers (pinned), copies timed
+    Uh = U0.cpu().pin_memory()
+    Uout = torch.empty_like(Uh).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    Ud.copy_(U0)
+    ctx.step(Ud, dt, stats=False)
+    torch.cuda.synchronize()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ea.record()
+    for _ in range(e2e_steps):
+        Ud.copy_(Uh, non_blocking=True)
+        ctx.step(Ud, dt, stats=False)
+        Uout.copy_(Ud, non_blocking=True)
+    eb.record()
+    torch.cuda.synchronize()
+    e2e_ms = ea.elapsed_time(eb) / e2e_steps
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    nbytes = U0.numel() * 8
+
+    # ---- per-kernel-class times of the same step (eager launches, CUDA events on the context stream)
+    Ud.copy_(U0)
+    st, pr = ctx.step_profile(Ud, dt)
+    Ud.copy_(U0)
+    st2 = ctx.step(Ud, dt, stats=True)
+    torch.cuda.synchronize()
+    gpu_out = Ud.cpu().numpy()
+    ev_f, lin_f, upd_f = newton_flops_per_iter(P.net.nspec)
+    iters = st.newton_iters_total
+    newton_ms_launch = pr.ms_newton / max(pr.launches_newton, 1)
+    if prec == sdc.PREC_FP64:
+        fp64_flops = iters * (ev_f + lin_f + upd_f)
+        fp32_flops = 0
+    else:
+        fp64_flops = iters * (ev_f + upd_f)
+        fp32_flops = iters * lin_f
+    achieved = fp64_flops / max(pr.launches_newton, 1) / (newton_ms_launch * 1e-3) / 1e12
+    roof = {"kernel": "newton_kernel (implicit reaction update)", "bound": "alu",
+            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (recipe unit counts and clock; "
+                           "an FMA-chain probe measured 1.256 TFLOP/s)",
+            "flops_per_launch": fp64_flops / max(pr.launches_newton, 1), "ms_per_launch": newton_ms_launch,
+            "newton_iters_per_solve": iters / max(st.newton_solves, 1)}
+    if fp32_flops:
+        roof["fp32_achieved"] = fp32_flops / max(pr.launches_newton, 1) / (newton_ms_launch * 1e-3) / 1e12
+        roof["fp32_peak"] = FP32_PEAK_TFLOPS
+    n_st = pr.launches_stencil
+    st_bytes = P.nzones * (stencil_bytes_per_zone(P, False) * P.n_iters +
+                           stencil_bytes_per_zone(P, True) * (P.n_nodes - 2) * P.n_iters) / max(n_st, 1)
+    stencil_ms = pr.ms_stencil / max(n_st, 1)
+    hbm_peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm_peak = json.load(f).get("hbm_gbs")
+    except (OSError, ValueError):
+        pass
+    hbm_peak = hbm_peak or 6800.0
+    st_gbs = st_bytes / (stencil_ms * 1e-3) / 1e9
+    roof_st = {"kernel": "stencil_kernel (advective term + fused rhs)", "bound": "hbm", "achieved": st_gbs,
+               "peak": hbm_peak, "unit": "GB/s", "frac": st_gbs / hbm_peak, "traffic": None,
+               "bytes_per_launch": st_bytes, "ms_per_launch": stencil_ms}
+
+    line = None
+    if rank == 0:
+        cpu, err = (None, None)
+        if ws == 1 and not args.no_cpu_baseline:
+            cpu, err = cpu_baseline_and_error(P, U, dt, gpu_out)
+        per_step = ctx.launches_per_step()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == sdc.PREC_FP64 else "f64 residual/update, f32 Jacobian/LU",
+            "data": "synthetic",
+            "config": {"workload": desc, "zones": P.nzones, "nspec": P.net.nspec, "nodes": P.n_nodes,
+                       "iters": P.n_iters, "prec": args.prec, "seed": args.seed,
+                       "l2": "flushed before every timed step (256 MB write)",
+                       "parallelism": "independent box per GPU" if ws > 1 else "1 GPU"},
+            "clocks": ck,
+            "e2e": {"value": units * ws / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes},
+            "gpu_launches": per_step * args.steps,
+            "roofline": roof,
+            "roofline_stencil": roof_st,
+            "profile_ms": {"stencil": pr.ms_stencil, "newton": pr.ms_newton, "other": pr.ms_other,
+                           "launches": [pr.launches_stencil, pr.launches_newton, pr.launches_other]},
+            "newton": {"iters_total": st2.newton_iters_total, "solves": st2.newton_solves,
+                       "fails": st2.n_fail},
+            "cpu_baseline": cpu,
+            "oracle_error": err,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

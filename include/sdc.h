@@ -144,6 +144,20 @@ sdc_status sdc_react_newton(sdc_ctx* ctx, const double* rhs, double dt_m, double
    returns SDC_ERR_NEWTON_NOCONV when stats is given and some zone failed. */
 sdc_status sdc_step(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats);
 
+/* Per-class CUDA-event times of one eagerly launched step. */
+typedef struct {
+    int launches_stencil, launches_newton, launches_other;
+    float ms_stencil, ms_newton, ms_other; /* summed event durations of those launches */
+} sdc_profile;
+
+/* sdc_step without the graph: the same kernels with the same arguments (same
+   results), each launch bracketed by CUDA events on the context stream, for
+   measurement.  Waits for the stream.  stats as in sdc_step. */
+sdc_status sdc_step_profile(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats, sdc_profile* prof);
+
+/* Number of kernels one sdc_step launches (its graph plus the dt store). */
+sdc_status sdc_launches_per_step(const sdc_ctx* ctx, int* launches);
+
 /* CFL time step: dt = cfl / max over zones of sum_d (|u_d| + c) / dx_d.
    Waits for the stream; *dt_out is a host pointer. */
 sdc_status sdc_cfl_dt(sdc_ctx* ctx, const double* U, double cfl, double* dt_out);

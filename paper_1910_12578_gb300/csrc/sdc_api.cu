@@ -93,6 +93,35 @@ __global__ void cfl_kernel(NetParams P, int dim, int nbox, long long N, const Bo
 
 inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
 
+// Event pairs bracketing each launch of an eagerly enqueued step.
+enum { CLS_STENCIL = 0, CLS_NEWTON = 1, CLS_OTHER = 2 };
+struct Prof {
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> cls;
+    cudaStream_t st = nullptr;
+    cudaError_t mark() {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        ev.push_back(e);
+        return cudaEventRecord(e, st);
+    }
+    ~Prof() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
+// record an event before and after a launch when profiling
+#define SDC_LAUNCH(prof, klass, call)                                      \
+    do {                                                                   \
+        if (prof && (e = prof->mark()) != cudaSuccess) return e;           \
+        if ((e = (call)) != cudaSuccess) return e;                         \
+        if (prof) {                                                        \
+            if ((e = prof->mark()) != cudaSuccess) return e;               \
+            prof->cls.push_back(klass);                                    \
+        }                                                                  \
+    } while (0)
+
 }  // namespace
 
 struct sdc_ctx {
@@ -187,7 +216,8 @@ RhsArgs rhs_args(const sdc_ctx* c, const double* const* Aold, const double* cons
 }
 
 // Enqueue one SDC step on stream st (dt already in c->d_dt); U is node M-1.
-cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st) {
+// With prof, every kernel launch is bracketed by events (eager profiling).
+cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nullptr) {
     const long long N = c->Ntot;
     const size_t ubytes = sizeof(double) * c->nvar * N;
     cudaError_t e;
@@ -195,10 +225,9 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st) {
     double* node[3] = {c->node_ws[0], c->M == 3 ? c->node_ws[1] : U, U};
     if ((e = cudaMemcpyAsync(node[0], U, ubytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
     RhsArgs none = rhs_args(c, (const double* const*)c->Ag[0], (const double* const*)c->Rg[0], 0);
-    if ((e = launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles, c->ntiles, node[0], c->A0,
-                            STENCIL_A, none, st)) != cudaSuccess)
-        return e;
-    if ((e = launch_reaction_source(c->P, N, c->dim, node[0], c->R0, st)) != cudaSuccess) return e;
+    SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles, c->ntiles,
+                                                 node[0], c->A0, STENCIL_A, none, st));
+    SDC_LAUNCH(prof, CLS_OTHER, launch_reaction_source(c->P, N, c->dim, node[0], c->R0, st));
     const double* Aold[3] = {c->A0, c->A0, c->A0};
     const double* Rold[3] = {c->R0, c->R0, c->R0};
     for (int k = 0; k < c->K; k++) {
@@ -208,23 +237,22 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st) {
         for (int m = 0; m < c->M - 1; m++) {
             RhsArgs ra = rhs_args(c, Aold, Rold, m);
             if (m == 0) {
-                rhs_node0_kernel<<<grid_for((long long)c->nvar * N, EW_BLOCK), EW_BLOCK, 0, st>>>(
-                    c->nvar, c->dim, N, node[0], ra);
-                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                SDC_LAUNCH(prof, CLS_OTHER, (rhs_node0_kernel<<<grid_for((long long)c->nvar * N, EW_BLOCK), EW_BLOCK, 0,
+                                                                 st>>>(c->nvar, c->dim, N, node[0], ra),
+                                             cudaGetLastError()));
             } else {
-                if ((e = launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles, c->ntiles, node[m],
-                                        Anew[m], STENCIL_A_RHS, ra, st)) != cudaSuccess)
-                    return e;
+                SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles,
+                                                             c->ntiles, node[m], Anew[m], STENCIL_A_RHS, ra, st));
             }
             const double* guess = (k == 0) ? node[0] : node[m + 1];
-            if ((e = launch_newton(c->P, c->cfg, c->prec, N, c->dim, c->rhs, guess, node[m + 1], Rnew[m + 1], c->d_dt,
-                                   c->tau[m + 1] - c->tau[m], 0.0, nullptr, nullptr, c->d_stats, st)) != cudaSuccess)
-                return e;
+            SDC_LAUNCH(prof, CLS_NEWTON, launch_newton(c->P, c->cfg, c->prec, N, c->dim, c->rhs, guess, node[m + 1],
+                                                       Rnew[m + 1], c->d_dt, c->tau[m + 1] - c->tau[m], 0.0, nullptr,
+                                                       nullptr, c->d_stats, st));
         }
         if (k < c->K - 1) {
-            if ((e = launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles, c->ntiles, node[c->M - 1],
-                                    Anew[c->M - 1], STENCIL_A, none, st)) != cudaSuccess)
-                return e;
+            SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles,
+                                                         c->ntiles, node[c->M - 1], Anew[c->M - 1], STENCIL_A, none,
+                                                         st));
         }
         for (int l = 1; l < c->M; l++) {
             Aold[l] = Anew[l];
@@ -475,6 +503,35 @@ sdc_status sdc_step(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats) {
     SDC_TRY(cudaGetLastError());
     SDC_TRY(cudaGraphLaunch(ctx->gexec, ctx->stream));
     if (stats) return read_stats(ctx, stats);
+    return SDC_OK;
+}
+
+sdc_status sdc_step_profile(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats, sdc_profile* prof) {
+    if (!ctx || !U || !(dt > 0.0) || !prof) return SDC_ERR_INVALID_ARG;
+    memset(prof, 0, sizeof(*prof));
+    Prof P;
+    P.st = ctx->stream;
+    set_scalar_kernel<<<1, 1, 0, ctx->stream>>>(ctx->d_dt, dt);
+    SDC_TRY(cudaGetLastError());
+    SDC_TRY(enqueue_step(ctx, U, ctx->stream, &P));
+    SDC_TRY(cudaStreamSynchronize(ctx->stream));
+    for (size_t i = 0; i < P.cls.size(); i++) {
+        float ms = 0.0f;
+        SDC_TRY(cudaEventElapsedTime(&ms, P.ev[2 * i], P.ev[2 * i + 1]));
+        if (P.cls[i] == CLS_STENCIL) { prof->launches_stencil++; prof->ms_stencil += ms; }
+        else if (P.cls[i] == CLS_NEWTON) { prof->launches_newton++; prof->ms_newton += ms; }
+        else { prof->launches_other++; prof->ms_other += ms; }
+    }
+    prof->launches_other++;  // the kernel that stores dt
+    if (stats) return read_stats(ctx, stats);
+    return SDC_OK;
+}
+
+sdc_status sdc_launches_per_step(const sdc_ctx* ctx, int* launches) {
+    if (!ctx || !launches) return SDC_ERR_INVALID_ARG;
+    // dt store, A(U^n), R(U^n), per iteration and node a rhs kernel and a Newton
+    // kernel, and A at the last node for every iteration but the last
+    *launches = 3 + ctx->K * 2 * (ctx->M - 1) + (ctx->K - 1);
     return SDC_OK;
 }
 

@@ -22,7 +22,8 @@ PREC_FP64, PREC_FP32_JAC = 0, 1
 
 # entry points declared in include/sdc.h
 EXPORTS = ["sdc_init_box", "sdc_advective_term", "sdc_node_integral", "sdc_react_newton", "sdc_step",
-           "sdc_cfl_dt", "sdc_sizes", "sdc_destroy", "sdc_status_string"]
+           "sdc_step_profile", "sdc_launches_per_step", "sdc_cfl_dt", "sdc_sizes", "sdc_destroy",
+           "sdc_status_string"]
 
 
 class SdcError(RuntimeError):
@@ -56,6 +57,14 @@ class Stats(C.Structure):
                 "n_fail": self.n_fail, "hist": list(self.hist)}
 
 
+class Profile(C.Structure):
+    _fields_ = [("launches_stencil", C.c_int), ("launches_newton", C.c_int), ("launches_other", C.c_int),
+                ("ms_stencil", C.c_float), ("ms_newton", C.c_float), ("ms_other", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -77,13 +86,15 @@ def load(path: str = LIB_PATH):
     L.sdc_react_newton.argtypes = [vp, dp, C.c_double, dp, dp, vp, vp, C.POINTER(Stats)]
     L.sdc_step.argtypes = [vp, dp, C.c_double, C.POINTER(Stats)]
     L.sdc_cfl_dt.argtypes = [vp, dp, C.c_double, C.POINTER(C.c_double)]
+    L.sdc_step_profile.argtypes = [vp, dp, C.c_double, C.POINTER(Stats), C.POINTER(Profile)]
+    L.sdc_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
     L.sdc_sizes.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.sdc_destroy.argtypes = [vp]
     L.sdc_destroy.restype = None
     L.sdc_status_string.argtypes = [C.c_int]
     L.sdc_status_string.restype = C.c_char_p
     for name in ("sdc_init_box", "sdc_advective_term", "sdc_node_integral", "sdc_react_newton", "sdc_step",
-                 "sdc_cfl_dt", "sdc_sizes"):
+                 "sdc_cfl_dt", "sdc_sizes", "sdc_step_profile", "sdc_launches_per_step"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -190,6 +201,20 @@ class Context:
         s = self.L.sdc_step(self._h, _ptr(U), float(dt), C.byref(st) if st is not None else None)
         self._check(s, "sdc_step", allow_noconv=True)
         return st
+
+    def step_profile(self, U, dt):
+        """One eagerly launched step (same kernels and results as step) with
+        per-class CUDA-event times; returns (Stats, Profile)."""
+        st = Stats()
+        pr = Profile()
+        s = self.L.sdc_step_profile(self._h, _ptr(U), float(dt), C.byref(st), C.byref(pr))
+        self._check(s, "sdc_step_profile", allow_noconv=True)
+        return st, pr
+
+    def launches_per_step(self):
+        n = C.c_int()
+        self._check(self.L.sdc_launches_per_step(self._h, C.byref(n)), "sdc_launches_per_step")
+        return n.value
 
     def cfl_dt(self, U, cfl):
         out = C.c_double()
