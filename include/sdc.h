@@ -50,7 +50,8 @@ typedef enum {
     SDC_ERR_OOM = 3,           /* workspace allocation failed */
     SDC_ERR_NEWTON_NOCONV = 4, /* some zones did not converge (best iterate kept) */
     SDC_ERR_NONPHYSICAL = 5,   /* a zone had no admissible Newton step */
-    SDC_ERR_TIMEOUT = 6        /* a bounded device wait gave up */
+    SDC_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+    SDC_ERR_TOO_LARGE = 7      /* the problem does not fit the fixed scratch of sdc_step_static */
 } sdc_status;
 
 typedef enum { SDC_PREC_FP64 = 0, SDC_PREC_FP32_JAC = 1 } sdc_precision;
@@ -164,6 +165,34 @@ sdc_status sdc_cfl_dt(sdc_ctx* ctx, const double* U, double cfl, double* dt_out)
 
 /* Sizes of the context: total zones, nvar, n (reactive fields). */
 sdc_status sdc_sizes(const sdc_ctx* ctx, long long* ntot, int* nvar, int* nreactive);
+
+/* One SDC step that allocates nothing (the paper has no counterpart: this is a
+   convenience of this library).  It is meant for callers that cannot call
+   cudaMalloc: code running under an allocator or memory budget that another
+   framework owns, hosts that forbid device allocations after start-up, or
+   code that must not trigger the implicit synchronisation of an allocation.
+   Same arguments and results as sdc_init_box + sdc_step + sdc_destroy (the
+   same kernels, launched eagerly on cuda_stream), but the whole workspace
+   (node states, A and R of two iterations, the rhs, box and tile tables, dt,
+   statistics) lives in one file-scope device array of SDC_STATIC_SCRATCH_BYTES
+   that every GPU loading the library holds until the process exits.
+   - Capacity: (8 + 2(M-1))*nvar + (1 + 2(M-1))*n doubles per zone plus the
+     tables must fit in SDC_STATIC_SCRATCH_BYTES (48 MiB: e.g. 32^3 zones with
+     7 species and 3 nodes); larger problems return SDC_ERR_TOO_LARGE before
+     any work is enqueued; at most SDC_STATIC_MAX_BOXES boxes.
+   - The first call on a device looks up the array's device address with
+     cudaGetSymbolAddress (that device current); make that first call before
+     any stream capture.
+   - All calls share the array and it keeps the last call's contents (the
+     statistics are cleared by every call).  Calls whose work overlaps on the
+     GPU (other streams, other threads) race on it: serialise them.
+   - stats: NULL (asynchronous) or filled after waiting for cuda_stream;
+     SDC_ERR_NEWTON_NOCONV as in sdc_step.
+   It calls no cudaMalloc, cudaFree or other allocating routine. */
+#define SDC_STATIC_SCRATCH_BYTES (48ull << 20)
+#define SDC_STATIC_MAX_BOXES 32
+sdc_status sdc_step_static(const sdc_box* boxes, int nbox, const sdc_network* net, const sdc_params* prm,
+                           void* cuda_stream, double* U, double dt, sdc_stats* stats);
 
 /* Release the context and its workspace (NULL is allowed). */
 void sdc_destroy(sdc_ctx* ctx);

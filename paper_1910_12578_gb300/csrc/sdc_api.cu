@@ -290,6 +290,7 @@ const char* sdc_status_string(sdc_status s) {
         case SDC_ERR_NEWTON_NOCONV: return "Newton iteration did not converge in some zones";
         case SDC_ERR_NONPHYSICAL: return "no admissible Newton step in some zones";
         case SDC_ERR_TIMEOUT: return "bounded device wait expired";
+        case SDC_ERR_TOO_LARGE: return "problem exceeds the static scratch of sdc_step_static (48 MiB)";
     }
     return "unknown status";
 }
@@ -552,3 +553,210 @@ sdc_status sdc_cfl_dt(sdc_ctx* ctx, const double* U, double cfl, double* dt_out)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// sdc_step_static: one SDC step whose workspace lives in a fixed device array,
+// for callers that cannot allocate device memory.  In host code the array's
+// name is only a host-side stand-in: its device address comes from
+// cudaGetSymbolAddress, looked up once per device with that device current.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+static __device__ __align__(256) unsigned char g_static_scratch[SDC_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int STATIC_MAX_DEVICES = 64;
+std::mutex g_static_mutex;
+void* g_static_ptr[STATIC_MAX_DEVICES] = {nullptr};
+
+// device address of the scratch array on the current device
+cudaError_t static_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= STATIC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return cudaSuccess;
+}
+
+struct StaticTables {
+    int nbox;
+    int t[3];                                   // stencil tile
+    long long off[SDC_STATIC_MAX_BOXES];
+    int n[SDC_STATIC_MAX_BOXES][3];
+    double idx[SDC_STATIC_MAX_BOXES][3];
+    int tile_first[SDC_STATIC_MAX_BOXES + 1];   // prefix sum of tiles per box
+};
+
+// box table and tile list written into the scratch array
+__global__ void static_tables_kernel(StaticTables T, BoxDev* boxes, TileDev* tiles) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < T.nbox) {
+        boxes[i].off = T.off[i];
+        for (int d = 0; d < 3; d++) {
+            boxes[i].n[d] = T.n[i][d];
+            boxes[i].idx[d] = T.idx[i][d];
+        }
+    }
+    if (i >= T.tile_first[T.nbox]) return;
+    int b = 0;
+    while (b + 1 < T.nbox && T.tile_first[b + 1] <= i) b++;
+    const int local = i - T.tile_first[b];
+    const int nx = (T.n[b][0] + T.t[0] - 1) / T.t[0], ny = (T.n[b][1] + T.t[1] - 1) / T.t[1];
+    TileDev td;
+    td.box = b;
+    td.o[0] = (local % nx) * T.t[0];
+    td.o[1] = ((local / nx) % ny) * T.t[1];
+    td.o[2] = (local / (nx * ny)) * T.t[2];
+    tiles[i] = td;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" sdc_status sdc_step_static(const sdc_box* boxes, int nbox, const sdc_network* net, const sdc_params* prm,
+                                      void* cuda_stream, double* U, double dt, sdc_stats* stats) {
+    if (!boxes || nbox < 1 || nbox > SDC_STATIC_MAX_BOXES || !net || !prm || !U || !(dt > 0.0))
+        return SDC_ERR_INVALID_ARG;
+    const int dim = boxes[0].dim;
+    if (dim != 1 && dim != 3) return SDC_ERR_INVALID_ARG;
+    if (net->nspec < 1 || net->nspec > SDC_MAX_SPEC || net->nreac < 1 || net->nreac > net->nspec - 1)
+        return SDC_ERR_INVALID_ARG;
+    if (!net->mass || !net->a || !net->nu || !net->Q || !net->reac || !net->cnt || !net->prod)
+        return SDC_ERR_INVALID_ARG;
+    if (net->rate_law != SDC_RATE_POWER && net->rate_law != SDC_RATE_ARRHENIUS) return SDC_ERR_INVALID_ARG;
+    for (int j = 0; j < net->nreac; j++) {
+        for (int s = 0; s < 2; s++) {
+            const int sp = net->reac[2 * j + s];
+            if (sp >= net->nspec || sp < -1) return SDC_ERR_INVALID_ARG;
+            if (sp >= 0 && (net->cnt[2 * j + s] < 1 || net->cnt[2 * j + s] > 3)) return SDC_ERR_INVALID_ARG;
+        }
+        if (net->reac[2 * j] < 0 || net->reac[2 * j] == net->reac[2 * j + 1]) return SDC_ERR_INVALID_ARG;
+        if (net->prod[j] < 0 || net->prod[j] >= net->nspec) return SDC_ERR_INVALID_ARG;
+    }
+    if (!(prm->gamma > 1.0) || (prm->n_nodes != 2 && prm->n_nodes != 3) || prm->n_iters < 1 ||
+        prm->newton_maxit < 1 || !(prm->newton_rtol > 0.0) ||
+        (prm->prec != SDC_PREC_FP64 && prm->prec != SDC_PREC_FP32_JAC))
+        return SDC_ERR_INVALID_ARG;
+    int topo = is_alpha_chain(net) ? TOPO_CHAIN : TOPO_GENERIC;
+    if (!newton_supported(net->nspec, topo)) {
+        topo = TOPO_GENERIC;
+        if (!newton_supported(net->nspec, topo)) return SDC_ERR_INVALID_ARG;
+    }
+    if (!stencil_supported(dim, net->nspec)) return SDC_ERR_INVALID_ARG;
+
+    // tables and sizes (stack only)
+    StaticTables T;
+    memset(&T, 0, sizeof(T));
+    T.nbox = nbox;
+    stencil_tile(dim, T.t);
+    long long Ntot = 0;
+    for (int b = 0; b < nbox; b++) {
+        if (boxes[b].dim != dim) return SDC_ERR_INVALID_ARG;
+        for (int d = 0; d < 3; d++) {
+            if (boxes[b].n[d] < 1 || (d >= dim && boxes[b].n[d] != 1)) return SDC_ERR_INVALID_ARG;
+            if (d < dim && !(boxes[b].dx[d] > 0.0)) return SDC_ERR_INVALID_ARG;
+            T.n[b][d] = boxes[b].n[d];
+            T.idx[b][d] = d < dim ? 1.0 / boxes[b].dx[d] : 0.0;
+        }
+        T.off[b] = Ntot;
+        Ntot += (long long)boxes[b].n[0] * boxes[b].n[1] * boxes[b].n[2];
+        const long long nt = (long long)((boxes[b].n[0] + T.t[0] - 1) / T.t[0]) *
+                             ((boxes[b].n[1] + T.t[1] - 1) / T.t[1]) * ((boxes[b].n[2] + T.t[2] - 1) / T.t[2]);
+        if ((long long)T.tile_first[b] + nt > (1ll << 30)) return SDC_ERR_TOO_LARGE;
+        T.tile_first[b + 1] = T.tile_first[b] + (int)nt;
+    }
+    const int nvar = 2 + dim + net->nspec, nw = net->nspec + 1, M = prm->n_nodes;
+    const size_t ub = sizeof(double) * (size_t)nvar * Ntot, rb = sizeof(double) * (size_t)nw * Ntot;
+    size_t off = 0;
+    const size_t o_dt = off; off = align256(off + sizeof(double));
+    const size_t o_stats = off; off = align256(off + sizeof(DevStats));
+    const size_t o_boxes = off; off = align256(off + sizeof(BoxDev) * nbox);
+    const size_t o_tiles = off; off = align256(off + sizeof(TileDev) * (size_t)T.tile_first[nbox]);
+    size_t o_node[2], o_A0, o_R0, o_rhs, o_Ag[2][3] = {{0}}, o_Rg[2][3] = {{0}};
+    o_node[0] = off; off = align256(off + ub);
+    o_node[1] = off; if (M == 3) off = align256(off + ub);
+    o_A0 = off; off = align256(off + ub);
+    o_R0 = off; off = align256(off + rb);
+    o_rhs = off; off = align256(off + ub);
+    for (int g = 0; g < 2; g++)
+        for (int m = 1; m < M; m++) {
+            o_Ag[g][m] = off; off = align256(off + ub);
+            o_Rg[g][m] = off; off = align256(off + rb);
+        }
+    if (off > SDC_STATIC_SCRATCH_BYTES) return SDC_ERR_TOO_LARGE;
+
+    unsigned char* base = nullptr;
+    SDC_TRY(static_scratch((void**)&base));
+    SDC_TRY(stencil_prepare(dim, net->nspec));
+
+    // a context on the stack whose pointers all lie inside the scratch array
+    sdc_ctx c;
+    c.stream = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&c.device);
+    c.nbox = nbox;
+    c.dim = dim;
+    c.nspec = net->nspec;
+    c.nvar = nvar;
+    c.nw = nw;
+    c.Ntot = Ntot;
+    c.M = M;
+    c.K = prm->n_iters;
+    c.limiter = prm->limiter ? 1 : 0;
+    c.prec = prm->prec;
+    c.cfg.rtol = prm->newton_rtol;
+    c.cfg.maxit = prm->newton_maxit;
+    weights(M, c.tau, c.q);
+    NetParams& P = c.P;
+    memset(&P, 0, sizeof(P));
+    P.nspec = net->nspec;
+    P.nreac = net->nreac;
+    P.law = net->rate_law;
+    P.topo = topo;
+    P.gamma = prm->gamma;
+    P.gm1 = prm->gamma - 1.0;
+    for (int i = 0; i < net->nspec; i++) P.mass[i] = net->mass[i];
+    for (int j = 0; j < net->nreac; j++) {
+        P.a[j] = net->a[j];
+        P.nu[j] = net->nu[j];
+        P.Q[j] = net->Q[j];
+        P.r0[j] = net->reac[2 * j];
+        P.c0[j] = net->cnt[2 * j];
+        P.r1[j] = net->reac[2 * j + 1];
+        P.c1[j] = net->reac[2 * j + 1] >= 0 ? net->cnt[2 * j + 1] : 0;
+        P.prod[j] = net->prod[j];
+        P.order[j] = P.c0[j] + P.c1[j];
+    }
+    c.d_dt = (double*)(base + o_dt);
+    c.d_stats = (DevStats*)(base + o_stats);
+    c.d_boxes = (BoxDev*)(base + o_boxes);
+    c.d_tiles = (TileDev*)(base + o_tiles);
+    c.ntiles = T.tile_first[nbox];
+    c.node_ws[0] = (double*)(base + o_node[0]);
+    c.node_ws[1] = M == 3 ? (double*)(base + o_node[1]) : nullptr;
+    c.A0 = (double*)(base + o_A0);
+    c.R0 = (double*)(base + o_R0);
+    c.rhs = (double*)(base + o_rhs);
+    for (int g = 0; g < 2; g++)
+        for (int m = 1; m < M; m++) {
+            c.Ag[g][m] = (double*)(base + o_Ag[g][m]);
+            c.Rg[g][m] = (double*)(base + o_Rg[g][m]);
+        }
+    const int nt = c.ntiles > nbox ? c.ntiles : nbox;
+    static_tables_kernel<<<grid_for(nt, EW_BLOCK), EW_BLOCK, 0, c.stream>>>(T, c.d_boxes, c.d_tiles);
+    SDC_TRY(cudaGetLastError());
+    set_scalar_kernel<<<1, 1, 0, c.stream>>>(c.d_dt, dt);
+    SDC_TRY(cudaGetLastError());
+    SDC_TRY(enqueue_step(&c, U, c.stream));
+    if (stats) return read_stats(&c, stats);
+    return SDC_OK;
+}

@@ -17,13 +17,14 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libsdc.so")
 
 SDC_OK, SDC_ERR_INVALID_ARG, SDC_ERR_CUDA, SDC_ERR_OOM, SDC_ERR_NEWTON_NOCONV, SDC_ERR_NONPHYSICAL, \
-    SDC_ERR_TIMEOUT = range(7)
+    SDC_ERR_TIMEOUT, SDC_ERR_TOO_LARGE = range(8)
+STATIC_SCRATCH_BYTES = 48 << 20
 PREC_FP64, PREC_FP32_JAC = 0, 1
 
 # entry points declared in include/sdc.h
 EXPORTS = ["sdc_init_box", "sdc_advective_term", "sdc_node_integral", "sdc_react_newton", "sdc_step",
            "sdc_step_profile", "sdc_launches_per_step", "sdc_cfl_dt", "sdc_sizes", "sdc_destroy",
-           "sdc_status_string"]
+           "sdc_status_string", "sdc_step_static"]
 
 
 class SdcError(RuntimeError):
@@ -88,13 +89,15 @@ def load(path: str = LIB_PATH):
     L.sdc_cfl_dt.argtypes = [vp, dp, C.c_double, C.POINTER(C.c_double)]
     L.sdc_step_profile.argtypes = [vp, dp, C.c_double, C.POINTER(Stats), C.POINTER(Profile)]
     L.sdc_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
+    L.sdc_step_static.argtypes = [C.POINTER(Box), C.c_int, C.POINTER(Network), C.POINTER(Params), vp, dp,
+                                  C.c_double, C.POINTER(Stats)]
     L.sdc_sizes.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.sdc_destroy.argtypes = [vp]
     L.sdc_destroy.restype = None
     L.sdc_status_string.argtypes = [C.c_int]
     L.sdc_status_string.restype = C.c_char_p
     for name in ("sdc_init_box", "sdc_advective_term", "sdc_node_integral", "sdc_react_newton", "sdc_step",
-                 "sdc_cfl_dt", "sdc_sizes", "sdc_step_profile", "sdc_launches_per_step"):
+                 "sdc_cfl_dt", "sdc_sizes", "sdc_step_profile", "sdc_launches_per_step", "sdc_step_static"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -220,6 +223,49 @@ class Context:
         out = C.c_double()
         self._check(self.L.sdc_cfl_dt(self._h, _ptr(U), float(cfl), C.byref(out)), "sdc_cfl_dt")
         return out.value
+
+
+def _marshal(problems, prec):
+    """Box array, network and parameter structs (plus the arrays they point into)."""
+    if not isinstance(problems, (list, tuple)):
+        problems = [problems]
+    boxes = (Box * len(problems))()
+    for i, p in enumerate(problems):
+        boxes[i].dim = p.dim
+        for d in range(3):
+            boxes[i].n[d] = int(p.n[d])
+            boxes[i].dx[d] = float(p.dx[d])
+    P0 = problems[0]
+    net = P0.net
+    keep = [np.ascontiguousarray(net.mass, dtype=np.float64), np.ascontiguousarray(net.a, dtype=np.float64),
+            np.ascontiguousarray(net.nu, dtype=np.float64), np.ascontiguousarray(net.Q, dtype=np.float64),
+            np.ascontiguousarray(net.reac, dtype=np.int32).ravel(),
+            np.ascontiguousarray(net.cnt, dtype=np.int32).ravel(), np.ascontiguousarray(net.prod, dtype=np.int32)]
+    m, a, nu, Q, reac, cnt, prod = keep
+    nw = Network(net.nspec, net.nreac, net.rate_law,
+                 m.ctypes.data_as(C.POINTER(C.c_double)), a.ctypes.data_as(C.POINTER(C.c_double)),
+                 nu.ctypes.data_as(C.POINTER(C.c_double)), Q.ctypes.data_as(C.POINTER(C.c_double)),
+                 reac.ctypes.data_as(C.POINTER(C.c_int)), cnt.ctypes.data_as(C.POINTER(C.c_int)),
+                 prod.ctypes.data_as(C.POINTER(C.c_int)))
+    prm = Params(P0.gamma, P0.n_nodes, P0.n_iters, P0.limiter, int(prec), P0.newton_rtol, P0.newton_maxit)
+    return boxes, len(problems), nw, prm, keep
+
+
+def step_static(problems, U, dt, prec=PREC_FP64, stream=None, stats=True):
+    """One SDC step through sdc_step_static: no device allocation by the
+    library (its workspace is a fixed 48 MiB device array shared by all calls
+    in the process; calls that overlap on the GPU race)."""
+    import torch
+    L = load()
+    boxes, nbox, nw, prm, keep = _marshal(problems, prec)
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    st = Stats() if stats else None
+    s = L.sdc_step_static(boxes, nbox, C.byref(nw), C.byref(prm), C.c_void_p(stream.cuda_stream), _ptr(U),
+                          float(dt), C.byref(st) if st is not None else None)
+    del keep
+    if s not in (SDC_OK, SDC_ERR_NEWTON_NOCONV):
+        raise SdcError(s, "sdc_step_static")
+    return st
 
 
 def init_box(problems, prec=PREC_FP64, stream=None) -> Context:
