@@ -93,6 +93,14 @@ __global__ void cfl_kernel(NetParams P, int dim, int nbox, long long N, const Bo
 
 inline unsigned grid_for(long long n, int block) { return (unsigned)((n + block - 1) / block); }
 
+__global__ void selftest_math_kernel(const double* __restrict__ x, long long n, double* __restrict__ r,
+                                     double* __restrict__ q) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    r[i] = rcp_nr(x[i]);
+    q[i] = sqrt_nr(x[i]);
+}
+
 // Event pairs bracketing each launch of an eagerly enqueued step.
 enum { CLS_STENCIL = 0, CLS_NEWTON = 1, CLS_OTHER = 2 };
 struct Prof {
@@ -374,7 +382,10 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     P.topo = topo_used;
     P.gamma = prm->gamma;
     P.gm1 = prm->gamma - 1.0;
-    for (int i = 0; i < net->nspec; i++) P.mass[i] = net->mass[i];
+    for (int i = 0; i < net->nspec; i++) {
+        P.mass[i] = net->mass[i];
+        P.inv_mass[i] = 1.0 / net->mass[i];
+    }
     for (int j = 0; j < net->nreac; j++) {
         P.a[j] = net->a[j];
         P.nu[j] = net->nu[j];
@@ -391,7 +402,7 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     std::vector<BoxDev> hb(nbox);
     std::vector<TileDev> ht;
     int tl[3];
-    stencil_tile(dim, tl);
+    stencil_tile(dim, net->nspec, tl);
     long long off = 0;
     for (int b = 0; b < nbox; b++) {
         hb[b].off = off;
@@ -528,6 +539,14 @@ sdc_status sdc_step_profile(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats
     return SDC_OK;
 }
 
+sdc_status sdc_selftest_math(const double* x, long long n, double* rcp_out, double* sqrt_out, void* cuda_stream) {
+    if (!x || !rcp_out || !sqrt_out || n < 0) return SDC_ERR_INVALID_ARG;
+    if (n == 0) return SDC_OK;
+    selftest_math_kernel<<<grid_for(n, EW_BLOCK), EW_BLOCK, 0, (cudaStream_t)cuda_stream>>>(x, n, rcp_out, sqrt_out);
+    SDC_TRY(cudaGetLastError());
+    return SDC_OK;
+}
+
 sdc_status sdc_launches_per_step(const sdc_ctx* ctx, int* launches) {
     if (!ctx || !launches) return SDC_ERR_INVALID_ARG;
     // dt store, A(U^n), R(U^n), per iteration and node a rhs kernel and a Newton
@@ -658,7 +677,7 @@ extern "C" sdc_status sdc_step_static(const sdc_box* boxes, int nbox, const sdc_
     StaticTables T;
     memset(&T, 0, sizeof(T));
     T.nbox = nbox;
-    stencil_tile(dim, T.t);
+    stencil_tile(dim, net->nspec, T.t);
     long long Ntot = 0;
     for (int b = 0; b < nbox; b++) {
         if (boxes[b].dim != dim) return SDC_ERR_INVALID_ARG;
@@ -724,7 +743,10 @@ extern "C" sdc_status sdc_step_static(const sdc_box* boxes, int nbox, const sdc_
     P.topo = topo;
     P.gamma = prm->gamma;
     P.gm1 = prm->gamma - 1.0;
-    for (int i = 0; i < net->nspec; i++) P.mass[i] = net->mass[i];
+    for (int i = 0; i < net->nspec; i++) {
+        P.mass[i] = net->mass[i];
+        P.inv_mass[i] = 1.0 / net->mass[i];
+    }
     for (int j = 0; j < net->nreac; j++) {
         P.a[j] = net->a[j];
         P.nu[j] = net->nu[j];

@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sdc_fastmath.cuh"
+
 #define SDCD_MAXS 16
 #define SDCD_MAXR 16
 
@@ -24,6 +26,7 @@ struct NetParams {
     double gm1;                          // gamma - 1
     double gamma;
     double mass[SDCD_MAXS];
+    double inv_mass[SDCD_MAXS];
     double a[SDCD_MAXR], nu[SDCD_MAXR], Q[SDCD_MAXR];
     int r0[SDCD_MAXR], c0[SDCD_MAXR], r1[SDCD_MAXR], c1[SDCD_MAXR], prod[SDCD_MAXR];
     int order[SDCD_MAXR];                // sum of reactant multiplicities
@@ -61,7 +64,7 @@ template <int NR>
 __device__ __forceinline__ void rate_consts(const NetParams& P, double rho, double T, double* k, double* dk) {
     if (P.law == LAW_POWER) {
         const double lT = log(T);
-        const double iT = 1.0 / T;
+        const double iT = rcp_nr(T);
 #pragma unroll
         for (int j = 0; j < NR; j++) {
             double rp = ipow_small(rho, P.order[j] - 1);
@@ -70,7 +73,7 @@ __device__ __forceinline__ void rate_consts(const NetParams& P, double rho, doub
             dk[j] = P.nu[j] * kk * iT;
         }
     } else {
-        const double iT = 1.0 / T;
+        const double iT = rcp_nr(T);
 #pragma unroll
         for (int j = 0; j < NR; j++) {
             double rp = ipow_small(rho, P.order[j] - 1);
@@ -125,9 +128,9 @@ __device__ __forceinline__ void sources(const NetParams& P, double rho, const do
 // M = c I - dtm dR/dw, built from the rate constants (no transcendentals).
 // dT/d(rho E) = (gamma-1)/rho;  dY_i/d(rho X_i) = 1/(rho mass_i).
 template <int NS, int TOPO, typename MT>
-__device__ __forceinline__ void build_matrix(const NetParams& P, double rho, double inv_rho, const double* k,
-                                             const double* dk, const double* Y, double c, double dtm,
-                                             MT (*M)[NS + 1]) {
+__device__ __forceinline__ void build_matrix(const NetParams& P, double rho, double inv_rho, const double* ym,
+                                             const double* k, const double* dk, const double* Y, double c,
+                                             double dtm, MT (*M)[NS + 1]) {
     constexpr int N = NS + 1;
     constexpr int NR = NS - 1;
 #pragma unroll
@@ -144,12 +147,12 @@ __device__ __forceinline__ void build_matrix(const NetParams& P, double rho, dou
             if (j == 0) {
                 MT y0 = (MT)Y[0];
                 drE = (MT)dk[0] * (y0 * y0 * y0) * dTdE;
-                drX0 = (MT)k[0] * ((MT)3 * y0 * y0) * (MT)(inv_rho / P.mass[0]);
+                drX0 = (MT)k[0] * ((MT)3 * y0 * y0) * (MT)ym[0];
             } else {
                 MT y0 = (MT)Y[0], yj = (MT)Y[j];
                 drE = (MT)dk[j] * (yj * y0) * dTdE;
-                drXj = (MT)k[j] * y0 * (MT)(inv_rho / P.mass[j]);
-                drX0 = (MT)k[j] * yj * (MT)(inv_rho / P.mass[0]);
+                drXj = (MT)k[j] * y0 * (MT)ym[j];
+                drX0 = (MT)k[j] * yj * (MT)ym[0];
             }
             // rows: E gets Q_j; species rows get mass_i * s_ij
             const MT qj = s * (MT)P.Q[j];
@@ -186,7 +189,7 @@ __device__ __forceinline__ void build_matrix(const NetParams& P, double rho, dou
                 int o = sl == 0 ? P.r1[j] : P.r0[j];
                 int oc = sl == 0 ? P.c1[j] : P.c0[j];
                 if (o >= 0) dp *= ipow_small(Y[o], oc);
-                dr[1 + sp] += k[j] * dp * (inv_rho / P.mass[sp]);
+                dr[1 + sp] += k[j] * dp * ym[sp];
             }
             double sto[NS];
 #pragma unroll
@@ -212,15 +215,25 @@ __device__ __forceinline__ bool lu_solve(MT (*M)[N], VT* b) {
     MT inv_piv[N];
 #pragma unroll
     for (int kc = 0; kc < N; kc++) {
-        // pivot search
-        MT best = fabs(M[kc][kc]);
+        // pivot search (|x| compared as bit patterns: they order like the values)
         int piv = kc;
+        if (sizeof(MT) == 8) {
+            long long best = __double_as_longlong((double)M[kc][kc]) & ABS_MASK;
 #pragma unroll
-        for (int i = kc + 1; i < N; i++) {
-            MT v = fabs(M[i][kc]);
-            if (v > best) { best = v; piv = i; }
+            for (int i = kc + 1; i < N; i++) {
+                const long long v = __double_as_longlong((double)M[i][kc]) & ABS_MASK;
+                if (v > best) { best = v; piv = i; }
+            }
+            if (best == 0) return false;
+        } else {
+            int best = __float_as_int((float)M[kc][kc]) & 0x7fffffff;
+#pragma unroll
+            for (int i = kc + 1; i < N; i++) {
+                const int v = __float_as_int((float)M[i][kc]) & 0x7fffffff;
+                if (v > best) { best = v; piv = i; }
+            }
+            if (best == 0) return false;
         }
-        if (best == (MT)0) return false;
         // exchange rows kc and piv
 #pragma unroll
         for (int i = kc + 1; i < N; i++) {
@@ -235,7 +248,7 @@ __device__ __forceinline__ bool lu_solve(MT (*M)[N], VT* b) {
             b[kc] = sw ? y : x;
             b[i] = sw ? x : y;
         }
-        const MT ip = (MT)1 / M[kc][kc];
+        const MT ip = (sizeof(MT) == 8) ? (MT)rcp_nr((double)M[kc][kc]) : (MT)1 / M[kc][kc];
         inv_piv[kc] = ip;
 #pragma unroll
         for (int i = kc + 1; i < N; i++) {

@@ -85,7 +85,7 @@ reaction_source_kernel(NetParams P, long long N, int dim, const double* __restri
     double k[NR], dk[NR], Y[NS], Rz[NW];
     rate_consts<NR>(P, rho, T, k, dk);
 #pragma unroll
-    for (int i = 0; i < NS; i++) Y[i] = U[(2 + dim + i) * N + z] * (inv_rho / P.mass[i]);
+    for (int i = 0; i < NS; i++) Y[i] = U[(2 + dim + i) * N + z] * (inv_rho * P.inv_mass[i]);
     sources<NS, TOPO>(P, rho, k, Y, Rz);
 #pragma unroll
     for (int r = 0; r < NW; r++) R[r * N + z] = Rz[r];

@@ -57,12 +57,12 @@ __device__ __forceinline__ int newton_zone(const NetParams& P, const NewtonCfg& 
                                            const double* rw, double dtm, double* w, double* Rout, int& iters) {
     constexpr int N = NS + 1;
     constexpr int NR = NS - 1;
-    const double inv_rho = 1.0 / rho;
+    const double inv_rho = rcp_nr(rho);
     const double ke = 0.5 * m2 * inv_rho;
     double ym[NS];
 #pragma unroll
-    for (int i = 0; i < NS; i++) ym[i] = inv_rho / P.mass[i];
-    const double sE_inv = 1.0 / fabs(rw[0]);
+    for (int i = 0; i < NS; i++) ym[i] = inv_rho * P.inv_mass[i];
+    const double sE_inv = rcp_nr(fabs(rw[0]));
 
     // a start without a positive temperature is replaced by rhs
     {
@@ -78,7 +78,7 @@ __device__ __forceinline__ int newton_zone(const NetParams& P, const NewtonCfg& 
         const double x = rw[1 + i] * inv_rho, xg = w[1 + i] * inv_rho;
         double lo = x < 0.0 ? x : 0.0;
         lo = xg < lo ? xg : lo;
-        lower[i] = lo - XMARGIN;
+        lower[i] = (lo - XMARGIN) * rho;  // as a bound on rho X_i
     }
     double k[NR], dk[NR], Y[NS], G[N];
     double phi;
@@ -92,9 +92,9 @@ __device__ __forceinline__ int newton_zone(const NetParams& P, const NewtonCfg& 
         double h = PTC_H0;
         int it;
         for (it = 1; it <= cfg.maxit; it++) {
-            const double c = newton ? 1.0 : 1.0 + 1.0 / h;
+            const double c = newton ? 1.0 : 1.0 + rcp_nr(h);
             MT M[N][N];
-            build_matrix<NS, TOPO, MT>(P, rho, inv_rho, k, dk, Y, c, dtm, M);
+            build_matrix<NS, TOPO, MT>(P, rho, inv_rho, ym, k, dk, Y, c, dtm, M);
             MT dv[N];
 #pragma unroll
             for (int r = 0; r < N; r++) dv[r] = (MT)G[r];
@@ -104,7 +104,7 @@ __device__ __forceinline__ int newton_zone(const NetParams& P, const NewtonCfg& 
             for (int r = 0; r < N; r++) tr[r] = w[r] - (double)dv[r];
             bool ok = true;
 #pragma unroll
-            for (int i = 0; i < NS; i++) ok = ok && (tr[1 + i] * inv_rho >= lower[i]);
+            for (int i = 0; i < NS; i++) ok = ok && (tr[1 + i] >= lower[i]);
             double kt[NR], dkt[NR], Yt[NS], Gt[N];
             double phit = 0.0;
             if (ok) ok = eval_state<NS, TOPO>(P, rho, inv_rho, ke, ym, tr, rw, dtm, sE_inv, kt, dkt, Yt, Gt, phit);
@@ -127,8 +127,9 @@ __device__ __forceinline__ int newton_zone(const NetParams& P, const NewtonCfg& 
             phi = phit;
             if (newton) {
                 bool conv = fabs((double)dv[0]) <= cfg.rtol * fabs(w[0]);
+                const double tol_x = cfg.rtol * rho;
 #pragma unroll
-                for (int i = 0; i < NS; i++) conv = conv && (fabs((double)dv[1 + i]) <= cfg.rtol * rho);
+                for (int i = 0; i < NS; i++) conv = conv && (fabs((double)dv[1 + i]) <= tol_x);
                 if (conv) { status = ZONE_OK; break; }
             } else {
                 h *= PTC_GROW;

@@ -14,14 +14,19 @@ namespace sdcd {
     X(3, 7)                  \
     X(3, 13)
 
-template <int DIM> struct Tile;
-template <> struct Tile<1> { static constexpr int X = 64, Y = 1, Z = 1; };
-template <> struct Tile<3> { static constexpr int X = 8, Y = 8, Z = 4; };
+// Tiles: 1D lines of 64 zones; in 3D cubes of 8^3 (one face per thread in every
+// direction), or 8 x 8 x 4 when 8^3 primitives and slopes would not fit in
+// shared memory (many species).
+template <int DIM, int NS> struct Tile;
+template <int NS> struct Tile<1, NS> { static constexpr int X = 64, Y = 1, Z = 1; };
+template <int NS> struct Tile<3, NS> {
+    static constexpr int X = 8, Y = 8, Z = (NS <= 7 ? 8 : 4);
+};
 
 template <int DIM, int NS>
 constexpr size_t smem_bytes() {
-    using G = TileGeom<DIM, Tile<DIM>::X, Tile<DIM>::Y, Tile<DIM>::Z>;
-    return sizeof(double) * (size_t)(2 + DIM + NS) * (G::NC + G::NF);
+    using G = TileGeom<DIM, Tile<DIM, NS>::X, Tile<DIM, NS>::Y, Tile<DIM, NS>::Z>;
+    return sizeof(double) * (size_t)(2 + DIM + NS) * (G::NC + G::NB);
 }
 
 bool stencil_supported(int dim, int nspec) {
@@ -32,9 +37,14 @@ bool stencil_supported(int dim, int nspec) {
     return false;
 }
 
-void stencil_tile(int dim, int t[3]) {
-    if (dim == 1) { t[0] = Tile<1>::X; t[1] = 1; t[2] = 1; }
-    else { t[0] = Tile<3>::X; t[1] = Tile<3>::Y; t[2] = Tile<3>::Z; }
+void stencil_tile(int dim, int nspec, int t[3]) {
+    t[0] = 64; t[1] = 1; t[2] = 1;
+#define X(d, ns)                                                                       \
+    if (dim == d && nspec == ns) {                                                     \
+        t[0] = Tile<d, ns>::X; t[1] = Tile<d, ns>::Y; t[2] = Tile<d, ns>::Z;           \
+    }
+    SDC_STENCIL_CASES(X)
+#undef X
 }
 
 size_t stencil_smem_bytes(int dim, int nspec) {
@@ -48,7 +58,7 @@ size_t stencil_smem_bytes(int dim, int nspec) {
 cudaError_t stencil_prepare(int dim, int nspec) {
 #define X(d, ns)                                                                                          \
     if (dim == d && nspec == ns) {                                                                        \
-        constexpr int TX = Tile<d>::X, TY = Tile<d>::Y, TZ = Tile<d>::Z;                                  \
+        constexpr int TX = Tile<d, ns>::X, TY = Tile<d, ns>::Y, TZ = Tile<d, ns>::Z;                      \
         cudaError_t e = cudaFuncSetAttribute(stencil_kernel<d, ns, TX, TY, TZ, STENCIL_A>,                \
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,                 \
                                              (int)smem_bytes<d, ns>());                                   \
@@ -67,14 +77,15 @@ cudaError_t launch_stencil(const NetParams& P, int dim, int limiter, long long N
     if (ntiles <= 0) return cudaSuccess;
 #define X(d, ns)                                                                                           \
     if (dim == d && P.nspec == ns) {                                                                       \
-        constexpr int TX = Tile<d>::X, TY = Tile<d>::Y, TZ = Tile<d>::Z;                                   \
+        constexpr int TX = Tile<d, ns>::X, TY = Tile<d, ns>::Y, TZ = Tile<d, ns>::Z;                       \
+        constexpr int NTH = TileGeom<d, TX, TY, TZ>::THREADS;                                              \
         const size_t sm = smem_bytes<d, ns>();                                                             \
         if (mode == STENCIL_A)                                                                             \
             stencil_kernel<d, ns, TX, TY, TZ, STENCIL_A>                                                   \
-                <<<ntiles, TX * TY * TZ, sm, st>>>(P, limiter, Ntot, boxes, tiles, U, A, ra);              \
+                <<<ntiles, NTH, sm, st>>>(P, limiter, Ntot, boxes, tiles, U, A, ra);                       \
         else                                                                                               \
             stencil_kernel<d, ns, TX, TY, TZ, STENCIL_A_RHS>                                               \
-                <<<ntiles, TX * TY * TZ, sm, st>>>(P, limiter, Ntot, boxes, tiles, U, A, ra);              \
+                <<<ntiles, NTH, sm, st>>>(P, limiter, Ntot, boxes, tiles, U, A, ra);                       \
         return cudaGetLastError();                                                                         \
     }
     SDC_STENCIL_CASES(X)

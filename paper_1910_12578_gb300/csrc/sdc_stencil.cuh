@@ -4,17 +4,22 @@
 //
 // Method of lines: conserved -> primitive (rho, u, p, X), per direction a
 // piecewise-linear reconstruction with MC-limited (or unlimited centred)
-// slopes, interface mass fractions renormalised to sum to one, HLLC flux
-// (Davis wave speeds, species flux = X of the side upwind of the contact
-// times the mass flux), A = -sum_d (F_{i+1/2} - F_{i-1/2}) / dx_d.
+// slopes, the upwind interface mass fractions renormalised to sum to one,
+// HLLC flux (Davis wave speeds, species flux = X of the side upwind of the
+// contact times the mass flux), A = -sum_d (F_{i+1/2} - F_{i-1/2}) / dx_d.
 //
-// One CTA owns a TX x TY x TZ tile of one box.  The primitives of the tile
-// and of its 2-zone halo along each axis (a cross-shaped region; every box is
+// One CTA owns a TX x TY x TZ tile of one box.  The primitives of the tile and
+// of its 2-zone halo along each axis (a cross-shaped region; every box is
 // periodic on itself, so the halo wraps inside the box) are staged once in
-// shared memory; every face flux is computed once per direction from shared
-// memory and exchanged through a shared flux buffer.
+// shared memory.  Per direction: every zone's half slope is computed once into
+// a shared buffer, every face flux once (one face per thread when the tile is
+// a cube), the fluxes reuse the slope buffer, and each thread accumulates the
+// flux difference of its zones.  GB300 runs FP64 at 1/61 of its FP32 rate,
+// so divisions and square roots are Newton-Raphson refinements of hardware
+// approximations and the limiter works on bit patterns (sdc_fastmath.cuh).
 #pragma once
 #include "sdc_dev.cuh"
+#include "sdc_fastmath.cuh"
 
 namespace sdcd {
 
@@ -46,68 +51,6 @@ struct RhsArgs {
     int M;
 };
 
-__device__ __forceinline__ double mc_slope(int limiter, double qm, double q0, double qp) {
-    const double dl = q0 - qm, dr = qp - q0, dc = 0.5 * (dl + dr);
-    if (!limiter) return dc;
-    if (dl * dr <= 0.0) return 0.0;
-    double lim = fmin(2.0 * fabs(dl), 2.0 * fabs(dr));
-    lim = fmin(lim, fabs(dc));
-    return dc > 0.0 ? lim : -lim;
-}
-
-// HLLC flux through a face normal to `dir`; q = [rho, u_0.., p, X_0..].
-template <int DIM, int NS>
-__device__ __forceinline__ void hllc_flux(double g, double gm1_inv, int dir, const double* qL, const double* qR,
-                                          double* F) {
-    const double rL = qL[0], rR = qR[0];
-    const double unL = qL[1 + dir], unR = qR[1 + dir];
-    const double pL = qL[1 + DIM], pR = qR[1 + DIM];
-    double kL = 0.0, kR = 0.0;
-#pragma unroll
-    for (int d = 0; d < DIM; d++) {
-        kL += qL[1 + d] * qL[1 + d];
-        kR += qR[1 + d] * qR[1 + d];
-    }
-    const double EL = pL * gm1_inv + 0.5 * rL * kL;
-    const double ER = pR * gm1_inv + 0.5 * rR * kR;
-    const double cL = sqrt(g * pL / rL), cR = sqrt(g * pR / rR);
-    const double SL = fmin(unL - cL, unR - cR);
-    const double SR = fmax(unL + cL, unR + cR);
-    const double Ss = (pR - pL + rL * unL * (SL - unL) - rR * unR * (SR - unR)) /
-                      (rL * (SL - unL) - rR * (SR - unR));
-    // region: SL >= 0 -> F_L; else Ss >= 0 -> F*_L; else SR > 0 -> F*_R; else F_R
-    const bool left = (SL >= 0.0) || (Ss >= 0.0);
-    const bool star = (SL < 0.0) && (Ss >= 0.0 || SR > 0.0);
-    const double r = left ? rL : rR, un = left ? unL : unR, p = left ? pL : pR, E = left ? EL : ER;
-    const double S = left ? SL : SR;
-    const double* q = left ? qL : qR;
-    const double* qx = (Ss >= 0.0) ? qL : qR;  // species: side upwind of the contact
-    double Fh[2 + DIM];
-    Fh[0] = r * un;
-#pragma unroll
-    for (int d = 0; d < DIM; d++) Fh[1 + d] = r * un * q[1 + d] + (d == dir ? p : 0.0);
-    Fh[1 + DIM] = (E + p) * un;
-    if (star) {
-        const double fac = r * (S - un) / (S - Ss);
-        double Us[2 + DIM];
-        Us[0] = fac;
-#pragma unroll
-        for (int d = 0; d < DIM; d++) Us[1 + d] = fac * (d == dir ? Ss : q[1 + d]);
-        Us[1 + DIM] = fac * (E / r + (Ss - un) * (Ss + p / (r * (S - un))));
-        double Uk[2 + DIM];
-        Uk[0] = r;
-#pragma unroll
-        for (int d = 0; d < DIM; d++) Uk[1 + d] = r * q[1 + d];
-        Uk[1 + DIM] = E;
-#pragma unroll
-        for (int f = 0; f < 2 + DIM; f++) Fh[f] = Fh[f] + S * (Us[f] - Uk[f]);
-    }
-#pragma unroll
-    for (int f = 0; f < 2 + DIM; f++) F[f] = Fh[f];
-#pragma unroll
-    for (int s = 0; s < NS; s++) F[2 + DIM + s] = Fh[0] * qx[2 + DIM + s];
-}
-
 template <int DIM, int TX, int TY, int TZ>
 struct TileGeom {
     static constexpr int HX = TX + 4;
@@ -115,11 +58,18 @@ struct TileGeom {
     static constexpr int NYH = (DIM >= 2) ? TX * 4 * TZ : 0;  // y halo slabs
     static constexpr int NZH = (DIM >= 3) ? TX * TY * 4 : 0;  // z halo slabs
     static constexpr int NC = NXE + NYH + NZH;
+    // slopes: positions -1..T_d along d, the others inside the tile
+    static constexpr int SX = (TX + 2) * TY * TZ;
+    static constexpr int SY = (DIM >= 2) ? TX * (TY + 2) * TZ : 0;
+    static constexpr int SZ = (DIM >= 3) ? TX * TY * (TZ + 2) : 0;
+    static constexpr int NSL = SX > SY ? (SX > SZ ? SX : SZ) : (SY > SZ ? SY : SZ);
     static constexpr int FX = (TX + 1) * TY * TZ;
     static constexpr int FY = (DIM >= 2) ? TX * (TY + 1) * TZ : 0;
     static constexpr int FZ = (DIM >= 3) ? TX * TY * (TZ + 1) : 0;
     static constexpr int NF = FX > FY ? (FX > FZ ? FX : FZ) : (FY > FZ ? FY : FZ);
+    static constexpr int NB = NSL > NF ? NSL : NF;           // slope / flux buffer
     static constexpr int NT = TX * TY * TZ;
+    static constexpr int THREADS = NF;                       // one face per thread per direction
 };
 
 // shared-memory slot of tile-local zone (x, y, z); at most one coordinate
@@ -143,23 +93,71 @@ __device__ __forceinline__ int wrap(int g, int n) {
     return g < 0 ? g + n : g;
 }
 
+// HLLC flux of the hydrodynamic fields through a face normal to `dir`;
+// q = [rho, u_0.., p].  Returns S* (its sign picks the species' upwind side).
+template <int DIM>
+__device__ __forceinline__ double hllc_hydro(double g, double gm1_inv, int dir, const double* qL, const double* qR,
+                                             double* Fh) {
+    const double rL = qL[0], rR = qR[0];
+    const double unL = qL[1 + dir], unR = qR[1 + dir];
+    const double pL = qL[1 + DIM], pR = qR[1 + DIM];
+    double kL = 0.0, kR = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) {
+        kL = fma(qL[1 + d], qL[1 + d], kL);
+        kR = fma(qR[1 + d], qR[1 + d], kR);
+    }
+    const double EL = fma(pL, gm1_inv, 0.5 * rL * kL);
+    const double ER = fma(pR, gm1_inv, 0.5 * rR * kR);
+    const double irL = rcp_nr(rL), irR = rcp_nr(rR);
+    const double cL = sqrt_nr(g * pL * irL), cR = sqrt_nr(g * pR * irR);
+    const double SL = fmin(unL - cL, unR - cR);
+    const double SR = fmax(unL + cL, unR + cR);
+    const double aL = rL * (SL - unL), aR = rR * (SR - unR);  // mass fluxes relative to the waves
+    const double Ss = (pR - pL + unL * aL - unR * aR) * rcp_nr(aL - aR);
+    // region: SL >= 0 -> F_L; else Ss >= 0 -> F*_L; else SR > 0 -> F*_R; else F_R
+    const bool left = (SL >= 0.0) || (Ss >= 0.0);
+    const bool star = (SL < 0.0) && (Ss >= 0.0 || SR > 0.0);
+    const double r = left ? rL : rR, un = left ? unL : unR, p = left ? pL : pR, E = left ? EL : ER;
+    const double S = left ? SL : SR, a = left ? aL : aR, ir = left ? irL : irR;
+    const double* q = left ? qL : qR;
+    Fh[0] = r * un;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) Fh[1 + d] = r * un * q[1 + d] + (d == dir ? p : 0.0);
+    Fh[1 + DIM] = (E + p) * un;
+    if (star) {
+        // U*_K = fac [1, S* (normal) / u_t, E/r + (S* - u)(S* + p/(r (S - u)))], fac = r (S - u)/(S - S*)
+        const double fac = a * rcp_nr(S - Ss);
+        const double eS = fma(ir, E, (Ss - un) * fma(p, rcp_nr(a), Ss));
+        Fh[0] = fma(S, fac - r, Fh[0]);
+#pragma unroll
+        for (int d = 0; d < DIM; d++) {
+            const double ud = (d == dir) ? Ss : q[1 + d];
+            Fh[1 + d] = fma(S, fac * ud - r * q[1 + d], Fh[1 + d]);
+        }
+        Fh[1 + DIM] = fma(S, fac * eS - E, Fh[1 + DIM]);
+    }
+    return Ss;
+}
+
 template <int DIM, int NS, int TX, int TY, int TZ, int MODE>
-__global__ void __launch_bounds__(TX * TY * TZ)
+__global__ void __launch_bounds__(TileGeom<DIM, TX, TY, TZ>::THREADS, 1)
 stencil_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __restrict__ boxes,
                const TileDev* __restrict__ tiles, const double* __restrict__ U, double* __restrict__ Aout,
                RhsArgs ra) {
     using G = TileGeom<DIM, TX, TY, TZ>;
     constexpr int NV = 2 + DIM + NS;
+    constexpr int NH = 2 + DIM;   // hydrodynamic fields (rho, u, p / rho, rho u, rho E)
     extern __shared__ double smem[];
     double* sq = smem;                 // [NV][NC] primitives
-    double* sf = smem + NV * G::NC;    // [NV][NF] face fluxes of one direction
+    double* sb = smem + NV * G::NC;    // [NV][NB] half slopes, then face fluxes
 
     const TileDev t = tiles[blockIdx.x];
     const BoxDev b = boxes[t.box];
     const int ex = min(TX, b.n[0] - t.o[0]);
     const int ey = DIM >= 2 ? min(TY, b.n[1] - t.o[1]) : 1;
     const int ez = DIM >= 3 ? min(TZ, b.n[2] - t.o[2]) : 1;
-    const double g = P.gamma, gm1 = P.gm1, gm1_inv = 1.0 / P.gm1;
+    const double g = P.gamma, gm1 = P.gm1, gm1_inv = rcp_nr(P.gm1);
 
     // ---- stage primitives of the tile and its cross-shaped halo
     for (int s = threadIdx.x; s < G::NC; s += blockDim.x) {
@@ -192,22 +190,22 @@ stencil_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __restric
         const int gz = DIM >= 3 ? wrap(t.o[2] + z, b.n[2]) : 0;
         const long long gi = b.off + gx + (long long)b.n[0] * (gy + (long long)b.n[1] * gz);
         const double rho = __ldg(U + gi);
-        const double ir = 1.0 / rho;
+        const double ir = rcp_nr(rho);
         double ke = 0.0;
         sq[0 * G::NC + s] = rho;
 #pragma unroll
         for (int d = 0; d < DIM; d++) {
-            const double u = __ldg(U + (1 + d) * Ntot + gi) * ir;
+            const double m = __ldg(U + (1 + d) * Ntot + gi);
+            const double u = m * ir;
             sq[(1 + d) * G::NC + s] = u;
-            ke += 0.5 * rho * u * u;
+            ke = fma(m, u, ke);
         }
-        sq[(1 + DIM) * G::NC + s] = gm1 * (__ldg(U + (1 + DIM) * Ntot + gi) - ke);
+        sq[(1 + DIM) * G::NC + s] = gm1 * fma(-0.5, ke, __ldg(U + (1 + DIM) * Ntot + gi));
 #pragma unroll
         for (int sp = 0; sp < NS; sp++) sq[(2 + DIM + sp) * G::NC + s] = __ldg(U + (2 + DIM + sp) * Ntot + gi) * ir;
     }
     __syncthreads();
 
-    // zone owned by this thread
     const int tx = threadIdx.x % TX, ty = (threadIdx.x / TX) % TY, tz = threadIdx.x / (TX * TY);
     const bool own = (threadIdx.x < G::NT) && tx < ex && ty < ey && tz < ez;
     double A[NV];
@@ -216,56 +214,94 @@ stencil_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __restric
 
 #pragma unroll
     for (int dir = 0; dir < DIM; dir++) {
-        // faces of this direction: position i in [0, e_dir] along dir (face i sits
-        // between zones i-1 and i), the other two coordinates inside the tile
-        const int e0 = dir == 0 ? ex + 1 : ex;
-        const int e1 = dir == 1 ? ey + 1 : ey;
-        const int e2 = dir == 2 ? ez + 1 : ez;
-        const int T0 = dir == 0 ? TX + 1 : TX;
-        const int T1 = dir == 1 ? TY + 1 : TY;
+        const int e[3] = {ex, ey, ez};
+        const int T[3] = {TX, TY, TZ};
+        // ---- half slopes of the zones at positions -1..e_dir along dir
+        {
+            const int S0 = dir == 0 ? TX + 2 : TX, S1 = dir == 1 ? TY + 2 : TY;
+            const int nsl = S0 * S1 * (dir == 2 ? TZ + 2 : TZ);
+            for (int si = threadIdx.x; si < nsl; si += blockDim.x) {
+                int c[3] = {si % S0, (si / S0) % S1, si / (S0 * S1)};
+                c[dir] -= 1;
+                if (c[dir] > e[dir] || c[(dir + 1) % 3] >= e[(dir + 1) % 3] || c[(dir + 2) % 3] >= e[(dir + 2) % 3])
+                    continue;
+                int sl[3];
+#pragma unroll
+                for (int o = 0; o < 3; o++) {
+                    int cc[3] = {c[0], c[1], c[2]};
+                    cc[dir] += o - 1;
+                    sl[o] = slot_of<DIM, TX, TY, TZ>(cc[0], cc[1], cc[2], ey, ez);
+                }
+#pragma unroll
+                for (int f = 0; f < NV; f++)
+                    sb[f * G::NB + si] = mc_half_slope(limiter, sq[f * G::NC + sl[0]], sq[f * G::NC + sl[1]],
+                                                       sq[f * G::NC + sl[2]]);
+            }
+        }
+        __syncthreads();
+        // ---- face fluxes: face i along dir sits between zones i-1 and i
+        const int T0 = dir == 0 ? TX + 1 : TX, T1 = dir == 1 ? TY + 1 : TY;
         const int nfaces = T0 * T1 * (dir == 2 ? TZ + 1 : TZ);
-        for (int fi = threadIdx.x; fi < nfaces; fi += blockDim.x) {
-            const int c0 = fi % T0, c1 = (fi / T0) % T1, c2 = fi / (T0 * T1);
-            if (c0 >= e0 || c1 >= e1 || c2 >= e2) continue;
-            int sl[4];
-#pragma unroll
-            for (int o = 0; o < 4; o++) {
+        const int S0 = dir == 0 ? TX + 2 : TX, S1 = dir == 1 ? TY + 2 : TY;
+        double F[NV];
+        int fi_mine = -1;
+        {
+            const int fi = threadIdx.x;  // THREADS >= faces of every direction
+            if (fi < nfaces) {
+                const int c0 = fi % T0, c1 = (fi / T0) % T1, c2 = fi / (T0 * T1);
                 int c[3] = {c0, c1, c2};
-                c[dir] += o - 2;
-                sl[o] = slot_of<DIM, TX, TY, TZ>(c[0], c[1], c[2], ey, ez);
+                if (c[0] < (dir == 0 ? ex + 1 : ex) && c[1] < (dir == 1 ? ey + 1 : ey) &&
+                    c[2] < (dir == 2 ? ez + 1 : ez)) {
+                    fi_mine = fi;
+                    int cl[3] = {c0, c1, c2}, cr[3] = {c0, c1, c2};
+                    cl[dir] -= 1;
+                    const int zl = slot_of<DIM, TX, TY, TZ>(cl[0], cl[1], cl[2], ey, ez);
+                    const int zr = slot_of<DIM, TX, TY, TZ>(cr[0], cr[1], cr[2], ey, ez);
+                    int sc[3] = {c0, c1, c2};  // slope index of the right zone (position +1 offset)
+                    sc[dir] += 1;
+                    const int sr = sc[0] + S0 * (sc[1] + S1 * sc[2]);
+                    sc[dir] -= 1;
+                    const int slf = sc[0] + S0 * (sc[1] + S1 * sc[2]);
+                    double qL[NH], qR[NH];
+#pragma unroll
+                    for (int f = 0; f < NH; f++) {
+                        qL[f] = sq[f * G::NC + zl] + sb[f * G::NB + slf];
+                        qR[f] = sq[f * G::NC + zr] - sb[f * G::NB + sr];
+                    }
+                    const double Ss = hllc_hydro<DIM>(g, gm1_inv, dir, qL, qR, F);
+                    // species: upwind side of the contact, renormalised
+                    const bool lft = Ss >= 0.0;
+                    const int zu = lft ? zl : zr, su = lft ? slf : sr;
+                    double X[NS > 0 ? NS : 1];
+                    double sum = 0.0;
+#pragma unroll
+                    for (int s = 0; s < NS; s++) {
+                        const double q = sq[(NH + s) * G::NC + zu], h = sb[(NH + s) * G::NB + su];
+                        X[s] = lft ? q + h : q - h;
+                        sum += X[s];
+                    }
+                    const double fm = F[0] * rcp_nr(sum);
+#pragma unroll
+                    for (int s = 0; s < NS; s++) F[NH + s] = fm * X[s];
+                }
             }
-            double qL[NV], qR[NV];
+        }
+        __syncthreads();  // every slope is read: the buffer now takes the fluxes
+        if (fi_mine >= 0) {
 #pragma unroll
-            for (int f = 0; f < NV; f++) {
-                const double a0 = sq[f * G::NC + sl[0]], a1 = sq[f * G::NC + sl[1]];
-                const double a2 = sq[f * G::NC + sl[2]], a3 = sq[f * G::NC + sl[3]];
-                qL[f] = a1 + 0.5 * mc_slope(limiter, a0, a1, a2);
-                qR[f] = a2 - 0.5 * mc_slope(limiter, a1, a2, a3);
-            }
-            if (NS > 0) {
-                double sL = 0.0, sR = 0.0;
-#pragma unroll
-                for (int s = 0; s < NS; s++) { sL += qL[2 + DIM + s]; sR += qR[2 + DIM + s]; }
-                const double iL = 1.0 / sL, iR = 1.0 / sR;
-#pragma unroll
-                for (int s = 0; s < NS; s++) { qL[2 + DIM + s] *= iL; qR[2 + DIM + s] *= iR; }
-            }
-            double F[NV];
-            hllc_flux<DIM, NS>(g, gm1_inv, dir, qL, qR, F);
-#pragma unroll
-            for (int f = 0; f < NV; f++) sf[f * G::NF + fi] = F[f];
+            for (int f = 0; f < NV; f++) sb[f * G::NB + fi_mine] = F[f];
         }
         __syncthreads();
         if (own) {
             int c[3] = {tx, ty, tz};
-            const int T0s = dir == 0 ? TX + 1 : TX, T1s = dir == 1 ? TY + 1 : TY;
-            const int lo = c[0] + T0s * (c[1] + T1s * c[2]);
+            const int lo = c[0] + T0 * (c[1] + T1 * c[2]);
             c[dir] += 1;
-            const int hi = c[0] + T0s * (c[1] + T1s * c[2]);
+            const int hi = c[0] + T0 * (c[1] + T1 * c[2]);
             const double idx = b.idx[dir];
 #pragma unroll
-            for (int f = 0; f < NV; f++) A[f] -= (sf[f * G::NF + hi] - sf[f * G::NF + lo]) * idx;
+            for (int f = 0; f < NV; f++) A[f] = fma(-(sb[f * G::NB + hi] - sb[f * G::NB + lo]), idx, A[f]);
         }
+        (void)T;
         __syncthreads();
     }
 
@@ -281,15 +317,18 @@ stencil_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __restric
         for (int l = 0; l < 3; l++) qdt[l] = ra.qw[l] * dt;
 #pragma unroll
         for (int f = 0; f < NV; f++) {
-            double v = __ldg(U + f * Ntot + gi) + dtm * (A[f] - __ldg(ra.Aold_m + f * Ntot + gi));
+            double v = fma(dtm, A[f] - __ldg(ra.Aold_m + f * Ntot + gi), __ldg(U + f * Ntot + gi));
             const bool reactive = f >= 1 + DIM;
             const int r = f - 1 - DIM;
-            if (reactive) v -= dtm * __ldg(ra.Rnext + r * Ntot + gi);
+            if (reactive) v = fma(-dtm, __ldg(ra.Rnext + r * Ntot + gi), v);
             double I = 0.0;
-            for (int l = 0; l < ra.M; l++) {
-                double src = __ldg(ra.Aold[l] + f * Ntot + gi);
-                if (reactive) src += __ldg(ra.Rold[l] + r * Ntot + gi);
-                I += qdt[l] * src;
+#pragma unroll
+            for (int l = 0; l < 3; l++) {
+                if (l < ra.M) {
+                    double src = __ldg(ra.Aold[l] + f * Ntot + gi);
+                    if (reactive) src += __ldg(ra.Rold[l] + r * Ntot + gi);
+                    I = fma(qdt[l], src, I);
+                }
             }
             ra.rhs[f * Ntot + gi] = v + I;
         }

@@ -24,7 +24,7 @@ PREC_FP64, PREC_FP32_JAC = 0, 1
 # entry points declared in include/sdc.h
 EXPORTS = ["sdc_init_box", "sdc_advective_term", "sdc_node_integral", "sdc_react_newton", "sdc_step",
            "sdc_step_profile", "sdc_launches_per_step", "sdc_cfl_dt", "sdc_sizes", "sdc_destroy",
-           "sdc_status_string", "sdc_step_static"]
+           "sdc_status_string", "sdc_step_static", "sdc_selftest_math"]
 
 
 class SdcError(RuntimeError):
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
     L.sdc_cfl_dt.argtypes = [vp, dp, C.c_double, C.POINTER(C.c_double)]
     L.sdc_step_profile.argtypes = [vp, dp, C.c_double, C.POINTER(Stats), C.POINTER(Profile)]
     L.sdc_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
+    L.sdc_selftest_math.argtypes = [dp, C.c_longlong, dp, dp, vp]
     L.sdc_step_static.argtypes = [C.POINTER(Box), C.c_int, C.POINTER(Network), C.POINTER(Params), vp, dp,
                                   C.c_double, C.POINTER(Stats)]
     L.sdc_sizes.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -97,7 +98,7 @@ def load(path: str = LIB_PATH):
     L.sdc_status_string.argtypes = [C.c_int]
     L.sdc_status_string.restype = C.c_char_p
     for name in ("sdc_init_box", "sdc_advective_term", "sdc_node_integral", "sdc_react_newton", "sdc_step",
-                 "sdc_cfl_dt", "sdc_sizes", "sdc_step_profile", "sdc_launches_per_step", "sdc_step_static"):
+                 "sdc_cfl_dt", "sdc_sizes", "sdc_step_profile", "sdc_launches_per_step", "sdc_step_static", "sdc_selftest_math"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -266,6 +267,18 @@ def step_static(problems, U, dt, prec=PREC_FP64, stream=None, stats=True):
     if s not in (SDC_OK, SDC_ERR_NEWTON_NOCONV):
         raise SdcError(s, "sdc_step_static")
     return st
+
+
+def selftest_math(x):
+    """The library's Newton-Raphson reciprocal and square root of x (CUDA float64)."""
+    import torch
+    r = torch.empty_like(x)
+    q = torch.empty_like(x)
+    s = load().sdc_selftest_math(_ptr(x), x.numel(), _ptr(r), _ptr(q),
+                                 C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if s != SDC_OK:
+        raise SdcError(s, "sdc_selftest_math")
+    return r, q
 
 
 def init_box(problems, prec=PREC_FP64, stream=None) -> Context:

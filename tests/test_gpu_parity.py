@@ -138,6 +138,25 @@ def test_step_parity(torch_cuda, name, nsteps, prec):
     assert fails == sum(s.n_fail for s in sts) or prec == 1
 
 
+def test_newton_raphson_reciprocal_and_sqrt_within_two_ulp(torch_cuda):
+    """The stencil and Newton kernels replace IEEE division and sqrt by
+    Newton-Raphson refinement of the hardware approximations: compare with
+    CUDA's correctly rounded 1/x and sqrt(x) over 1e-30..1e30."""
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    g = torch.Generator(device="cuda").manual_seed(7)
+    x = torch.pow(10.0, torch.empty(1 << 20, dtype=torch.float64, device="cuda").uniform_(-30, 30, generator=g))
+    r, q = sdc.selftest_math(x)
+    r_ref = 1.0 / x
+    q_ref = torch.sqrt(x)
+
+    def ulps(a, b):
+        return ((a.view(torch.int64) - b.view(torch.int64)).abs()).max().item()
+
+    assert ulps(r, r_ref) <= 2
+    assert ulps(q, q_ref) <= 2
+
+
 def test_step_is_deterministic(torch_cuda):
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
