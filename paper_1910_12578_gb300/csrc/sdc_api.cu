@@ -424,6 +424,7 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     };
     cudaError_t e;
     if ((e = stencil_prepare(dim, net->nspec)) != cudaSuccess) return fail(e);
+    if ((e = newton_prepare(net->nspec, topo_used)) != cudaSuccess) return fail(e);
     if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->d_boxes, sizeof(BoxDev) * nbox)) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->d_tiles, sizeof(TileDev) * ht.size())) != cudaSuccess) return fail(e);
@@ -717,6 +718,7 @@ extern "C" sdc_status sdc_step_static(const sdc_box* boxes, int nbox, const sdc_
     unsigned char* base = nullptr;
     SDC_TRY(static_scratch((void**)&base));
     SDC_TRY(stencil_prepare(dim, net->nspec));
+    SDC_TRY(newton_prepare(net->nspec, topo));
 
     // a context on the stack whose pointers all lie inside the scratch array
     sdc_ctx c;

@@ -11,6 +11,7 @@ namespace sdcd {
 // topology for the small ones.
 bool newton_supported(int nspec, int topo);
 bool stencil_supported(int dim, int nspec);
+cudaError_t newton_prepare(int nspec, int topo);  // raise the dynamic shared-memory limit
 void stencil_tile(int dim, int nspec, int t[3]);
 size_t stencil_smem_bytes(int dim, int nspec);
 cudaError_t stencil_prepare(int dim, int nspec);  // raise the dynamic shared-memory limit

@@ -42,6 +42,8 @@ def problems():
     P.n = (24, 16, 12)   # ragged box: not a multiple of the 8x8x4 tile along y? (16 yes, 12 partial)
     P.dx = (1 / 24, 1 / 16, 1 / 12)
     out["ragged"] = (P, W.hot_spot_state(P, 2.0, T0=0.5))
+    P, U = W.config_box(n=16, nspec=13, n_iters=4, seed=0, T0=0.5)
+    out["box16_13"] = (P, U)
     return out
 
 
@@ -88,7 +90,8 @@ def test_node_integral_parity(torch_cuda, name):
 
 
 @pytest.mark.parametrize("name,k_iters,prec", [("1d", 1, 0), ("1d", 2, 0), ("box16", 1, 0), ("box16", 2, 0),
-                                               ("box16", 2, 1), ("ragged", 2, 0)])
+                                               ("box16", 2, 1), ("ragged", 2, 0), ("box16_13", 1, 0),
+                                               ("box16_13", 2, 0), ("box16_13", 2, 1)])
 def test_react_newton_parity(torch_cuda, name, k_iters, prec):
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
@@ -118,7 +121,8 @@ def test_react_newton_parity(torch_cuda, name, k_iters, prec):
         assert np.mean(zi.cpu().numpy() == zi_o) > 0.99
 
 
-@pytest.mark.parametrize("name,nsteps,prec", [("1d", 10, 0), ("box16", 2, 0), ("box16", 1, 1), ("ragged", 1, 0)])
+@pytest.mark.parametrize("name,nsteps,prec", [("1d", 10, 0), ("box16", 2, 0), ("box16", 1, 1), ("ragged", 1, 0),
+                                              ("box16_13", 1, 0), ("box16_13", 1, 1)])
 def test_step_parity(torch_cuda, name, nsteps, prec):
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
@@ -222,3 +226,42 @@ def test_full_size_config_step_parity(torch_cuda):
         e = rel_err(Ud.cpu().numpy(), Uo, P.nvar, P.dim)
         assert e.max() <= tol, (prec, e)
         assert st.newton_solves == st_o.newton_solves
+
+
+def test_full_size_256_13species_sampled(torch_cuda):
+    """256^3, 13 species (14 x 14 Jacobian), 3 nodes, 4 iterations: one full GPU
+    step at the benchmark size, checked zone by zone on samples.  One step
+    moves information at most 2 zones per advective evaluation, 18 zones in
+    all, so the oracle run on a 37^3 periodic sub-box centred on a sample zone
+    (initial data cut from the full box) gives that zone's exact result: the
+    sub-box's own wrap-around only reaches its outer shell."""
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = W.config_box(n=256, nspec=13, n_iters=4, seed=1, T0=0.5)
+    o_full = O.Oracle(P)
+    dt = o_full.cfl_dt(U)
+    samples = [(128, 128, 128), (128, 140, 120), (100, 128, 150), (0, 0, 0), (200, 31, 77), (135, 121, 131)]
+    R = 18
+    subs = []
+    for (x, y, z) in samples:
+        ix = np.arange(x - R, x + R + 1) % 256
+        iy = np.arange(y - R, y + R + 1) % 256
+        iz = np.arange(z - R, z + R + 1) % 256
+        subs.append(U[:, iz][:, :, iy][:, :, :, ix].copy())
+    for prec, tol in ((0, TOL64), (1, TOL32)):
+        ctx = sdc.Context(P, prec=prec)
+        Ud = dev(torch, U)
+        ctx.step(Ud, dt)
+        torch.cuda.synchronize()
+        G = Ud.cpu().numpy()
+        del Ud, ctx
+        torch.cuda.empty_cache()
+        scale = np.abs(G).reshape(P.nvar, -1).max(1)
+        scale[5:] = np.maximum(scale[5:], 1e-6 * scale[0])   # trace species: 1e-18 rho absolute
+        for (x, y, z), sub in zip(samples, subs):
+            Ps = W.Problem(dim=3, n=(2 * R + 1,) * 3, dx=P.dx, gamma=P.gamma, net=P.net, n_nodes=3, n_iters=4)
+            Vs, _ = O.Oracle(Ps).step(sub, dt)
+            ref = Vs[:, R, R, R]
+            got = G[:, z, y, x]
+            err = np.abs(got - ref) / scale
+            assert err.max() <= tol, ((x, y, z), prec, err)
