@@ -161,6 +161,28 @@ sdc_status sdc_step_profile(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats
    doubles x (device arrays), for testing against correctly rounded results. */
 sdc_status sdc_selftest_math(const double* x, long long n, double* rcp_out, double* sqrt_out, void* cuda_stream);
 
+/* Kernel variants of a context, chosen by measurement.
+   stencil: tile shape of the advective-term kernel (0: 8^3 zones, 576 threads,
+   one face per thread per direction; 1: 8 x 8 x 4 zones, 320 threads; one shape
+   only in 1D and for 13 species).  newton: 0 = one zone per thread on a static
+   grid; 1 = a persistent grid fed by a device work queue, each lane taking the
+   next zone when its own is solved, so zones with many Newton iterations do not
+   hold their warp (the 13-species kernel has one variant).  Defaults: 0, 0. */
+typedef struct {
+    int stencil_variants, newton_variants;  /* candidates tried */
+    int stencil_choice, newton_choice;      /* chosen */
+    float ms_stencil[4], ms_newton[4];      /* per candidate: summed event time of one step */
+} sdc_tuning;
+
+/* Time one eager step per candidate on a scratch copy of U (U is not changed)
+   and keep the fastest tile shape and Newton variant for the context; the next
+   sdc_step recaptures its graph.  Allocates and frees one U-sized scratch
+   array; waits for the stream.  out may be NULL. */
+sdc_status sdc_autotune(sdc_ctx* ctx, const double* U, double dt, sdc_tuning* out);
+
+/* Set the variants directly (as sdc_autotune would). */
+sdc_status sdc_set_variants(sdc_ctx* ctx, int stencil_variant, int newton_variant);
+
 /* Number of kernels one sdc_step launches (its graph plus the dt store). */
 sdc_status sdc_launches_per_step(const sdc_ctx* ctx, int* launches);
 

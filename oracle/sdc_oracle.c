@@ -366,10 +366,12 @@ static int lu_solve(int n, double* J, double* b) {
 /* dw/dtau = -G(w) (the burning ODE relaxed towards rhs), then sets     */
 /* w <- w - delta.                                                     */
 /*   - start in Newton mode;                                           */
-/*   - a trial is admissible when T > 0 (finite) and every mass         */
-/*     fraction stays above min(0, X_i of rhs, X_i of the start) - 0.01 */
-/*     (a wide floor: it stops excursions into grossly negative         */
-/*     compositions, not the small negative values a root can have);    */
+/*   - a trial is admissible when T > 0 (finite) and, if every rhs mass */
+/*     fraction is >= -0.01, every mass fraction stays above            */
+/*     min(0, X_i of rhs, X_i of the start) - 0.01 (a wide floor: it    */
+/*     stops excursions into grossly negative compositions, not the     */
+/*     small negative values a root can have; an rhs already pushed     */
+/*     further negative by the correction terms gets no floor);         */
 /*   - a start without a positive temperature is replaced by rhs;       */
 /*   - a Newton trial that is not admissible or raises the scaled       */
 /*     residual norm switches to pseudo mode with h = 1 (w unchanged);  */
@@ -405,11 +407,16 @@ int orc_newton_zone(const orc_problem* P, double rho, const double* mom, const d
     double Tg = orc_temperature(P, rho, mom, w[0]);
     if (!(Tg > 0.0 && Tg < INFINITY))
         for (int r = 0; r < n; r++) w[r] = rhs_w[r];
+    /* the floor applies when the rhs is physical (every X_i >= -0.01); an rhs
+       that the correction terms pushed further negative has no floor */
+    int physical = 1;
+    for (int i = 0; i < ns; i++)
+        if (!(rhs_w[1 + i] / rho >= -NEWTON_XMARGIN)) physical = 0;
     for (int i = 0; i < ns; i++) {
         double x = rhs_w[1 + i] / rho, xg = w[1 + i] / rho;
         double lo = x < 0.0 ? x : 0.0;
         if (xg < lo) lo = xg;
-        lower[i] = lo - NEWTON_XMARGIN;
+        lower[i] = physical ? lo - NEWTON_XMARGIN : -INFINITY;
     }
     double T0 = orc_temperature(P, rho, mom, w[0]);
     if (!(T0 > 0.0 && T0 < INFINITY)) { *iters = 0; return ORC_NEWTON_NONPHYSICAL; }
@@ -439,7 +446,18 @@ int orc_newton_zone(const orc_problem* P, double rho, const double* mom, const d
             phit = scaled_norm2(n, Gt, sE, rho);
             if (!(phit < INFINITY)) ok = 0;
         }
-        if (newton && (!ok || phit > phi)) {
+        /* the Newton step meets the stop test: converged (a residual that grew
+           by round-off at the root does not count against it) */
+        int small = 0;
+        if (newton && ok) {
+            double err = fabs(d[0]) / fabs(trial[0]);
+            for (int i = 0; i < ns; i++) {
+                double e = fabs(d[1 + i]) / rho;
+                if (e > err) err = e;
+            }
+            small = err <= P->newton_rtol;
+        }
+        if (newton && !small && (!ok || phit > phi)) {
             newton = 0;
             h = PTC_H0;
             continue;

@@ -101,6 +101,8 @@ __global__ void selftest_math_kernel(const double* __restrict__ x, long long n, 
     q[i] = sqrt_nr(x[i]);
 }
 
+constexpr int QUEUE_SLOTS = 64;
+
 // Event pairs bracketing each launch of an eagerly enqueued step.
 enum { CLS_STENCIL = 0, CLS_NEWTON = 1, CLS_OTHER = 2 };
 struct Prof {
@@ -158,6 +160,12 @@ struct sdc_ctx {
     std::vector<void*> allocs;
     cudaGraphExec_t gexec = nullptr;
     double* gU = nullptr;
+    // kernel variants (chosen by sdc_autotune) and the Newton work queues
+    int stencil_variant = 0, newton_variant = 0;
+    int persistent_blocks = 0;
+    unsigned long long* d_queue = nullptr;  // one counter per Newton launch of a step
+    std::vector<sdc_box> boxes;
+    int tiles_capacity = 0;
 };
 
 namespace {
@@ -230,11 +238,15 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
     const size_t ubytes = sizeof(double) * c->nvar * N;
     cudaError_t e;
     if ((e = cudaMemsetAsync(c->d_stats, 0, sizeof(DevStats), st)) != cudaSuccess) return e;
+    if (c->d_queue &&
+        (e = cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned long long) * QUEUE_SLOTS, st)) != cudaSuccess)
+        return e;
+    int qslot = 0;
     double* node[3] = {c->node_ws[0], c->M == 3 ? c->node_ws[1] : U, U};
     if ((e = cudaMemcpyAsync(node[0], U, ubytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
     RhsArgs none = rhs_args(c, (const double* const*)c->Ag[0], (const double* const*)c->Rg[0], 0);
     SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles, c->ntiles,
-                                                 node[0], c->A0, STENCIL_A, none, st));
+                                                 node[0], c->A0, STENCIL_A, none, st, c->stencil_variant));
     SDC_LAUNCH(prof, CLS_OTHER, launch_reaction_source(c->P, N, c->dim, node[0], c->R0, st));
     const double* Aold[3] = {c->A0, c->A0, c->A0};
     const double* Rold[3] = {c->R0, c->R0, c->R0};
@@ -250,23 +262,48 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
                                              cudaGetLastError()));
             } else {
                 SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles,
-                                                             c->ntiles, node[m], Anew[m], STENCIL_A_RHS, ra, st));
+                                                             c->ntiles, node[m], Anew[m], STENCIL_A_RHS, ra, st,
+                                                             c->stencil_variant));
             }
             const double* guess = (k == 0) ? node[0] : node[m + 1];
+            unsigned long long* q = (c->d_queue && qslot < QUEUE_SLOTS) ? c->d_queue + qslot++ : nullptr;
             SDC_LAUNCH(prof, CLS_NEWTON, launch_newton(c->P, c->cfg, c->prec, N, c->dim, c->rhs, guess, node[m + 1],
                                                        Rnew[m + 1], c->d_dt, c->tau[m + 1] - c->tau[m], 0.0, nullptr,
-                                                       nullptr, c->d_stats, st));
+                                                       nullptr, c->d_stats, st, c->newton_variant, q,
+                                                       c->persistent_blocks));
         }
         if (k < c->K - 1) {
             SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles,
                                                          c->ntiles, node[c->M - 1], Anew[c->M - 1], STENCIL_A, none,
-                                                         st));
+                                                         st, c->stencil_variant));
         }
         for (int l = 1; l < c->M; l++) {
             Aold[l] = Anew[l];
             Rold[l] = Rnew[l];
         }
     }
+    return cudaSuccess;
+}
+
+// stencil tiles of every box for tile shape `variant`
+std::vector<TileDev> tile_list(const sdc_ctx* c, int variant) {
+    std::vector<TileDev> ht;
+    int tl[3];
+    stencil_tile(c->dim, c->nspec, variant, tl);
+    for (int b = 0; b < (int)c->boxes.size(); b++)
+        for (int z = 0; z < c->boxes[b].n[2]; z += tl[2])
+            for (int y = 0; y < c->boxes[b].n[1]; y += tl[1])
+                for (int x = 0; x < c->boxes[b].n[0]; x += tl[0]) ht.push_back(TileDev{b, {x, y, z}});
+    return ht;
+}
+
+cudaError_t set_stencil_variant(sdc_ctx* c, int variant) {
+    std::vector<TileDev> ht = tile_list(c, variant);
+    if ((int)ht.size() > c->tiles_capacity) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpy(c->d_tiles, ht.data(), sizeof(TileDev) * ht.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    c->ntiles = (int)ht.size();
+    c->stencil_variant = variant;
     return cudaSuccess;
 }
 
@@ -398,11 +435,8 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
         P.order[j] = P.c0[j] + P.c1[j];
     }
 
-    // boxes and stencil tiles
+    // boxes and stencil tiles (the tile table is sized for the smallest tile shape)
     std::vector<BoxDev> hb(nbox);
-    std::vector<TileDev> ht;
-    int tl[3];
-    stencil_tile(dim, net->nspec, tl);
     long long off = 0;
     for (int b = 0; b < nbox; b++) {
         hb[b].off = off;
@@ -411,10 +445,15 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
             hb[b].idx[d] = d < dim ? 1.0 / boxes[b].dx[d] : 0.0;
         }
         off += (long long)boxes[b].n[0] * boxes[b].n[1] * boxes[b].n[2];
-        for (int z = 0; z < boxes[b].n[2]; z += tl[2])
-            for (int y = 0; y < boxes[b].n[1]; y += tl[1])
-                for (int x = 0; x < boxes[b].n[0]; x += tl[0]) ht.push_back(TileDev{b, {x, y, z}});
     }
+    c->boxes.assign(boxes, boxes + nbox);
+    int max_tiles = 0;
+    for (int v = 0; v < stencil_variants(dim, net->nspec); v++) {
+        const int nt = (int)tile_list(c, v).size();
+        if (nt > max_tiles) max_tiles = nt;
+    }
+    c->tiles_capacity = max_tiles;
+    std::vector<TileDev> ht = tile_list(c, 0);
     c->ntiles = (int)ht.size();
 
     sdc_status st = SDC_OK;
@@ -427,7 +466,9 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     if ((e = newton_prepare(net->nspec, topo_used)) != cudaSuccess) return fail(e);
     if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->d_boxes, sizeof(BoxDev) * nbox)) != cudaSuccess) return fail(e);
-    if ((e = ctx_alloc(c, (void**)&c->d_tiles, sizeof(TileDev) * ht.size())) != cudaSuccess) return fail(e);
+    if ((e = ctx_alloc(c, (void**)&c->d_tiles, sizeof(TileDev) * c->tiles_capacity)) != cudaSuccess) return fail(e);
+    if ((e = ctx_alloc(c, (void**)&c->d_queue, sizeof(unsigned long long) * QUEUE_SLOTS)) != cudaSuccess) return fail(e);
+    c->persistent_blocks = newton_variants(net->nspec, topo_used) > 1 ? newton_persistent_blocks(P, c->prec) : 0;
     if ((e = ctx_alloc(c, (void**)&c->d_dt, sizeof(double))) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->d_stats, sizeof(DevStats))) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->d_smax, sizeof(unsigned long long))) != cudaSuccess) return fail(e);
@@ -465,7 +506,7 @@ sdc_status sdc_advective_term(sdc_ctx* ctx, const double* U, double* A) {
     RhsArgs none;
     memset(&none, 0, sizeof(none));
     SDC_TRY(launch_stencil(ctx->P, ctx->dim, ctx->limiter, ctx->Ntot, ctx->d_boxes, ctx->d_tiles, ctx->ntiles, U, A,
-                           STENCIL_A, none, ctx->stream));
+                           STENCIL_A, none, ctx->stream, ctx->stencil_variant));
     return SDC_OK;
 }
 
@@ -483,8 +524,10 @@ sdc_status sdc_react_newton(sdc_ctx* ctx, const double* rhs, double dt_m, double
                             int* zone_status, int* zone_iters, sdc_stats* stats) {
     if (!ctx || !rhs || !U_inout || !R_out || rhs == U_inout) return SDC_ERR_INVALID_ARG;
     if (stats) SDC_TRY(cudaMemsetAsync(ctx->d_stats, 0, sizeof(DevStats), ctx->stream));
+    SDC_TRY(cudaMemsetAsync(ctx->d_queue, 0, sizeof(unsigned long long), ctx->stream));
     SDC_TRY(launch_newton(ctx->P, ctx->cfg, ctx->prec, ctx->Ntot, ctx->dim, rhs, U_inout, U_inout, R_out, nullptr,
-                          1.0, dt_m, zone_status, zone_iters, ctx->d_stats, ctx->stream));
+                          1.0, dt_m, zone_status, zone_iters, ctx->d_stats, ctx->stream, ctx->newton_variant,
+                          ctx->d_queue, ctx->persistent_blocks));
     if (stats) return read_stats(ctx, stats);
     return SDC_OK;
 }
@@ -545,6 +588,82 @@ sdc_status sdc_selftest_math(const double* x, long long n, double* rcp_out, doub
     if (n == 0) return SDC_OK;
     selftest_math_kernel<<<grid_for(n, EW_BLOCK), EW_BLOCK, 0, (cudaStream_t)cuda_stream>>>(x, n, rcp_out, sqrt_out);
     SDC_TRY(cudaGetLastError());
+    return SDC_OK;
+}
+
+sdc_status sdc_autotune(sdc_ctx* ctx, const double* U, double dt, sdc_tuning* out) {
+    if (!ctx || !U || !(dt > 0.0)) return SDC_ERR_INVALID_ARG;
+    const size_t ub = sizeof(double) * ctx->nvar * ctx->Ntot;
+    double* scratch = nullptr;
+    SDC_TRY(cudaMalloc((void**)&scratch, ub));
+    sdc_tuning t;
+    memset(&t, 0, sizeof(t));
+    t.stencil_variants = stencil_variants(ctx->dim, ctx->nspec);
+    t.newton_variants = newton_variants(ctx->nspec, ctx->P.topo);
+    sdc_status st = SDC_OK;
+    // one eager step per candidate (after one warm-up step); the step's stencil
+    // time depends only on the tile shape and its Newton time only on the
+    // Newton variant, so each is chosen on its own
+    auto trial = [&](float* ms_st, float* ms_nw) -> sdc_status {
+        sdc_profile pr;
+        for (int rep = 0; rep < 2; rep++) {
+            if (cudaMemcpyAsync(scratch, U, ub, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+                return SDC_ERR_CUDA;
+            sdc_status s2 = sdc_step_profile(ctx, scratch, dt, nullptr, &pr);
+            if (s2 != SDC_OK && s2 != SDC_ERR_NEWTON_NOCONV) return s2;
+        }
+        *ms_st = pr.ms_stencil;
+        *ms_nw = pr.ms_newton;
+        return SDC_OK;
+    };
+    const int nv0 = ctx->newton_variant;
+    float best_st = 0.0f, best_nw = 0.0f;
+    int vs = 0, vn = 0;
+    for (int v = 0; v < t.stencil_variants && st == SDC_OK; v++) {
+        if (set_stencil_variant(ctx, v) != cudaSuccess) { st = SDC_ERR_CUDA; break; }
+        float a, b;
+        st = trial(&a, &b);
+        t.ms_stencil[v] = a;
+        if (st == SDC_OK && (v == 0 || a < best_st)) { best_st = a; vs = v; }
+    }
+    for (int v = 0; v < t.newton_variants && st == SDC_OK; v++) {
+        ctx->newton_variant = v;
+        float a, b;
+        st = trial(&a, &b);
+        t.ms_newton[v] = b;
+        if (st == SDC_OK && (v == 0 || b < best_nw)) { best_nw = b; vn = v; }
+    }
+    cudaFree(scratch);
+    if (st != SDC_OK) {
+        ctx->newton_variant = nv0;
+        set_stencil_variant(ctx, 0);
+        return st;
+    }
+    SDC_TRY(set_stencil_variant(ctx, vs));
+    ctx->newton_variant = vn;
+    t.stencil_choice = vs;
+    t.newton_choice = vn;
+    // the captured graph used the previous variants
+    if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+        ctx->gU = nullptr;
+    }
+    if (out) *out = t;
+    return SDC_OK;
+}
+
+sdc_status sdc_set_variants(sdc_ctx* ctx, int stencil_variant, int newton_variant) {
+    if (!ctx || stencil_variant < 0 || stencil_variant >= stencil_variants(ctx->dim, ctx->nspec) ||
+        newton_variant < 0 || newton_variant >= newton_variants(ctx->nspec, ctx->P.topo))
+        return SDC_ERR_INVALID_ARG;
+    SDC_TRY(set_stencil_variant(ctx, stencil_variant));
+    ctx->newton_variant = newton_variant;
+    if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+        ctx->gU = nullptr;
+    }
     return SDC_OK;
 }
 
@@ -678,7 +797,7 @@ extern "C" sdc_status sdc_step_static(const sdc_box* boxes, int nbox, const sdc_
     StaticTables T;
     memset(&T, 0, sizeof(T));
     T.nbox = nbox;
-    stencil_tile(dim, net->nspec, T.t);
+    stencil_tile(dim, net->nspec, 0, T.t);
     long long Ntot = 0;
     for (int b = 0; b < nbox; b++) {
         if (boxes[b].dim != dim) return SDC_ERR_INVALID_ARG;

@@ -12,21 +12,28 @@ namespace sdcd {
 bool newton_supported(int nspec, int topo);
 bool stencil_supported(int dim, int nspec);
 cudaError_t newton_prepare(int nspec, int topo);  // raise the dynamic shared-memory limit
-void stencil_tile(int dim, int nspec, int t[3]);
-size_t stencil_smem_bytes(int dim, int nspec);
+int stencil_variants(int dim, int nspec);  // tile shapes available to the autotuner
+void stencil_tile(int dim, int nspec, int variant, int t[3]);
+size_t stencil_smem_bytes(int dim, int nspec, int variant);
 cudaError_t stencil_prepare(int dim, int nspec);  // raise the dynamic shared-memory limit
 
 // dtm = (dt_dev ? *dt_dev * dt_frac : dtm_host)
+// variant 0: one zone per thread on a static grid; 1: persistent grid of
+// persistent_blocks fed by the zero-initialised device counter *queue (zones
+// of uneven cost balance across lanes); the group kernel ignores the variant.
+int newton_variants(int nspec, int topo);
 cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, long long N, int dim,
                           const double* rhs, const double* guess, double* Uout, double* Rout,
                           const double* dt_dev, double dt_frac, double dtm_host, int* zone_status,
-                          int* zone_iters, DevStats* stats, cudaStream_t st);
+                          int* zone_iters, DevStats* stats, cudaStream_t st, int variant = 0,
+                          unsigned long long* queue = nullptr, int persistent_blocks = 0);
+int newton_persistent_blocks(const NetParams& P, int prec);  // resident blocks x SMs
 
 cudaError_t launch_reaction_source(const NetParams& P, long long N, int dim, const double* U, double* R,
                                    cudaStream_t st);
 
 cudaError_t launch_stencil(const NetParams& P, int dim, int limiter, long long Ntot, const BoxDev* boxes,
                            const TileDev* tiles, int ntiles, const double* U, double* A, int mode,
-                           const RhsArgs& ra, cudaStream_t st);
+                           const RhsArgs& ra, cudaStream_t st, int variant = 0);
 
 }  // namespace sdcd

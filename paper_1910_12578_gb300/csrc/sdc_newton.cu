@@ -8,13 +8,54 @@ namespace sdcd {
 
 constexpr int NEWTON_BLOCK = 128;
 
+// Load zone z into a solver state and evaluate it.
+template <int NS, int TOPO>
+__device__ __forceinline__ void load_zone(ZoneState<NS>& S, const NetParams& P, long long N, int dim, long long z,
+                                          const double* __restrict__ rhs, const double* guess, double dtm,
+                                          double* mom) {
+    constexpr int NW = NS + 1;
+    const double rho = rhs[z];
+    double m2 = 0.0;
+    for (int d = 0; d < 3; d++) mom[d] = 0.0;
+    for (int d = 0; d < dim; d++) {
+        mom[d] = rhs[(1 + d) * N + z];
+        m2 += mom[d] * mom[d];
+    }
+    const double scale = rho / guess[z];
+#pragma unroll
+    for (int r = 0; r < NW; r++) {
+        S.rw[r] = rhs[(1 + dim + r) * N + z];
+        S.w[r] = guess[(1 + dim + r) * N + z] * scale;
+    }
+    zone_init<NS, TOPO>(S, P, rho, m2, dtm);
+}
+
+// Store the solution and R of a finished zone.
+template <int NS, int TOPO>
+__device__ __forceinline__ void store_zone(const ZoneState<NS>& S, const NetParams& P, long long N, int dim,
+                                           long long z, const double* mom, double* Uout, double* __restrict__ Rout,
+                                           int* __restrict__ zone_status, int* __restrict__ zone_iters) {
+    constexpr int NW = NS + 1;
+    double R[NW];
+    zone_source<NS, TOPO>(S, P, R);
+    Uout[z] = S.rho;
+    for (int d = 0; d < dim; d++) Uout[(1 + d) * N + z] = mom[d];
+#pragma unroll
+    for (int r = 0; r < NW; r++) {
+        Uout[(1 + dim + r) * N + z] = S.w[r];
+        Rout[r * N + z] = R[r];
+    }
+    if (zone_status) zone_status[z] = S.status;
+    if (zone_iters) zone_iters[z] = S.iters;
+}
+
+// One zone per thread, a static grid over the zones.
 template <int NS, int TOPO, typename MT>
 __global__ void __launch_bounds__(NEWTON_BLOCK)
 newton_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __restrict__ rhs,
               const double* guess, double* Uout, double* __restrict__ Rout, const double* __restrict__ dt_dev,
               double dt_frac, double dtm_host, int* __restrict__ zone_status, int* __restrict__ zone_iters,
               DevStats* __restrict__ stats) {
-    constexpr int NW = NS + 1;
     __shared__ unsigned int hist[64];
     for (int i = threadIdx.x; i < 64; i += blockDim.x) hist[i] = 0;
     __syncthreads();
@@ -23,29 +64,13 @@ newton_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __
     int iters = 0, status = ZONE_OK;
     if (active) {
         const double dtm = dt_dev ? (*dt_dev) * dt_frac : dtm_host;
-        const double rho = rhs[z];
-        double mom[3] = {0.0, 0.0, 0.0}, m2 = 0.0;
-        for (int d = 0; d < dim; d++) {
-            mom[d] = rhs[(1 + d) * N + z];
-            m2 += mom[d] * mom[d];
-        }
-        double rw[NW], w[NW], R[NW];
-        const double scale = rho / guess[z];
-#pragma unroll
-        for (int r = 0; r < NW; r++) {
-            rw[r] = rhs[(1 + dim + r) * N + z];
-            w[r] = guess[(1 + dim + r) * N + z] * scale;
-        }
-        status = newton_zone<NS, TOPO, MT>(P, cfg, rho, m2, rw, dtm, w, R, iters);
-        Uout[z] = rho;
-        for (int d = 0; d < dim; d++) Uout[(1 + d) * N + z] = mom[d];
-#pragma unroll
-        for (int r = 0; r < NW; r++) {
-            Uout[(1 + dim + r) * N + z] = w[r];
-            Rout[r * N + z] = R[r];
-        }
-        if (zone_status) zone_status[z] = status;
-        if (zone_iters) zone_iters[z] = iters;
+        ZoneState<NS> S;
+        double mom[3];
+        load_zone<NS, TOPO>(S, P, N, dim, z, rhs, guess, dtm, mom);
+        while (!S.done) zone_iterate<NS, TOPO, MT>(S, P, cfg, dtm);
+        store_zone<NS, TOPO>(S, P, N, dim, z, mom, Uout, Rout, zone_status, zone_iters);
+        iters = S.iters;
+        status = S.status;
         atomicAdd(&hist[iters < 63 ? iters : 63], 1u);
     }
     // warp-aggregated totals
@@ -64,6 +89,75 @@ newton_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __
         if (fl) atomicAdd(&stats->fails, fl);
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < 64; i += blockDim.x)
+        if (hist[i]) atomicAdd(&stats->hist[i], (unsigned long long)hist[i]);
+}
+
+// Persistent grid fed by a device work queue: every lane owns one zone's
+// solve; when it finishes, the lane stores it and takes the next zone from the
+// queue (one atomic per warp refill), so zones that need many iterations do
+// not hold the other lanes of their warp idle.  Each zone's arithmetic is the
+// same as in newton_kernel, so results agree bit for bit.
+template <int NS, int TOPO, typename MT>
+__global__ void __launch_bounds__(NEWTON_BLOCK)
+newton_queue_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __restrict__ rhs,
+                    const double* guess, double* Uout, double* __restrict__ Rout, const double* __restrict__ dt_dev,
+                    double dt_frac, double dtm_host, int* __restrict__ zone_status, int* __restrict__ zone_iters,
+                    DevStats* __restrict__ stats, unsigned long long* __restrict__ queue) {
+    __shared__ unsigned int hist[64];
+    __shared__ unsigned long long blk_iters, blk_solves, blk_fails;
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) hist[i] = 0;
+    if (threadIdx.x == 0) { blk_iters = 0; blk_solves = 0; blk_fails = 0; }
+    __syncthreads();
+    const double dtm = dt_dev ? (*dt_dev) * dt_frac : dtm_host;
+    const int lane = threadIdx.x & 31;
+    ZoneState<NS> S;
+    double mom[3];
+    long long z = -1;
+    bool exhausted = false;
+    S.done = true;
+    unsigned long long my_iters = 0, my_solves = 0, my_fails = 0;
+    for (;;) {
+        // lanes without a zone take the next ones from the queue
+        const bool need = (z < 0) && !exhausted;
+        const unsigned want = __ballot_sync(0xffffffffu, need);
+        if (want) {
+            unsigned long long base = 0;
+            const int leader = __ffs(want) - 1;
+            if (lane == leader) base = atomicAdd(queue, (unsigned long long)__popc(want));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (need) {
+                const long long zi = (long long)(base + __popc(want & ((1u << lane) - 1u)));
+                if (zi < N) {
+                    z = zi;
+                    load_zone<NS, TOPO>(S, P, N, dim, z, rhs, guess, dtm, mom);
+                } else {
+                    exhausted = true;
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, z >= 0)) break;
+        if (z >= 0 && !S.done) zone_iterate<NS, TOPO, MT>(S, P, cfg, dtm);
+        if (z >= 0 && S.done) {
+            store_zone<NS, TOPO>(S, P, N, dim, z, mom, Uout, Rout, zone_status, zone_iters);
+            atomicAdd(&hist[S.iters < 63 ? S.iters : 63], 1u);
+            my_iters += (unsigned long long)S.iters;
+            my_solves += 1;
+            if (S.status != ZONE_OK) my_fails += 1;
+            z = -1;
+        }
+    }
+    atomicAdd(&blk_iters, my_iters);
+    atomicAdd(&blk_solves, my_solves);
+    if (my_fails) atomicAdd(&blk_fails, my_fails);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (blk_solves) {
+            atomicAdd(&stats->iters_total, blk_iters);
+            atomicAdd(&stats->solves, blk_solves);
+        }
+        if (blk_fails) atomicAdd(&stats->fails, blk_fails);
+    }
     for (int i = threadIdx.x; i < 64; i += blockDim.x)
         if (hist[i]) atomicAdd(&stats->hist[i], (unsigned long long)hist[i]);
 }
@@ -207,10 +301,30 @@ bool newton_supported(int nspec, int topo) {
     return false;
 }
 
+int newton_variants(int nspec, int topo) { return newton_group_case(nspec, topo) ? 1 : 2; }
+
+int newton_persistent_blocks(const NetParams& P, int prec) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+#define X(ns, tp)                                                                                          \
+    if (P.nspec == ns && P.topo == tp) {                                                                   \
+        if (prec == 0)                                                                                     \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, newton_queue_kernel<ns, tp, double>, NEWTON_BLOCK, 0); \
+        else                                                                                               \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, newton_queue_kernel<ns, tp, float>, NEWTON_BLOCK, 0);  \
+    }
+    SDC_NEWTON_CASES(X)
+#undef X
+    if (per < 1) per = 1;
+    return sms * per;
+}
+
 cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, long long N, int dim,
                           const double* rhs, const double* guess, double* Uout, double* Rout,
                           const double* dt_dev, double dt_frac, double dtm_host, int* zone_status,
-                          int* zone_iters, DevStats* stats, cudaStream_t st) {
+                          int* zone_iters, DevStats* stats, cudaStream_t st, int variant,
+                          unsigned long long* queue, int persistent_blocks) {
     if (N <= 0) return cudaSuccess;
     if (P.nspec == 13 && P.topo == TOPO_CHAIN) {
         constexpr int ZPB = NEWTON_BLOCK / GROUP_L;
@@ -224,17 +338,28 @@ cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, lo
         return cudaGetLastError();
     }
     const unsigned grid = (unsigned)((N + NEWTON_BLOCK - 1) / NEWTON_BLOCK);
-#define X(ns, tp)                                                                                         \
-    if (P.nspec == ns && P.topo == tp) {                                                                  \
-        if (prec == 0)                                                                                    \
-            newton_kernel<ns, tp, double><<<grid, NEWTON_BLOCK, 0, st>>>(P, cfg, N, dim, rhs, guess, Uout,  \
-                                                                         Rout, dt_dev, dt_frac, dtm_host, \
-                                                                         zone_status, zone_iters, stats); \
-        else                                                                                              \
-            newton_kernel<ns, tp, float><<<grid, NEWTON_BLOCK, 0, st>>>(P, cfg, N, dim, rhs, guess, Uout,   \
-                                                                        Rout, dt_dev, dt_frac, dtm_host,  \
-                                                                        zone_status, zone_iters, stats);  \
-        return cudaGetLastError();                                                                        \
+    const bool q = variant == 1 && queue != nullptr && persistent_blocks > 0;
+    const unsigned pgrid = q ? (unsigned)(persistent_blocks < (long long)grid ? persistent_blocks : grid) : 0u;
+#define X(ns, tp)                                                                                          \
+    if (P.nspec == ns && P.topo == tp) {                                                                   \
+        if (q) {                                                                                           \
+            if (prec == 0)                                                                                 \
+                newton_queue_kernel<ns, tp, double><<<pgrid, NEWTON_BLOCK, 0, st>>>(                       \
+                    P, cfg, N, dim, rhs, guess, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status,        \
+                    zone_iters, stats, queue);                                                             \
+            else                                                                                           \
+                newton_queue_kernel<ns, tp, float><<<pgrid, NEWTON_BLOCK, 0, st>>>(                        \
+                    P, cfg, N, dim, rhs, guess, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status,        \
+                    zone_iters, stats, queue);                                                             \
+        } else if (prec == 0)                                                                              \
+            newton_kernel<ns, tp, double><<<grid, NEWTON_BLOCK, 0, st>>>(P, cfg, N, dim, rhs, guess, Uout,   \
+                                                                         Rout, dt_dev, dt_frac, dtm_host,  \
+                                                                         zone_status, zone_iters, stats);  \
+        else                                                                                               \
+            newton_kernel<ns, tp, float><<<grid, NEWTON_BLOCK, 0, st>>>(P, cfg, N, dim, rhs, guess, Uout,    \
+                                                                        Rout, dt_dev, dt_frac, dtm_host,   \
+                                                                        zone_status, zone_iters, stats);   \
+        return cudaGetLastError();                                                                         \
     }
     SDC_NEWTON_CASES(X)
 #undef X

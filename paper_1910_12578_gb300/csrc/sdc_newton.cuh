@@ -3,12 +3,14 @@
 //   G(w) = w - dt_m R(w; rho, rho u) - rhs_w = 0,   w = (rho E, rho X_i)
 // solved by Newton iteration on M = c I - dt_m dR/dw (c = 1), globalised by
 // pseudo-transient continuation (c = 1 + 1/h):
-//   start in Newton mode; a trial is admissible when T > 0 (finite) and every
-//   X_i >= min(0, X_i(rhs), X_i(start)) - 0.01; a Newton trial that is not
+//   start in Newton mode; a trial is admissible when T > 0 (finite) and, when
+//   every X_i(rhs) >= -0.01, every X_i >= min(0, X_i(rhs), X_i(start)) - 0.01
+//   (no floor for an rhs pushed further negative); a Newton trial that is not
 //   admissible or raises the scaled residual switches to pseudo mode (h = 1);
 //   an admissible pseudo trial is taken and h *= 3, a rejected one h /= 4;
-//   h >= 1e3 returns to Newton mode; converged when a taken Newton step has
-//   max(|d(rho E)|/|rho E|, max_i |d(rho X_i)|/rho) <= rtol.
+//   h >= 1e3 returns to Newton mode; converged when an admissible Newton step
+//   has max(|d(rho E)|/|rho E|, max_i |d(rho X_i)|/rho) <= rtol (taken even if
+//   the residual grew by round-off at the root).
 // One thread owns one zone; the dense matrix lives in registers as MT
 // (double: FP64 path; float: FP32 Jacobian / LU with FP64 residual and update,
 // so that Newton acts as iterative refinement).
@@ -50,106 +52,139 @@ __device__ __forceinline__ bool eval_state(const NetParams& P, double rho, doubl
     return s < INFINITY;
 }
 
-// Solve one zone.  On entry w holds the (density-rescaled) guess; on exit the
-// last taken iterate, R its reactive source.  Returns a ZONE_* code.
-template <int NS, int TOPO, typename MT>
-__device__ __forceinline__ int newton_zone(const NetParams& P, const NewtonCfg& cfg, double rho, double m2,
-                                           const double* rw, double dtm, double* w, double* Rout, int& iters) {
-    constexpr int N = NS + 1;
-    constexpr int NR = NS - 1;
-    const double inv_rho = rcp_nr(rho);
-    const double ke = 0.5 * m2 * inv_rho;
-    double ym[NS];
-#pragma unroll
-    for (int i = 0; i < NS; i++) ym[i] = inv_rho * P.inv_mass[i];
-    const double sE_inv = rcp_nr(fabs(rw[0]));
+// Register-resident state of one zone's solve.
+template <int NS>
+struct ZoneState {
+    static constexpr int N = NS + 1;
+    static constexpr int NR = NS - 1;
+    double rho, inv_rho, ke, sE_inv, phi, h;
+    double ym[NS], lower[NS], rw[N], w[N], G[N], k[NR], dk[NR], Y[NS];
+    int iters, status;
+    bool newton, have_k, done;
+};
 
+// Set up a zone: rw = reactive part of the rhs, w = the (density-rescaled)
+// guess, m2 = |rho u|^2 of the rhs.  Evaluates the residual at the start.
+template <int NS, int TOPO>
+__device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, double rho, double m2, double dtm) {
+    constexpr int N = NS + 1;
+    S.rho = rho;
+    S.inv_rho = rcp_nr(rho);
+    S.ke = 0.5 * m2 * S.inv_rho;
+#pragma unroll
+    for (int i = 0; i < NS; i++) S.ym[i] = S.inv_rho * P.inv_mass[i];
+    S.sE_inv = rcp_nr(fabs(S.rw[0]));
     // a start without a positive temperature is replaced by rhs
     {
-        const double Tg = P.gm1 * (w[0] - ke) * inv_rho;
+        const double Tg = P.gm1 * (S.w[0] - S.ke) * S.inv_rho;
         if (!(Tg > 0.0 && Tg < INFINITY)) {
 #pragma unroll
-            for (int r = 0; r < N; r++) w[r] = rw[r];
+            for (int r = 0; r < N; r++) S.w[r] = S.rw[r];
         }
     }
-    double lower[NS];
+    // the floor applies when the rhs is physical (every X_i >= -0.01)
+    bool physical = true;
+#pragma unroll
+    for (int i = 0; i < NS; i++) physical = physical && (S.rw[1 + i] * S.inv_rho >= -XMARGIN);
 #pragma unroll
     for (int i = 0; i < NS; i++) {
-        const double x = rw[1 + i] * inv_rho, xg = w[1 + i] * inv_rho;
+        const double x = S.rw[1 + i] * S.inv_rho, xg = S.w[1 + i] * S.inv_rho;
         double lo = x < 0.0 ? x : 0.0;
         lo = xg < lo ? xg : lo;
-        lower[i] = (lo - XMARGIN) * rho;  // as a bound on rho X_i
+        S.lower[i] = physical ? (lo - XMARGIN) * rho : -INFINITY;  // as a bound on rho X_i
     }
-    double k[NR], dk[NR], Y[NS], G[N];
-    double phi;
-    int status = ZONE_MAXIT;
-    iters = 0;
-    const bool have_k = eval_state<NS, TOPO>(P, rho, inv_rho, ke, ym, w, rw, dtm, sE_inv, k, dk, Y, G, phi);
-    if (!have_k) {
-        status = ZONE_NONPHYSICAL;
-    } else {
-        bool newton = true;
-        double h = PTC_H0;
-        int it;
-        for (it = 1; it <= cfg.maxit; it++) {
-            const double c = newton ? 1.0 : 1.0 + rcp_nr(h);
-            MT M[N][N];
-            build_matrix<NS, TOPO, MT>(P, rho, inv_rho, ym, k, dk, Y, c, dtm, M);
-            MT dv[N];
+    S.iters = 0;
+    S.status = ZONE_MAXIT;
+    S.newton = true;
+    S.h = PTC_H0;
+    S.have_k = eval_state<NS, TOPO>(P, rho, S.inv_rho, S.ke, S.ym, S.w, S.rw, dtm, S.sE_inv, S.k, S.dk, S.Y, S.G,
+                                    S.phi);
+    S.done = !S.have_k;
+    if (!S.have_k) S.status = ZONE_NONPHYSICAL;
+}
+
+// One pass of the solve (one linear solve); sets done and status at the end.
+template <int NS, int TOPO, typename MT>
+__device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& P, const NewtonCfg& cfg, double dtm) {
+    constexpr int N = NS + 1;
+    constexpr int NR = NS - 1;
+    S.iters++;
+    const double c = S.newton ? 1.0 : 1.0 + rcp_nr(S.h);
+    MT M[N][N];
+    build_matrix<NS, TOPO, MT>(P, S.rho, S.inv_rho, S.ym, S.k, S.dk, S.Y, c, dtm, M);
+    MT dv[N];
 #pragma unroll
-            for (int r = 0; r < N; r++) dv[r] = (MT)G[r];
-            if (!lu_solve<N, MT, MT>(M, dv)) { status = ZONE_SINGULAR; break; }
-            double tr[N];
+    for (int r = 0; r < N; r++) dv[r] = (MT)S.G[r];
+    if (!lu_solve<N, MT, MT>(M, dv)) {
+        S.status = ZONE_SINGULAR;
+        S.done = true;
+        return;
+    }
+    double tr[N];
 #pragma unroll
-            for (int r = 0; r < N; r++) tr[r] = w[r] - (double)dv[r];
-            bool ok = true;
+    for (int r = 0; r < N; r++) tr[r] = S.w[r] - (double)dv[r];
+    bool ok = true;
 #pragma unroll
-            for (int i = 0; i < NS; i++) ok = ok && (tr[1 + i] >= lower[i]);
-            double kt[NR], dkt[NR], Yt[NS], Gt[N];
-            double phit = 0.0;
-            if (ok) ok = eval_state<NS, TOPO>(P, rho, inv_rho, ke, ym, tr, rw, dtm, sE_inv, kt, dkt, Yt, Gt, phit);
-            if (newton && (!ok || phit > phi)) {
-                newton = false;
-                h = PTC_H0;
-                continue;
-            }
-            if (!ok) {
-                h /= PTC_SHRINK;
-                if (h < PTC_HMIN) { status = ZONE_NONPHYSICAL; break; }
-                continue;
-            }
+    for (int i = 0; i < NS; i++) ok = ok && (tr[1 + i] >= S.lower[i]);
+    double kt[NR], dkt[NR], Yt[NS], Gt[N];
+    double phit = 0.0;
+    if (ok)
+        ok = eval_state<NS, TOPO>(P, S.rho, S.inv_rho, S.ke, S.ym, tr, S.rw, dtm, S.sE_inv, kt, dkt, Yt, Gt, phit);
+    // an admissible Newton step that meets the stop test converges even if the
+    // residual grew by round-off at the root
+    bool small = false;
+    if (S.newton && ok) {
+        small = fabs((double)dv[0]) <= cfg.rtol * fabs(tr[0]);
+        const double tol_x = cfg.rtol * S.rho;
 #pragma unroll
-            for (int r = 0; r < N; r++) { w[r] = tr[r]; G[r] = Gt[r]; }
-#pragma unroll
-            for (int j = 0; j < NR; j++) { k[j] = kt[j]; dk[j] = dkt[j]; }
-#pragma unroll
-            for (int i = 0; i < NS; i++) Y[i] = Yt[i];
-            phi = phit;
-            if (newton) {
-                bool conv = fabs((double)dv[0]) <= cfg.rtol * fabs(w[0]);
-                const double tol_x = cfg.rtol * rho;
-#pragma unroll
-                for (int i = 0; i < NS; i++) conv = conv && (fabs((double)dv[1 + i]) <= tol_x);
-                if (conv) { status = ZONE_OK; break; }
-            } else {
-                h *= PTC_GROW;
-                if (h >= PTC_HNEWTON) newton = true;
-            }
+        for (int i = 0; i < NS; i++) small = small && (fabs((double)dv[1 + i]) <= tol_x);
+    }
+    if (S.newton && !small && (!ok || phit > S.phi)) {
+        S.newton = false;
+        S.h = PTC_H0;
+    } else if (!ok) {
+        S.h /= PTC_SHRINK;
+        if (S.h < PTC_HMIN) {
+            S.status = ZONE_NONPHYSICAL;
+            S.done = true;
+            return;
         }
-        iters = it > cfg.maxit ? cfg.maxit : it;
-    }
-    // reactive source at the final state (from its cached rate constants)
-    if (have_k) {
-        sources<NS, TOPO>(P, rho, k, Y, Rout);
     } else {
-        const double T = P.gm1 * (w[0] - ke) * inv_rho;
-        double kf[NR], dkf[NR], Yf[NS];
-        rate_consts<NR>(P, rho, T, kf, dkf);
 #pragma unroll
-        for (int i = 0; i < NS; i++) Yf[i] = w[1 + i] * ym[i];
-        sources<NS, TOPO>(P, rho, kf, Yf, Rout);
+        for (int r = 0; r < N; r++) { S.w[r] = tr[r]; S.G[r] = Gt[r]; }
+#pragma unroll
+        for (int j = 0; j < NR; j++) { S.k[j] = kt[j]; S.dk[j] = dkt[j]; }
+#pragma unroll
+        for (int i = 0; i < NS; i++) S.Y[i] = Yt[i];
+        S.phi = phit;
+        if (S.newton) {
+            if (small) {
+                S.status = ZONE_OK;
+                S.done = true;
+                return;
+            }
+        } else {
+            S.h *= PTC_GROW;
+            if (S.h >= PTC_HNEWTON) S.newton = true;
+        }
     }
-    return status;
+    if (S.iters >= cfg.maxit) S.done = true;  // status stays ZONE_MAXIT
+}
+
+// Reactive source at the final state (from its cached rate constants).
+template <int NS, int TOPO>
+__device__ __forceinline__ void zone_source(const ZoneState<NS>& S, const NetParams& P, double* Rout) {
+    constexpr int NR = NS - 1;
+    if (S.have_k) {
+        sources<NS, TOPO>(P, S.rho, S.k, S.Y, Rout);
+    } else {
+        const double T = P.gm1 * (S.w[0] - S.ke) * S.inv_rho;
+        double kf[NR], dkf[NR], Yf[NS];
+        rate_consts<NR>(P, S.rho, T, kf, dkf);
+#pragma unroll
+        for (int i = 0; i < NS; i++) Yf[i] = S.w[1 + i] * S.ym[i];
+        sources<NS, TOPO>(P, S.rho, kf, Yf, Rout);
+    }
 }
 
 }  // namespace sdcd

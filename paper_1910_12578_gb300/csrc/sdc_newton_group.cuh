@@ -148,13 +148,21 @@ __device__ __forceinline__ int newton_zone_group(const NetParams& P, const Newto
         }
         __syncwarp(mask);
     }
-    // admissibility floor on rho X_i for this lane's species rows
+    // admissibility floor on rho X_i for this lane's species rows; it applies
+    // when the rhs is physical (every X_i >= -0.01)
+    bool physical = true;
+#pragma unroll
+    for (int t = 0; t < RL; t++) {
+        const int row = lane + L * t;
+        if (row >= 1 && row < N) physical = physical && (rw_rows[t] * inv_rho >= -XMARGIN);
+    }
+    physical = group_all<L>(mask, physical);
     double lower[RL];
 #pragma unroll
     for (int t = 0; t < RL; t++) {
         const int row = lane + L * t;
         lower[t] = -INFINITY;
-        if (row >= 1 && row < N) {
+        if (physical && row >= 1 && row < N) {
             const double x = rw_rows[t] * inv_rho, xg = zs[Lay::O_W + row] * inv_rho;
             double lo = x < 0.0 ? x : 0.0;
             lo = xg < lo ? xg : lo;
@@ -318,7 +326,22 @@ __device__ __forceinline__ int newton_zone_group(const NetParams& P, const Newto
                 phit = group_eval<NS, MT, L>(P, mask, lane, zs, Lay::O_TR, Lay::O_KT, Lay::O_DKT, Lay::O_YT, Lay::O_GT,
                                              rho, inv_rho, ke, ym, rw_rows, dtm, sE_inv);
             ok = ok && phit < INFINITY;
-            if (newton && (!ok || phit > phi)) {
+            // an admissible Newton step that meets the stop test converges even
+            // if the residual grew by round-off at the root
+            bool small = false;
+            if (newton && ok) {
+                const double trE = zs[Lay::O_TR + 0];
+                small = true;
+#pragma unroll
+                for (int t = 0; t < RL; t++) {
+                    const int row = lane + L * t;
+                    if (row >= N) break;
+                    const double dd = fabs(zs[Lay::O_D + row]);
+                    small = small && (row == 0 ? dd <= cfg.rtol * fabs(trE) : dd <= cfg.rtol * rho);
+                }
+                small = group_all<L>(mask, small);
+            }
+            if (newton && !small && (!ok || phit > phi)) {
                 newton = false;
                 h = PTC_H0;
                 __syncwarp(mask);
@@ -343,17 +366,7 @@ __device__ __forceinline__ int newton_zone_group(const NetParams& P, const Newto
             phi = phit;
             __syncwarp(mask);
             if (newton) {
-                const double wE = zs[Lay::O_W + 0];
-                bool conv = true;
-#pragma unroll
-                for (int t = 0; t < RL; t++) {
-                    const int row = lane + L * t;
-                    if (row >= N) break;
-                    const double dd = fabs(zs[Lay::O_D + row]);
-                    conv = conv && (row == 0 ? dd <= cfg.rtol * fabs(wE) : dd <= cfg.rtol * rho);
-                }
-                conv = group_all<L>(mask, conv);
-                if (conv) { status = ZONE_OK; break; }
+                if (small) { status = ZONE_OK; break; }
             } else {
                 h *= PTC_GROW;
                 if (h >= PTC_HNEWTON) newton = true;

@@ -14,20 +14,23 @@ namespace sdcd {
     X(3, 7)                  \
     X(3, 13)
 
-// Tiles: 1D lines of 64 zones; in 3D cubes of 8^3 (one face per thread in every
-// direction), or 8 x 8 x 4 when 8^3 primitives and slopes would not fit in
-// shared memory (many species).
-template <int DIM, int NS> struct Tile;
-template <int NS> struct Tile<1, NS> { static constexpr int X = 64, Y = 1, Z = 1; };
-template <int NS> struct Tile<3, NS> {
-    static constexpr int X = 8, Y = 8, Z = (NS <= 7 ? 8 : 4);
+// Tile shapes (variant V, chosen by the autotuner): 1D lines of 64 zones; in 3D
+// cubes of 8^3 (one face per thread in every direction; V = 0) or 8 x 8 x 4
+// (V = 1, and the only shape when 8^3 primitives and slopes would not fit in
+// shared memory with many species).
+template <int DIM, int NS, int V> struct Tile;
+template <int NS, int V> struct Tile<1, NS, V> { static constexpr int X = 64, Y = 1, Z = 1; };
+template <int NS, int V> struct Tile<3, NS, V> {
+    static constexpr int X = 8, Y = 8, Z = (NS <= 7 && V == 0 ? 8 : 4);
 };
 
-template <int DIM, int NS>
+template <int DIM, int NS, int V>
 constexpr size_t smem_bytes() {
-    using G = TileGeom<DIM, Tile<DIM, NS>::X, Tile<DIM, NS>::Y, Tile<DIM, NS>::Z>;
+    using G = TileGeom<DIM, Tile<DIM, NS, V>::X, Tile<DIM, NS, V>::Y, Tile<DIM, NS, V>::Z>;
     return sizeof(double) * (size_t)(2 + DIM + NS) * (G::NC + G::NB);
 }
+
+int stencil_variants(int dim, int nspec) { return (dim == 3 && nspec <= 7) ? 2 : 1; }
 
 bool stencil_supported(int dim, int nspec) {
 #define X(d, ns) \
@@ -37,56 +40,70 @@ bool stencil_supported(int dim, int nspec) {
     return false;
 }
 
-void stencil_tile(int dim, int nspec, int t[3]) {
+void stencil_tile(int dim, int nspec, int variant, int t[3]) {
     t[0] = 64; t[1] = 1; t[2] = 1;
-#define X(d, ns)                                                                       \
-    if (dim == d && nspec == ns) {                                                     \
-        t[0] = Tile<d, ns>::X; t[1] = Tile<d, ns>::Y; t[2] = Tile<d, ns>::Z;           \
+#define X(d, ns)                                                                                   \
+    if (dim == d && nspec == ns) {                                                                 \
+        if (variant == 0) { t[0] = Tile<d, ns, 0>::X; t[1] = Tile<d, ns, 0>::Y; t[2] = Tile<d, ns, 0>::Z; } \
+        else { t[0] = Tile<d, ns, 1>::X; t[1] = Tile<d, ns, 1>::Y; t[2] = Tile<d, ns, 1>::Z; }     \
     }
     SDC_STENCIL_CASES(X)
 #undef X
 }
 
-size_t stencil_smem_bytes(int dim, int nspec) {
+size_t stencil_smem_bytes(int dim, int nspec, int variant) {
 #define X(d, ns) \
-    if (dim == d && nspec == ns) return smem_bytes<d, ns>();
+    if (dim == d && nspec == ns) return variant == 0 ? smem_bytes<d, ns, 0>() : smem_bytes<d, ns, 1>();
     SDC_STENCIL_CASES(X)
 #undef X
     return 0;
 }
 
+template <int d, int ns, int V>
+cudaError_t prepare_one() {
+    constexpr int TX = Tile<d, ns, V>::X, TY = Tile<d, ns, V>::Y, TZ = Tile<d, ns, V>::Z;
+    cudaError_t e = cudaFuncSetAttribute(stencil_kernel<d, ns, TX, TY, TZ, STENCIL_A>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<d, ns, V>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(stencil_kernel<d, ns, TX, TY, TZ, STENCIL_A_RHS>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<d, ns, V>());
+}
+
 cudaError_t stencil_prepare(int dim, int nspec) {
-#define X(d, ns)                                                                                          \
-    if (dim == d && nspec == ns) {                                                                        \
-        constexpr int TX = Tile<d, ns>::X, TY = Tile<d, ns>::Y, TZ = Tile<d, ns>::Z;                      \
-        cudaError_t e = cudaFuncSetAttribute(stencil_kernel<d, ns, TX, TY, TZ, STENCIL_A>,                \
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,                 \
-                                             (int)smem_bytes<d, ns>());                                   \
-        if (e != cudaSuccess) return e;                                                                   \
-        return cudaFuncSetAttribute(stencil_kernel<d, ns, TX, TY, TZ, STENCIL_A_RHS>,                     \
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<d, ns>()); \
+#define X(d, ns)                                                     \
+    if (dim == d && nspec == ns) {                                   \
+        cudaError_t e = prepare_one<d, ns, 0>();                     \
+        if (e != cudaSuccess || stencil_variants(d, ns) < 2) return e; \
+        return prepare_one<d, ns, 1>();                              \
     }
     SDC_STENCIL_CASES(X)
 #undef X
     return cudaErrorInvalidValue;
 }
 
+template <int d, int ns, int V>
+cudaError_t launch_one(const NetParams& P, int limiter, long long Ntot, const BoxDev* boxes, const TileDev* tiles,
+                       int ntiles, const double* U, double* A, int mode, const RhsArgs& ra, cudaStream_t st) {
+    constexpr int TX = Tile<d, ns, V>::X, TY = Tile<d, ns, V>::Y, TZ = Tile<d, ns, V>::Z;
+    constexpr int NTH = TileGeom<d, TX, TY, TZ>::THREADS;
+    const size_t sm = smem_bytes<d, ns, V>();
+    if (mode == STENCIL_A)
+        stencil_kernel<d, ns, TX, TY, TZ, STENCIL_A><<<ntiles, NTH, sm, st>>>(P, limiter, Ntot, boxes, tiles, U, A, ra);
+    else
+        stencil_kernel<d, ns, TX, TY, TZ, STENCIL_A_RHS>
+            <<<ntiles, NTH, sm, st>>>(P, limiter, Ntot, boxes, tiles, U, A, ra);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_stencil(const NetParams& P, int dim, int limiter, long long Ntot, const BoxDev* boxes,
                            const TileDev* tiles, int ntiles, const double* U, double* A, int mode,
-                           const RhsArgs& ra, cudaStream_t st) {
+                           const RhsArgs& ra, cudaStream_t st, int variant) {
     if (ntiles <= 0) return cudaSuccess;
-#define X(d, ns)                                                                                           \
-    if (dim == d && P.nspec == ns) {                                                                       \
-        constexpr int TX = Tile<d, ns>::X, TY = Tile<d, ns>::Y, TZ = Tile<d, ns>::Z;                       \
-        constexpr int NTH = TileGeom<d, TX, TY, TZ>::THREADS;                                              \
-        const size_t sm = smem_bytes<d, ns>();                                                             \
-        if (mode == STENCIL_A)                                                                             \
-            stencil_kernel<d, ns, TX, TY, TZ, STENCIL_A>                                                   \
-                <<<ntiles, NTH, sm, st>>>(P, limiter, Ntot, boxes, tiles, U, A, ra);                       \
-        else                                                                                               \
-            stencil_kernel<d, ns, TX, TY, TZ, STENCIL_A_RHS>                                               \
-                <<<ntiles, NTH, sm, st>>>(P, limiter, Ntot, boxes, tiles, U, A, ra);                       \
-        return cudaGetLastError();                                                                         \
+#define X(d, ns)                                                                                      \
+    if (dim == d && P.nspec == ns) {                                                                  \
+        if (variant == 0 || stencil_variants(d, ns) < 2)                                              \
+            return launch_one<d, ns, 0>(P, limiter, Ntot, boxes, tiles, ntiles, U, A, mode, ra, st);  \
+        return launch_one<d, ns, 1>(P, limiter, Ntot, boxes, tiles, ntiles, U, A, mode, ra, st);      \
     }
     SDC_STENCIL_CASES(X)
 #undef X

@@ -24,7 +24,7 @@ PREC_FP64, PREC_FP32_JAC = 0, 1
 # entry points declared in include/sdc.h
 EXPORTS = ["sdc_init_box", "sdc_advective_term", "sdc_node_integral", "sdc_react_newton", "sdc_step",
            "sdc_step_profile", "sdc_launches_per_step", "sdc_cfl_dt", "sdc_sizes", "sdc_destroy",
-           "sdc_status_string", "sdc_step_static", "sdc_selftest_math"]
+           "sdc_status_string", "sdc_step_static", "sdc_selftest_math", "sdc_autotune", "sdc_set_variants"]
 
 
 class SdcError(RuntimeError):
@@ -56,6 +56,17 @@ class Stats(C.Structure):
     def as_dict(self):
         return {"newton_iters_total": self.newton_iters_total, "newton_solves": self.newton_solves,
                 "n_fail": self.n_fail, "hist": list(self.hist)}
+
+
+class Tuning(C.Structure):
+    _fields_ = [("stencil_variants", C.c_int), ("newton_variants", C.c_int), ("stencil_choice", C.c_int),
+                ("newton_choice", C.c_int), ("ms_stencil", C.c_float * 4), ("ms_newton", C.c_float * 4)]
+
+    def as_dict(self):
+        return {"stencil_variants": self.stencil_variants, "newton_variants": self.newton_variants,
+                "stencil_choice": self.stencil_choice, "newton_choice": self.newton_choice,
+                "ms_stencil": list(self.ms_stencil)[:self.stencil_variants],
+                "ms_newton": list(self.ms_newton)[:self.newton_variants]}
 
 
 class Profile(C.Structure):
@@ -90,6 +101,8 @@ def load(path: str = LIB_PATH):
     L.sdc_step_profile.argtypes = [vp, dp, C.c_double, C.POINTER(Stats), C.POINTER(Profile)]
     L.sdc_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
     L.sdc_selftest_math.argtypes = [dp, C.c_longlong, dp, dp, vp]
+    L.sdc_autotune.argtypes = [vp, dp, C.c_double, C.POINTER(Tuning)]
+    L.sdc_set_variants.argtypes = [vp, C.c_int, C.c_int]
     L.sdc_step_static.argtypes = [C.POINTER(Box), C.c_int, C.POINTER(Network), C.POINTER(Params), vp, dp,
                                   C.c_double, C.POINTER(Stats)]
     L.sdc_sizes.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -98,7 +111,8 @@ def load(path: str = LIB_PATH):
     L.sdc_status_string.argtypes = [C.c_int]
     L.sdc_status_string.restype = C.c_char_p
     for name in ("sdc_init_box", "sdc_advective_term", "sdc_node_integral", "sdc_react_newton", "sdc_step",
-                 "sdc_cfl_dt", "sdc_sizes", "sdc_step_profile", "sdc_launches_per_step", "sdc_step_static", "sdc_selftest_math"):
+                 "sdc_cfl_dt", "sdc_sizes", "sdc_step_profile", "sdc_launches_per_step", "sdc_step_static", "sdc_selftest_math", "sdc_autotune",
+                 "sdc_set_variants"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -214,6 +228,16 @@ class Context:
         s = self.L.sdc_step_profile(self._h, _ptr(U), float(dt), C.byref(st), C.byref(pr))
         self._check(s, "sdc_step_profile", allow_noconv=True)
         return st, pr
+
+    def autotune(self, U, dt):
+        """Pick the stencil tile shape and Newton variant by timing one step of
+        each on a scratch copy of U; returns the Tuning record."""
+        t = Tuning()
+        self._check(self.L.sdc_autotune(self._h, _ptr(U), float(dt), C.byref(t)), "sdc_autotune")
+        return t
+
+    def set_variants(self, stencil_variant, newton_variant):
+        self._check(self.L.sdc_set_variants(self._h, int(stencil_variant), int(newton_variant)), "sdc_set_variants")
 
     def launches_per_step(self):
         n = C.c_int()

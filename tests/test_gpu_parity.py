@@ -161,6 +161,44 @@ def test_newton_raphson_reciprocal_and_sqrt_within_two_ulp(torch_cuda):
     assert ulps(q, q_ref) <= 2
 
 
+@pytest.mark.parametrize("name", ["box16", "ragged"])
+def test_kernel_variants_agree_bitwise(torch_cuda, name):
+    """The queue-fed persistent Newton kernel and the 8x8x4 tile shape do the
+    same arithmetic per zone and per face as the defaults: identical results."""
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = PROBS[name]
+    outs = []
+    for sv, nv in ((0, 0), (0, 1), (1, 0), (1, 1)):
+        ctx = sdc.Context(P)
+        ctx.set_variants(sv, nv)
+        Ud = dev(torch, U)
+        st = ctx.step(Ud, 1e-3)
+        st = ctx.step(Ud, 1e-3)
+        outs.append((Ud.cpu().numpy(), st.newton_iters_total, st.n_fail, list(st.hist)))
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0])
+        assert o[1:] == outs[0][1:]
+
+
+def test_autotune_keeps_U_and_picks_valid_variants(torch_cuda):
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = PROBS["box16"]
+    ctx = sdc.Context(P)
+    Ud = dev(torch, U)
+    t = ctx.autotune(Ud, 1e-3)
+    torch.cuda.synchronize()
+    assert np.array_equal(Ud.cpu().numpy(), U.reshape(Ud.shape))
+    assert 0 <= t.stencil_choice < t.stencil_variants == 2
+    assert 0 <= t.newton_choice < t.newton_variants == 2
+    assert all(x > 0 for x in t.as_dict()["ms_newton"])
+    o = O.Oracle(P)
+    Uo, _ = o.step(U, 1e-3)
+    ctx.step(Ud, 1e-3)
+    assert rel_err(Ud.cpu().numpy(), Uo, P.nvar, P.dim).max() <= TOL64
+
+
 def test_step_is_deterministic(torch_cuda):
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
