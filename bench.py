@@ -168,6 +168,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def rank_seed(seed, rank):
+    """Each rank runs its own box: the ranks' problems are independent (weak scaling)."""
+    return seed + rank
+
+
+def job_value(local_ms, units_per_rank, steps, world_size, reduce_max=None):
+    """Whole-job throughput: the slowest rank's time (max over ranks) and the
+    units of all ranks.  reduce_max(x) returns the maximum of x over the ranks."""
+    t = reduce_max(local_ms) if (reduce_max and world_size > 1) else local_ms
+    return units_per_rank * steps * world_size / (t * 1e-3), t
+
+
+def torch_reduce_max(device):
+    def f(x):
+        import torch
+        import torch.distributed as tdist
+        v = torch.tensor([x], dtype=torch.float64, device=device)
+        tdist.all_reduce(v, op=tdist.ReduceOp.MAX)
+        return float(v.item())
+    return f
+
+
 def dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -345,7 +367,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if not os.path.exists(sdc.LIB_PATH):
         B.build()
-    P, U, desc = workload(args.config, args.seed + rank)
+    P, U, desc = workload(args.config, rank_seed(args.seed, rank))
     P0 = as_list(P)[0]
     prec = sdc.PREC_FP64 if args.prec == "fp64" else sdc.PREC_FP32_JAC
     ctx = sdc.Context(P, prec=prec)
@@ -384,12 +406,7 @@ def run_ours(args):
     barrier()
     ck = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = units * args.steps * ws / (total_ms * 1e-3)
+    value, total_ms = job_value(sum(step_ms), units, args.steps, ws, torch_reduce_max("cuda"))
 
     # ---- end to end through the public API with host buffers (pinned), copies timed
     Uh = U0.cpu().pin_memory()
@@ -407,11 +424,7 @@ def run_ours(args):
         Uout.copy_(Ud, non_blocking=True)
     eb.record()
     torch.cuda.synchronize()
-    e2e_ms = ea.elapsed_time(eb) / e2e_steps
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_value, _ = job_value(ea.elapsed_time(eb) / e2e_steps, units, 1, ws, torch_reduce_max("cuda"))
     nbytes = U0.numel() * 8
 
     # ---- per-kernel-class times of the same step (eager launches, CUDA events on the context stream)
@@ -479,7 +492,7 @@ def run_ours(args):
                        "l2": "flushed before every timed step (256 MB write)",
                        "parallelism": "independent box per GPU" if ws > 1 else "1 GPU"},
             "clocks": ck,
-            "e2e": {"value": units * ws / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes},
             "gpu_launches": per_step * args.steps,
             "roofline": roof,
