@@ -8,9 +8,9 @@
 //    (a few correct bits, issued outside the FP64 FMA pipe); two steps give a
 //    result within a few ulp of the correctly rounded value;
 //  * exact operations on IEEE-754 bit patterns done on the integer pipe: |x|,
-//    sign tests, x2 and x1/2 by exponent increment/decrement (exact for normal
-//    numbers), and min of non-negative doubles (their bit patterns order like
-//    the values).
+//    sign tests, x1/4 by an exponent decrement (exact while the result stays
+//    normal; callers guard the range), and min of non-negative doubles (their
+//    bit patterns order like the values).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -61,20 +61,23 @@ constexpr long long EXP_ONE = 1ll << 52;  // one unit of the exponent field
 // MC-limited slope from three values with integer-pipe limiting:
 //   dl = q0 - qm, dr = qp - q0; slope = 0 when dl*dr <= 0, else
 //   sign(dl+dr) * min(2|dl|, 2|dr|, |dl+dr|/2).
-// Returns half the slope (the offset from the zone average to a face).
-// Matches the plain formula exactly for normal numbers (the scalings by two
-// are exponent shifts); it differs only when dl*dr underflows to zero.
+// Returns half the slope (the offset from the zone average to a face), formed
+// as sign(s) * min(|dl|, |dr|, |s|/4) with s = dl + dr: the minimum is taken on
+// bit patterns (they order like the values for every non-negative double,
+// subnormals included) and |s|/4 is an exponent decrement of two, exact while
+// |s| >= 2^-1020.  Below that the offset is returned as zero; it then differs
+// from the plain formula by less than 2^-1022 in absolute value.  The plain
+// formula's dl*dr test also reads zero when the product underflows; here only
+// the signs decide.  Everywhere else the two agree exactly.
 __device__ __forceinline__ double mc_half_slope(int limiter, double qm, double q0, double qp) {
     const double dl = q0 - qm, dr = qp - q0, s = dl + dr;
     if (!limiter) return 0.25 * s;
     const long long bl = dbits(dl), br = dbits(dr), bs = dbits(s);
-    const long long al = bl & ABS_MASK, ar = br & ABS_MASK;
-    if (((bl ^ br) < 0) || al == 0 || ar == 0) return 0.0;
-    // both nonzero with one sign: s has that sign and |s| >= 2 min(|dl|, |dr|)
-    const long long m2 = (al < ar ? al : ar) + EXP_ONE;   // 2 min(|dl|, |dr|)
-    const long long hs = (bs & ABS_MASK) - EXP_ONE;        // |s| / 2
-    long long lim = m2 < hs ? m2 : hs;
-    lim -= EXP_ONE;                                       // half the limited slope
+    const long long al = bl & ABS_MASK, ar = br & ABS_MASK, as = bs & ABS_MASK;
+    if (((bl ^ br) < 0) || al == 0 || ar == 0 || as < 3 * EXP_ONE) return 0.0;
+    const long long q = as - 2 * EXP_ONE;  // |s| / 4
+    long long lim = al < ar ? al : ar;
+    lim = lim < q ? lim : q;
     return bitsd(lim | (bs & SIGN_BIT));
 }
 

@@ -68,6 +68,34 @@ def test_advective_term_parity(torch_cuda, name):
     assert err.max() <= TOL64, err
 
 
+def test_advective_term_subnormal_inputs(torch_cuda):
+    """States with subnormal momenta and mass fractions (a symmetric cancellation
+    leaves momenta near 1e-310): the MC limiter's bit-pattern arithmetic must stay
+    finite and agree with the plain formula."""
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = PROBS["box16"]
+    U = U.copy()
+    rng = np.random.default_rng(11)
+    tiny = rng.choice([-1.0, 1.0], size=U.shape[1:]) * rng.uniform(0.0, 3e-308, size=U.shape[1:])
+    U[2] = np.where(rng.random(U.shape[1:]) < 0.5, tiny, 0.0)       # y momentum: 0 or subnormal
+    U[3] = tiny * (rng.random(U.shape[1:]) < 0.25)                   # z momentum: sparse subnormals
+    U[-1] = U[0] * np.abs(tiny) * 1e-3                                # a trace species in the subnormal range
+    o = O.Oracle(P)
+    A_orc = o.advective(U)
+    ctx = sdc.Context(P)
+    Ud = dev(torch, U)
+    Ad = torch.empty_like(Ud)
+    ctx.advective_term(Ud, Ad)
+    torch.cuda.synchronize()
+    A_gpu = Ad.cpu().numpy()
+    assert np.isfinite(A_gpu).all()
+    # fields whose true values are subnormal compare in absolute terms (2^-1022 bound)
+    scale = np.abs(A_orc).reshape(P.nvar, -1).max(1)
+    diff = np.abs(A_gpu - A_orc).reshape(P.nvar, -1).max(1)
+    assert (diff <= np.maximum(TOL64 * scale, 1e-300)).all(), (diff, scale)
+
+
 @pytest.mark.parametrize("name", ["1d", "box16"])
 def test_node_integral_parity(torch_cuda, name):
     torch = torch_cuda
