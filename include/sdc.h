@@ -186,6 +186,25 @@ sdc_status sdc_set_variants(sdc_ctx* ctx, int stencil_variant, int newton_varian
 /* Number of kernels one sdc_step launches (its graph plus the dt store). */
 sdc_status sdc_launches_per_step(const sdc_ctx* ctx, int* launches);
 
+/* Adjoint of one SDC step (vector-Jacobian product of sdc_step):
+     gU_n = (dU^{n+1}/dU^n)^T gU_np1,   g_a += (dU^{n+1}/da)^T gU_np1
+   with a the rate prefactors of the network.  U_n is the step's checkpoint
+   (its input state); the step is recomputed from it with every node state kept,
+   then swept in reverse: the implicit reaction update through the
+   implicit-function theorem (a transposed solve with the Jacobian at the
+   converged root), the right-hand side and quadrature as linear maps, and the
+   advective term through its face fluxes with the limiter and HLLC branches of
+   the recomputed step fixed.  All pointers are device arrays: U_n, gU_np1, gU_n
+   [nvar][Ntot]; g_a [nreac], accumulated (NULL: not formed).  The first call
+   allocates an adjoint workspace in the context.  Supported: the networks of
+   the thread-per-zone kernels (not the 13-species chain): SDC_ERR_INVALID_ARG
+   otherwise.  Deterministic (no floating-point atomics). */
+sdc_status sdc_step_backward(sdc_ctx* ctx, const double* U_n, double dt, const double* gU_np1, double* gU_n,
+                             double* g_a);
+
+/* Replace the rate prefactors a_j of the context's network (host array [nreac]). */
+sdc_status sdc_set_rates(sdc_ctx* ctx, const double* a);
+
 /* CFL time step: dt = cfl / max over zones of sum_d (|u_d| + c) / dx_d.
    Waits for the stream; *dt_out is a host pointer. */
 sdc_status sdc_cfl_dt(sdc_ctx* ctx, const double* U, double cfl, double* dt_out);

@@ -18,7 +18,7 @@ LIB = os.path.join(PKG, "libsdc.so")
 BUILD = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-UNITS = ["sdc_newton.cu", "sdc_stencil.cu", "sdc_api.cu"]
+UNITS = ["sdc_newton.cu", "sdc_stencil.cu", "sdc_api.cu", "sdc_adjoint.cu"]
 
 
 def _nvcc() -> str:

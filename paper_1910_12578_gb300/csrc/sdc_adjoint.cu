@@ -1,0 +1,322 @@
+// sdc_adjoint.cu -- kernels of the adjoint of one SDC step (paper section 2,
+// Eq. sdc:general): the advective-term VJP (per face, forward mode, then a
+// deterministic per-zone gather), the VJP of the reactive source and of the
+// implicit reaction update (implicit-function theorem: a transposed solve with
+// the Jacobian at the converged root), the adjoint of the right-hand side, and
+// a fixed-order reduction of the rate-prefactor gradient.
+#include "sdc_adjoint.cuh"
+#include "sdc_adjoint_launch.h"
+
+namespace sdcd {
+
+constexpr int ADJ_BLOCK = 128;
+
+__device__ __forceinline__ int box_of(const BoxDev* boxes, int nbox, long long z) {
+    int lo = 0, hi = nbox - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (boxes[mid].off <= z) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// global index of the zone shifted by o along dir inside its (periodic) box
+__device__ __forceinline__ long long shifted(const BoxDev& b, long long z, int dir, int o) {
+    const long long l = z - b.off;
+    int c[3];
+    c[0] = (int)(l % b.n[0]);
+    c[1] = (int)((l / b.n[0]) % b.n[1]);
+    c[2] = (int)(l / ((long long)b.n[0] * b.n[1]));
+    c[dir] = ((c[dir] + o) % b.n[dir] + b.n[dir]) % b.n[dir];
+    return b.off + c[0] + (long long)b.n[0] * (c[1] + (long long)b.n[1] * c[2]);
+}
+
+// G[dir][z][4*NV]: transposed Jacobian of the flux through the face between z
+// and z+1 (along dir) times that face's adjoint, for the inputs of zones
+// z-1, z, z+1, z+2.
+template <int DIM, int NS>
+__global__ void __launch_bounds__(ADJ_BLOCK)
+stencil_vjp_kernel(double gamma, int limiter, long long N, const BoxDev* __restrict__ boxes, int nbox,
+                   const double* __restrict__ U, const double* __restrict__ Abar, double* __restrict__ G) {
+    constexpr int NV = 2 + DIM + NS;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * DIM) return;
+    const int dir = (int)(t / N);
+    const long long z = t - (long long)dir * N;
+    const BoxDev b = boxes[box_of(boxes, nbox, z)];
+    long long zz[4];
+#pragma unroll
+    for (int o = 0; o < 4; o++) zz[o] = shifted(b, z, dir, o - 1);
+    // face adjoint: A_l -= F idx, A_{l+1} += F idx
+    double Fbar[NV];
+#pragma unroll
+    for (int f = 0; f < NV; f++) Fbar[f] = (Abar[f * N + zz[2]] - Abar[f * N + zz[1]]) * b.idx[dir];
+    Dual Uz[4][NV];
+#pragma unroll
+    for (int o = 0; o < 4; o++)
+#pragma unroll
+        for (int f = 0; f < NV; f++) Uz[o][f] = Dual(U[f * N + zz[o]], 0.0);
+    double* out = G + ((long long)dir * N + z) * (4 * NV);
+    for (int j = 0; j < 4 * NV; j++) {
+        const int o = j / NV, f = j % NV;
+        Uz[o][f].d = 1.0;
+        Dual F[NV];
+        face_flux_dual<DIM, NS>(gamma, limiter, dir, Uz, F);
+        Uz[o][f].d = 0.0;
+        double c = 0.0;
+#pragma unroll
+        for (int q = 0; q < NV; q++) c += Fbar[q] * F[q].d;
+        out[j] = c;
+    }
+}
+
+// Ubar_z += sum over directions and over the four faces whose stencil holds z
+template <int DIM, int NS>
+__global__ void __launch_bounds__(ADJ_BLOCK)
+stencil_vjp_gather(long long N, const BoxDev* __restrict__ boxes, int nbox, const double* __restrict__ G,
+                   double* __restrict__ Ubar) {
+    constexpr int NV = 2 + DIM + NS;
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= N) return;
+    const BoxDev b = boxes[box_of(boxes, nbox, z)];
+    double acc[NV];
+#pragma unroll
+    for (int f = 0; f < NV; f++) acc[f] = 0.0;
+    for (int dir = 0; dir < DIM; dir++)
+#pragma unroll
+        for (int o = 0; o < 4; o++) {
+            // z is input slot o of the face whose left zone is z + 1 - o
+            const long long l = shifted(b, z, dir, 1 - o);
+            const double* g = G + ((long long)dir * N + l) * (4 * NV) + o * NV;
+#pragma unroll
+            for (int f = 0; f < NV; f++) acc[f] += g[f];
+        }
+#pragma unroll
+    for (int f = 0; f < NV; f++) Ubar[f * N + z] += acc[f];
+}
+
+// dR/dw (n x n, row = reactive field, col = unknown), dR/da_j (n x nr) and R
+// at the state (rho, mom, w) of an alpha chain or a generic network.
+template <int NS, int TOPO>
+__device__ __forceinline__ void reaction_derivs(const NetParams& P, double rho, double m2, const double* w,
+                                                double (*dR)[NS + 1], double (*dRa)[NS - 1]) {
+    constexpr int N = NS + 1;
+    constexpr int NR = NS - 1;
+    const double inv_rho = 1.0 / rho;
+    const double T = P.gm1 * (w[0] - 0.5 * m2 * inv_rho) * inv_rho;
+    double k[NR], dk[NR], Y[NS];
+    rate_consts<NR>(P, rho, T, k, dk);
+#pragma unroll
+    for (int i = 0; i < NS; i++) Y[i] = w[1 + i] * inv_rho / P.mass[i];
+    // M = 0 I - 1 * dR/dw = -dR/dw  (build_matrix with c = 0, dtm = 1)
+    double ym[NS];
+#pragma unroll
+    for (int i = 0; i < NS; i++) ym[i] = inv_rho / P.mass[i];
+    double M[N][N];
+    build_matrix<NS, TOPO, double>(P, rho, inv_rho, ym, k, dk, Y, 0.0, 1.0, M);
+#pragma unroll
+    for (int r = 0; r < N; r++)
+#pragma unroll
+        for (int c = 0; c < N; c++) dR[r][c] = -M[r][c];
+    // dR/da_j = (R with only reaction j, at a_j = 1): R_r = rho C_rj r_j, r_j linear in a_j
+#pragma unroll
+    for (int j = 0; j < NR; j++) {
+        double kj[NR];
+#pragma unroll
+        for (int q = 0; q < NR; q++) kj[q] = 0.0;
+        kj[j] = (P.a[j] != 0.0) ? k[j] / P.a[j] : ipow_small(rho, P.order[j] - 1) *
+                                                   (P.law == LAW_POWER ? exp(P.nu[j] * log(T)) : exp(-P.nu[j] / T));
+        double Rj[N];
+        sources<NS, TOPO>(P, rho, kj, Y, Rj);
+#pragma unroll
+        for (int r = 0; r < N; r++) dRa[r][j] = Rj[r];
+    }
+}
+
+// Reactive-source VJP at the state U (with Rbar) and, when dtm > 0, the VJP of
+// the implicit update whose root is U: rhsbar = d rhs.  abar_zone[j*N + z] +=.
+template <int NS, int TOPO>
+__global__ void __launch_bounds__(ADJ_BLOCK)
+reaction_vjp_kernel(NetParams P, long long N, int dim, const double* __restrict__ U, const double* __restrict__ Rbar,
+                    double* __restrict__ Ubar, double dtm, double* __restrict__ rhsbar,
+                    double* __restrict__ abar_zone) {
+    constexpr int NW = NS + 1;
+    constexpr int NR = NS - 1;
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= N) return;
+    const double rho = U[z];
+    double mom[3] = {0.0, 0.0, 0.0}, m2 = 0.0;
+    for (int d = 0; d < dim; d++) {
+        mom[d] = U[(1 + d) * N + z];
+        m2 += mom[d] * mom[d];
+    }
+    double w[NW];
+#pragma unroll
+    for (int r = 0; r < NW; r++) w[r] = U[(1 + dim + r) * N + z];
+    double dR[NW][NW], dRa[NW][NR];
+    reaction_derivs<NS, TOPO>(P, rho, m2, w, dR, dRa);
+    const double cE_rho = -w[0] / rho + m2 / (rho * rho);  // dT/d(rho) / dT/d(rho E)
+    double ub_rho = Ubar[z], ub_m[3] = {0.0, 0.0, 0.0}, ub_w[NW];
+    for (int d = 0; d < dim; d++) ub_m[d] = Ubar[(1 + d) * N + z];
+#pragma unroll
+    for (int r = 0; r < NW; r++) ub_w[r] = Ubar[(1 + dim + r) * N + z];
+    double ga[NR];
+#pragma unroll
+    for (int j = 0; j < NR; j++) ga[j] = 0.0;
+    if (Rbar) {
+        double rb[NW];
+#pragma unroll
+        for (int r = 0; r < NW; r++) rb[r] = Rbar[r * N + z];
+#pragma unroll
+        for (int c = 0; c < NW; c++) {
+            double s = 0.0;
+#pragma unroll
+            for (int r = 0; r < NW; r++) s += dR[r][c] * rb[r];
+            ub_w[c] += s;
+        }
+        double DE = 0.0;
+#pragma unroll
+        for (int r = 0; r < NW; r++) DE += rb[r] * dR[r][0];
+        ub_rho += DE * cE_rho;
+        for (int d = 0; d < dim; d++) ub_m[d] -= DE * mom[d] / rho;
+#pragma unroll
+        for (int j = 0; j < NR; j++) {
+            double s = 0.0;
+#pragma unroll
+            for (int r = 0; r < NW; r++) s += rb[r] * dRa[r][j];
+            ga[j] += s;
+        }
+    }
+    if (dtm > 0.0) {
+        // J^T lambda = ub_w, J = I - dtm dR/dw
+        double JT[NW][NW];
+#pragma unroll
+        for (int r = 0; r < NW; r++)
+#pragma unroll
+            for (int c = 0; c < NW; c++) JT[c][r] = (r == c ? 1.0 : 0.0) - dtm * dR[r][c];
+        double lam[NW];
+#pragma unroll
+        for (int r = 0; r < NW; r++) lam[r] = ub_w[r];
+        if (!lu_solve<NW, double, double>(JT, lam)) {
+            // singular Jacobian at the root: the update is not differentiable here
+#pragma unroll
+            for (int r = 0; r < NW; r++) lam[r] = 0.0;
+        }
+        double DE = 0.0;
+#pragma unroll
+        for (int r = 0; r < NW; r++) DE += lam[r] * dR[r][0];
+        rhsbar[z] = ub_rho + dtm * DE * cE_rho;
+        for (int d = 0; d < dim; d++) rhsbar[(1 + d) * N + z] = ub_m[d] - dtm * DE * mom[d] / rho;
+#pragma unroll
+        for (int r = 0; r < NW; r++) rhsbar[(1 + dim + r) * N + z] = lam[r];
+#pragma unroll
+        for (int j = 0; j < NR; j++) {
+            double s = 0.0;
+#pragma unroll
+            for (int r = 0; r < NW; r++) s += lam[r] * dRa[r][j];
+            ga[j] += dtm * s;
+        }
+    } else {
+        Ubar[z] = ub_rho;
+        for (int d = 0; d < dim; d++) Ubar[(1 + d) * N + z] = ub_m[d];
+#pragma unroll
+        for (int r = 0; r < NW; r++) Ubar[(1 + dim + r) * N + z] = ub_w[r];
+    }
+#pragma unroll
+    for (int j = 0; j < NR; j++) abar_zone[j * N + z] += ga[j];
+}
+
+// adjoint of rhs_m = U_m + dtm (A_m_new - A_m_old) - dtm R_{m+1}_old + sum_l q_l dt (A_l_old + R_l_old)
+__global__ void rhs_adjoint_kernel(RhsAdjArgs a) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)a.nvar * a.N) return;
+    const int f = (int)(i / a.N);
+    const long long z = i - (long long)f * a.N;
+    const double g = a.rhsbar[i];
+    const bool reactive = f >= 1 + a.dim;
+    const int r = f - 1 - a.dim;
+    a.Ubar_m[i] += g;
+    if (a.Abar_new_m) {
+        a.Abar_new_m[i] += a.dtm * g;
+        a.Abar_old[a.m][i] -= a.dtm * g;
+    }
+    if (reactive) a.Rbar_old[a.m + 1][r * a.N + z] -= a.dtm * g;
+    for (int l = 0; l < a.M; l++) {
+        a.Abar_old[l][i] += a.qdt[l] * g;
+        if (reactive) a.Rbar_old[l][r * a.N + z] += a.qdt[l] * g;
+    }
+}
+
+// g_a[j] += sum_z abar_zone[j*N + z] (fixed order: one block per reaction)
+__global__ void reduce_rows_kernel(long long N, const double* __restrict__ x, double* __restrict__ out) {
+    __shared__ double s[256];
+    const int j = blockIdx.x;
+    double acc = 0.0;
+    for (long long z = threadIdx.x; z < N; z += blockDim.x) acc += x[(long long)j * N + z];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[j] += s[0];
+}
+
+// ---------------------------------------------------------------- dispatch
+#define SDC_ADJ_CASES(X) \
+    X(1, 2, TOPO_GENERIC) \
+    X(3, 2, TOPO_GENERIC) \
+    X(3, 5, TOPO_CHAIN)   \
+    X(3, 7, TOPO_CHAIN)
+
+bool adjoint_supported(int dim, int nspec, int topo) {
+#define X(d, ns, tp) \
+    if (dim == d && nspec == ns && topo == tp) return true;
+    SDC_ADJ_CASES(X)
+#undef X
+    return false;
+}
+
+cudaError_t launch_stencil_vjp(const NetParams& P, int dim, int limiter, long long N, const BoxDev* boxes, int nbox,
+                               const double* U, const double* Abar, double* G, double* Ubar, cudaStream_t st) {
+    const unsigned g1 = (unsigned)((N * dim + ADJ_BLOCK - 1) / ADJ_BLOCK);
+    const unsigned g2 = (unsigned)((N + ADJ_BLOCK - 1) / ADJ_BLOCK);
+#define X(d, ns, tp)                                                                                        \
+    if (dim == d && P.nspec == ns && P.topo == tp) {                                                        \
+        stencil_vjp_kernel<d, ns><<<g1, ADJ_BLOCK, 0, st>>>(P.gamma, limiter, N, boxes, nbox, U, Abar, G);  \
+        cudaError_t e = cudaGetLastError();                                                                 \
+        if (e != cudaSuccess) return e;                                                                     \
+        stencil_vjp_gather<d, ns><<<g2, ADJ_BLOCK, 0, st>>>(N, boxes, nbox, G, Ubar);                       \
+        return cudaGetLastError();                                                                          \
+    }
+    SDC_ADJ_CASES(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_reaction_vjp(const NetParams& P, int dim, long long N, const double* U, const double* Rbar,
+                                double* Ubar, double dtm, double* rhsbar, double* abar_zone, cudaStream_t st) {
+    const unsigned g = (unsigned)((N + ADJ_BLOCK - 1) / ADJ_BLOCK);
+#define X(d, ns, tp)                                                                                           \
+    if (dim == d && P.nspec == ns && P.topo == tp) {                                                           \
+        reaction_vjp_kernel<ns, tp><<<g, ADJ_BLOCK, 0, st>>>(P, N, dim, U, Rbar, Ubar, dtm, rhsbar, abar_zone); \
+        return cudaGetLastError();                                                                             \
+    }
+    SDC_ADJ_CASES(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rhs_adjoint(const RhsAdjArgs& a, cudaStream_t st) {
+    const long long n = (long long)a.nvar * a.N;
+    rhs_adjoint_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_rows(long long N, int rows, const double* x, double* out, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    reduce_rows_kernel<<<rows, 256, 0, st>>>(N, x, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sdcd

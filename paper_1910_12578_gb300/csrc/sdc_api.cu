@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/sdc.h"
+#include "sdc_adjoint_launch.h"
 #include "sdc_launch.h"
 
 using namespace sdcd;
@@ -166,6 +167,17 @@ struct sdc_ctx {
     unsigned long long* d_queue = nullptr;  // one counter per Newton launch of a step
     std::vector<sdc_box> boxes;
     int tiles_capacity = 0;
+    // adjoint workspace (allocated by the first sdc_step_backward)
+    struct {
+        bool ready = false;
+        double* work = nullptr;        // the recomputed step
+        std::vector<double*> store;    // U_m^{(k+1)}, k = 0..K-1, m = 1..M-1
+        double* Ubar_node[3] = {nullptr, nullptr, nullptr};
+        double* Abar[2][3] = {{nullptr}};
+        double* Rbar[2][3] = {{nullptr}};
+        double *Abar_n = nullptr, *Rbar_n = nullptr, *Ubar_n = nullptr, *rhsbar = nullptr;
+        double *G = nullptr, *abar_zone = nullptr;
+    } adj;
 };
 
 namespace {
@@ -233,7 +245,8 @@ RhsArgs rhs_args(const sdc_ctx* c, const double* const* Aold, const double* cons
 
 // Enqueue one SDC step on stream st (dt already in c->d_dt); U is node M-1.
 // With prof, every kernel launch is bracketed by events (eager profiling).
-cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nullptr) {
+cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nullptr,
+                         double* const* store = nullptr) {
     const long long N = c->Ntot;
     const size_t ubytes = sizeof(double) * c->nvar * N;
     cudaError_t e;
@@ -271,6 +284,10 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
                                                        Rnew[m + 1], c->d_dt, c->tau[m + 1] - c->tau[m], 0.0, nullptr,
                                                        nullptr, c->d_stats, st, c->newton_variant, q,
                                                        c->persistent_blocks));
+            if (store &&
+                (e = cudaMemcpyAsync(store[k * (c->M - 1) + m], node[m + 1], ubytes, cudaMemcpyDeviceToDevice, st)) !=
+                    cudaSuccess)
+                return e;
         }
         if (k < c->K - 1) {
             SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles,
@@ -672,6 +689,117 @@ sdc_status sdc_launches_per_step(const sdc_ctx* ctx, int* launches) {
     // dt store, A(U^n), R(U^n), per iteration and node a rhs kernel and a Newton
     // kernel, and A at the last node for every iteration but the last
     *launches = 3 + ctx->K * 2 * (ctx->M - 1) + (ctx->K - 1);
+    return SDC_OK;
+}
+
+sdc_status sdc_set_rates(sdc_ctx* ctx, const double* a) {
+    if (!ctx || !a) return SDC_ERR_INVALID_ARG;
+    for (int j = 0; j < ctx->P.nreac; j++) ctx->P.a[j] = a[j];
+    if (ctx->gexec) {  // the captured graph holds the old constants
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+        ctx->gU = nullptr;
+    }
+    return SDC_OK;
+}
+
+sdc_status sdc_step_backward(sdc_ctx* ctx, const double* U_n, double dt, const double* gU_np1, double* gU_n,
+                             double* g_a) {
+    if (!ctx || !U_n || !gU_np1 || !gU_n || !(dt > 0.0)) return SDC_ERR_INVALID_ARG;
+    if (!adjoint_supported(ctx->dim, ctx->nspec, ctx->P.topo)) return SDC_ERR_INVALID_ARG;
+    sdc_ctx* c = ctx;
+    const long long N = c->Ntot;
+    const int M = c->M, K = c->K, nw = c->nw, nr = c->P.nreac;
+    const size_t ub = sizeof(double) * c->nvar * N, rb = sizeof(double) * nw * N;
+    cudaStream_t st = c->stream;
+    auto& A = c->adj;
+    if (!A.ready) {
+        SDC_TRY(ctx_alloc(c, (void**)&A.work, ub));
+        A.store.assign(K * (M - 1), nullptr);
+        for (auto& p : A.store) SDC_TRY(ctx_alloc(c, (void**)&p, ub));
+        for (int m = 0; m < M; m++) SDC_TRY(ctx_alloc(c, (void**)&A.Ubar_node[m], ub));
+        for (int g = 0; g < 2; g++)
+            for (int m = 0; m < M; m++) {
+                SDC_TRY(ctx_alloc(c, (void**)&A.Abar[g][m], ub));
+                SDC_TRY(ctx_alloc(c, (void**)&A.Rbar[g][m], rb));
+            }
+        SDC_TRY(ctx_alloc(c, (void**)&A.Abar_n, ub));
+        SDC_TRY(ctx_alloc(c, (void**)&A.Rbar_n, rb));
+        SDC_TRY(ctx_alloc(c, (void**)&A.Ubar_n, ub));
+        SDC_TRY(ctx_alloc(c, (void**)&A.rhsbar, ub));
+        SDC_TRY(ctx_alloc(c, (void**)&A.G, sizeof(double) * (size_t)c->dim * N * 4 * c->nvar));
+        SDC_TRY(ctx_alloc(c, (void**)&A.abar_zone, sizeof(double) * (size_t)(nr > 0 ? nr : 1) * N));
+        A.ready = true;
+    }
+    // 1. recompute the step from the checkpoint, keeping every node state
+    SDC_TRY(cudaMemcpyAsync(A.work, U_n, ub, cudaMemcpyDeviceToDevice, st));
+    set_scalar_kernel<<<1, 1, 0, st>>>(c->d_dt, dt);
+    SDC_TRY(cudaGetLastError());
+    SDC_TRY(enqueue_step(c, A.work, st, nullptr, A.store.data()));
+    // 2. reverse sweep
+    for (int m = 0; m < M; m++) SDC_TRY(cudaMemsetAsync(A.Ubar_node[m], 0, ub, st));
+    for (int g = 0; g < 2; g++)
+        for (int m = 0; m < M; m++) {
+            SDC_TRY(cudaMemsetAsync(A.Abar[g][m], 0, ub, st));
+            SDC_TRY(cudaMemsetAsync(A.Rbar[g][m], 0, rb, st));
+        }
+    SDC_TRY(cudaMemsetAsync(A.Abar_n, 0, ub, st));
+    SDC_TRY(cudaMemsetAsync(A.Rbar_n, 0, rb, st));
+    SDC_TRY(cudaMemsetAsync(A.Ubar_n, 0, ub, st));
+    SDC_TRY(cudaMemsetAsync(A.abar_zone, 0, sizeof(double) * (size_t)(nr > 0 ? nr : 1) * N, st));
+    SDC_TRY(cudaMemcpyAsync(A.Ubar_node[M - 1], gU_np1, ub, cudaMemcpyDeviceToDevice, st));
+    int gnew = 0, gold = 1;
+    for (int k = K - 1; k >= 0; k--) {
+        double *Aold[3], *Rold[3];
+        for (int l = 0; l < 3; l++) {
+            const bool un = (l == 0 || k == 0);  // values at U^n
+            Aold[l] = un ? A.Abar_n : A.Abar[gold][l];
+            Rold[l] = un ? A.Rbar_n : A.Rbar[gold][l];
+        }
+        auto Ust = [&](int m) { return A.store[k * (M - 1) + (m - 1)]; };  // U_m^{(k+1)}, m >= 1
+        if (k < K - 1)
+            SDC_TRY(launch_stencil_vjp(c->P, c->dim, c->limiter, N, c->d_boxes, c->nbox, Ust(M - 1),
+                                       A.Abar[gnew][M - 1], A.G, A.Ubar_node[M - 1], st));
+        for (int m = M - 2; m >= 0; m--) {
+            const double dtm = dt * (c->tau[m + 1] - c->tau[m]);
+            SDC_TRY(launch_reaction_vjp(c->P, c->dim, N, Ust(m + 1), A.Rbar[gnew][m + 1], A.Ubar_node[m + 1], dtm,
+                                        A.rhsbar, A.abar_zone, st));
+            RhsAdjArgs ra;
+            memset(&ra, 0, sizeof(ra));
+            ra.nvar = c->nvar;
+            ra.dim = c->dim;
+            ra.M = M;
+            ra.m = m;
+            ra.N = N;
+            ra.rhsbar = A.rhsbar;
+            ra.Ubar_m = m >= 1 ? A.Ubar_node[m] : A.Ubar_n;
+            ra.Abar_new_m = m >= 1 ? A.Abar[gnew][m] : nullptr;
+            for (int l = 0; l < 3; l++) {
+                ra.Abar_old[l] = Aold[l];
+                ra.Rbar_old[l] = Rold[l];
+                ra.qdt[l] = c->q[m][l] * dt;
+            }
+            ra.dtm = dtm;
+            SDC_TRY(launch_rhs_adjoint(ra, st));
+            if (m >= 1)
+                SDC_TRY(launch_stencil_vjp(c->P, c->dim, c->limiter, N, c->d_boxes, c->nbox, Ust(m), A.Abar[gnew][m],
+                                           A.G, A.Ubar_node[m], st));
+        }
+        // the adjoints of this iteration's inputs are the next ones' outputs
+        const int t = gnew;
+        gnew = gold;
+        gold = t;
+        for (int m = 0; m < M; m++) {
+            SDC_TRY(cudaMemsetAsync(A.Abar[gold][m], 0, ub, st));
+            SDC_TRY(cudaMemsetAsync(A.Rbar[gold][m], 0, rb, st));
+        }
+        for (int m = 1; m < M; m++) SDC_TRY(cudaMemsetAsync(A.Ubar_node[m], 0, ub, st));
+    }
+    // A(U^n) and R(U^n)
+    SDC_TRY(launch_stencil_vjp(c->P, c->dim, c->limiter, N, c->d_boxes, c->nbox, U_n, A.Abar_n, A.G, A.Ubar_n, st));
+    SDC_TRY(launch_reaction_vjp(c->P, c->dim, N, U_n, A.Rbar_n, A.Ubar_n, 0.0, nullptr, A.abar_zone, st));
+    SDC_TRY(cudaMemcpyAsync(gU_n, A.Ubar_n, ub, cudaMemcpyDeviceToDevice, st));
+    if (g_a) SDC_TRY(launch_reduce_rows(N, nr, A.abar_zone, g_a, st));
     return SDC_OK;
 }
 

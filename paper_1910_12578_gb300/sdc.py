@@ -24,7 +24,8 @@ PREC_FP64, PREC_FP32_JAC = 0, 1
 # entry points declared in include/sdc.h
 EXPORTS = ["sdc_init_box", "sdc_advective_term", "sdc_node_integral", "sdc_react_newton", "sdc_step",
            "sdc_step_profile", "sdc_launches_per_step", "sdc_cfl_dt", "sdc_sizes", "sdc_destroy",
-           "sdc_status_string", "sdc_step_static", "sdc_selftest_math", "sdc_autotune", "sdc_set_variants"]
+           "sdc_status_string", "sdc_step_static", "sdc_selftest_math", "sdc_autotune", "sdc_set_variants",
+           "sdc_step_backward", "sdc_set_rates"]
 
 
 class SdcError(RuntimeError):
@@ -102,6 +103,8 @@ def load(path: str = LIB_PATH):
     L.sdc_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
     L.sdc_selftest_math.argtypes = [dp, C.c_longlong, dp, dp, vp]
     L.sdc_autotune.argtypes = [vp, dp, C.c_double, C.POINTER(Tuning)]
+    L.sdc_step_backward.argtypes = [vp, dp, C.c_double, dp, dp, dp]
+    L.sdc_set_rates.argtypes = [vp, C.POINTER(C.c_double)]
     L.sdc_set_variants.argtypes = [vp, C.c_int, C.c_int]
     L.sdc_step_static.argtypes = [C.POINTER(Box), C.c_int, C.POINTER(Network), C.POINTER(Params), vp, dp,
                                   C.c_double, C.POINTER(Stats)]
@@ -112,7 +115,7 @@ def load(path: str = LIB_PATH):
     L.sdc_status_string.restype = C.c_char_p
     for name in ("sdc_init_box", "sdc_advective_term", "sdc_node_integral", "sdc_react_newton", "sdc_step",
                  "sdc_cfl_dt", "sdc_sizes", "sdc_step_profile", "sdc_launches_per_step", "sdc_step_static", "sdc_selftest_math", "sdc_autotune",
-                 "sdc_set_variants"):
+                 "sdc_set_variants", "sdc_step_backward", "sdc_set_rates"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -239,6 +242,18 @@ class Context:
     def set_variants(self, stencil_variant, newton_variant):
         self._check(self.L.sdc_set_variants(self._h, int(stencil_variant), int(newton_variant)), "sdc_set_variants")
 
+    def step_backward(self, U_n, dt, gU_np1, gU_n, g_a=None):
+        """Adjoint of one step from its checkpoint U_n: gU_n = J^T gU_np1,
+        g_a += (dU^{n+1}/da)^T gU_np1 (g_a: CUDA float64 [nreac] or None)."""
+        ga = _ptr(g_a) if g_a is not None else None
+        self._check(self.L.sdc_step_backward(self._h, _ptr(U_n), float(dt), _ptr(gU_np1), _ptr(gU_n), ga),
+                    "sdc_step_backward")
+
+    def set_rates(self, a):
+        """Replace the rate prefactors a_j (host values)."""
+        arr = np.ascontiguousarray(np.asarray(a, dtype=np.float64).ravel())
+        self._check(self.L.sdc_set_rates(self._h, arr.ctypes.data_as(C.POINTER(C.c_double))), "sdc_set_rates")
+
     def launches_per_step(self):
         n = C.c_int()
         self._check(self.L.sdc_launches_per_step(self._h, C.byref(n)), "sdc_launches_per_step")
@@ -307,3 +322,47 @@ def selftest_math(x):
 
 def init_box(problems, prec=PREC_FP64, stream=None) -> Context:
     return Context(problems, prec=prec, stream=stream)
+
+
+def _autograd_function():
+    import torch
+
+    class SDCStep(torch.autograd.Function):
+        """One SDC step as a differentiable op: forward = sdc_step on a copy of U
+        with rate prefactors a; backward = sdc_step_backward from the saved input
+        state (a per-step checkpoint), giving dL/dU and dL/da."""
+
+        @staticmethod
+        def forward(fctx, U, a, context, dt):
+            context.set_rates(a.detach().cpu().numpy())
+            Un = U.detach().contiguous().clone()
+            out = Un.clone()
+            context.step(out, dt, stats=False)
+            fctx.save_for_backward(Un, a.detach())
+            fctx.context = context
+            fctx.dt = dt
+            return out
+
+        @staticmethod
+        def backward(fctx, gU):
+            Un, a = fctx.saved_tensors
+            context = fctx.context
+            context.set_rates(a.cpu().numpy())
+            gUn = torch.empty_like(Un)
+            ga = torch.zeros(a.numel(), dtype=torch.float64, device=Un.device)
+            context.step_backward(Un, fctx.dt, gU.contiguous(), gUn, ga)
+            return gUn, ga.to(a.device), None, None
+
+    return SDCStep
+
+
+_SDCStep = None
+
+
+def sdc_step_fn(U, a, context, dt):
+    """Differentiable SDC step: U [nvar][Ntot] (CUDA float64), a [nreac] rate
+    prefactors (float64 tensor, gradients flow to it)."""
+    global _SDCStep
+    if _SDCStep is None:
+        _SDCStep = _autograd_function()
+    return _SDCStep.apply(U, a, context, dt)
