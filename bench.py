@@ -37,6 +37,13 @@ UNIT = "zone-node-iterations/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per zone of one Newton launch, from one ncu
+# capture per kernel variant on the 64^3 workload (262,144 zones), keyed by (nspec, Newton variant, prec).
+# The traffic of these kernels grows in proportion to the zones (no re-reads), so a launch over N zones
+# moves N times this.  A variant or precision without a capture reports null.
+NEWTON_TRAFFIC_PER_ZONE = {
+    (7, 1, "fp64"): (44.760576e6 + 33.863680e6) / 262144,   # newton_queue_kernel<7, chain, double>
+}
 
 
 def parse():
@@ -51,6 +58,8 @@ def parse():
     p.add_argument("--seed", type=int, default=None,
                    help="network / box seed (default: 1 for the single boxes, 3 for the batch)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--adjoint", action=argparse.BooleanOptionalAction, default=True,
+                   help="also time one backward step (sdc_step_backward) of the workload")
     return p.parse_args()
 
 
@@ -444,9 +453,13 @@ def run_ours(args):
         fp64_flops = iters * (ev_f + upd_f)
         fp32_flops = iters * lin_f
     achieved = fp64_flops / max(pr.launches_newton, 1) / (newton_ms_launch * 1e-3) / 1e12
+    newton_choice = tuning["newton_choice"] if tuning else 0
+    per_zone = NEWTON_TRAFFIC_PER_ZONE.get((P0.net.nspec, newton_choice, args.prec))
     roof = {"kernel": "newton_kernel (implicit reaction update)", "bound": "alu",
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": per_zone * nzones(P) if per_zone is not None else None,
+            "traffic_unit": "bytes per launch (ncu DRAM read + write)",
             "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (recipe unit counts and clock; "
                            "an FMA-chain probe measured 1.256 TFLOP/s)",
             "flops_per_launch": fp64_flops / max(pr.launches_newton, 1), "ms_per_launch": newton_ms_launch,
@@ -469,6 +482,29 @@ def run_ours(args):
     roof_st = {"kernel": "stencil_kernel (advective term + fused rhs)", "bound": "hbm", "achieved": st_gbs,
                "peak": hbm_peak, "unit": "GB/s", "frac": st_gbs / hbm_peak, "traffic": None,
                "bytes_per_launch": st_bytes, "ms_per_launch": stencil_ms}
+
+    # ---- one backward (adjoint) step of the same workload, where the network has one
+    adjoint = None
+    if args.adjoint:
+        gU = torch.ones_like(U0)
+        gUn = torch.empty_like(U0)
+        ga = torch.zeros(P0.net.nreac, dtype=torch.float64, device="cuda")
+        try:
+            ctx.step_backward(U0, dt, gU, gUn, ga)          # allocates the adjoint workspace
+            torch.cuda.synchronize()
+            ab = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ab[0].record()
+            for _ in range(2):
+                ctx.step_backward(U0, dt, gU, gUn, ga)
+            ab[1].record()
+            torch.cuda.synchronize()
+            bms = ab[0].elapsed_time(ab[1]) / 2
+            adjoint = {"ms_per_backward_step": bms, "ms_per_forward_step": total_ms / args.steps,
+                       "ratio": bms / (total_ms / args.steps),
+                       "note": "recomputes the forward step from its checkpoint, then the reverse sweep; "
+                               "gradient of sum(U^{n+1}) with respect to U^n and the rate prefactors"}
+        except sdc.SdcError as e:
+            adjoint = {"unavailable": str(e)}
 
     line = None
     if rank == 0:
@@ -503,6 +539,7 @@ def run_ours(args):
                        "fails": st2.n_fail},
             "cpu_baseline": cpu,
             "oracle_error": err,
+            "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
