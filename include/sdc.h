@@ -202,6 +202,19 @@ sdc_status sdc_launches_per_step(const sdc_ctx* ctx, int* launches);
 sdc_status sdc_step_backward(sdc_ctx* ctx, const double* U_n, double dt, const double* gU_np1, double* gU_n,
                              double* g_a);
 
+/* Vector-Jacobian product of the advective term A(U) of Eq. 1 (section 2: the
+   divergence of the hydrodynamic fluxes):  Ubar += (dA/dU)^T Abar  at the state
+   U, with the branches of the MC limiter and of HLLC those that U selects.
+   U, Abar, Ubar: device arrays [nvar][Ntot]; Ubar is accumulated.  mode 0: a
+   reverse sweep through each face flux (what sdc_step_backward uses); mode 1:
+   forward-mode dual numbers, one input direction at a time (4 nvar passes per
+   face: an independent formulation, slower, for cross-checks).  Both write
+   per-face products to the adjoint workspace (allocated on first use) and add
+   them up per zone in a fixed order (deterministic).  Supported networks as in
+   sdc_step_backward; SDC_ERR_INVALID_ARG otherwise or for another mode.
+   Asynchronous on the context's stream. */
+sdc_status sdc_advective_term_vjp(sdc_ctx* ctx, const double* U, const double* Abar, double* Ubar, int mode);
+
 /* Replace the rate prefactors a_j of the context's network (host array [nreac]). */
 sdc_status sdc_set_rates(sdc_ctx* ctx, const double* a);
 

@@ -70,6 +70,39 @@ stencil_vjp_kernel(double gamma, int limiter, long long N, const BoxDev* __restr
     }
 }
 
+// Same product as stencil_vjp_kernel, by a reverse sweep through the face flux.
+template <int DIM, int NS>
+__global__ void __launch_bounds__(ADJ_BLOCK)
+stencil_vjp_rev_kernel(double gamma, int limiter, long long N, const BoxDev* __restrict__ boxes, int nbox,
+                       const double* __restrict__ U, const double* __restrict__ Abar, double* __restrict__ G) {
+    constexpr int NV = 2 + DIM + NS;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * DIM) return;
+    const int dir = (int)(t / N);
+    const long long z = t - (long long)dir * N;
+    const BoxDev b = boxes[box_of(boxes, nbox, z)];
+    long long zz[4];
+#pragma unroll
+    for (int o = 0; o < 4; o++) zz[o] = shifted(b, z, dir, o - 1);
+    double Fbar[NV];
+#pragma unroll
+    for (int f = 0; f < NV; f++) Fbar[f] = (Abar[f * N + zz[2]] - Abar[f * N + zz[1]]) * b.idx[dir];
+    double Uz[4][NV], Ub[4][NV];
+#pragma unroll
+    for (int o = 0; o < 4; o++)
+#pragma unroll
+        for (int f = 0; f < NV; f++) {
+            Uz[o][f] = U[f * N + zz[o]];
+            Ub[o][f] = 0.0;
+        }
+    face_flux_vjp<DIM, NS>(gamma, limiter, dir, Uz, Fbar, Ub);
+    double* out = G + ((long long)dir * N + z) * (4 * NV);
+#pragma unroll
+    for (int o = 0; o < 4; o++)
+#pragma unroll
+        for (int f = 0; f < NV; f++) out[o * NV + f] = Ub[o][f];
+}
+
 // Ubar_z += sum over directions and over the four faces whose stencil holds z
 template <int DIM, int NS>
 __global__ void __launch_bounds__(ADJ_BLOCK)
@@ -278,13 +311,17 @@ bool adjoint_supported(int dim, int nspec, int topo) {
 }
 
 cudaError_t launch_stencil_vjp(const NetParams& P, int dim, int limiter, long long N, const BoxDev* boxes, int nbox,
-                               const double* U, const double* Abar, double* G, double* Ubar, cudaStream_t st) {
+                               const double* U, const double* Abar, double* G, double* Ubar, cudaStream_t st,
+                               int mode) {
     const unsigned g1 = (unsigned)((N * dim + ADJ_BLOCK - 1) / ADJ_BLOCK);
     const unsigned g2 = (unsigned)((N + ADJ_BLOCK - 1) / ADJ_BLOCK);
-#define X(d, ns, tp)                                                                                        \
-    if (dim == d && P.nspec == ns && P.topo == tp) {                                                        \
-        stencil_vjp_kernel<d, ns><<<g1, ADJ_BLOCK, 0, st>>>(P.gamma, limiter, N, boxes, nbox, U, Abar, G);  \
-        cudaError_t e = cudaGetLastError();                                                                 \
+#define X(d, ns, tp)                                                                                            \
+    if (dim == d && P.nspec == ns && P.topo == tp) {                                                            \
+        if (mode == 0)                                                                                          \
+            stencil_vjp_rev_kernel<d, ns><<<g1, ADJ_BLOCK, 0, st>>>(P.gamma, limiter, N, boxes, nbox, U, Abar, G); \
+        else                                                                                                    \
+            stencil_vjp_kernel<d, ns><<<g1, ADJ_BLOCK, 0, st>>>(P.gamma, limiter, N, boxes, nbox, U, Abar, G);  \
+        cudaError_t e = cudaGetLastError();                                                                     \
         if (e != cudaSuccess) return e;                                                                     \
         stencil_vjp_gather<d, ns><<<g2, ADJ_BLOCK, 0, st>>>(N, boxes, nbox, G, Ubar);                       \
         return cudaGetLastError();                                                                          \

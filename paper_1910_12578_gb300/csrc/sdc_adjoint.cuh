@@ -10,10 +10,14 @@
 //    with D_E = (dR/d(rho E))^T lambda.  R is linear in every rate prefactor a_j.
 //  * Advective term: A = -sum_d (F_{i+1/2} - F_{i-1/2}) / dx_d.  Every face flux
 //    depends on the four zones i-1 .. i+2 along its direction; its transposed
-//    Jacobian times the face adjoint is formed in forward mode (dual numbers,
-//    one input direction at a time) with the branches of the limiter and of
-//    HLLC fixed by the primal values, and written per face; a gather adds the
-//    four face contributions of every zone in a fixed order (deterministic).
+//    Jacobian times the face adjoint is formed by a reverse sweep through the
+//    face's operations (face_flux_vjp: one forward pass, then the adjoint of
+//    each operation in reverse order, about three forward passes of work) with
+//    the branches of the limiter and of HLLC fixed by the primal values, and
+//    written per face; a gather adds the four face contributions of every zone
+//    in a fixed order (deterministic).  face_flux_dual forms the same product
+//    in forward mode (dual numbers, one input direction at a time: 4 nvar
+//    passes), an independent formulation kept to cross-check the reverse one.
 #pragma once
 #include "sdc_dev.cuh"
 #include "sdc_stencil.cuh"
@@ -129,6 +133,261 @@ __device__ void face_flux_dual(double gamma, int limiter, int dir, const Dual (*
     for (int s = 0; s < NS; s++) sum = sum + qx[2 + DIM + s];
 #pragma unroll
     for (int s = 0; s < NS; s++) F[2 + DIM + s] = Fh[0] * (qx[2 + DIM + s] / sum);
+}
+
+// Coefficients of the limited slope as a linear form in the three values,
+// slope = cm qm + c0 q0 + cp qp, on the branch the values select (ties as in
+// mc_slope_dual: the first argument of each min wins).
+__device__ __forceinline__ void mc_slope_coef(int limiter, double qm, double q0, double qp, double& cm, double& c0,
+                                              double& cp) {
+    const double dl = q0 - qm, dr = qp - q0, dc = 0.5 * (dl + dr);
+    if (!limiter) { cm = -0.5; c0 = 0.0; cp = 0.5; return; }
+    if (dl * dr <= 0.0) { cm = 0.0; c0 = 0.0; cp = 0.0; return; }
+    const bool left = fabs(dl) <= fabs(dr);            // min(2|dl|, 2|dr|)
+    const double m2 = 2.0 * (left ? fabs(dl) : fabs(dr));
+    if (m2 <= fabs(dc)) {                               // slope = 2 dl or 2 dr (dl, dr, dc share a sign)
+        if (left) { cm = -2.0; c0 = 2.0; cp = 0.0; }
+        else { cm = 0.0; c0 = -2.0; cp = 2.0; }
+    } else {                                            // slope = dc
+        cm = -0.5; c0 = 0.0; cp = 0.5;
+    }
+}
+
+// Ub[z][f] += (d F / d Uz[z][f])^T Fbar for the face flux of face_flux_dual:
+// the same operations, differentiated by a reverse sweep.
+template <int DIM, int NS>
+__device__ __forceinline__ void face_flux_vjp(double gamma, int limiter, int dir, const double (*Uz)[2 + DIM + NS],
+                                              const double* Fbar, double (*Ub)[2 + DIM + NS]) {
+    constexpr int NV = 2 + DIM + NS;
+    constexpr int IE = 1 + DIM, IX = 2 + DIM;
+    const double gm1 = gamma - 1.0, igm1 = 1.0 / gm1;
+    // ---------------- forward: primitives of the four zones
+    double q[4][NV];
+#pragma unroll
+    for (int z = 0; z < 4; z++) {
+        const double rho = Uz[z][0], ir = 1.0 / rho;
+        double mu = 0.0;
+        q[z][0] = rho;
+#pragma unroll
+        for (int d = 0; d < DIM; d++) {
+            const double u = Uz[z][1 + d] * ir;
+            q[z][1 + d] = u;
+            mu += u * Uz[z][1 + d];
+        }
+        q[z][IE] = gm1 * (Uz[z][IE] - 0.5 * mu);
+#pragma unroll
+        for (int s = 0; s < NS; s++) q[z][IX + s] = Uz[z][IX + s] * ir;
+    }
+    // interface states
+    double qL[NV], qR[NV];
+#pragma unroll
+    for (int f = 0; f < NV; f++) {
+        double cm, c0, cp;
+        mc_slope_coef(limiter, q[0][f], q[1][f], q[2][f], cm, c0, cp);
+        qL[f] = q[1][f] + 0.5 * (cm * q[0][f] + c0 * q[1][f] + cp * q[2][f]);
+        mc_slope_coef(limiter, q[1][f], q[2][f], q[3][f], cm, c0, cp);
+        qR[f] = q[2][f] - 0.5 * (cm * q[1][f] + c0 * q[2][f] + cp * q[3][f]);
+    }
+    // HLLC (Davis speeds, Toro's contact speed)
+    const double rL = qL[0], rR = qR[0], unL = qL[1 + dir], unR = qR[1 + dir], pL = qL[IE], pR = qR[IE];
+    double kL = 0.0, kR = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) {
+        kL += qL[1 + d] * qL[1 + d];
+        kR += qR[1 + d] * qR[1 + d];
+    }
+    const double EL = pL * igm1 + 0.5 * rL * kL, ER = pR * igm1 + 0.5 * rR * kR;
+    const double irL = 1.0 / rL, irR = 1.0 / rR;
+    const double cL = sqrt(gamma * pL * irL), cR = sqrt(gamma * pR * irR);
+    const bool slL = (unL - cL) <= (unR - cR);
+    const double SL = slL ? unL - cL : unR - cR;
+    const bool srL = (unL + cL) >= (unR + cR);
+    const double SR = srL ? unL + cL : unR + cR;
+    const double aL = rL * (SL - unL), aR = rR * (SR - unR);
+    const double iDen = 1.0 / (aL - aR);
+    const double Ss = (pR - pL + unL * aL - unR * aR) * iDen;
+    const bool left = (SL >= 0.0) || (Ss >= 0.0);
+    const bool star = (SL < 0.0) && (Ss >= 0.0 || SR > 0.0);
+    const double* qs = left ? qL : qR;
+    const double r = left ? rL : rR, un = left ? unL : unR, p = left ? pL : pR, E = left ? EL : ER;
+    const double S = left ? SL : SR;
+    double F0 = r * un;  // mass flux (after the star correction)
+    double D = 0.0, Q = 1.0, fac = 0.0, B = 0.0, H = 0.0;
+    if (star) {
+        D = r * (S - un);
+        Q = S - Ss;
+        fac = D / Q;
+        B = Ss + p / D;
+        H = E / r + (Ss - un) * B;
+        F0 += S * (fac - r);
+    }
+    const double* qx = (Ss >= 0.0) ? qL : qR;
+    double sum = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; s++) sum += qx[IX + s];
+    const double isum = 1.0 / sum;
+
+    // ---------------- reverse
+    double qLb[NV], qRb[NV];
+#pragma unroll
+    for (int f = 0; f < NV; f++) { qLb[f] = 0.0; qRb[f] = 0.0; }
+    // species: F_s = F0 X_s / sum, X from the side upwind of the contact
+    double wsum = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; s++) wsum += Fbar[IX + s] * qx[IX + s];
+    wsum *= isum;
+    {
+        double* qxb = (Ss >= 0.0) ? qLb : qRb;
+#pragma unroll
+        for (int s = 0; s < NS; s++) qxb[IX + s] += F0 * isum * (Fbar[IX + s] - wsum);
+    }
+    double Fhb[2 + DIM];
+#pragma unroll
+    for (int f = 0; f < 2 + DIM; f++) Fhb[f] = Fbar[f];
+    Fhb[0] += wsum;
+    double rb = 0.0, unb = 0.0, pb = 0.0, Eb = 0.0, Sb = 0.0, Ssb = 0.0, vb[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; d++) vb[d] = 0.0;
+    if (star) {
+        // F += S (Us - Uk): Us = fac (1, v with v_dir = Ss, H), Uk = (r, r v, E)
+        double facb = S * Fhb[0];
+        Sb += Fhb[0] * (fac - r);
+        rb -= S * Fhb[0];
+#pragma unroll
+        for (int d = 0; d < DIM; d++) {
+            const double usd = fac * (d == dir ? Ss : qs[1 + d]);
+            Sb += Fhb[1 + d] * (usd - r * qs[1 + d]);
+            const double usb = S * Fhb[1 + d];
+            if (d == dir) { facb += usb * Ss; Ssb += usb * fac; }
+            else { facb += usb * qs[1 + d]; vb[d] += usb * fac; }
+            rb -= usb * qs[1 + d];
+            vb[d] -= usb * r;
+        }
+        Sb += Fhb[IE] * (fac * H - E);
+        const double ueb = S * Fhb[IE];
+        Eb -= ueb;
+        facb += ueb * H;
+        const double Hb = ueb * fac;
+        // H = E / r + (Ss - un) B,  B = Ss + p / D
+        Eb += Hb / r;
+        rb -= Hb * E / (r * r);
+        Ssb += Hb * B;
+        unb -= Hb * B;
+        const double Bb = Hb * (Ss - un);
+        Ssb += Bb;
+        pb += Bb / D;
+        double Db = -Bb * p / (D * D);
+        // fac = D / Q,  Q = S - Ss,  D = r (S - un)
+        Db += facb / Q;
+        const double Qb = -facb * fac / Q;
+        Sb += Qb;
+        Ssb -= Qb;
+        rb += Db * (S - un);
+        Sb += Db * r;
+        unb -= Db * r;
+    }
+    // side flux: (r un, r un v + p e_dir, (E + p) un)
+    rb += Fhb[0] * un;
+    unb += Fhb[0] * r;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) {
+        rb += Fhb[1 + d] * un * qs[1 + d];
+        unb += Fhb[1 + d] * r * qs[1 + d];
+        vb[d] += Fhb[1 + d] * r * un;
+        if (d == dir) pb += Fhb[1 + d];
+    }
+    Eb += Fhb[IE] * un;
+    pb += Fhb[IE] * un;
+    unb += Fhb[IE] * (E + p);
+    unb += vb[dir];  // v_dir is un
+    {
+        double* qKb = left ? qLb : qRb;
+        qKb[0] += rb;
+        qKb[1 + dir] += unb;
+#pragma unroll
+        for (int d = 0; d < DIM; d++)
+            if (d != dir) qKb[1 + d] += vb[d];
+        qKb[IE] += pb;
+    }
+    double ELb = left ? Eb : 0.0, ERb = left ? 0.0 : Eb;
+    double SLb = left ? Sb : 0.0, SRb = left ? 0.0 : Sb;
+    // Ss = (pR - pL + unL aL - unR aR) / (aL - aR)
+    {
+        const double Nb = Ssb * iDen, Denb = -Ssb * Ss * iDen;
+        qRb[IE] += Nb;
+        qLb[IE] -= Nb;
+        const double aLb = Nb * unL + Denb, aRb = -Nb * unR - Denb;
+        qLb[1 + dir] += Nb * aL;
+        qRb[1 + dir] -= Nb * aR;
+        qLb[0] += aLb * (SL - unL);
+        SLb += aLb * rL;
+        qLb[1 + dir] -= aLb * rL;
+        qRb[0] += aRb * (SR - unR);
+        SRb += aRb * rR;
+        qRb[1 + dir] -= aRb * rR;
+    }
+    // Davis speeds
+    double cLb = 0.0, cRb = 0.0;
+    if (slL) { qLb[1 + dir] += SLb; cLb -= SLb; } else { qRb[1 + dir] += SLb; cRb -= SLb; }
+    if (srL) { qLb[1 + dir] += SRb; cLb += SRb; } else { qRb[1 + dir] += SRb; cRb += SRb; }
+    // E = p / (gamma - 1) + r |v|^2 / 2
+    qLb[IE] += ELb * igm1;
+    qLb[0] += ELb * 0.5 * kL;
+    qRb[IE] += ERb * igm1;
+    qRb[0] += ERb * 0.5 * kR;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) {
+        qLb[1 + d] += ELb * rL * qL[1 + d];
+        qRb[1 + d] += ERb * rR * qR[1 + d];
+    }
+    // c = sqrt(gamma p / r)
+    {
+        const double tL = cLb * gamma * 0.5 / cL, tR = cRb * gamma * 0.5 / cR;
+        qLb[IE] += tL * irL;
+        qLb[0] -= tL * pL * irL * irL;
+        qRb[IE] += tR * irR;
+        qRb[0] -= tR * pR * irR * irR;
+    }
+    // interface states -> zone primitives
+    double qb[4][NV];
+#pragma unroll
+    for (int z = 0; z < 4; z++)
+#pragma unroll
+        for (int f = 0; f < NV; f++) qb[z][f] = 0.0;
+#pragma unroll
+    for (int f = 0; f < NV; f++) {
+        double cm, c0, cp;
+        mc_slope_coef(limiter, q[0][f], q[1][f], q[2][f], cm, c0, cp);
+        qb[0][f] += 0.5 * cm * qLb[f];
+        qb[1][f] += (1.0 + 0.5 * c0) * qLb[f];
+        qb[2][f] += 0.5 * cp * qLb[f];
+        mc_slope_coef(limiter, q[1][f], q[2][f], q[3][f], cm, c0, cp);
+        qb[1][f] -= 0.5 * cm * qRb[f];
+        qb[2][f] += (1.0 - 0.5 * c0) * qRb[f];
+        qb[3][f] -= 0.5 * cp * qRb[f];
+    }
+    // primitives -> conserved: u = m / rho, p = (gamma - 1)(E - |m|^2 / (2 rho)), X = rho X / rho
+#pragma unroll
+    for (int z = 0; z < 4; z++) {
+        const double ir = 1.0 / q[z][0];
+        double u2 = 0.0;
+#pragma unroll
+        for (int d = 0; d < DIM; d++) u2 += q[z][1 + d] * q[z][1 + d];
+        const double pbz = qb[z][IE] * gm1;
+        double rhob = qb[z][0] + pbz * 0.5 * u2;
+#pragma unroll
+        for (int d = 0; d < DIM; d++) {
+            rhob -= qb[z][1 + d] * q[z][1 + d] * ir;
+            Ub[z][1 + d] += qb[z][1 + d] * ir - pbz * q[z][1 + d];
+        }
+        Ub[z][IE] += pbz;
+#pragma unroll
+        for (int s = 0; s < NS; s++) {
+            rhob -= qb[z][IX + s] * q[z][IX + s] * ir;
+            Ub[z][IX + s] += qb[z][IX + s] * ir;
+        }
+        Ub[z][0] += rhob;
+    }
 }
 
 }  // namespace sdcd

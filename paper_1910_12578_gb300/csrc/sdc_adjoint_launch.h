@@ -22,7 +22,8 @@ struct RhsAdjArgs {
 
 bool adjoint_supported(int dim, int nspec, int topo);
 cudaError_t launch_stencil_vjp(const NetParams& P, int dim, int limiter, long long N, const BoxDev* boxes, int nbox,
-                               const double* U, const double* Abar, double* G, double* Ubar, cudaStream_t st);
+                               const double* U, const double* Abar, double* G, double* Ubar, cudaStream_t st,
+                               int mode = 0);  // 0: reverse sweep per face, 1: forward-mode dual numbers
 cudaError_t launch_reaction_vjp(const NetParams& P, int dim, long long N, const double* U, const double* Rbar,
                                 double* Ubar, double dtm, double* rhsbar, double* abar_zone, cudaStream_t st);
 cudaError_t launch_rhs_adjoint(const RhsAdjArgs& a, cudaStream_t st);

@@ -339,6 +339,36 @@ sdc_status read_stats(sdc_ctx* c, sdc_stats* stats) {
     return stats->n_fail ? SDC_ERR_NEWTON_NOCONV : SDC_OK;
 }
 
+// the adjoint workspace of the context, allocated on first use
+cudaError_t adjoint_workspace(sdc_ctx* c) {
+    auto& A = c->adj;
+    if (A.ready) return cudaSuccess;
+    const long long N = c->Ntot;
+    const int M = c->M, K = c->K, nw = c->nw, nr = c->P.nreac;
+    const size_t ub = sizeof(double) * c->nvar * N, rb = sizeof(double) * nw * N;
+    cudaError_t e;
+#define ADJ_ALLOC(ptr, bytes) \
+    if ((e = ctx_alloc(c, (void**)&(ptr), (bytes))) != cudaSuccess) return e;
+    ADJ_ALLOC(A.work, ub);
+    A.store.assign(K * (M - 1), nullptr);
+    for (auto& p : A.store) ADJ_ALLOC(p, ub);
+    for (int m = 0; m < M; m++) ADJ_ALLOC(A.Ubar_node[m], ub);
+    for (int g = 0; g < 2; g++)
+        for (int m = 0; m < M; m++) {
+            ADJ_ALLOC(A.Abar[g][m], ub);
+            ADJ_ALLOC(A.Rbar[g][m], rb);
+        }
+    ADJ_ALLOC(A.Abar_n, ub);
+    ADJ_ALLOC(A.Rbar_n, rb);
+    ADJ_ALLOC(A.Ubar_n, ub);
+    ADJ_ALLOC(A.rhsbar, ub);
+    ADJ_ALLOC(A.G, sizeof(double) * (size_t)c->dim * N * 4 * c->nvar);
+    ADJ_ALLOC(A.abar_zone, sizeof(double) * (size_t)(nr > 0 ? nr : 1) * N);
+#undef ADJ_ALLOC
+    A.ready = true;
+    return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
@@ -703,6 +733,15 @@ sdc_status sdc_set_rates(sdc_ctx* ctx, const double* a) {
     return SDC_OK;
 }
 
+sdc_status sdc_advective_term_vjp(sdc_ctx* ctx, const double* U, const double* Abar, double* Ubar, int mode) {
+    if (!ctx || !U || !Abar || !Ubar || (mode != 0 && mode != 1)) return SDC_ERR_INVALID_ARG;
+    if (!adjoint_supported(ctx->dim, ctx->nspec, ctx->P.topo)) return SDC_ERR_INVALID_ARG;
+    SDC_TRY(adjoint_workspace(ctx));
+    SDC_TRY(launch_stencil_vjp(ctx->P, ctx->dim, ctx->limiter, ctx->Ntot, ctx->d_boxes, ctx->nbox, U, Abar,
+                               ctx->adj.G, Ubar, ctx->stream, mode));
+    return SDC_OK;
+}
+
 sdc_status sdc_step_backward(sdc_ctx* ctx, const double* U_n, double dt, const double* gU_np1, double* gU_n,
                              double* g_a) {
     if (!ctx || !U_n || !gU_np1 || !gU_n || !(dt > 0.0)) return SDC_ERR_INVALID_ARG;
@@ -713,24 +752,7 @@ sdc_status sdc_step_backward(sdc_ctx* ctx, const double* U_n, double dt, const d
     const size_t ub = sizeof(double) * c->nvar * N, rb = sizeof(double) * nw * N;
     cudaStream_t st = c->stream;
     auto& A = c->adj;
-    if (!A.ready) {
-        SDC_TRY(ctx_alloc(c, (void**)&A.work, ub));
-        A.store.assign(K * (M - 1), nullptr);
-        for (auto& p : A.store) SDC_TRY(ctx_alloc(c, (void**)&p, ub));
-        for (int m = 0; m < M; m++) SDC_TRY(ctx_alloc(c, (void**)&A.Ubar_node[m], ub));
-        for (int g = 0; g < 2; g++)
-            for (int m = 0; m < M; m++) {
-                SDC_TRY(ctx_alloc(c, (void**)&A.Abar[g][m], ub));
-                SDC_TRY(ctx_alloc(c, (void**)&A.Rbar[g][m], rb));
-            }
-        SDC_TRY(ctx_alloc(c, (void**)&A.Abar_n, ub));
-        SDC_TRY(ctx_alloc(c, (void**)&A.Rbar_n, rb));
-        SDC_TRY(ctx_alloc(c, (void**)&A.Ubar_n, ub));
-        SDC_TRY(ctx_alloc(c, (void**)&A.rhsbar, ub));
-        SDC_TRY(ctx_alloc(c, (void**)&A.G, sizeof(double) * (size_t)c->dim * N * 4 * c->nvar));
-        SDC_TRY(ctx_alloc(c, (void**)&A.abar_zone, sizeof(double) * (size_t)(nr > 0 ? nr : 1) * N));
-        A.ready = true;
-    }
+    SDC_TRY(adjoint_workspace(c));
     // 1. recompute the step from the checkpoint, keeping every node state
     SDC_TRY(cudaMemcpyAsync(A.work, U_n, ub, cudaMemcpyDeviceToDevice, st));
     set_scalar_kernel<<<1, 1, 0, st>>>(c->d_dt, dt);

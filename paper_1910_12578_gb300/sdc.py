@@ -25,7 +25,7 @@ PREC_FP64, PREC_FP32_JAC = 0, 1
 EXPORTS = ["sdc_init_box", "sdc_advective_term", "sdc_node_integral", "sdc_react_newton", "sdc_step",
            "sdc_step_profile", "sdc_launches_per_step", "sdc_cfl_dt", "sdc_sizes", "sdc_destroy",
            "sdc_status_string", "sdc_step_static", "sdc_selftest_math", "sdc_autotune", "sdc_set_variants",
-           "sdc_step_backward", "sdc_set_rates"]
+           "sdc_step_backward", "sdc_set_rates", "sdc_advective_term_vjp"]
 
 
 class SdcError(RuntimeError):
@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH):
     L.sdc_autotune.argtypes = [vp, dp, C.c_double, C.POINTER(Tuning)]
     L.sdc_step_backward.argtypes = [vp, dp, C.c_double, dp, dp, dp]
     L.sdc_set_rates.argtypes = [vp, C.POINTER(C.c_double)]
+    L.sdc_advective_term_vjp.argtypes = [vp, dp, dp, dp, C.c_int]
     L.sdc_set_variants.argtypes = [vp, C.c_int, C.c_int]
     L.sdc_step_static.argtypes = [C.POINTER(Box), C.c_int, C.POINTER(Network), C.POINTER(Params), vp, dp,
                                   C.c_double, C.POINTER(Stats)]
@@ -115,7 +116,7 @@ def load(path: str = LIB_PATH):
     L.sdc_status_string.restype = C.c_char_p
     for name in ("sdc_init_box", "sdc_advective_term", "sdc_node_integral", "sdc_react_newton", "sdc_step",
                  "sdc_cfl_dt", "sdc_sizes", "sdc_step_profile", "sdc_launches_per_step", "sdc_step_static", "sdc_selftest_math", "sdc_autotune",
-                 "sdc_set_variants", "sdc_step_backward", "sdc_set_rates"):
+                 "sdc_set_variants", "sdc_step_backward", "sdc_set_rates", "sdc_advective_term_vjp"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -248,6 +249,11 @@ class Context:
         ga = _ptr(g_a) if g_a is not None else None
         self._check(self.L.sdc_step_backward(self._h, _ptr(U_n), float(dt), _ptr(gU_np1), _ptr(gU_n), ga),
                     "sdc_step_backward")
+
+    def advective_term_vjp(self, U, Abar, Ubar, mode=0):
+        """Ubar += (dA/dU)^T Abar at U (mode 0: reverse sweep per face; 1: forward-mode duals)."""
+        self._check(self.L.sdc_advective_term_vjp(self._h, _ptr(U), _ptr(Abar), _ptr(Ubar), int(mode)),
+                    "sdc_advective_term_vjp")
 
     def set_rates(self, a):
         """Replace the rate prefactors a_j (host values)."""

@@ -97,7 +97,8 @@ def generic_state(P, seed):
     """Smooth state without ties: the hot-spot temperature modulated by 10%,
     density 1 +- 0.1, a mean flow in every direction (no sonic or contact
     sign change at any face) with 0.03 modulation, and a smooth positive
-    composition (X_0 about 0.8)."""
+    composition with X_0 between 0.7 and 0.9 (a field that is uniform up to
+    rounding would leave the limiter's branch to rounding)."""
     rng = np.random.default_rng(seed)
     shp = (P.n[2], P.n[1], P.n[0])
     Th = base_T(P)
@@ -107,7 +108,7 @@ def generic_state(P, seed):
     ns = P.net.nspec
     c = rng.uniform(0.5, 1.0, ns - 1)
     Xo = np.stack([c[i] * (1.0 + 0.5 * smooth_field(rng, shp)) for i in range(ns - 1)])
-    Xo *= 0.2 / Xo.sum(0)
+    Xo *= 0.2 * (1.0 + 0.5 * smooth_field(rng, shp)) / Xo.sum(0)   # X_0 varies too (0.7 .. 0.9)
     X = [1.0 - Xo.sum(0)] + list(Xo)
     return W.conserved_from(P.gamma, rho, vel, T, X)
 
@@ -185,6 +186,74 @@ def T_gradient(P, U0, gU0):
 
 
 # ------------------------------------------------------------------ tests
+def vjp_case(name, limiter):
+    if name == "1d":
+        P, U = W.config_1d()
+    elif name == "box16":
+        P, U = W.config_box(n=16, nspec=7, n_iters=3, seed=1, T0=0.5)
+    else:
+        P, _ = W.config_box(n=16, nspec=7, n_iters=3, seed=1, T0=0.5)
+        U = None
+    P = copy.deepcopy(P)
+    P.limiter = limiter
+    if U is None:
+        U = generic_state(P, 5)
+    return P, U
+
+
+@pytest.mark.parametrize("name,limiter", [("1d", 1), ("box16", 0), ("smooth16", 0), ("smooth16", 1)])
+def test_advective_vjp_reverse_sweep_matches_forward_mode(torch_cuda, name, limiter):
+    """sdc_advective_term_vjp: the reverse sweep per face (mode 0, used by the
+    backward step) against forward-mode dual numbers (mode 1), and accumulation.
+    The two round u = m / rho and p differently, so a limiter tie that only
+    rounding separates may take different branches in the two: the MC cases
+    use states whose neighbouring values differ far above rounding (the
+    hot-spot box's far field does not)."""
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = vjp_case(name, limiter)
+    ctx = sdc.Context(P)
+    Ud = torch.from_numpy(U).cuda()
+    Ab = torch.from_numpy(np.random.default_rng(4).normal(size=U.shape)).cuda()
+    g0, g1 = torch.zeros_like(Ud), torch.zeros_like(Ud)
+    ctx.advective_term_vjp(Ud, Ab, g0, 0)
+    ctx.advective_term_vjp(Ud, Ab, g1, 1)
+    torch.cuda.synchronize()
+    a, b = g0.cpu().numpy(), g1.cpu().numpy()
+    scale = np.abs(b).reshape(b.shape[0], -1).max(1)
+    err = (np.abs(a - b).reshape(b.shape[0], -1).max(1) / np.maximum(scale, 1e-300 + 1e-12 * scale.max())).max()
+    print(name, "limiter", limiter, "reverse vs forward mode:", err)
+    assert np.isfinite(a).all()
+    assert err <= 1e-12
+    ctx.advective_term_vjp(Ud, Ab, g0, 0)
+    torch.cuda.synchronize()
+    assert np.array_equal(g0.cpu().numpy(), 2.0 * a)
+
+
+def test_advective_vjp_matches_oracle_differences(torch_cuda):
+    """v . (dA/dU)^T Abar against the fourth-order difference of Abar . A(U + t v)
+    of the oracle's advective term (centred slopes).  The Davis wave speeds
+    (min and max of the two sides' u -/+ c) switch sides on surfaces that cut
+    many faces of a smooth 3D flow, so the difference uses a step of 1e-8
+    relative, small enough to cross none of those switches (1e-6 crosses some:
+    the differences then move by ~2e-6), with round-off near 3e-9."""
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = vjp_case("smooth16", 0)
+    o = O.Oracle(P)
+    rng = np.random.default_rng(8)
+    Abar = rng.normal(size=U.shape)
+    v = U * rng.normal(size=U.shape)
+    ctx = sdc.Context(P)
+    g = torch.zeros(U.shape, dtype=torch.float64, device="cuda")
+    ctx.advective_term_vjp(torch.from_numpy(U).cuda(), torch.from_numpy(Abar).cuda(), g, 0)
+    torch.cuda.synchronize()
+    lhs = float(np.sum(v * g.cpu().numpy()))
+    d = fd(lambda t: float(np.sum(Abar * o.advective(U + t * v))), 0.0, 1e-8)
+    print("advective VJP vs oracle difference:", abs(lhs - d) / abs(d))
+    assert abs(lhs - d) <= 1e-7 * abs(d)
+
+
 def yields(P, U):
     """Mass of every product species A_1 .. A_{n-1} in the box."""
     dV = P.dx[0] * P.dx[1] * P.dx[2]
