@@ -36,8 +36,13 @@ struct GroupLayout {
     static constexpr int O_YT = O_Y + NS;
     static constexpr int O_R = O_YT + NS;      // reaction rates r_j (scratch)
     static constexpr int O_DR = O_R + NR;      // dr_j/dw_E, dr_j/dw_X0, dr_j/dw_Xj (scratch)
-    static constexpr int O_IP = O_DR + 3 * NR; // reciprocal pivots
-    static constexpr int RAW = O_IP + N;
+    static constexpr int O_IP = O_DR + 3 * NR; // reciprocal pivots (as MT)
+    // the right-hand side / solution of the linear solve as MT: the FP64 slot
+    // O_D itself for double, a slot of its own for float (so that the whole
+    // solve stays in float: one conversion in, one out)
+    static constexpr int V_D = (N * (int)sizeof(MT) + 7) / 8;
+    static constexpr int O_DM = sizeof(MT) == 8 ? O_D : O_IP + N;
+    static constexpr int RAW = sizeof(MT) == 8 ? O_IP + N : O_DM + V_D;
     static constexpr int STRIDE = RAW | 1;     // odd stride in doubles spreads the banks
 };
 
@@ -47,6 +52,27 @@ __device__ __forceinline__ double group_sum(unsigned mask, double v) {
     for (int o = 1; o < L; o <<= 1) v += __shfl_xor_sync(mask, v, o);
     return v;
 }
+
+template <int L, typename T>
+__device__ __forceinline__ T group_sum_t(unsigned mask, T v) {
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) v += __shfl_xor_sync(mask, v, o);
+    return v;
+}
+
+// |x| as an integer bit pattern (non-negative values order like their patterns)
+template <typename MT>
+struct AbsBits;
+template <>
+struct AbsBits<double> {
+    using type = long long;
+};
+template <>
+struct AbsBits<float> {
+    using type = int;
+};
+__device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & ABS_MASK; }
+__device__ __forceinline__ int abs_bits(float x) { return __float_as_int(x) & 0x7fffffff; }
 
 template <int L>
 __device__ __forceinline__ bool group_all(unsigned mask, bool p) {
@@ -126,6 +152,9 @@ __device__ __forceinline__ int newton_zone_group(const NetParams& P, const Newto
     constexpr int N = Lay::N, NR = Lay::NR;
     constexpr int RL = (N + L - 1) / L;
     MT* M = reinterpret_cast<MT*>(zs + Lay::O_M);
+    MT* dm = reinterpret_cast<MT*>(zs + Lay::O_DM);   // right-hand side, then the Newton step
+    MT* ipm = reinterpret_cast<MT*>(zs + Lay::O_IP);  // reciprocal pivots
+    using IT = typename AbsBits<MT>::type;
     const double inv_rho = rcp_nr(rho);
     const double ke = 0.5 * m2 * inv_rho;
     double ym[NS];
@@ -242,26 +271,27 @@ __device__ __forceinline__ int newton_zone_group(const NetParams& P, const Newto
                         Mr[1 + j] -= (MT)(am * zs[Lay::O_DR + 3 * j + 2]);
                     }
                 }
-                zs[Lay::O_D + row] = zs[Lay::O_G + row];
+                dm[row] = (MT)zs[Lay::O_G + row];
             }
             __syncwarp(mask);
             // ---- LU with partial pivoting, rows exchanged column-wise across the lanes
             bool singular = false;
             for (int k = 0; k < N; k++) {
-                // pivot: largest |M[i][k]|, i >= k, ties to the lowest row
-                double best = -1.0;
+                // pivot: largest |M[i][k]|, i >= k, ties to the lowest row (|x|
+                // compared as bit patterns on the integer pipe: they order like the values)
+                IT best = -1;
                 int piv = N;
                 for (int i = k + lane; i < N; i += L) {
-                    const double v = fabs((double)M[i * N + k]);
+                    const IT v = abs_bits(M[i * N + k]);
                     if (v > best) { best = v; piv = i; }
                 }
 #pragma unroll
                 for (int o = 1; o < L; o <<= 1) {
-                    const double ob = __shfl_xor_sync(mask, best, o);
+                    const IT ob = __shfl_xor_sync(mask, best, o);
                     const int op = __shfl_xor_sync(mask, piv, o);
                     if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
                 }
-                if (!(best > 0.0)) { singular = true; break; }
+                if (!(best > 0)) { singular = true; break; }
                 if (piv != k) {
                     for (int q = k + lane; q < N; q += L) {
                         const MT a = M[k * N + q];
@@ -269,44 +299,35 @@ __device__ __forceinline__ int newton_zone_group(const NetParams& P, const Newto
                         M[piv * N + q] = a;
                     }
                     if (lane == 0) {
-                        const double a = zs[Lay::O_D + k];
-                        zs[Lay::O_D + k] = zs[Lay::O_D + piv];
-                        zs[Lay::O_D + piv] = a;
+                        const MT a = dm[k];
+                        dm[k] = dm[piv];
+                        dm[piv] = a;
                     }
                 }
                 __syncwarp(mask);
                 const MT pv = M[k * N + k];
                 const MT ip = (sizeof(MT) == 8) ? (MT)rcp_nr((double)pv) : (MT)1 / pv;
-                if (lane == 0) zs[Lay::O_IP + k] = (double)ip;
-                const double dk_ = zs[Lay::O_D + k];
+                if (lane == 0) ipm[k] = ip;
+                const MT dk_ = dm[k];
                 for (int i = k + 1 + lane; i < N; i += L) {
                     const MT l = M[i * N + k] * ip;
                     M[i * N + k] = l;
                     for (int q = k + 1; q < N; q++) M[i * N + q] -= l * M[k * N + q];
-                    if (sizeof(MT) == 8)
-                        zs[Lay::O_D + i] -= (double)l * dk_;
-                    else
-                        zs[Lay::O_D + i] = (double)((MT)zs[Lay::O_D + i] - l * (MT)dk_);
+                    dm[i] -= l * dk_;
                 }
                 __syncwarp(mask);
             }
             if (singular) { status = ZONE_SINGULAR; break; }
             // ---- back substitution (dot products split across the lanes)
             for (int i = N - 1; i >= 0; i--) {
-                double part = 0.0;
-                for (int q = i + 1 + lane; q < N; q += L) {
-                    if (sizeof(MT) == 8)
-                        part += (double)M[i * N + q] * zs[Lay::O_D + q];
-                    else
-                        part = (double)((MT)part + M[i * N + q] * (MT)zs[Lay::O_D + q]);
-                }
-                part = group_sum<L>(mask, part);
-                if (lane == 0) {
-                    if (sizeof(MT) == 8)
-                        zs[Lay::O_D + i] = (zs[Lay::O_D + i] - part) * zs[Lay::O_IP + i];
-                    else
-                        zs[Lay::O_D + i] = (double)(((MT)zs[Lay::O_D + i] - (MT)part) * (MT)zs[Lay::O_IP + i]);
-                }
+                MT part = 0;
+                for (int q = i + 1 + lane; q < N; q += L) part += M[i * N + q] * dm[q];
+                part = group_sum_t<L, MT>(mask, part);
+                if (lane == 0) dm[i] = (dm[i] - part) * ipm[i];
+                __syncwarp(mask);
+            }
+            if (sizeof(MT) != 8) {
+                for (int r = lane; r < N; r += L) zs[Lay::O_D + r] = (double)dm[r];
                 __syncwarp(mask);
             }
             // ---- trial state, admissibility, residual at the trial
