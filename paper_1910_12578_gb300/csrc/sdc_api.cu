@@ -515,7 +515,7 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     if ((e = ctx_alloc(c, (void**)&c->d_boxes, sizeof(BoxDev) * nbox)) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->d_tiles, sizeof(TileDev) * c->tiles_capacity)) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->d_queue, sizeof(unsigned long long) * QUEUE_SLOTS)) != cudaSuccess) return fail(e);
-    c->persistent_blocks = newton_variants(net->nspec, topo_used) > 1 ? newton_persistent_blocks(P, c->prec) : 0;
+    c->persistent_blocks = newton_group_case(net->nspec, topo_used) ? 0 : newton_persistent_blocks(P, c->prec);
     if ((e = ctx_alloc(c, (void**)&c->d_dt, sizeof(double))) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->d_stats, sizeof(DevStats))) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->d_smax, sizeof(unsigned long long))) != cudaSuccess) return fail(e);

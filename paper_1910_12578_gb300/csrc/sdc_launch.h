@@ -22,6 +22,7 @@ cudaError_t stencil_prepare(int dim, int nspec);  // raise the dynamic shared-me
 // persistent_blocks fed by the zero-initialised device counter *queue (zones
 // of uneven cost balance across lanes); the group kernel ignores the variant.
 int newton_variants(int nspec, int topo);
+bool newton_group_case(int nspec, int topo);  // the 13-species chain (a group of lanes per zone)
 cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, long long N, int dim,
                           const double* rhs, const double* guess, double* Uout, double* Rout,
                           const double* dt_dev, double dt_frac, double dtm_host, int* zone_status,

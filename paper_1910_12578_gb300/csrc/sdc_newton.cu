@@ -162,8 +162,12 @@ newton_queue_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const doub
         if (hist[i]) atomicAdd(&stats->hist[i], (unsigned long long)hist[i]);
 }
 
-// L lanes per zone (alpha chain); zone state in dynamic shared memory
-constexpr int GROUP_L = 4;
+// L lanes per zone (alpha chain), GROUP_ZONES zones per block of 32 L threads;
+// zone state in dynamic shared memory.  Variant 0: L = 4, variant 1: L = 2
+// (half the lanes share each zone's split work, so instructions that every
+// lane of a group repeats -- pivot reciprocals, transcendentals, the lane-0
+// steps of the back substitution -- occupy half the warp slots per zone).
+constexpr int GROUP_ZONES = 32;
 
 template <int NS, typename MT, int L>
 __global__ void __launch_bounds__(NEWTON_BLOCK)
@@ -181,7 +185,7 @@ newton_group_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const doub
     const int lane = threadIdx.x % L;
     const int gz = threadIdx.x / L;  // zone of this group within the block
     const unsigned mask = ((1u << L) - 1u) << ((threadIdx.x & 31) & ~(L - 1));
-    const long long z = (long long)blockIdx.x * (NEWTON_BLOCK / L) + gz;
+    const long long z = (long long)blockIdx.x * GROUP_ZONES + gz;
     const bool active = z < N;
     double* zs = gsm + (size_t)gz * Lay::STRIDE;
     int iters = 0, status = ZONE_OK;
@@ -244,7 +248,7 @@ newton_group_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const doub
 
 template <int NS, typename MT>
 constexpr size_t group_smem() {
-    return sizeof(double) * (size_t)GroupLayout<NS, MT>::STRIDE * (NEWTON_BLOCK / GROUP_L);
+    return sizeof(double) * (size_t)GroupLayout<NS, MT>::STRIDE * GROUP_ZONES;
 }
 
 template <int NS, int TOPO>
@@ -285,11 +289,18 @@ bool newton_group_case(int nspec, int topo) { return nspec == 13 && topo == TOPO
 
 cudaError_t newton_prepare(int nspec, int topo) {
     if (!newton_group_case(nspec, topo)) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(newton_group_kernel<13, double, GROUP_L>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)group_smem<13, double>());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(newton_group_kernel<13, float, GROUP_L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)group_smem<13, float>());
+    const int sd = (int)group_smem<13, double>(), sf = (int)group_smem<13, float>();
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(newton_group_kernel<13, double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  sd)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(newton_group_kernel<13, float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  sf)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(newton_group_kernel<13, double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  sd)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(newton_group_kernel<13, float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
 }
 
 bool newton_supported(int nspec, int topo) {
@@ -301,7 +312,8 @@ bool newton_supported(int nspec, int topo) {
     return false;
 }
 
-int newton_variants(int nspec, int topo) { return newton_group_case(nspec, topo) ? 1 : 2; }
+// 7-and-fewer-species kernels: static grid (0) or persistent queue (1); 13-species chain: 4 (0) or 2 (1) lanes per zone
+int newton_variants(int, int) { return 2; }
 
 int newton_persistent_blocks(const NetParams& P, int prec) {
     int dev = 0, sms = 0, per = 0;
@@ -327,14 +339,18 @@ cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, lo
                           unsigned long long* queue, int persistent_blocks) {
     if (N <= 0) return cudaSuccess;
     if (P.nspec == 13 && P.topo == TOPO_CHAIN) {
-        constexpr int ZPB = NEWTON_BLOCK / GROUP_L;
-        const unsigned ggrid = (unsigned)((N + ZPB - 1) / ZPB);
-        if (prec == 0)
-            newton_group_kernel<13, double, GROUP_L><<<ggrid, NEWTON_BLOCK, group_smem<13, double>(), st>>>(
-                P, cfg, N, dim, rhs, guess, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, zone_iters, stats);
-        else
-            newton_group_kernel<13, float, GROUP_L><<<ggrid, NEWTON_BLOCK, group_smem<13, float>(), st>>>(
-                P, cfg, N, dim, rhs, guess, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, zone_iters, stats);
+        const unsigned ggrid = (unsigned)((N + GROUP_ZONES - 1) / GROUP_ZONES);
+#define SDC_GROUP_LAUNCH(MT, L)                                                                                    \
+    newton_group_kernel<13, MT, L><<<ggrid, 32 * L, group_smem<13, MT>(), st>>>(                                   \
+        P, cfg, N, dim, rhs, guess, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, zone_iters, stats)
+        if (variant == 1) {
+            if (prec == 0) SDC_GROUP_LAUNCH(double, 2);
+            else SDC_GROUP_LAUNCH(float, 2);
+        } else {
+            if (prec == 0) SDC_GROUP_LAUNCH(double, 4);
+            else SDC_GROUP_LAUNCH(float, 4);
+        }
+#undef SDC_GROUP_LAUNCH
         return cudaGetLastError();
     }
     const unsigned grid = (unsigned)((N + NEWTON_BLOCK - 1) / NEWTON_BLOCK);

@@ -209,6 +209,36 @@ def test_kernel_variants_agree_bitwise(torch_cuda, name):
         assert o[1:] == outs[0][1:]
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_13species_group_widths_match_oracle(torch_cuda, prec):
+    """The 13-species Newton with 4 (variant 0) and 2 (variant 1) lanes per zone:
+    each against the oracle over two SDC steps; the two agree to round-off
+    (their partial sums associate differently) and each is deterministic."""
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = PROBS["box16_13"]
+    o = O.Oracle(P)
+    dt = o.cfl_dt(U)
+    V = U.copy()
+    for _ in range(2):
+        V, _ = o.step(V, dt)
+    outs = []
+    for nv in (0, 1, 1):
+        ctx = sdc.Context(P, prec=prec)
+        ctx.set_variants(0, nv)
+        Ud = dev(torch, U)
+        for _ in range(2):
+            st = ctx.step(Ud, dt)
+        assert st.n_fail == 0
+        outs.append(Ud.cpu().numpy())
+    tol = TOL64 if prec == 0 else TOL32
+    for g in outs:
+        e = rel_err(g, V, P.nvar, P.dim)
+        assert e.max() <= tol, e
+    assert np.array_equal(outs[1], outs[2])
+    assert rel_err(outs[1], outs[0], P.nvar, P.dim).max() <= (1e-13 if prec == 0 else TOL32)
+
+
 def test_autotune_keeps_U_and_picks_valid_variants(torch_cuda):
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
