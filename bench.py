@@ -289,7 +289,7 @@ def cpu_baseline_sampled(P, U, dt, gpu_out, seed, target_s=10.0, max_steps=3):
         iz = np.arange(z - R, z + R + 1) % P.n[2]
         sub = U.reshape(P.nvar, P.n[2], P.n[1], P.n[0])[:, iz][:, :, iy][:, :, :, ix].copy()
         Ps = W.Problem(dim=3, n=(2 * R + 1,) * 3, dx=P.dx, gamma=P.gamma, net=P.net, n_nodes=P.n_nodes,
-                       n_iters=P.n_iters)
+                       n_iters=P.n_iters, nodes=P.nodes)
         Vs, _ = O.Oracle(Ps).step(sub, dt)
         worst = max(worst, float((np.abs(g[:, z, y, x] - Vs[:, R, R, R]) / scale).max()))
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))

@@ -39,8 +39,11 @@ class _Problem(C.Structure):
         ("mass", C.c_double * MAX_SPEC), ("a", C.c_double * MAX_REAC), ("nu", C.c_double * MAX_REAC),
         ("Q", C.c_double * MAX_REAC), ("reac", (C.c_int * 2) * MAX_REAC), ("cnt", (C.c_int * 2) * MAX_REAC),
         ("prod", C.c_int * MAX_REAC), ("n_nodes", C.c_int), ("n_iters", C.c_int),
-        ("newton_rtol", C.c_double), ("newton_maxit", C.c_int),
+        ("newton_rtol", C.c_double), ("newton_maxit", C.c_int), ("node_type", C.c_int),
     ]
+
+
+NODE_TYPES = {"lobatto": 0, "radau": 1}
 
 
 class _Stats(C.Structure):
@@ -59,8 +62,8 @@ def lib():
         ip = C.POINTER(C.c_int)
         pp = C.POINTER(_Problem)
         _lib.orc_nvar.argtypes = [pp]
-        _lib.orc_quad_weights.argtypes = [C.c_int, dp]
-        _lib.orc_nodes.argtypes = [C.c_int, dp]
+        _lib.orc_quad_weights.argtypes = [C.c_int, C.c_int, dp]
+        _lib.orc_nodes.argtypes = [C.c_int, C.c_int, dp]
         _lib.orc_temperature.argtypes = [pp, C.c_double, dp, C.c_double]
         _lib.orc_temperature.restype = C.c_double
         _lib.orc_advective.argtypes = [pp, dp, dp]
@@ -111,6 +114,7 @@ class Oracle:
             s.prod[j] = int(net.prod[j])
         s.n_nodes, s.n_iters = P.n_nodes, P.n_iters
         s.newton_rtol, s.newton_maxit = P.newton_rtol, P.newton_maxit
+        s.node_type = NODE_TYPES[P.nodes]
         self.s = s
         self.L = lib()
         self.nvar = P.nvar
@@ -213,8 +217,15 @@ class Oracle:
         return U, dt_used, stats
 
 
-def quad_weights(M):
+def quad_weights(M, nodes="lobatto"):
     q = np.zeros((M - 1) * M)
-    rc = lib().orc_quad_weights(int(M), _dp(q))
+    rc = lib().orc_quad_weights(NODE_TYPES[nodes], int(M), _dp(q))
     assert rc == 0
     return q.reshape(M - 1, M)
+
+
+def nodes(M, nodes="lobatto"):
+    tau = np.zeros(M)
+    rc = lib().orc_nodes(NODE_TYPES[nodes], int(M), _dp(tau))
+    assert rc == 0
+    return tau

@@ -33,26 +33,51 @@ static long long nzones(const orc_problem* P) {
 /* ------------------------------------------------------------------ */
 /* Temporal nodes and the node-to-node quadrature (section 2: the     */
 /* integral of Eq. sdc:general, trapezoid / Simpson rule).            */
-/* Gauss-Lobatto nodes on [0,1]: M=2 -> {0,1}, M=3 -> {0,1/2,1}.      */
+/* Gauss-Lobatto nodes on [0,1]: M=2 -> {0,1}, M=3 -> {0,1/2,1}; the   */
+/* quadrature interpolates through all M nodes.                       */
+/* Radau (section 4: other quadratures for highly stiff reactions):   */
+/* node 0 at t^n and the s = M-1 right-endpoint Gauss-Radau points,   */
+/* the zeros of P_s(2t-1) - P_{s-1}(2t-1) (P Legendre): s=1 -> {1},   */
+/* s=2 -> {1/3, 1}, s=3 -> {(4-sqrt6)/10, (4+sqrt6)/10, 1}; the        */
+/* quadrature interpolates through those s points only, so that the   */
+/* converged sweep is Radau IIA collocation.                          */
 /* ------------------------------------------------------------------ */
-int orc_nodes(int M, double* tau) {
-    if (M == 2) { tau[0] = 0.0; tau[1] = 1.0; return 0; }
-    if (M == 3) { tau[0] = 0.0; tau[1] = 0.5; tau[2] = 1.0; return 0; }
+int orc_nodes(int type, int M, double* tau) {
+    if (type == ORC_NODES_LOBATTO) {
+        if (M == 2) { tau[0] = 0.0; tau[1] = 1.0; return 0; }
+        if (M == 3) { tau[0] = 0.0; tau[1] = 0.5; tau[2] = 1.0; return 0; }
+        return -1;
+    }
+    if (type == ORC_NODES_RADAU) {
+        tau[0] = 0.0;
+        if (M == 2) { tau[1] = 1.0; return 0; }
+        if (M == 3) { tau[1] = 1.0 / 3.0; tau[2] = 1.0; return 0; }
+        if (M == 4) {
+            tau[1] = (4.0 - sqrt(6.0)) / 10.0;
+            tau[2] = (4.0 + sqrt(6.0)) / 10.0;
+            tau[3] = 1.0;
+            return 0;
+        }
+        return -1;
+    }
     return -1;
 }
 
 /* q_{m,l} = integral over [tau_m, tau_{m+1}] of the Lagrange basis
-   polynomial L_l through the M nodes.  The polynomial is expanded into
+   polynomial L_l through the interpolation nodes (all M for Lobatto, nodes
+   1..M-1 for Radau; q_{m,0} = 0 there).  The polynomial is expanded into
    monomial coefficients and integrated term by term. */
-int orc_quad_weights(int M, double* q) {
+int orc_quad_weights(int type, int M, double* q) {
     double tau[8];
-    if (orc_nodes(M, tau) != 0) return -1;
-    for (int l = 0; l < M; l++) {
-        /* coefficients c[0..M-1] of L_l(t) = prod_{j!=l} (t - tau_j)/(tau_l - tau_j) */
+    if (orc_nodes(type, M, tau) != 0) return -1;
+    int l0 = (type == ORC_NODES_RADAU) ? 1 : 0;
+    for (int m = 0; m < M - 1; m++) q[m * M + 0] = 0.0;
+    for (int l = l0; l < M; l++) {
+        /* coefficients c[0..] of L_l(t) = prod_{j!=l} (t - tau_j)/(tau_l - tau_j) */
         double c[8] = {0};
         c[0] = 1.0;
         int deg = 0;
-        for (int j = 0; j < M; j++) {
+        for (int j = l0; j < M; j++) {
             if (j == l) continue;
             double den = tau[l] - tau[j];
             double nc[8] = {0};
@@ -551,7 +576,7 @@ void orc_node_integral(const orc_problem* P, const double* const* A_nodes,
     int M = P->n_nodes, dim = P->dim, nv = orc_nvar(P);
     long long N = nzones(P);
     double q[64];
-    orc_quad_weights(M, q);
+    orc_quad_weights(P->node_type, M, q);
     for (int f = 0; f < nv; f++)
         for (long long z = 0; z < N; z++) {
             double s = 0.0;
@@ -579,9 +604,8 @@ void orc_node_integral(const orc_problem* P, const double* const* A_nodes,
 int orc_sdc_step_nodes(const orc_problem* P, double* U, double dt, orc_stats* st, double* nodes_out) {
     int M = P->n_nodes, K = P->n_iters, dim = P->dim, nv = orc_nvar(P), n = P->nspec + 1;
     long long N = nzones(P);
-    if (M != 2 && M != 3) return -1;
     double tau[8];
-    orc_nodes(M, tau);
+    if (orc_nodes(P->node_type, M, tau) != 0) return -1;
     size_t sz_u = sizeof(double) * nv * N, sz_r = sizeof(double) * n * N;
     double *Un[8], *Aold[8], *Anew[8], *Rold[8], *Rnew[8];
     for (int m = 0; m < M; m++) {

@@ -56,11 +56,16 @@ typedef struct {
     int reac[ORC_MAX_REAC][2];          /* reactant species, -1 = none   */
     int cnt[ORC_MAX_REAC][2];           /* reactant multiplicities        */
     int prod[ORC_MAX_REAC];             /* product species                */
-    int n_nodes;        /* M: 2 (trapezoid) or 3 (Simpson)                 */
+    int n_nodes;        /* M: temporal nodes including node 0 at t^n       */
     int n_iters;        /* K: SDC iterations per step                      */
     double newton_rtol; /* scaled update norm that ends the Newton loop    */
     int newton_maxit;
+    int node_type;      /* ORC_NODES_LOBATTO (M = 2: trapezoid, 3: Simpson)  */
+                        /* or ORC_NODES_RADAU (M = 2..4: Radau IIA points)   */
 } orc_problem;
+
+#define ORC_NODES_LOBATTO 0
+#define ORC_NODES_RADAU 1
 
 typedef struct {
     long long newton_iters_total;
@@ -73,9 +78,10 @@ typedef struct {
 int orc_nvar(const orc_problem* P);
 
 /* node positions in [0,1] and node-to-node weights q[m*M + l] (units of dt),
-   q_{m,l} = int_{tau_m}^{tau_{m+1}} L_l(tau) dtau.  Returns 0 or -1 for bad M. */
-int orc_nodes(int M, double* tau);
-int orc_quad_weights(int M, double* q);
+   q_{m,l} = int_{tau_m}^{tau_{m+1}} L_l(tau) dtau (L_l through the interpolation
+   nodes of the node type).  Returns 0 or -1 for a bad type or M. */
+int orc_nodes(int type, int M, double* tau);
+int orc_quad_weights(int type, int M, double* q);
 
 /* ideal-gas helpers at one zone (conserved in, primitive out) */
 double orc_temperature(const orc_problem* P, double rho, const double* mom, double rhoE);

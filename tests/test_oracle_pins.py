@@ -51,10 +51,34 @@ def test_quadrature_exact_on_polynomials(M):
         assert q.sum(0) == pytest.approx([1 / 6, 2 / 3, 1 / 6], abs=1e-15)
 
 
+@pytest.mark.parametrize("s", [1, 2, 3])
+def test_radau_nodes_are_radau_polynomial_zeros(s):
+    """Radau nodes: 0, then the zeros of P_s(2t-1) - P_{s-1}(2t-1) on (0, 1]."""
+    from numpy.polynomial import legendre as Lg
+    c = np.zeros(s + 1)
+    c[s] = 1.0
+    c[s - 1] = -1.0
+    roots = np.sort(np.real(Lg.legroots(c)))
+    t = (roots + 1.0) / 2.0
+    tau = O.nodes(s + 1, "radau")
+    assert tau[0] == 0.0
+    assert tau[1:] == pytest.approx(t, abs=1e-14)
+
+
+def test_radau_weights_match_radau_iia_tableau():
+    """Cumulative Radau node-to-node weights are the Radau IIA coefficients
+    (tests/golden/radau_iia_tableau.txt, Hairer & Wanner section IV.5)."""
+    r6 = math.sqrt(6.0)
+    for s, j, l, p, q, d in _read_golden("radau_iia_tableau.txt"):
+        w = O.quad_weights(s + 1, "radau")
+        assert np.all(w[:, 0] == 0.0)
+        assert w[:j, l].sum() == pytest.approx((p + q * r6) / d, abs=1e-14)
+
+
 # ---------------------------------------------------------------- helpers
-def uniform_1d(net, nx=4, rho=1.0, u=0.0, T=1.0, X=None, M=2, K=2, gamma=5.0 / 3.0, limiter=1):
+def uniform_1d(net, nx=4, rho=1.0, u=0.0, T=1.0, X=None, M=2, K=2, gamma=5.0 / 3.0, limiter=1, nodes="lobatto"):
     P = W.Problem(dim=1, n=(nx, 1, 1), dx=(1.0 / nx, 1.0, 1.0), gamma=gamma, net=net,
-                  n_nodes=M, n_iters=K, limiter=limiter)
+                  n_nodes=M, n_iters=K, limiter=limiter, nodes=nodes)
     X = X if X is not None else [1.0] + [0.0] * (net.nspec - 1)
     ones = np.ones(nx)
     U = W.conserved_from(gamma, rho * ones, [u * ones], T * ones, [x * ones for x in X])
@@ -163,6 +187,42 @@ def test_amplification_factor_closed_forms(row):
     assert np.array_equal(U1[2], U[2])
 
 
+@pytest.mark.parametrize("row", _read_golden("radau_amplification.txt"))
+def test_radau_amplification_factor_closed_forms(row):
+    """Radau nodes on y' = -k y (A -> B, Q = 0, no flow): the hand-derived g(z)
+    for K = 1, 2 and the Radau IIA stability function as K -> inf."""
+    M, K, num, den = row
+    net = W.decay_network(Q=0.0)
+    T = 1.0
+    k = 1e3 * math.exp(-10.0 / T)
+    P, U = uniform_1d(net, T=T, M=M, K=(K if K > 0 else 60), nodes="radau")
+    P.newton_rtol = 1e-14
+    o = O.Oracle(P)
+    U1, _ = o.step(U, 0.1 / k)
+    g = U1[3, 0, 0, :] / U[3, 0, 0, :]
+    assert np.all(np.abs(g - num / den) <= 2e-15)
+    assert np.allclose(U1[3] + U1[4], U[0], rtol=0, atol=1e-15)
+
+
+def test_radau_sweep_damps_stiff_modes():
+    """With Radau nodes one sweep gives g = 1/((1 - z/3)(1 - 2z/3)) -> 0 as z -> -inf
+    (L-stable, like its Radau IIA limit); the Gauss-Lobatto sweep's limit, Lobatto
+    IIIA (1 + z/2 + z^2/12)/(1 - z/2 + z^2/12), tends to 1 instead."""
+    net = W.decay_network(Q=0.0)
+    k = 1e3 * math.exp(-10.0)
+    for z in [-10.0, -1e3, -1e6]:
+        P, U = uniform_1d(net, T=1.0, M=3, K=1, nodes="radau")
+        U1, _ = O.Oracle(P).step(U, -z / k)
+        assert U1[3, 0, 0, 0] / U[3, 0, 0, 0] == pytest.approx(1 / ((1 - z / 3) * (1 - 2 * z / 3)), rel=1e-12)
+    P, U = uniform_1d(net, T=1.0, M=3, K=60)
+    P.newton_rtol = 1e-14
+    z = -1e3
+    U1, _ = O.Oracle(P).step(U, -z / k)
+    lobatto = (1 + z / 2 + z * z / 12) / (1 - z / 2 + z * z / 12)
+    assert U1[3, 0, 0, 0] / U[3, 0, 0, 0] == pytest.approx(lobatto, rel=1e-10)
+    assert lobatto > 0.98
+
+
 def test_sweep_is_backward_euler_limit_for_stiff_decay():
     """K=1, M=2 is backward Euler: for z -> -inf the factor tends to 0 like 1/(1-z)."""
     net = W.decay_network(Q=0.0)
@@ -184,13 +244,17 @@ def _run_to(P, U, t_final, nsteps):
     return V
 
 
-@pytest.mark.parametrize("M,K,order", [(2, 1, 1), (2, 2, 2), (3, 1, 1), (3, 2, 2), (3, 3, 3), (3, 4, 4)])
-def test_order_decay_with_heating(M, K, order):
+@pytest.mark.parametrize("M,K,order,nodes", [(2, 1, 1, "lobatto"), (2, 2, 2, "lobatto"), (3, 1, 1, "lobatto"),
+                                              (3, 2, 2, "lobatto"), (3, 3, 3, "lobatto"), (3, 4, 4, "lobatto"),
+                                              (2, 2, 1, "radau"), (3, 1, 1, "radau"), (3, 2, 2, "radau"),
+                                              (3, 4, 3, "radau"), (4, 4, 4, "radau"), (4, 6, 5, "radau")])
+def test_order_decay_with_heating(M, K, order, nodes):
     """Section 2: each iteration raises the order by one up to the order of the
-    integral (2 with the trapezoid, 4 with Simpson).  Spatially uniform state,
-    so A = 0 exactly; the T-dependent A -> B with Q = 1 is nonlinear."""
+    integral (2 with the trapezoid, 4 with Simpson; with Radau nodes the order of
+    Radau IIA collocation, 2(M-1) - 1).  Spatially uniform state, so A = 0
+    exactly; the T-dependent A -> B with Q = 1 is nonlinear."""
     net = W.decay_network(Q=1.0)
-    P, U = uniform_1d(net, T=2.0, M=M, K=K)
+    P, U = uniform_1d(net, T=2.0, M=M, K=K, nodes=nodes)
     P.newton_rtol = 1e-14
     ref = _run_to(P, U, 0.3, 2048)
     errs = []
