@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--config", choices=["box64", "box256", "batch200"], default="box64")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--prec", choices=["fp64", "fp32jac"], default="fp64")
+    p.add_argument("--nodes", choices=["lobatto", "radau"], default="lobatto",
+                   help="temporal node set: Gauss-Lobatto (trapezoid/Simpson) or node 0 + Radau IIA points")
     p.add_argument("--seed", type=int, default=None,
                    help="network / box seed (default: 1 for the single boxes, 3 for the batch)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -63,7 +65,7 @@ def parse():
     return p.parse_args()
 
 
-def workload(name, seed):
+def workload(name, seed, nodes="lobatto"):
     """(problems, initial state, description): a Problem and its U, or for the
     batched workload a list of Problems and the concatenated U."""
     if name == "batch200":
@@ -73,7 +75,9 @@ def workload(name, seed):
         U = np.concatenate([b[1].reshape(b[0].nvar, -1) for b in boxes], axis=1)
         desc = ("200 ragged periodic boxes (edges from {16,24,32,48,64} per axis, dx=1/64), 7-species alpha chain "
                 "(seeded), hot spots 1.2-3x over T0=0.5, 3 Gauss-Lobatto nodes, 3 SDC iterations, CFL 0.5")
-        return Ps, U, desc
+        for p in Ps:
+            p.nodes = nodes
+        return Ps, U, _nodes_desc(desc, nodes)
     if name == "box64":
         P, U = W.config_box(n=64, nspec=7, n_nodes=3, n_iters=3, seed=seed, T0=0.5)
         desc = ("64^3 periodic box, 7-species alpha chain (seeded), hot spot 2x over T0=0.5, "
@@ -82,7 +86,15 @@ def workload(name, seed):
         P, U = W.config_box(n=256, nspec=13, n_nodes=3, n_iters=4, seed=seed, T0=0.5)
         desc = ("256^3 periodic box, 13-species alpha chain (seeded), hot spot 2x over T0=0.5, "
                 "3 Gauss-Lobatto nodes, 4 SDC iterations, CFL 0.5")
-    return P, U, desc
+    P.nodes = nodes
+    return P, U, _nodes_desc(desc, nodes)
+
+
+def _nodes_desc(desc, nodes):
+    if nodes == "lobatto":
+        return desc
+    return desc.replace("3 Gauss-Lobatto nodes", "3 nodes (0 and the Radau IIA points 1/3, 1; the integral through the "
+                        "Radau points)")
 
 
 def units_per_step(P):
@@ -213,10 +225,11 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle as O
-    P, U, desc = workload(args.config, args.seed)
+    P, U, desc = workload(args.config, args.seed, args.nodes)
     if args.config == "box256":
         # bounded sample: a 64^3 box with the same network and parameters
         P, U = W.config_box(n=64, nspec=13, n_nodes=3, n_iters=4, seed=args.seed, T0=0.5)
+        P.nodes = args.nodes
         desc += " (sample: 64^3 box, same network)"
     if isinstance(P, list):
         # bounded sample: the first 8 boxes of the batch, each its own oracle step
@@ -268,6 +281,7 @@ def cpu_baseline_sampled(P, U, dt, gpu_out, seed, target_s=10.0, max_steps=3):
     import numpy as np
     import oracle as O
     Pc, Uc = W.config_box(n=64, nspec=P.net.nspec, n_nodes=P.n_nodes, n_iters=P.n_iters, seed=seed, T0=0.5)
+    Pc.nodes = P.nodes
     oc = O.Oracle(Pc)
     dtc = oc.cfl_dt(Uc)
     t0 = time.perf_counter()
@@ -376,7 +390,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if not os.path.exists(sdc.LIB_PATH):
         B.build()
-    P, U, desc = workload(args.config, rank_seed(args.seed, rank))
+    P, U, desc = workload(args.config, rank_seed(args.seed, rank), args.nodes)
     P0 = as_list(P)[0]
     prec = sdc.PREC_FP64 if args.prec == "fp64" else sdc.PREC_FP32_JAC
     ctx = sdc.Context(P, prec=prec)
@@ -524,7 +538,8 @@ def run_ours(args):
             "dtype": "f64" if prec == sdc.PREC_FP64 else "f64 residual/update, f32 Jacobian/LU",
             "data": "synthetic",
             "config": {"workload": desc, "zones": nzones(P), "nspec": P0.net.nspec, "nodes": P0.n_nodes,
-                       "iters": P0.n_iters, "prec": args.prec, "seed": args.seed, "kernel_variants": tuning,
+                       "iters": P0.n_iters, "nodes": args.nodes, "prec": args.prec, "seed": args.seed,
+                       "kernel_variants": tuning,
                        "l2": "flushed before every timed step (256 MB write)",
                        "parallelism": "independent box per GPU" if ws > 1 else "1 GPU"},
             "clocks": ck,

@@ -89,13 +89,25 @@ typedef struct {
 
 typedef struct {
     double gamma;          /* gamma-law gas, p = rho T                      */
-    int n_nodes;           /* M: 2 (trapezoid) or 3 (Simpson)               */
+    int n_nodes;           /* M: temporal nodes including node 0 (2 or 3)   */
     int n_iters;           /* K: SDC iterations per step, >= 1              */
     int limiter;           /* 1 = MC limited PLM, 0 = unlimited centred PLM */
     sdc_precision prec;    /* Newton linear algebra precision               */
     double newton_rtol;    /* scaled Newton update that ends the solve      */
     int newton_maxit;      /* iteration cap per zone solve                  */
+    int node_type;         /* SDC_NODES_LOBATTO or SDC_NODES_RADAU          */
 } sdc_params;
+
+/* Temporal node sets of the SDC step (n_nodes = M):
+   SDC_NODES_LOBATTO: Gauss-Lobatto nodes {0,1} or {0,1/2,1}; the integral of
+     Eq. sdc:general by the trapezoid (M = 2) or Simpson's (M = 3) rule through
+     all nodes (section 2).
+   SDC_NODES_RADAU: node 0 at t^n and the M-1 right-endpoint Gauss-Radau points
+     ({1} or {1/3, 1}); the integral through those points only, so that the
+     iteration converges to Radau IIA collocation, which is L-stable: an
+     instance of the alternative quadratures for very stiff burning that the
+     paper's closing section (Future Developments) names as work in progress. */
+enum { SDC_NODES_LOBATTO = 0, SDC_NODES_RADAU = 1 };
 
 typedef struct {
     long long newton_iters_total; /* sum over zone solves of the iterations   */

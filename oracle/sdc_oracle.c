@@ -35,7 +35,8 @@ static long long nzones(const orc_problem* P) {
 /* integral of Eq. sdc:general, trapezoid / Simpson rule).            */
 /* Gauss-Lobatto nodes on [0,1]: M=2 -> {0,1}, M=3 -> {0,1/2,1}; the   */
 /* quadrature interpolates through all M nodes.                       */
-/* Radau (section 4: other quadratures for highly stiff reactions):   */
+/* Radau (section 5, Future Developments: other quadratures for very  */
+/* stiff burning):                                                     */
 /* node 0 at t^n and the s = M-1 right-endpoint Gauss-Radau points,   */
 /* the zeros of P_s(2t-1) - P_{s-1}(2t-1) (P Legendre): s=1 -> {1},   */
 /* s=2 -> {1/3, 1}, s=3 -> {(4-sqrt6)/10, (4+sqrt6)/10, 1}; the        */

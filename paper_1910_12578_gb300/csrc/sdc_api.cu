@@ -214,12 +214,30 @@ bool is_alpha_chain(const sdc_network* net) {
     return true;
 }
 
-void weights(int M, double tau[3], double q[2][3]) {
-    // integrals of the Lagrange basis through the Gauss-Lobatto nodes over
-    // each sub-interval, in units of the step: trapezoid / Simpson halves
+// Node positions (units of the step) and node-to-node weights q[m][l] of the
+// integral in Eq. sdc:general.  Gauss-Lobatto: the Lagrange interpolant through
+// all nodes integrated node to node (trapezoid; Simpson in two halves).
+// Radau: node 0 plus the right-endpoint Gauss-Radau points, the interpolant
+// through those points only (weight 0 for node 0): the Radau IIA coefficients
+// as differences a_{m+1,l} - a_{m,l} (s = 1: a = 1; s = 2: a = [[5/12, -1/12],
+// [3/4, 1/4]]).
+void weights(int type, int M, double tau[3], double q[2][3]) {
+    for (int m = 0; m < 2; m++)
+        for (int l = 0; l < 3; l++) q[m][l] = 0.0;
+    if (type == SDC_NODES_RADAU) {
+        if (M == 2) {
+            tau[0] = 0.0; tau[1] = 1.0; tau[2] = 1.0;
+            q[0][1] = 1.0;
+        } else {
+            tau[0] = 0.0; tau[1] = 1.0 / 3.0; tau[2] = 1.0;
+            q[0][1] = 5.0 / 12.0; q[0][2] = -1.0 / 12.0;
+            q[1][1] = 1.0 / 3.0; q[1][2] = 1.0 / 3.0;
+        }
+        return;
+    }
     if (M == 2) {
-        tau[0] = 0.0; tau[1] = 1.0;
-        q[0][0] = 0.5; q[0][1] = 0.5; q[0][2] = 0.0;
+        tau[0] = 0.0; tau[1] = 1.0; tau[2] = 1.0;
+        q[0][0] = 0.5; q[0][1] = 0.5;
     } else {
         tau[0] = 0.0; tau[1] = 0.5; tau[2] = 1.0;
         q[0][0] = 5.0 / 24.0; q[0][1] = 1.0 / 3.0; q[0][2] = -1.0 / 24.0;
@@ -429,7 +447,8 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     }
     if (!(prm->gamma > 1.0) || (prm->n_nodes != 2 && prm->n_nodes != 3) || prm->n_iters < 1 ||
         prm->newton_maxit < 1 || !(prm->newton_rtol > 0.0) ||
-        (prm->prec != SDC_PREC_FP64 && prm->prec != SDC_PREC_FP32_JAC))
+        (prm->prec != SDC_PREC_FP64 && prm->prec != SDC_PREC_FP32_JAC) ||
+        (prm->node_type != SDC_NODES_LOBATTO && prm->node_type != SDC_NODES_RADAU))
         return SDC_ERR_INVALID_ARG;
     const int topo = is_alpha_chain(net) ? TOPO_CHAIN : TOPO_GENERIC;
     int topo_used = topo;
@@ -457,7 +476,7 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     c->prec = prm->prec;
     c->cfg.rtol = prm->newton_rtol;
     c->cfg.maxit = prm->newton_maxit;
-    weights(c->M, c->tau, c->q);
+    weights(prm->node_type, c->M, c->tau, c->q);
     NetParams& P = c->P;
     memset(&P, 0, sizeof(P));
     P.nspec = net->nspec;
@@ -934,7 +953,8 @@ extern "C" sdc_status sdc_step_static(const sdc_box* boxes, int nbox, const sdc_
     }
     if (!(prm->gamma > 1.0) || (prm->n_nodes != 2 && prm->n_nodes != 3) || prm->n_iters < 1 ||
         prm->newton_maxit < 1 || !(prm->newton_rtol > 0.0) ||
-        (prm->prec != SDC_PREC_FP64 && prm->prec != SDC_PREC_FP32_JAC))
+        (prm->prec != SDC_PREC_FP64 && prm->prec != SDC_PREC_FP32_JAC) ||
+        (prm->node_type != SDC_NODES_LOBATTO && prm->node_type != SDC_NODES_RADAU))
         return SDC_ERR_INVALID_ARG;
     int topo = is_alpha_chain(net) ? TOPO_CHAIN : TOPO_GENERIC;
     if (!newton_supported(net->nspec, topo)) {
@@ -1005,7 +1025,7 @@ extern "C" sdc_status sdc_step_static(const sdc_box* boxes, int nbox, const sdc_
     c.prec = prm->prec;
     c.cfg.rtol = prm->newton_rtol;
     c.cfg.maxit = prm->newton_maxit;
-    weights(M, c.tau, c.q);
+    weights(prm->node_type, M, c.tau, c.q);
     NetParams& P = c.P;
     memset(&P, 0, sizeof(P));
     P.nspec = net->nspec;

@@ -56,10 +56,11 @@ def torch_cuda():
 
 
 # ------------------------------------------------------------------ inputs
-def hot_spot_problem(n, limiter):
+def hot_spot_problem(n, limiter, nodes="lobatto"):
     P, U = W.config_box(n=n, nspec=7, n_iters=3, seed=1, T0=0.5)
     P = copy.deepcopy(P)
     P.limiter = limiter
+    P.nodes = nodes
     return P, U
 
 
@@ -294,11 +295,12 @@ def rate_errors(ga, d_rel, J, d_yield):
     return err_rel, err_y
 
 
-@pytest.mark.parametrize("n,nsteps,limiter", [(8, 2, 1), (32, 5, 1), (8, 2, 0), (32, 5, 0)])
-def test_rate_gradient_hot_spot(torch_cuda, n, nsteps, limiter):
+@pytest.mark.parametrize("n,nsteps,limiter,nodes", [(8, 2, 1, "lobatto"), (32, 5, 1, "lobatto"), (8, 2, 0, "lobatto"),
+                                                    (32, 5, 0, "lobatto"), (8, 2, 1, "radau")])
+def test_rate_gradient_hot_spot(torch_cuda, n, nsteps, limiter, nodes):
     """dL/da_j of the released energy and of the product yields against GPU
-    finite differences."""
-    P, U = hot_spot_problem(n, limiter)
+    finite differences (Gauss-Lobatto and Radau node sets)."""
+    P, U = hot_spot_problem(n, limiter, nodes)
     dt = O.Oracle(P).cfl_dt(U)
     model = GpuModel(torch_cuda, P, nsteps, dt)
     U0 = state_from_T(P, base_T(P))

@@ -44,6 +44,22 @@ def problems():
     out["ragged"] = (P, W.hot_spot_state(P, 2.0, T0=0.5))
     P, U = W.config_box(n=16, nspec=13, n_iters=4, seed=0, T0=0.5)
     out["box16_13"] = (P, U)
+    # Radau node set (node 0 + Radau IIA points; quadrature through those points)
+    # (cfg 1 doubles a 1e-14 perturbation about every step under any node set;
+    # Radau with M = 2, K = 2 grows it ~2800x over 10 steps, so the 10-step 1D
+    # case uses M = 3, K = 3 and M = 2 is covered on 16^3 over 2 steps)
+    P, U = W.config_1d()
+    P.nodes, P.n_nodes, P.n_iters = "radau", 3, 3
+    out["1d_radau"] = (P, U)
+    P, U = W.config_box(n=16, nspec=7, seed=0, T0=0.5)
+    P.nodes = "radau"
+    out["box16_radau"] = (P, U)
+    P, U = W.config_box(n=16, nspec=7, n_nodes=2, n_iters=2, seed=0, T0=0.5)
+    P.nodes = "radau"
+    out["box16_radau2"] = (P, U)
+    P, U = W.config_box(n=16, nspec=13, n_iters=4, seed=0, T0=0.5)
+    P.nodes = "radau"
+    out["box16_13_radau"] = (P, U)
     return out
 
 
@@ -150,7 +166,9 @@ def test_react_newton_parity(torch_cuda, name, k_iters, prec):
 
 
 @pytest.mark.parametrize("name,nsteps,prec", [("1d", 10, 0), ("box16", 2, 0), ("box16", 1, 1), ("ragged", 1, 0),
-                                              ("box16_13", 1, 0), ("box16_13", 1, 1)])
+                                              ("box16_13", 1, 0), ("box16_13", 1, 1),
+                                              ("1d_radau", 10, 0), ("box16_radau", 2, 0), ("box16_radau", 1, 1),
+                                              ("box16_radau2", 2, 0), ("box16_13_radau", 1, 0)])
 def test_step_parity(torch_cuda, name, nsteps, prec):
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
