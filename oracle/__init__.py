@@ -40,6 +40,7 @@ class _Problem(C.Structure):
         ("Q", C.c_double * MAX_REAC), ("reac", (C.c_int * 2) * MAX_REAC), ("cnt", (C.c_int * 2) * MAX_REAC),
         ("prod", C.c_int * MAX_REAC), ("n_nodes", C.c_int), ("n_iters", C.c_int),
         ("newton_rtol", C.c_double), ("newton_maxit", C.c_int), ("node_type", C.c_int),
+        ("split_op", C.c_int),
     ]
 
 
@@ -74,6 +75,7 @@ def lib():
         _lib.orc_react_newton.argtypes = [pp, dp, C.c_double, dp, dp, ip, ip, C.POINTER(_Stats)]
         _lib.orc_node_integral.argtypes = [pp, C.POINTER(dp), C.POINTER(dp), C.c_double, C.c_int, dp]
         _lib.orc_sdc_step.argtypes = [pp, dp, C.c_double, C.POINTER(_Stats)]
+        _lib.orc_strang_step.argtypes = [pp, dp, C.c_double, C.POINTER(_Stats)]
         _lib.orc_sdc_step_nodes.argtypes = [pp, dp, C.c_double, C.POINTER(_Stats), dp]
         _lib.orc_cfl_dt.argtypes = [pp, dp, C.c_double]
         _lib.orc_cfl_dt.restype = C.c_double
@@ -115,6 +117,7 @@ class Oracle:
         s.n_nodes, s.n_iters = P.n_nodes, P.n_iters
         s.newton_rtol, s.newton_maxit = P.newton_rtol, P.newton_maxit
         s.node_type = NODE_TYPES[P.nodes]
+        s.split_op = 0
         self.s = s
         self.L = lib()
         self.nvar = P.nvar
@@ -197,6 +200,15 @@ class Oracle:
             assert rc == 0
             return U, st, out
         rc = self.L.orc_sdc_step(C.byref(self.s), _dp(U), float(dt), C.byref(st))
+        assert rc == 0
+        return U, st
+
+    def strang_step(self, U, dt):
+        """Strang-split baseline: reactions dt/2, advection dt, reactions dt/2,
+        each by this problem's SDC step with the other operator off."""
+        U = np.array(self._flat(U), copy=True)
+        st = _Stats()
+        rc = self.L.orc_strang_step(C.byref(self.s), _dp(U), float(dt), C.byref(st))
         assert rc == 0
         return U, st
 

@@ -602,6 +602,34 @@ void orc_node_integral(const orc_problem* P, const double* const* A_nodes,
 /*   A at the last node is evaluated for the next iteration's integral. */
 /*   U^{n+1} = U^{M-1,(K)}.                                             */
 /* ------------------------------------------------------------------ */
+/* the operators of one sub-problem: A = 0 when only reactions run, R = 0
+   (and the implicit update w = rhs) when only advection runs */
+static void step_advective(const orc_problem* P, const double* U, double* A) {
+    if (P->split_op == ORC_OP_REACT) {
+        memset(A, 0, sizeof(double) * orc_nvar(P) * nzones(P));
+        return;
+    }
+    orc_advective(P, U, A);
+}
+
+static void step_source(const orc_problem* P, const double* U, double* R) {
+    if (P->split_op == ORC_OP_ADVECT) {
+        memset(R, 0, sizeof(double) * (P->nspec + 1) * nzones(P));
+        return;
+    }
+    orc_reaction_source(P, U, R);
+}
+
+static void step_implicit(const orc_problem* P, const double* rhs, double dtm, double* U, double* R,
+                          orc_stats* st) {
+    if (P->split_op == ORC_OP_ADVECT) {
+        memcpy(U, rhs, sizeof(double) * orc_nvar(P) * nzones(P));
+        memset(R, 0, sizeof(double) * (P->nspec + 1) * nzones(P));
+        return;
+    }
+    orc_react_newton(P, rhs, dtm, U, R, NULL, NULL, st);
+}
+
 int orc_sdc_step_nodes(const orc_problem* P, double* U, double dt, orc_stats* st, double* nodes_out) {
     int M = P->n_nodes, K = P->n_iters, dim = P->dim, nv = orc_nvar(P), n = P->nspec + 1;
     long long N = nzones(P);
@@ -621,8 +649,8 @@ int orc_sdc_step_nodes(const orc_problem* P, double* U, double dt, orc_stats* st
 
     /* iterate 0 */
     for (int m = 0; m < M; m++) memcpy(Un[m], U, sz_u);
-    orc_advective(P, U, Aold[0]);
-    orc_reaction_source(P, U, Rold[0]);
+    step_advective(P, U, Aold[0]);
+    step_source(P, U, Rold[0]);
     for (int m = 1; m < M; m++) {
         memcpy(Aold[m], Aold[0], sz_u);
         memcpy(Rold[m], Rold[0], sz_r);
@@ -634,7 +662,7 @@ int orc_sdc_step_nodes(const orc_problem* P, double* U, double dt, orc_stats* st
         memcpy(Rnew[0], Rold[0], sz_r);
         for (int m = 0; m < M - 1; m++) {
             double dtm = dt * (tau[m + 1] - tau[m]);
-            if (m > 0) orc_advective(P, Un[m], Anew[m]);
+            if (m > 0) step_advective(P, Un[m], Anew[m]);
             orc_node_integral(P, (const double* const*)Aold, (const double* const*)Rold, dt, m, I);
             for (int f = 0; f < nv; f++)
                 for (long long z = 0; z < N; z++) {
@@ -643,9 +671,9 @@ int orc_sdc_step_nodes(const orc_problem* P, double* U, double dt, orc_stats* st
                     rhs[f * N + z] = v + I[f * N + z];
                 }
             /* Un[m+1] holds U^{m+1,(k)} (the guess) and receives U^{m+1,(k+1)} */
-            orc_react_newton(P, rhs, dtm, Un[m + 1], Rnew[m + 1], NULL, NULL, st);
+            step_implicit(P, rhs, dtm, Un[m + 1], Rnew[m + 1], st);
         }
-        if (k < K - 1) orc_advective(P, Un[M - 1], Anew[M - 1]);
+        if (k < K - 1) step_advective(P, Un[M - 1], Anew[M - 1]);
         for (int m = 0; m < M; m++) {
             double* t = Aold[m]; Aold[m] = Anew[m]; Anew[m] = t;
             t = Rold[m]; Rold[m] = Rnew[m]; Rnew[m] = t;
@@ -664,6 +692,15 @@ int orc_sdc_step_nodes(const orc_problem* P, double* U, double dt, orc_stats* st
 
 int orc_sdc_step(const orc_problem* P, double* U, double dt, orc_stats* st) {
     return orc_sdc_step_nodes(P, U, dt, st, NULL);
+}
+
+int orc_strang_step(const orc_problem* P, double* U, double dt, orc_stats* st) {
+    orc_problem Pr = *P, Pa = *P;
+    Pr.split_op = ORC_OP_REACT;
+    Pa.split_op = ORC_OP_ADVECT;
+    if (orc_sdc_step(&Pr, U, 0.5 * dt, st) != 0) return -1;
+    if (orc_sdc_step(&Pa, U, dt, st) != 0) return -1;
+    return orc_sdc_step(&Pr, U, 0.5 * dt, st);
 }
 
 double orc_cfl_dt(const orc_problem* P, const double* U, double cfl) {

@@ -62,7 +62,14 @@ typedef struct {
     int newton_maxit;
     int node_type;      /* ORC_NODES_LOBATTO (M = 2: trapezoid, 3: Simpson)  */
                         /* or ORC_NODES_RADAU (M = 2..4: Radau IIA points)   */
+    int split_op;       /* ORC_OP_BOTH (the coupled SDC step), ORC_OP_ADVECT  */
+                        /* (R = 0) or ORC_OP_REACT (A = 0): the sub-problems  */
+                        /* of the Strang-split baseline                       */
 } orc_problem;
+
+#define ORC_OP_BOTH 0
+#define ORC_OP_ADVECT 1
+#define ORC_OP_REACT 2
 
 #define ORC_NODES_LOBATTO 0
 #define ORC_NODES_RADAU 1
@@ -117,6 +124,12 @@ void orc_node_integral(const orc_problem* P, const double* const* A_nodes,
 
 /* one SDC time step of size dt, in place on U (nvar*N) */
 int orc_sdc_step(const orc_problem* P, double* U, double dt, orc_stats* st);
+
+/* Strang-split baseline (section 2 contrasts SDC with operator splitting,
+   whose coupling error SDC removes): reactions over dt/2, advection over dt,
+   reactions over dt/2, each sub-problem integrated by the SDC step of P with
+   the other operator set to zero.  Returns 0 or -1. */
+int orc_strang_step(const orc_problem* P, double* U, double dt, orc_stats* st);
 
 /* dt = cfl / max_zones sum_d (|u_d| + c) / dx_d */
 double orc_cfl_dt(const orc_problem* P, const double* U, double cfl);

@@ -342,6 +342,95 @@ def test_newton_reports_status():
 
 
 # ---------------------------------------------------------------- conservation / symmetry
+# ---------------------------------------------------------------- Strang-split baseline
+def test_strang_without_flow_is_two_reaction_half_steps():
+    """A uniform state at rest has A = 0 exactly, so the Strang step is two
+    reaction half steps of the sweep: g(z/2)^2 with the sweep's hand-derived
+    g(z) (A -> B with Q = 0 at fixed T, z = -k dt)."""
+    forms = {(2, 1): lambda z: 1 / (1 - z),
+             (2, 2): lambda z: (1 - z - z * z / 2) / (1 - z) ** 2,
+             (3, 1): lambda z: 1 / (1 - z / 2) ** 2}
+    net = W.decay_network(Q=0.0)
+    k = 1e3 * math.exp(-10.0)
+    z = -0.1
+    for (M, K), g in forms.items():
+        P, U = uniform_1d(net, T=1.0, M=M, K=K)
+        P.newton_rtol = 1e-14
+        U1, _ = O.Oracle(P).strang_step(U, -z / k)
+        assert np.all(np.abs(U1[3, 0, 0, :] / U[3, 0, 0, :] - g(z / 2) ** 2) <= 2e-15)
+
+
+def test_strang_without_reactions_is_the_coupled_step():
+    """All rates zero: the reaction half steps leave U unchanged and the Strang
+    step reduces to the advection step, the coupled step with R = 0."""
+    P, U, _ = _translation_problem(64)
+    o = O.Oracle(P)
+    dt = o.cfl_dt(U)
+    V1, _ = o.strang_step(U, dt)
+    V2, _ = o.step(U, dt)
+    assert np.abs(V1 - V2).max() <= 1e-15 * np.abs(V2).max()
+
+
+def _coupled_1d(M, K, nodes="lobatto"):
+    """Flow and burning in one problem: config 1 with k0 = 1e4 (14% of the fuel
+    burns in t = 0.05), centred slopes (smooth in U)."""
+    P, U = W.config_1d(64)
+    P.net = W.decay_network(k0=1e4)
+    P.limiter, P.n_nodes, P.n_iters, P.nodes = 0, M, K, nodes
+    P.newton_rtol = 1e-14
+    return P, U
+
+
+def test_strang_is_second_order_and_sdc_removes_its_coupling_error():
+    """Section 2: operator splitting leaves a coupling error that the SDC update
+    removes.  Same sub-integrators (the M = 3, K = 3 sweep with one operator
+    off), t = 0.05 in 16, 32, 64 steps, against the coupled M = 3, K = 4 sweep in
+    512 steps: Strang converges at second order, the coupled step at third, and
+    its error is an order of magnitude smaller at every step size."""
+    tf = 0.05
+    Pr, U = _coupled_1d(3, 4)
+    ref = _run_to(Pr, U, tf, 512)
+    P, _ = _coupled_1d(3, 3)
+    o = O.Oracle(P)
+    es, ec = [], []
+    for n in (16, 32, 64):
+        V = U.copy()
+        for _ in range(n):
+            V, _ = o.strang_step(V, tf / n)
+        es.append(np.abs(V - ref).max())
+        ec.append(np.abs(_run_to(P, U, tf, n) - ref).max())
+    rs = [math.log2(es[i] / es[i + 1]) for i in range(2)]
+    rc = [math.log2(ec[i] / ec[i + 1]) for i in range(2)]
+    assert rs[-1] == pytest.approx(2.0, abs=0.3), (es, rs)
+    assert rc[-1] == pytest.approx(3.0, abs=0.35), (ec, rc)
+    assert all(c < s / 10 for c, s in zip(ec, es)), (ec, es)
+
+
+def test_strang_conserves():
+    """Each sub-step conserves, so the split step keeps mass, sum X and the total
+    energy including binding energy (12^3 burning box)."""
+    P, U = W.config_box(n=12, nspec=7, seed=0, T0=0.5, amp=2.0)
+    o = O.Oracle(P)
+    b = P.net.binding()
+    mass = np.asarray(P.net.mass)
+
+    def totals(V):
+        rho = V[0]
+        Y = V[5:] / mass[:, None, None, None] / rho
+        return V[0].sum(), (V[4] - rho * np.tensordot(b, Y, axes=1)).sum()
+
+    m0, e0 = totals(U)
+    V = U.copy()
+    for _ in range(3):
+        V, st = o.strang_step(V, o.cfl_dt(V))
+        assert st.n_fail == 0
+    m1, e1 = totals(V)
+    assert abs(m1 - m0) <= 1e-13 * abs(m0)
+    assert abs(e1 - e0) <= 1e-12 * abs(e0)
+    assert np.abs(V[5:].sum(0) - V[0]).max() <= 1e-13
+    assert V[6].max() > 1e-3
+
+
 def test_conservation_3d_hot_spot():
     """Mass, momentum, sum X = 1 per zone and total energy including the
     binding energy released by the network are conserved to round-off."""
