@@ -214,6 +214,16 @@ sdc_status sdc_launches_per_step(const sdc_ctx* ctx, int* launches);
 sdc_status sdc_step_backward(sdc_ctx* ctx, const double* U_n, double dt, const double* gU_np1, double* gU_n,
                              double* g_a);
 
+/* Strang-split baseline step (no counterpart in the method itself: section 2
+   contrasts the SDC update with operator splitting, whose coupling error the
+   SDC update removes): reactions over dt/2, advection over dt, reactions over
+   dt/2, each sub-problem integrated by this context's SDC step (same nodes,
+   iterations, kernels and precision) with the other operator set to zero; with
+   R = 0 the implicit update is w = rhs.  U: device [nvar][Ntot], advanced in
+   place.  stats as in sdc_step (summed over the two reaction sub-steps).  The
+   three sub-steps are captured as one CUDA graph per U pointer. */
+sdc_status sdc_step_strang(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats);
+
 /* Vector-Jacobian product of the advective term A(U) of Eq. 1 (section 2: the
    divergence of the hydrodynamic fluxes):  Ubar += (dA/dU)^T Abar  at the state
    U, with the branches of the MC limiter and of HLLC those that U selects.

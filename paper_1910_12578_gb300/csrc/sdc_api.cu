@@ -161,6 +161,9 @@ struct sdc_ctx {
     std::vector<void*> allocs;
     cudaGraphExec_t gexec = nullptr;
     double* gU = nullptr;
+    cudaGraphExec_t gexec_strang = nullptr;  // the Strang-split step's graph
+    double* gU_strang = nullptr;
+    double* d_dt_half = nullptr;             // dt/2 of the split step (next to d_dt)
     // kernel variants (chosen by sdc_autotune) and the Newton work queues
     int stencil_variant = 0, newton_variant = 0;
     int persistent_blocks = 0;
@@ -245,7 +248,8 @@ void weights(int type, int M, double tau[3], double q[2][3]) {
     }
 }
 
-RhsArgs rhs_args(const sdc_ctx* c, const double* const* Aold, const double* const* Rold, int m) {
+RhsArgs rhs_args(const sdc_ctx* c, const double* const* Aold, const double* const* Rold, int m,
+                 const double* dt_dev) {
     RhsArgs ra;
     for (int l = 0; l < 3; l++) {
         ra.Aold[l] = l < c->M ? Aold[l] : nullptr;
@@ -255,59 +259,85 @@ RhsArgs rhs_args(const sdc_ctx* c, const double* const* Aold, const double* cons
     ra.Rnext = Rold[m + 1];
     ra.Aold_m = Aold[m];
     ra.rhs = c->rhs;
-    ra.dt = c->d_dt;
+    ra.dt = dt_dev;
     ra.dtm_frac = c->tau[m + 1] - c->tau[m];
     ra.M = c->M;
     return ra;
 }
 
-// Enqueue one SDC step on stream st (dt already in c->d_dt); U is node M-1.
-// With prof, every kernel launch is bracketed by events (eager profiling).
+// Operators of a step: both (the coupled SDC step), or one of them alone (the
+// sub-problems of the Strang-split step: A = 0, or R = 0 with the implicit
+// update reduced to w = rhs).
+enum { OP_BOTH = 0, OP_ADVECT = 1, OP_REACT = 2 };
+
+// Enqueue one SDC step on stream st (dt already in *dt_dev, c->d_dt by
+// default); U is node M-1.  With prof, every kernel launch is bracketed by
+// events (eager profiling).  reset_stats = false keeps accumulating the Newton
+// statistics (the sub-steps of a split step).
 cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nullptr,
-                         double* const* store = nullptr) {
+                         double* const* store = nullptr, int op = OP_BOTH, const double* dt_dev = nullptr,
+                         bool reset_stats = true) {
     const long long N = c->Ntot;
     const size_t ubytes = sizeof(double) * c->nvar * N;
+    const bool with_A = op != OP_REACT, with_R = op != OP_ADVECT;
+    if (!dt_dev) dt_dev = c->d_dt;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(c->d_stats, 0, sizeof(DevStats), st)) != cudaSuccess) return e;
+    if (reset_stats && (e = cudaMemsetAsync(c->d_stats, 0, sizeof(DevStats), st)) != cudaSuccess) return e;
     if (c->d_queue &&
         (e = cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned long long) * QUEUE_SLOTS, st)) != cudaSuccess)
         return e;
     int qslot = 0;
     double* node[3] = {c->node_ws[0], c->M == 3 ? c->node_ws[1] : U, U};
     if ((e = cudaMemcpyAsync(node[0], U, ubytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
-    RhsArgs none = rhs_args(c, (const double* const*)c->Ag[0], (const double* const*)c->Rg[0], 0);
-    SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles, c->ntiles,
-                                                 node[0], c->A0, STENCIL_A, none, st, c->stencil_variant));
-    SDC_LAUNCH(prof, CLS_OTHER, launch_reaction_source(c->P, N, c->dim, node[0], c->R0, st));
+    RhsArgs none = rhs_args(c, (const double* const*)c->Ag[0], (const double* const*)c->Rg[0], 0, dt_dev);
+    if (with_A) {
+        SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles, c->ntiles,
+                                                     node[0], c->A0, STENCIL_A, none, st, c->stencil_variant));
+    } else if ((e = cudaMemsetAsync(c->A0, 0, ubytes, st)) != cudaSuccess) {
+        return e;
+    }
+    if (with_R) {
+        SDC_LAUNCH(prof, CLS_OTHER, launch_reaction_source(c->P, N, c->dim, node[0], c->R0, st));
+    } else if ((e = cudaMemsetAsync(c->R0, 0, sizeof(double) * c->nw * N, st)) != cudaSuccess) {
+        return e;
+    }
     const double* Aold[3] = {c->A0, c->A0, c->A0};
     const double* Rold[3] = {c->R0, c->R0, c->R0};
     for (int k = 0; k < c->K; k++) {
         const int g = k & 1;
-        double* Anew[3] = {c->A0, c->Ag[g][1], c->Ag[g][2]};
-        double* Rnew[3] = {c->R0, c->Rg[g][1], c->Rg[g][2]};
+        // an operator that is off stays zero: its arrays are all the zeroed node-0 array
+        double* Anew[3] = {c->A0, with_A ? c->Ag[g][1] : c->A0, with_A ? c->Ag[g][2] : c->A0};
+        double* Rnew[3] = {c->R0, with_R ? c->Rg[g][1] : c->R0, with_R ? c->Rg[g][2] : c->R0};
         for (int m = 0; m < c->M - 1; m++) {
-            RhsArgs ra = rhs_args(c, Aold, Rold, m);
-            if (m == 0) {
+            RhsArgs ra = rhs_args(c, Aold, Rold, m, dt_dev);
+            if (m == 0 || !with_A) {
+                // no A^{m,(k+1)} - A^{m,(k)} term: node 0 is fixed, or A is off
                 SDC_LAUNCH(prof, CLS_OTHER, (rhs_node0_kernel<<<grid_for((long long)c->nvar * N, EW_BLOCK), EW_BLOCK, 0,
-                                                                 st>>>(c->nvar, c->dim, N, node[0], ra),
+                                                                 st>>>(c->nvar, c->dim, N, node[m], ra),
                                              cudaGetLastError()));
             } else {
                 SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles,
                                                              c->ntiles, node[m], Anew[m], STENCIL_A_RHS, ra, st,
                                                              c->stencil_variant));
             }
-            const double* guess = (k == 0) ? node[0] : node[m + 1];
-            unsigned long long* q = (c->d_queue && qslot < QUEUE_SLOTS) ? c->d_queue + qslot++ : nullptr;
-            SDC_LAUNCH(prof, CLS_NEWTON, launch_newton(c->P, c->cfg, c->prec, N, c->dim, c->rhs, guess, node[m + 1],
-                                                       Rnew[m + 1], c->d_dt, c->tau[m + 1] - c->tau[m], 0.0, nullptr,
-                                                       nullptr, c->d_stats, st, c->newton_variant, q,
-                                                       c->persistent_blocks));
+            if (with_R) {
+                const double* guess = (k == 0) ? node[0] : node[m + 1];
+                unsigned long long* q = (c->d_queue && qslot < QUEUE_SLOTS) ? c->d_queue + qslot++ : nullptr;
+                SDC_LAUNCH(prof, CLS_NEWTON, launch_newton(c->P, c->cfg, c->prec, N, c->dim, c->rhs, guess,
+                                                           node[m + 1], Rnew[m + 1], dt_dev,
+                                                           c->tau[m + 1] - c->tau[m], 0.0, nullptr, nullptr,
+                                                           c->d_stats, st, c->newton_variant, q,
+                                                           c->persistent_blocks));
+            } else if ((e = cudaMemcpyAsync(node[m + 1], c->rhs, ubytes, cudaMemcpyDeviceToDevice, st)) !=
+                       cudaSuccess) {
+                return e;  // R = 0: the implicit update is w = rhs
+            }
             if (store &&
                 (e = cudaMemcpyAsync(store[k * (c->M - 1) + m], node[m + 1], ubytes, cudaMemcpyDeviceToDevice, st)) !=
                     cudaSuccess)
                 return e;
         }
-        if (k < c->K - 1) {
+        if (k < c->K - 1 && with_A) {
             SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles,
                                                          c->ntiles, node[c->M - 1], Anew[c->M - 1], STENCIL_A, none,
                                                          st, c->stencil_variant));
@@ -318,6 +348,14 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
         }
     }
     return cudaSuccess;
+}
+
+// the captured graphs hold constants and variants: drop them after a change
+void drop_graphs(sdc_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->gexec_strang) cudaGraphExecDestroy(c->gexec_strang);
+    c->gexec = c->gexec_strang = nullptr;
+    c->gU = c->gU_strang = nullptr;
 }
 
 // stencil tiles of every box for tile shape `variant`
@@ -407,7 +445,7 @@ const char* sdc_status_string(sdc_status s) {
 
 void sdc_destroy(sdc_ctx* ctx) {
     if (!ctx) return;
-    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    drop_graphs(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (void* p : ctx->allocs) cudaFree(p);
     delete ctx;
@@ -535,7 +573,8 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     if ((e = ctx_alloc(c, (void**)&c->d_tiles, sizeof(TileDev) * c->tiles_capacity)) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->d_queue, sizeof(unsigned long long) * QUEUE_SLOTS)) != cudaSuccess) return fail(e);
     c->persistent_blocks = newton_group_case(net->nspec, topo_used) ? 0 : newton_persistent_blocks(P, c->prec);
-    if ((e = ctx_alloc(c, (void**)&c->d_dt, sizeof(double))) != cudaSuccess) return fail(e);
+    if ((e = ctx_alloc(c, (void**)&c->d_dt, 2 * sizeof(double))) != cudaSuccess) return fail(e);
+    c->d_dt_half = c->d_dt + 1;
     if ((e = ctx_alloc(c, (void**)&c->d_stats, sizeof(DevStats))) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->d_smax, sizeof(unsigned long long))) != cudaSuccess) return fail(e);
     const size_t ub = sizeof(double) * c->nvar * Ntot, rb = sizeof(double) * c->nw * Ntot;
@@ -628,6 +667,42 @@ sdc_status sdc_step(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats) {
     return SDC_OK;
 }
 
+sdc_status sdc_step_strang(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats) {
+    if (!ctx || !U || !(dt > 0.0)) return SDC_ERR_INVALID_ARG;
+    if (!ctx->gexec_strang || ctx->gU_strang != U) {
+        if (ctx->gexec_strang) {
+            cudaGraphExecDestroy(ctx->gexec_strang);
+            ctx->gexec_strang = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        cudaStream_t cs = ctx->cap_stream;
+        SDC_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaMemsetAsync(ctx->d_stats, 0, sizeof(DevStats), cs);
+        if (e == cudaSuccess) e = enqueue_step(ctx, U, cs, nullptr, nullptr, OP_REACT, ctx->d_dt_half, false);
+        if (e == cudaSuccess) e = enqueue_step(ctx, U, cs, nullptr, nullptr, OP_ADVECT, ctx->d_dt, false);
+        if (e == cudaSuccess) e = enqueue_step(ctx, U, cs, nullptr, nullptr, OP_REACT, ctx->d_dt_half, false);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_status(e != cudaSuccess ? e : e2);
+        }
+        e = cudaGraphInstantiate(&ctx->gexec_strang, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            ctx->gexec_strang = nullptr;
+            return cuda_status(e);
+        }
+        ctx->gU_strang = U;
+    }
+    set_scalar_kernel<<<1, 1, 0, ctx->stream>>>(ctx->d_dt, dt);
+    SDC_TRY(cudaGetLastError());
+    set_scalar_kernel<<<1, 1, 0, ctx->stream>>>(ctx->d_dt_half, 0.5 * dt);
+    SDC_TRY(cudaGetLastError());
+    SDC_TRY(cudaGraphLaunch(ctx->gexec_strang, ctx->stream));
+    if (stats) return read_stats(ctx, stats);
+    return SDC_OK;
+}
+
 sdc_status sdc_step_profile(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats, sdc_profile* prof) {
     if (!ctx || !U || !(dt > 0.0) || !prof) return SDC_ERR_INVALID_ARG;
     memset(prof, 0, sizeof(*prof));
@@ -710,11 +785,7 @@ sdc_status sdc_autotune(sdc_ctx* ctx, const double* U, double dt, sdc_tuning* ou
     t.stencil_choice = vs;
     t.newton_choice = vn;
     // the captured graph used the previous variants
-    if (ctx->gexec) {
-        cudaGraphExecDestroy(ctx->gexec);
-        ctx->gexec = nullptr;
-        ctx->gU = nullptr;
-    }
+    drop_graphs(ctx);
     if (out) *out = t;
     return SDC_OK;
 }
@@ -725,11 +796,7 @@ sdc_status sdc_set_variants(sdc_ctx* ctx, int stencil_variant, int newton_varian
         return SDC_ERR_INVALID_ARG;
     SDC_TRY(set_stencil_variant(ctx, stencil_variant));
     ctx->newton_variant = newton_variant;
-    if (ctx->gexec) {
-        cudaGraphExecDestroy(ctx->gexec);
-        ctx->gexec = nullptr;
-        ctx->gU = nullptr;
-    }
+    drop_graphs(ctx);
     return SDC_OK;
 }
 
@@ -744,11 +811,7 @@ sdc_status sdc_launches_per_step(const sdc_ctx* ctx, int* launches) {
 sdc_status sdc_set_rates(sdc_ctx* ctx, const double* a) {
     if (!ctx || !a) return SDC_ERR_INVALID_ARG;
     for (int j = 0; j < ctx->P.nreac; j++) ctx->P.a[j] = a[j];
-    if (ctx->gexec) {  // the captured graph holds the old constants
-        cudaGraphExecDestroy(ctx->gexec);
-        ctx->gexec = nullptr;
-        ctx->gU = nullptr;
-    }
+    drop_graphs(ctx);  // the captured graphs hold the old constants
     return SDC_OK;
 }
 

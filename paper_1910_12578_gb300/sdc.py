@@ -25,7 +25,7 @@ PREC_FP64, PREC_FP32_JAC = 0, 1
 EXPORTS = ["sdc_init_box", "sdc_advective_term", "sdc_node_integral", "sdc_react_newton", "sdc_step",
            "sdc_step_profile", "sdc_launches_per_step", "sdc_cfl_dt", "sdc_sizes", "sdc_destroy",
            "sdc_status_string", "sdc_step_static", "sdc_selftest_math", "sdc_autotune", "sdc_set_variants",
-           "sdc_step_backward", "sdc_set_rates", "sdc_advective_term_vjp"]
+           "sdc_step_backward", "sdc_set_rates", "sdc_advective_term_vjp", "sdc_step_strang"]
 
 
 class SdcError(RuntimeError):
@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH):
     L.sdc_step_backward.argtypes = [vp, dp, C.c_double, dp, dp, dp]
     L.sdc_set_rates.argtypes = [vp, C.POINTER(C.c_double)]
     L.sdc_advective_term_vjp.argtypes = [vp, dp, dp, dp, C.c_int]
+    L.sdc_step_strang.argtypes = [vp, dp, C.c_double, C.POINTER(Stats)]
     L.sdc_set_variants.argtypes = [vp, C.c_int, C.c_int]
     L.sdc_step_static.argtypes = [C.POINTER(Box), C.c_int, C.POINTER(Network), C.POINTER(Params), vp, dp,
                                   C.c_double, C.POINTER(Stats)]
@@ -119,7 +120,8 @@ def load(path: str = LIB_PATH):
     L.sdc_status_string.restype = C.c_char_p
     for name in ("sdc_init_box", "sdc_advective_term", "sdc_node_integral", "sdc_react_newton", "sdc_step",
                  "sdc_cfl_dt", "sdc_sizes", "sdc_step_profile", "sdc_launches_per_step", "sdc_step_static", "sdc_selftest_math", "sdc_autotune",
-                 "sdc_set_variants", "sdc_step_backward", "sdc_set_rates", "sdc_advective_term_vjp"):
+                 "sdc_set_variants", "sdc_step_backward", "sdc_set_rates", "sdc_advective_term_vjp",
+                 "sdc_step_strang"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -226,6 +228,13 @@ class Context:
         st = Stats() if stats else None
         s = self.L.sdc_step(self._h, _ptr(U), float(dt), C.byref(st) if st is not None else None)
         self._check(s, "sdc_step", allow_noconv=True)
+        return st
+
+    def step_strang(self, U, dt, stats=True):
+        """One Strang-split step (reactions dt/2, advection dt, reactions dt/2) of U in place."""
+        st = Stats() if stats else None
+        s = self.L.sdc_step_strang(self._h, _ptr(U), float(dt), C.byref(st) if st is not None else None)
+        self._check(s, "sdc_step_strang", allow_noconv=True)
         return st
 
     def step_profile(self, U, dt):

@@ -188,6 +188,37 @@ def test_step_parity(torch_cuda, name, nsteps, prec):
     assert fails == sum(s.n_fail for s in sts) or prec == 1
 
 
+@pytest.mark.parametrize("name,nsteps,prec", [("1d", 4, 0), ("box16", 2, 0), ("box16", 1, 1), ("box16_radau", 1, 0),
+                                              ("box16_13", 1, 0)])
+def test_strang_step_parity(torch_cuda, name, nsteps, prec):
+    """sdc_step_strang (reactions dt/2, advection dt, reactions dt/2 by the same
+    SDC step with one operator off) against the oracle's split step."""
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = PROBS[name]
+    o = O.Oracle(P)
+    ctx = sdc.Context(P, prec=prec)
+    V = U.copy()
+    Ud = dev(torch, U)
+    fails_o = fails_g = 0
+    for _ in range(nsteps):
+        dt = o.cfl_dt(V)
+        V, st_o = o.strang_step(V, dt)
+        st = ctx.step_strang(Ud, dt)
+        fails_o += st_o.n_fail
+        fails_g += st.n_fail
+    torch.cuda.synchronize()
+    tol = TOL64 if prec == 0 else TOL32
+    e = rel_err(Ud.cpu().numpy(), V, P.nvar, P.dim)
+    assert e.max() <= tol, e
+    assert fails_g == fails_o or prec == 1
+    # the split step really differs from the coupled one
+    Uc = dev(torch, U)
+    ctx.step(Uc, o.cfl_dt(U))
+    W1, _ = o.strang_step(U, o.cfl_dt(U))
+    assert not np.allclose(Uc.cpu().numpy(), W1.reshape(Uc.shape), rtol=1e-9, atol=0)
+
+
 def test_newton_raphson_reciprocal_and_sqrt_within_two_ulp(torch_cuda):
     """The stencil and Newton kernels replace IEEE division and sqrt by
     Newton-Raphson refinement of the hardware approximations: compare with
