@@ -40,7 +40,7 @@ class _Problem(C.Structure):
         ("Q", C.c_double * MAX_REAC), ("reac", (C.c_int * 2) * MAX_REAC), ("cnt", (C.c_int * 2) * MAX_REAC),
         ("prod", C.c_int * MAX_REAC), ("n_nodes", C.c_int), ("n_iters", C.c_int),
         ("newton_rtol", C.c_double), ("newton_maxit", C.c_int), ("node_type", C.c_int),
-        ("split_op", C.c_int),
+        ("split_op", C.c_int), ("space_order", C.c_int),
     ]
 
 
@@ -68,6 +68,10 @@ def lib():
         _lib.orc_temperature.argtypes = [pp, C.c_double, dp, C.c_double]
         _lib.orc_temperature.restype = C.c_double
         _lib.orc_advective.argtypes = [pp, dp, dp]
+        _lib.orc_advective_term.argtypes = [pp, dp, dp]
+        _lib.orc_reaction_source4.argtypes = [pp, dp, dp]
+        _lib.orc_avg_to_point.argtypes = [pp, C.c_int, dp, dp]
+        _lib.orc_point_to_avg.argtypes = [pp, C.c_int, dp, dp]
         _lib.orc_hllc.argtypes = [pp, C.c_int, dp, dp, dp]
         _lib.orc_rates.argtypes = [pp, C.c_double, dp, dp, dp, dp]
         _lib.orc_reaction_source.argtypes = [pp, dp, dp]
@@ -118,6 +122,7 @@ class Oracle:
         s.newton_rtol, s.newton_maxit = P.newton_rtol, P.newton_maxit
         s.node_type = NODE_TYPES[P.nodes]
         s.split_op = 0
+        s.space_order = int(P.space_order)
         self.s = s
         self.L = lib()
         self.nvar = P.nvar
@@ -130,16 +135,35 @@ class Oracle:
         return U
 
     def advective(self, U):
+        """A(U) of the problem's spatial order (PLM/HLLC, or the fourth-order operator)."""
         U = self._flat(U)
         A = np.empty_like(U)
-        self.L.orc_advective(C.byref(self.s), _dp(U), _dp(A))
+        self.L.orc_advective_term(C.byref(self.s), _dp(U), _dp(A))
         return A
 
     def reaction_source(self, U):
+        """R on zone averages (second order) or the averaged source of the fourth-order scheme."""
         U = self._flat(U)
         R = np.empty((self.n,) + U.shape[1:])
-        self.L.orc_reaction_source(C.byref(self.s), _dp(U), _dp(R))
+        if self.P.space_order == 4:
+            self.L.orc_reaction_source4(C.byref(self.s), _dp(U), _dp(R))
+        else:
+            self.L.orc_reaction_source(C.byref(self.s), _dp(U), _dp(R))
         return R
+
+    def avg_to_point(self, F):
+        """Zone-centre values from zone averages, f - L f / 24 (fields first)."""
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        out = np.empty_like(F)
+        self.L.orc_avg_to_point(C.byref(self.s), int(F.shape[0]), _dp(F), _dp(out))
+        return out
+
+    def point_to_avg(self, F):
+        """Zone averages from zone-centre values, f + L f / 24 (fields first)."""
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        out = np.empty_like(F)
+        self.L.orc_point_to_avg(C.byref(self.s), int(F.shape[0]), _dp(F), _dp(out))
+        return out
 
     def rates(self, rho, mom, w, jac=True):
         mom = np.ascontiguousarray(np.atleast_1d(mom), dtype=np.float64)

@@ -65,6 +65,8 @@ typedef struct {
     int split_op;       /* ORC_OP_BOTH (the coupled SDC step), ORC_OP_ADVECT  */
                         /* (R = 0) or ORC_OP_REACT (A = 0): the sub-problems  */
                         /* of the Strang-split baseline                       */
+    int space_order;    /* 2: PLM/HLLC, R on zone averages; 4: the fourth-    */
+                        /* order operators (orc_advective4, ..._newton4)      */
 } orc_problem;
 
 #define ORC_OP_BOTH 0
@@ -124,6 +126,17 @@ void orc_node_integral(const orc_problem* P, const double* const* A_nodes,
 
 /* one SDC time step of size dt, in place on U (nvar*N) */
 int orc_sdc_step(const orc_problem* P, double* U, double dt, orc_stats* st);
+
+/* Fourth-order operators (space_order = 4): average <-> zone-centre maps
+   over nf field-major fields, the advective term, the averaged reactive
+   source and the implicit update solved at zone centres. */
+void orc_avg_to_point(const orc_problem* P, int nf, const double* avg, double* point);
+void orc_point_to_avg(const orc_problem* P, int nf, const double* point, double* avg);
+void orc_advective4(const orc_problem* P, const double* U, double* A);
+void orc_advective_term(const orc_problem* P, const double* U, double* A);
+void orc_reaction_source4(const orc_problem* P, const double* U, double* R);
+void orc_react_newton4(const orc_problem* P, const double* rhs, double dt_m, double* U_inout, double* R_out,
+                       orc_stats* st);
 
 /* Strang-split baseline (section 2 contrasts SDC with operator splitting,
    whose coupling error SDC removes): reactions over dt/2, advection over dt,

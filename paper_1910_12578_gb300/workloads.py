@@ -107,6 +107,7 @@ class Problem:
     n_nodes: int = 3             # M (Gauss-Lobatto nodes)
     n_iters: int = 3             # K (SDC iterations)
     nodes: str = "lobatto"       # "lobatto" (Gauss-Lobatto) or "radau" (node 0 + Radau IIA points)
+    space_order: int = 2         # 2: PLM/HLLC; 4: the fourth-order finite-volume operators
     limiter: int = 1             # 1 = MC, 0 = unlimited centred slopes
     newton_rtol: float = 1e-10
     newton_maxit: int = 100

@@ -342,6 +342,166 @@ def test_newton_reports_status():
 
 
 # ---------------------------------------------------------------- conservation / symmetry
+# ---------------------------------------------------------------- fourth-order operators
+def _trig_box(n):
+    """f(x) = sin(2 pi x) sin(2 pi y) cos(2 pi z) on n^3: zone-centre values and
+    exact zone averages (each factor's average is its centre value times
+    sin(pi h) / (pi h))."""
+    h = 1.0 / n
+    c = (np.arange(n) + 0.5) * h
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    f = np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Y) * np.cos(2 * np.pi * Z)
+    s = math.sin(math.pi * h) / (math.pi * h)
+    net = W.decay_network()
+    P = W.Problem(dim=3, n=(n, n, n), dx=(h, h, h), gamma=1.4, net=net, space_order=4)
+    return P, f[None], (f * s ** 3)[None]
+
+
+def test_average_point_maps_are_fourth_order():
+    """f_c = <f> - L<f>/24 and <f> = f_c + L f_c/24 against closed-form averages."""
+    e1, e2 = [], []
+    for n in (8, 16, 32):
+        P, point, avg = _trig_box(n)
+        o = O.Oracle(P)
+        e1.append(np.abs(o.avg_to_point(avg.reshape(1, -1)) - point.reshape(1, -1)).max())
+        e2.append(np.abs(o.point_to_avg(point.reshape(1, -1)) - avg.reshape(1, -1)).max())
+    for e in (e1, e2):
+        assert math.log2(e[1] / e[2]) == pytest.approx(4.0, abs=0.2), e
+
+
+def _nonlinear_1d_state(n, gamma=1.4):
+    """Smooth rho, u, p (all varying); exact zone averages of the conserved
+    fields by 8-point Gauss-Legendre quadrature, exact flux at the faces."""
+    def prim(x):
+        return (1 + 0.2 * np.sin(2 * np.pi * x), 0.3 + 0.1 * np.cos(2 * np.pi * x),
+                1 + 0.15 * np.sin(2 * np.pi * x + 0.7))
+
+    def cons(x):
+        rho, u, p = prim(x)
+        return np.stack([rho, rho * u, p / (gamma - 1) + 0.5 * rho * u * u, rho, 0 * rho])
+
+    def flux(x):
+        rho, u, p = prim(x)
+        E = p / (gamma - 1) + 0.5 * rho * u * u
+        return np.stack([rho * u, rho * u * u + p, (E + p) * u, rho * u, 0 * rho])
+
+    h = 1.0 / n
+    xc = (np.arange(n) + 0.5) * h
+    gx, gw = np.polynomial.legendre.leggauss(8)
+    U = sum(w * cons(xc + 0.5 * h * t) for t, w in zip(gx, gw)) / 2.0
+    A_exact = -(flux(xc + h / 2) - flux(xc - h / 2)) / h
+    return U, A_exact
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_advective_term_order_on_a_nonlinear_state(order):
+    """The average of the flux divergence over a zone is the difference of the
+    face fluxes over h: the centred PLM/HLLC term converges at second order, the
+    fourth-order term at fourth (every field)."""
+    errs = []
+    for n in (32, 64, 128):
+        U, Aex = _nonlinear_1d_state(n)
+        P = W.Problem(dim=1, n=(n, 1, 1), dx=(1.0 / n, 1, 1), gamma=1.4, net=W.decay_network(), limiter=0,
+                      space_order=order)
+        A = O.Oracle(P).advective(U.reshape(5, 1, 1, n)).reshape(5, n)
+        errs.append(np.abs(A - Aex)[:4].max(axis=1))
+    rates = np.log2(errs[1] / errs[2])
+    assert np.all(np.abs(rates - order) <= 0.2), rates
+
+
+def test_advective4_fourth_order_in_3d():
+    """Uniform u and p, rho = 1 + 0.2 sin sin sin: every component of A is linear in
+    rho, and its exact average is the difference of the face averages of the flux."""
+    errs = []
+    for n in (16, 32):
+        h = 1.0 / n
+        c = (np.arange(n) + 0.5) * h
+        Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+        s = math.sin(math.pi * h) / (math.pi * h)
+        u = (0.3, -0.2, 0.1)
+        fac = [np.sin(2 * np.pi * X), np.sin(2 * np.pi * Y), np.sin(2 * np.pi * Z)]
+        rho = 1 + 0.2 * fac[0] * fac[1] * fac[2] * s ** 3
+        P = W.Problem(dim=3, n=(n, n, n), dx=(h, h, h), gamma=1.4, net=W.decay_network(), limiter=0, space_order=4)
+        U = W.conserved_from(P.gamma, rho, [ui * np.ones_like(X) for ui in u], 1.0 / rho,
+                             [np.ones_like(X), np.zeros_like(X)])
+        A = O.Oracle(P).advective(U).reshape(U.shape)
+        cent = [X, Y, Z]
+        Aex = np.zeros_like(X)
+        for d in range(3):
+            other = 0.2 * s ** 2 * np.prod([fac[e] for e in range(3) if e != d], axis=0)
+            Aex -= u[d] * other * (np.sin(2 * np.pi * (cent[d] + h / 2)) - np.sin(2 * np.pi * (cent[d] - h / 2))) / h
+        errs.append(np.abs(A[0] - Aex).max())
+    assert math.log2(errs[0] / errs[1]) == pytest.approx(4.0, abs=0.2), errs
+
+
+def _run_1d_burning(n, order, tf=0.1):
+    P, U = W.config_1d(n)
+    P.net = W.decay_network(k0=1e3)
+    P.limiter, P.n_nodes, P.n_iters, P.space_order = 0, 3, 4, order
+    P.newton_rtol = 1e-14
+    o = O.Oracle(P)
+    if order == 4:   # config 1's profile gives zone-centre values
+        U = o.point_to_avg(U.reshape(P.nvar, -1)).reshape(U.shape)
+    nsteps = int(round(tf * n / 0.25))
+    V = U.copy()
+    for _ in range(nsteps):
+        V, st = o.step(V, tf / nsteps)
+    return V.reshape(P.nvar, -1)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_sdc_space_time_order(order):
+    """Section 2: the fourth-order method (Simpson's rule, four iterations, the
+    fourth-order operators) converges at fourth order in space and time together
+    (dt = h/4 on 1D flow with burning, zone averages of a 1024-zone run as the
+    reference); the PLM/HLLC step at second order."""
+    ref = _run_1d_burning(1024, order)
+    errs = [np.abs(_run_1d_burning(n, order) - ref.reshape(ref.shape[0], n, -1).mean(axis=2)).max()
+            for n in (64, 128, 256)]
+    rate = math.log2(errs[1] / errs[2])
+    assert rate == pytest.approx(order, abs=0.35), errs
+
+
+def test_fourth_order_conserves():
+    """Mass, sum X and total energy with binding energy (12^3 burning box): the
+    average <-> centre maps are linear and sum to zero over a periodic box."""
+    P, U = W.config_box(n=12, nspec=7, seed=0, T0=0.5, amp=2.0)
+    P.space_order = 4
+    o = O.Oracle(P)
+    b = P.net.binding()
+    mass = np.asarray(P.net.mass)
+
+    def totals(V):
+        rho = V[0]
+        Y = V[5:] / mass[:, None, None, None] / rho
+        return V[0].sum(), (V[4] - rho * np.tensordot(b, Y, axes=1)).sum()
+
+    m0, e0 = totals(U)
+    V = U.copy()
+    for _ in range(3):
+        V, st = o.step(V, o.cfl_dt(V))
+        assert st.n_fail == 0
+    m1, e1 = totals(V)
+    assert abs(m1 - m0) <= 1e-13 * abs(m0)
+    assert abs(e1 - e0) <= 1e-12 * abs(e0)
+    assert np.abs(V[5:].sum(0) - V[0]).max() <= 1e-13
+    assert V[6].max() > 1e-3
+
+
+def test_fourth_order_step_on_a_uniform_state_is_the_second_order_step():
+    """Uniform state: every second difference vanishes exactly, so the
+    fourth-order step is the second-order one up to round-off (its implicit
+    update forms <rhs> + dt_m <R> where the second-order one keeps the Newton
+    iterate; the two agree to the iterate's residual)."""
+    net = W.decay_network(Q=1.0)
+    for M, K in ((2, 2), (3, 3)):
+        P, U = uniform_1d(net, T=1.3, M=M, K=K)
+        V2, _ = O.Oracle(P).step(U, 0.05)
+        P.space_order = 4
+        V4, _ = O.Oracle(P).step(U, 0.05)
+        assert np.abs(V2 - V4).max() <= 1e-15 * np.abs(V2).max()
+
+
 # ---------------------------------------------------------------- Strang-split baseline
 def test_strang_without_flow_is_two_reaction_half_steps():
     """A uniform state at rest has A = 0 exactly, so the Strang step is two
