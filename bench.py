@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--config", choices=["box64", "box256", "batch200"], default="box64")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--prec", choices=["fp64", "fp32jac"], default="fp64")
+    p.add_argument("--space-order", type=int, choices=[2, 4], default=2,
+                   help="2: PLM/MC/HLLC; 4: the fourth-order finite-volume operators (smooth-flow form)")
     p.add_argument("--nodes", choices=["lobatto", "radau"], default="lobatto",
                    help="temporal node set: Gauss-Lobatto (trapezoid/Simpson) or node 0 + Radau IIA points")
     p.add_argument("--seed", type=int, default=None,
@@ -228,10 +230,15 @@ def run_reference(args):
         return 0
     import oracle as O
     P, U, desc = workload(args.config, args.seed, args.nodes)
+    for p_ in (P if isinstance(P, list) else [P]):
+        p_.space_order = args.space_order
+    if args.space_order == 4:
+        desc += "; fourth-order finite-volume operators (no limiter)"
     if args.config == "box256":
         # bounded sample: a 64^3 box with the same network and parameters
         P, U = W.config_box(n=64, nspec=13, n_nodes=3, n_iters=4, seed=args.seed, T0=0.5)
         P.nodes = args.nodes
+        P.space_order = args.space_order
         desc += " (sample: 64^3 box, same network)"
     if isinstance(P, list):
         # bounded sample: the first 8 boxes of the batch, each its own oracle step
@@ -284,6 +291,7 @@ def cpu_baseline_sampled(P, U, dt, gpu_out, seed, target_s=10.0, max_steps=3):
     import oracle as O
     Pc, Uc = W.config_box(n=64, nspec=P.net.nspec, n_nodes=P.n_nodes, n_iters=P.n_iters, seed=seed, T0=0.5)
     Pc.nodes = P.nodes
+    Pc.space_order = P.space_order
     oc = O.Oracle(Pc)
     dtc = oc.cfl_dt(Uc)
     t0 = time.perf_counter()
@@ -393,6 +401,10 @@ def run_ours(args):
     if not os.path.exists(sdc.LIB_PATH):
         B.build()
     P, U, desc = workload(args.config, rank_seed(args.seed, rank), args.nodes)
+    for p_ in as_list(P):
+        p_.space_order = args.space_order
+    if args.space_order == 4:
+        desc += "; fourth-order finite-volume operators (no limiter)"
     P0 = as_list(P)[0]
     prec = sdc.PREC_FP64 if args.prec == "fp64" else sdc.PREC_FP32_JAC
     ctx = sdc.Context(P, prec=prec)
@@ -596,7 +608,8 @@ def run_ours(args):
             "dtype": "f64" if prec == sdc.PREC_FP64 else "f64 residual/update, f32 Jacobian/LU",
             "data": "synthetic",
             "config": {"workload": desc, "zones": nzones(P), "nspec": P0.net.nspec, "nodes": P0.n_nodes,
-                       "iters": P0.n_iters, "nodes": args.nodes, "prec": args.prec, "seed": args.seed,
+                       "iters": P0.n_iters, "nodes": args.nodes, "space_order": args.space_order,
+                       "prec": args.prec, "seed": args.seed,
                        "kernel_variants": tuning,
                        "l2": "flushed before every timed step (256 MB write)",
                        "parallelism": "independent box per GPU" if ws > 1 else "1 GPU"},

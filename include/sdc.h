@@ -96,7 +96,19 @@ typedef struct {
     double newton_rtol;    /* scaled Newton update that ends the solve      */
     int newton_maxit;      /* iteration cap per zone solve                  */
     int node_type;         /* SDC_NODES_LOBATTO or SDC_NODES_RADAU          */
+    int space_order;       /* 2: PLM + limiter + HLLC, R on zone averages;   */
+                           /* 4: the fourth-order finite-volume operators    */
 } sdc_params;
+
+/* space_order = 4 (section 2: the fourth-order method pairs Simpson's rule with
+   McCorquodale & Colella's reconstruction), smooth-flow form without limiting:
+   zone centres f_c = <f> - L<f>/24 (L: second differences summed over the
+   dimensions), primitive averages W(U_c) + L W(<U>)/24, face averages by the
+   7/12, -1/12 stencil, face fluxes F(W_f) + L_t F(<W>_f)/24 with face-centre
+   states W_f = <W>_f - L_t <W>_f/24 (L_t across the face), averaged sources
+   R(U_c) + L R(U_c)/24, and the implicit update solved at zone centres with
+   <U> = <rhs> + dt_m <R>.  The limiter argument is ignored; the adjoint and
+   sdc_step_static take space_order 2 only. */
 
 /* Temporal node sets of the SDC step (n_nodes = M):
    SDC_NODES_LOBATTO: Gauss-Lobatto nodes {0,1} or {0,1/2,1}; the integral of

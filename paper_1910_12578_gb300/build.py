@@ -1,6 +1,6 @@
 """Build libsdc.so in-tree with nvcc for sm_103a (GB300).
 
-The three translation units compile in parallel, then link into
+The translation units compile in parallel, then link into
 paper_1910_12578_gb300/libsdc.so.  Rebuilds only when a source is newer than
 the library.
 """
@@ -18,7 +18,7 @@ LIB = os.path.join(PKG, "libsdc.so")
 BUILD = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-UNITS = ["sdc_newton.cu", "sdc_stencil.cu", "sdc_api.cu", "sdc_adjoint.cu"]
+UNITS = ["sdc_newton.cu", "sdc_stencil.cu", "sdc_api.cu", "sdc_adjoint.cu", "sdc_fourth.cu"]
 
 
 def _nvcc() -> str:

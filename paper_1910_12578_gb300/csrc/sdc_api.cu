@@ -8,6 +8,7 @@
 
 #include "../../include/sdc.h"
 #include "sdc_adjoint_launch.h"
+#include "sdc_fourth_launch.h"
 #include "sdc_launch.h"
 
 using namespace sdcd;
@@ -18,10 +19,13 @@ constexpr int EW_BLOCK = 256;
 
 __global__ void set_scalar_kernel(double* p, double v) { *p = v; }
 
-// rhs at node 0 (A at node 0 never changes within a step, so its correction is zero):
-//   rhs = U^0 - dtm R^{1,(k)} + sum_l (q_l dt) (A_l + R_l)^{(k)}
-__global__ void rhs_node0_kernel(int nvar, int dim, long long N, const double* __restrict__ U0,
-                                 RhsArgs ra) {
+// rhs of Eq. sdc:general from elementwise arrays:
+//   rhs = U^m + dtm (A^{m,(k+1)} - A^{m,(k)}) - dtm R^{m+1,(k)} + sum_l (q_l dt) (A_l + R_l)^{(k)}
+// Anew_m = NULL drops the A difference (node 0, whose A never changes within a
+// step, or a step with A off); the second-order path fuses the other nodes'
+// rhs into the stencil kernel instead.
+__global__ void rhs_kernel(int nvar, int dim, long long N, const double* __restrict__ Um,
+                           const double* __restrict__ Anew_m, RhsArgs ra) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)nvar * N) return;
     const int f = (int)(i / N);
@@ -30,7 +34,8 @@ __global__ void rhs_node0_kernel(int nvar, int dim, long long N, const double* _
     const double dtm = dt * ra.dtm_frac;
     const bool reactive = f >= 1 + dim;
     const int r = f - 1 - dim;
-    double v = U0[i];
+    double v = Um[i];
+    if (Anew_m) v += dtm * (Anew_m[i] - ra.Aold_m[i]);
     if (reactive) v -= dtm * ra.Rnext[r * N + z];
     double I = 0.0;
     for (int l = 0; l < ra.M; l++) {
@@ -164,6 +169,8 @@ struct sdc_ctx {
     cudaGraphExec_t gexec_strang = nullptr;  // the Strang-split step's graph
     double* gU_strang = nullptr;
     double* d_dt_half = nullptr;             // dt/2 of the split step (next to d_dt)
+    int space_order = 2;                     // 2: PLM/HLLC stencil; 4: the fourth-order operators
+    FourthWs fw;                             // their workspace (space_order 4)
     // kernel variants (chosen by sdc_autotune) and the Newton work queues
     int stencil_variant = 0, newton_variant = 0;
     int persistent_blocks = 0;
@@ -290,14 +297,24 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
     double* node[3] = {c->node_ws[0], c->M == 3 ? c->node_ws[1] : U, U};
     if ((e = cudaMemcpyAsync(node[0], U, ubytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
     RhsArgs none = rhs_args(c, (const double* const*)c->Ag[0], (const double* const*)c->Rg[0], 0, dt_dev);
+    const bool fourth = c->space_order == 4;
     if (with_A) {
-        SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles, c->ntiles,
-                                                     node[0], c->A0, STENCIL_A, none, st, c->stencil_variant));
+        if (fourth)
+            SDC_LAUNCH(prof, CLS_STENCIL, launch_advective4(c->P, c->dim, N, c->d_boxes, c->nbox, node[0], c->A0,
+                                                            c->fw, st));
+        else
+            SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles,
+                                                         c->ntiles, node[0], c->A0, STENCIL_A, none, st,
+                                                         c->stencil_variant));
     } else if ((e = cudaMemsetAsync(c->A0, 0, ubytes, st)) != cudaSuccess) {
         return e;
     }
     if (with_R) {
-        SDC_LAUNCH(prof, CLS_OTHER, launch_reaction_source(c->P, N, c->dim, node[0], c->R0, st));
+        if (fourth)
+            SDC_LAUNCH(prof, CLS_OTHER, launch_reaction_source4(c->P, c->dim, N, c->d_boxes, c->nbox, node[0], c->R0,
+                                                                c->fw, st));
+        else
+            SDC_LAUNCH(prof, CLS_OTHER, launch_reaction_source(c->P, N, c->dim, node[0], c->R0, st));
     } else if ((e = cudaMemsetAsync(c->R0, 0, sizeof(double) * c->nw * N, st)) != cudaSuccess) {
         return e;
     }
@@ -312,8 +329,14 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
             RhsArgs ra = rhs_args(c, Aold, Rold, m, dt_dev);
             if (m == 0 || !with_A) {
                 // no A^{m,(k+1)} - A^{m,(k)} term: node 0 is fixed, or A is off
-                SDC_LAUNCH(prof, CLS_OTHER, (rhs_node0_kernel<<<grid_for((long long)c->nvar * N, EW_BLOCK), EW_BLOCK, 0,
-                                                                 st>>>(c->nvar, c->dim, N, node[m], ra),
+                SDC_LAUNCH(prof, CLS_OTHER, (rhs_kernel<<<grid_for((long long)c->nvar * N, EW_BLOCK), EW_BLOCK, 0,
+                                                           st>>>(c->nvar, c->dim, N, node[m], nullptr, ra),
+                                             cudaGetLastError()));
+            } else if (fourth) {
+                SDC_LAUNCH(prof, CLS_STENCIL, launch_advective4(c->P, c->dim, N, c->d_boxes, c->nbox, node[m],
+                                                                Anew[m], c->fw, st));
+                SDC_LAUNCH(prof, CLS_OTHER, (rhs_kernel<<<grid_for((long long)c->nvar * N, EW_BLOCK), EW_BLOCK, 0,
+                                                           st>>>(c->nvar, c->dim, N, node[m], Anew[m], ra),
                                              cudaGetLastError()));
             } else {
                 SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles,
@@ -323,11 +346,18 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
             if (with_R) {
                 const double* guess = (k == 0) ? node[0] : node[m + 1];
                 unsigned long long* q = (c->d_queue && qslot < QUEUE_SLOTS) ? c->d_queue + qslot++ : nullptr;
-                SDC_LAUNCH(prof, CLS_NEWTON, launch_newton(c->P, c->cfg, c->prec, N, c->dim, c->rhs, guess,
-                                                           node[m + 1], Rnew[m + 1], dt_dev,
-                                                           c->tau[m + 1] - c->tau[m], 0.0, nullptr, nullptr,
-                                                           c->d_stats, st, c->newton_variant, q,
-                                                           c->persistent_blocks));
+                if (fourth)
+                    SDC_LAUNCH(prof, CLS_NEWTON, launch_newton4(c->P, c->cfg, c->prec, c->dim, N, c->d_boxes, c->nbox,
+                                                                c->rhs, guess, node[m + 1], Rnew[m + 1], dt_dev,
+                                                                c->tau[m + 1] - c->tau[m], 0.0, nullptr, nullptr,
+                                                                c->d_stats, c->fw, st, c->newton_variant, q,
+                                                                c->persistent_blocks));
+                else
+                    SDC_LAUNCH(prof, CLS_NEWTON, launch_newton(c->P, c->cfg, c->prec, N, c->dim, c->rhs, guess,
+                                                               node[m + 1], Rnew[m + 1], dt_dev,
+                                                               c->tau[m + 1] - c->tau[m], 0.0, nullptr, nullptr,
+                                                               c->d_stats, st, c->newton_variant, q,
+                                                               c->persistent_blocks));
             } else if ((e = cudaMemcpyAsync(node[m + 1], c->rhs, ubytes, cudaMemcpyDeviceToDevice, st)) !=
                        cudaSuccess) {
                 return e;  // R = 0: the implicit update is w = rhs
@@ -338,9 +368,13 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
                 return e;
         }
         if (k < c->K - 1 && with_A) {
-            SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles,
-                                                         c->ntiles, node[c->M - 1], Anew[c->M - 1], STENCIL_A, none,
-                                                         st, c->stencil_variant));
+            if (fourth)
+                SDC_LAUNCH(prof, CLS_STENCIL, launch_advective4(c->P, c->dim, N, c->d_boxes, c->nbox, node[c->M - 1],
+                                                                Anew[c->M - 1], c->fw, st));
+            else
+                SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles,
+                                                             c->ntiles, node[c->M - 1], Anew[c->M - 1], STENCIL_A,
+                                                             none, st, c->stencil_variant));
         }
         for (int l = 1; l < c->M; l++) {
             Aold[l] = Anew[l];
@@ -486,7 +520,8 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     if (!(prm->gamma > 1.0) || (prm->n_nodes != 2 && prm->n_nodes != 3) || prm->n_iters < 1 ||
         prm->newton_maxit < 1 || !(prm->newton_rtol > 0.0) ||
         (prm->prec != SDC_PREC_FP64 && prm->prec != SDC_PREC_FP32_JAC) ||
-        (prm->node_type != SDC_NODES_LOBATTO && prm->node_type != SDC_NODES_RADAU))
+        (prm->node_type != SDC_NODES_LOBATTO && prm->node_type != SDC_NODES_RADAU) ||
+        (prm->space_order != 2 && prm->space_order != 4))
         return SDC_ERR_INVALID_ARG;
     const int topo = is_alpha_chain(net) ? TOPO_CHAIN : TOPO_GENERIC;
     int topo_used = topo;
@@ -514,6 +549,7 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     c->prec = prm->prec;
     c->cfg.rtol = prm->newton_rtol;
     c->cfg.maxit = prm->newton_maxit;
+    c->space_order = prm->space_order;
     weights(prm->node_type, c->M, c->tau, c->q);
     NetParams& P = c->P;
     memset(&P, 0, sizeof(P));
@@ -588,6 +624,13 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
             if ((e = ctx_alloc(c, (void**)&c->Ag[g][m], ub)) != cudaSuccess) return fail(e);
             if ((e = ctx_alloc(c, (void**)&c->Rg[g][m], rb)) != cudaSuccess) return fail(e);
         }
+    if (c->space_order == 4) {
+        FourthWs& w = c->fw;
+        double** arrays[] = {&w.Uc, &w.W2, &w.Wc, &w.Wa, &w.Wf, &w.Wfc, &w.Fc, &w.F2, &w.Fa, &w.rc, &w.gc};
+        for (double** a : arrays)
+            if ((e = ctx_alloc(c, (void**)a, ub)) != cudaSuccess) return fail(e);
+        if ((e = ctx_alloc(c, (void**)&w.Rc, rb)) != cudaSuccess) return fail(e);
+    }
     if ((e = cudaMemcpy(c->d_boxes, hb.data(), sizeof(BoxDev) * nbox, cudaMemcpyHostToDevice)) != cudaSuccess)
         return fail(e);
     if ((e = cudaMemcpy(c->d_tiles, ht.data(), sizeof(TileDev) * ht.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -608,6 +651,10 @@ sdc_status sdc_sizes(const sdc_ctx* ctx, long long* ntot, int* nvar, int* nreact
 
 sdc_status sdc_advective_term(sdc_ctx* ctx, const double* U, double* A) {
     if (!ctx || !U || !A || U == A) return SDC_ERR_INVALID_ARG;
+    if (ctx->space_order == 4) {
+        SDC_TRY(launch_advective4(ctx->P, ctx->dim, ctx->Ntot, ctx->d_boxes, ctx->nbox, U, A, ctx->fw, ctx->stream));
+        return SDC_OK;
+    }
     RhsArgs none;
     memset(&none, 0, sizeof(none));
     SDC_TRY(launch_stencil(ctx->P, ctx->dim, ctx->limiter, ctx->Ntot, ctx->d_boxes, ctx->d_tiles, ctx->ntiles, U, A,
@@ -630,9 +677,14 @@ sdc_status sdc_react_newton(sdc_ctx* ctx, const double* rhs, double dt_m, double
     if (!ctx || !rhs || !U_inout || !R_out || rhs == U_inout) return SDC_ERR_INVALID_ARG;
     if (stats) SDC_TRY(cudaMemsetAsync(ctx->d_stats, 0, sizeof(DevStats), ctx->stream));
     SDC_TRY(cudaMemsetAsync(ctx->d_queue, 0, sizeof(unsigned long long), ctx->stream));
-    SDC_TRY(launch_newton(ctx->P, ctx->cfg, ctx->prec, ctx->Ntot, ctx->dim, rhs, U_inout, U_inout, R_out, nullptr,
-                          1.0, dt_m, zone_status, zone_iters, ctx->d_stats, ctx->stream, ctx->newton_variant,
-                          ctx->d_queue, ctx->persistent_blocks));
+    if (ctx->space_order == 4)
+        SDC_TRY(launch_newton4(ctx->P, ctx->cfg, ctx->prec, ctx->dim, ctx->Ntot, ctx->d_boxes, ctx->nbox, rhs, U_inout,
+                               U_inout, R_out, nullptr, 1.0, dt_m, zone_status, zone_iters, ctx->d_stats, ctx->fw,
+                               ctx->stream, ctx->newton_variant, ctx->d_queue, ctx->persistent_blocks));
+    else
+        SDC_TRY(launch_newton(ctx->P, ctx->cfg, ctx->prec, ctx->Ntot, ctx->dim, rhs, U_inout, U_inout, R_out,
+                              nullptr, 1.0, dt_m, zone_status, zone_iters, ctx->d_stats, ctx->stream,
+                              ctx->newton_variant, ctx->d_queue, ctx->persistent_blocks));
     if (stats) return read_stats(ctx, stats);
     return SDC_OK;
 }
@@ -804,6 +856,14 @@ sdc_status sdc_launches_per_step(const sdc_ctx* ctx, int* launches) {
     if (!ctx || !launches) return SDC_ERR_INVALID_ARG;
     // dt store, A(U^n), R(U^n), per iteration and node a rhs kernel and a Newton
     // kernel, and A at the last node for every iteration but the last
+    if (ctx->space_order == 4) {
+        // fourth order: A is a sequence of kernels and is evaluated apart from
+        // the rhs at nodes m >= 1; the source and the implicit update add maps
+        const int LA = fourth_advective_launches(ctx->dim), K = ctx->K, M = ctx->M;
+        *launches = 1 + LA + FOURTH_SOURCE_LAUNCHES + K * (M - 1) * (1 + FOURTH_NEWTON_LAUNCHES) +
+                    K * (M - 2) * LA + (K - 1) * LA;
+        return SDC_OK;
+    }
     *launches = 3 + ctx->K * 2 * (ctx->M - 1) + (ctx->K - 1);
     return SDC_OK;
 }
@@ -817,7 +877,7 @@ sdc_status sdc_set_rates(sdc_ctx* ctx, const double* a) {
 
 sdc_status sdc_advective_term_vjp(sdc_ctx* ctx, const double* U, const double* Abar, double* Ubar, int mode) {
     if (!ctx || !U || !Abar || !Ubar || (mode != 0 && mode != 1)) return SDC_ERR_INVALID_ARG;
-    if (!adjoint_supported(ctx->dim, ctx->nspec, ctx->P.topo)) return SDC_ERR_INVALID_ARG;
+    if (!adjoint_supported(ctx->dim, ctx->nspec, ctx->P.topo) || ctx->space_order != 2) return SDC_ERR_INVALID_ARG;
     SDC_TRY(adjoint_workspace(ctx));
     SDC_TRY(launch_stencil_vjp(ctx->P, ctx->dim, ctx->limiter, ctx->Ntot, ctx->d_boxes, ctx->nbox, U, Abar,
                                ctx->adj.G, Ubar, ctx->stream, mode));
@@ -827,7 +887,7 @@ sdc_status sdc_advective_term_vjp(sdc_ctx* ctx, const double* U, const double* A
 sdc_status sdc_step_backward(sdc_ctx* ctx, const double* U_n, double dt, const double* gU_np1, double* gU_n,
                              double* g_a) {
     if (!ctx || !U_n || !gU_np1 || !gU_n || !(dt > 0.0)) return SDC_ERR_INVALID_ARG;
-    if (!adjoint_supported(ctx->dim, ctx->nspec, ctx->P.topo)) return SDC_ERR_INVALID_ARG;
+    if (!adjoint_supported(ctx->dim, ctx->nspec, ctx->P.topo) || ctx->space_order != 2) return SDC_ERR_INVALID_ARG;
     sdc_ctx* c = ctx;
     const long long N = c->Ntot;
     const int M = c->M, K = c->K, nw = c->nw, nr = c->P.nreac;
@@ -1017,8 +1077,10 @@ extern "C" sdc_status sdc_step_static(const sdc_box* boxes, int nbox, const sdc_
     if (!(prm->gamma > 1.0) || (prm->n_nodes != 2 && prm->n_nodes != 3) || prm->n_iters < 1 ||
         prm->newton_maxit < 1 || !(prm->newton_rtol > 0.0) ||
         (prm->prec != SDC_PREC_FP64 && prm->prec != SDC_PREC_FP32_JAC) ||
-        (prm->node_type != SDC_NODES_LOBATTO && prm->node_type != SDC_NODES_RADAU))
+        (prm->node_type != SDC_NODES_LOBATTO && prm->node_type != SDC_NODES_RADAU) ||
+        (prm->space_order != 2 && prm->space_order != 4))
         return SDC_ERR_INVALID_ARG;
+    if (prm->space_order != 2) return SDC_ERR_INVALID_ARG;  // the fixed scratch holds the second-order step
     int topo = is_alpha_chain(net) ? TOPO_CHAIN : TOPO_GENERIC;
     if (!newton_supported(net->nspec, topo)) {
         topo = TOPO_GENERIC;

@@ -47,7 +47,8 @@ class Network(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("n_nodes", C.c_int), ("n_iters", C.c_int), ("limiter", C.c_int),
-                ("prec", C.c_int), ("newton_rtol", C.c_double), ("newton_maxit", C.c_int), ("node_type", C.c_int)]
+                ("prec", C.c_int), ("newton_rtol", C.c_double), ("newton_maxit", C.c_int), ("node_type", C.c_int),
+                ("space_order", C.c_int)]
 
 
 NODE_TYPES = {"lobatto": 0, "radau": 1}
@@ -178,7 +179,7 @@ class Context:
                      reac.ctypes.data_as(C.POINTER(C.c_int)), cnt.ctypes.data_as(C.POINTER(C.c_int)),
                      prod.ctypes.data_as(C.POINTER(C.c_int)))
         prm = Params(P0.gamma, P0.n_nodes, P0.n_iters, P0.limiter, int(prec), P0.newton_rtol, P0.newton_maxit,
-                     NODE_TYPES[P0.nodes])
+                     NODE_TYPES[P0.nodes], int(P0.space_order))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._h = C.c_void_p()
         s = L.sdc_init_box(boxes, len(problems), C.byref(nw), C.byref(prm), C.c_void_p(self.stream.cuda_stream),
@@ -307,7 +308,7 @@ def _marshal(problems, prec):
                  reac.ctypes.data_as(C.POINTER(C.c_int)), cnt.ctypes.data_as(C.POINTER(C.c_int)),
                  prod.ctypes.data_as(C.POINTER(C.c_int)))
     prm = Params(P0.gamma, P0.n_nodes, P0.n_iters, P0.limiter, int(prec), P0.newton_rtol, P0.newton_maxit,
-                 NODE_TYPES[P0.nodes])
+                 NODE_TYPES[P0.nodes], int(P0.space_order))
     return boxes, len(problems), nw, prm, keep
 
 

@@ -4,6 +4,8 @@ the same seeded inputs, through the C ABI.
 Tolerances: FP64 path 1e-12 relative per field (species relative to
 max(|rho X_i|_inf, 1e-6 |rho|_inf)); FP32-Jacobian path 1e-9.
 """
+import copy
+
 import numpy as np
 import pytest
 
@@ -60,13 +62,19 @@ def problems():
     P, U = W.config_box(n=16, nspec=13, n_iters=4, seed=0, T0=0.5)
     P.nodes = "radau"
     out["box16_13_radau"] = (P, U)
+    # fourth-order finite-volume operators
+    for name in ("1d", "box16", "ragged", "box16_13"):
+        P, U = out[name]
+        P = copy.deepcopy(P)
+        P.space_order = 4
+        out[name + "_o4"] = (P, U)
     return out
 
 
 PROBS = problems()
 
 
-@pytest.mark.parametrize("name", ["1d", "box16", "ragged"])
+@pytest.mark.parametrize("name", ["1d", "box16", "ragged", "1d_o4", "box16_o4", "ragged_o4"])
 def test_advective_term_parity(torch_cuda, name):
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
@@ -168,7 +176,9 @@ def test_react_newton_parity(torch_cuda, name, k_iters, prec):
 @pytest.mark.parametrize("name,nsteps,prec", [("1d", 10, 0), ("box16", 2, 0), ("box16", 1, 1), ("ragged", 1, 0),
                                               ("box16_13", 1, 0), ("box16_13", 1, 1),
                                               ("1d_radau", 10, 0), ("box16_radau", 2, 0), ("box16_radau", 1, 1),
-                                              ("box16_radau2", 2, 0), ("box16_13_radau", 1, 0)])
+                                              ("box16_radau2", 2, 0), ("box16_13_radau", 1, 0),
+                                              ("1d_o4", 4, 0), ("box16_o4", 2, 0), ("box16_o4", 1, 1),
+                                              ("ragged_o4", 1, 0), ("box16_13_o4", 1, 0)])
 def test_step_parity(torch_cuda, name, nsteps, prec):
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
@@ -189,7 +199,7 @@ def test_step_parity(torch_cuda, name, nsteps, prec):
 
 
 @pytest.mark.parametrize("name,nsteps,prec", [("1d", 4, 0), ("box16", 2, 0), ("box16", 1, 1), ("box16_radau", 1, 0),
-                                              ("box16_13", 1, 0)])
+                                              ("box16_13", 1, 0), ("box16_o4", 1, 0)])
 def test_strang_step_parity(torch_cuda, name, nsteps, prec):
     """sdc_step_strang (reactions dt/2, advection dt, reactions dt/2 by the same
     SDC step with one operator off) against the oracle's split step."""
@@ -217,6 +227,20 @@ def test_strang_step_parity(torch_cuda, name, nsteps, prec):
     ctx.step(Uc, o.cfl_dt(U))
     W1, _ = o.strang_step(U, o.cfl_dt(U))
     assert not np.allclose(Uc.cpu().numpy(), W1.reshape(Uc.shape), rtol=1e-9, atol=0)
+
+
+def test_fourth_order_rejected_where_unsupported(torch_cuda):
+    """The adjoint (and its advective VJP) take the second-order operators only."""
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = PROBS["box16_o4"]
+    ctx = sdc.Context(P)
+    Ud = dev(torch, U)
+    g = torch.zeros_like(Ud)
+    with pytest.raises(sdc.SdcError):
+        ctx.step_backward(Ud, 1e-3, g, torch.empty_like(Ud))
+    with pytest.raises(sdc.SdcError):
+        ctx.advective_term_vjp(Ud, g, torch.empty_like(Ud))
 
 
 def test_newton_raphson_reciprocal_and_sqrt_within_two_ulp(torch_cuda):
