@@ -14,7 +14,9 @@
 // The averaged source is R(U_c) + L R(U_c)/24; the implicit update is solved at
 // zone centres (U_c - dt_m R(U_c) = rhs_c) and gives <U> = <rhs> + dt_m <R>.
 // Every operator is a sequence of elementwise kernels over field-major arrays,
-// one thread per zone, periodic within each box.
+// one thread per zone, periodic within each box.  GB300 issues FP64 at 2 lanes
+// per SM per clock, so even these stencils are bound by the FP64 pipe: the
+// kernels divide once per zone (a Newton-Raphson reciprocal) and multiply.
 #include "sdc_fourth_launch.h"
 #include "sdc_launch.h"
 
@@ -89,16 +91,16 @@ __global__ void prim_kernel(int dim, int nspec, double gm1, long long N, const d
                             double* __restrict__ W) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= N) return;
-    const double rho = U[z];
+    const double rho = U[z], ir = rcp_nr(rho);  // one reciprocal, then products (FP64 pipe)
     W[z] = rho;
     double ke = 0.0;
     for (int d = 0; d < dim; d++) {
-        const double u = U[(1 + d) * N + z] / rho;
+        const double m = U[(1 + d) * N + z], u = m * ir;
         W[(1 + d) * N + z] = u;
-        ke += 0.5 * rho * u * u;
+        ke += 0.5 * m * u;
     }
     W[(1 + dim) * N + z] = gm1 * (U[(1 + dim) * N + z] - ke);
-    for (int s = 0; s < nspec; s++) W[(2 + dim + s) * N + z] = U[(2 + dim + s) * N + z] / rho;
+    for (int s = 0; s < nspec; s++) W[(2 + dim + s) * N + z] = U[(2 + dim + s) * N + z] * ir;
 }
 
 // face averages of the primitives, the face between z and its +1 neighbour along dir
@@ -115,11 +117,11 @@ __global__ void face_avg_kernel(int dir, int nf, long long N, const BoxDev* __re
 }
 
 // physical Euler flux along dir of the primitive state q
-__device__ __forceinline__ void euler_flux(int dim, int nspec, double gamma, int dir, const double* q, double* F) {
+__device__ __forceinline__ void euler_flux(int dim, int nspec, double igm1, int dir, const double* q, double* F) {
     const double rho = q[0], un = q[1 + dir], p = q[1 + dim];
     double ke = 0.0;
     for (int d = 0; d < dim; d++) ke += 0.5 * rho * q[1 + d] * q[1 + d];
-    const double E = p / (gamma - 1.0) + ke;
+    const double E = p * igm1 + ke;
     F[0] = rho * un;
     for (int d = 0; d < dim; d++) F[1 + d] = rho * un * q[1 + d] + (d == dir ? p : 0.0);
     F[1 + dim] = (E + p) * un;
@@ -127,7 +129,7 @@ __device__ __forceinline__ void euler_flux(int dim, int nspec, double gamma, int
 }
 
 // Fc = F(Wfc) (face centres), F2 = F(Wf) (from the face averages)
-__global__ void face_flux_kernel(int dim, int nspec, double gamma, int dir, long long N,
+__global__ void face_flux_kernel(int dim, int nspec, double igm1, int dir, long long N,
                                  const double* __restrict__ Wfc, const double* __restrict__ Wf,
                                  double* __restrict__ Fc, double* __restrict__ F2) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -135,10 +137,10 @@ __global__ void face_flux_kernel(int dim, int nspec, double gamma, int dir, long
     const int nv = 2 + dim + nspec;
     double q[F_MAXV], F[F_MAXV];
     for (int f = 0; f < nv; f++) q[f] = Wfc[(long long)f * N + z];
-    euler_flux(dim, nspec, gamma, dir, q, F);
+    euler_flux(dim, nspec, igm1, dir, q, F);
     for (int f = 0; f < nv; f++) Fc[(long long)f * N + z] = F[f];
     for (int f = 0; f < nv; f++) q[f] = Wf[(long long)f * N + z];
-    euler_flux(dim, nspec, gamma, dir, q, F);
+    euler_flux(dim, nspec, igm1, dir, q, F);
     for (int f = 0; f < nv; f++) F2[(long long)f * N + z] = F[f];
 }
 
@@ -148,11 +150,11 @@ __global__ void div_kernel(int dir, int nf, long long N, const BoxDev* __restric
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= N) return;
     const ZoneCoord q = zone_coord(boxes, nbox, z);
-    const double dx = 1.0 / boxes[box_index(boxes, nbox, z)].idx[dir];
+    const double idx = boxes[box_index(boxes, nbox, z)].idx[dir];
     const long long zm = neighbour(q, dir, -1);
     for (int f = 0; f < nf; f++) {
         const long long o = (long long)f * N;
-        const double d = (Fa[o + z] - Fa[o + zm]) / dx;
+        const double d = (Fa[o + z] - Fa[o + zm]) * idx;
         A[o + z] = first ? -d : A[o + z] - d;
     }
 }
@@ -193,7 +195,7 @@ cudaError_t launch_advective4(const NetParams& P, int dim, long long N, const Bo
         face_avg_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dir, nv, N, boxes, nbox, w.Wa, w.Wf);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = lap(dim, nv, N, boxes, nbox, w.Wf, w.Wf, -1.0 / 24.0, dir, w.Wfc, st)) != cudaSuccess) return e;
-        face_flux_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dim, P.nspec, P.gamma, dir, N, w.Wfc, w.Wf, w.Fc, w.F2);
+        face_flux_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dim, P.nspec, 1.0 / P.gm1, dir, N, w.Wfc, w.Wf, w.Fc, w.F2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = lap(dim, nv, N, boxes, nbox, w.Fc, w.F2, 1.0 / 24.0, dir, w.Fa, st)) != cudaSuccess) return e;
         div_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dir, nv, N, boxes, nbox, w.Fa, A, dir == 0 ? 1 : 0);
