@@ -130,9 +130,10 @@ typedef struct {
 
 /* Create a context for nbox boxes with one network and one parameter set,
    allocate its device workspace and upload the network.
-   Errors: SDC_ERR_INVALID_ARG (nbox < 1, bad dims, nspec > SDC_MAX_SPEC,
-   nreac > SDC_MAX_REAC, species index out of range, n_nodes not 2/3,
-   n_iters < 1, gamma <= 1), SDC_ERR_OOM, SDC_ERR_CUDA.  *out is NULL on error. */
+   Errors: SDC_ERR_INVALID_ARG (nbox < 1, bad dims, a box of 2^31 zones or
+   more, nspec > SDC_MAX_SPEC, nreac > SDC_MAX_REAC, species index out of
+   range, n_nodes not 2/3, n_iters < 1, gamma <= 1, node_type or space_order
+   not one of theirs), SDC_ERR_OOM, SDC_ERR_CUDA.  *out is NULL on error. */
 sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net,
                         const sdc_params* prm, void* cuda_stream, sdc_ctx** out);
 

@@ -21,19 +21,22 @@ __device__ __forceinline__ int box_of(const BoxDev* boxes, int nbox, long long z
 }
 
 // global index of the zone shifted by o along dir inside its (periodic) box
+// (32-bit arithmetic inside the box: a box holds fewer than 2^31 zones, and
+// 64-bit division would run on the narrow FP64 pipe)
 __device__ __forceinline__ long long shifted(const BoxDev& b, long long z, int dir, int o) {
-    const long long l = z - b.off;
+    const int l = (int)(z - b.off);
     int c[3];
-    c[0] = (int)(l % b.n[0]);
-    c[1] = (int)((l / b.n[0]) % b.n[1]);
-    c[2] = (int)(l / ((long long)b.n[0] * b.n[1]));
+    c[0] = l % b.n[0];
+    c[1] = (l / b.n[0]) % b.n[1];
+    c[2] = l / (b.n[0] * b.n[1]);
     c[dir] = ((c[dir] + o) % b.n[dir] + b.n[dir]) % b.n[dir];
-    return b.off + c[0] + (long long)b.n[0] * (c[1] + (long long)b.n[1] * c[2]);
+    return b.off + (long long)(c[0] + b.n[0] * (c[1] + b.n[1] * c[2]));
 }
 
-// G[dir][z][4*NV]: transposed Jacobian of the flux through the face between z
-// and z+1 (along dir) times that face's adjoint, for the inputs of zones
-// z-1, z, z+1, z+2.
+// G[dir][4*NV][z] (field-major, so that the writes here and the reads of the
+// gather are coalesced): transposed Jacobian of the flux through the face
+// between z and z+1 (along dir) times that face's adjoint, for the inputs of
+// zones z-1, z, z+1, z+2 (slot o*NV + f).
 template <int DIM, int NS>
 __global__ void __launch_bounds__(ADJ_BLOCK)
 stencil_vjp_kernel(double gamma, int limiter, long long N, const BoxDev* __restrict__ boxes, int nbox,
@@ -56,7 +59,7 @@ stencil_vjp_kernel(double gamma, int limiter, long long N, const BoxDev* __restr
     for (int o = 0; o < 4; o++)
 #pragma unroll
         for (int f = 0; f < NV; f++) Uz[o][f] = Dual(U[f * N + zz[o]], 0.0);
-    double* out = G + ((long long)dir * N + z) * (4 * NV);
+    double* out = G + (long long)dir * N * (4 * NV) + z;
     for (int j = 0; j < 4 * NV; j++) {
         const int o = j / NV, f = j % NV;
         Uz[o][f].d = 1.0;
@@ -66,7 +69,7 @@ stencil_vjp_kernel(double gamma, int limiter, long long N, const BoxDev* __restr
         double c = 0.0;
 #pragma unroll
         for (int q = 0; q < NV; q++) c += Fbar[q] * F[q].d;
-        out[j] = c;
+        out[(long long)j * N] = c;
     }
 }
 
@@ -96,11 +99,11 @@ stencil_vjp_rev_kernel(double gamma, int limiter, long long N, const BoxDev* __r
             Ub[o][f] = 0.0;
         }
     face_flux_vjp<DIM, NS>(gamma, limiter, dir, Uz, Fbar, Ub);
-    double* out = G + ((long long)dir * N + z) * (4 * NV);
+    double* out = G + (long long)dir * N * (4 * NV) + z;
 #pragma unroll
     for (int o = 0; o < 4; o++)
 #pragma unroll
-        for (int f = 0; f < NV; f++) out[o * NV + f] = Ub[o][f];
+        for (int f = 0; f < NV; f++) out[(long long)(o * NV + f) * N] = Ub[o][f];
 }
 
 // Ubar_z += sum over directions and over the four faces whose stencil holds z
@@ -120,9 +123,9 @@ stencil_vjp_gather(long long N, const BoxDev* __restrict__ boxes, int nbox, cons
         for (int o = 0; o < 4; o++) {
             // z is input slot o of the face whose left zone is z + 1 - o
             const long long l = shifted(b, z, dir, 1 - o);
-            const double* g = G + ((long long)dir * N + l) * (4 * NV) + o * NV;
+            const double* g = G + (long long)dir * N * (4 * NV) + (long long)(o * NV) * N + l;
 #pragma unroll
-            for (int f = 0; f < NV; f++) acc[f] += g[f];
+            for (int f = 0; f < NV; f++) acc[f] += g[(long long)f * N];
         }
 #pragma unroll
     for (int f = 0; f < NV; f++) Ubar[f * N + z] += acc[f];

@@ -500,7 +500,9 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
             if (d >= dim && boxes[b].n[d] != 1) return SDC_ERR_INVALID_ARG;
             if (d < dim && !(boxes[b].dx[d] > 0.0)) return SDC_ERR_INVALID_ARG;
         }
-        Ntot += (long long)boxes[b].n[0] * boxes[b].n[1] * boxes[b].n[2];
+        const long long nb = (long long)boxes[b].n[0] * boxes[b].n[1] * boxes[b].n[2];
+        if (nb >= (1ll << 31)) return SDC_ERR_INVALID_ARG;  // zone indices inside a box are 32-bit
+        Ntot += nb;
     }
     if (net->nspec < 1 || net->nspec > SDC_MAX_SPEC || net->nreac < 1 || net->nreac > SDC_MAX_REAC)
         return SDC_ERR_INVALID_ARG;

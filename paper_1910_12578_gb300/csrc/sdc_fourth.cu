@@ -48,10 +48,12 @@ __device__ __forceinline__ ZoneCoord zone_coord(const BoxDev* boxes, int nbox, l
     ZoneCoord q;
     q.off = b.off;
     for (int d = 0; d < 3; d++) q.n[d] = b.n[d];
-    const long long l = z - b.off;
-    q.c[0] = (int)(l % b.n[0]);
-    q.c[1] = (int)((l / b.n[0]) % b.n[1]);
-    q.c[2] = (int)(l / ((long long)b.n[0] * b.n[1]));
+    // 32-bit arithmetic inside the box (fewer than 2^31 zones): 64-bit division
+    // would run on the narrow FP64 pipe
+    const int l = (int)(z - b.off);
+    q.c[0] = l % b.n[0];
+    q.c[1] = (l / b.n[0]) % b.n[1];
+    q.c[2] = l / (b.n[0] * b.n[1]);
     return q;
 }
 
@@ -59,7 +61,7 @@ __device__ __forceinline__ ZoneCoord zone_coord(const BoxDev* boxes, int nbox, l
 __device__ __forceinline__ long long neighbour(const ZoneCoord& q, int d, int o) {
     int c[3] = {q.c[0], q.c[1], q.c[2]};
     c[d] = ((c[d] + o) % q.n[d] + q.n[d]) % q.n[d];
-    return q.off + c[0] + (long long)q.n[0] * (c[1] + (long long)q.n[1] * c[2]);
+    return q.off + (long long)(c[0] + q.n[0] * (c[1] + q.n[1] * c[2]));
 }
 
 // out = a + coef * sum_{d < dim, d != skip} (b(z+e_d) - 2 b(z) + b(z-e_d)), nf fields

@@ -1,7 +1,7 @@
 """Run SDC steps of a named workload for a profiler (ncu) or a quick timing.
 
     python -m paper_1910_12578_gb300.profile_step --config box64 --stencil-variant 1 --newton-variant 1 \\
-        --warmup 1 --steps 2 [--eager] [--prec fp32jac]
+        --warmup 1 --steps 2 [--eager] [--prec fp32jac] [--space-order 4] [--nodes radau] [--backward]
 
 Every step starts from the same seeded initial state.  With --eager the kernels
 are launched one by one (sdc_step_profile, CUDA events per kernel class);
@@ -46,6 +46,9 @@ def main(argv=None):
     p.add_argument("--eager", action="store_true")
     p.add_argument("--warmup", type=int, default=1)
     p.add_argument("--steps", type=int, default=1)
+    p.add_argument("--space-order", type=int, choices=[2, 4], default=2)
+    p.add_argument("--nodes", choices=["lobatto", "radau"], default="lobatto")
+    p.add_argument("--backward", action="store_true", help="then one adjoint step (sdc_step_backward)")
     a = p.parse_args(argv)
     seed = a.seed if a.seed is not None else (3 if a.config == "batch200" else 1)
 
@@ -53,6 +56,8 @@ def main(argv=None):
 
     from paper_1910_12578_gb300 import sdc
     P, U = workload(a.config, seed)
+    for q in (P if isinstance(P, list) else [P]):
+        q.space_order, q.nodes = a.space_order, a.nodes
     P0 = P[0] if isinstance(P, list) else P
     ctx = sdc.Context(P, prec=sdc.PREC_FP64 if a.prec == "fp64" else sdc.PREC_FP32_JAC)
     U0 = torch.from_numpy(U).cuda()
@@ -81,8 +86,18 @@ def main(argv=None):
         if i >= a.warmup:
             out.append(rec)
     torch.cuda.synchronize()
+    back = None
+    if a.backward:
+        gU, gUn = torch.ones_like(U0), torch.empty_like(U0)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        ctx.step_backward(U0, dt, gU, gUn)
+        ev[1].record()
+        torch.cuda.synchronize()
+        back = ev[0].elapsed_time(ev[1])
     print(json.dumps({"config": a.config, "seed": seed, "prec": a.prec, "variants": variants,
-                      "eager": a.eager, "steps": out}), flush=True)
+                      "space_order": a.space_order, "nodes": a.nodes, "eager": a.eager, "steps": out,
+                      "backward_ms": back}), flush=True)
     ctx.close()
     return 0
 
