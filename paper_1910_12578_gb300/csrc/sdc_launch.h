@@ -19,8 +19,10 @@ cudaError_t stencil_prepare(int dim, int nspec);  // raise the dynamic shared-me
 
 // dtm = (dt_dev ? *dt_dev * dt_frac : dtm_host)
 // variant 0: one zone per thread on a static grid; 1: persistent grid of
-// persistent_blocks fed by the zero-initialised device counter *queue (zones
-// of uneven cost balance across lanes); the group kernel ignores the variant.
+// persistent_blocks fed by the zero-initialised device counter *queue, one
+// zone per lane at a time (zones of uneven cost balance across lanes); 2: the
+// same grid and counter, 32 neighbouring zones per warp at a time.  The
+// 13-species group kernel: 4 lanes per zone (0) or 2 (1).
 int newton_variants(int nspec, int topo);
 bool newton_group_case(int nspec, int topo);  // the 13-species chain (a group of lanes per zone)
 cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, long long N, int dim,

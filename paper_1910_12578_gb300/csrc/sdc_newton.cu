@@ -162,6 +162,61 @@ newton_queue_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const doub
         if (hist[i]) atomicAdd(&stats->hist[i], (unsigned long long)hist[i]);
 }
 
+// Persistent grid fed by a device work queue at warp granularity: each warp
+// takes the next 32 zones with one atomic, solves them in lockstep as
+// newton_kernel does, and takes the next chunk when all 32 are done.  The
+// zones of a chunk are neighbours, so their iteration counts are alike (no
+// lanes left in other phases of their solves, as in newton_queue_kernel), and
+// warps that draw slow chunks do not hold up the rest of the grid.  Each
+// zone's arithmetic is that of newton_kernel: results agree bit for bit.
+template <int NS, int TOPO, typename MT>
+__global__ void __launch_bounds__(NEWTON_BLOCK)
+newton_warpqueue_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __restrict__ rhs,
+                        const double* guess, double* Uout, double* __restrict__ Rout,
+                        const double* __restrict__ dt_dev, double dt_frac, double dtm_host,
+                        int* __restrict__ zone_status, int* __restrict__ zone_iters, DevStats* __restrict__ stats,
+                        unsigned long long* __restrict__ queue) {
+    __shared__ unsigned int hist[64];
+    __shared__ unsigned long long blk_iters, blk_solves, blk_fails;
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) hist[i] = 0;
+    if (threadIdx.x == 0) { blk_iters = 0; blk_solves = 0; blk_fails = 0; }
+    __syncthreads();
+    const double dtm = dt_dev ? (*dt_dev) * dt_frac : dtm_host;
+    const int lane = threadIdx.x & 31;
+    unsigned long long my_iters = 0, my_solves = 0, my_fails = 0;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(queue, 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= (unsigned long long)N) break;  // the same for every lane of the warp
+        const long long z = (long long)base + lane;
+        if (z < N) {
+            ZoneState<NS> S;
+            double mom[3];
+            load_zone<NS, TOPO>(S, P, N, dim, z, rhs, guess, dtm, mom);
+            while (!S.done) zone_iterate<NS, TOPO, MT>(S, P, cfg, dtm);
+            store_zone<NS, TOPO>(S, P, N, dim, z, mom, Uout, Rout, zone_status, zone_iters);
+            atomicAdd(&hist[S.iters < 63 ? S.iters : 63], 1u);
+            my_iters += (unsigned long long)S.iters;
+            my_solves += 1;
+            if (S.status != ZONE_OK) my_fails += 1;
+        }
+    }
+    atomicAdd(&blk_iters, my_iters);
+    atomicAdd(&blk_solves, my_solves);
+    if (my_fails) atomicAdd(&blk_fails, my_fails);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (blk_solves) {
+            atomicAdd(&stats->iters_total, blk_iters);
+            atomicAdd(&stats->solves, blk_solves);
+        }
+        if (blk_fails) atomicAdd(&stats->fails, blk_fails);
+    }
+    for (int i = threadIdx.x; i < 64; i += blockDim.x)
+        if (hist[i]) atomicAdd(&stats->hist[i], (unsigned long long)hist[i]);
+}
+
 // L lanes per zone (alpha chain), GROUP_ZONES zones per block of 32 L threads;
 // zone state in dynamic shared memory.  Variant 0: L = 4, variant 1: L = 2
 // (half the lanes share each zone's split work, so instructions that every
@@ -312,8 +367,9 @@ bool newton_supported(int nspec, int topo) {
     return false;
 }
 
-// 7-and-fewer-species kernels: static grid (0) or persistent queue (1); 13-species chain: 4 (0) or 2 (1) lanes per zone
-int newton_variants(int, int) { return 2; }
+// 7-and-fewer-species kernels: static grid (0), persistent grid with a per-lane
+// work queue (1) or a per-warp one (2); 13-species chain: 4 (0) or 2 (1) lanes per zone
+int newton_variants(int nspec, int topo) { return newton_group_case(nspec, topo) ? 2 : 3; }
 
 int newton_persistent_blocks(const NetParams& P, int prec) {
     int dev = 0, sms = 0, per = 0;
@@ -354,11 +410,20 @@ cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, lo
         return cudaGetLastError();
     }
     const unsigned grid = (unsigned)((N + NEWTON_BLOCK - 1) / NEWTON_BLOCK);
-    const bool q = variant == 1 && queue != nullptr && persistent_blocks > 0;
+    const bool q = (variant == 1 || variant == 2) && queue != nullptr && persistent_blocks > 0;
     const unsigned pgrid = q ? (unsigned)(persistent_blocks < (long long)grid ? persistent_blocks : grid) : 0u;
 #define X(ns, tp)                                                                                          \
     if (P.nspec == ns && P.topo == tp) {                                                                   \
-        if (q) {                                                                                           \
+        if (q && variant == 2) {                                                                           \
+            if (prec == 0)                                                                                 \
+                newton_warpqueue_kernel<ns, tp, double><<<pgrid, NEWTON_BLOCK, 0, st>>>(                   \
+                    P, cfg, N, dim, rhs, guess, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status,        \
+                    zone_iters, stats, queue);                                                             \
+            else                                                                                           \
+                newton_warpqueue_kernel<ns, tp, float><<<pgrid, NEWTON_BLOCK, 0, st>>>(                    \
+                    P, cfg, N, dim, rhs, guess, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status,        \
+                    zone_iters, stats, queue);                                                             \
+        } else if (q) {                                                                                    \
             if (prec == 0)                                                                                 \
                 newton_queue_kernel<ns, tp, double><<<pgrid, NEWTON_BLOCK, 0, st>>>(                       \
                     P, cfg, N, dim, rhs, guess, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status,        \

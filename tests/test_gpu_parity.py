@@ -264,13 +264,14 @@ def test_newton_raphson_reciprocal_and_sqrt_within_two_ulp(torch_cuda):
 
 @pytest.mark.parametrize("name", ["box16", "ragged"])
 def test_kernel_variants_agree_bitwise(torch_cuda, name):
-    """The queue-fed persistent Newton kernel and the 8x8x4 tile shape do the
-    same arithmetic per zone and per face as the defaults: identical results."""
+    """The queue-fed persistent Newton kernels (per lane and per warp) and the
+    8x8x4 tile shape do the same arithmetic per zone and per face as the
+    defaults: identical results."""
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
     P, U = PROBS[name]
     outs = []
-    for sv, nv in ((0, 0), (0, 1), (1, 0), (1, 1)):
+    for sv, nv in ((0, 0), (0, 1), (0, 2), (1, 0), (1, 1), (1, 2)):
         ctx = sdc.Context(P)
         ctx.set_variants(sv, nv)
         Ud = dev(torch, U)
@@ -322,7 +323,7 @@ def test_autotune_keeps_U_and_picks_valid_variants(torch_cuda):
     torch.cuda.synchronize()
     assert np.array_equal(Ud.cpu().numpy(), U.reshape(Ud.shape))
     assert 0 <= t.stencil_choice < t.stencil_variants == 2
-    assert 0 <= t.newton_choice < t.newton_variants == 2
+    assert 0 <= t.newton_choice < t.newton_variants == 3   # static grid, lane queue, warp queue
     assert all(x > 0 for x in t.as_dict()["ms_newton"])
     o = O.Oracle(P)
     Uo, _ = o.step(U, 1e-3)
