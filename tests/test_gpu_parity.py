@@ -400,10 +400,11 @@ def test_full_size_config_step_parity(torch_cuda):
 
 def test_full_size_256_13species_sampled(torch_cuda):
     """256^3, 13 species (14 x 14 Jacobian), 3 nodes, 4 iterations: one full GPU
-    step at the benchmark size, checked zone by zone on samples.  One step
-    moves information at most 2 zones per advective evaluation, 18 zones in
-    all, so the oracle run on a 37^3 periodic sub-box centred on a sample zone
-    (initial data cut from the full box) gives that zone's exact result: the
+    step at the benchmark size, checked against the oracle on a contiguous 64^3
+    block at the hot spot and on scattered sample zones.  One step moves
+    information at most 2 zones per advective evaluation, 18 zones in all, so
+    the oracle run on a periodic sub-box with 18 zones of padding (initial data
+    cut from the full box) gives the exact result in its interior: the
     sub-box's own wrap-around only reaches its outer shell."""
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
@@ -418,6 +419,13 @@ def test_full_size_256_13species_sampled(torch_cuda):
         iy = np.arange(y - R, y + R + 1) % 256
         iz = np.arange(z - R, z + R + 1) % 256
         subs.append(U[:, iz][:, :, iy][:, :, :, ix].copy())
+    # and a contiguous 64^3 block at the hot spot, every zone and field, from the
+    # oracle run on its 100^3 periodic surrounding (18 zones of padding)
+    c0, h, pad = 96, 64, R
+    blk = np.arange(c0 - pad, c0 + h + pad)
+    Vb, _ = O.Oracle(W.Problem(dim=3, n=(h + 2 * pad,) * 3, dx=P.dx, gamma=P.gamma, net=P.net, n_nodes=3,
+                               n_iters=4)).step(U[:, blk][:, :, blk][:, :, :, blk].copy(), dt)
+    Vb = Vb.reshape(P.nvar, h + 2 * pad, h + 2 * pad, h + 2 * pad)[:, pad:pad + h, pad:pad + h, pad:pad + h]
     for prec, tol in ((0, TOL64), (1, TOL32)):
         ctx = sdc.Context(P, prec=prec)
         Ud = dev(torch, U)
@@ -428,6 +436,9 @@ def test_full_size_256_13species_sampled(torch_cuda):
         torch.cuda.empty_cache()
         scale = np.abs(G).reshape(P.nvar, -1).max(1)
         scale[5:] = np.maximum(scale[5:], 1e-6 * scale[0])   # trace species: 1e-18 rho absolute
+        Gb = G[:, c0:c0 + h, c0:c0 + h, c0:c0 + h]
+        err_b = (np.abs(Gb - Vb).reshape(P.nvar, -1).max(1) / scale).max()
+        assert err_b <= tol, (prec, err_b)
         for (x, y, z), sub in zip(samples, subs):
             Ps = W.Problem(dim=3, n=(2 * R + 1,) * 3, dx=P.dx, gamma=P.gamma, net=P.net, n_nodes=3, n_iters=4)
             Vs, _ = O.Oracle(Ps).step(sub, dt)
