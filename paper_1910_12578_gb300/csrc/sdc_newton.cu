@@ -341,11 +341,27 @@ reaction_source_kernel(NetParams P, long long N, int dim, const double* __restri
 
 // the 13-species chain: a group of lanes per zone (newton_group_kernel)
 bool newton_group_case(int nspec, int topo) { return nspec == 13 && topo == TOPO_CHAIN; }
+// the 5- and 7-species chains also have the group kernel, as Newton variant 3
+bool newton_small_group_case(int nspec, int topo) { return topo == TOPO_CHAIN && (nspec == 5 || nspec == 7); }
 
 cudaError_t newton_prepare(int nspec, int topo) {
+    cudaError_t e;
+    if (newton_small_group_case(nspec, topo)) {
+        if (nspec == 5) {
+            if ((e = cudaFuncSetAttribute(newton_group_kernel<5, double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)group_smem<5, double>())) != cudaSuccess)
+                return e;
+            return cudaFuncSetAttribute(newton_group_kernel<5, float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)group_smem<5, float>());
+        }
+        if ((e = cudaFuncSetAttribute(newton_group_kernel<7, double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)group_smem<7, double>())) != cudaSuccess)
+            return e;
+        return cudaFuncSetAttribute(newton_group_kernel<7, float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)group_smem<7, float>());
+    }
     if (!newton_group_case(nspec, topo)) return cudaSuccess;
     const int sd = (int)group_smem<13, double>(), sf = (int)group_smem<13, float>();
-    cudaError_t e;
     if ((e = cudaFuncSetAttribute(newton_group_kernel<13, double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   sd)) != cudaSuccess)
         return e;
@@ -368,8 +384,13 @@ bool newton_supported(int nspec, int topo) {
 }
 
 // 7-and-fewer-species kernels: static grid (0), persistent grid with a per-lane
-// work queue (1) or a per-warp one (2); 13-species chain: 4 (0) or 2 (1) lanes per zone
-int newton_variants(int nspec, int topo) { return newton_group_case(nspec, topo) ? 2 : 3; }
+// work queue (1) or a per-warp one (2), and for the 5- and 7-species chains a
+// group of 4 lanes per zone as for 13 species (3); 13-species chain: 4 (0) or
+// 2 (1) lanes per zone
+int newton_variants(int nspec, int topo) {
+    if (newton_group_case(nspec, topo)) return 2;
+    return newton_small_group_case(nspec, topo) ? 4 : 3;
+}
 
 int newton_persistent_blocks(const NetParams& P, int prec) {
     int dev = 0, sms = 0, per = 0;
@@ -407,6 +428,21 @@ cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, lo
             else SDC_GROUP_LAUNCH(float, 4);
         }
 #undef SDC_GROUP_LAUNCH
+        return cudaGetLastError();
+    }
+    if (variant == 3 && newton_small_group_case(P.nspec, P.topo)) {
+        const unsigned ggrid = (unsigned)((N + GROUP_ZONES - 1) / GROUP_ZONES);
+#define SDC_SMALL_GROUP_LAUNCH(NSV, MT)                                                                            \
+    newton_group_kernel<NSV, MT, 4><<<ggrid, 128, group_smem<NSV, MT>(), st>>>(                                      \
+        P, cfg, N, dim, rhs, guess, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, zone_iters, stats)
+        if (P.nspec == 5) {
+            if (prec == 0) SDC_SMALL_GROUP_LAUNCH(5, double);
+            else SDC_SMALL_GROUP_LAUNCH(5, float);
+        } else {
+            if (prec == 0) SDC_SMALL_GROUP_LAUNCH(7, double);
+            else SDC_SMALL_GROUP_LAUNCH(7, float);
+        }
+#undef SDC_SMALL_GROUP_LAUNCH
         return cudaGetLastError();
     }
     const unsigned grid = (unsigned)((N + NEWTON_BLOCK - 1) / NEWTON_BLOCK);

@@ -313,6 +313,35 @@ def test_13species_group_widths_match_oracle(torch_cuda, prec):
     assert rel_err(outs[1], outs[0], P.nvar, P.dim).max() <= (1e-13 if prec == 0 else TOL32)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_group_per_zone_newton_for_7_species(torch_cuda, prec):
+    """Newton variant 3 for the 7-species chain: a group of 4 lanes per zone
+    (shared memory, warp shuffles), the 13-species kernel's scheme.  Against the
+    oracle over two steps, and against the thread-per-zone kernel to round-off
+    (the groups' partial sums associate differently)."""
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = PROBS["box16"]
+    o = O.Oracle(P)
+    dt = o.cfl_dt(U)
+    V = U.copy()
+    for _ in range(2):
+        V, _ = o.step(V, dt)
+    outs = []
+    for nv in (0, 3):
+        ctx = sdc.Context(P, prec=prec)
+        ctx.set_variants(0, nv)
+        Ud = dev(torch, U)
+        for _ in range(2):
+            st = ctx.step(Ud, dt)
+        assert st.n_fail == 0
+        outs.append(Ud.cpu().numpy())
+    tol = TOL64 if prec == 0 else TOL32
+    for g in outs:
+        assert rel_err(g, V, P.nvar, P.dim).max() <= tol
+    assert rel_err(outs[1], outs[0], P.nvar, P.dim).max() <= (1e-13 if prec == 0 else TOL32)
+
+
 def test_autotune_keeps_U_and_picks_valid_variants(torch_cuda):
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
@@ -323,7 +352,7 @@ def test_autotune_keeps_U_and_picks_valid_variants(torch_cuda):
     torch.cuda.synchronize()
     assert np.array_equal(Ud.cpu().numpy(), U.reshape(Ud.shape))
     assert 0 <= t.stencil_choice < t.stencil_variants == 2
-    assert 0 <= t.newton_choice < t.newton_variants == 3   # static grid, lane queue, warp queue
+    assert 0 <= t.newton_choice < t.newton_variants == 4   # static grid, lane queue, warp queue, 4-lane groups
     assert all(x > 0 for x in t.as_dict()["ms_newton"])
     o = O.Oracle(P)
     Uo, _ = o.step(U, 1e-3)
