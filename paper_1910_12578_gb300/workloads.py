@@ -177,6 +177,45 @@ def config_box(n: int = 64, nspec: int = 7, n_nodes: int = 3, n_iters: int = 3,
     return P, hot_spot_state(P, amp, T0=T0)
 
 
+def shock_tube_state(P: Problem, axis: int, left, right, x0: float = 0.5) -> np.ndarray:
+    """Planar Riemann problem along `axis`: (rho, u_axis, p) = `left` where the
+    scaled coordinate x_axis / L is below x0, `right` above it; the other
+    velocity components are zero and X_0 = 1.  The box is periodic, so a
+    second, mirrored discontinuity sits at x_axis = 0."""
+    shape = (P.n[2], P.n[1], P.n[0])
+    c = _centres(P.n[axis], P.dx[axis]) / (P.n[axis] * P.dx[axis])
+    side = (c < x0).reshape([-1 if a == axis else 1 for a in (2, 1, 0)])
+    side = np.broadcast_to(side, shape)
+    rho = np.where(side, left[0], right[0]).astype(np.float64)
+    un = np.where(side, left[1], right[1]).astype(np.float64)
+    p = np.where(side, left[2], right[2]).astype(np.float64)
+    vel = [un if d == axis else np.zeros(shape) for d in range(P.dim)]
+    X = [np.ones(shape)] + [np.zeros(shape) for _ in range(P.net.nspec - 1)]
+    U = conserved_from(P.gamma, rho, vel, p / rho, X)
+    return U
+
+
+SOD_LEFT = (1.0, 0.0, 1.0)      # (rho, u, p), Sod's shock tube, gamma = 1.4
+SOD_RIGHT = (0.125, 0.0, 0.1)
+
+
+def config_sod(n: int = 128, dim: int = 1, axis: int = 0, nspec: int = 7, seed: int = 0,
+               k0: float = 1e3) -> tuple:
+    """Sod's shock tube on the unit interval (dim = 1, A -> B with rate
+    k0 exp(-10/T), so the shock-heated gas reacts; k0 = 0 leaves it inert) or
+    across an n^3 periodic box along `axis` (dim = 3, seeded alpha chain);
+    gamma = 1.4, 2 nodes, 2 iterations."""
+    if dim == 1:
+        net = decay_network(k0=k0)
+        P = Problem(dim=1, n=(n, 1, 1), dx=(1.0 / n, 1.0, 1.0), gamma=1.4, net=net, n_nodes=2, n_iters=2)
+    else:
+        net = alpha_chain(nspec, np.random.default_rng(seed))
+        h = 1.0 / n
+        P = Problem(dim=3, n=(n, n, n), dx=(h, h, h), gamma=1.4, net=net, n_nodes=2, n_iters=2)
+    U = shock_tube_state(P, axis, SOD_LEFT, SOD_RIGHT)
+    return P, U.reshape(P.nvar, P.n[2], P.n[1], P.n[0])
+
+
 def batched_boxes(nbox: int = 200, nspec: int = 7, seed: int = 0,
                   edges=(16, 24, 32, 48, 64)) -> tuple:
     """Ragged batch: per box, edges drawn from `edges` per axis, hot-spot

@@ -62,6 +62,11 @@ def problems():
     P, U = W.config_box(n=16, nspec=13, n_iters=4, seed=0, T0=0.5)
     P.nodes = "radau"
     out["box16_13_radau"] = (P, U)
+    # Sod's shock tube: 1D with the shock-heated gas reacting, and planar across
+    # a 16^3 box along y and along z (limiter clipping, HLLC on both sides of a contact)
+    out["sod1d"] = W.config_sod(n=128, dim=1)
+    out["sod3d_y"] = W.config_sod(n=16, dim=3, axis=1)
+    out["sod3d_z"] = W.config_sod(n=16, dim=3, axis=2, nspec=13)
     # fourth-order finite-volume operators
     for name in ("1d", "box16", "ragged", "box16_13"):
         P, U = out[name]
@@ -74,7 +79,8 @@ def problems():
 PROBS = problems()
 
 
-@pytest.mark.parametrize("name", ["1d", "box16", "ragged", "1d_o4", "box16_o4", "ragged_o4"])
+@pytest.mark.parametrize("name", ["1d", "box16", "ragged", "sod1d", "sod3d_y", "sod3d_z", "1d_o4", "box16_o4",
+                                  "ragged_o4"])
 def test_advective_term_parity(torch_cuda, name):
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
@@ -178,7 +184,9 @@ def test_react_newton_parity(torch_cuda, name, k_iters, prec):
                                               ("1d_radau", 10, 0), ("box16_radau", 2, 0), ("box16_radau", 1, 1),
                                               ("box16_radau2", 2, 0), ("box16_13_radau", 1, 0),
                                               ("1d_o4", 4, 0), ("box16_o4", 2, 0), ("box16_o4", 1, 1),
-                                              ("ragged_o4", 1, 0), ("box16_13_o4", 1, 0)])
+                                              ("ragged_o4", 1, 0), ("box16_13_o4", 1, 0),
+                                              ("sod1d", 20, 0), ("sod1d", 20, 1), ("sod3d_y", 3, 0),
+                                              ("sod3d_y", 2, 1), ("sod3d_z", 2, 0)])
 def test_step_parity(torch_cuda, name, nsteps, prec):
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
@@ -199,7 +207,8 @@ def test_step_parity(torch_cuda, name, nsteps, prec):
 
 
 @pytest.mark.parametrize("name,nsteps,prec", [("1d", 4, 0), ("box16", 2, 0), ("box16", 1, 1), ("box16_radau", 1, 0),
-                                              ("box16_13", 1, 0), ("box16_o4", 1, 0)])
+                                              ("box16_13", 1, 0), ("box16_o4", 1, 0),
+                                              ("sod1d", 10, 0)])
 def test_strang_step_parity(torch_cuda, name, nsteps, prec):
     """sdc_step_strang (reactions dt/2, advection dt, reactions dt/2 by the same
     SDC step with one operator off) against the oracle's split step."""

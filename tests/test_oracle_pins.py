@@ -136,6 +136,128 @@ def test_hllc_resolves_contact():
     assert F[3:] == pytest.approx(1.0 * u * qL[3:], rel=1e-14)
 
 
+def _exact_riemann(left, right, g, xi):
+    """Exact solution of the 1D Euler Riemann problem for a gamma-law gas
+    (Toro, chapter 4): star pressure by Newton on f_L(p) + f_R(p) + du = 0
+    (shock branch for p above the side's pressure, rarefaction branch below),
+    then (rho, u, p) sampled along the rays xi = x / t.  Test-only and
+    independent of the oracle's HLLC."""
+    (rl, ul, pl), (rr, ur, pr) = left, right
+    cl, cr = math.sqrt(g * pl / rl), math.sqrt(g * pr / rr)
+    gm, gp = g - 1.0, g + 1.0
+
+    def f(p, rk, pk, ck):
+        if p > pk:
+            A, B = 2.0 / (gp * rk), gm / gp * pk
+            s = math.sqrt(A / (p + B))
+            return (p - pk) * s, s * (1.0 - 0.5 * (p - pk) / (p + B))
+        r = p / pk
+        return 2.0 * ck / gm * (r ** (0.5 * gm / g) - 1.0), r ** (-0.5 * gp / g) / (rk * ck)
+
+    p = 0.5 * (pl + pr)
+    for _ in range(60):
+        fl, dl = f(p, rl, pl, cl)
+        fr, dr = f(p, rr, pr, cr)
+        step = (fl + fr + ur - ul) / (dl + dr)
+        p = max(p - step, 1e-14)
+        if abs(step) <= 1e-15 * p:
+            break
+    fl, _ = f(p, rl, pl, cl)
+    fr, _ = f(p, rr, pr, cr)
+    u = 0.5 * (ul + ur) + 0.5 * (fr - fl)
+
+    def side(s, rk, uk, pk, ck, sgn):
+        # sgn = +1 for the left wave (seen as s increases), -1 for the right one (mirrored)
+        ss, us = sgn * s, sgn * uk
+        if p > pk:
+            speed = us - ck * math.sqrt(0.5 * gp / g * p / pk + 0.5 * gm / g)
+            if ss < speed:
+                return rk, uk, pk
+            return rk * (p / pk + gm / gp) / (gm / gp * p / pk + 1.0), u, p
+        head, tail = us - ck, sgn * u - ck * (p / pk) ** (0.5 * gm / g)
+        if ss <= head:
+            return rk, uk, pk
+        if ss >= tail:
+            return rk * (p / pk) ** (1.0 / g), u, p
+        c = 2.0 / gp * (ck + 0.5 * gm * (us - ss))
+        return rk * (c / ck) ** (2.0 / gm), sgn * 2.0 / gp * (ck + 0.5 * gm * us + ss), pk * (c / ck) ** (2.0 * g / gm)
+
+    out = np.array([side(s, rl, ul, pl, cl, 1.0) if s <= u else side(s, rr, ur, pr, cr, -1.0) for s in xi]).T
+    return out, p, u
+
+
+def test_exact_riemann_solver_star_state_golden():
+    """The test's exact Riemann solver reproduces the tabulated star state of Sod's problem."""
+    gold = {}
+    with open(os.path.join(GOLDEN, "sod_star_state.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                gold[k] = float(v)
+    xi = np.array([-0.01, 0.5, 1.2, 1.5])   # just left of the contact, in the shocked gas
+    sol, p, u = _exact_riemann(W.SOD_LEFT, W.SOD_RIGHT, 1.4, xi)
+    assert p == pytest.approx(gold["p_star"], abs=6e-6)
+    assert u == pytest.approx(gold["u_star"], abs=6e-6)
+    assert sol[0, 0] == pytest.approx(gold["rho_star_left"], abs=6e-6)
+    assert sol[0, 2] == pytest.approx(gold["rho_star_right"], abs=6e-6)
+    assert sol[2, 1] == pytest.approx(p, rel=1e-14) and sol[1, 1] == pytest.approx(u, rel=1e-14)
+
+
+def _sod_run(n, tf=0.1):
+    P, U = W.config_sod(n=n, dim=1, k0=0.0)
+    o = O.Oracle(P)
+    t, V = 0.0, U
+    while t < tf - 1e-14:
+        dt = min(o.cfl_dt(V), tf - t)
+        V, _ = o.step(V, dt)
+        t += dt
+    V = V.reshape(P.nvar, n)
+    x = (np.arange(n) + 0.5) / n
+    m = (x > 0.25) & (x < 0.75)    # the mirrored Riemann problem at x = 0 stays outside
+    ex, _, _ = _exact_riemann(W.SOD_LEFT, W.SOD_RIGHT, P.gamma, (x[m] - 0.5) / tf)
+    rho, u = V[0, m], V[1, m] / V[0, m]
+    p = (P.gamma - 1.0) * (V[2, m] - 0.5 * V[1, m] ** 2 / V[0, m])
+    return np.array([np.abs(q - e).mean() * 0.5 for q, e in zip((rho, u, p), ex)])
+
+
+def test_sod_shock_tube_converges_to_exact_solution():
+    """PLM + MC + HLLC under the SDC step (section 2) on Sod's shock tube at
+    t = 0.1: the L1 error against the exact Riemann solution over [0.25, 0.75]
+    is small and falls at about first order (the rate that a shock and a
+    contact allow) from 100 to 200 zones."""
+    e1, e2 = _sod_run(100), _sod_run(200)
+    assert (e1 < [5.5e-3, 9.5e-3, 4.0e-3]).all(), e1
+    assert (e1 / e2 > 1.6).all(), e1 / e2
+
+
+def test_planar_shock_tube_same_along_every_axis():
+    """A planar shock tube across a 3D box gives, along each axis, the 1D result
+    with the velocity component permuted (transverse flux differences vanish)."""
+    net = W.decay_network()
+    P1 = W.Problem(dim=1, n=(16, 1, 1), dx=(1 / 16, 1, 1), gamma=1.4, net=net, n_nodes=2, n_iters=2)
+    U1 = W.shock_tube_state(P1, 0, W.SOD_LEFT, W.SOD_RIGHT)
+    o1 = O.Oracle(P1)
+    V1, dts1 = U1.reshape(P1.nvar, 1, 1, 16), None
+    for axis in range(3):
+        P = W.Problem(dim=3, n=(16, 16, 16), dx=(1 / 16,) * 3, gamma=1.4, net=net, n_nodes=2, n_iters=2)
+        U = W.shock_tube_state(P, axis, W.SOD_LEFT, W.SOD_RIGHT)
+        V, dts, _ = O.Oracle(P).run(U, 3)
+        if dts1 is None:
+            # the 3D CFL step counts the sound speed along all three axes: the 1D run takes the same steps
+            for dt in dts:
+                V1, _ = o1.step(V1, dt)
+            V1, dts1 = V1.reshape(P1.nvar, 16), dts
+        assert dts == pytest.approx(dts1, rel=1e-15)
+        V = np.moveaxis(V.reshape(P.nvar, 16, 16, 16), 3 - axis, -1)
+        line = V[:, 5, 11, :]
+        assert np.abs(V - line[:, None, None, :]).max() == 0.0        # stays planar
+        for d in range(3):
+            if d != axis:
+                assert np.abs(line[1 + d]).max() == 0.0                # no transverse momentum
+        got = np.concatenate([line[[0, 1 + axis, 4]], line[5:]])
+        assert np.abs(got - V1).max() <= 1e-14 * np.abs(V1).max()
+
+
 # ---------------------------------------------------------------- Jacobian
 @pytest.mark.parametrize("which", ["decay", "chain7", "chain13"])
 def test_jacobian_matches_finite_differences(which):
