@@ -189,14 +189,18 @@ sdc_status sdc_selftest_math(const double* x, long long n, double* rcp_out, doub
 /* Kernel variants of a context, chosen by measurement.
    stencil: tile shape of the advective-term kernel (0: 8^3 zones, 576 threads,
    one face per thread per direction; 1: 8 x 8 x 4 zones, 320 threads; one shape
-   only in 1D and for 13 species).  newton: 0 = one zone per thread on a static
-   grid; 1 = a persistent grid fed by a device work queue, each lane taking the
-   next zone when its own is solved, so zones with many Newton iterations do not
-   hold their warp (the 13-species kernel has one variant).  Defaults: 0, 0. */
+   only in 1D and for 13 species).  newton, networks of up to 7 species: 0 = one
+   zone per thread on a static grid; 1 = a persistent grid fed by a device work
+   queue, each lane taking the next zone when its own is solved, so zones with
+   many Newton iterations do not hold their warp; 2 = the same with a queue of
+   32-zone chunks per warp; 3 (5- and 7-species chains) = a group of 4 lanes per
+   zone.  13-species chain: 0 / 1 = a group of 4 / 2 lanes per zone; 2, 3, 4 =
+   variants 0, 1, 2 of the smaller networks.  Defaults: 0, 0. */
+#define SDC_MAX_VARIANTS 8
 typedef struct {
     int stencil_variants, newton_variants;  /* candidates tried */
     int stencil_choice, newton_choice;      /* chosen */
-    float ms_stencil[4], ms_newton[4];      /* per candidate: summed event time of one step */
+    float ms_stencil[SDC_MAX_VARIANTS], ms_newton[SDC_MAX_VARIANTS];  /* per candidate: event time of one step */
 } sdc_tuning;
 
 /* Time one eager step per candidate on a scratch copy of U (U is not changed)

@@ -610,7 +610,7 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     if ((e = ctx_alloc(c, (void**)&c->d_boxes, sizeof(BoxDev) * nbox)) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->d_tiles, sizeof(TileDev) * c->tiles_capacity)) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->d_queue, sizeof(unsigned long long) * QUEUE_SLOTS)) != cudaSuccess) return fail(e);
-    c->persistent_blocks = newton_group_case(net->nspec, topo_used) ? 0 : newton_persistent_blocks(P, c->prec);
+    c->persistent_blocks = newton_persistent_blocks(P, c->prec);
     if ((e = ctx_alloc(c, (void**)&c->d_dt, 2 * sizeof(double))) != cudaSuccess) return fail(e);
     c->d_dt_half = c->d_dt + 1;
     if ((e = ctx_alloc(c, (void**)&c->d_stats, sizeof(DevStats))) != cudaSuccess) return fail(e);
@@ -795,6 +795,10 @@ sdc_status sdc_autotune(sdc_ctx* ctx, const double* U, double dt, sdc_tuning* ou
     memset(&t, 0, sizeof(t));
     t.stencil_variants = stencil_variants(ctx->dim, ctx->nspec);
     t.newton_variants = newton_variants(ctx->nspec, ctx->P.topo);
+    if (t.stencil_variants > SDC_MAX_VARIANTS || t.newton_variants > SDC_MAX_VARIANTS) {
+        cudaFree(scratch);
+        return SDC_ERR_INVALID_ARG;
+    }
     sdc_status st = SDC_OK;
     // one eager step per candidate (after one warm-up step); the step's stencil
     // time depends only on the tile shape and its Newton time only on the

@@ -207,6 +207,146 @@ __device__ __forceinline__ void build_matrix(const NetParams& P, double rho, dou
     }
 }
 
+// The alpha chain's Newton matrix M = c I - dtm dR/dw in bordered form.  In the
+// elimination order (X_1 .. X_{ns-1} | X_0, E) the chain block is lower
+// bidiagonal (species i is made by reaction i-1 from species i-1 and used by
+// reaction i); the alpha and energy rows and columns form the border.  Chain
+// index k stands for species X_{k+1} (w index 2 + k).
+template <int NS, typename MT>
+struct ChainSys {
+    static constexpr int NC = NS - 1;
+    MT bd[NC], bs[NC];      // M[X_k][X_k], M[X_k][X_{k-1}] (bs[0] unused)
+    MT uE[NC], uA[NC];      // M[X_k][E], M[X_k][X_0]
+    MT vE[NC], vA[NC];      // M[E][X_k], M[X_0][X_k]
+    MT dEE, dEA, dAE, dAA;  // M[E][E], M[E][X_0], M[X_0][E], M[X_0][X_0]
+};
+
+// Entries of ChainSys, each formed by the same operations, in the same order,
+// as the dense build_matrix forms it (the structural zeros are not stored).
+template <int NS, typename MT>
+__device__ __forceinline__ void build_chain(const NetParams& P, const double* ym, const double* k, const double* dk,
+                                            const double* Y, double c, double dtm, double rho, double inv_rho,
+                                            ChainSys<NS, MT>& A) {
+    constexpr int NC = NS - 1;
+    constexpr int NR = NS - 1;
+#pragma unroll
+    for (int q = 0; q < NC; q++) {
+        A.bd[q] = (MT)c;
+        A.bs[q] = A.uE[q] = A.uA[q] = A.vE[q] = A.vA[q] = (MT)0;
+    }
+    A.dEE = A.dAA = (MT)c;
+    A.dEA = A.dAE = (MT)0;
+    const MT dTdE = (MT)(P.gm1 * inv_rho);
+    const MT s = (MT)(dtm * rho);
+#pragma unroll
+    for (int j = 0; j < NR; j++) {
+        MT drE, drX0, drXj = (MT)0;
+        if (j == 0) {
+            MT y0 = (MT)Y[0];
+            drE = (MT)dk[0] * (y0 * y0 * y0) * dTdE;
+            drX0 = (MT)k[0] * ((MT)3 * y0 * y0) * (MT)ym[0];
+        } else {
+            MT y0 = (MT)Y[0], yj = (MT)Y[j];
+            drE = (MT)dk[j] * (yj * y0) * dTdE;
+            drXj = (MT)k[j] * y0 * (MT)ym[j];
+            drX0 = (MT)k[j] * yj * (MT)ym[0];
+        }
+        const MT qj = s * (MT)P.Q[j];
+        A.dEE -= qj * drE;
+        A.dEA -= qj * drX0;
+        if (j > 0) A.vE[j - 1] -= qj * drXj;
+        if (j == 0) {
+            const MT a0 = s * (MT)P.mass[0] * (MT)(-3.0), a1 = s * (MT)P.mass[1];
+            A.dAE -= a0 * drE;   A.dAA -= a0 * drX0;
+            A.uE[0] -= a1 * drE; A.uA[0] -= a1 * drX0;
+        } else {
+            const MT am = s * (MT)P.mass[j] * (MT)(-1.0);
+            const MT a0 = s * (MT)P.mass[0] * (MT)(-1.0);
+            const MT ap = s * (MT)P.mass[j + 1];
+            A.uE[j - 1] -= am * drE;  A.uA[j - 1] -= am * drX0;  A.bd[j - 1] -= am * drXj;
+            A.dAE -= a0 * drE;        A.dAA -= a0 * drX0;        A.vA[j - 1] -= a0 * drXj;
+            if (j < NC) { A.uE[j] -= ap * drE; A.uA[j] -= ap * drX0; A.bs[j] -= ap * drXj; }
+        }
+    }
+}
+
+__device__ __forceinline__ long long abs_pattern(double x) { return __double_as_longlong(x) & ABS_MASK; }
+__device__ __forceinline__ int abs_pattern(float x) { return __float_as_int(x) & 0x7fffffff; }
+
+// Solve M d = b for the bordered chain system (b in w order, overwritten by d).
+// Gaussian elimination in the order (X_1 .. X_{ns-1} | X_0, E): at chain
+// column k the pivot is the larger (ties: the first) of the row carried from
+// the previous step and chain row k+1, so that the bidiagonal band keeps its
+// shape and every chain step costs O(1); the border rows are eliminated along
+// and the remaining 2 x 2 border block is solved with partial pivoting.  The
+// solution equals the dense pivoted LU's to rounding.  Returns false on a zero
+// pivot.
+template <int NS, typename MT>
+__device__ __forceinline__ bool chain_solve(const ChainSys<NS, MT>& A, MT* b) {
+    constexpr int NC = NS - 1;
+    MT pip[NC], pe[NC], puE[NC], puA[NC], pg[NC];  // pivot rows: 1/p, entry at k+1, border columns, rhs
+    MT cp = A.bd[0], cuE = A.uE[0], cuA = A.uA[0], cg = b[2];  // the carried row
+    MT dEE = A.dEE, dEA = A.dEA, dAE = A.dAE, dAA = A.dAA, gE = b[0], gA = b[1];
+    MT wE = A.vE[0], wA = A.vA[0];  // border rows at the current column
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < NC; k++) {
+        MT p, e, quE, quA, qg;
+        if (k + 1 < NC) {
+            const MT ns_ = A.bs[k + 1], nd = A.bd[k + 1], nuE = A.uE[k + 1], nuA = A.uA[k + 1], ng = b[3 + k];
+            const bool sw = abs_pattern(ns_) > abs_pattern(cp);
+            p = sw ? ns_ : cp;
+            e = sw ? nd : (MT)0;
+            quE = sw ? nuE : cuE;
+            quA = sw ? nuA : cuA;
+            qg = sw ? ng : cg;
+            const MT op = sw ? cp : ns_, od = sw ? (MT)0 : nd;
+            const MT ouE = sw ? cuE : nuE, ouA = sw ? cuA : nuA, og = sw ? cg : ng;
+            ok = ok && (p != (MT)0);
+            const MT ip = (sizeof(MT) == 8) ? (MT)rcp_nr((double)p) : (MT)1 / p;
+            pip[k] = ip;
+            const MT l = op * ip;
+            cp = od - l * e;
+            cuE = ouE - l * quE;
+            cuA = ouA - l * quA;
+            cg = og - l * qg;
+        } else {
+            p = cp; e = (MT)0; quE = cuE; quA = cuA; qg = cg;
+            ok = ok && (p != (MT)0);
+            pip[k] = (sizeof(MT) == 8) ? (MT)rcp_nr((double)p) : (MT)1 / p;
+        }
+        pe[k] = e; puE[k] = quE; puA[k] = quA; pg[k] = qg;
+        const MT lE = wE * pip[k], lA = wA * pip[k];
+        dEE -= lE * quE; dEA -= lE * quA; gE -= lE * qg;
+        dAE -= lA * quE; dAA -= lA * quA; gA -= lA * qg;
+        if (k + 1 < NC) {
+            wE = A.vE[k + 1] - lE * e;
+            wA = A.vA[k + 1] - lA * e;
+        }
+    }
+    // 2 x 2 border block, partial pivoting
+    const bool sw = abs_pattern(dAE) > abs_pattern(dEE);
+    const MT a = sw ? dAE : dEE, bb = sw ? dAA : dEA, c2 = sw ? dEE : dAE, d2 = sw ? dEA : dAA;
+    const MT r1 = sw ? gA : gE, r2 = sw ? gE : gA;
+    ok = ok && (a != (MT)0);
+    const MT ia = (sizeof(MT) == 8) ? (MT)rcp_nr((double)a) : (MT)1 / a;
+    const MT l = c2 * ia;
+    const MT s22 = d2 - l * bb;
+    ok = ok && (s22 != (MT)0);
+    const MT xA = (r2 - l * r1) * ((sizeof(MT) == 8) ? (MT)rcp_nr((double)s22) : (MT)1 / s22);
+    const MT xE = (r1 - bb * xA) * ia;
+    b[0] = xE;
+    b[1] = xA;
+    MT xn = (MT)0;
+#pragma unroll
+    for (int k = NC - 1; k >= 0; k--) {
+        const MT x = (pg[k] - pe[k] * xn - puE[k] * xE - puA[k] * xA) * pip[k];
+        b[2 + k] = x;
+        xn = x;
+    }
+    return ok;
+}
+
 // In-place LU with partial pivoting (largest |entry|, ties to the lowest row)
 // and solve of M d = b; b is overwritten with d.  Row exchanges are done with
 // predicated selects so that M stays in registers.  Returns false on a zero pivot.

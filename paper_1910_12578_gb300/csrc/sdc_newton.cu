@@ -337,7 +337,8 @@ reaction_source_kernel(NetParams P, long long N, int dim, const double* __restri
     X(4, TOPO_GENERIC)      \
     X(5, TOPO_GENERIC)      \
     X(5, TOPO_CHAIN)        \
-    X(7, TOPO_CHAIN)
+    X(7, TOPO_CHAIN)        \
+    X(13, TOPO_CHAIN)
 
 // the 13-species chain: a group of lanes per zone (newton_group_kernel)
 bool newton_group_case(int nspec, int topo) { return nspec == 13 && topo == TOPO_CHAIN; }
@@ -386,9 +387,10 @@ bool newton_supported(int nspec, int topo) {
 // 7-and-fewer-species kernels: static grid (0), persistent grid with a per-lane
 // work queue (1) or a per-warp one (2), and for the 5- and 7-species chains a
 // group of 4 lanes per zone as for 13 species (3); 13-species chain: 4 (0) or
-// 2 (1) lanes per zone
+// 2 (1) lanes per zone, or one zone per thread as for the smaller networks on
+// a static grid (2), with a per-lane (3) or a per-warp (4) work queue
 int newton_variants(int nspec, int topo) {
-    if (newton_group_case(nspec, topo)) return 2;
+    if (newton_group_case(nspec, topo)) return 5;
     return newton_small_group_case(nspec, topo) ? 4 : 3;
 }
 
@@ -415,7 +417,7 @@ cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, lo
                           int* zone_iters, DevStats* stats, cudaStream_t st, int variant,
                           unsigned long long* queue, int persistent_blocks) {
     if (N <= 0) return cudaSuccess;
-    if (P.nspec == 13 && P.topo == TOPO_CHAIN) {
+    if (newton_group_case(P.nspec, P.topo) && variant < 2) {
         const unsigned ggrid = (unsigned)((N + GROUP_ZONES - 1) / GROUP_ZONES);
 #define SDC_GROUP_LAUNCH(MT, L)                                                                                    \
     newton_group_kernel<13, MT, L><<<ggrid, 32 * L, group_smem<13, MT>(), st>>>(                                   \
@@ -445,6 +447,8 @@ cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, lo
 #undef SDC_SMALL_GROUP_LAUNCH
         return cudaGetLastError();
     }
+    // one zone per thread; the 13-species chain numbers these variants from 2
+    if (newton_group_case(P.nspec, P.topo)) variant -= 2;
     const unsigned grid = (unsigned)((N + NEWTON_BLOCK - 1) / NEWTON_BLOCK);
     const bool q = (variant == 1 || variant == 2) && queue != nullptr && persistent_blocks > 0;
     const unsigned pgrid = q ? (unsigned)(persistent_blocks < (long long)grid ? persistent_blocks : grid) : 0u;

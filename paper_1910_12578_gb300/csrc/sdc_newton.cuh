@@ -11,9 +11,11 @@
 //   h >= 1e3 returns to Newton mode; converged when an admissible Newton step
 //   has max(|d(rho E)|/|rho E|, max_i |d(rho X_i)|/rho) <= rtol (taken even if
 //   the residual grew by round-off at the root).
-// One thread owns one zone; the dense matrix lives in registers as MT
-// (double: FP64 path; float: FP32 Jacobian / LU with FP64 residual and update,
-// so that Newton acts as iterative refinement).
+// One thread owns one zone; the matrix lives in registers as MT (double: FP64
+// path; float: FP32 Jacobian / LU with FP64 residual and update, so that Newton
+// acts as iterative refinement): dense with a pivoted LU for a general network,
+// in the bordered bidiagonal form of the alpha chain (build_chain, chain_solve)
+// for the chain.
 #pragma once
 #include "sdc_dev.cuh"
 
@@ -110,12 +112,21 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     constexpr int NR = NS - 1;
     S.iters++;
     const double c = S.newton ? 1.0 : 1.0 + rcp_nr(S.h);
-    MT M[N][N];
-    build_matrix<NS, TOPO, MT>(P, S.rho, S.inv_rho, S.ym, S.k, S.dk, S.Y, c, dtm, M);
     MT dv[N];
 #pragma unroll
     for (int r = 0; r < N; r++) dv[r] = (MT)S.G[r];
-    if (!lu_solve<N, MT, MT>(M, dv)) {
+    bool solved;
+    if constexpr (TOPO == TOPO_CHAIN) {
+        // the chain's sparsity: bordered bidiagonal system, O(n) elimination
+        ChainSys<NS, MT> A;
+        build_chain<NS, MT>(P, S.ym, S.k, S.dk, S.Y, c, dtm, S.rho, S.inv_rho, A);
+        solved = chain_solve<NS, MT>(A, dv);
+    } else {
+        MT M[N][N];
+        build_matrix<NS, TOPO, MT>(P, S.rho, S.inv_rho, S.ym, S.k, S.dk, S.Y, c, dtm, M);
+        solved = lu_solve<N, MT, MT>(M, dv);
+    }
+    if (!solved) {
         S.status = ZONE_SINGULAR;
         S.done = true;
         return;

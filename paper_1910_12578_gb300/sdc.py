@@ -63,9 +63,13 @@ class Stats(C.Structure):
                 "n_fail": self.n_fail, "hist": list(self.hist)}
 
 
+MAX_VARIANTS = 8   # SDC_MAX_VARIANTS of sdc.h
+
+
 class Tuning(C.Structure):
     _fields_ = [("stencil_variants", C.c_int), ("newton_variants", C.c_int), ("stencil_choice", C.c_int),
-                ("newton_choice", C.c_int), ("ms_stencil", C.c_float * 4), ("ms_newton", C.c_float * 4)]
+                ("newton_choice", C.c_int), ("ms_stencil", C.c_float * MAX_VARIANTS),
+                ("ms_newton", C.c_float * MAX_VARIANTS)]
 
     def as_dict(self):
         return {"stencil_variants": self.stencil_variants, "newton_variants": self.newton_variants,

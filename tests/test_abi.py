@@ -51,3 +51,31 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu():
     assert L.sdc_init_box(boxes, 1, ctypes.byref(net), ctypes.byref(prm), None, ctypes.byref(out)) == \
         sdc.SDC_ERR_INVALID_ARG
     assert out.value is None
+
+
+def test_binding_structures_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets that
+    a C compiler gives the header's struct (compiled here with gcc)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    from paper_1910_12578_gb300 import sdc
+    pairs = {"sdc_box": sdc.Box, "sdc_network": sdc.Network, "sdc_params": sdc.Params, "sdc_stats": sdc.Stats,
+             "sdc_profile": sdc.Profile, "sdc_tuning": sdc.Tuning}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sdc.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'    printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])

@@ -296,7 +296,10 @@ def test_kernel_variants_agree_bitwise(torch_cuda, name):
 def test_13species_group_widths_match_oracle(torch_cuda, prec):
     """The 13-species Newton with 4 (variant 0) and 2 (variant 1) lanes per zone:
     each against the oracle over two SDC steps; the two agree to round-off
-    (their partial sums associate differently) and each is deterministic."""
+    (their partial sums associate differently) and each is deterministic.  The
+    thread-per-zone kernels (variants 2-4: static grid, lane queue, warp queue;
+    bordered chain elimination) against the oracle, bit for bit among
+    themselves, and to round-off against the group kernel."""
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
     P, U = PROBS["box16_13"]
@@ -320,6 +323,19 @@ def test_13species_group_widths_match_oracle(torch_cuda, prec):
         assert e.max() <= tol, e
     assert np.array_equal(outs[1], outs[2])
     assert rel_err(outs[1], outs[0], P.nvar, P.dim).max() <= (1e-13 if prec == 0 else TOL32)
+    thr = []
+    for nv in (2, 3, 4):
+        ctx = sdc.Context(P, prec=prec)
+        ctx.set_variants(0, nv)
+        Ud = dev(torch, U)
+        for _ in range(2):
+            st = ctx.step(Ud, dt)
+        assert st.n_fail == 0
+        thr.append(Ud.cpu().numpy())
+    for g in thr:
+        assert rel_err(g, V, P.nvar, P.dim).max() <= tol
+    assert np.array_equal(thr[0], thr[1]) and np.array_equal(thr[0], thr[2])
+    assert rel_err(thr[0], outs[0], P.nvar, P.dim).max() <= (1e-13 if prec == 0 else TOL32)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
