@@ -153,8 +153,11 @@ sdc_status sdc_node_integral(sdc_ctx* ctx, const double* A_nodes, const double* 
 /* Implicit reaction update of Eq. sdc:general at every zone:
    solve  w - dt_m R(w; rho, rho u) = rhs_w  for the reactive fields w, with
    rho and rho*u taken from rhs (R has no mass or momentum component), by
-   Newton iteration on the analytic Jacobian I - dt_m dR/dw (dense LU with
-   partial pivoting) globalised by pseudo-transient continuation.
+   Newton iteration on the analytic Jacobian I - dt_m dR/dw globalised by
+   pseudo-transient continuation.  The linear systems: dense LU with partial
+   pivoting for a general network; for the alpha chain, elimination of its
+   bordered bidiagonal form (chain species first, pivoting within the band,
+   then the 2 x 2 alpha / energy block), the same solution to rounding.
    rhs: [nvar][Ntot].  U_inout: [nvar][Ntot], the guess on entry (its mass
    fractions and specific energy are carried to the density of rhs), the
    solution on exit.  R_out: [n][Ntot] = R(solution).  zone_status, zone_iters:

@@ -576,6 +576,7 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
         P.prod[j] = net->prod[j];
         P.order[j] = P.c0[j] + P.c1[j];
     }
+    set_chain_coefs(P);
 
     // boxes and stencil tiles (the tile table is sized for the smallest tile shape)
     std::vector<BoxDev> hb(nbox);
@@ -1180,6 +1181,7 @@ extern "C" sdc_status sdc_step_static(const sdc_box* boxes, int nbox, const sdc_
         P.prod[j] = net->prod[j];
         P.order[j] = P.c0[j] + P.c1[j];
     }
+    set_chain_coefs(P);
     c.d_dt = (double*)(base + o_dt);
     c.d_stats = (DevStats*)(base + o_stats);
     c.d_boxes = (BoxDev*)(base + o_boxes);

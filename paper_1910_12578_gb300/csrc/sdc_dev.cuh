@@ -30,7 +30,48 @@ struct NetParams {
     double a[SDCD_MAXR], nu[SDCD_MAXR], Q[SDCD_MAXR];
     int r0[SDCD_MAXR], c0[SDCD_MAXR], r1[SDCD_MAXR], c1[SDCD_MAXR], prod[SDCD_MAXR];
     int order[SDCD_MAXR];                // sum of reactant multiplicities
+    // alpha chain: reaction j's share of the Newton matrix, per row (E, X_0, the
+    // consumed X_j, the product X_{j+1}) and column (E, X_0, X_j); see build_chain
+    double kc[SDCD_MAXR][12];
+    float kcf[SDCD_MAXR][12];
 };
+
+// Coefficients of build_chain from the masses and energies of the alpha chain
+// (j = 0: 3 A_0 -> A_1; j >= 1: A_j + A_0 -> A_{j+1}).  Row i of dR/dw takes
+// rho * (Q_j or mass_i * s_ij) * dr_j/dw; with dr_j/d(rho X_c) = k_j dP_j/dY_c /
+// (rho mass_c) and dr_j/d(rho E) = f'_j(T)/f_j(T) k_j P_j (gamma-1)/rho, the
+// density cancels: entry (i, c) gains  -(Q_j or mass_i s_ij) / mass_c times
+// dt_m k_j dP_j/dY_c, and entry (i, E) gains -(Q_j or mass_i s_ij) times
+// dt_m (gamma-1) dk_j P_j.  For j = 0 the factor 3 of dP_0/dY_0 = 3 Y_0^2 is
+// folded into the X_0 column's coefficients.
+inline void set_chain_coefs(NetParams& P) {
+    for (int j = 0; j < SDCD_MAXR; j++)
+        for (int e = 0; e < 12; e++) P.kc[j][e] = 0.0;
+    if (P.topo != TOPO_CHAIN) return;
+    const double* m = P.mass;
+    for (int j = 0; j < P.nreac; j++) {
+        double* c = P.kc[j];
+        const double f0 = j == 0 ? 3.0 : 1.0;        // dP/dY_0 = f0 * (Y_0^2 or Y_j)
+        const double s0 = j == 0 ? -3.0 : -1.0;      // stoichiometry of A_0
+        // row E
+        c[0] = P.Q[j];
+        c[1] = f0 * P.Q[j] / m[0];
+        c[2] = j == 0 ? 0.0 : P.Q[j] / m[j];
+        // row X_0
+        c[3] = s0 * m[0];
+        c[4] = f0 * s0;
+        c[5] = j == 0 ? 0.0 : s0 * m[0] / m[j];
+        // row X_j (consumed; none for j = 0)
+        c[6] = j == 0 ? 0.0 : -m[j];
+        c[7] = j == 0 ? 0.0 : -m[j] / m[0];
+        c[8] = j == 0 ? 0.0 : -1.0;
+        // row X_{j+1} (made)
+        c[9] = m[j + 1];
+        c[10] = f0 * m[j + 1] / m[0];
+        c[11] = j == 0 ? 0.0 : m[j + 1] / m[j];
+        for (int e = 0; e < 12; e++) P.kcf[j][e] = (float)c[e];
+    }
+}
 
 // Newton controls (pseudo-transient continuation constants are fixed).
 struct NewtonCfg {
@@ -221,12 +262,14 @@ struct ChainSys {
     MT dEE, dEA, dAE, dAA;  // M[E][E], M[E][X_0], M[X_0][E], M[X_0][X_0]
 };
 
-// Entries of ChainSys, each formed by the same operations, in the same order,
-// as the dense build_matrix forms it (the structural zeros are not stored).
+// Entries of ChainSys: M = c I - dt_m dR/dw from the rate constants, with the
+// per-reaction coefficients of set_chain_coefs (the density cancels).  With
+// P_j = Y_j Y_0 (P_0 = Y_0^3), reaction j contributes t_E = dt_m (gamma-1)
+// dk_j P_j to the E column, t_A = dt_m k_j dP_j/dY_0 (without the factor 3 of
+// j = 0) to the X_0 column and t_J = dt_m k_j Y_0 to the X_j column.
 template <int NS, typename MT>
-__device__ __forceinline__ void build_chain(const NetParams& P, const double* ym, const double* k, const double* dk,
-                                            const double* Y, double c, double dtm, double rho, double inv_rho,
-                                            ChainSys<NS, MT>& A) {
+__device__ __forceinline__ void build_chain(const NetParams& P, const double* k, const double* dk, const double* Y,
+                                            double c, double dtm, ChainSys<NS, MT>& A) {
     constexpr int NC = NS - 1;
     constexpr int NR = NS - 1;
 #pragma unroll
@@ -236,36 +279,34 @@ __device__ __forceinline__ void build_chain(const NetParams& P, const double* ym
     }
     A.dEE = A.dAA = (MT)c;
     A.dEA = A.dAE = (MT)0;
-    const MT dTdE = (MT)(P.gm1 * inv_rho);
-    const MT s = (MT)(dtm * rho);
+    const MT dt_ = (MT)dtm, dg = (MT)(dtm * P.gm1);
+    const MT y0 = (MT)Y[0];
 #pragma unroll
     for (int j = 0; j < NR; j++) {
-        MT drE, drX0, drXj = (MT)0;
+        const MT* cf;
+        if constexpr (sizeof(MT) == 8) cf = P.kc[j];
+        else cf = P.kcf[j];
         if (j == 0) {
-            MT y0 = (MT)Y[0];
-            drE = (MT)dk[0] * (y0 * y0 * y0) * dTdE;
-            drX0 = (MT)k[0] * ((MT)3 * y0 * y0) * (MT)ym[0];
+            const MT y02 = y0 * y0;
+            const MT t = dt_ * (MT)k[0];
+            const MT tE = dg * (MT)dk[0] * (y02 * y0);
+            const MT tA = t * y02;
+            A.dEE = fma(-cf[0], tE, A.dEE);   A.dEA = fma(-cf[1], tA, A.dEA);
+            A.dAE = fma(-cf[3], tE, A.dAE);   A.dAA = fma(-cf[4], tA, A.dAA);
+            A.uE[0] = fma(-cf[9], tE, A.uE[0]); A.uA[0] = fma(-cf[10], tA, A.uA[0]);
         } else {
-            MT y0 = (MT)Y[0], yj = (MT)Y[j];
-            drE = (MT)dk[j] * (yj * y0) * dTdE;
-            drXj = (MT)k[j] * y0 * (MT)ym[j];
-            drX0 = (MT)k[j] * yj * (MT)ym[0];
-        }
-        const MT qj = s * (MT)P.Q[j];
-        A.dEE -= qj * drE;
-        A.dEA -= qj * drX0;
-        if (j > 0) A.vE[j - 1] -= qj * drXj;
-        if (j == 0) {
-            const MT a0 = s * (MT)P.mass[0] * (MT)(-3.0), a1 = s * (MT)P.mass[1];
-            A.dAE -= a0 * drE;   A.dAA -= a0 * drX0;
-            A.uE[0] -= a1 * drE; A.uA[0] -= a1 * drX0;
-        } else {
-            const MT am = s * (MT)P.mass[j] * (MT)(-1.0);
-            const MT a0 = s * (MT)P.mass[0] * (MT)(-1.0);
-            const MT ap = s * (MT)P.mass[j + 1];
-            A.uE[j - 1] -= am * drE;  A.uA[j - 1] -= am * drX0;  A.bd[j - 1] -= am * drXj;
-            A.dAE -= a0 * drE;        A.dAA -= a0 * drX0;        A.vA[j - 1] -= a0 * drXj;
-            if (j < NC) { A.uE[j] -= ap * drE; A.uA[j] -= ap * drX0; A.bs[j] -= ap * drXj; }
+            const MT yj = (MT)Y[j];
+            const MT t = dt_ * (MT)k[j];
+            const MT tE = dg * (MT)dk[j] * (yj * y0);
+            const MT tA = t * yj, tJ = t * y0;
+            A.dEE = fma(-cf[0], tE, A.dEE);   A.dEA = fma(-cf[1], tA, A.dEA);   A.vE[j - 1] = fma(-cf[2], tJ, A.vE[j - 1]);
+            A.dAE = fma(-cf[3], tE, A.dAE);   A.dAA = fma(-cf[4], tA, A.dAA);   A.vA[j - 1] = fma(-cf[5], tJ, A.vA[j - 1]);
+            A.uE[j - 1] = fma(-cf[6], tE, A.uE[j - 1]);
+            A.uA[j - 1] = fma(-cf[7], tA, A.uA[j - 1]);
+            A.bd[j - 1] = fma(-cf[8], tJ, A.bd[j - 1]);
+            A.uE[j] = fma(-cf[9], tE, A.uE[j]);
+            A.uA[j] = fma(-cf[10], tA, A.uA[j]);
+            A.bs[j] = fma(-cf[11], tJ, A.bs[j]);
         }
     }
 }

@@ -119,7 +119,7 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     if constexpr (TOPO == TOPO_CHAIN) {
         // the chain's sparsity: bordered bidiagonal system, O(n) elimination
         ChainSys<NS, MT> A;
-        build_chain<NS, MT>(P, S.ym, S.k, S.dk, S.Y, c, dtm, S.rho, S.inv_rho, A);
+        build_chain<NS, MT>(P, S.k, S.dk, S.Y, c, dtm, A);
         solved = chain_solve<NS, MT>(A, dv);
     } else {
         MT M[N][N];
