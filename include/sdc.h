@@ -189,6 +189,12 @@ sdc_status sdc_step_profile(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats
    doubles x (device arrays), for testing against correctly rounded results. */
 sdc_status sdc_selftest_math(const double* x, long long n, double* rcp_out, double* sqrt_out, void* cuda_stream);
 
+/* Diagnostic: the library's power-law rate factor T^nu = 2^(nu log2 T) (its
+   table-driven log2 and exp2, used by the reaction kernels in place of
+   exp(nu log T)) for n pairs (T, nu) of device doubles, T > 0; out[i] = T[i]^nu[i].
+   Asynchronous on cuda_stream. */
+sdc_status sdc_selftest_pow(const double* T, const double* nu, long long n, double* out, void* cuda_stream);
+
 /* Kernel variants of a context, chosen by measurement.
    stencil: tile shape of the advective-term kernel (0: 8^3 zones, 576 threads,
    one face per thread per direction; 1: 8 x 8 x 4 zones, 320 threads; one shape

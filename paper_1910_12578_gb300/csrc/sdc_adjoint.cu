@@ -161,7 +161,7 @@ __device__ __forceinline__ void reaction_derivs(const NetParams& P, double rho, 
 #pragma unroll
         for (int q = 0; q < NR; q++) kj[q] = 0.0;
         kj[j] = (P.a[j] != 0.0) ? k[j] / P.a[j] : ipow_small(rho, P.order[j] - 1) *
-                                                   (P.law == LAW_POWER ? exp(P.nu[j] * log(T)) : exp(-P.nu[j] / T));
+                                                   (P.law == LAW_POWER ? exp2_tab(P.nu[j] * log2_tab(T)) : exp(-P.nu[j] / T));
         double Rj[N];
         sources<NS, TOPO>(P, rho, kj, Y, Rj);
 #pragma unroll

@@ -107,6 +107,13 @@ __global__ void selftest_math_kernel(const double* __restrict__ x, long long n, 
     q[i] = sqrt_nr(x[i]);
 }
 
+__global__ void selftest_pow_kernel(const double* __restrict__ T, const double* __restrict__ nu, long long n,
+                                    double* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = exp2_tab(nu[i] * log2_tab(T[i]));
+}
+
 constexpr int QUEUE_SLOTS = 64;
 
 // Event pairs bracketing each launch of an eagerly enqueued step.
@@ -783,6 +790,14 @@ sdc_status sdc_selftest_math(const double* x, long long n, double* rcp_out, doub
     if (!x || !rcp_out || !sqrt_out || n < 0) return SDC_ERR_INVALID_ARG;
     if (n == 0) return SDC_OK;
     selftest_math_kernel<<<grid_for(n, EW_BLOCK), EW_BLOCK, 0, (cudaStream_t)cuda_stream>>>(x, n, rcp_out, sqrt_out);
+    SDC_TRY(cudaGetLastError());
+    return SDC_OK;
+}
+
+sdc_status sdc_selftest_pow(const double* T, const double* nu, long long n, double* out, void* cuda_stream) {
+    if (!T || !nu || !out || n < 0) return SDC_ERR_INVALID_ARG;
+    if (n == 0) return SDC_OK;
+    selftest_pow_kernel<<<grid_for(n, EW_BLOCK), EW_BLOCK, 0, (cudaStream_t)cuda_stream>>>(T, nu, n, out);
     SDC_TRY(cudaGetLastError());
     return SDC_OK;
 }

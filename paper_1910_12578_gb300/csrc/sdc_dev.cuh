@@ -10,6 +10,7 @@
 #include <stdint.h>
 
 #include "sdc_fastmath.cuh"
+#include "sdc_pow.cuh"
 
 #define SDCD_MAXS 16
 #define SDCD_MAXR 16
@@ -100,16 +101,17 @@ __device__ __forceinline__ double ipow_small(double x, int c) {
     return r;
 }
 
-// k_j = a_j rho^(o_j - 1) f_j(T) and dk_j/dT for every reaction.
+// k_j = a_j rho^(o_j - 1) f_j(T) and dk_j/dT for every reaction; the power
+// law's T^nu_j = 2^(nu_j log2 T) by the table-driven log2 / exp2 of sdc_pow.cuh.
 template <int NR>
 __device__ __forceinline__ void rate_consts(const NetParams& P, double rho, double T, double* k, double* dk) {
     if (P.law == LAW_POWER) {
-        const double lT = log(T);
+        const double l2T = log2_tab(T);
         const double iT = rcp_nr(T);
 #pragma unroll
         for (int j = 0; j < NR; j++) {
             double rp = ipow_small(rho, P.order[j] - 1);
-            double kk = P.a[j] * rp * exp(P.nu[j] * lT);
+            double kk = P.a[j] * rp * exp2_tab(P.nu[j] * l2T);
             k[j] = kk;
             dk[j] = P.nu[j] * kk * iT;
         }

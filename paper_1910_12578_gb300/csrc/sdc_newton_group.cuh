@@ -99,10 +99,10 @@ __device__ __forceinline__ double group_eval(const NetParams& P, unsigned mask, 
     // Y: species i = lane (mod L)
     for (int i = lane; i < NS; i += L) zs[O_y + i] = zs[O_w + 1 + i] * ym[i];
     // rate constants of this lane's reactions
-    const double lT = log(T), iT = rcp_nr(T);
+    const double l2T = log2_tab(T), iT = rcp_nr(T);
     for (int j = lane; j < NR; j += L) {
         const double rp = ipow_small(rho, P.order[j] - 1);
-        const double kk = P.a[j] * rp * exp(P.nu[j] * lT);
+        const double kk = P.a[j] * rp * exp2_tab(P.nu[j] * l2T);
         zs[O_k + j] = kk;
         zs[O_dk + j] = P.nu[j] * kk * iT;
     }
@@ -400,9 +400,9 @@ __device__ __forceinline__ int newton_zone_group(const NetParams& P, const Newto
     if (!have_k) {
         // fall back to a fresh evaluation (T not positive: the rates are not finite)
         const double T = P.gm1 * (zs[Lay::O_W] - ke) * inv_rho;
-        const double lT = log(T);
+        const double l2T = log2_tab(T);
         for (int j = lane; j < NR; j += L) {
-            zs[Lay::O_K + j] = P.a[j] * ipow_small(rho, P.order[j] - 1) * exp(P.nu[j] * lT);
+            zs[Lay::O_K + j] = P.a[j] * ipow_small(rho, P.order[j] - 1) * exp2_tab(P.nu[j] * l2T);
         }
         for (int i = lane; i < NS; i += L) zs[Lay::O_Y + i] = zs[Lay::O_W + 1 + i] * ym[i];
         __syncwarp(mask);

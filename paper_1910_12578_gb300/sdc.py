@@ -24,7 +24,8 @@ PREC_FP64, PREC_FP32_JAC = 0, 1
 # entry points declared in include/sdc.h
 EXPORTS = ["sdc_init_box", "sdc_advective_term", "sdc_node_integral", "sdc_react_newton", "sdc_step",
            "sdc_step_profile", "sdc_launches_per_step", "sdc_cfl_dt", "sdc_sizes", "sdc_destroy",
-           "sdc_status_string", "sdc_step_static", "sdc_selftest_math", "sdc_autotune", "sdc_set_variants",
+           "sdc_status_string", "sdc_step_static", "sdc_selftest_math", "sdc_selftest_pow", "sdc_autotune",
+           "sdc_set_variants",
            "sdc_step_backward", "sdc_set_rates", "sdc_advective_term_vjp", "sdc_step_strang"]
 
 
@@ -110,6 +111,7 @@ def load(path: str = LIB_PATH):
     L.sdc_step_profile.argtypes = [vp, dp, C.c_double, C.POINTER(Stats), C.POINTER(Profile)]
     L.sdc_launches_per_step.argtypes = [vp, C.POINTER(C.c_int)]
     L.sdc_selftest_math.argtypes = [dp, C.c_longlong, dp, dp, vp]
+    L.sdc_selftest_pow.argtypes = [dp, dp, C.c_longlong, dp, vp]
     L.sdc_autotune.argtypes = [vp, dp, C.c_double, C.POINTER(Tuning)]
     L.sdc_step_backward.argtypes = [vp, dp, C.c_double, dp, dp, dp]
     L.sdc_set_rates.argtypes = [vp, C.POINTER(C.c_double)]
@@ -124,7 +126,7 @@ def load(path: str = LIB_PATH):
     L.sdc_status_string.argtypes = [C.c_int]
     L.sdc_status_string.restype = C.c_char_p
     for name in ("sdc_init_box", "sdc_advective_term", "sdc_node_integral", "sdc_react_newton", "sdc_step",
-                 "sdc_cfl_dt", "sdc_sizes", "sdc_step_profile", "sdc_launches_per_step", "sdc_step_static", "sdc_selftest_math", "sdc_autotune",
+                 "sdc_cfl_dt", "sdc_sizes", "sdc_step_profile", "sdc_launches_per_step", "sdc_step_static", "sdc_selftest_math", "sdc_selftest_pow", "sdc_autotune",
                  "sdc_set_variants", "sdc_step_backward", "sdc_set_rates", "sdc_advective_term_vjp",
                  "sdc_step_strang"):
         getattr(L, name).restype = C.c_int
@@ -343,6 +345,17 @@ def selftest_math(x):
     if s != SDC_OK:
         raise SdcError(s, "sdc_selftest_math")
     return r, q
+
+
+def selftest_pow(T, nu):
+    """The library's power-law rate factor T^nu (CUDA float64 tensors of one size)."""
+    import torch
+    out = torch.empty_like(T)
+    s = load().sdc_selftest_pow(_ptr(T), _ptr(nu), T.numel(), _ptr(out),
+                                C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if s != SDC_OK:
+        raise SdcError(s, "sdc_selftest_pow")
+    return out
 
 
 def init_box(problems, prec=PREC_FP64, stream=None) -> Context:

@@ -79,3 +79,43 @@ def test_binding_structures_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f in py._fields_:
             assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
+
+
+def test_pow_tables_header_is_the_generator_output():
+    """sdc_pow_tables.h is exactly what the committed gen_pow_tables.py writes."""
+    import subprocess
+    import sys
+    d = os.path.join(ROOT, "paper_1910_12578_gb300", "csrc")
+    out = subprocess.run([sys.executable, "gen_pow_tables.py"], cwd=d, check=True, capture_output=True,
+                         text=True).stdout
+    assert out == open(os.path.join(d, "sdc_pow_tables.h")).read()
+
+
+def test_pow_tables_hold_their_defining_values():
+    """Every table entry against its definition in double arithmetic (an
+    independent check of the generator): 2^(i/64), c_j (1 + (j + 1/2)/128) = 1,
+    hi + lo = log2(1/c_j), and the Taylor coefficients."""
+    import math
+    src = open(os.path.join(ROOT, "paper_1910_12578_gb300", "csrc", "sdc_pow_tables.h")).read()
+
+    def table(name):
+        body = re.search(name + r"\[\d+\] = \{(.*?)\};", src, re.S).group(1)
+        return [float.fromhex(t.strip()) for t in body.split(",") if t.strip()]
+
+    def const(name):
+        return float.fromhex(re.search(r"constexpr double " + name + r" = (\S+);", src).group(1))
+
+    e2 = table("POW_EXP2_T")
+    assert len(e2) == 64
+    for i, v in enumerate(e2):
+        assert abs(v - 2.0 ** (i / 64)) <= 2.3e-16 * v
+    c, hi, lo = table("POW_LOG_C"), table("POW_LOG_HI"), table("POW_LOG_LO")
+    assert len(c) == len(hi) == len(lo) == 128
+    for j in range(128):
+        assert abs(c[j] * (1 + (j + 0.5) / 128) - 1) <= 2.3e-16
+        assert abs(hi[j] + lo[j] + math.log2(c[j])) <= 4e-16
+        assert abs(lo[j]) <= 1.2e-16 * max(hi[j], 2.0 ** -60)
+    for n in range(1, 7):
+        assert const("POW_LOG_A%d" % n) == pytest.approx((-1) ** (n + 1) / (n * math.log(2)), rel=2e-16)
+    for n in range(1, 6):
+        assert const("POW_EXP_B%d" % n) == pytest.approx(math.log(2) ** n / math.factorial(n), rel=4e-16)

@@ -271,6 +271,41 @@ def test_newton_raphson_reciprocal_and_sqrt_within_two_ulp(torch_cuda):
     assert ulps(q, q_ref) <= 2
 
 
+def test_table_driven_power_law_rate_factor(torch_cuda):
+    """T^nu = 2^(nu log2 T) by the table-driven log2 / exp2 of the reaction
+    kernels, against 40-digit decimal references over T in [0.02, 50] (log-
+    uniform), nu in [0, 25]: within ln 2 (2.3e-16 |y| + 1e-17 nu) + 4e-16
+    relative (y = nu log2 T: the roundings of log2 T and of nu log2 T, 2.6e-16
+    for exp2 and half an ulp for the rounded reference), and on average no
+    less accurate than the library's exp(nu log T).  nu = 0 gives exactly 1; a subnormal T and |y| >= 1000 take the
+    library path."""
+    torch = torch_cuda
+    from decimal import Decimal, getcontext
+    from paper_1910_12578_gb300 import sdc
+    getcontext().prec = 40
+    rng = np.random.default_rng(11)
+    n = 20000
+    T = 10 ** rng.uniform(np.log10(0.02), np.log10(50.0), n)
+    nu = rng.uniform(0.0, 25.0, n)
+    T[:4] = [1.0, 2.0, 0.5, 1.0 + 2 ** -52]
+    nu[:4] = [17.3, 3.0, 7.0, 20.0]
+    got = sdc.selftest_pow(dev(torch, T), dev(torch, nu)).cpu().numpy()
+    lib = torch.exp(dev(torch, nu) * torch.log(dev(torch, T))).cpu().numpy()
+    ref = np.array([float((Decimal(float(t)).ln() * Decimal(float(v))).exp()) for t, v in zip(T, nu)])
+    y = np.abs(nu * np.log2(T))
+    bound = np.log(2) * (2.3e-16 * y + 1e-17 * nu) + 4e-16
+    err = np.abs(got - ref) / ref
+    lib_err = np.abs(lib - ref) / ref
+    assert (err <= bound).all(), ((err / bound).max(), T[np.argmax(err / bound)], nu[np.argmax(err / bound)])
+    assert err.mean() <= lib_err.mean() * 1.05 + 1e-17, (err.mean(), lib_err.mean())
+    # special arguments
+    Ts = dev(torch, np.array([5e-320, 2.0, 0.5, 3.0]))
+    nus = dev(torch, np.array([0.5, 1500.0, 1200.0, 0.0]))
+    sp = sdc.selftest_pow(Ts, nus).cpu().numpy()
+    assert sp[0] == pytest.approx(np.sqrt(5e-320), rel=1e-12)
+    assert sp[1] == np.inf and sp[2] == 0.0 and sp[3] == 1.0
+
+
 @pytest.mark.parametrize("name", ["box16", "ragged"])
 def test_kernel_variants_agree_bitwise(torch_cuda, name):
     """The queue-fed persistent Newton kernels (per lane and per warp) and the
