@@ -43,8 +43,10 @@ struct NetParams {
 // (rho mass_c) and dr_j/d(rho E) = f'_j(T)/f_j(T) k_j P_j (gamma-1)/rho, the
 // density cancels: entry (i, c) gains  -(Q_j or mass_i s_ij) / mass_c times
 // dt_m k_j dP_j/dY_c, and entry (i, E) gains -(Q_j or mass_i s_ij) times
-// dt_m (gamma-1) dk_j P_j.  For j = 0 the factor 3 of dP_0/dY_0 = 3 Y_0^2 is
-// folded into the X_0 column's coefficients.
+// dt_m (gamma-1) dk_j P_j = nu_j dt_m (gamma-1) f k_j P_j (dk_j/dT = nu_j k_j f,
+// f = 1/T for the power law, 1/T^2 for the Arrhenius law).  For j = 0 the
+// factor 3 of dP_0/dY_0 = 3 Y_0^2 is folded into the X_0 column's
+// coefficients, and nu_j into the E column's.
 inline void set_chain_coefs(NetParams& P) {
     for (int j = 0; j < SDCD_MAXR; j++)
         for (int e = 0; e < 12; e++) P.kc[j][e] = 0.0;
@@ -70,6 +72,11 @@ inline void set_chain_coefs(NetParams& P) {
         c[9] = m[j + 1];
         c[10] = f0 * m[j + 1] / m[0];
         c[11] = j == 0 ? 0.0 : m[j + 1] / m[j];
+        // the E column's t_E carries dk_j / (k_j f) = nu_j (rate_consts_k)
+        c[0] *= P.nu[j];
+        c[3] *= P.nu[j];
+        c[6] *= P.nu[j];
+        c[9] *= P.nu[j];
         for (int e = 0; e < 12; e++) P.kcf[j][e] = (float)c[e];
     }
 }
@@ -127,16 +134,33 @@ __device__ __forceinline__ void rate_consts(const NetParams& P, double rho, doub
     }
 }
 
-// Reactive sources R(w) = [R(rho E), R(rho X_0..)] from the rate constants and Y.
-// Alpha chain topology: j = 0 is 3 A0 -> A1, j >= 1 is A_j + A0 -> A_{j+1}.
+// k_j only, and the factor f with dk_j/dT = nu_j k_j f (power law: f = 1/T;
+// Arrhenius: f = 1/T^2): the alpha chain's matrix takes nu_j from its
+// coefficients (set_chain_coefs), so the solve needs no dk_j.
+template <int NR>
+__device__ __forceinline__ void rate_consts_k(const NetParams& P, double rho, double T, double* k, double& dfac) {
+    const double iT = rcp_nr(T);
+    if (P.law == LAW_POWER) {
+        const double l2T = log2_tab(T);
+#pragma unroll
+        for (int j = 0; j < NR; j++) k[j] = P.a[j] * ipow_small(rho, P.order[j] - 1) * exp2_tab(P.nu[j] * l2T);
+        dfac = iT;
+    } else {
+#pragma unroll
+        for (int j = 0; j < NR; j++) k[j] = P.a[j] * ipow_small(rho, P.order[j] - 1) * exp(-P.nu[j] * iT);
+        dfac = iT * iT;
+    }
+}
+
+// Per-species sums S_i = sum_j s_ij r_j and E = sum_j Q_j r_j of the rates
+// r_j = k_j prod Y (R(rho X_i) = rho mass_i S_i, R(rho E) = rho E).
 template <int NS, int TOPO>
-__device__ __forceinline__ void sources(const NetParams& P, double rho, const double* k, const double* Y,
-                                        double* R) {
+__device__ __forceinline__ void source_sums(const NetParams& P, const double* k, const double* Y, double* S,
+                                            double& RE) {
     constexpr int NR = NS - 1;
-    double S[NS];
 #pragma unroll
     for (int i = 0; i < NS; i++) S[i] = 0.0;
-    double RE = 0.0;
+    RE = 0.0;
     if (TOPO == TOPO_CHAIN) {
 #pragma unroll
         for (int j = 0; j < NR; j++) {
@@ -163,6 +187,15 @@ __device__ __forceinline__ void sources(const NetParams& P, double rho, const do
             S[P.prod[j]] += r;
         }
     }
+}
+
+// Reactive sources R(w) = [R(rho E), R(rho X_0..)] from the rate constants and Y.
+// Alpha chain topology: j = 0 is 3 A0 -> A1, j >= 1 is A_j + A0 -> A_{j+1}.
+template <int NS, int TOPO>
+__device__ __forceinline__ void sources(const NetParams& P, double rho, const double* k, const double* Y,
+                                        double* R) {
+    double S[NS], RE;
+    source_sums<NS, TOPO>(P, k, Y, S, RE);
     R[0] = rho * RE;
 #pragma unroll
     for (int i = 0; i < NS; i++) R[1 + i] = rho * P.mass[i] * S[i];
@@ -266,11 +299,12 @@ struct ChainSys {
 
 // Entries of ChainSys: M = c I - dt_m dR/dw from the rate constants, with the
 // per-reaction coefficients of set_chain_coefs (the density cancels).  With
-// P_j = Y_j Y_0 (P_0 = Y_0^3), reaction j contributes t_E = dt_m (gamma-1)
-// dk_j P_j to the E column, t_A = dt_m k_j dP_j/dY_0 (without the factor 3 of
-// j = 0) to the X_0 column and t_J = dt_m k_j Y_0 to the X_j column.
+// P_j = Y_j Y_0 (P_0 = Y_0^3), reaction j contributes t_E = dt_m (gamma-1) f
+// k_j P_j to the E column (nu_j is in the coefficients; f from rate_consts_k),
+// t_A = dt_m k_j dP_j/dY_0 (without the factor 3 of j = 0) to the X_0 column
+// and t_J = dt_m k_j Y_0 to the X_j column.
 template <int NS, typename MT>
-__device__ __forceinline__ void build_chain(const NetParams& P, const double* k, const double* dk, const double* Y,
+__device__ __forceinline__ void build_chain(const NetParams& P, const double* k, double dfac, const double* Y,
                                             double c, double dtm, ChainSys<NS, MT>& A) {
     constexpr int NC = NS - 1;
     constexpr int NR = NS - 1;
@@ -281,7 +315,7 @@ __device__ __forceinline__ void build_chain(const NetParams& P, const double* k,
     }
     A.dEE = A.dAA = (MT)c;
     A.dEA = A.dAE = (MT)0;
-    const MT dt_ = (MT)dtm, dg = (MT)(dtm * P.gm1);
+    const MT dt_ = (MT)dtm, dg = (MT)(dtm * P.gm1 * dfac);
     const MT y0 = (MT)Y[0];
 #pragma unroll
     for (int j = 0; j < NR; j++) {
@@ -291,7 +325,7 @@ __device__ __forceinline__ void build_chain(const NetParams& P, const double* k,
         if (j == 0) {
             const MT y02 = y0 * y0;
             const MT t = dt_ * (MT)k[0];
-            const MT tE = dg * (MT)dk[0] * (y02 * y0);
+            const MT tE = dg * (MT)k[0] * (y02 * y0);
             const MT tA = t * y02;
             A.dEE = fma(-cf[0], tE, A.dEE);   A.dEA = fma(-cf[1], tA, A.dEA);
             A.dAE = fma(-cf[3], tE, A.dAE);   A.dAA = fma(-cf[4], tA, A.dAA);
@@ -299,7 +333,7 @@ __device__ __forceinline__ void build_chain(const NetParams& P, const double* k,
         } else {
             const MT yj = (MT)Y[j];
             const MT t = dt_ * (MT)k[j];
-            const MT tE = dg * (MT)dk[j] * (yj * y0);
+            const MT tE = dg * (MT)k[j] * (yj * y0);
             const MT tA = t * yj, tJ = t * y0;
             A.dEE = fma(-cf[0], tE, A.dEE);   A.dEA = fma(-cf[1], tA, A.dEA);   A.vE[j - 1] = fma(-cf[2], tJ, A.vE[j - 1]);
             A.dAE = fma(-cf[3], tE, A.dAE);   A.dAA = fma(-cf[4], tA, A.dAA);   A.vA[j - 1] = fma(-cf[5], tJ, A.vA[j - 1]);
@@ -313,8 +347,6 @@ __device__ __forceinline__ void build_chain(const NetParams& P, const double* k,
     }
 }
 
-__device__ __forceinline__ long long abs_pattern(double x) { return __double_as_longlong(x) & ABS_MASK; }
-__device__ __forceinline__ int abs_pattern(float x) { return __float_as_int(x) & 0x7fffffff; }
 
 // Solve M d = b for the bordered chain system (b in w order, overwritten by d).
 // Gaussian elimination in the order (X_1 .. X_{ns-1} | X_0, E): at chain
@@ -337,7 +369,7 @@ __device__ __forceinline__ bool chain_solve(const ChainSys<NS, MT>& A, MT* b) {
         MT p, e, quE, quA, qg;
         if (k + 1 < NC) {
             const MT ns_ = A.bs[k + 1], nd = A.bd[k + 1], nuE = A.uE[k + 1], nuA = A.uA[k + 1], ng = b[3 + k];
-            const bool sw = abs_pattern(ns_) > abs_pattern(cp);
+            const bool sw = mag2(ns_) > mag2(cp);
             p = sw ? ns_ : cp;
             e = sw ? nd : (MT)0;
             quE = sw ? nuE : cuE;
@@ -368,7 +400,7 @@ __device__ __forceinline__ bool chain_solve(const ChainSys<NS, MT>& A, MT* b) {
         }
     }
     // 2 x 2 border block, partial pivoting
-    const bool sw = abs_pattern(dAE) > abs_pattern(dEE);
+    const bool sw = mag2(dAE) > mag2(dEE);
     const MT a = sw ? dAE : dEE, bb = sw ? dAA : dEA, c2 = sw ? dEE : dAE, d2 = sw ? dEA : dAA;
     const MT r1 = sw ? gA : gE, r2 = sw ? gE : gA;
     ok = ok && (a != (MT)0);
@@ -398,21 +430,13 @@ __device__ __forceinline__ bool lu_solve(MT (*M)[N], VT* b) {
     MT inv_piv[N];
 #pragma unroll
     for (int kc = 0; kc < N; kc++) {
-        // pivot search (|x| compared as bit patterns: they order like the values)
+        // pivot search (|x| compared as shifted bit patterns, mag2: they order like the values)
         int piv = kc;
-        if (sizeof(MT) == 8) {
-            long long best = __double_as_longlong((double)M[kc][kc]) & ABS_MASK;
+        {
+            auto best = mag2(M[kc][kc]);
 #pragma unroll
             for (int i = kc + 1; i < N; i++) {
-                const long long v = __double_as_longlong((double)M[i][kc]) & ABS_MASK;
-                if (v > best) { best = v; piv = i; }
-            }
-            if (best == 0) return false;
-        } else {
-            int best = __float_as_int((float)M[kc][kc]) & 0x7fffffff;
-#pragma unroll
-            for (int i = kc + 1; i < N; i++) {
-                const int v = __float_as_int((float)M[i][kc]) & 0x7fffffff;
+                const auto v = mag2(M[i][kc]);
                 if (v > best) { best = v; piv = i; }
             }
             if (best == 0) return false;

@@ -58,6 +58,13 @@ constexpr long long SIGN_BIT = (long long)0x8000000000000000ull;
 constexpr long long ABS_MASK = 0x7FFFFFFFFFFFFFFFll;
 constexpr long long EXP_ONE = 1ll << 52;  // one unit of the exponent field
 
+// |x| as an unsigned integer that orders like |x|: the bit pattern shifted
+// left by one, which drops the sign (a mask of the sign bit would be compiled
+// into an FP64 absolute value on the FP64 pipe; the shift stays on the integer
+// pipe).  Zero for +-0.
+__device__ __forceinline__ unsigned long long mag2(double x) { return (unsigned long long)dbits(x) << 1; }
+__device__ __forceinline__ unsigned int mag2(float x) { return (unsigned int)__float_as_int(x) << 1; }
+
 // MC-limited slope from three values with integer-pipe limiting:
 //   dl = q0 - qm, dr = qp - q0; slope = 0 when dl*dr <= 0, else
 //   sign(dl+dr) * min(2|dl|, 2|dr|, |dl+dr|/2).
@@ -73,12 +80,14 @@ __device__ __forceinline__ double mc_half_slope(int limiter, double qm, double q
     const double dl = q0 - qm, dr = qp - q0, s = dl + dr;
     if (!limiter) return 0.25 * s;
     const long long bl = dbits(dl), br = dbits(dr), bs = dbits(s);
-    const long long al = bl & ABS_MASK, ar = br & ABS_MASK, as = bs & ABS_MASK;
-    if (((bl ^ br) < 0) || al == 0 || ar == 0 || as < 3 * EXP_ONE) return 0.0;
-    const long long q = as - 2 * EXP_ONE;  // |s| / 4
-    long long lim = al < ar ? al : ar;
+    // magnitudes as bit patterns shifted left by one (mag2)
+    const unsigned long long al = mag2(dl), ar = mag2(dr), as = mag2(s);
+    constexpr unsigned long long E2 = (unsigned long long)EXP_ONE << 1;
+    if (((bl ^ br) < 0) || al == 0 || ar == 0 || as < 3 * E2) return 0.0;
+    const unsigned long long q = as - 2 * E2;  // |s| / 4
+    unsigned long long lim = al < ar ? al : ar;
     lim = lim < q ? lim : q;
-    return bitsd(lim | (bs & SIGN_BIT));
+    return bitsd((long long)(lim >> 1) | (bs & SIGN_BIT));
 }
 
 }  // namespace sdcd

@@ -27,18 +27,23 @@ struct ZoneEval {
     static constexpr int NR = NS - 1;
 };
 
-// Evaluate T, rate constants, Y and the residual at state w.
-// Returns false when T is not positive and finite.
+// Evaluate T, rate constants, Y and the residual at state w, in the order of
+// operations of the definition, G = w - dt_m R(w) - rhs_w, and its scaled norm
+// phi = (G_E/|rhs_E|)^2 + sum_i (G_i/rho)^2.  For the alpha chain only k_j and
+// the factor f of dk_j/dT = nu_j k_j f are formed (the matrix takes nu_j from
+// its coefficients); otherwise k_j and dk_j.  Returns false when T is not
+// positive and finite.
 template <int NS, int TOPO>
 __device__ __forceinline__ bool eval_state(const NetParams& P, double rho, double inv_rho, double ke,
                                            const double* ym, const double* w, const double* rw, double dtm,
-                                           double sE_inv, double* k, double* dk, double* Y, double* G,
+                                           double sE_inv, double* k, double* dk, double& dfac, double* Y, double* G,
                                            double& phi) {
     constexpr int N = NS + 1;
     constexpr int NR = NS - 1;
     const double T = P.gm1 * (w[0] - ke) * inv_rho;
     if (!(T > 0.0 && T < INFINITY)) return false;
-    rate_consts<NR>(P, rho, T, k, dk);
+    if constexpr (TOPO == TOPO_CHAIN) rate_consts_k<NR>(P, rho, T, k, dfac);
+    else rate_consts<NR>(P, rho, T, k, dk);
 #pragma unroll
     for (int i = 0; i < NS; i++) Y[i] = w[1 + i] * ym[i];
     double R[N];
@@ -59,7 +64,7 @@ template <int NS>
 struct ZoneState {
     static constexpr int N = NS + 1;
     static constexpr int NR = NS - 1;
-    double rho, inv_rho, ke, sE_inv, phi, h;
+    double rho, inv_rho, ke, sE_inv, phi, h, dfac;
     double ym[NS], lower[NS], rw[N], w[N], G[N], k[NR], dk[NR], Y[NS];
     int iters, status;
     bool newton, have_k, done;
@@ -99,8 +104,8 @@ __device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, 
     S.status = ZONE_MAXIT;
     S.newton = true;
     S.h = PTC_H0;
-    S.have_k = eval_state<NS, TOPO>(P, rho, S.inv_rho, S.ke, S.ym, S.w, S.rw, dtm, S.sE_inv, S.k, S.dk, S.Y, S.G,
-                                    S.phi);
+    S.have_k = eval_state<NS, TOPO>(P, rho, S.inv_rho, S.ke, S.ym, S.w, S.rw, dtm, S.sE_inv, S.k, S.dk, S.dfac, S.Y,
+                                    S.G, S.phi);
     S.done = !S.have_k;
     if (!S.have_k) S.status = ZONE_NONPHYSICAL;
 }
@@ -119,7 +124,7 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     if constexpr (TOPO == TOPO_CHAIN) {
         // the chain's sparsity: bordered bidiagonal system, O(n) elimination
         ChainSys<NS, MT> A;
-        build_chain<NS, MT>(P, S.k, S.dk, S.Y, c, dtm, A);
+        build_chain<NS, MT>(P, S.k, S.dfac, S.Y, c, dtm, A);
         solved = chain_solve<NS, MT>(A, dv);
     } else {
         MT M[N][N];
@@ -138,9 +143,10 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
 #pragma unroll
     for (int i = 0; i < NS; i++) ok = ok && (tr[1 + i] >= S.lower[i]);
     double kt[NR], dkt[NR], Yt[NS], Gt[N];
-    double phit = 0.0;
+    double phit = 0.0, dfact = 0.0;
     if (ok)
-        ok = eval_state<NS, TOPO>(P, S.rho, S.inv_rho, S.ke, S.ym, tr, S.rw, dtm, S.sE_inv, kt, dkt, Yt, Gt, phit);
+        ok = eval_state<NS, TOPO>(P, S.rho, S.inv_rho, S.ke, S.ym, tr, S.rw, dtm, S.sE_inv, kt, dkt, dfact, Yt, Gt,
+                                  phit);
     // an admissible Newton step that meets the stop test converges even if the
     // residual grew by round-off at the root
     bool small = false;
@@ -164,7 +170,13 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
 #pragma unroll
         for (int r = 0; r < N; r++) { S.w[r] = tr[r]; S.G[r] = Gt[r]; }
 #pragma unroll
-        for (int j = 0; j < NR; j++) { S.k[j] = kt[j]; S.dk[j] = dkt[j]; }
+        for (int j = 0; j < NR; j++) S.k[j] = kt[j];
+        if constexpr (TOPO == TOPO_CHAIN) {
+            S.dfac = dfact;
+        } else {
+#pragma unroll
+            for (int j = 0; j < NR; j++) S.dk[j] = dkt[j];
+        }
 #pragma unroll
         for (int i = 0; i < NS; i++) S.Y[i] = Yt[i];
         S.phi = phit;

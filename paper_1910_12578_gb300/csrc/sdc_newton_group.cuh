@@ -60,19 +60,17 @@ __device__ __forceinline__ T group_sum_t(unsigned mask, T v) {
     return v;
 }
 
-// |x| as an integer bit pattern (non-negative values order like their patterns)
+// |x| as an unsigned integer that orders like |x| (mag2 of sdc_fastmath.cuh)
 template <typename MT>
 struct AbsBits;
 template <>
 struct AbsBits<double> {
-    using type = long long;
+    using type = unsigned long long;
 };
 template <>
 struct AbsBits<float> {
-    using type = int;
+    using type = unsigned int;
 };
-__device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & ABS_MASK; }
-__device__ __forceinline__ int abs_bits(float x) { return __float_as_int(x) & 0x7fffffff; }
 
 template <int L>
 __device__ __forceinline__ bool group_all(unsigned mask, bool p) {
@@ -279,11 +277,11 @@ __device__ __forceinline__ int newton_zone_group(const NetParams& P, const Newto
             for (int k = 0; k < N; k++) {
                 // pivot: largest |M[i][k]|, i >= k, ties to the lowest row (|x|
                 // compared as bit patterns on the integer pipe: they order like the values)
-                IT best = -1;
+                IT best = 0;
                 int piv = N;
                 for (int i = k + lane; i < N; i += L) {
-                    const IT v = abs_bits(M[i * N + k]);
-                    if (v > best) { best = v; piv = i; }
+                    const IT v = mag2(M[i * N + k]);
+                    if (v > best || piv == N) { best = v; piv = i; }
                 }
 #pragma unroll
                 for (int o = 1; o < L; o <<= 1) {
