@@ -137,17 +137,19 @@ __device__ __forceinline__ void rate_consts(const NetParams& P, double rho, doub
 // k_j only, and the factor f with dk_j/dT = nu_j k_j f (power law: f = 1/T;
 // Arrhenius: f = 1/T^2): the alpha chain's matrix takes nu_j from its
 // coefficients (set_chain_coefs), so the solve needs no dk_j.
+// ak[j] = a_j rho^(o_j - 1), fixed during one zone's solve (k_j = ak[j] f_j(T)).
 template <int NR>
-__device__ __forceinline__ void rate_consts_k(const NetParams& P, double rho, double T, double* k, double& dfac) {
+__device__ __forceinline__ void rate_consts_k(const NetParams& P, const double* ak, double T, double* k,
+                                              double& dfac) {
     const double iT = rcp_nr(T);
     if (P.law == LAW_POWER) {
         const double l2T = log2_tab(T);
 #pragma unroll
-        for (int j = 0; j < NR; j++) k[j] = P.a[j] * ipow_small(rho, P.order[j] - 1) * exp2_tab(P.nu[j] * l2T);
+        for (int j = 0; j < NR; j++) k[j] = ak[j] * exp2_tab(P.nu[j] * l2T);
         dfac = iT;
     } else {
 #pragma unroll
-        for (int j = 0; j < NR; j++) k[j] = P.a[j] * ipow_small(rho, P.order[j] - 1) * exp(-P.nu[j] * iT);
+        for (int j = 0; j < NR; j++) k[j] = ak[j] * exp(-P.nu[j] * iT);
         dfac = iT * iT;
     }
 }

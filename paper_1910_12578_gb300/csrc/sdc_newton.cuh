@@ -29,32 +29,33 @@ struct ZoneEval {
 
 // Evaluate T, rate constants, Y and the residual at state w, in the order of
 // operations of the definition, G = w - dt_m R(w) - rhs_w, and its scaled norm
-// phi = (G_E/|rhs_E|)^2 + sum_i (G_i/rho)^2.  For the alpha chain only k_j and
+// times rho^2, phi = (G_E rho/|rhs_E|)^2 + sum_i G_i^2 (the solve only compares
+// norms of one zone, so the common factor 1/rho^2 of the scaled norm
+// (G_E/|rhs_E|)^2 + sum_i (G_i/rho)^2 is left out).  For the alpha chain only k_j and
 // the factor f of dk_j/dT = nu_j k_j f are formed (the matrix takes nu_j from
 // its coefficients); otherwise k_j and dk_j.  Returns false when T is not
 // positive and finite.
 template <int NS, int TOPO>
 __device__ __forceinline__ bool eval_state(const NetParams& P, double rho, double inv_rho, double ke,
-                                           const double* ym, const double* w, const double* rw, double dtm,
-                                           double sE_inv, double* k, double* dk, double& dfac, double* Y, double* G,
-                                           double& phi) {
+                                           const double* ym, const double* ak, const double* w, const double* rw,
+                                           double dtm, double wE, double* k, double* dk, double& dfac, double* Y,
+                                           double* G, double& phi) {
     constexpr int N = NS + 1;
     constexpr int NR = NS - 1;
     const double T = P.gm1 * (w[0] - ke) * inv_rho;
     if (!(T > 0.0 && T < INFINITY)) return false;
-    if constexpr (TOPO == TOPO_CHAIN) rate_consts_k<NR>(P, rho, T, k, dfac);
+    if constexpr (TOPO == TOPO_CHAIN) rate_consts_k<NR>(P, ak, T, k, dfac);
     else rate_consts<NR>(P, rho, T, k, dk);
 #pragma unroll
     for (int i = 0; i < NS; i++) Y[i] = w[1 + i] * ym[i];
     double R[N];
     sources<NS, TOPO>(P, rho, k, Y, R);
-    double s = 0.0;
 #pragma unroll
-    for (int r = 0; r < N; r++) {
-        G[r] = w[r] - dtm * R[r] - rw[r];
-        const double g = r == 0 ? G[r] * sE_inv : G[r] * inv_rho;
-        s += g * g;
-    }
+    for (int r = 0; r < N; r++) G[r] = w[r] - dtm * R[r] - rw[r];
+    const double gE = G[0] * wE;
+    double s = gE * gE;
+#pragma unroll
+    for (int r = 1; r < N; r++) s = fma(G[r], G[r], s);
     phi = s;
     return s < INFINITY;
 }
@@ -64,8 +65,9 @@ template <int NS>
 struct ZoneState {
     static constexpr int N = NS + 1;
     static constexpr int NR = NS - 1;
-    double rho, inv_rho, ke, sE_inv, phi, h, dfac;
+    double rho, inv_rho, ke, wE, phi, h, dfac;
     double ym[NS], lower[NS], rw[N], w[N], G[N], k[NR], dk[NR], Y[NS];
+    double ak[NR];  // a_j rho^(o_j - 1) (alpha chain)
     int iters, status;
     bool newton, have_k, done;
 };
@@ -80,7 +82,12 @@ __device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, 
     S.ke = 0.5 * m2 * S.inv_rho;
 #pragma unroll
     for (int i = 0; i < NS; i++) S.ym[i] = S.inv_rho * P.inv_mass[i];
-    S.sE_inv = rcp_nr(fabs(S.rw[0]));
+    if constexpr (TOPO == TOPO_CHAIN) {
+        constexpr int NR = NS - 1;
+#pragma unroll
+        for (int j = 0; j < NR; j++) S.ak[j] = P.a[j] * ipow_small(rho, P.order[j] - 1);
+    }
+    S.wE = rho * rcp_nr(fabs(S.rw[0]));  // rho / |rhs_E|
     // a start without a positive temperature is replaced by rhs
     {
         const double Tg = P.gm1 * (S.w[0] - S.ke) * S.inv_rho;
@@ -104,7 +111,7 @@ __device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, 
     S.status = ZONE_MAXIT;
     S.newton = true;
     S.h = PTC_H0;
-    S.have_k = eval_state<NS, TOPO>(P, rho, S.inv_rho, S.ke, S.ym, S.w, S.rw, dtm, S.sE_inv, S.k, S.dk, S.dfac, S.Y,
+    S.have_k = eval_state<NS, TOPO>(P, rho, S.inv_rho, S.ke, S.ym, S.ak, S.w, S.rw, dtm, S.wE, S.k, S.dk, S.dfac, S.Y,
                                     S.G, S.phi);
     S.done = !S.have_k;
     if (!S.have_k) S.status = ZONE_NONPHYSICAL;
@@ -145,7 +152,7 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     double kt[NR], dkt[NR], Yt[NS], Gt[N];
     double phit = 0.0, dfact = 0.0;
     if (ok)
-        ok = eval_state<NS, TOPO>(P, S.rho, S.inv_rho, S.ke, S.ym, tr, S.rw, dtm, S.sE_inv, kt, dkt, dfact, Yt, Gt,
+        ok = eval_state<NS, TOPO>(P, S.rho, S.inv_rho, S.ke, S.ym, S.ak, tr, S.rw, dtm, S.wE, kt, dkt, dfact, Yt, Gt,
                                   phit);
     // an admissible Newton step that meets the stop test converges even if the
     // residual grew by round-off at the root
