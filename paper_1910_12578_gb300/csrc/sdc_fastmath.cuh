@@ -38,18 +38,20 @@ __device__ __forceinline__ double rcp_nr(double x) {
     return fma(y, e, y);
 }
 
-// sqrt(x) for finite, positive, normal x: x * rsqrt(x) with rsqrt refined by
-// two Newton-Raphson steps
-__device__ __forceinline__ double sqrt_nr(double x) {
+// 1/sqrt(x) for finite, positive, normal x: the hardware approximation
+// refined by two Newton-Raphson steps
+__device__ __forceinline__ double rsqrt_nr(double x) {
     double y = rsqrt_seed(x);
     double h = 0.5 * y;
     double e = fma(-x * y, y, 1.0);
     y = fma(h, e, y);
     h = 0.5 * y;
     e = fma(-x * y, y, 1.0);
-    y = fma(h, e, y);
-    return x * y;
+    return fma(h, e, y);
 }
+
+// sqrt(x) for finite, positive, normal x: x * rsqrt(x)
+__device__ __forceinline__ double sqrt_nr(double x) { return x * rsqrt_nr(x); }
 
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 __device__ __forceinline__ double bitsd(long long b) { return __longlong_as_double(b); }

@@ -160,8 +160,15 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     if (S.newton && ok) {
         small = fabs((double)dv[0]) <= cfg.rtol * fabs(tr[0]);
         const double tol_x = cfg.rtol * S.rho;
+        if constexpr (sizeof(MT) == 8) {
+            // |dv_i| <= tol_x on the integer pipe (mag2 orders like |x|; a nan step fails)
+            const unsigned long long mt = mag2(tol_x);
 #pragma unroll
-        for (int i = 0; i < NS; i++) small = small && (fabs((double)dv[1 + i]) <= tol_x);
+            for (int i = 0; i < NS; i++) small = small && (mag2((double)dv[1 + i]) <= mt);
+        } else {
+#pragma unroll
+            for (int i = 0; i < NS; i++) small = small && (fabs((double)dv[1 + i]) <= tol_x);
+        }
     }
     if (S.newton && !small && (!ok || phit > S.phi)) {
         S.newton = false;

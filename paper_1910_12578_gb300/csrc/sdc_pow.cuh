@@ -10,7 +10,7 @@
 // = 2^y, y = nu log2 T, therefore within ln 2 (2.2e-16 |y| + 5e-18 nu) +
 // 2.6e-16 relative (the rounding of the product nu log2 T dominates, as that of
 // nu log T does in exp(nu log T)).  Arguments outside the tables' range (T not
-// a positive normal number; |y| >= 1000) take the library functions.
+// a positive normal number; |y| >= 512) take the library functions.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -42,7 +42,9 @@ __device__ __forceinline__ double log2_tab(double x) {
 
 // 2^y
 __device__ __forceinline__ double exp2_tab(double y) {
-    if (!(fabs(y) < 1000.0)) return exp2(y);
+    // |y| < 512 (and not nan) read from the exponent field, on the integer pipe;
+    // beyond it the library (the scaling below keeps 2^y normal for |y| < 1021)
+    if (((dbits(y) >> 52) & 0x7ff) >= 1023 + 9) return exp2(y);
     const double SHIFT = 0x1.8p52;           // 64 y + SHIFT rounds 64 y to an integer in the low bits
     const double t = fma(y, 64.0, SHIFT);
     const double nf = t - SHIFT;

@@ -95,47 +95,49 @@ __device__ __forceinline__ int wrap(int g, int n) {
 
 // HLLC flux of the hydrodynamic fields through a face normal to `dir`;
 // q = [rho, u_0.., p].  Returns S* (its sign picks the species' upwind side).
+// The sound speeds are gamma p / sqrt(gamma p rho) (no reciprocal of rho), the
+// total energy is formed for the upwind side only, and the star state's energy
+// flux uses fac * e* = (E (S - u) + (S* - u)(S* rho (S - u) + p)) / (S - S*),
+// the same quantity as rho*_K E*_K with e* = E/rho + (S* - u)(S* + p/(rho (S - u))).
 template <int DIM>
 __device__ __forceinline__ double hllc_hydro(double g, double gm1_inv, int dir, const double* qL, const double* qR,
                                              double* Fh) {
     const double rL = qL[0], rR = qR[0];
     const double unL = qL[1 + dir], unR = qR[1 + dir];
     const double pL = qL[1 + DIM], pR = qR[1 + DIM];
-    double kL = 0.0, kR = 0.0;
-#pragma unroll
-    for (int d = 0; d < DIM; d++) {
-        kL = fma(qL[1 + d], qL[1 + d], kL);
-        kR = fma(qR[1 + d], qR[1 + d], kR);
-    }
-    const double EL = fma(pL, gm1_inv, 0.5 * rL * kL);
-    const double ER = fma(pR, gm1_inv, 0.5 * rR * kR);
-    const double irL = rcp_nr(rL), irR = rcp_nr(rR);
-    const double cL = sqrt_nr(g * pL * irL), cR = sqrt_nr(g * pR * irR);
+    const double gpL = g * pL, gpR = g * pR;
+    const double cL = gpL * rsqrt_nr(gpL * rL), cR = gpR * rsqrt_nr(gpR * rR);
     const double SL = fmin(unL - cL, unR - cR);
     const double SR = fmax(unL + cL, unR + cR);
-    const double aL = rL * (SL - unL), aR = rR * (SR - unR);  // mass fluxes relative to the waves
+    const double dL = SL - unL, dR = SR - unR;
+    const double aL = rL * dL, aR = rR * dR;  // mass fluxes relative to the waves
     const double Ss = (pR - pL + unL * aL - unR * aR) * rcp_nr(aL - aR);
     // region: SL >= 0 -> F_L; else Ss >= 0 -> F*_L; else SR > 0 -> F*_R; else F_R
     const bool left = (SL >= 0.0) || (Ss >= 0.0);
     const bool star = (SL < 0.0) && (Ss >= 0.0 || SR > 0.0);
-    const double r = left ? rL : rR, un = left ? unL : unR, p = left ? pL : pR, E = left ? EL : ER;
-    const double S = left ? SL : SR, a = left ? aL : aR, ir = left ? irL : irR;
+    const double r = left ? rL : rR, un = left ? unL : unR, p = left ? pL : pR;
+    const double S = left ? SL : SR, a = left ? aL : aR, dS = left ? dL : dR;
     const double* q = left ? qL : qR;
+    double k2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; d++) k2 = fma(q[1 + d], q[1 + d], k2);
+    const double E = fma(p, gm1_inv, 0.5 * r * k2);
     Fh[0] = r * un;
 #pragma unroll
     for (int d = 0; d < DIM; d++) Fh[1 + d] = r * un * q[1 + d] + (d == dir ? p : 0.0);
     Fh[1 + DIM] = (E + p) * un;
     if (star) {
-        // U*_K = fac [1, S* (normal) / u_t, E/r + (S* - u)(S* + p/(r (S - u)))], fac = r (S - u)/(S - S*)
-        const double fac = a * rcp_nr(S - Ss);
-        const double eS = fma(ir, E, (Ss - un) * fma(p, rcp_nr(a), Ss));
+        // U*_K = fac [1, S* (normal) / u_t, e*], fac = rho (S - u)/(S - S*)
+        const double inv = rcp_nr(S - Ss);
+        const double fac = a * inv;
+        const double feS = fma(Ss - un, fma(Ss, a, p), E * dS) * inv;
         Fh[0] = fma(S, fac - r, Fh[0]);
 #pragma unroll
         for (int d = 0; d < DIM; d++) {
             const double ud = (d == dir) ? Ss : q[1 + d];
             Fh[1 + d] = fma(S, fac * ud - r * q[1 + d], Fh[1 + d]);
         }
-        Fh[1 + DIM] = fma(S, fac * eS - E, Fh[1 + DIM]);
+        Fh[1 + DIM] = fma(S, feS - E, Fh[1 + DIM]);
     }
     return Ss;
 }

@@ -277,7 +277,7 @@ def test_table_driven_power_law_rate_factor(torch_cuda):
     uniform), nu in [0, 25]: within ln 2 (2.3e-16 |y| + 1e-17 nu) + 4e-16
     relative (y = nu log2 T: the roundings of log2 T and of nu log2 T, 2.6e-16
     for exp2 and half an ulp for the rounded reference), and on average no
-    less accurate than the library's exp(nu log T).  nu = 0 gives exactly 1; a subnormal T and |y| >= 1000 take the
+    less accurate than the library's exp(nu log T).  nu = 0 gives exactly 1; a subnormal T and |y| >= 512 take the
     library path."""
     torch = torch_cuda
     from decimal import Decimal, getcontext
