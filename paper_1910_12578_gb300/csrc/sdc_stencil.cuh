@@ -72,6 +72,16 @@ struct TileGeom {
     static constexpr int THREADS = NF;                       // one face per thread per direction
 };
 
+// CTAs per SM the launch bounds ask for: two where two tiles' shared memory
+// (primitives and the slope / flux buffer) fit in an SM's 228 KB, so that one
+// CTA's barrier phases overlap the other's arithmetic; the registers per
+// thread are then capped at 64K / (2 THREADS).
+template <int DIM, int NS, int TX, int TY, int TZ>
+constexpr int stencil_min_blocks() {
+    using G = TileGeom<DIM, TX, TY, TZ>;
+    return sizeof(double) * (size_t)(2 + DIM + NS) * (G::NC + G::NB) <= 112 * 1024 ? 2 : 1;
+}
+
 // shared-memory slot of tile-local zone (x, y, z); at most one coordinate
 // lies outside the tile extents (ex, ey, ez)
 template <int DIM, int TX, int TY, int TZ>
@@ -143,7 +153,8 @@ __device__ __forceinline__ double hllc_hydro(double g, double gm1_inv, int dir, 
 }
 
 template <int DIM, int NS, int TX, int TY, int TZ, int MODE>
-__global__ void __launch_bounds__(TileGeom<DIM, TX, TY, TZ>::THREADS, 1)
+__global__ void __launch_bounds__(TileGeom<DIM, TX, TY, TZ>::THREADS,
+                                  stencil_min_blocks<DIM, NS, TX, TY, TZ>())
 stencil_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __restrict__ boxes,
                const TileDev* __restrict__ tiles, const double* __restrict__ U, double* __restrict__ Aout,
                RhsArgs ra) {
