@@ -26,24 +26,28 @@ __global__ void set_scalar_kernel(double* p, double v) { *p = v; }
 // rhs into the stencil kernel instead.
 __global__ void rhs_kernel(int nvar, int dim, long long N, const double* __restrict__ Um,
                            const double* __restrict__ Anew_m, RhsArgs ra) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)nvar * N) return;
-    const int f = (int)(i / N);
-    const long long z = i - (long long)f * N;
+    // one thread per zone, every field: the step's scalars once per zone
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= N) return;
     const double dt = *ra.dt;
     const double dtm = dt * ra.dtm_frac;
-    const bool reactive = f >= 1 + dim;
-    const int r = f - 1 - dim;
-    double v = Um[i];
-    if (Anew_m) v += dtm * (Anew_m[i] - ra.Aold_m[i]);
-    if (reactive) v -= dtm * ra.Rnext[r * N + z];
-    double I = 0.0;
-    for (int l = 0; l < ra.M; l++) {
-        double src = ra.Aold[l][i];
-        if (reactive) src += ra.Rold[l][r * N + z];
-        I += (ra.qw[l] * dt) * src;
+    double qdt[3];
+    for (int l = 0; l < 3; l++) qdt[l] = ra.qw[l] * dt;
+    for (int f = 0; f < nvar; f++) {
+        const long long i = (long long)f * N + z;
+        const bool reactive = f >= 1 + dim;
+        const long long ir = (long long)(f - 1 - dim) * N + z;
+        double v = Um[i];
+        if (Anew_m) v += dtm * (Anew_m[i] - ra.Aold_m[i]);
+        if (reactive) v -= dtm * ra.Rnext[ir];
+        double I = 0.0;
+        for (int l = 0; l < ra.M; l++) {
+            double src = ra.Aold[l][i];
+            if (reactive) src += ra.Rold[l][ir];
+            I += qdt[l] * src;
+        }
+        ra.rhs[i] = v + I;
     }
-    ra.rhs[i] = v + I;
 }
 
 // I = sum_l (q_l dt) (A_l + R_l)
@@ -262,20 +266,38 @@ void weights(int type, int M, double tau[3], double q[2][3]) {
     }
 }
 
+// The terms of the node integral sum_l q_{m,l} (A_l + R_l): nodes with weight
+// zero are left out (Radau: node 0), and nodes whose A and R are the same
+// arrays (every node in the first iteration, when all hold A and R at U^n)
+// become one term with the summed weight; ra.M counts the terms.
 RhsArgs rhs_args(const sdc_ctx* c, const double* const* Aold, const double* const* Rold, int m,
                  const double* dt_dev) {
     RhsArgs ra;
+    int nt = 0;
     for (int l = 0; l < 3; l++) {
-        ra.Aold[l] = l < c->M ? Aold[l] : nullptr;
-        ra.Rold[l] = l < c->M ? Rold[l] : nullptr;
-        ra.qw[l] = c->q[m][l];
+        ra.Aold[l] = nullptr;
+        ra.Rold[l] = nullptr;
+        ra.qw[l] = 0.0;
+    }
+    for (int l = 0; l < c->M; l++) {
+        const double w = c->q[m][l];
+        if (w == 0.0) continue;
+        int t = 0;
+        while (t < nt && !(ra.Aold[t] == Aold[l] && ra.Rold[t] == Rold[l])) t++;
+        if (t == nt) {
+            ra.Aold[nt] = Aold[l];
+            ra.Rold[nt] = Rold[l];
+            ra.qw[nt] = 0.0;
+            nt++;
+        }
+        ra.qw[t] += w;
     }
     ra.Rnext = Rold[m + 1];
     ra.Aold_m = Aold[m];
     ra.rhs = c->rhs;
     ra.dt = dt_dev;
     ra.dtm_frac = c->tau[m + 1] - c->tau[m];
-    ra.M = c->M;
+    ra.M = nt;
     return ra;
 }
 
@@ -336,13 +358,13 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
             RhsArgs ra = rhs_args(c, Aold, Rold, m, dt_dev);
             if (m == 0 || !with_A) {
                 // no A^{m,(k+1)} - A^{m,(k)} term: node 0 is fixed, or A is off
-                SDC_LAUNCH(prof, CLS_OTHER, (rhs_kernel<<<grid_for((long long)c->nvar * N, EW_BLOCK), EW_BLOCK, 0,
+                SDC_LAUNCH(prof, CLS_OTHER, (rhs_kernel<<<grid_for(N, EW_BLOCK), EW_BLOCK, 0,
                                                            st>>>(c->nvar, c->dim, N, node[m], nullptr, ra),
                                              cudaGetLastError()));
             } else if (fourth) {
                 SDC_LAUNCH(prof, CLS_STENCIL, launch_advective4(c->P, c->dim, N, c->d_boxes, c->nbox, node[m],
                                                                 Anew[m], c->fw, st));
-                SDC_LAUNCH(prof, CLS_OTHER, (rhs_kernel<<<grid_for((long long)c->nvar * N, EW_BLOCK), EW_BLOCK, 0,
+                SDC_LAUNCH(prof, CLS_OTHER, (rhs_kernel<<<grid_for(N, EW_BLOCK), EW_BLOCK, 0,
                                                            st>>>(c->nvar, c->dim, N, node[m], Anew[m], ra),
                                              cudaGetLastError()));
             } else {
