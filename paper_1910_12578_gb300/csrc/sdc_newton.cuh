@@ -70,6 +70,7 @@ struct ZoneState {
     double ak[NR];  // a_j rho^(o_j - 1) (alpha chain)
     int iters, status;
     bool newton, have_k, done;
+    bool r_final;   // G holds R at the solution (set by the stop test's last step)
 };
 
 // Set up a zone: rw = reactive part of the rhs, w = the (density-rescaled)
@@ -110,11 +111,30 @@ __device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, 
     S.iters = 0;
     S.status = ZONE_MAXIT;
     S.newton = true;
+    S.r_final = false;
     S.h = PTC_H0;
     S.have_k = eval_state<NS, TOPO>(P, rho, S.inv_rho, S.ke, S.ym, S.ak, S.w, S.rw, dtm, S.wE, S.k, S.dk, S.dfac, S.Y,
                                     S.G, S.phi);
     S.done = !S.have_k;
     if (!S.have_k) S.status = ZONE_NONPHYSICAL;
+}
+
+// The stop test: max(|d(rho E)|/|rho E|, max_i |d(rho X_i)|/rho) <= rtol at the trial.
+template <int NS, typename MT>
+__device__ __forceinline__ bool newton_step_small(const ZoneState<NS>& S, const NewtonCfg& cfg, const MT* dv,
+                                                  const double* tr) {
+    bool small = fabs((double)dv[0]) <= cfg.rtol * fabs(tr[0]);
+    const double tol_x = cfg.rtol * S.rho;
+    if constexpr (sizeof(MT) == 8) {
+        // |dv_i| <= tol_x on the integer pipe (mag2 orders like |x|; a nan step fails)
+        const unsigned long long mt = mag2(tol_x);
+#pragma unroll
+        for (int i = 0; i < NS; i++) small = small && (mag2((double)dv[1 + i]) <= mt);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NS; i++) small = small && (fabs((double)dv[1 + i]) <= tol_x);
+    }
+    return small;
 }
 
 // One pass of the solve (one linear solve); sets done and status at the end.
@@ -149,6 +169,38 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     bool ok = true;
 #pragma unroll
     for (int i = 0; i < NS; i++) ok = ok && (tr[1 + i] >= S.lower[i]);
+    // (NS <= 7: with 13 species the extra live arrays of this path cost more in
+    // register spills than the evaluation it saves)
+    if (NS <= 7 && S.newton && ok && newton_step_small<NS, MT>(S, cfg, dv, tr)) {
+        // The step meets the stop test, so an admissible trial (T positive and
+        // finite, R finite) is the solution: only R at the trial is needed, not
+        // the residual, its norm or the matrix's factor f.  Otherwise the full
+        // evaluation below takes the decision.
+        const double T = P.gm1 * (tr[0] - S.ke) * S.inv_rho;
+        if (T > 0.0 && T < INFINITY) {
+            double kf[NR], dkf[NR], Yf[NS], Rf[N];
+            if constexpr (TOPO == TOPO_CHAIN) {
+                double dff;
+                rate_consts_k<NR>(P, S.ak, T, kf, dff);
+            } else {
+                rate_consts<NR>(P, S.rho, T, kf, dkf);
+            }
+#pragma unroll
+            for (int i = 0; i < NS; i++) Yf[i] = tr[1 + i] * S.ym[i];
+            sources<NS, TOPO>(P, S.rho, kf, Yf, Rf);
+            bool finite = true;
+#pragma unroll
+            for (int r = 0; r < N; r++) finite = finite && (((dbits(Rf[r]) >> 52) & 0x7ff) != 0x7ff);
+            if (finite) {
+#pragma unroll
+                for (int r = 0; r < N; r++) { S.w[r] = tr[r]; S.G[r] = Rf[r]; }
+                S.r_final = true;
+                S.status = ZONE_OK;
+                S.done = true;
+                return;
+            }
+        }
+    }
     double kt[NR], dkt[NR], Yt[NS], Gt[N];
     double phit = 0.0, dfact = 0.0;
     if (ok)
@@ -156,20 +208,7 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
                                   phit);
     // an admissible Newton step that meets the stop test converges even if the
     // residual grew by round-off at the root
-    bool small = false;
-    if (S.newton && ok) {
-        small = fabs((double)dv[0]) <= cfg.rtol * fabs(tr[0]);
-        const double tol_x = cfg.rtol * S.rho;
-        if constexpr (sizeof(MT) == 8) {
-            // |dv_i| <= tol_x on the integer pipe (mag2 orders like |x|; a nan step fails)
-            const unsigned long long mt = mag2(tol_x);
-#pragma unroll
-            for (int i = 0; i < NS; i++) small = small && (mag2((double)dv[1 + i]) <= mt);
-        } else {
-#pragma unroll
-            for (int i = 0; i < NS; i++) small = small && (fabs((double)dv[1 + i]) <= tol_x);
-        }
-    }
+    const bool small = S.newton && ok && newton_step_small<NS, MT>(S, cfg, dv, tr);
     if (S.newton && !small && (!ok || phit > S.phi)) {
         S.newton = false;
         S.h = PTC_H0;
@@ -211,8 +250,12 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
 // Reactive source at the final state (from its cached rate constants).
 template <int NS, int TOPO>
 __device__ __forceinline__ void zone_source(const ZoneState<NS>& S, const NetParams& P, double* Rout) {
+    constexpr int N = NS + 1;
     constexpr int NR = NS - 1;
-    if (S.have_k) {
+    if (S.r_final) {
+#pragma unroll
+        for (int r = 0; r < N; r++) Rout[r] = S.G[r];
+    } else if (S.have_k) {
         sources<NS, TOPO>(P, S.rho, S.k, S.Y, Rout);
     } else {
         const double T = P.gm1 * (S.w[0] - S.ke) * S.inv_rho;
