@@ -64,7 +64,9 @@ __device__ __forceinline__ long long neighbour(const ZoneCoord& q, int d, int o)
     return q.off + (long long)(c[0] + q.n[0] * (c[1] + q.n[1] * c[2]));
 }
 
-// out = a + coef * sum_{d < dim, d != skip} (b(z+e_d) - 2 b(z) + b(z-e_d)), nf fields
+// out = a + coef * sum_{d < dim, d != skip} (b(z+e_d) - 2 b(z) + b(z-e_d)), nf fields,
+// formed as a + coef (sum of the neighbour pairs - 2 n_d b(z)): per field one add
+// per neighbour, then two FMAs (the FP64 pipe is the bound)
 __global__ void lap_combine_kernel(int dim, int nf, long long N, const BoxDev* __restrict__ boxes, int nbox,
                                    const double* __restrict__ a, const double* __restrict__ b, double coef, int skip,
                                    double* __restrict__ out) {
@@ -72,19 +74,24 @@ __global__ void lap_combine_kernel(int dim, int nf, long long N, const BoxDev* _
     if (z >= N) return;
     const ZoneCoord q = zone_coord(boxes, nbox, z);
     long long zp[3] = {z, z, z}, zm[3] = {z, z, z};
+    int nd = 0;
     for (int d = 0; d < dim; d++) {
         zp[d] = neighbour(q, d, 1);
         zm[d] = neighbour(q, d, -1);
+        if (d != skip) nd++;
     }
+    const double c2 = -2.0 * nd;
     for (int f = 0; f < nf; f++) {
         const long long o = (long long)f * N;
-        const double bz = b[o + z];
-        double l = 0.0;
+        double sn = 0.0;
+        bool first = true;
         for (int d = 0; d < dim; d++) {
             if (d == skip) continue;
-            l += b[o + zp[d]] - 2.0 * bz + b[o + zm[d]];
+            const double pair = b[o + zp[d]] + b[o + zm[d]];
+            sn = first ? pair : sn + pair;
+            first = false;
         }
-        out[o + z] = a[o + z] + coef * l;
+        out[o + z] = fma(coef, fma(c2, b[o + z], sn), a[o + z]);
     }
 }
 
@@ -121,9 +128,9 @@ __global__ void face_avg_kernel(int dir, int nf, long long N, const BoxDev* __re
 // physical Euler flux along dir of the primitive state q
 __device__ __forceinline__ void euler_flux(int dim, int nspec, double igm1, int dir, const double* q, double* F) {
     const double rho = q[0], un = q[1 + dir], p = q[1 + dim];
-    double ke = 0.0;
-    for (int d = 0; d < dim; d++) ke += 0.5 * rho * q[1 + d] * q[1 + d];
-    const double E = p * igm1 + ke;
+    double k2 = 0.0;
+    for (int d = 0; d < dim; d++) k2 = fma(q[1 + d], q[1 + d], k2);
+    const double E = fma(p, igm1, 0.5 * rho * k2);
     F[0] = rho * un;
     for (int d = 0; d < dim; d++) F[1 + d] = rho * un * q[1 + d] + (d == dir ? p : 0.0);
     F[1 + dim] = (E + p) * un;
@@ -165,14 +172,16 @@ __global__ void div_kernel(int dir, int nf, long long N, const BoxDev* __restric
 __global__ void update4_kernel(int nvar, int dim, long long N, const double* __restrict__ rhs,
                                const double* __restrict__ R, const double* __restrict__ dt_dev, double dt_frac,
                                double dtm_host, double* __restrict__ U) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)nvar * N) return;
-    const int f = (int)(i / N);
-    const long long z = i - (long long)f * N;
+    // one thread per zone, every field (no 64-bit division per element)
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= N) return;
     const double dtm = dt_dev ? (*dt_dev) * dt_frac : dtm_host;
-    double v = rhs[i];
-    if (f >= 1 + dim) v += dtm * R[(long long)(f - 1 - dim) * N + z];
-    U[i] = v;
+    for (int f = 0; f < nvar; f++) {
+        const long long i = (long long)f * N + z;
+        double v = rhs[i];
+        if (f >= 1 + dim) v += dtm * R[(long long)(f - 1 - dim) * N + z];
+        U[i] = v;
+    }
 }
 
 cudaError_t lap(int dim, int nf, long long N, const BoxDev* boxes, int nbox, const double* a, const double* b,
@@ -228,7 +237,7 @@ cudaError_t launch_newton4(const NetParams& P, const NewtonCfg& cfg, int prec, i
                            zone_iters, stats, st, variant, queue, persistent_blocks)) != cudaSuccess)
         return e;
     if ((e = lap(dim, n, N, boxes, nbox, w.Rc, w.Rc, 1.0 / 24.0, -1, Rout, st)) != cudaSuccess) return e;
-    update4_kernel<<<fgrid((long long)nv * N), F_BLOCK, 0, st>>>(nv, dim, N, rhs, Rout, dt_dev, dt_frac, dtm_host,
+    update4_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(nv, dim, N, rhs, Rout, dt_dev, dt_frac, dtm_host,
                                                                   Uout);
     return cudaGetLastError();
 }
