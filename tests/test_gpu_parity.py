@@ -468,6 +468,91 @@ def test_batched_boxes_match_per_box_oracle(torch_cuda):
         off += nz
 
 
+def test_tiny_boxes_match_per_box_oracle(torch_cuda):
+    """Boxes narrower than the tile and than the 2-zone halo (edges 1, 2, 3, 5;
+    the periodic halo wraps onto the box itself), with seeded flow in every
+    direction, in one context: each box equals the oracle run on it alone over
+    two steps."""
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    rng = np.random.default_rng(21)
+    net = W.alpha_chain(7, np.random.default_rng(5))
+    Ps, Us = [], []
+    for n in [(1, 2, 3), (3, 3, 3), (5, 1, 2), (2, 5, 1), (1, 1, 1)]:
+        h = 1.0 / 64
+        P = W.Problem(dim=3, n=n, dx=(h, h, h), gamma=5 / 3, net=net, n_nodes=3, n_iters=2)
+        shp = (n[2], n[1], n[0])
+        rho = 1.0 + 0.1 * rng.random(shp)
+        vel = [0.2 * (rng.random(shp) - 0.5) for _ in range(3)]
+        T = 0.5 + 0.5 * rng.random(shp)
+        X = rng.dirichlet(np.ones(7), size=shp)
+        U = W.conserved_from(P.gamma, rho, vel, T, [X[..., i] for i in range(7)])
+        Ps.append(P)
+        Us.append(U)
+    dt = min(O.Oracle(P).cfl_dt(U) for P, U in zip(Ps, Us))
+    ctx = sdc.Context(Ps)
+    Ud = dev(torch, np.concatenate([U.reshape(P.nvar, -1) for P, U in zip(Ps, Us)], axis=1))
+    for _ in range(2):
+        st = ctx.step(Ud, dt)
+    torch.cuda.synchronize()
+    G = Ud.cpu().numpy()
+    off = 0
+    for P, U in zip(Ps, Us):
+        o = O.Oracle(P)
+        V = U
+        for _ in range(2):
+            V, _ = o.step(V, dt)
+        nz = P.nzones
+        e = rel_err(G[:, off:off + nz], V.reshape(P.nvar, -1), P.nvar, P.dim)
+        assert e.max() <= TOL64, (P.n, e)
+        off += nz
+    assert st.n_fail == 0
+
+
+def test_newton_status_codes_on_unphysical_zones(torch_cuda):
+    """Zones whose rhs has no positive temperature (rho E below the kinetic
+    energy), or a grossly negative composition (no admissibility floor then),
+    against the oracle: the same per-zone status (nonphysical where no state
+    with a positive temperature exists), the same failure count, and the other
+    zones' solutions to 1e-12."""
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = PROBS["box16"]
+    o = O.Oracle(P)
+    dt = o.cfl_dt(U)
+    rhs, guess, dtm = oracle_sweep_inputs(o, U, dt, k_iters=1)
+    rhs = rhs.reshape(P.nvar, -1).copy()
+    guess = guess.reshape(P.nvar, -1).copy()
+    d = P.dim
+    bad_T = [5, 777, 3000]
+    for z in bad_T:                              # rho E below the kinetic energy: T < 0
+        ke = 0.5 * np.sum(rhs[1:1 + d, z] ** 2) / rhs[0, z]
+        rhs[1 + d, z] = 0.5 * ke
+        guess[1 + d, z] = 0.5 * ke
+    bad_X = [100, 2048]
+    for z in bad_X:                              # X_0 = -0.5, X_1 = 1.5
+        rhs[2 + d, z] = -0.5 * rhs[0, z]
+        rhs[3 + d, z] = 1.5 * rhs[0, z]
+    shp = (P.nvar,) + U.shape[1:]
+    Uo, Ro, zs_o, zi_o, st_o = o.react_newton(rhs.reshape(shp), dtm, guess.reshape(shp))
+    ctx = sdc.Context(P)
+    Ud = dev(torch, guess.reshape(shp))
+    Rd = torch.empty((P.net.nspec + 1,) + U.shape[1:], dtype=torch.float64, device="cuda")
+    zs = torch.empty(U.shape[1:], dtype=torch.int32, device="cuda")
+    zi = torch.empty(U.shape[1:], dtype=torch.int32, device="cuda")
+    st = ctx.react_newton(dev(torch, rhs.reshape(shp)), dtm, Ud, Rd, zs, zi)
+    torch.cuda.synchronize()
+    zs_g = zs.cpu().numpy().reshape(-1)
+    assert np.array_equal(zs_g, zs_o.reshape(-1))
+    assert st.n_fail == st_o.n_fail and st.n_fail >= len(bad_T)
+    assert all(zs_g[z] != 0 for z in bad_T)
+    good = zs_g == 0
+    G = Ud.cpu().numpy().reshape(P.nvar, -1)
+    Uo = Uo.reshape(P.nvar, -1)
+    e = rel_err(G[:, good], Uo[:, good], P.nvar, P.dim)
+    assert e.max() <= TOL64, e
+
+
 def test_full_size_config_step_parity(torch_cuda):
     """64^3, 7 species, 3 Gauss-Lobatto nodes, 3 iterations: one full step at
     the size the benchmark times, every zone compared with the oracle."""
