@@ -58,8 +58,9 @@ def parse():
     p.add_argument("--prec", choices=["fp64", "fp32jac"], default="fp64")
     p.add_argument("--space-order", type=int, choices=[2, 4], default=2,
                    help="2: PLM/MC/HLLC; 4: the fourth-order finite-volume operators (smooth-flow form)")
-    p.add_argument("--nodes", choices=["lobatto", "radau"], default="lobatto",
-                   help="temporal node set: Gauss-Lobatto (trapezoid/Simpson) or node 0 + Radau IIA points")
+    p.add_argument("--nodes", choices=["lobatto", "radau", "radau4"], default="lobatto",
+                   help="temporal node set: Gauss-Lobatto (trapezoid/Simpson), node 0 + the Radau IIA points "
+                        "1/3, 1, or (radau4) node 0 + the three Radau IIA points of s = 3")
     p.add_argument("--seed", type=int, default=None,
                    help="network / box seed (default: 1 for the single boxes, 3 for the batch)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -81,7 +82,7 @@ def workload(name, seed, nodes="lobatto"):
         desc = ("200 ragged periodic boxes (edges from {16,24,32,48,64} per axis, dx=1/64), 7-species alpha chain "
                 "(seeded), hot spots 1.2-3x over T0=0.5, 3 Gauss-Lobatto nodes, 3 SDC iterations, CFL 0.5")
         for p in Ps:
-            p.nodes = nodes
+            _set_nodes(p, nodes)
         return Ps, U, _nodes_desc(desc, nodes)
     if name == "box64":
         P, U = W.config_box(n=64, nspec=7, n_nodes=3, n_iters=3, seed=seed, T0=0.5)
@@ -91,13 +92,22 @@ def workload(name, seed, nodes="lobatto"):
         P, U = W.config_box(n=256, nspec=13, n_nodes=3, n_iters=4, seed=seed, T0=0.5)
         desc = ("256^3 periodic box, 13-species alpha chain (seeded), hot spot 2x over T0=0.5, "
                 "3 Gauss-Lobatto nodes, 4 SDC iterations, CFL 0.5")
-    P.nodes = nodes
+    _set_nodes(P, nodes)
     return P, U, _nodes_desc(desc, nodes)
+
+
+def _set_nodes(P, nodes):
+    P.nodes = "lobatto" if nodes == "lobatto" else "radau"
+    if nodes == "radau4":
+        P.n_nodes = 4
 
 
 def _nodes_desc(desc, nodes):
     if nodes == "lobatto":
         return desc
+    if nodes == "radau4":
+        return desc.replace("3 Gauss-Lobatto nodes", "4 nodes (0 and the Radau IIA points (4 -/+ sqrt 6)/10, 1; the "
+                            "integral through the Radau points)")
     return desc.replace("3 Gauss-Lobatto nodes", "3 nodes (0 and the Radau IIA points 1/3, 1; the integral through the "
                         "Radau points)")
 
@@ -238,7 +248,7 @@ def run_reference(args):
     if args.config == "box256":
         # bounded sample: a 64^3 box with the same network and parameters
         P, U = W.config_box(n=64, nspec=13, n_nodes=3, n_iters=4, seed=args.seed, T0=0.5)
-        P.nodes = args.nodes
+        _set_nodes(P, args.nodes)
         P.space_order = args.space_order
         desc += " (sample: 64^3 box, same network)"
     if isinstance(P, list):

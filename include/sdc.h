@@ -89,7 +89,8 @@ typedef struct {
 
 typedef struct {
     double gamma;          /* gamma-law gas, p = rho T                      */
-    int n_nodes;           /* M: temporal nodes including node 0 (2 or 3)   */
+    int n_nodes;           /* M: temporal nodes including node 0 (2 or 3;
+                              Radau also 4)                                   */
     int n_iters;           /* K: SDC iterations per step, >= 1              */
     int limiter;           /* 1 = MC limited PLM, 0 = unlimited centred PLM */
     sdc_precision prec;    /* Newton linear algebra precision               */
@@ -115,7 +116,8 @@ typedef struct {
      Eq. sdc:general by the trapezoid (M = 2) or Simpson's (M = 3) rule through
      all nodes (section 2).
    SDC_NODES_RADAU: node 0 at t^n and the M-1 right-endpoint Gauss-Radau points
-     ({1} or {1/3, 1}); the integral through those points only, so that the
+     ({1}, {1/3, 1} or {(4-sqrt 6)/10, (4+sqrt 6)/10, 1}); the integral through
+     those points only, so that the
      iteration converges to Radau IIA collocation, which is L-stable: an
      instance of the alternative quadratures for very stiff burning that the
      paper's closing section (Future Developments) names as work in progress. */
@@ -132,8 +134,9 @@ typedef struct {
    allocate its device workspace and upload the network.
    Errors: SDC_ERR_INVALID_ARG (nbox < 1, bad dims, a box of 2^31 zones or
    more, nspec > SDC_MAX_SPEC, nreac > SDC_MAX_REAC, species index out of
-   range, n_nodes not 2/3, n_iters < 1, gamma <= 1, node_type or space_order
-   not one of theirs), SDC_ERR_OOM, SDC_ERR_CUDA.  *out is NULL on error. */
+   range, n_nodes not 2/3 (2-4 for Radau nodes), n_iters < 1, gamma <= 1,
+   node_type or space_order not one of theirs), SDC_ERR_OOM, SDC_ERR_CUDA.
+   *out is NULL on error. */
 sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net,
                         const sdc_params* prm, void* cuda_stream, sdc_ctx** out);
 
@@ -295,7 +298,8 @@ sdc_status sdc_sizes(const sdc_ctx* ctx, long long* ntot, int* nvar, int* nreact
      GPU (other streams, other threads) race on it: serialise them.
    - stats: NULL (asynchronous) or filled after waiting for cuda_stream;
      SDC_ERR_NEWTON_NOCONV as in sdc_step.
-   It calls no cudaMalloc, cudaFree or other allocating routine. */
+   It calls no cudaMalloc, cudaFree or other allocating routine.  n_nodes 2 or 3
+   (four Radau nodes need a context). */
 #define SDC_STATIC_SCRATCH_BYTES (48ull << 20)
 #define SDC_STATIC_MAX_BOXES 32
 sdc_status sdc_step_static(const sdc_box* boxes, int nbox, const sdc_network* net, const sdc_params* prm,

@@ -14,10 +14,10 @@ struct RhsAdjArgs {
     const double* rhsbar;
     double* Ubar_m;         // adjoint of U_m (of this iteration), or of U^n for m = 0
     double* Abar_new_m;     // adjoint of A_m of this iteration (NULL for m = 0)
-    double* Abar_old[3];    // adjoints of A_l of the previous iteration
-    double* Rbar_old[3];    // adjoints of R_l of the previous iteration
+    double* Abar_old[MAXM];  // adjoints of A_l of the previous iteration
+    double* Rbar_old[MAXM];  // adjoints of R_l of the previous iteration
     double dtm;
-    double qdt[3];          // q_{m,l} dt
+    double qdt[MAXM];        // q_{m,l} dt
 };
 
 bool adjoint_supported(int dim, int nspec, int topo);

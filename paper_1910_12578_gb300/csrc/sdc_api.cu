@@ -31,8 +31,8 @@ __global__ void rhs_kernel(int nvar, int dim, long long N, const double* __restr
     if (z >= N) return;
     const double dt = *ra.dt;
     const double dtm = dt * ra.dtm_frac;
-    double qdt[3];
-    for (int l = 0; l < 3; l++) qdt[l] = ra.qw[l] * dt;
+    double qdt[MAXM];
+    for (int l = 0; l < MAXM; l++) qdt[l] = ra.qw[l] * dt;
     for (int f = 0; f < nvar; f++) {
         const long long i = (long long)f * N + z;
         const bool reactive = f >= 1 + dim;
@@ -52,7 +52,8 @@ __global__ void rhs_kernel(int nvar, int dim, long long N, const double* __restr
 
 // I = sum_l (q_l dt) (A_l + R_l)
 __global__ void node_integral_kernel(int nvar, int dim, int M, long long N, const double* __restrict__ A,
-                                     const double* __restrict__ R, double q0, double q1, double q2, double dt,
+                                     const double* __restrict__ R, double q0, double q1, double q2, double q3,
+                                     double dt,
                                      double* __restrict__ I) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)nvar * N) return;
@@ -61,7 +62,7 @@ __global__ void node_integral_kernel(int nvar, int dim, int M, long long N, cons
     const int n = nvar - 1 - dim;
     const bool reactive = f >= 1 + dim;
     const int r = f - 1 - dim;
-    const double q[3] = {q0, q1, q2};
+    const double q[MAXM] = {q0, q1, q2, q3};
     double s = 0.0;
     for (int l = 0; l < M; l++) {
         double src = A[(long long)l * nvar * N + i];
@@ -160,17 +161,17 @@ struct sdc_ctx {
     NetParams P;
     NewtonCfg cfg;
     int M = 0, K = 0, limiter = 1, prec = 0;
-    double tau[3] = {0, 0, 0};
-    double q[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    double tau[MAXM] = {0, 0, 0, 0};
+    double q[MAXM - 1][MAXM] = {{0}};
     BoxDev* d_boxes = nullptr;
     TileDev* d_tiles = nullptr;
     int ntiles = 0;
     double* d_dt = nullptr;
-    double* node_ws[2] = {nullptr, nullptr};  // node 0 (copy of U^n), node 1 when M = 3
+    double* node_ws[MAXM - 1] = {nullptr};    // node 0 (copy of U^n), nodes 1..M-2
     double* A0 = nullptr;                     // A at node 0 (fixed within a step)
     double* R0 = nullptr;
-    double* Ag[2][3] = {{nullptr}};           // two generations of A at nodes 1..M-1
-    double* Rg[2][3] = {{nullptr}};
+    double* Ag[2][MAXM] = {{nullptr}};        // two generations of A at nodes 1..M-1
+    double* Rg[2][MAXM] = {{nullptr}};
     double* rhs = nullptr;
     DevStats* d_stats = nullptr;
     unsigned long long* d_smax = nullptr;
@@ -193,9 +194,9 @@ struct sdc_ctx {
         bool ready = false;
         double* work = nullptr;        // the recomputed step
         std::vector<double*> store;    // U_m^{(k+1)}, k = 0..K-1, m = 1..M-1
-        double* Ubar_node[3] = {nullptr, nullptr, nullptr};
-        double* Abar[2][3] = {{nullptr}};
-        double* Rbar[2][3] = {{nullptr}};
+        double* Ubar_node[MAXM] = {nullptr};
+        double* Abar[2][MAXM] = {{nullptr}};
+        double* Rbar[2][MAXM] = {{nullptr}};
         double *Abar_n = nullptr, *Rbar_n = nullptr, *Ubar_n = nullptr, *rhsbar = nullptr;
         double *G = nullptr, *abar_zone = nullptr;
     } adj;
@@ -242,13 +243,29 @@ bool is_alpha_chain(const sdc_network* net) {
 // through those points only (weight 0 for node 0): the Radau IIA coefficients
 // as differences a_{m+1,l} - a_{m,l} (s = 1: a = 1; s = 2: a = [[5/12, -1/12],
 // [3/4, 1/4]]).
-void weights(int type, int M, double tau[3], double q[2][3]) {
-    for (int m = 0; m < 2; m++)
-        for (int l = 0; l < 3; l++) q[m][l] = 0.0;
+void weights(int type, int M, double tau[MAXM], double q[MAXM - 1][MAXM]) {
+    for (int m = 0; m < MAXM - 1; m++)
+        for (int l = 0; l < MAXM; l++) q[m][l] = 0.0;
+    for (int l = 0; l < MAXM; l++) tau[l] = 1.0;
     if (type == SDC_NODES_RADAU) {
         if (M == 2) {
             tau[0] = 0.0; tau[1] = 1.0; tau[2] = 1.0;
             q[0][1] = 1.0;
+        } else if (M == 4) {
+            // s = 3: c = (4 -/+ sqrt 6)/10, 1 and the Radau IIA coefficients
+            // a_11 = (88 - 7 r)/360, a_12 = (296 - 169 r)/1800, a_13 = (-2 + 3 r)/225,
+            // a_21 = (296 + 169 r)/1800, a_22 = (88 + 7 r)/360, a_23 = (-2 - 3 r)/225,
+            // a_31 = (16 - r)/36, a_32 = (16 + r)/36, a_33 = 1/9 (r = sqrt 6)
+            const double r = sqrt(6.0);
+            const double a[3][3] = {{(88.0 - 7.0 * r) / 360.0, (296.0 - 169.0 * r) / 1800.0, (-2.0 + 3.0 * r) / 225.0},
+                                    {(296.0 + 169.0 * r) / 1800.0, (88.0 + 7.0 * r) / 360.0, (-2.0 - 3.0 * r) / 225.0},
+                                    {(16.0 - r) / 36.0, (16.0 + r) / 36.0, 1.0 / 9.0}};
+            tau[0] = 0.0; tau[1] = (4.0 - r) / 10.0; tau[2] = (4.0 + r) / 10.0; tau[3] = 1.0;
+            for (int l = 0; l < 3; l++) {
+                q[0][1 + l] = a[0][l];
+                q[1][1 + l] = a[1][l] - a[0][l];
+                q[2][1 + l] = a[2][l] - a[1][l];
+            }
         } else {
             tau[0] = 0.0; tau[1] = 1.0 / 3.0; tau[2] = 1.0;
             q[0][1] = 5.0 / 12.0; q[0][2] = -1.0 / 12.0;
@@ -274,7 +291,7 @@ RhsArgs rhs_args(const sdc_ctx* c, const double* const* Aold, const double* cons
                  const double* dt_dev) {
     RhsArgs ra;
     int nt = 0;
-    for (int l = 0; l < 3; l++) {
+    for (int l = 0; l < MAXM; l++) {
         ra.Aold[l] = nullptr;
         ra.Rold[l] = nullptr;
         ra.qw[l] = 0.0;
@@ -323,7 +340,10 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
         (e = cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned long long) * QUEUE_SLOTS, st)) != cudaSuccess)
         return e;
     int qslot = 0;
-    double* node[3] = {c->node_ws[0], c->M == 3 ? c->node_ws[1] : U, U};
+    double* node[MAXM];
+    node[0] = c->node_ws[0];
+    for (int m = 1; m < c->M - 1; m++) node[m] = c->node_ws[m];
+    node[c->M - 1] = U;
     if ((e = cudaMemcpyAsync(node[0], U, ubytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
     RhsArgs none = rhs_args(c, (const double* const*)c->Ag[0], (const double* const*)c->Rg[0], 0, dt_dev);
     const bool fourth = c->space_order == 4;
@@ -347,13 +367,19 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
     } else if ((e = cudaMemsetAsync(c->R0, 0, sizeof(double) * c->nw * N, st)) != cudaSuccess) {
         return e;
     }
-    const double* Aold[3] = {c->A0, c->A0, c->A0};
-    const double* Rold[3] = {c->R0, c->R0, c->R0};
+    const double* Aold[MAXM] = {c->A0, c->A0, c->A0, c->A0};
+    const double* Rold[MAXM] = {c->R0, c->R0, c->R0, c->R0};
     for (int k = 0; k < c->K; k++) {
         const int g = k & 1;
         // an operator that is off stays zero: its arrays are all the zeroed node-0 array
-        double* Anew[3] = {c->A0, with_A ? c->Ag[g][1] : c->A0, with_A ? c->Ag[g][2] : c->A0};
-        double* Rnew[3] = {c->R0, with_R ? c->Rg[g][1] : c->R0, with_R ? c->Rg[g][2] : c->R0};
+        double* Anew[MAXM];
+        double* Rnew[MAXM];
+        Anew[0] = c->A0;
+        Rnew[0] = c->R0;
+        for (int m = 1; m < MAXM; m++) {
+            Anew[m] = (with_A && m < c->M) ? c->Ag[g][m] : c->A0;
+            Rnew[m] = (with_R && m < c->M) ? c->Rg[g][m] : c->R0;
+        }
         for (int m = 0; m < c->M - 1; m++) {
             RhsArgs ra = rhs_args(c, Aold, Rold, m, dt_dev);
             if (m == 0 || !with_A) {
@@ -548,7 +574,8 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
         if (net->reac[2 * j] == net->reac[2 * j + 1]) return SDC_ERR_INVALID_ARG;
         if (net->prod[j] < 0 || net->prod[j] >= net->nspec) return SDC_ERR_INVALID_ARG;
     }
-    if (!(prm->gamma > 1.0) || (prm->n_nodes != 2 && prm->n_nodes != 3) || prm->n_iters < 1 ||
+    if (!(prm->gamma > 1.0) || prm->n_nodes < 2 || prm->n_nodes > 3 + (prm->node_type == SDC_NODES_RADAU) ||
+        prm->n_iters < 1 ||
         prm->newton_maxit < 1 || !(prm->newton_rtol > 0.0) ||
         (prm->prec != SDC_PREC_FP64 && prm->prec != SDC_PREC_FP32_JAC) ||
         (prm->node_type != SDC_NODES_LOBATTO && prm->node_type != SDC_NODES_RADAU) ||
@@ -647,7 +674,8 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     if ((e = ctx_alloc(c, (void**)&c->d_smax, sizeof(unsigned long long))) != cudaSuccess) return fail(e);
     const size_t ub = sizeof(double) * c->nvar * Ntot, rb = sizeof(double) * c->nw * Ntot;
     if ((e = ctx_alloc(c, (void**)&c->node_ws[0], ub)) != cudaSuccess) return fail(e);
-    if (c->M == 3 && (e = ctx_alloc(c, (void**)&c->node_ws[1], ub)) != cudaSuccess) return fail(e);
+    for (int m = 1; m < c->M - 1; m++)
+        if ((e = ctx_alloc(c, (void**)&c->node_ws[m], ub)) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->A0, ub)) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->R0, rb)) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->rhs, ub)) != cudaSuccess) return fail(e);
@@ -699,7 +727,7 @@ sdc_status sdc_node_integral(sdc_ctx* ctx, const double* A_nodes, const double* 
     if (!ctx || !A_nodes || !R_nodes || !I || m < 0 || m >= ctx->M - 1) return SDC_ERR_INVALID_ARG;
     const long long n = (long long)ctx->nvar * ctx->Ntot;
     node_integral_kernel<<<grid_for(n, EW_BLOCK), EW_BLOCK, 0, ctx->stream>>>(
-        ctx->nvar, ctx->dim, ctx->M, ctx->Ntot, A_nodes, R_nodes, ctx->q[m][0], ctx->q[m][1], ctx->q[m][2], dt, I);
+        ctx->nvar, ctx->dim, ctx->M, ctx->Ntot, A_nodes, R_nodes, ctx->q[m][0], ctx->q[m][1], ctx->q[m][2], ctx->q[m][3], dt, I);
     SDC_TRY(cudaGetLastError());
     return SDC_OK;
 }
@@ -958,8 +986,8 @@ sdc_status sdc_step_backward(sdc_ctx* ctx, const double* U_n, double dt, const d
     SDC_TRY(cudaMemcpyAsync(A.Ubar_node[M - 1], gU_np1, ub, cudaMemcpyDeviceToDevice, st));
     int gnew = 0, gold = 1;
     for (int k = K - 1; k >= 0; k--) {
-        double *Aold[3], *Rold[3];
-        for (int l = 0; l < 3; l++) {
+        double *Aold[MAXM], *Rold[MAXM];
+        for (int l = 0; l < MAXM; l++) {
             const bool un = (l == 0 || k == 0);  // values at U^n
             Aold[l] = un ? A.Abar_n : A.Abar[gold][l];
             Rold[l] = un ? A.Rbar_n : A.Rbar[gold][l];
@@ -982,7 +1010,7 @@ sdc_status sdc_step_backward(sdc_ctx* ctx, const double* U_n, double dt, const d
             ra.rhsbar = A.rhsbar;
             ra.Ubar_m = m >= 1 ? A.Ubar_node[m] : A.Ubar_n;
             ra.Abar_new_m = m >= 1 ? A.Abar[gnew][m] : nullptr;
-            for (int l = 0; l < 3; l++) {
+            for (int l = 0; l < MAXM; l++) {
                 ra.Abar_old[l] = Aold[l];
                 ra.Rbar_old[l] = Rold[l];
                 ra.qdt[l] = c->q[m][l] * dt;

@@ -17,6 +17,9 @@
 
 namespace sdcd {
 
+// temporal nodes of a step, at most (Radau: node 0 and three Radau IIA points)
+constexpr int MAXM = 4;
+
 enum { TOPO_GENERIC = 0, TOPO_CHAIN = 1 };
 enum { LAW_POWER = 0, LAW_ARRHENIUS = 1 };
 enum { ZONE_OK = 0, ZONE_MAXIT = 1, ZONE_NONPHYSICAL = 2, ZONE_SINGULAR = 3 };

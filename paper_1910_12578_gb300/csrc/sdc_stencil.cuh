@@ -40,15 +40,15 @@ enum { STENCIL_A = 0, STENCIL_A_RHS = 1 };
 // Arguments of the fused right-hand side (Eq. sdc:general, node m -> m+1):
 //   rhs = U^m + dtm (A^m_new - A^m_old) - dtm R^{m+1}_old + sum_l (q_l dt) (A_l_old + R_l_old)
 struct RhsArgs {
-    const double* Aold[3];   // A^{(k)} at the nodes
-    const double* Rold[3];   // R^{(k)} at the nodes ([n][Ntot])
-    const double* Rnext;     // R^{m+1,(k)}
-    const double* Aold_m;    // A^{m,(k)}
+    const double* Aold[MAXM];  // A^{(k)} of the integral's terms
+    const double* Rold[MAXM];  // R^{(k)} of the integral's terms ([n][Ntot])
+    const double* Rnext;       // R^{m+1,(k)}
+    const double* Aold_m;      // A^{m,(k)}
     double* rhs;
-    const double* dt;        // device scalar: the step size
-    double qw[3];            // q_{m,l} (units of dt)
-    double dtm_frac;         // dt_m / dt
-    int M;
+    const double* dt;          // device scalar: the step size
+    double qw[MAXM];           // weights of the terms (units of dt)
+    double dtm_frac;           // dt_m / dt
+    int M;                     // number of terms
 };
 
 template <int DIM, int TX, int TY, int TZ>
@@ -328,9 +328,9 @@ stencil_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __restric
     if (MODE == STENCIL_A_RHS) {
         const double dt = *ra.dt;
         const double dtm = dt * ra.dtm_frac;
-        double qdt[3];
+        double qdt[MAXM];
 #pragma unroll
-        for (int l = 0; l < 3; l++) qdt[l] = ra.qw[l] * dt;
+        for (int l = 0; l < MAXM; l++) qdt[l] = ra.qw[l] * dt;
 #pragma unroll
         for (int f = 0; f < NV; f++) {
             double v = fma(dtm, A[f] - __ldg(ra.Aold_m + f * Ntot + gi), __ldg(U + f * Ntot + gi));
@@ -339,7 +339,7 @@ stencil_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __restric
             if (reactive) v = fma(-dtm, __ldg(ra.Rnext + r * Ntot + gi), v);
             double I = 0.0;
 #pragma unroll
-            for (int l = 0; l < 3; l++) {
+            for (int l = 0; l < MAXM; l++) {
                 if (l < ra.M) {
                     double src = __ldg(ra.Aold[l] + f * Ntot + gi);
                     if (reactive) src += __ldg(ra.Rold[l] + r * Ntot + gi);

@@ -57,10 +57,13 @@ def torch_cuda():
 
 # ------------------------------------------------------------------ inputs
 def hot_spot_problem(n, limiter, nodes="lobatto"):
+    """nodes: "lobatto", "radau" (3 nodes) or "radau4" (node 0 and three Radau points)."""
     P, U = W.config_box(n=n, nspec=7, n_iters=3, seed=1, T0=0.5)
     P = copy.deepcopy(P)
     P.limiter = limiter
-    P.nodes = nodes
+    P.nodes = "radau" if nodes == "radau4" else nodes
+    if nodes == "radau4":
+        P.n_nodes = 4
     return P, U
 
 
@@ -301,7 +304,7 @@ def rate_errors(ga, d_rel, J, d_yield):
 
 
 @pytest.mark.parametrize("n,nsteps,limiter,nodes", [(8, 2, 1, "lobatto"), (32, 5, 1, "lobatto"), (8, 2, 0, "lobatto"),
-                                                    (32, 5, 0, "lobatto"), (8, 2, 1, "radau")])
+                                                    (32, 5, 0, "lobatto"), (8, 2, 1, "radau"), (8, 2, 1, "radau4")])
 def test_rate_gradient_hot_spot(torch_cuda, n, nsteps, limiter, nodes):
     """dL/da_j of the released energy and of the product yields against GPU
     finite differences (Gauss-Lobatto and Radau node sets)."""

@@ -62,6 +62,13 @@ def problems():
     P, U = W.config_box(n=16, nspec=13, n_iters=4, seed=0, T0=0.5)
     P.nodes = "radau"
     out["box16_13_radau"] = (P, U)
+    # four Radau nodes (node 0 and the three Radau IIA points of s = 3)
+    P, U = W.config_1d()
+    P.nodes, P.n_nodes, P.n_iters = "radau", 4, 4
+    out["1d_radau4"] = (P, U)
+    P, U = W.config_box(n=16, nspec=7, n_nodes=4, n_iters=3, seed=0, T0=0.5)
+    P.nodes = "radau"
+    out["box16_radau4"] = (P, U)
     # Sod's shock tube: 1D with the shock-heated gas reacting, and planar across
     # a 16^3 box along y and along z (limiter clipping, HLLC on both sides of a contact)
     out["sod1d"] = W.config_sod(n=128, dim=1)
@@ -185,6 +192,7 @@ def test_react_newton_parity(torch_cuda, name, k_iters, prec):
                                               ("box16_radau2", 2, 0), ("box16_13_radau", 1, 0),
                                               ("1d_o4", 4, 0), ("box16_o4", 2, 0), ("box16_o4", 1, 1),
                                               ("ragged_o4", 1, 0), ("box16_13_o4", 1, 0),
+                                              ("1d_radau4", 6, 0), ("box16_radau4", 2, 0), ("box16_radau4", 1, 1),
                                               ("sod1d", 20, 0), ("sod1d", 20, 1), ("sod3d_y", 3, 0),
                                               ("sod3d_y", 2, 1), ("sod3d_z", 2, 0)])
 def test_step_parity(torch_cuda, name, nsteps, prec):
@@ -208,7 +216,7 @@ def test_step_parity(torch_cuda, name, nsteps, prec):
 
 @pytest.mark.parametrize("name,nsteps,prec", [("1d", 4, 0), ("box16", 2, 0), ("box16", 1, 1), ("box16_radau", 1, 0),
                                               ("box16_13", 1, 0), ("box16_o4", 1, 0),
-                                              ("sod1d", 10, 0)])
+                                              ("sod1d", 10, 0), ("box16_radau4", 1, 0)])
 def test_strang_step_parity(torch_cuda, name, nsteps, prec):
     """sdc_step_strang (reactions dt/2, advection dt, reactions dt/2 by the same
     SDC step with one operator off) against the oracle's split step."""
