@@ -10,10 +10,10 @@
  *     U^{m+1,(k+1)} = U^{m,(k+1)} + dt_m [A^{m,(k+1)} - A^{m,(k)}]
  *                   + dt_m [R^{m+1,(k+1)} - R^{m+1,(k)}]
  *                   + int_{t^m}^{t^{m+1}} (A^{(k)} + R^{(k)}) dt
- *   with zone averages, explicit in A and implicit in R (an implicit
- *   equation for the new state), the integral built from the previous
- *   iteration at every node: trapezoid rule (2 Gauss-Lobatto nodes) or
- *   Simpson's rule (3 Gauss-Lobatto nodes).
+ *   with zone averages, explicit in A and implicit in R (the new node state
+ *   solves a nonlinear system zone by zone), the integral formed from the
+ *   previous iterate at every node: trapezoid rule (2 Gauss-Lobatto nodes),
+ *   Simpson's rule (3 Gauss-Lobatto nodes), or through the Radau points.
  *
  * Conventions used by every call:
  *   - Conserved fields, in this order: rho, rho*u_0..rho*u_{dim-1}, rho*E,
@@ -142,7 +142,7 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net,
 
 /* A(U): advective term, the divergence of the HLLC fluxes of a method-of-lines
    PLM reconstruction (MC limiter) of the primitive variables
-   (paper section 2, Eq. 1: "the divergence of the hydrodynamic fluxes").
+   (paper section 2, Eq. 1: A is minus the divergence of the advective fluxes).
    U, A: [nvar][Ntot] device arrays; A may not alias U. */
 sdc_status sdc_advective_term(sdc_ctx* ctx, const double* U, double* A);
 
@@ -253,8 +253,8 @@ sdc_status sdc_step_backward(sdc_ctx* ctx, const double* U_n, double dt, const d
    three sub-steps are captured as one CUDA graph per U pointer. */
 sdc_status sdc_step_strang(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats);
 
-/* Vector-Jacobian product of the advective term A(U) of Eq. 1 (section 2: the
-   divergence of the hydrodynamic fluxes):  Ubar += (dA/dU)^T Abar  at the state
+/* Vector-Jacobian product of the advective term A(U) of Eq. 1 (section 2: minus
+   the divergence of the advective fluxes):  Ubar += (dA/dU)^T Abar  at the state
    U, with the branches of the MC limiter and of HLLC those that U selects.
    U, Abar, Ubar: device arrays [nvar][Ntot]; Ubar is accumulated.  mode 0: a
    reverse sweep through each face flux (what sdc_step_backward uses); mode 1:

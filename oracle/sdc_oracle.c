@@ -512,8 +512,8 @@ static int lu_solve(int n, double* J, double* b) {
 }
 
 /* ------------------------------------------------------------------ */
-/* Implicit reaction update (section 2: the update is an implicit     */
-/* equation for the new state).  Solve                                 */
+/* Implicit reaction update (section 2: the reactive part of the node */
+/* update is implicit in the new state).  Solve                         */
 /*   G(w) = w - dt_m R(w) - rhs_w = 0,   J_G = I - dt_m dR/dw          */
 /* by Newton iteration, globalised by pseudo-transient continuation:   */
 /* an iteration solves (c I - dt_m dR/dw) delta = G(w) with c = 1 for a */

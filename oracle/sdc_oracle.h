@@ -11,10 +11,10 @@
  *   U^{m+1,(k+1)} = U^{m,(k+1)} + dt_m [A^{m,(k+1)} - A^{m,(k)}]
  *                 + dt_m [R^{m+1,(k+1)} - R^{m+1,(k)}]
  *                 + int_{t^m}^{t^{m+1}} (A^{(k)} + R^{(k)}) dt   (Eq. sdc:general)
- * with zone averages, R evaluated on the zone average, the implicit equation
- * solved by Newton iteration, and the integral built from the previous
- * iteration's values at every node (trapezoid rule for 2 nodes, Simpson's
- * rule for 3 nodes).
+ * with zone averages, R evaluated on the zone average, the nonlinear system of
+ * the new node state solved by Newton iteration, and the integral formed from
+ * the previous iterate at every node (trapezoid rule for 2 nodes, Simpson's
+ * rule for 3 nodes; or through the Radau points).
  *
  * Conventions (shared by every function here):
  *   dim in {1,2,3}; nvar = 2 + dim + nspec;

@@ -1,5 +1,5 @@
 // sdc_newton.cuh -- per-zone implicit reaction update of Eq. sdc:general
-// (paper section 2: "an implicit equation for the new state"):
+// (paper section 2: the reactive part of the node update is implicit in the new state):
 //   G(w) = w - dt_m R(w; rho, rho u) - rhs_w = 0,   w = (rho E, rho X_i)
 // solved by Newton iteration on M = c I - dt_m dR/dw (c = 1), globalised by
 // pseudo-transient continuation (c = 1 + 1/h):

@@ -1,5 +1,5 @@
-// sdc_stencil.cuh -- advective term A(U) (paper section 2, Eq. 1: the
-// divergence of the hydrodynamic fluxes) fused with the right-hand side of the
+// sdc_stencil.cuh -- advective term A(U) (paper section 2, Eq. 1: minus the
+// divergence of the advective fluxes) fused with the right-hand side of the
 // implicit update of Eq. sdc:general.
 //
 // Method of lines: conserved -> primitive (rho, u, p, X), per direction a

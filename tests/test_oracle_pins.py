@@ -371,8 +371,8 @@ def _run_to(P, U, t_final, nsteps):
                                               (2, 2, 1, "radau"), (3, 1, 1, "radau"), (3, 2, 2, "radau"),
                                               (3, 4, 3, "radau"), (4, 4, 4, "radau"), (4, 6, 5, "radau")])
 def test_order_decay_with_heating(M, K, order, nodes):
-    """Section 2: each iteration raises the order by one up to the order of the
-    integral (2 with the trapezoid, 4 with Simpson; with Radau nodes the order of
+    """Section 2: every sweep adds one order of accuracy, capped by the
+    quadrature's own order (2 with the trapezoid, 4 with Simpson; with Radau nodes the order of
     Radau IIA collocation, 2(M-1) - 1).  Spatially uniform state, so A = 0
     exactly; the T-dependent A -> B with Q = 1 is nonlinear."""
     net = W.decay_network(Q=1.0)
