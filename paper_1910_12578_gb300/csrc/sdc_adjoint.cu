@@ -138,16 +138,16 @@ __device__ __forceinline__ void reaction_derivs(const NetParams& P, double rho, 
                                                 double (*dR)[NS + 1], double (*dRa)[NS - 1]) {
     constexpr int N = NS + 1;
     constexpr int NR = NS - 1;
-    const double inv_rho = 1.0 / rho;
+    const double inv_rho = rcp_nr(rho);
     const double T = P.gm1 * (w[0] - 0.5 * m2 * inv_rho) * inv_rho;
     double k[NR], dk[NR], Y[NS];
     rate_consts<NR>(P, rho, T, k, dk);
-#pragma unroll
-    for (int i = 0; i < NS; i++) Y[i] = w[1 + i] * inv_rho / P.mass[i];
-    // M = 0 I - 1 * dR/dw = -dR/dw  (build_matrix with c = 0, dtm = 1)
     double ym[NS];
 #pragma unroll
-    for (int i = 0; i < NS; i++) ym[i] = inv_rho / P.mass[i];
+    for (int i = 0; i < NS; i++) ym[i] = inv_rho * P.inv_mass[i];
+#pragma unroll
+    for (int i = 0; i < NS; i++) Y[i] = w[1 + i] * ym[i];
+    // M = 0 I - 1 * dR/dw = -dR/dw  (build_matrix with c = 0, dtm = 1)
     double M[N][N];
     build_matrix<NS, TOPO, double>(P, rho, inv_rho, ym, k, dk, Y, 0.0, 1.0, M);
 #pragma unroll
@@ -160,7 +160,7 @@ __device__ __forceinline__ void reaction_derivs(const NetParams& P, double rho, 
         double kj[NR];
 #pragma unroll
         for (int q = 0; q < NR; q++) kj[q] = 0.0;
-        kj[j] = (P.a[j] != 0.0) ? k[j] / P.a[j] : ipow_small(rho, P.order[j] - 1) *
+        kj[j] = (P.a[j] != 0.0) ? k[j] * rcp_nr(P.a[j]) : ipow_small(rho, P.order[j] - 1) *
                                                    (P.law == LAW_POWER ? exp2_tab(P.nu[j] * log2_tab(T)) : exp(-P.nu[j] / T));
         double Rj[N];
         sources<NS, TOPO>(P, rho, kj, Y, Rj);
@@ -191,7 +191,8 @@ reaction_vjp_kernel(NetParams P, long long N, int dim, const double* __restrict_
     for (int r = 0; r < NW; r++) w[r] = U[(1 + dim + r) * N + z];
     double dR[NW][NW], dRa[NW][NR];
     reaction_derivs<NS, TOPO>(P, rho, m2, w, dR, dRa);
-    const double cE_rho = -w[0] / rho + m2 / (rho * rho);  // dT/d(rho) / dT/d(rho E)
+    const double irho = rcp_nr(rho);
+    const double cE_rho = -w[0] * irho + m2 * (irho * irho);  // dT/d(rho) / dT/d(rho E)
     double ub_rho = Ubar[z], ub_m[3] = {0.0, 0.0, 0.0}, ub_w[NW];
     for (int d = 0; d < dim; d++) ub_m[d] = Ubar[(1 + d) * N + z];
 #pragma unroll
@@ -214,7 +215,7 @@ reaction_vjp_kernel(NetParams P, long long N, int dim, const double* __restrict_
 #pragma unroll
         for (int r = 0; r < NW; r++) DE += rb[r] * dR[r][0];
         ub_rho += DE * cE_rho;
-        for (int d = 0; d < dim; d++) ub_m[d] -= DE * mom[d] / rho;
+        for (int d = 0; d < dim; d++) ub_m[d] -= DE * mom[d] * irho;
 #pragma unroll
         for (int j = 0; j < NR; j++) {
             double s = 0.0;
@@ -242,7 +243,7 @@ reaction_vjp_kernel(NetParams P, long long N, int dim, const double* __restrict_
 #pragma unroll
         for (int r = 0; r < NW; r++) DE += lam[r] * dR[r][0];
         rhsbar[z] = ub_rho + dtm * DE * cE_rho;
-        for (int d = 0; d < dim; d++) rhsbar[(1 + d) * N + z] = ub_m[d] - dtm * DE * mom[d] / rho;
+        for (int d = 0; d < dim; d++) rhsbar[(1 + d) * N + z] = ub_m[d] - dtm * DE * mom[d] * irho;
 #pragma unroll
         for (int r = 0; r < NW; r++) rhsbar[(1 + dim + r) * N + z] = lam[r];
 #pragma unroll
@@ -264,22 +265,24 @@ reaction_vjp_kernel(NetParams P, long long N, int dim, const double* __restrict_
 
 // adjoint of rhs_m = U_m + dtm (A_m_new - A_m_old) - dtm R_{m+1}_old + sum_l q_l dt (A_l_old + R_l_old)
 __global__ void rhs_adjoint_kernel(RhsAdjArgs a) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)a.nvar * a.N) return;
-    const int f = (int)(i / a.N);
-    const long long z = i - (long long)f * a.N;
-    const double g = a.rhsbar[i];
-    const bool reactive = f >= 1 + a.dim;
-    const int r = f - 1 - a.dim;
-    a.Ubar_m[i] += g;
-    if (a.Abar_new_m) {
-        a.Abar_new_m[i] += a.dtm * g;
-        a.Abar_old[a.m][i] -= a.dtm * g;
-    }
-    if (reactive) a.Rbar_old[a.m + 1][r * a.N + z] -= a.dtm * g;
-    for (int l = 0; l < a.M; l++) {
-        a.Abar_old[l][i] += a.qdt[l] * g;
-        if (reactive) a.Rbar_old[l][r * a.N + z] += a.qdt[l] * g;
+    // one thread per zone, every field (no 64-bit division per element)
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= a.N) return;
+    for (int f = 0; f < a.nvar; f++) {
+        const long long i = (long long)f * a.N + z;
+        const double g = a.rhsbar[i];
+        const bool reactive = f >= 1 + a.dim;
+        const long long ir = (long long)(f - 1 - a.dim) * a.N + z;
+        a.Ubar_m[i] += g;
+        if (a.Abar_new_m) {
+            a.Abar_new_m[i] += a.dtm * g;
+            a.Abar_old[a.m][i] -= a.dtm * g;
+        }
+        if (reactive) a.Rbar_old[a.m + 1][ir] -= a.dtm * g;
+        for (int l = 0; l < a.M; l++) {
+            a.Abar_old[l][i] += a.qdt[l] * g;
+            if (reactive) a.Rbar_old[l][ir] += a.qdt[l] * g;
+        }
     }
 }
 
@@ -348,8 +351,8 @@ cudaError_t launch_reaction_vjp(const NetParams& P, int dim, long long N, const 
 }
 
 cudaError_t launch_rhs_adjoint(const RhsAdjArgs& a, cudaStream_t st) {
-    const long long n = (long long)a.nvar * a.N;
-    rhs_adjoint_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
+    if (a.N <= 0) return cudaSuccess;
+    rhs_adjoint_kernel<<<(unsigned)((a.N + 255) / 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

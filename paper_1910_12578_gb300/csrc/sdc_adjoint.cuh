@@ -136,19 +136,25 @@ __device__ void face_flux_dual(double gamma, int limiter, int dir, const Dual (*
 }
 
 // Coefficients of the limited slope as a linear form in the three values,
-// slope = cm qm + c0 q0 + cp qp, on the branch the values select (ties as in
-// mc_slope_dual: the first argument of each min wins).
+// slope = cm qm + c0 q0 + cp qp, on the branch that the forward kernel's limiter
+// (mc_half_slope) selects for these values: zero slope where dl and dr differ
+// in sign, one is zero or |dl + dr| is below 2^-1020; else the smallest of
+// |dl|, |dr|, |dl + dr|/4 (ties: |dr| over |dl|, the centred |dl + dr|/4 over
+// both), compared as bit patterns on the integer pipe.
 __device__ __forceinline__ void mc_slope_coef(int limiter, double qm, double q0, double qp, double& cm, double& c0,
                                               double& cp) {
-    const double dl = q0 - qm, dr = qp - q0, dc = 0.5 * (dl + dr);
     if (!limiter) { cm = -0.5; c0 = 0.0; cp = 0.5; return; }
-    if (dl * dr <= 0.0) { cm = 0.0; c0 = 0.0; cp = 0.0; return; }
-    const bool left = fabs(dl) <= fabs(dr);            // min(2|dl|, 2|dr|)
-    const double m2 = 2.0 * (left ? fabs(dl) : fabs(dr));
-    if (m2 <= fabs(dc)) {                               // slope = 2 dl or 2 dr (dl, dr, dc share a sign)
+    const double dl = q0 - qm, dr = qp - q0, s = dl + dr;
+    const unsigned long long al = mag2(dl), ar = mag2(dr), as = mag2(s);
+    constexpr unsigned long long E2 = (unsigned long long)EXP_ONE << 1;
+    if (((dbits(dl) ^ dbits(dr)) < 0) || al == 0 || ar == 0 || as < 3 * E2) { cm = 0.0; c0 = 0.0; cp = 0.0; return; }
+    const unsigned long long q = as - 2 * E2;  // |s| / 4
+    const bool left = al < ar;                 // 2 dl (else 2 dr)
+    const unsigned long long lim = left ? al : ar;
+    if (lim < q) {
         if (left) { cm = -2.0; c0 = 2.0; cp = 0.0; }
         else { cm = 0.0; c0 = -2.0; cp = 2.0; }
-    } else {                                            // slope = dc
+    } else {                                   // slope = (dl + dr) / 2
         cm = -0.5; c0 = 0.0; cp = 0.5;
     }
 }
@@ -160,12 +166,14 @@ __device__ __forceinline__ void face_flux_vjp(double gamma, int limiter, int dir
                                               const double* Fbar, double (*Ub)[2 + DIM + NS]) {
     constexpr int NV = 2 + DIM + NS;
     constexpr int IE = 1 + DIM, IX = 2 + DIM;
-    const double gm1 = gamma - 1.0, igm1 = 1.0 / gm1;
+    const double gm1 = gamma - 1.0, igm1 = rcp_nr(gm1);
     // ---------------- forward: primitives of the four zones
-    double q[4][NV];
+    // (reciprocals and square roots by the Newton-Raphson forms of the forward kernel)
+    double q[4][NV], irz[4];
 #pragma unroll
     for (int z = 0; z < 4; z++) {
-        const double rho = Uz[z][0], ir = 1.0 / rho;
+        const double rho = Uz[z][0], ir = rcp_nr(rho);
+        irz[z] = ir;
         double mu = 0.0;
         q[z][0] = rho;
 #pragma unroll
@@ -197,35 +205,38 @@ __device__ __forceinline__ void face_flux_vjp(double gamma, int limiter, int dir
         kR += qR[1 + d] * qR[1 + d];
     }
     const double EL = pL * igm1 + 0.5 * rL * kL, ER = pR * igm1 + 0.5 * rR * kR;
-    const double irL = 1.0 / rL, irR = 1.0 / rR;
-    const double cL = sqrt(gamma * pL * irL), cR = sqrt(gamma * pR * irR);
+    const double irL = rcp_nr(rL), irR = rcp_nr(rR);
+    const double cL = sqrt_nr(gamma * pL * irL), cR = sqrt_nr(gamma * pR * irR);
     const bool slL = (unL - cL) <= (unR - cR);
     const double SL = slL ? unL - cL : unR - cR;
     const bool srL = (unL + cL) >= (unR + cR);
     const double SR = srL ? unL + cL : unR + cR;
     const double aL = rL * (SL - unL), aR = rR * (SR - unR);
-    const double iDen = 1.0 / (aL - aR);
+    const double iDen = rcp_nr(aL - aR);
     const double Ss = (pR - pL + unL * aL - unR * aR) * iDen;
     const bool left = (SL >= 0.0) || (Ss >= 0.0);
     const bool star = (SL < 0.0) && (Ss >= 0.0 || SR > 0.0);
     const double* qs = left ? qL : qR;
     const double r = left ? rL : rR, un = left ? unL : unR, p = left ? pL : pR, E = left ? EL : ER;
     const double S = left ? SL : SR;
+    const double ir = left ? irL : irR;
     double F0 = r * un;  // mass flux (after the star correction)
-    double D = 0.0, Q = 1.0, fac = 0.0, B = 0.0, H = 0.0;
+    double D = 0.0, Q = 1.0, fac = 0.0, B = 0.0, H = 0.0, iD = 0.0, iQ = 0.0;
     if (star) {
         D = r * (S - un);
         Q = S - Ss;
-        fac = D / Q;
-        B = Ss + p / D;
-        H = E / r + (Ss - un) * B;
+        iD = rcp_nr(D);
+        iQ = rcp_nr(Q);
+        fac = D * iQ;
+        B = Ss + p * iD;
+        H = E * ir + (Ss - un) * B;
         F0 += S * (fac - r);
     }
     const double* qx = (Ss >= 0.0) ? qL : qR;
     double sum = 0.0;
 #pragma unroll
     for (int s = 0; s < NS; s++) sum += qx[IX + s];
-    const double isum = 1.0 / sum;
+    const double isum = rcp_nr(sum);
 
     // ---------------- reverse
     double qLb[NV], qRb[NV];
@@ -269,17 +280,17 @@ __device__ __forceinline__ void face_flux_vjp(double gamma, int limiter, int dir
         facb += ueb * H;
         const double Hb = ueb * fac;
         // H = E / r + (Ss - un) B,  B = Ss + p / D
-        Eb += Hb / r;
-        rb -= Hb * E / (r * r);
+        Eb += Hb * ir;
+        rb -= Hb * E * (ir * ir);
         Ssb += Hb * B;
         unb -= Hb * B;
         const double Bb = Hb * (Ss - un);
         Ssb += Bb;
-        pb += Bb / D;
-        double Db = -Bb * p / (D * D);
+        pb += Bb * iD;
+        double Db = -Bb * p * (iD * iD);
         // fac = D / Q,  Q = S - Ss,  D = r (S - un)
-        Db += facb / Q;
-        const double Qb = -facb * fac / Q;
+        Db += facb * iQ;
+        const double Qb = -facb * fac * iQ;
         Sb += Qb;
         Ssb -= Qb;
         rb += Db * (S - un);
@@ -342,7 +353,7 @@ __device__ __forceinline__ void face_flux_vjp(double gamma, int limiter, int dir
     }
     // c = sqrt(gamma p / r)
     {
-        const double tL = cLb * gamma * 0.5 / cL, tR = cRb * gamma * 0.5 / cR;
+        const double tL = cLb * gamma * 0.5 * rcp_nr(cL), tR = cRb * gamma * 0.5 * rcp_nr(cR);
         qLb[IE] += tL * irL;
         qLb[0] -= tL * pL * irL * irL;
         qRb[IE] += tR * irR;
@@ -369,7 +380,7 @@ __device__ __forceinline__ void face_flux_vjp(double gamma, int limiter, int dir
     // primitives -> conserved: u = m / rho, p = (gamma - 1)(E - |m|^2 / (2 rho)), X = rho X / rho
 #pragma unroll
     for (int z = 0; z < 4; z++) {
-        const double ir = 1.0 / q[z][0];
+        const double ir = irz[z];
         double u2 = 0.0;
 #pragma unroll
         for (int d = 0; d < DIM; d++) u2 += q[z][1 + d] * q[z][1 + d];
