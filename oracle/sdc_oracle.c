@@ -265,7 +265,7 @@ void orc_advective(const orc_problem* P, const double* U, double* A) {
 /* ------------------------------------------------------------------ */
 /* Fourth-order finite-volume operators (section 2: the fourth-order  */
 /* method combines Simpson's rule with the spatial reconstruction of  */
-/* McCorquodale & Colella).  Smooth-flow form, without limiting:      */
+/* McCorquodale & Colella).  Smooth-flow form (limiter = 0):         */
 /*   point <-> average: f_c = <f> - L<f>/24,  <f> = f_c + L f_c/24,    */
 /*     L = sum over the box's dimensions of the second difference;    */
 /*   primitive averages <W> = W(U_c) + L W(<U>)/24;                   */
@@ -276,7 +276,10 @@ void orc_advective(const orc_problem* P, const double* U, double* A) {
 /*   face-average fluxes <F> = F(W_f) + L_t F(<W>_{i+1/2})/24;          */
 /*   A = -sum_d (<F>_{i+1/2} - <F>_{i-1/2}) / dx_d.                    */
 /* Both sides of a face see the same state, so F is the physical      */
-/* Euler flux (species: mass flux times X).                           */
+/* Euler flux (species: mass flux times X).  Limited form (limiter =  */
+/* 1): the face averages are limited per side (Colella & Sekora, see  */
+/* cs_face / cs_zone below) and F is the HLLC flux between the two    */
+/* sides, at the face centres and from the face averages alike.       */
 /* ------------------------------------------------------------------ */
 static long long shifted_zone(const orc_problem* P, long long z, int d, int o) {
     int c[3];
@@ -342,6 +345,105 @@ static void euler_flux(const orc_problem* P, int dir, const double* q, double* F
     for (int s = 0; s < P->nspec; s++) F[2 + dim + s] = rho * un * q[2 + dim + s];
 }
 
+/* Limited form of the fourth-order face values (reading of the paper's
+   fourth-order method for flows with steep fronts: the extremum-preserving PPM
+   limiter of Colella & Sekora (2008) applied to the face values, then a
+   Riemann solver between the two limited states of every face).  C = 1.25. */
+#define CS_C 1.25
+
+static int same_sign3(double a, double b, double c) {
+    return (a > 0.0 && b > 0.0 && c > 0.0) || (a < 0.0 && b < 0.0 && c < 0.0);
+}
+
+/* face between zone i (a0) and i+1 (ap), neighbours am = a_{i-1}, app = a_{i+2}:
+   a face value outside [a_i, a_{i+1}] is replaced by the mean of the two
+   averages less a sixth of a limited second difference.  The face estimate
+   d2f = 3 (a_i - 2 a_f + a_{i+1}) is h^2 f'' (exact on parabolas), and solving it
+   for a_f gives a_f = (a_i + a_{i+1})/2 - d2f/6, so the replacement returns the
+   face value unchanged wherever the limiter does not bind */
+static double cs_face(double am, double a0, double ap, double app, double af) {
+    if ((af - a0) * (ap - af) < 0.0) {
+        double d2f = 3.0 * (a0 - 2.0 * af + ap);
+        double d2l = am - 2.0 * a0 + ap, d2r = a0 - 2.0 * ap + app;
+        double d2 = 0.0;
+        if (same_sign3(d2f, d2l, d2r)) {
+            double m = fmin(fmin(CS_C * fabs(d2l), CS_C * fabs(d2r)), fabs(d2f));
+            d2 = d2f > 0.0 ? m : -m;
+        }
+        af = 0.5 * (a0 + ap) - d2 / 6.0;
+    }
+    return af;
+}
+
+/* zone i (average a0, neighbours amm..app) with face values *fm (i-1/2) and
+   *fp (i+1/2): at an extremum (of the face values about the average, or of the
+   averages at distance one or two) the deviations are scaled by a limited
+   second derivative over the parabola's own; elsewhere the PPM overshoot limits
+   apply.  The distance-two test catches an extremum that sits on a face of the
+   zone: there the parabola meets the overshoot bound |dp| = 2 |dm| exactly, and
+   the overshoot limit would clip smooth data by O(h^4) */
+static void cs_zone(double amm, double am, double a0, double ap, double app, double* fm, double* fp) {
+    double dm = *fm - a0, dp = *fp - a0;
+    if (dp * dm >= 0.0 || (am - a0) * (a0 - ap) <= 0.0 || (amm - a0) * (a0 - app) <= 0.0) {
+        double d2 = -2.0 * (6.0 * a0 - 3.0 * (*fm + *fp));
+        double d2c = am - 2.0 * a0 + ap, d2l = amm - 2.0 * am + a0, d2r = a0 - 2.0 * ap + app;
+        double lim = 0.0;
+        if (same_sign3(d2, d2c, d2l) && same_sign3(d2, d2c, d2r)) {
+            double m = fmin(fmin(fabs(d2), CS_C * fabs(d2c)), fmin(CS_C * fabs(d2l), CS_C * fabs(d2r)));
+            lim = d2 > 0.0 ? m : -m;
+        }
+        if (d2 != 0.0) {
+            *fm = a0 + dm * lim / d2;
+            *fp = a0 + dp * lim / d2;
+        } else {
+            *fm = a0;
+            *fp = a0;
+        }
+    } else {
+        if (fabs(dp) >= 2.0 * fabs(dm)) *fp = a0 - 2.0 * dm;
+        if (fabs(dm) >= 2.0 * fabs(dp)) *fm = a0 - 2.0 * dp;
+    }
+}
+
+/* the limited left and right states of the face between z and its +1
+   neighbour along dir (WL: zone z's upper face value, WR: zone z+1's lower
+   one), from the averaged primitives Wa and the interpolated face values Wf */
+static void limited_face_states(const orc_problem* P, int dir, const double* Wa, const double* Wf, double* WL,
+                                double* WR) {
+    int nv = orc_nvar(P);
+    long long N = nzones(P);
+    double* Wfl = (double*)malloc(sizeof(double) * nv * N);
+#pragma omp parallel for schedule(static)
+    for (long long z = 0; z < N; z++) {
+        long long zm = shifted_zone(P, z, dir, -1), zp = shifted_zone(P, z, dir, 1), zpp = shifted_zone(P, z, dir, 2);
+        for (int f = 0; f < nv; f++)
+            Wfl[f * N + z] = cs_face(Wa[f * N + zm], Wa[f * N + z], Wa[f * N + zp], Wa[f * N + zpp], Wf[f * N + z]);
+    }
+#pragma omp parallel for schedule(static)
+    for (long long z = 0; z < N; z++) {
+        long long zmm = shifted_zone(P, z, dir, -2), zm = shifted_zone(P, z, dir, -1);
+        long long zp = shifted_zone(P, z, dir, 1), zpp = shifted_zone(P, z, dir, 2);
+        double qm[64], qp[64];
+        for (int f = 0; f < nv; f++) {
+            qm[f] = Wfl[f * N + zm];
+            qp[f] = Wfl[f * N + z];
+            cs_zone(Wa[f * N + zmm], Wa[f * N + zm], Wa[f * N + z], Wa[f * N + zp], Wa[f * N + zpp], &qm[f],
+                    &qp[f]);
+        }
+        /* limited mass fractions renormalised to sum to one, as in the PLM states */
+        if (P->nspec > 0) {
+            double sm = 0.0, sp = 0.0;
+            for (int s = 0; s < P->nspec; s++) { sm += qm[2 + P->dim + s]; sp += qp[2 + P->dim + s]; }
+            for (int s = 0; s < P->nspec; s++) { qm[2 + P->dim + s] /= sm; qp[2 + P->dim + s] /= sp; }
+        }
+        for (int f = 0; f < nv; f++) {
+            WL[f * N + z] = qp[f];   /* upper face of z */
+            WR[f * N + zm] = qm[f];  /* lower face of z = upper face of z-1, seen from the right */
+        }
+    }
+    free(Wfl);
+}
+
 void orc_advective4(const orc_problem* P, const double* U, double* A) {
     int dim = P->dim, nv = orc_nvar(P);
     long long N = nzones(P);
@@ -349,6 +451,11 @@ void orc_advective4(const orc_problem* P, const double* U, double* A) {
     double *Uc = (double*)malloc(sz), *W2 = (double*)malloc(sz), *Wc = (double*)malloc(sz);
     double *Wa = (double*)malloc(sz), *Wf = (double*)malloc(sz), *Wfc = (double*)malloc(sz);
     double *Fc = (double*)malloc(sz), *F2 = (double*)malloc(sz), *Fa = (double*)malloc(sz);
+    double *WL = NULL, *WR = NULL, *WLc = NULL, *WRc = NULL;
+    if (P->limiter) {
+        WL = (double*)malloc(sz); WR = (double*)malloc(sz);
+        WLc = (double*)malloc(sz); WRc = (double*)malloc(sz);
+    }
     orc_avg_to_point(P, nv, U, Uc);
     prim_fields(P, U, W2);
     prim_fields(P, Uc, Wc);
@@ -364,16 +471,34 @@ void orc_advective4(const orc_problem* P, const double* U, double* A) {
                 Wf[f * N + z] = 7.0 / 12.0 * (Wa[f * N + z] + Wa[f * N + zp]) -
                                 1.0 / 12.0 * (Wa[f * N + zm] + Wa[f * N + zpp]);
         }
-        lap_combine(P, nv, Wf, Wf, -1.0 / 24.0, dir, Wfc);
+        if (P->limiter) {
+            /* limited: the two states of every face, then HLLC between them at the
+               face centres (transverse maps of each side) and from the averages */
+            limited_face_states(P, dir, Wa, Wf, WL, WR);
+            lap_combine(P, nv, WL, WL, -1.0 / 24.0, dir, WLc);
+            lap_combine(P, nv, WR, WR, -1.0 / 24.0, dir, WRc);
 #pragma omp parallel for schedule(static)
-        for (long long z = 0; z < N; z++) {
-            double q[64], F[64];
-            for (int f = 0; f < nv; f++) q[f] = Wfc[f * N + z];
-            euler_flux(P, dir, q, F);
-            for (int f = 0; f < nv; f++) Fc[f * N + z] = F[f];
-            for (int f = 0; f < nv; f++) q[f] = Wf[f * N + z];
-            euler_flux(P, dir, q, F);
-            for (int f = 0; f < nv; f++) F2[f * N + z] = F[f];
+            for (long long z = 0; z < N; z++) {
+                double qL[64], qR[64], F[64];
+                for (int f = 0; f < nv; f++) { qL[f] = WLc[f * N + z]; qR[f] = WRc[f * N + z]; }
+                orc_hllc(P, dir, qL, qR, F);
+                for (int f = 0; f < nv; f++) Fc[f * N + z] = F[f];
+                for (int f = 0; f < nv; f++) { qL[f] = WL[f * N + z]; qR[f] = WR[f * N + z]; }
+                orc_hllc(P, dir, qL, qR, F);
+                for (int f = 0; f < nv; f++) F2[f * N + z] = F[f];
+            }
+        } else {
+            lap_combine(P, nv, Wf, Wf, -1.0 / 24.0, dir, Wfc);
+#pragma omp parallel for schedule(static)
+            for (long long z = 0; z < N; z++) {
+                double q[64], F[64];
+                for (int f = 0; f < nv; f++) q[f] = Wfc[f * N + z];
+                euler_flux(P, dir, q, F);
+                for (int f = 0; f < nv; f++) Fc[f * N + z] = F[f];
+                for (int f = 0; f < nv; f++) q[f] = Wf[f * N + z];
+                euler_flux(P, dir, q, F);
+                for (int f = 0; f < nv; f++) F2[f * N + z] = F[f];
+            }
         }
         lap_combine(P, nv, Fc, F2, 1.0 / 24.0, dir, Fa);
         double dx = P->dx[dir];
@@ -384,6 +509,7 @@ void orc_advective4(const orc_problem* P, const double* U, double* A) {
         }
     }
     free(Uc); free(W2); free(Wc); free(Wa); free(Wf); free(Wfc); free(Fc); free(F2); free(Fa);
+    free(WL); free(WR); free(WLc); free(WRc);
 }
 
 void orc_advective_term(const orc_problem* P, const double* U, double* A) {
