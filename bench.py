@@ -57,7 +57,10 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--prec", choices=["fp64", "fp32jac"], default="fp64")
     p.add_argument("--space-order", type=int, choices=[2, 4], default=2,
-                   help="2: PLM/MC/HLLC; 4: the fourth-order finite-volume operators (smooth-flow form)")
+                   help="2: PLM/MC/HLLC; 4: the fourth-order finite-volume operators")
+    p.add_argument("--limiter", type=int, choices=[0, 1], default=1,
+                   help="1: MC slopes (order 2) or limited face states with HLLC (order 4); 0: unlimited centred "
+                        "slopes (order 2) or the smooth-flow form (order 4)")
     p.add_argument("--nodes", choices=["lobatto", "radau", "radau4"], default="lobatto",
                    help="temporal node set: Gauss-Lobatto (trapezoid/Simpson), node 0 + the Radau IIA points "
                         "1/3, 1, or (radau4) node 0 + the three Radau IIA points of s = 3")
@@ -69,6 +72,13 @@ def parse():
     p.add_argument("--adjoint", action=argparse.BooleanOptionalAction, default=True,
                    help="also time one backward step (sdc_step_backward) of the workload")
     return p.parse_args()
+
+
+def space_desc(args):
+    if args.space_order == 4:
+        return ("; fourth-order finite-volume operators, " +
+                ("limited face states and HLLC" if args.limiter else "smooth-flow form (no limiter)"))
+    return "" if args.limiter else "; unlimited centred slopes"
 
 
 def workload(name, seed, nodes="lobatto"):
@@ -242,14 +252,13 @@ def run_reference(args):
     import oracle as O
     P, U, desc = workload(args.config, args.seed, args.nodes)
     for p_ in (P if isinstance(P, list) else [P]):
-        p_.space_order = args.space_order
-    if args.space_order == 4:
-        desc += "; fourth-order finite-volume operators (no limiter)"
+        p_.space_order, p_.limiter = args.space_order, args.limiter
+    desc += space_desc(args)
     if args.config == "box256":
         # bounded sample: a 64^3 box with the same network and parameters
         P, U = W.config_box(n=64, nspec=13, n_nodes=3, n_iters=4, seed=args.seed, T0=0.5)
         _set_nodes(P, args.nodes)
-        P.space_order = args.space_order
+        P.space_order, P.limiter = args.space_order, args.limiter
         desc += " (sample: 64^3 box, same network)"
     if isinstance(P, list):
         # bounded sample: the first 8 boxes of the batch, each its own oracle step
@@ -304,7 +313,7 @@ def cpu_baseline_sampled(P, U, dt, gpu_out, seed, target_s=10.0, max_steps=3):
     import oracle as O
     Pc, Uc = W.config_box(n=64, nspec=P.net.nspec, n_nodes=P.n_nodes, n_iters=P.n_iters, seed=seed, T0=0.5)
     Pc.nodes = P.nodes
-    Pc.space_order = P.space_order
+    Pc.space_order, Pc.limiter = P.space_order, P.limiter
     oc = O.Oracle(Pc)
     dtc = oc.cfl_dt(Uc)
     t0 = time.perf_counter()
@@ -314,14 +323,16 @@ def cpu_baseline_sampled(P, U, dt, gpu_out, seed, target_s=10.0, max_steps=3):
         steps += 1
     el = time.perf_counter() - t0
     h = 64
-    # per advective evaluation 2 zones (PLM/HLLC) or 3 (fourth order); the fourth-order
-    # implicit update reaches 2 more through its average <-> centre maps
-    pad = (2 if P.space_order == 2 else 5) * (1 + P.n_iters * (P.n_nodes - 1))
+    # per advective evaluation 2 zones (PLM/HLLC), 3 (fourth order, smooth form) or 4
+    # (limited: the zone limiter reads two zones out); the fourth-order implicit
+    # update reaches 2 more through its average <-> centre maps
+    reach = 2 if P.space_order == 2 else (6 if P.limiter else 5)
+    pad = reach * (1 + P.n_iters * (P.n_nodes - 1))
     c0 = P.n[0] // 2 - h // 2
     blk = np.arange(c0 - pad, c0 + h + pad) % P.n[0]
     Ub = U.reshape(P.nvar, P.n[2], P.n[1], P.n[0])[:, blk][:, :, blk][:, :, :, blk].copy()
     Pb = W.Problem(dim=3, n=(h + 2 * pad,) * 3, dx=P.dx, gamma=P.gamma, net=P.net, n_nodes=P.n_nodes,
-                   n_iters=P.n_iters, nodes=P.nodes, space_order=P.space_order)
+                   n_iters=P.n_iters, nodes=P.nodes, space_order=P.space_order, limiter=P.limiter)
     Vb, _ = O.Oracle(Pb).step(Ub, dt)
     Vb = Vb.reshape(P.nvar, h + 2 * pad, h + 2 * pad, h + 2 * pad)[:, pad:pad + h, pad:pad + h, pad:pad + h]
     g = gpu_out.reshape(P.nvar, P.n[2], P.n[1], P.n[0])[:, c0:c0 + h, c0:c0 + h, c0:c0 + h]
@@ -416,9 +427,8 @@ def run_ours(args):
         B.build()
     P, U, desc = workload(args.config, rank_seed(args.seed, rank), args.nodes)
     for p_ in as_list(P):
-        p_.space_order = args.space_order
-    if args.space_order == 4:
-        desc += "; fourth-order finite-volume operators (no limiter)"
+        p_.space_order, p_.limiter = args.space_order, args.limiter
+    desc += space_desc(args)
     P0 = as_list(P)[0]
     prec = sdc.PREC_FP64 if args.prec == "fp64" else sdc.PREC_FP32_JAC
     ctx = sdc.Context(P, prec=prec)
@@ -624,9 +634,9 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == sdc.PREC_FP64 else "f64 residual/update, f32 Jacobian/LU",
             "data": "synthetic",
-            "config": {"workload": desc, "zones": nzones(P), "nspec": P0.net.nspec, "nodes": P0.n_nodes,
+            "config": {"workload": desc, "zones": nzones(P), "nspec": P0.net.nspec, "n_nodes": P0.n_nodes,
                        "iters": P0.n_iters, "nodes": args.nodes, "space_order": args.space_order,
-                       "prec": args.prec, "seed": args.seed,
+                       "limiter": args.limiter, "prec": args.prec, "seed": args.seed,
                        "kernel_variants": tuning,
                        "l2": "flushed before every timed step (256 MB write)",
                        "parallelism": "independent box per GPU" if ws > 1 else "1 GPU"},

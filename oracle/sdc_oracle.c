@@ -382,9 +382,20 @@ static double cs_face(double am, double a0, double ap, double app, double af) {
    apply.  The distance-two test catches an extremum that sits on a face of the
    zone: there the parabola meets the overshoot bound |dp| = 2 |dm| exactly, and
    the overshoot limit would clip smooth data by O(h^4) */
+/* a difference of two averages, zero when it is within 1e-12 of their
+   magnitudes: averages that mirror each other across a plane of symmetry of
+   the data differ only by rounding, and the extremum tests below would
+   otherwise take their branch from the order of that rounding */
+#define CS_FLAT 1e-12
+static double avg_diff(double a, double b) {
+    double d = a - b;
+    return fabs(d) <= CS_FLAT * (fabs(a) + fabs(b)) ? 0.0 : d;
+}
+
 static void cs_zone(double amm, double am, double a0, double ap, double app, double* fm, double* fp) {
     double dm = *fm - a0, dp = *fp - a0;
-    if (dp * dm >= 0.0 || (am - a0) * (a0 - ap) <= 0.0 || (amm - a0) * (a0 - app) <= 0.0) {
+    if (dp * dm >= 0.0 || avg_diff(am, a0) * avg_diff(a0, ap) <= 0.0 ||
+        avg_diff(amm, a0) * avg_diff(a0, app) <= 0.0) {
         double d2 = -2.0 * (6.0 * a0 - 3.0 * (*fm + *fp));
         double d2c = am - 2.0 * a0 + ap, d2l = amm - 2.0 * am + a0, d2r = a0 - 2.0 * ap + app;
         double lim = 0.0;

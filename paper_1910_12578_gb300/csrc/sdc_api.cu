@@ -349,8 +349,8 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
     const bool fourth = c->space_order == 4;
     if (with_A) {
         if (fourth)
-            SDC_LAUNCH(prof, CLS_STENCIL, launch_advective4(c->P, c->dim, N, c->d_boxes, c->nbox, node[0], c->A0,
-                                                            c->fw, st));
+            SDC_LAUNCH(prof, CLS_STENCIL, launch_advective4(c->P, c->dim, c->limiter, N, c->d_boxes, c->nbox,
+                                                            node[0], c->A0, c->fw, st));
         else
             SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles,
                                                          c->ntiles, node[0], c->A0, STENCIL_A, none, st,
@@ -388,8 +388,8 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
                                                            st>>>(c->nvar, c->dim, N, node[m], nullptr, ra),
                                              cudaGetLastError()));
             } else if (fourth) {
-                SDC_LAUNCH(prof, CLS_STENCIL, launch_advective4(c->P, c->dim, N, c->d_boxes, c->nbox, node[m],
-                                                                Anew[m], c->fw, st));
+                SDC_LAUNCH(prof, CLS_STENCIL, launch_advective4(c->P, c->dim, c->limiter, N, c->d_boxes, c->nbox,
+                                                                node[m], Anew[m], c->fw, st));
                 SDC_LAUNCH(prof, CLS_OTHER, (rhs_kernel<<<grid_for(N, EW_BLOCK), EW_BLOCK, 0,
                                                            st>>>(c->nvar, c->dim, N, node[m], Anew[m], ra),
                                              cudaGetLastError()));
@@ -424,8 +424,8 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
         }
         if (k < c->K - 1 && with_A) {
             if (fourth)
-                SDC_LAUNCH(prof, CLS_STENCIL, launch_advective4(c->P, c->dim, N, c->d_boxes, c->nbox, node[c->M - 1],
-                                                                Anew[c->M - 1], c->fw, st));
+                SDC_LAUNCH(prof, CLS_STENCIL, launch_advective4(c->P, c->dim, c->limiter, N, c->d_boxes, c->nbox,
+                                                                node[c->M - 1], Anew[c->M - 1], c->fw, st));
             else
                 SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles,
                                                              c->ntiles, node[c->M - 1], Anew[c->M - 1], STENCIL_A,
@@ -689,6 +689,11 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
         double** arrays[] = {&w.Uc, &w.W2, &w.Wc, &w.Wa, &w.Wf, &w.Wfc, &w.Fc, &w.F2, &w.Fa, &w.rc, &w.gc};
         for (double** a : arrays)
             if ((e = ctx_alloc(c, (void**)a, ub)) != cudaSuccess) return fail(e);
+        if (c->limiter) {
+            double** sides[] = {&w.WL, &w.WR, &w.WLc, &w.WRc};
+            for (double** a : sides)
+                if ((e = ctx_alloc(c, (void**)a, ub)) != cudaSuccess) return fail(e);
+        }
         if ((e = ctx_alloc(c, (void**)&w.Rc, rb)) != cudaSuccess) return fail(e);
     }
     if ((e = cudaMemcpy(c->d_boxes, hb.data(), sizeof(BoxDev) * nbox, cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -712,7 +717,8 @@ sdc_status sdc_sizes(const sdc_ctx* ctx, long long* ntot, int* nvar, int* nreact
 sdc_status sdc_advective_term(sdc_ctx* ctx, const double* U, double* A) {
     if (!ctx || !U || !A || U == A) return SDC_ERR_INVALID_ARG;
     if (ctx->space_order == 4) {
-        SDC_TRY(launch_advective4(ctx->P, ctx->dim, ctx->Ntot, ctx->d_boxes, ctx->nbox, U, A, ctx->fw, ctx->stream));
+        SDC_TRY(launch_advective4(ctx->P, ctx->dim, ctx->limiter, ctx->Ntot, ctx->d_boxes, ctx->nbox, U, A, ctx->fw,
+                                  ctx->stream));
         return SDC_OK;
     }
     RhsArgs none;
@@ -931,7 +937,7 @@ sdc_status sdc_launches_per_step(const sdc_ctx* ctx, int* launches) {
     if (ctx->space_order == 4) {
         // fourth order: A is a sequence of kernels and is evaluated apart from
         // the rhs at nodes m >= 1; the source and the implicit update add maps
-        const int LA = fourth_advective_launches(ctx->dim), K = ctx->K, M = ctx->M;
+        const int LA = fourth_advective_launches(ctx->dim, ctx->limiter), K = ctx->K, M = ctx->M;
         *launches = 1 + LA + FOURTH_SOURCE_LAUNCHES + K * (M - 1) * (1 + FOURTH_NEWTON_LAUNCHES) +
                     K * (M - 2) * LA + (K - 1) * LA;
         return SDC_OK;

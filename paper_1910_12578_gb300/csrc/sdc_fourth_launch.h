@@ -1,6 +1,8 @@
 // sdc_fourth_launch.h -- launchers of the fourth-order finite-volume operators
 // (paper section 2: the fourth-order method pairs Simpson's rule with the
-// spatial reconstruction of McCorquodale & Colella), smooth-flow form.
+// spatial reconstruction of McCorquodale & Colella), smooth-flow form
+// (limiter 0) or limited form (limiter 1: face averages limited per side,
+// HLLC between the two sides).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -13,21 +15,25 @@ namespace sdcd {
 struct FourthWs {
     double *Uc = nullptr, *W2 = nullptr, *Wc = nullptr, *Wa = nullptr;  // [nvar][N]
     double *Wf = nullptr, *Wfc = nullptr, *Fc = nullptr, *F2 = nullptr, *Fa = nullptr;
+    // limited form only: the two sides of every face, averages and centres
+    double *WL = nullptr, *WR = nullptr, *WLc = nullptr, *WRc = nullptr;
     double *rc = nullptr, *gc = nullptr;  // zone-centre rhs and guess of the implicit update [nvar][N]
     double* Rc = nullptr;                 // zone-centre source [nspec + 1][N]
 };
 
 // doubles of workspace per zone
-inline long long fourth_ws_doubles_per_zone(int nvar, int nw) { return 11LL * nvar + nw; }
+inline long long fourth_ws_doubles_per_zone(int nvar, int nw, int limiter) {
+    return (limiter ? 15LL : 11LL) * nvar + nw;
+}
 
 // kernel launches of one fourth-order advective term
-inline int fourth_advective_launches(int dim) { return 4 + 5 * dim; }
+inline int fourth_advective_launches(int dim, int limiter) { return 4 + (limiter ? 8 : 5) * dim; }
 // kernel launches of one fourth-order implicit update (maps, Newton, map, update)
 constexpr int FOURTH_NEWTON_LAUNCHES = 5;
 constexpr int FOURTH_SOURCE_LAUNCHES = 3;
 
-// A = fourth-order advective term of the averages U
-cudaError_t launch_advective4(const NetParams& P, int dim, long long N, const BoxDev* boxes, int nbox,
+// A = fourth-order advective term of the averages U (limiter: 0 smooth form, 1 limited form)
+cudaError_t launch_advective4(const NetParams& P, int dim, int limiter, long long N, const BoxDev* boxes, int nbox,
                               const double* U, double* A, const FourthWs& w, cudaStream_t st);
 // R = averaged reactive source, R(U_c) + L R(U_c)/24 with U_c = U - L U/24
 cudaError_t launch_reaction_source4(const NetParams& P, int dim, long long N, const BoxDev* boxes, int nbox,

@@ -20,6 +20,29 @@ def rel_err(gpu, orc, nvar, dim, species_floor=1e-6):
     return np.array(out)
 
 
+def flux_term_scale(U, P):
+    """Per field, a bound on the terms whose difference over dx is the
+    advective term: the HLLC flux combines F(U) and S U, each at most
+    (|U_f| + p) (|u| + c) per field (p only in the momenta and the energy),
+    over the smallest dx.  A's rounding error is a small multiple of the unit
+    round-off times this, whatever the size of A itself."""
+    V = np.asarray(U).reshape(P.nvar, -1)
+    dim = P.dim
+    rho = V[0]
+    u = V[1:1 + dim] / rho
+    ke = 0.5 * rho * (u * u).sum(0)
+    p = (P.gamma - 1.0) * (V[1 + dim] - ke)
+    c = np.sqrt(P.gamma * np.maximum(p, 0.0) / rho)
+    speed = (np.abs(u).max(0) + c).max()
+    pmax = np.abs(p).max()
+    idx = 1.0 / min(P.dx[:dim])
+    out = []
+    for f in range(P.nvar):
+        extra = pmax if 1 <= f <= 1 + dim else 0.0
+        out.append((np.abs(V[f]).max() + extra) * speed * idx)
+    return np.array(out)
+
+
 def rel_err_R(gpu, orc, n, scale):
     g = np.asarray(gpu).reshape(n, -1)
     o = np.asarray(orc).reshape(n, -1)
