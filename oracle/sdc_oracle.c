@@ -382,14 +382,14 @@ static double cs_face(double am, double a0, double ap, double app, double af) {
    apply.  The distance-two test catches an extremum that sits on a face of the
    zone: there the parabola meets the overshoot bound |dp| = 2 |dm| exactly, and
    the overshoot limit would clip smooth data by O(h^4) */
-/* a difference of two averages, zero when it is within 1e-12 of their
-   magnitudes: averages that mirror each other across a plane of symmetry of
-   the data differ only by rounding, and the extremum tests below would
-   otherwise take their branch from the order of that rounding */
-#define CS_FLAT 1e-12
+/* a difference of two averages, zero when it is at most 2^-36 (1.5e-11) of
+   the larger magnitude: averages that mirror each other across a plane of
+   symmetry of the data differ only by rounding (up to 2^-39 of their size on
+   the seeded boxes, whose coordinates are rounded), and the extremum tests
+   below would otherwise take their branch from the order of that rounding */
 static double avg_diff(double a, double b) {
     double d = a - b;
-    return fabs(d) <= CS_FLAT * (fabs(a) + fabs(b)) ? 0.0 : d;
+    return fabs(d) <= ldexp(fmax(fabs(a), fabs(b)), -36) ? 0.0 : d;
 }
 
 static void cs_zone(double amm, double am, double a0, double ap, double app, double* fm, double* fp) {

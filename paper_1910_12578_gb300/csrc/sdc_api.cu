@@ -686,14 +686,14 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
         }
     if (c->space_order == 4) {
         FourthWs& w = c->fw;
-        double** arrays[] = {&w.Uc, &w.W2, &w.Wc, &w.Wa, &w.Wf, &w.Wfc, &w.Fc, &w.F2, &w.Fa, &w.rc, &w.gc};
+        double** arrays[] = {&w.Uc, &w.W2, &w.Wc, &w.Wa, &w.Fc, &w.F2, &w.Fa, &w.rc, &w.gc};
         for (double** a : arrays)
             if ((e = ctx_alloc(c, (void**)a, ub)) != cudaSuccess) return fail(e);
-        if (c->limiter) {
-            double** sides[] = {&w.WL, &w.WR, &w.WLc, &w.WRc};
-            for (double** a : sides)
-                if ((e = ctx_alloc(c, (void**)a, ub)) != cudaSuccess) return fail(e);
-        }
+        // the face states: one face average and its centre map (smooth form) or
+        // the two limited sides (limited form)
+        double** faces[] = {c->limiter ? &w.WL : &w.Wf, c->limiter ? &w.WR : &w.Wfc};
+        for (double** a : faces)
+            if ((e = ctx_alloc(c, (void**)a, ub)) != cudaSuccess) return fail(e);
         if ((e = ctx_alloc(c, (void**)&w.Rc, rb)) != cudaSuccess) return fail(e);
     }
     if ((e = cudaMemcpy(c->d_boxes, hb.data(), sizeof(BoxDev) * nbox, cudaMemcpyHostToDevice)) != cudaSuccess)

@@ -16,7 +16,7 @@
 // difference (Colella & Sekora's face limiter); then every zone limits its two
 // face values, by a limited curvature at an extremum (of the face values about
 // the average, or of the averages at distance one or two, differences within
-// 1e-12 of the averages counting as ties) and by the PPM
+// 2^-36 of the averages counting as ties) and by the PPM
 // overshoot bounds elsewhere; the limited mass fractions are renormalised; the
 // two sides of a face then give its flux by HLLC, at the face centres and from
 // the face averages alike.  The averaged source is R(U_c) + L R(U_c)/24; the implicit update is solved at
@@ -164,136 +164,222 @@ __global__ void face_flux_kernel(int dim, int nspec, double igm1, int dir, long 
 // ---- limited form
 constexpr double CS_C = 1.25;  // bound of the limited curvature over its neighbours'
 
-__device__ __forceinline__ bool same_sign3(double a, double b, double c) {
-    return (a > 0.0 && b > 0.0 && c > 0.0) || (a < 0.0 && b < 0.0 && c < 0.0);
+// zone indices o steps from z along d, periodic in the box (|o| <= 2, any n >= 1)
+struct Line {
+    long long z, stride;
+    int c, n;
+    __device__ __forceinline__ long long at(int o) const {
+        int cc = c + o;
+        while (cc < 0) cc += n;
+        while (cc >= n) cc -= n;
+        return z + (long long)(cc - c) * stride;
+    }
+};
+
+// element d of a 3-array by selects (a runtime index would put the array on the stack)
+__device__ __forceinline__ int sel3(const int* a, int d) { return d == 0 ? a[0] : (d == 1 ? a[1] : a[2]); }
+
+__device__ __forceinline__ Line line_of(const ZoneCoord& q, long long z, int d) {
+    Line l;
+    l.z = z;
+    l.c = sel3(q.c, d);
+    l.n = sel3(q.n, d);
+    l.stride = d == 0 ? 1 : (d == 1 ? (long long)q.n[0] : (long long)q.n[0] * q.n[1]);
+    return l;
 }
+
+// Sign tests on bit patterns (integer pipe; FP64 compares and products issue on
+// the narrow FP64 pipe).  They equal the plain products' tests except when a
+// product of two nonzero differences underflows to zero.
+__device__ __forceinline__ bool nonzero(double x) { return mag2(x) != 0ull; }
+// x y < 0
+__device__ __forceinline__ bool opposite(double x, double y) {
+    return nonzero(x) && nonzero(y) && (dbits(x) ^ dbits(y)) < 0;
+}
+// x y > 0
+__device__ __forceinline__ bool same2(double x, double y) {
+    return nonzero(x) && nonzero(y) && (dbits(x) ^ dbits(y)) >= 0;
+}
+// of two values of one sign, the smaller in magnitude
+__device__ __forceinline__ double min_mag(double x, double y) { return mag2(x) <= mag2(y) ? x : y; }
 
 // face between zones a0 and ap (neighbours am, app): a value outside [a0, ap]
 // becomes (a0 + ap)/2 - d2/6, d2 the second difference 3 (a0 - 2 af + ap)
 // limited by C times those of the two zones; the unlimited d2 returns af itself
 __device__ __forceinline__ double cs_face(double am, double a0, double ap, double app, double af) {
-    if ((af - a0) * (ap - af) < 0.0) {
-        const double d2f = 3.0 * (a0 - 2.0 * af + ap);
-        const double d2l = am - 2.0 * a0 + ap, d2r = a0 - 2.0 * ap + app;
-        double d2 = 0.0;
-        if (same_sign3(d2f, d2l, d2r)) {
-            const double m = fmin(fmin(CS_C * fabs(d2l), CS_C * fabs(d2r)), fabs(d2f));
-            d2 = d2f > 0.0 ? m : -m;
-        }
-        af = 0.5 * (a0 + ap) - d2 * (1.0 / 6.0);
-    }
-    return af;
+    if (!opposite(af - a0, ap - af)) return af;
+    const double d2f = 3.0 * fma(-2.0, af, a0 + ap);
+    const double d2l = fma(-2.0, a0, am + ap), d2r = fma(-2.0, ap, a0 + app);
+    double d2 = 0.0;
+    if (same2(d2f, d2l) && same2(d2f, d2r)) d2 = min_mag(d2f, CS_C * min_mag(d2l, d2r));
+    return fma(d2, -1.0 / 6.0, 0.5 * (a0 + ap));
 }
 
-// a difference of two averages, zero within 1e-12 of their magnitudes:
-// averages mirrored across a plane of symmetry of the data differ only by
-// rounding, and the extremum tests would take their branch from its order
-constexpr double CS_FLAT = 1e-12;
+// a difference of two averages, zero where it is at most 2^-36 of the larger
+// magnitude: averages mirrored across a plane of symmetry of the data differ
+// only by rounding, and the extremum tests would take their branch from its
+// order.  2^-36 |x| is the bit pattern of x less 36 in the exponent field (mag2
+// units of 2^53); below |x| = 2^-986 only an exact zero counts.
 __device__ __forceinline__ double avg_diff(double a, double b) {
+    constexpr unsigned long long E36 = 36ull << 53;
     const double d = a - b;
-    return fabs(d) <= CS_FLAT * (fabs(a) + fabs(b)) ? 0.0 : d;
+    const unsigned long long M = max(mag2(a), mag2(b));
+    const unsigned long long thr = M > E36 ? M - E36 : 0ull;
+    return mag2(d) <= thr ? 0.0 : d;
 }
 
 // zone a0 (neighbours amm .. app) with face values fm (lower) and fp (upper)
 __device__ __forceinline__ void cs_zone(double amm, double am, double a0, double ap, double app, double& fm,
                                         double& fp) {
     const double dm = fm - a0, dp = fp - a0;
-    if (dp * dm >= 0.0 || avg_diff(am, a0) * avg_diff(a0, ap) <= 0.0 ||
-        avg_diff(amm, a0) * avg_diff(a0, app) <= 0.0) {
+    if (!opposite(dp, dm) || !same2(avg_diff(am, a0), avg_diff(a0, ap)) ||
+        !same2(avg_diff(amm, a0), avg_diff(a0, app))) {
         // extremum: scale both deviations by the limited curvature over the parabola's
-        const double d2 = 6.0 * (fm + fp - 2.0 * a0);
-        const double d2c = am - 2.0 * a0 + ap, d2l = amm - 2.0 * am + a0, d2r = a0 - 2.0 * ap + app;
-        double lim = 0.0;
-        if (same_sign3(d2, d2c, d2l) && same_sign3(d2, d2c, d2r)) {
-            const double m = fmin(fmin(fabs(d2), CS_C * fabs(d2c)), fmin(CS_C * fabs(d2l), CS_C * fabs(d2r)));
-            lim = d2 > 0.0 ? m : -m;
+        const double d2 = 6.0 * fma(-2.0, a0, fm + fp);
+        const double d2c = fma(-2.0, a0, am + ap), d2l = fma(-2.0, am, amm + a0), d2r = fma(-2.0, ap, a0 + app);
+        if (same2(d2, d2c) && same2(d2, d2l) && same2(d2, d2r)) {
+            const double cm = CS_C * min_mag(d2c, min_mag(d2l, d2r));
+            if (mag2(d2) <= mag2(cm)) {
+                // the parabola's own curvature is the smallest: the deviations stand
+                fm = a0 + dm;
+                fp = a0 + dp;
+            } else {
+                // in (0, 1); the Newton-Raphson reciprocal takes normal d2 only
+                // (2^-1021 <= |d2| < 2^1022), the division the rest
+                const unsigned long long e2 = mag2(d2) >> 53;
+                const double sc = (e2 >= 2ull && e2 < 2045ull) ? cm * rcp_nr(d2) : cm / d2;
+                fm = fma(dm, sc, a0);
+                fp = fma(dp, sc, a0);
+            }
+        } else {
+            fm = a0;
+            fp = a0;
         }
-        const double s = d2 != 0.0 ? lim / d2 : 0.0;
-        fm = fma(dm, s, a0);
-        fp = fma(dp, s, a0);
     } else {
         // monotone: the parabola may not overshoot the far face
-        if (fabs(dp) >= 2.0 * fabs(dm)) fp = a0 - 2.0 * dm;
-        if (fabs(dm) >= 2.0 * fabs(dp)) fm = a0 - 2.0 * dp;
+        const double tm = dm + dm, tp = dp + dp;
+        if (mag2(dp) >= mag2(tm)) fp = a0 - tm;
+        if (mag2(dm) >= mag2(tp)) fm = a0 - tp;
     }
 }
 
-// Wl = face-limited face averages (the face between z and its +1 neighbour along dir)
-__global__ void limit_face_kernel(int dir, int nf, long long N, const BoxDev* __restrict__ boxes, int nbox,
-                                  const double* __restrict__ Wa, const double* __restrict__ Wf,
-                                  double* __restrict__ Wl) {
+// One thread per zone: the zone's two face averages along dir from the
+// primitive averages z-2 .. z+2, each through the face limiter, then both
+// through the zone limiter; WL[z] = the upper face (left side of the face
+// z+1/2), WR[z-1] = the lower face (right side of the face z-1/2).  The limited
+// mass fractions are renormalised: stored first, then read back and scaled.
+__global__ void limit4_kernel(int dim, int nspec, int dir, long long N, const BoxDev* __restrict__ boxes, int nbox,
+                              const double* __restrict__ Wa, double* __restrict__ WL, double* __restrict__ WR) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= N) return;
     const ZoneCoord q = zone_coord(boxes, nbox, z);
-    const long long zm = neighbour(q, dir, -1), zp = neighbour(q, dir, 1), zpp = neighbour(q, dir, 2);
-    for (int f = 0; f < nf; f++) {
-        const long long o = (long long)f * N;
-        Wl[o + z] = cs_face(Wa[o + zm], Wa[o + z], Wa[o + zp], Wa[o + zpp], Wf[o + z]);
-    }
-}
-
-// zone z limits its two face values: WL[z] = its upper face (left side of the
-// face z+1/2), WR[z-1] = its lower face (right side of the face z-1/2)
-__global__ void limit_zone_kernel(int dim, int nspec, int dir, long long N, const BoxDev* __restrict__ boxes,
-                                  int nbox, const double* __restrict__ Wa, const double* __restrict__ Wl,
-                                  double* __restrict__ WL, double* __restrict__ WR) {
-    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (z >= N) return;
-    const ZoneCoord q = zone_coord(boxes, nbox, z);
-    const long long zmm = neighbour(q, dir, -2), zm = neighbour(q, dir, -1);
-    const long long zp = neighbour(q, dir, 1), zpp = neighbour(q, dir, 2);
+    const Line l = line_of(q, z, dir);
+    const long long i0 = l.at(-2), i1 = l.at(-1), i3 = l.at(1), i4 = l.at(2);
     const int nh = 2 + dim, nv = nh + nspec;
-    double fm[F_MAXV], fp[F_MAXV];
+    double sm = 0.0, sp = 0.0;
     for (int f = 0; f < nv; f++) {
         const long long o = (long long)f * N;
-        fm[f] = Wl[o + zm];
-        fp[f] = Wl[o + z];
-        cs_zone(Wa[o + zmm], Wa[o + zm], Wa[o + z], Wa[o + zp], Wa[o + zpp], fm[f], fp[f]);
+        const double amm = Wa[o + i0], am = Wa[o + i1], a0 = Wa[o + z], ap = Wa[o + i3], app = Wa[o + i4];
+        double fm = 7.0 / 12.0 * (am + a0) - 1.0 / 12.0 * (amm + ap);
+        double fp = 7.0 / 12.0 * (a0 + ap) - 1.0 / 12.0 * (am + app);
+        fm = cs_face(amm, am, a0, ap, fm);
+        fp = cs_face(am, a0, ap, app, fp);
+        cs_zone(amm, am, a0, ap, app, fm, fp);
+        WL[o + z] = fp;
+        WR[o + i1] = fm;
+        if (f >= nh) {
+            sm += fm;
+            sp += fp;
+        }
     }
     if (nspec > 0) {
-        double sm = 0.0, sp = 0.0;
-        for (int s = 0; s < nspec; s++) {
-            sm += fm[nh + s];
-            sp += fp[nh + s];
+        const double rm = 1.0 / sm, rp = 1.0 / sp;
+        for (int f = nh; f < nv; f++) {
+            const long long o = (long long)f * N;
+            WL[o + z] *= rp;
+            WR[o + i1] *= rm;
         }
-        for (int s = 0; s < nspec; s++) {
-            fm[nh + s] /= sm;
-            fp[nh + s] /= sp;
-        }
-    }
-    for (int f = 0; f < nv; f++) {
-        WL[(long long)f * N + z] = fp[f];
-        WR[(long long)f * N + zm] = fm[f];
     }
 }
 
-// Fc = HLLC(WLc, WRc) (face centres), F2 = HLLC(WL, WR) (from the face
-// averages); species: mass flux times X of the side upwind of the contact
+// transverse neighbours of z (the dimensions other than dir): up to 2 pairs
+struct Transverse {
+    long long p[2], m[2];
+    int nt;
+};
+
+__device__ __forceinline__ Transverse transverse_of(const ZoneCoord& q, long long z, int dim, int dir) {
+    // the dimensions other than dir, ascending: (1, 2), (0, 2) or (0, 1)
+    const int d1 = dir == 0 ? 1 : 0, d2 = dir == 2 ? 1 : 2;
+    Transverse t;
+    t.nt = (d1 < dim) + (d2 < dim);
+    t.p[0] = t.m[0] = t.p[1] = t.m[1] = z;
+    if (d1 < dim) {
+        const Line l = line_of(q, z, d1);
+        t.p[0] = l.at(1);
+        t.m[0] = l.at(-1);
+    }
+    if (d2 < dim) {
+        const Line l = line_of(q, z, d2);
+        t.p[1] = l.at(1);
+        t.m[1] = l.at(-1);
+    }
+    return t;
+}
+
+// a + coef (sum over the transverse pairs of b(+) + b(-) - 2 nt b(z)), the
+// arithmetic of lap_combine_kernel
+__device__ __forceinline__ double lap_t(const double* __restrict__ b, long long o, long long z, const Transverse& t,
+                                        double a, double coef) {
+    if (t.nt == 0) return a;
+    double sn = b[o + t.p[0]] + b[o + t.m[0]];
+    if (t.nt == 2) sn = sn + (b[o + t.p[1]] + b[o + t.m[1]]);
+    return fma(coef, fma(-2.0 * t.nt, b[o + z], sn), a);
+}
+
+// Fc = HLLC between the face-centre states (WL, WR less L_t/24 of themselves,
+// formed here from the transverse neighbours), F2 = HLLC between WL and WR;
+// species: mass flux times X of the side upwind of the contact
 template <int DIM>
-__global__ void face_hllc_kernel(int nspec, double g, double gm1_inv, int dir, long long N,
-                                 const double* __restrict__ WLc, const double* __restrict__ WRc,
-                                 const double* __restrict__ WL, const double* __restrict__ WR,
-                                 double* __restrict__ Fc, double* __restrict__ F2) {
+__global__ void face_hllc4_kernel(int nspec, double g, double gm1_inv, int dir, long long N,
+                                  const BoxDev* __restrict__ boxes, int nbox, const double* __restrict__ WL,
+                                  const double* __restrict__ WR, double* __restrict__ Fc, double* __restrict__ F2) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= N) return;
     constexpr int NH = 2 + DIM;
     const int nv = NH + nspec;
-    for (int side = 0; side < 2; side++) {
-        const double* L = side ? WL : WLc;
-        const double* R = side ? WR : WRc;
-        double* F = side ? F2 : Fc;
-        double qL[NH], qR[NH], Fh[NH];
+    const ZoneCoord q = zone_coord(boxes, nbox, z);
+    const Transverse t = transverse_of(q, z, DIM, dir);
+    constexpr double c24 = -1.0 / 24.0;
+    double qL[NH], qR[NH], Fh[NH];
+    // face centres
 #pragma unroll
-        for (int f = 0; f < NH; f++) {
-            qL[f] = L[(long long)f * N + z];
-            qR[f] = R[(long long)f * N + z];
-        }
-        const double Ss = hllc_hydro<DIM>(g, gm1_inv, dir, qL, qR, Fh);
-#pragma unroll
-        for (int f = 0; f < NH; f++) F[(long long)f * N + z] = Fh[f];
-        const double* Xup = Ss >= 0.0 ? L : R;
-        for (int f = NH; f < nv; f++) F[(long long)f * N + z] = Fh[0] * Xup[(long long)f * N + z];
+    for (int f = 0; f < NH; f++) {
+        const long long o = (long long)f * N;
+        qL[f] = lap_t(WL, o, z, t, WL[o + z], c24);
+        qR[f] = lap_t(WR, o, z, t, WR[o + z], c24);
     }
+    double Ss = hllc_hydro<DIM>(g, gm1_inv, dir, qL, qR, Fh);
+#pragma unroll
+    for (int f = 0; f < NH; f++) Fc[(long long)f * N + z] = Fh[f];
+    {
+        const double* X = Ss >= 0.0 ? WL : WR;
+        for (int f = NH; f < nv; f++) {
+            const long long o = (long long)f * N;
+            Fc[o + z] = Fh[0] * lap_t(X, o, z, t, X[o + z], c24);
+        }
+    }
+    // face averages
+#pragma unroll
+    for (int f = 0; f < NH; f++) {
+        qL[f] = WL[(long long)f * N + z];
+        qR[f] = WR[(long long)f * N + z];
+    }
+    Ss = hllc_hydro<DIM>(g, gm1_inv, dir, qL, qR, Fh);
+#pragma unroll
+    for (int f = 0; f < NH; f++) F2[(long long)f * N + z] = Fh[f];
+    const double* X = Ss >= 0.0 ? WL : WR;
+    for (int f = NH; f < nv; f++) F2[(long long)f * N + z] = Fh[0] * X[(long long)f * N + z];
 }
 
 // A (first direction: =, else -=) the flux difference over dx
@@ -303,7 +389,7 @@ __global__ void div_kernel(int dir, int nf, long long N, const BoxDev* __restric
     if (z >= N) return;
     const ZoneCoord q = zone_coord(boxes, nbox, z);
     const double idx = boxes[box_index(boxes, nbox, z)].idx[dir];
-    const long long zm = neighbour(q, dir, -1);
+    const long long zm = line_of(q, z, dir).at(-1);
     for (int f = 0; f < nf; f++) {
         const long long o = (long long)f * N;
         const double d = (Fa[o + z] - Fa[o + zm]) * idx;
@@ -333,20 +419,21 @@ cudaError_t lap(int dim, int nf, long long N, const BoxDev* boxes, int nbox, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_face_hllc(const NetParams& P, int dim, int dir, long long N, const FourthWs& w, cudaStream_t st) {
+cudaError_t launch_face_hllc4(const NetParams& P, int dim, int dir, long long N, const BoxDev* boxes, int nbox,
+                              const FourthWs& w, cudaStream_t st) {
     const double g = P.gamma, gi = 1.0 / P.gm1;
     switch (dim) {
         case 1:
-            face_hllc_kernel<1><<<fgrid(N), F_BLOCK, 0, st>>>(P.nspec, g, gi, dir, N, w.WLc, w.WRc, w.WL, w.WR, w.Fc,
-                                                               w.F2);
+            face_hllc4_kernel<1><<<fgrid(N), F_BLOCK, 0, st>>>(P.nspec, g, gi, dir, N, boxes, nbox, w.WL, w.WR, w.Fc,
+                                                                w.F2);
             break;
         case 2:
-            face_hllc_kernel<2><<<fgrid(N), F_BLOCK, 0, st>>>(P.nspec, g, gi, dir, N, w.WLc, w.WRc, w.WL, w.WR, w.Fc,
-                                                               w.F2);
+            face_hllc4_kernel<2><<<fgrid(N), F_BLOCK, 0, st>>>(P.nspec, g, gi, dir, N, boxes, nbox, w.WL, w.WR, w.Fc,
+                                                                w.F2);
             break;
         default:
-            face_hllc_kernel<3><<<fgrid(N), F_BLOCK, 0, st>>>(P.nspec, g, gi, dir, N, w.WLc, w.WRc, w.WL, w.WR, w.Fc,
-                                                               w.F2);
+            face_hllc4_kernel<3><<<fgrid(N), F_BLOCK, 0, st>>>(P.nspec, g, gi, dir, N, boxes, nbox, w.WL, w.WR, w.Fc,
+                                                                w.F2);
             break;
     }
     return cudaGetLastError();
@@ -365,24 +452,22 @@ cudaError_t launch_advective4(const NetParams& P, int dim, int limiter, long lon
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = lap(dim, nv, N, boxes, nbox, w.Wc, w.W2, 1.0 / 24.0, -1, w.Wa, st)) != cudaSuccess) return e;
     for (int dir = 0; dir < dim; dir++) {
-        face_avg_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dir, nv, N, boxes, nbox, w.Wa, w.Wf);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (limiter) {
-            // Wfc holds the face-limited averages here
-            limit_face_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dir, nv, N, boxes, nbox, w.Wa, w.Wf, w.Wfc);
+            // face averages, face and zone limiters in one pass; HLLC with the
+            // face-centre maps formed in place
+            limit4_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dim, P.nspec, dir, N, boxes, nbox, w.Wa, w.WL, w.WR);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            limit_zone_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dim, P.nspec, dir, N, boxes, nbox, w.Wa, w.Wfc, w.WL,
-                                                            w.WR);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            if ((e = lap(dim, nv, N, boxes, nbox, w.WL, w.WL, -1.0 / 24.0, dir, w.WLc, st)) != cudaSuccess) return e;
-            if ((e = lap(dim, nv, N, boxes, nbox, w.WR, w.WR, -1.0 / 24.0, dir, w.WRc, st)) != cudaSuccess) return e;
-            if ((e = launch_face_hllc(P, dim, dir, N, w, st)) != cudaSuccess) return e;
+            if ((e = launch_face_hllc4(P, dim, dir, N, boxes, nbox, w, st)) != cudaSuccess) return e;
         } else {
+            face_avg_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dir, nv, N, boxes, nbox, w.Wa, w.Wf);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
             if ((e = lap(dim, nv, N, boxes, nbox, w.Wf, w.Wf, -1.0 / 24.0, dir, w.Wfc, st)) != cudaSuccess) return e;
             face_flux_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dim, P.nspec, 1.0 / P.gm1, dir, N, w.Wfc, w.Wf, w.Fc,
                                                            w.F2);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
+        // face-average fluxes once per face (fused into the divergence, each face's
+        // map would be formed twice on the FP64 pipe), then the divergence
         if ((e = lap(dim, nv, N, boxes, nbox, w.Fc, w.F2, 1.0 / 24.0, dir, w.Fa, st)) != cudaSuccess) return e;
         div_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dir, nv, N, boxes, nbox, w.Fa, A, dir == 0 ? 1 : 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

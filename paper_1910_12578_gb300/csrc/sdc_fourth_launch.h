@@ -14,20 +14,17 @@ namespace sdcd {
 // device workspace of the fourth-order operators (owned by the context)
 struct FourthWs {
     double *Uc = nullptr, *W2 = nullptr, *Wc = nullptr, *Wa = nullptr;  // [nvar][N]
-    double *Wf = nullptr, *Wfc = nullptr, *Fc = nullptr, *F2 = nullptr, *Fa = nullptr;
-    // limited form only: the two sides of every face, averages and centres
-    double *WL = nullptr, *WR = nullptr, *WLc = nullptr, *WRc = nullptr;
+    double *Wf = nullptr, *Wfc = nullptr, *Fc = nullptr, *F2 = nullptr, *Fa = nullptr;  // smooth form: Wf, Wfc
+    double *WL = nullptr, *WR = nullptr;  // limited form: the two sides of every face
     double *rc = nullptr, *gc = nullptr;  // zone-centre rhs and guess of the implicit update [nvar][N]
     double* Rc = nullptr;                 // zone-centre source [nspec + 1][N]
 };
 
 // doubles of workspace per zone
-inline long long fourth_ws_doubles_per_zone(int nvar, int nw, int limiter) {
-    return (limiter ? 15LL : 11LL) * nvar + nw;
-}
+inline long long fourth_ws_doubles_per_zone(int nvar, int nw) { return 11LL * nvar + nw; }
 
 // kernel launches of one fourth-order advective term
-inline int fourth_advective_launches(int dim, int limiter) { return 4 + (limiter ? 8 : 5) * dim; }
+inline int fourth_advective_launches(int dim, int limiter) { return 4 + (limiter ? 4 : 5) * dim; }
 // kernel launches of one fourth-order implicit update (maps, Newton, map, update)
 constexpr int FOURTH_NEWTON_LAUNCHES = 5;
 constexpr int FOURTH_SOURCE_LAUNCHES = 3;

@@ -1,7 +1,8 @@
 """Run SDC steps of a named workload for a profiler (ncu) or a quick timing.
 
     python -m paper_1910_12578_gb300.profile_step --config box64 --stencil-variant 1 --newton-variant 1 \\
-        --warmup 1 --steps 2 [--eager] [--prec fp32jac] [--space-order 4] [--nodes radau] [--backward]
+        --warmup 1 --steps 2 [--eager] [--prec fp32jac] [--space-order 4] [--limiter 0] [--nodes radau] \\
+        [--backward]
 
 Every step starts from the same seeded initial state.  With --eager the kernels
 are launched one by one (sdc_step_profile, CUDA events per kernel class);
@@ -47,6 +48,7 @@ def main(argv=None):
     p.add_argument("--warmup", type=int, default=1)
     p.add_argument("--steps", type=int, default=1)
     p.add_argument("--space-order", type=int, choices=[2, 4], default=2)
+    p.add_argument("--limiter", type=int, choices=[0, 1], default=1)
     p.add_argument("--nodes", choices=["lobatto", "radau"], default="lobatto")
     p.add_argument("--backward", action="store_true", help="then one adjoint step (sdc_step_backward)")
     a = p.parse_args(argv)
@@ -57,7 +59,7 @@ def main(argv=None):
     from paper_1910_12578_gb300 import sdc
     P, U = workload(a.config, seed)
     for q in (P if isinstance(P, list) else [P]):
-        q.space_order, q.nodes = a.space_order, a.nodes
+        q.space_order, q.nodes, q.limiter = a.space_order, a.nodes, a.limiter
     P0 = P[0] if isinstance(P, list) else P
     ctx = sdc.Context(P, prec=sdc.PREC_FP64 if a.prec == "fp64" else sdc.PREC_FP32_JAC)
     U0 = torch.from_numpy(U).cuda()
@@ -96,7 +98,7 @@ def main(argv=None):
         torch.cuda.synchronize()
         back = ev[0].elapsed_time(ev[1])
     print(json.dumps({"config": a.config, "seed": seed, "prec": a.prec, "variants": variants,
-                      "space_order": a.space_order, "nodes": a.nodes, "eager": a.eager, "steps": out,
+                      "space_order": a.space_order, "limiter": a.limiter, "nodes": a.nodes, "eager": a.eager, "steps": out,
                       "backward_ms": back}), flush=True)
     ctx.close()
     return 0

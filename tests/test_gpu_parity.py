@@ -118,13 +118,15 @@ def test_advective_term_parity(torch_cuda, name):
     assert err.max() <= TOL64, err
 
 
-def test_advective_term_subnormal_inputs(torch_cuda):
+@pytest.mark.parametrize("name", ["box16", "box16_o4"])
+def test_advective_term_subnormal_inputs(torch_cuda, name):
     """States with subnormal momenta and mass fractions (a symmetric cancellation
-    leaves momenta near 1e-310): the MC limiter's bit-pattern arithmetic must stay
-    finite and agree with the plain formula."""
+    leaves momenta near 1e-310): the MC limiter's bit-pattern arithmetic, and the
+    fourth-order limiters' (bit-pattern sign tests and dead zone, a reciprocal of
+    a subnormal curvature), must stay finite and agree with the plain formula."""
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
-    P, U = PROBS["box16"]
+    P, U = PROBS[name]
     U = U.copy()
     rng = np.random.default_rng(11)
     tiny = rng.choice([-1.0, 1.0], size=U.shape[1:]) * rng.uniform(0.0, 3e-308, size=U.shape[1:])
