@@ -92,7 +92,8 @@ typedef struct {
     int n_nodes;           /* M: temporal nodes including node 0 (2 or 3;
                               Radau also 4)                                   */
     int n_iters;           /* K: SDC iterations per step, >= 1              */
-    int limiter;           /* 1 = MC limited PLM, 0 = unlimited centred PLM */
+    int limiter;           /* order 2: 1 = MC limited PLM, 0 = centred PLM;  */
+                           /* order 4: 1 = limited, 0 = smooth-flow form     */
     sdc_precision prec;    /* Newton linear algebra precision               */
     double newton_rtol;    /* scaled Newton update that ends the solve      */
     int newton_maxit;      /* iteration cap per zone solve                  */
@@ -102,14 +103,20 @@ typedef struct {
 } sdc_params;
 
 /* space_order = 4 (section 2: the fourth-order method pairs Simpson's rule with
-   McCorquodale & Colella's reconstruction), smooth-flow form without limiting:
-   zone centres f_c = <f> - L<f>/24 (L: second differences summed over the
-   dimensions), primitive averages W(U_c) + L W(<U>)/24, face averages by the
-   7/12, -1/12 stencil, face fluxes F(W_f) + L_t F(<W>_f)/24 with face-centre
-   states W_f = <W>_f - L_t <W>_f/24 (L_t across the face), averaged sources
+   McCorquodale & Colella's reconstruction): zone centres f_c = <f> - L<f>/24
+   (L: second differences summed over the dimensions), primitive averages
+   W(U_c) + L W(<U>)/24, face averages by the 7/12, -1/12 stencil, face fluxes
+   F_c + L_t F_2/24 (L_t: second differences across the face), averaged sources
    R(U_c) + L R(U_c)/24, and the implicit update solved at zone centres with
-   <U> = <rhs> + dt_m <R>.  The limiter argument is ignored; the adjoint and
-   sdc_step_static take space_order 2 only. */
+   <U> = <rhs> + dt_m <R>.  limiter = 0, smooth-flow form: F_c = F(W_f) at the
+   face-centre state W_f = <W>_f - L_t <W>_f/24, F_2 = F(<W>_f), the physical
+   flux.  limiter = 1, limited form: each face average is limited (Colella &
+   Sekora's face limiter), every zone limits its two face values (a limited
+   curvature at extrema, where differences of averages within 2^-36 of them
+   count as ties; the PPM overshoot bounds elsewhere) with the mass fractions
+   renormalised, and F_c, F_2 are HLLC fluxes between the two limited sides (at
+   the face centres, each side less L_t/24 of itself, and at the face averages).
+   The adjoint and sdc_step_static take space_order 2 only. */
 
 /* Temporal node sets of the SDC step (n_nodes = M):
    SDC_NODES_LOBATTO: Gauss-Lobatto nodes {0,1} or {0,1/2,1}; the integral of
