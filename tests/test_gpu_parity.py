@@ -47,7 +47,7 @@ def problems():
     P, U = W.config_box(n=16, nspec=13, n_iters=4, seed=0, T0=0.5)
     out["box16_13"] = (P, U)
     # Radau node set (node 0 + Radau IIA points; quadrature through those points)
-    # (cfg 1 doubles a 1e-14 perturbation about every step under any node set;
+    # (the 64-zone 1D flow doubles a 1e-14 perturbation about every step under any node set;
     # Radau with M = 2, K = 2 grows it ~2800x over 10 steps, so the 10-step 1D
     # case uses M = 3, K = 3 and M = 2 is covered on 16^3 over 2 steps)
     P, U = W.config_1d()

@@ -622,7 +622,7 @@ def _run_1d_burning(n, order, tf=0.1, limiter=0):
     P.limiter, P.n_nodes, P.n_iters, P.space_order = limiter, 3, 4, order
     P.newton_rtol = 1e-14
     o = O.Oracle(P)
-    if order == 4:   # config 1's profile gives zone-centre values
+    if order == 4:   # the 1D profile is given at zone centres
         U = o.point_to_avg(U.reshape(P.nvar, -1)).reshape(U.shape)
     nsteps = int(round(tf * n / 0.25))
     V = U.copy()
@@ -716,7 +716,7 @@ def test_strang_without_reactions_is_the_coupled_step():
 
 
 def _coupled_1d(M, K, nodes="lobatto"):
-    """Flow and burning in one problem: config 1 with k0 = 1e4 (14% of the fuel
+    """Flow and burning in one problem: the 64-zone 1D flow with k0 = 1e4 (14% of the fuel
     burns in t = 0.05), centred slopes (smooth in U)."""
     P, U = W.config_1d(64)
     P.net = W.decay_network(k0=1e4)
