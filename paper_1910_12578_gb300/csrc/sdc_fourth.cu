@@ -203,11 +203,11 @@ __device__ __forceinline__ bool same2(double x, double y) {
 // of two values of one sign, the smaller in magnitude
 __device__ __forceinline__ double min_mag(double x, double y) { return mag2(x) <= mag2(y) ? x : y; }
 
-// face between zones a0 and ap (neighbours am, app): a value outside [a0, ap]
-// becomes (a0 + ap)/2 - d2/6, d2 the second difference 3 (a0 - 2 af + ap)
-// limited by C times those of the two zones; the unlimited d2 returns af itself
-__device__ __forceinline__ double cs_face(double am, double a0, double ap, double app, double af) {
-    if (!opposite(af - a0, ap - af)) return af;
+// face between zones a0 and ap (neighbours am, app) whose value af lies outside
+// [a0, ap]: it becomes (a0 + ap)/2 - d2/6, d2 the second difference
+// 3 (a0 - 2 af + ap) limited by C times those of the two zones (0 unless all
+// three share a sign); the unlimited d2 would return af itself
+__device__ __forceinline__ double cs_face_limit(double am, double a0, double ap, double app, double af) {
     const double d2f = 3.0 * fma(-2.0, af, a0 + ap);
     const double d2l = fma(-2.0, a0, am + ap), d2r = fma(-2.0, ap, a0 + app);
     double d2 = 0.0;
@@ -215,28 +215,33 @@ __device__ __forceinline__ double cs_face(double am, double a0, double ap, doubl
     return fma(d2, -1.0 / 6.0, 0.5 * (a0 + ap));
 }
 
-// a difference of two averages, zero where it is at most 2^-36 of the larger
-// magnitude: averages mirrored across a plane of symmetry of the data differ
-// only by rounding, and the extremum tests would take their branch from its
-// order.  2^-36 |x| is the bit pattern of x less 36 in the exponent field (mag2
-// units of 2^53); below |x| = 2^-986 only an exact zero counts.
-__device__ __forceinline__ double avg_diff(double a, double b) {
+// d = a - b, and the same difference as the extremum tests see it: zero where
+// it is at most 2^-36 of the larger magnitude (averages mirrored across a plane
+// of symmetry of the data differ only by rounding, and the tests would take
+// their branch from its order).  2^-36 |x| is the bit pattern of x less 36 in
+// the exponent field (mag2 units of 2^53); below |x| = 2^-986 only zero counts.
+__device__ __forceinline__ double avg_diff(double a, double b, double& d) {
     constexpr unsigned long long E36 = 36ull << 53;
-    const double d = a - b;
+    d = a - b;
     const unsigned long long M = max(mag2(a), mag2(b));
     const unsigned long long thr = M > E36 ? M - E36 : 0ull;
     return mag2(d) <= thr ? 0.0 : d;
 }
 
-// zone a0 (neighbours amm .. app) with face values fm (lower) and fp (upper)
-__device__ __forceinline__ void cs_zone(double amm, double am, double a0, double ap, double app, double& fm,
-                                        double& fp) {
-    const double dm = fm - a0, dp = fp - a0;
-    if (!opposite(dp, dm) || !same2(avg_diff(am, a0), avg_diff(a0, ap)) ||
-        !same2(avg_diff(amm, a0), avg_diff(a0, app))) {
-        // extremum: scale both deviations by the limited curvature over the parabola's
-        const double d2 = 6.0 * fma(-2.0, a0, fm + fp);
-        const double d2c = fma(-2.0, a0, am + ap), d2l = fma(-2.0, am, amm + a0), d2r = fma(-2.0, ap, a0 + app);
+// zone limiter of zone a0 (neighbours amm .. app) with face values fm, fp and
+// their deviations dm = fm - a0, dp = fp - a0
+__device__ __forceinline__ void cs_zone(double amm, double am, double a0, double ap, double app, double dm,
+                                        double dp, double& fm, double& fp) {
+    double e1, e2, e3, e4;  // am - a0, a0 - ap, amm - a0, a0 - app
+    const double t1 = avg_diff(am, a0, e1), t2 = avg_diff(a0, ap, e2);
+    const double t3 = avg_diff(amm, a0, e3), t4 = avg_diff(a0, app, e4);
+    if (!opposite(dp, dm) || !same2(t1, t2) || !same2(t3, t4)) {
+        // extremum: scale both deviations by the limited curvature over the
+        // parabola's; the centred second differences from the differences above
+        // (they enter only through signs and magnitudes, where the limiter is
+        // continuous: a curvature near zero flattens either way)
+        const double d2 = 6.0 * (dm + dp);
+        const double d2c = e1 - e2, d2l = fma(-2.0, e1, e3), d2r = fma(2.0, e2, -e4);
         if (same2(d2, d2c) && same2(d2, d2l) && same2(d2, d2r)) {
             const double cm = CS_C * min_mag(d2c, min_mag(d2l, d2r));
             if (mag2(d2) <= mag2(cm)) {
@@ -246,8 +251,8 @@ __device__ __forceinline__ void cs_zone(double amm, double am, double a0, double
             } else {
                 // in (0, 1); the Newton-Raphson reciprocal takes normal d2 only
                 // (2^-1021 <= |d2| < 2^1022), the division the rest
-                const unsigned long long e2 = mag2(d2) >> 53;
-                const double sc = (e2 >= 2ull && e2 < 2045ull) ? cm * rcp_nr(d2) : cm / d2;
+                const unsigned long long ex = mag2(d2) >> 53;
+                const double sc = (ex >= 2ull && ex < 2045ull) ? cm * rcp_nr(d2) : cm / d2;
                 fm = fma(dm, sc, a0);
                 fp = fma(dp, sc, a0);
             }
@@ -256,10 +261,12 @@ __device__ __forceinline__ void cs_zone(double amm, double am, double a0, double
             fp = a0;
         }
     } else {
-        // monotone: the parabola may not overshoot the far face
-        const double tm = dm + dm, tp = dp + dp;
-        if (mag2(dp) >= mag2(tm)) fp = a0 - tm;
-        if (mag2(dm) >= mag2(tp)) fm = a0 - tp;
+        // monotone (dm, dp nonzero): the parabola may not overshoot the far face;
+        // |dp| >= 2 |dm| on the bit patterns (2 |dm| is |dm| with the exponent
+        // field raised by one; subnormal dm aside)
+        constexpr unsigned long long E1 = 1ull << 53;
+        if (mag2(dp) >= mag2(dm) + E1) fp = fma(-2.0, dm, a0);
+        if (mag2(dm) >= mag2(dp) + E1) fm = fma(-2.0, dp, a0);
     }
 }
 
@@ -268,6 +275,8 @@ __device__ __forceinline__ void cs_zone(double amm, double am, double a0, double
 // through the zone limiter; WL[z] = the upper face (left side of the face
 // z+1/2), WR[z-1] = the lower face (right side of the face z-1/2).  The limited
 // mass fractions are renormalised: stored first, then read back and scaled.
+// The face tests' differences give the deviations dm, dp when no face limiter
+// fires (fm - a0 = -(a0 - fm) exactly).
 __global__ void limit4_kernel(int dim, int nspec, int dir, long long N, const BoxDev* __restrict__ boxes, int nbox,
                               const double* __restrict__ Wa, double* __restrict__ WL, double* __restrict__ WR) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -282,9 +291,18 @@ __global__ void limit4_kernel(int dim, int nspec, int dir, long long N, const Bo
         const double amm = Wa[o + i0], am = Wa[o + i1], a0 = Wa[o + z], ap = Wa[o + i3], app = Wa[o + i4];
         double fm = 7.0 / 12.0 * (am + a0) - 1.0 / 12.0 * (amm + ap);
         double fp = 7.0 / 12.0 * (a0 + ap) - 1.0 / 12.0 * (am + app);
-        fm = cs_face(amm, am, a0, ap, fm);
-        fp = cs_face(am, a0, ap, app, fp);
-        cs_zone(amm, am, a0, ap, app, fm, fp);
+        // face tests: (af - left)(right - af) < 0 puts af outside its zones' range
+        double lo = a0 - fm;  // -dm
+        if (opposite(fm - am, lo)) {
+            fm = cs_face_limit(amm, am, a0, ap, fm);
+            lo = a0 - fm;
+        }
+        double dp = fp - a0;
+        if (opposite(dp, ap - fp)) {
+            fp = cs_face_limit(am, a0, ap, app, fp);
+            dp = fp - a0;
+        }
+        cs_zone(amm, am, a0, ap, app, -lo, dp, fm, fp);
         WL[o + z] = fp;
         WR[o + i1] = fm;
         if (f >= nh) {
