@@ -112,8 +112,9 @@ typedef struct {
    face-centre state W_f = <W>_f - L_t <W>_f/24, F_2 = F(<W>_f), the physical
    flux.  limiter = 1, limited form: each face average is limited (Colella &
    Sekora's face limiter), every zone limits its two face values (a limited
-   curvature at extrema, where differences of averages within 2^-36 of them
-   count as ties; the PPM overshoot bounds elsewhere) with the mass fractions
+   curvature at extrema, where a difference of averages within 2^-20 of the
+   other side's or 2^-48 of the averages counts as a tie; the PPM overshoot
+   bounds elsewhere) with the mass fractions
    renormalised, and F_c, F_2 are HLLC fluxes between the two limited sides (at
    the face centres, each side less L_t/24 of itself, and at the face averages).
    The adjoint and sdc_step_static take space_order 2 only. */

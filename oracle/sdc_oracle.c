@@ -382,20 +382,30 @@ static double cs_face(double am, double a0, double ap, double app, double af) {
    apply.  The distance-two test catches an extremum that sits on a face of the
    zone: there the parabola meets the overshoot bound |dp| = 2 |dm| exactly, and
    the overshoot limit would clip smooth data by O(h^4) */
-/* a difference of two averages, zero when it is at most 2^-36 (1.5e-11) of
-   the larger magnitude: averages that mirror each other across a plane of
-   symmetry of the data differ only by rounding (up to 2^-39 of their size on
-   the seeded boxes, whose coordinates are rounded), and the extremum tests
-   below would otherwise take their branch from the order of that rounding */
-static double avg_diff(double a, double b) {
-    double d = a - b;
-    return fabs(d) <= ldexp(fmax(fabs(a), fabs(b)), -36) ? 0.0 : d;
+/* The extremum tests below compare the signs of two differences of averages
+   on either side of the zone, e = a_left - a0 and e' = a0 - a_right.  Averages
+   that mirror each other across a plane of symmetry of the data differ only by
+   rounding, and a test would take its branch from the order of that rounding.
+   A difference counts as zero (a tie) when it is at most 2^-20 of the other one
+   or at most 2^-48 of the larger average it is formed from. */
+#define CS_TIE_REL 20
+#define CS_TIE_ABS 48
+static double tie_diff(double d, double other, double a, double b) {
+    if (fabs(d) <= ldexp(fabs(other), -CS_TIE_REL)) return 0.0;
+    if (fabs(d) <= ldexp(fmax(fabs(a), fabs(b)), -CS_TIE_ABS)) return 0.0;
+    return d;
+}
+
+/* e * e' <= 0 with ties counted as zero */
+static int not_same_side(double al, double a0, double ar) {
+    double e1 = al - a0, e2 = a0 - ar;
+    double t1 = tie_diff(e1, e2, al, a0), t2 = tie_diff(e2, e1, a0, ar);
+    return t1 * t2 <= 0.0;
 }
 
 static void cs_zone(double amm, double am, double a0, double ap, double app, double* fm, double* fp) {
     double dm = *fm - a0, dp = *fp - a0;
-    if (dp * dm >= 0.0 || avg_diff(am, a0) * avg_diff(a0, ap) <= 0.0 ||
-        avg_diff(amm, a0) * avg_diff(a0, app) <= 0.0) {
+    if (dp * dm >= 0.0 || not_same_side(am, a0, ap) || not_same_side(amm, a0, app)) {
         double d2 = -2.0 * (6.0 * a0 - 3.0 * (*fm + *fp));
         double d2c = am - 2.0 * a0 + ap, d2l = amm - 2.0 * am + a0, d2r = a0 - 2.0 * ap + app;
         double lim = 0.0;

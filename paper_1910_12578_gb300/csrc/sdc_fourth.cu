@@ -15,8 +15,8 @@
 // averages is replaced by their mean less a sixth of a limited second
 // difference (Colella & Sekora's face limiter); then every zone limits its two
 // face values, by a limited curvature at an extremum (of the face values about
-// the average, or of the averages at distance one or two, differences within
-// 2^-36 of the averages counting as ties) and by the PPM
+// the average, or of the averages at distance one or two, with differences of
+// rounding size counting as ties) and by the PPM
 // overshoot bounds elsewhere; the limited mass fractions are renormalised; the
 // two sides of a face then give its flux by HLLC, at the face centres and from
 // the face averages alike.  The averaged source is R(U_c) + L R(U_c)/24; the implicit update is solved at
@@ -215,26 +215,29 @@ __device__ __forceinline__ double cs_face_limit(double am, double a0, double ap,
     return fma(d2, -1.0 / 6.0, 0.5 * (a0 + ap));
 }
 
-// d = a - b, and the same difference as the extremum tests see it: zero where
-// it is at most 2^-36 of the larger magnitude (averages mirrored across a plane
-// of symmetry of the data differ only by rounding, and the tests would take
-// their branch from its order).  2^-36 |x| is the bit pattern of x less 36 in
-// the exponent field (mag2 units of 2^53); below |x| = 2^-986 only zero counts.
-__device__ __forceinline__ double avg_diff(double a, double b, double& d) {
-    constexpr unsigned long long E36 = 36ull << 53;
-    d = a - b;
-    const unsigned long long M = max(mag2(a), mag2(b));
-    const unsigned long long thr = M > E36 ? M - E36 : 0ull;
-    return mag2(d) <= thr ? 0.0 : d;
+// The extremum tests compare the signs of two differences of averages on
+// either side of the zone, e = a_left - a0 and e' = a0 - a_right.  Averages
+// mirrored across a plane of symmetry of the data differ only by rounding, and
+// a test would take its branch from the order of that rounding: a difference
+// counts as zero (a tie) when it is at most 2^-20 of the other one or at most
+// 2^-48 of the larger average it is formed from.  2^-k |x| is the bit pattern
+// of x less k in the exponent field (mag2 units of 2^53); where that leaves the
+// normal range only an exact zero counts.
+__device__ __forceinline__ double tie_diff(double d, double other, double a, double b) {
+    constexpr unsigned long long R20 = 20ull << 53, A48 = 48ull << 53;
+    const unsigned long long md = mag2(d), mo = mag2(other), M = max(mag2(a), mag2(b));
+    if (md <= (mo > R20 ? mo - R20 : 0ull)) return 0.0;
+    if (md <= (M > A48 ? M - A48 : 0ull)) return 0.0;
+    return d;
 }
 
 // zone limiter of zone a0 (neighbours amm .. app) with face values fm, fp and
 // their deviations dm = fm - a0, dp = fp - a0
 __device__ __forceinline__ void cs_zone(double amm, double am, double a0, double ap, double app, double dm,
                                         double dp, double& fm, double& fp) {
-    double e1, e2, e3, e4;  // am - a0, a0 - ap, amm - a0, a0 - app
-    const double t1 = avg_diff(am, a0, e1), t2 = avg_diff(a0, ap, e2);
-    const double t3 = avg_diff(amm, a0, e3), t4 = avg_diff(a0, app, e4);
+    const double e1 = am - a0, e2 = a0 - ap, e3 = amm - a0, e4 = a0 - app;
+    const double t1 = tie_diff(e1, e2, am, a0), t2 = tie_diff(e2, e1, a0, ap);
+    const double t3 = tie_diff(e3, e4, amm, a0), t4 = tie_diff(e4, e3, a0, app);
     if (!opposite(dp, dm) || !same2(t1, t2) || !same2(t3, t4)) {
         // extremum: scale both deviations by the limited curvature over the
         // parabola's; the centred second differences from the differences above

@@ -150,14 +150,14 @@ def config_1d(nx: int = 64, seed: int = 0) -> tuple:
 
 def hot_spot_state(P: Problem, amp: float, u0: float = 0.1, T0: float = 1.0) -> np.ndarray:
     """3D box [0, n*dx]^3: rho = 1, u = (u0, 0, 0), X_0 = 1, T = T0 (1 + (amp-1)
-    exp(-|x - x_c|^2 / 0.01)) in coordinates scaled by the box length."""
+    exp(-|x - x_c|^2 / 0.01)) in coordinates scaled by the box length.  The
+    offsets from the centre, (i + 1/2 - n/2) / n, are exact negatives of each
+    other across the box's mid-planes, so the state is mirror-symmetric to the
+    last bit (with n a power of two these are the centres less 1/2 exactly)."""
     n0, n1, n2 = P.n
-    L = [P.n[d] * P.dx[d] for d in range(3)]
-    x = _centres(n0, P.dx[0]) / L[0]
-    y = _centres(n1, P.dx[1]) / L[1]
-    z = _centres(n2, P.dx[2]) / L[2]
+    x, y, z = ((np.arange(m) + 0.5 - 0.5 * m) / m for m in (n0, n1, n2))
     Z, Y, Xc = np.meshgrid(z, y, x, indexing="ij")
-    r2 = (Xc - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2
+    r2 = Xc ** 2 + Y ** 2 + Z ** 2
     T = T0 * (1.0 + (amp - 1.0) * np.exp(-r2 / 0.01))
     rho = np.ones_like(T)
     vel = [u0 * np.ones_like(T), np.zeros_like(T), np.zeros_like(T)]

@@ -493,9 +493,11 @@ def test_batched_boxes_match_per_box_oracle(torch_cuda):
         off += nz
 
 
-def test_tiny_boxes_match_per_box_oracle(torch_cuda):
+@pytest.mark.parametrize("space_order", [2, 4])
+def test_tiny_boxes_match_per_box_oracle(torch_cuda, space_order):
     """Boxes narrower than the tile and than the 2-zone halo (edges 1, 2, 3, 5;
-    the periodic halo wraps onto the box itself), with seeded flow in every
+    the periodic halo wraps onto the box itself, several times for the limited
+    fourth-order stencil's two zones each side), with seeded flow in every
     direction, in one context: each box equals the oracle run on it alone over
     two steps."""
     torch = torch_cuda
@@ -505,7 +507,8 @@ def test_tiny_boxes_match_per_box_oracle(torch_cuda):
     Ps, Us = [], []
     for n in [(1, 2, 3), (3, 3, 3), (5, 1, 2), (2, 5, 1), (1, 1, 1)]:
         h = 1.0 / 64
-        P = W.Problem(dim=3, n=n, dx=(h, h, h), gamma=5 / 3, net=net, n_nodes=3, n_iters=2)
+        P = W.Problem(dim=3, n=n, dx=(h, h, h), gamma=5 / 3, net=net, n_nodes=3, n_iters=2,
+                      space_order=space_order)
         shp = (n[2], n[1], n[0])
         rho = 1.0 + 0.1 * rng.random(shp)
         vel = [0.2 * (rng.random(shp) - 0.5) for _ in range(3)]

@@ -263,10 +263,13 @@ def test_limited_fourth_order_sod_is_non_oscillatory_and_converges():
 def test_limited_fourth_order_well_conditioned_on_mirrored_data(ragged):
     """A hot spot centred on a face leaves averages that mirror each other and
     differ only by rounding; the zone limiter's extremum tests count such
-    differences (up to 2^-36 of the averages) as ties.  Pinned: one-ulp changes
-    of the input move two limited fourth-order steps by at most 2e-13 of each
-    field (without the dead zone they moved the 16^3 box by 3.6e-6), which is
-    what lets results computed with another rounding order agree to 1e-12."""
+    differences (up to 2^-20 of the difference on the zone's other side, or
+    2^-48 of the averages) as ties.  Pinned: one-ulp changes of the input move
+    two limited fourth-order steps by at most 2e-13 of each field (without the
+    tie rule they moved the 16^3 box by 3.6e-6; with a rule relative to the
+    averages alone, by 1e-12 to 1e-10 on these boxes or on 64^3, depending on
+    its threshold), which is what lets results computed with another rounding
+    order agree to 1e-12."""
     P, U = W.config_box(n=16, nspec=7, seed=0 if not ragged else 1, T0=0.5)
     if ragged:
         P.n, P.dx = (24, 16, 12), (1 / 24, 1 / 16, 1 / 12)
