@@ -32,7 +32,6 @@ namespace sdcd {
 namespace {
 
 constexpr int F_BLOCK = 256;
-constexpr int F_MAXV = 2 + 3 + SDCD_MAXS;
 
 inline unsigned fgrid(long long n) { return (unsigned)((n + F_BLOCK - 1) / F_BLOCK); }
 
@@ -65,39 +64,75 @@ __device__ __forceinline__ ZoneCoord zone_coord(const BoxDev* boxes, int nbox, l
     return q;
 }
 
-// index of the zone o steps from q along d (periodic in the box)
-__device__ __forceinline__ long long neighbour(const ZoneCoord& q, int d, int o) {
-    int c[3] = {q.c[0], q.c[1], q.c[2]};
-    c[d] = ((c[d] + o) % q.n[d] + q.n[d]) % q.n[d];
-    return q.off + (long long)(c[0] + q.n[0] * (c[1] + q.n[1] * c[2]));
+// zone indices o steps from z along d, periodic in the box (|o| <= 2, any n >= 1)
+struct Line {
+    long long z, stride;
+    int c, n;
+    __device__ __forceinline__ long long at(int o) const {
+        int cc = c + o;
+        while (cc < 0) cc += n;
+        while (cc >= n) cc -= n;
+        return z + (long long)(cc - c) * stride;
+    }
+};
+
+// element d of a 3-array by selects (a runtime index would put the array on the stack)
+__device__ __forceinline__ int sel3(const int* a, int d) { return d == 0 ? a[0] : (d == 1 ? a[1] : a[2]); }
+
+__device__ __forceinline__ Line line_of(const ZoneCoord& q, long long z, int d) {
+    Line l;
+    l.z = z;
+    l.c = sel3(q.c, d);
+    l.n = sel3(q.n, d);
+    l.stride = d == 0 ? 1 : (d == 1 ? (long long)q.n[0] : (long long)q.n[0] * q.n[1]);
+    return l;
 }
 
 // out = a + coef * sum_{d < dim, d != skip} (b(z+e_d) - 2 b(z) + b(z-e_d)), nf fields,
 // formed as a + coef (sum of the neighbour pairs - 2 n_d b(z)): per field one add
-// per neighbour, then two FMAs (the FP64 pipe is the bound)
+// per neighbour, then two FMAs (the FP64 pipe is the bound).  The neighbour
+// indices are scalars (an index array over a runtime dimension count would sit
+// on the stack).
 __global__ void lap_combine_kernel(int dim, int nf, long long N, const BoxDev* __restrict__ boxes, int nbox,
                                    const double* __restrict__ a, const double* __restrict__ b, double coef, int skip,
                                    double* __restrict__ out) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= N) return;
     const ZoneCoord q = zone_coord(boxes, nbox, z);
-    long long zp[3] = {z, z, z}, zm[3] = {z, z, z};
-    int nd = 0;
-    for (int d = 0; d < dim; d++) {
-        zp[d] = neighbour(q, d, 1);
-        zm[d] = neighbour(q, d, -1);
-        if (d != skip) nd++;
+    const bool u0 = 0 < dim && skip != 0, u1 = 1 < dim && skip != 1, u2 = 2 < dim && skip != 2;
+    long long p0 = z, m0 = z, p1 = z, m1 = z, p2 = z, m2 = z;
+    if (u0) {
+        const Line l = line_of(q, z, 0);
+        p0 = l.at(1);
+        m0 = l.at(-1);
     }
-    const double c2 = -2.0 * nd;
+    if (u1) {
+        const Line l = line_of(q, z, 1);
+        p1 = l.at(1);
+        m1 = l.at(-1);
+    }
+    if (u2) {
+        const Line l = line_of(q, z, 2);
+        p2 = l.at(1);
+        m2 = l.at(-1);
+    }
+    const double c2 = -2.0 * (int(u0) + int(u1) + int(u2));
     for (int f = 0; f < nf; f++) {
         const long long o = (long long)f * N;
         double sn = 0.0;
         bool first = true;
-        for (int d = 0; d < dim; d++) {
-            if (d == skip) continue;
-            const double pair = b[o + zp[d]] + b[o + zm[d]];
+        if (u0) {
+            sn = b[o + p0] + b[o + m0];
+            first = false;
+        }
+        if (u1) {
+            const double pair = b[o + p1] + b[o + m1];
             sn = first ? pair : sn + pair;
             first = false;
+        }
+        if (u2) {
+            const double pair = b[o + p2] + b[o + m2];
+            sn = first ? pair : sn + pair;
         }
         out[o + z] = fma(coef, fma(c2, b[o + z], sn), a[o + z]);
     }
@@ -126,67 +161,50 @@ __global__ void face_avg_kernel(int dir, int nf, long long N, const BoxDev* __re
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= N) return;
     const ZoneCoord q = zone_coord(boxes, nbox, z);
-    const long long zm = neighbour(q, dir, -1), zp = neighbour(q, dir, 1), zpp = neighbour(q, dir, 2);
+    const Line l = line_of(q, z, dir);
+    const long long zm = l.at(-1), zp = l.at(1), zpp = l.at(2);
     for (int f = 0; f < nf; f++) {
         const long long o = (long long)f * N;
         Wf[o + z] = 7.0 / 12.0 * (Wa[o + z] + Wa[o + zp]) - 1.0 / 12.0 * (Wa[o + zm] + Wa[o + zpp]);
     }
 }
 
-// physical Euler flux along dir of the primitive state q
-__device__ __forceinline__ void euler_flux(int dim, int nspec, double igm1, int dir, const double* q, double* F) {
-    const double rho = q[0], un = q[1 + dir], p = q[1 + dim];
-    double k2 = 0.0;
-    for (int d = 0; d < dim; d++) k2 = fma(q[1 + d], q[1 + d], k2);
-    const double E = fma(p, igm1, 0.5 * rho * k2);
-    F[0] = rho * un;
-    for (int d = 0; d < dim; d++) F[1 + d] = rho * un * q[1 + d] + (d == dir ? p : 0.0);
-    F[1 + dim] = (E + p) * un;
-    for (int s = 0; s < nspec; s++) F[2 + dim + s] = rho * un * q[2 + dim + s];
-}
-
-// Fc = F(Wfc) (face centres), F2 = F(Wf) (from the face averages)
-__global__ void face_flux_kernel(int dim, int nspec, double igm1, int dir, long long N,
-                                 const double* __restrict__ Wfc, const double* __restrict__ Wf,
-                                 double* __restrict__ Fc, double* __restrict__ F2) {
+// Fc = F(Wfc) (face centres), F2 = F(Wf) (from the face averages): the physical
+// Euler flux along dir, hydrodynamic fields in registers, species streamed
+// (mass flux times X)
+template <int DIM>
+__global__ void face_flux_kernel(int nspec, double igm1, int dir, long long N, const double* __restrict__ Wfc,
+                                 const double* __restrict__ Wf, double* __restrict__ Fc, double* __restrict__ F2) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= N) return;
-    const int nv = 2 + dim + nspec;
-    double q[F_MAXV], F[F_MAXV];
-    for (int f = 0; f < nv; f++) q[f] = Wfc[(long long)f * N + z];
-    euler_flux(dim, nspec, igm1, dir, q, F);
-    for (int f = 0; f < nv; f++) Fc[(long long)f * N + z] = F[f];
-    for (int f = 0; f < nv; f++) q[f] = Wf[(long long)f * N + z];
-    euler_flux(dim, nspec, igm1, dir, q, F);
-    for (int f = 0; f < nv; f++) F2[(long long)f * N + z] = F[f];
+    constexpr int NH = 2 + DIM;
+    const int nv = NH + nspec;
+#pragma unroll
+    for (int side = 0; side < 2; side++) {
+        const double* W = side ? Wf : Wfc;
+        double* F = side ? F2 : Fc;
+        double qv[NH];
+#pragma unroll
+        for (int f = 0; f < NH; f++) qv[f] = W[(long long)f * N + z];
+        const double rho = qv[0], p = qv[1 + DIM];
+        double un = qv[1];
+#pragma unroll
+        for (int d = 1; d < DIM; d++)
+            if (d == dir) un = qv[1 + d];
+        double k2 = 0.0;
+#pragma unroll
+        for (int d = 0; d < DIM; d++) k2 = fma(qv[1 + d], qv[1 + d], k2);
+        const double E = fma(p, igm1, 0.5 * rho * k2);
+        F[z] = rho * un;
+#pragma unroll
+        for (int d = 0; d < DIM; d++) F[(long long)(1 + d) * N + z] = rho * un * qv[1 + d] + (d == dir ? p : 0.0);
+        F[(long long)(1 + DIM) * N + z] = (E + p) * un;
+        for (int f = NH; f < nv; f++) F[(long long)f * N + z] = rho * un * W[(long long)f * N + z];
+    }
 }
 
 // ---- limited form
 constexpr double CS_C = 1.25;  // bound of the limited curvature over its neighbours'
-
-// zone indices o steps from z along d, periodic in the box (|o| <= 2, any n >= 1)
-struct Line {
-    long long z, stride;
-    int c, n;
-    __device__ __forceinline__ long long at(int o) const {
-        int cc = c + o;
-        while (cc < 0) cc += n;
-        while (cc >= n) cc -= n;
-        return z + (long long)(cc - c) * stride;
-    }
-};
-
-// element d of a 3-array by selects (a runtime index would put the array on the stack)
-__device__ __forceinline__ int sel3(const int* a, int d) { return d == 0 ? a[0] : (d == 1 ? a[1] : a[2]); }
-
-__device__ __forceinline__ Line line_of(const ZoneCoord& q, long long z, int d) {
-    Line l;
-    l.z = z;
-    l.c = sel3(q.c, d);
-    l.n = sel3(q.n, d);
-    l.stride = d == 0 ? 1 : (d == 1 ? (long long)q.n[0] : (long long)q.n[0] * q.n[1]);
-    return l;
-}
 
 // Sign tests on bit patterns (integer pipe; FP64 compares and products issue on
 // the narrow FP64 pipe).  They equal the plain products' tests except when a
@@ -440,6 +458,16 @@ cudaError_t lap(int dim, int nf, long long N, const BoxDev* boxes, int nbox, con
     return cudaGetLastError();
 }
 
+cudaError_t launch_face_flux(const NetParams& P, int dim, int dir, long long N, const FourthWs& w, cudaStream_t st) {
+    const double gi = 1.0 / P.gm1;
+    switch (dim) {
+        case 1: face_flux_kernel<1><<<fgrid(N), F_BLOCK, 0, st>>>(P.nspec, gi, dir, N, w.Wfc, w.Wf, w.Fc, w.F2); break;
+        case 2: face_flux_kernel<2><<<fgrid(N), F_BLOCK, 0, st>>>(P.nspec, gi, dir, N, w.Wfc, w.Wf, w.Fc, w.F2); break;
+        default: face_flux_kernel<3><<<fgrid(N), F_BLOCK, 0, st>>>(P.nspec, gi, dir, N, w.Wfc, w.Wf, w.Fc, w.F2); break;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_face_hllc4(const NetParams& P, int dim, int dir, long long N, const BoxDev* boxes, int nbox,
                               const FourthWs& w, cudaStream_t st) {
     const double g = P.gamma, gi = 1.0 / P.gm1;
@@ -483,9 +511,7 @@ cudaError_t launch_advective4(const NetParams& P, int dim, int limiter, long lon
             face_avg_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dir, nv, N, boxes, nbox, w.Wa, w.Wf);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             if ((e = lap(dim, nv, N, boxes, nbox, w.Wf, w.Wf, -1.0 / 24.0, dir, w.Wfc, st)) != cudaSuccess) return e;
-            face_flux_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dim, P.nspec, 1.0 / P.gm1, dir, N, w.Wfc, w.Wf, w.Fc,
-                                                           w.F2);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if ((e = launch_face_flux(P, dim, dir, N, w, st)) != cudaSuccess) return e;
         }
         // face-average fluxes once per face (fused into the divergence, each face's
         // map would be formed twice on the FP64 pipe), then the divergence
