@@ -88,71 +88,125 @@ __device__ __forceinline__ Line line_of(const ZoneCoord& q, long long z, int d) 
     return l;
 }
 
-// out = a + coef * sum_{d < dim, d != skip} (b(z+e_d) - 2 b(z) + b(z-e_d)), nf fields,
-// formed as a + coef (sum of the neighbour pairs - 2 n_d b(z)): per field one add
-// per neighbour, then two FMAs (the FP64 pipe is the bound).  The neighbour
-// indices are scalars (an index array over a runtime dimension count would sit
-// on the stack).
+// neighbours of z along the dimensions d < dim other than skip (skip = -1: all),
+// as scalars (an index array over a runtime dimension count would sit on the
+// stack), and -2 n_d
+struct LapNb {
+    long long p0, m0, p1, m1, p2, m2;
+    bool u0, u1, u2;
+    double c2;
+};
+
+__device__ __forceinline__ LapNb lap_nb(const ZoneCoord& q, long long z, int dim, int skip) {
+    LapNb nb;
+    nb.u0 = 0 < dim && skip != 0;
+    nb.u1 = 1 < dim && skip != 1;
+    nb.u2 = 2 < dim && skip != 2;
+    nb.p0 = nb.m0 = nb.p1 = nb.m1 = nb.p2 = nb.m2 = z;
+    if (nb.u0) {
+        const Line l = line_of(q, z, 0);
+        nb.p0 = l.at(1);
+        nb.m0 = l.at(-1);
+    }
+    if (nb.u1) {
+        const Line l = line_of(q, z, 1);
+        nb.p1 = l.at(1);
+        nb.m1 = l.at(-1);
+    }
+    if (nb.u2) {
+        const Line l = line_of(q, z, 2);
+        nb.p2 = l.at(1);
+        nb.m2 = l.at(-1);
+    }
+    nb.c2 = -2.0 * (int(nb.u0) + int(nb.u1) + int(nb.u2));
+    return nb;
+}
+
+// a + coef * sum_d (b(z+e_d) - 2 b(z) + b(z-e_d)) for one field (offset o), formed
+// as a + coef (sum of the neighbour pairs - 2 n_d b(z)): one add per neighbour,
+// then two FMAs (the FP64 pipe is the bound)
+__device__ __forceinline__ double lap_at(const double* __restrict__ b, long long o, long long z, const LapNb& nb,
+                                         double a, double coef) {
+    double sn = 0.0;
+    bool first = true;
+    if (nb.u0) {
+        sn = b[o + nb.p0] + b[o + nb.m0];
+        first = false;
+    }
+    if (nb.u1) {
+        const double pair = b[o + nb.p1] + b[o + nb.m1];
+        sn = first ? pair : sn + pair;
+        first = false;
+    }
+    if (nb.u2) {
+        const double pair = b[o + nb.p2] + b[o + nb.m2];
+        sn = first ? pair : sn + pair;
+    }
+    return fma(coef, fma(nb.c2, b[o + z], sn), a);
+}
+
+// out = a + coef * sum_{d < dim, d != skip} (b(z+e_d) - 2 b(z) + b(z-e_d)), nf fields
 __global__ void lap_combine_kernel(int dim, int nf, long long N, const BoxDev* __restrict__ boxes, int nbox,
                                    const double* __restrict__ a, const double* __restrict__ b, double coef, int skip,
                                    double* __restrict__ out) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= N) return;
-    const ZoneCoord q = zone_coord(boxes, nbox, z);
-    const bool u0 = 0 < dim && skip != 0, u1 = 1 < dim && skip != 1, u2 = 2 < dim && skip != 2;
-    long long p0 = z, m0 = z, p1 = z, m1 = z, p2 = z, m2 = z;
-    if (u0) {
-        const Line l = line_of(q, z, 0);
-        p0 = l.at(1);
-        m0 = l.at(-1);
-    }
-    if (u1) {
-        const Line l = line_of(q, z, 1);
-        p1 = l.at(1);
-        m1 = l.at(-1);
-    }
-    if (u2) {
-        const Line l = line_of(q, z, 2);
-        p2 = l.at(1);
-        m2 = l.at(-1);
-    }
-    const double c2 = -2.0 * (int(u0) + int(u1) + int(u2));
+    const LapNb nb = lap_nb(zone_coord(boxes, nbox, z), z, dim, skip);
     for (int f = 0; f < nf; f++) {
         const long long o = (long long)f * N;
-        double sn = 0.0;
-        bool first = true;
-        if (u0) {
-            sn = b[o + p0] + b[o + m0];
-            first = false;
-        }
-        if (u1) {
-            const double pair = b[o + p1] + b[o + m1];
-            sn = first ? pair : sn + pair;
-            first = false;
-        }
-        if (u2) {
-            const double pair = b[o + p2] + b[o + m2];
-            sn = first ? pair : sn + pair;
-        }
-        out[o + z] = fma(coef, fma(c2, b[o + z], sn), a[o + z]);
+        out[o + z] = lap_at(b, o, z, nb, a[o + z], coef);
     }
 }
 
-// primitives (rho, u, p, X) of the conserved fields, field-major
-__global__ void prim_kernel(int dim, int nspec, double gm1, long long N, const double* __restrict__ U,
-                            double* __restrict__ W) {
+// out1 = b1 + coef L b1 and out2 = b2 + coef L b2 (two maps over one index set)
+__global__ void lap_pair_kernel(int dim, int nf, long long N, const BoxDev* __restrict__ boxes, int nbox,
+                                const double* __restrict__ b1, double* __restrict__ out1,
+                                const double* __restrict__ b2, double* __restrict__ out2, double coef) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= N) return;
-    const double rho = U[z], ir = rcp_nr(rho);  // one reciprocal, then products (FP64 pipe)
-    W[z] = rho;
-    double ke = 0.0;
-    for (int d = 0; d < dim; d++) {
-        const double m = U[(1 + d) * N + z], u = m * ir;
-        W[(1 + d) * N + z] = u;
-        ke += 0.5 * m * u;
+    const LapNb nb = lap_nb(zone_coord(boxes, nbox, z), z, dim, -1);
+    for (int f = 0; f < nf; f++) {
+        const long long o = (long long)f * N;
+        out1[o + z] = lap_at(b1, o, z, nb, b1[o + z], coef);
+        out2[o + z] = lap_at(b2, o, z, nb, b2[o + z], coef);
     }
-    W[(1 + dim) * N + z] = gm1 * (U[(1 + dim) * N + z] - ke);
-    for (int s = 0; s < nspec; s++) W[(2 + dim + s) * N + z] = U[(2 + dim + s) * N + z] * ir;
+}
+
+// Wc = W(U_c) with U_c = U - L U/24 formed field by field as it is needed, and
+// W2 = W(U) = (rho, m/rho, (gamma-1)(E - m.u/2), rho X/rho): the centre map and
+// both primitive conversions in one pass, one reciprocal of rho each
+__global__ void prims4_kernel(int dim, int nspec, double gm1, long long N, const BoxDev* __restrict__ boxes, int nbox,
+                              const double* __restrict__ U, double* __restrict__ Wc, double* __restrict__ W2) {
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= N) return;
+    const LapNb nb = lap_nb(zone_coord(boxes, nbox, z), z, dim, -1);
+    constexpr double c24 = -1.0 / 24.0;
+    const double rho = U[z], ir = rcp_nr(rho);
+    const double rc = lap_at(U, 0, z, nb, rho, c24), irc = rcp_nr(rc);
+    W2[z] = rho;
+    Wc[z] = rc;
+    double ke = 0.0, kec = 0.0;
+    for (int d = 0; d < dim; d++) {
+        const long long o = (long long)(1 + d) * N;
+        const double m = U[o + z], u = m * ir;
+        const double mc = lap_at(U, o, z, nb, m, c24), uc = mc * irc;
+        W2[o + z] = u;
+        Wc[o + z] = uc;
+        ke += 0.5 * m * u;
+        kec += 0.5 * mc * uc;
+    }
+    {
+        const long long o = (long long)(1 + dim) * N;
+        const double E = U[o + z];
+        W2[o + z] = gm1 * (E - ke);
+        Wc[o + z] = gm1 * (lap_at(U, o, z, nb, E, c24) - kec);
+    }
+    for (int s = 0; s < nspec; s++) {
+        const long long o = (long long)(2 + dim + s) * N;
+        const double v = U[o + z];
+        W2[o + z] = v * ir;
+        Wc[o + z] = lap_at(U, o, z, nb, v, c24) * irc;
+    }
 }
 
 // face averages of the primitives, the face between z and its +1 neighbour along dir
@@ -436,18 +490,25 @@ __global__ void div_kernel(int dir, int nf, long long N, const BoxDev* __restric
     }
 }
 
-// <U> = <rhs> + dt_m <R> on the reactive fields, <rhs> on mass and momenta
-__global__ void update4_kernel(int nvar, int dim, long long N, const double* __restrict__ rhs,
-                               const double* __restrict__ R, const double* __restrict__ dt_dev, double dt_frac,
-                               double dtm_host, double* __restrict__ U) {
-    // one thread per zone, every field (no 64-bit division per element)
+// <R> = R_c + L R_c/24 (written), then <U> = <rhs> + dt_m <R> on the reactive
+// fields and <rhs> on mass and momenta, in one pass
+__global__ void lap_update4_kernel(int nvar, int dim, long long N, const BoxDev* __restrict__ boxes, int nbox,
+                                   const double* __restrict__ Rc, const double* __restrict__ rhs,
+                                   const double* __restrict__ dt_dev, double dt_frac, double dtm_host,
+                                   double* __restrict__ R, double* __restrict__ U) {
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= N) return;
+    const LapNb nb = lap_nb(zone_coord(boxes, nbox, z), z, dim, -1);
     const double dtm = dt_dev ? (*dt_dev) * dt_frac : dtm_host;
     for (int f = 0; f < nvar; f++) {
         const long long i = (long long)f * N + z;
         double v = rhs[i];
-        if (f >= 1 + dim) v += dtm * R[(long long)(f - 1 - dim) * N + z];
+        if (f >= 1 + dim) {
+            const long long o = (long long)(f - 1 - dim) * N;
+            const double r = lap_at(Rc, o, z, nb, Rc[o + z], 1.0 / 24.0);
+            R[o + z] = r;
+            v += dtm * r;
+        }
         U[i] = v;
     }
 }
@@ -494,10 +555,7 @@ cudaError_t launch_advective4(const NetParams& P, int dim, int limiter, long lon
                               const double* U, double* A, const FourthWs& w, cudaStream_t st) {
     const int nv = 2 + dim + P.nspec;
     cudaError_t e;
-    if ((e = lap(dim, nv, N, boxes, nbox, U, U, -1.0 / 24.0, -1, w.Uc, st)) != cudaSuccess) return e;
-    prim_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dim, P.nspec, P.gm1, N, U, w.W2);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    prim_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dim, P.nspec, P.gm1, N, w.Uc, w.Wc);
+    prims4_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dim, P.nspec, P.gm1, N, boxes, nbox, U, w.Wc, w.W2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = lap(dim, nv, N, boxes, nbox, w.Wc, w.W2, 1.0 / 24.0, -1, w.Wa, st)) != cudaSuccess) return e;
     for (int dir = 0; dir < dim; dir++) {
@@ -538,14 +596,14 @@ cudaError_t launch_newton4(const NetParams& P, const NewtonCfg& cfg, int prec, i
                            unsigned long long* queue, int persistent_blocks) {
     const int nv = 2 + dim + P.nspec, n = P.nspec + 1;
     cudaError_t e;
-    if ((e = lap(dim, nv, N, boxes, nbox, rhs, rhs, -1.0 / 24.0, -1, w.rc, st)) != cudaSuccess) return e;
-    if ((e = lap(dim, nv, N, boxes, nbox, guess, guess, -1.0 / 24.0, -1, w.gc, st)) != cudaSuccess) return e;
+    lap_pair_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dim, nv, N, boxes, nbox, rhs, w.rc, guess, w.gc, -1.0 / 24.0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_newton(P, cfg, prec, N, dim, w.rc, w.gc, w.gc, w.Rc, dt_dev, dt_frac, dtm_host, zone_status,
                            zone_iters, stats, st, variant, queue, persistent_blocks)) != cudaSuccess)
         return e;
-    if ((e = lap(dim, n, N, boxes, nbox, w.Rc, w.Rc, 1.0 / 24.0, -1, Rout, st)) != cudaSuccess) return e;
-    update4_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(nv, dim, N, rhs, Rout, dt_dev, dt_frac, dtm_host,
-                                                                  Uout);
+    (void)n;
+    lap_update4_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(nv, dim, N, boxes, nbox, w.Rc, rhs, dt_dev, dt_frac, dtm_host,
+                                                     Rout, Uout);
     return cudaGetLastError();
 }
 

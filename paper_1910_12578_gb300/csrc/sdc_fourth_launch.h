@@ -24,9 +24,9 @@ struct FourthWs {
 inline long long fourth_ws_doubles_per_zone(int nvar, int nw) { return 11LL * nvar + nw; }
 
 // kernel launches of one fourth-order advective term
-inline int fourth_advective_launches(int dim, int limiter) { return 4 + (limiter ? 4 : 5) * dim; }
-// kernel launches of one fourth-order implicit update (maps, Newton, map, update)
-constexpr int FOURTH_NEWTON_LAUNCHES = 5;
+inline int fourth_advective_launches(int dim, int limiter) { return 2 + (limiter ? 4 : 5) * dim; }
+// kernel launches of one fourth-order implicit update (both maps, Newton, map and update)
+constexpr int FOURTH_NEWTON_LAUNCHES = 3;
 constexpr int FOURTH_SOURCE_LAUNCHES = 3;
 
 // A = fourth-order advective term of the averages U (limiter: 0 smooth form, 1 limited form)
