@@ -20,9 +20,6 @@ struct FourthWs {
     double* Rc = nullptr;                 // zone-centre source [nspec + 1][N]
 };
 
-// doubles of workspace per zone
-inline long long fourth_ws_doubles_per_zone(int nvar, int nw) { return 11LL * nvar + nw; }
-
 // kernel launches of one fourth-order advective term
 inline int fourth_advective_launches(int dim, int limiter) { return 2 + (limiter ? 4 : 5) * dim; }
 // kernel launches of one fourth-order implicit update (both maps, Newton, map and update)
