@@ -35,6 +35,13 @@ struct ZoneEval {
 // the factor f of dk_j/dT = nu_j k_j f are formed (the matrix takes nu_j from
 // its coefficients); otherwise k_j and dk_j.  Returns false when T is not
 // positive and finite.
+// T > 0 and finite, on the bit pattern (integer pipe): a positive sign with a
+// nonzero pattern and an exponent field below 0x7ff (nan and inf excluded)
+__device__ __forceinline__ bool positive_finite(double T) {
+    const long long b = dbits(T);
+    return b > 0 && (b >> 52) < 0x7ff;
+}
+
 template <int NS, int TOPO>
 __device__ __forceinline__ bool eval_state(const NetParams& P, double rho, double inv_rho, double ke,
                                            const double* ym, const double* ak, const double* w, const double* rw,
@@ -43,15 +50,19 @@ __device__ __forceinline__ bool eval_state(const NetParams& P, double rho, doubl
     constexpr int N = NS + 1;
     constexpr int NR = NS - 1;
     const double T = P.gm1 * (w[0] - ke) * inv_rho;
-    if (!(T > 0.0 && T < INFINITY)) return false;
+    if (!positive_finite(T)) return false;
     if constexpr (TOPO == TOPO_CHAIN) rate_consts_k<NR>(P, ak, T, k, dfac);
     else rate_consts<NR>(P, rho, T, k, dk);
 #pragma unroll
     for (int i = 0; i < NS; i++) Y[i] = w[1 + i] * ym[i];
-    double R[N];
-    sources<NS, TOPO>(P, rho, k, Y, R);
+    // G = w - dt_m R(w) - rw with R(rho E) = rho RE and R(rho X_i) = rho mass_i S_i,
+    // formed as (w - rw) - (dt_m rho) (mass_i S_i): one product fewer per row
+    double S[NS], RE;
+    source_sums<NS, TOPO>(P, k, Y, S, RE);
+    const double dr = dtm * rho;
+    G[0] = fma(-dr, RE, w[0] - rw[0]);
 #pragma unroll
-    for (int r = 0; r < N; r++) G[r] = w[r] - dtm * R[r] - rw[r];
+    for (int i = 0; i < NS; i++) G[1 + i] = fma(-dr, P.mass[i] * S[i], w[1 + i] - rw[1 + i]);
     const double gE = G[0] * wE;
     double s = gE * gE;
 #pragma unroll
@@ -92,7 +103,7 @@ __device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, 
     // a start without a positive temperature is replaced by rhs
     {
         const double Tg = P.gm1 * (S.w[0] - S.ke) * S.inv_rho;
-        if (!(Tg > 0.0 && Tg < INFINITY)) {
+        if (!positive_finite(Tg)) {
 #pragma unroll
             for (int r = 0; r < N; r++) S.w[r] = S.rw[r];
         }
@@ -177,7 +188,7 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
         // the residual, its norm or the matrix's factor f.  Otherwise the full
         // evaluation below takes the decision.
         const double T = P.gm1 * (tr[0] - S.ke) * S.inv_rho;
-        if (T > 0.0 && T < INFINITY) {
+        if (positive_finite(T)) {
             double kf[NR], dkf[NR], Yf[NS], Rf[N];
             if constexpr (TOPO == TOPO_CHAIN) {
                 double dff;
