@@ -35,6 +35,13 @@ struct ZoneEval {
 // the factor f of dk_j/dT = nu_j k_j f are formed (the matrix takes nu_j from
 // its coefficients); otherwise k_j and dk_j.  Returns false when T is not
 // positive and finite.
+// The order of doubles as signed integers (negative patterns reversed), for
+// comparisons on the integer pipe; -0 sorts below +0 and a nan above +inf.
+__device__ __forceinline__ long long ordered_bits(double x) {
+    const long long b = dbits(x);
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffll);
+}
+
 // T > 0 and finite, on the bit pattern (integer pipe): a positive sign with a
 // nonzero pattern and an exponent field below 0x7ff (nan and inf excluded)
 __device__ __forceinline__ bool positive_finite(double T) {
@@ -177,9 +184,12 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     double tr[N];
 #pragma unroll
     for (int r = 0; r < N; r++) tr[r] = S.w[r] - (double)dv[r];
+    // admissible: every rho X_i at or above its floor (the floor is -inf or a
+    // nonzero value, so the two zeros never meet; a nan trial passes here and
+    // fails the evaluation below, as it fails this test in plain compares)
     bool ok = true;
 #pragma unroll
-    for (int i = 0; i < NS; i++) ok = ok && (tr[1 + i] >= S.lower[i]);
+    for (int i = 0; i < NS; i++) ok = ok && (ordered_bits(tr[1 + i]) >= ordered_bits(S.lower[i]));
     // (NS <= 7: with 13 species the extra live arrays of this path cost more in
     // register spills than the evaluation it saves)
     if (NS <= 7 && S.newton && ok && newton_step_small<NS, MT>(S, cfg, dv, tr)) {
