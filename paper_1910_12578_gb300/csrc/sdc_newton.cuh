@@ -75,7 +75,7 @@ __device__ __forceinline__ bool eval_state(const NetParams& P, double rho, doubl
 #pragma unroll
     for (int r = 1; r < N; r++) s = fma(G[r], G[r], s);
     phi = s;
-    return s < INFINITY;
+    return (dbits(s) >> 52) < 0x7ff;  // s >= 0: finite (nan and inf have the full exponent)
 }
 
 // Register-resident state of one zone's solve.
@@ -141,7 +141,9 @@ __device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, 
 template <int NS, typename MT>
 __device__ __forceinline__ bool newton_step_small(const ZoneState<NS>& S, const NewtonCfg& cfg, const MT* dv,
                                                   const double* tr) {
-    bool small = fabs((double)dv[0]) <= cfg.rtol * fabs(tr[0]);
+    // |dv_0| <= rtol |tr_0| on the bit patterns (rtol > 0: |rtol tr_0| is the rounded
+    // rtol |tr_0|; a nan step fails)
+    bool small = mag2((double)dv[0]) <= mag2(cfg.rtol * tr[0]);
     const double tol_x = cfg.rtol * S.rho;
     if constexpr (sizeof(MT) == 8) {
         // |dv_i| <= tol_x on the integer pipe (mag2 orders like |x|; a nan step fails)
@@ -230,7 +232,8 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     // an admissible Newton step that meets the stop test converges even if the
     // residual grew by round-off at the root
     const bool small = S.newton && ok && newton_step_small<NS, MT>(S, cfg, dv, tr);
-    if (S.newton && !small && (!ok || phit > S.phi)) {
+    // phit and phi are finite and non-negative where compared: ordered as integers
+    if (S.newton && !small && (!ok || ordered_bits(phit) > ordered_bits(S.phi))) {
         S.newton = false;
         S.h = PTC_H0;
     } else if (!ok) {
