@@ -7,10 +7,10 @@ for the exponential, 16 (1990) 378-400 for the logarithm):
   log2 x = e + log2(1/c_j) + log2(1 + r),  x = 2^e m, m in [1, 2),
            j = the top 7 fraction bits of m, c_j = 1/(1 + (j + 1/2)/128),
            r = m c_j - 1 (one FMA, |r| <= 1/255);
-  2^y    = 2^k 2^(i/64) 2^r,  64 y = 64 k + i + 64 r,  |r| <= 1/128.
+  2^y    = 2^k 2^(i/256) 2^r,  256 y = 256 k + i + 256 r,  |r| <= 1/512.
 The polynomials are the Taylor series, truncated where the remainder drops
 below 4e-17: log2(1 + r) = sum_{n=1..6} (-1)^(n+1) r^n / (n ln 2) and
-2^r - 1 = sum_{n=1..5} (r ln 2)^n / n!.  Every constant is computed here in
+2^r - 1 = sum_{n=1..4} (r ln 2)^n / n!.  Every constant is computed here in
 60-digit decimal arithmetic and rounded once to double; log2(1/c_j) is split
 into a double and the double nearest its remainder.
 
@@ -49,9 +49,9 @@ def main():
     out.append("")
     out.append("namespace sdcd {")
     out.append("")
-    out.append("// 2^(i/64), i = 0..63")
-    out.append("__device__ const double POW_EXP2_T[64] = {")
-    out.append(",\n".join("    " + d2h(exp2(Decimal(i) / 64)) for i in range(64)))
+    out.append("// 2^(i/256), i = 0..255")
+    out.append("__device__ const double POW_EXP2_T[256] = {")
+    out.append(",\n".join("    " + d2h(exp2(Decimal(i) / 256)) for i in range(256)))
     out.append("};")
     cs, his, los = [], [], []
     for j in range(128):
@@ -70,9 +70,9 @@ def main():
     out.append("// log2(1 + r) = r (a1 + r (a2 + ... + r a6)),  a_n = (-1)^(n+1) / (n ln 2)")
     for n in range(1, 7):
         out.append("constexpr double POW_LOG_A%d = %s;" % (n, d2h(Decimal((-1) ** (n + 1)) / (n * LN2))))
-    out.append("// 2^r - 1 = r (b1 + r (b2 + ... + r b5)),  b_n = (ln 2)^n / n!")
+    out.append("// 2^r - 1 = r (b1 + r (b2 + r (b3 + r b4))),  b_n = (ln 2)^n / n!")
     f = Decimal(1)
-    for n in range(1, 6):
+    for n in range(1, 5):
         f *= n
         out.append("constexpr double POW_EXP_B%d = %s;" % (n, d2h(LN2 ** n / f)))
     out.append("")

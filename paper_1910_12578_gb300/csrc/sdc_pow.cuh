@@ -1,7 +1,7 @@
 // sdc_pow.cuh -- T^nu = 2^(nu log2 T) for the power-law rate factors of the
 // reaction network, with a table-driven base-2 logarithm and exponential
 // (P. T. P. Tang, ACM TOMS 15 (1989) 144-157 and 16 (1990) 378-400): per call
-// about 13 FP64 instructions for log2 and 10 for exp2, against about 30 and 16
+// about 13 FP64 instructions for log2 and 9 for exp2, against about 30 and 16
 // for the library's log and exp, on a GPU whose FP64 pipe is the bottleneck.
 // Tables and coefficients: sdc_pow_tables.h, written by gen_pow_tables.py.
 //
@@ -45,19 +45,18 @@ __device__ __forceinline__ double exp2_tab(double y) {
     // |y| < 512 (and not nan) read from the exponent field, on the integer pipe;
     // beyond it the library (the scaling below keeps 2^y normal for |y| < 1021)
     if (((dbits(y) >> 52) & 0x7ff) >= 1023 + 9) return exp2(y);
-    const double SHIFT = 0x1.8p52;           // 64 y + SHIFT rounds 64 y to an integer in the low bits
-    const double t = fma(y, 64.0, SHIFT);
+    const double SHIFT = 0x1.8p52;           // 256 y + SHIFT rounds 256 y to an integer in the low bits
+    const double t = fma(y, 256.0, SHIFT);
     const double nf = t - SHIFT;
-    const double r = fma(nf, -0x1p-6, y);    // y - n/64 exactly, |r| <= 1/128
+    const double r = fma(nf, -0x1p-8, y);    // y - n/256 exactly, |r| <= 1/512
     const int n = (int)(dbits(t) & 0xffffffffll);
-    const int i = n & 63, k = n >> 6;
-    double p = fma(r, POW_EXP_B5, POW_EXP_B4);
-    p = fma(r, p, POW_EXP_B3);
+    const int i = n & 255, k = n >> 8;
+    double p = fma(r, POW_EXP_B4, POW_EXP_B3);
     p = fma(r, p, POW_EXP_B2);
     p = fma(r, p, POW_EXP_B1);
     p = r * p;
     const double ti = __ldg(POW_EXP2_T + i);
-    const double v = fma(ti, p, ti);         // 2^(i/64) 2^r, in [0.99, 2.02)
+    const double v = fma(ti, p, ti);         // 2^(i/256) 2^r, in [0.997, 2.003)
     return bitsd(dbits(v) + ((long long)k << 52));
 }
 
