@@ -44,6 +44,9 @@ L2_FLUSH_BYTES = 256 << 20
 NEWTON_TRAFFIC_PER_ZONE = {
     (7, 1, "fp64"): (44.363264e6 + 4.091392e6) / 262144,    # newton_queue_kernel<7, chain, double>; its writes
                                                               # stay in the 129 MB L2 at the 64^3 size
+    (13, 3, "fp64"): (70.107904e6 + 71.510016e6) / 262144,  # newton_queue_kernel<13, chain, double> on a 64^3
+                                                              # box of the 256^3 workload's network; its writes
+                                                              # already reach DRAM there, so 256^3 scales by zones
 }
 
 
