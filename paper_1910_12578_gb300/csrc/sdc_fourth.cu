@@ -456,7 +456,7 @@ __global__ void face_hllc4_kernel(int nspec, double g, double gm1_inv, int dir, 
 #pragma unroll
     for (int f = 0; f < NH; f++) Fc[(long long)f * N + z] = Fh[f];
     {
-        const double* X = Ss >= 0.0 ? WL : WR;
+        const double* X = nonneg(Ss) ? WL : WR;
         for (int f = NH; f < nv; f++) {
             const long long o = (long long)f * N;
             Fc[o + z] = Fh[0] * lap_t(X, o, z, t, X[o + z], c24);
@@ -471,7 +471,7 @@ __global__ void face_hllc4_kernel(int nspec, double g, double gm1_inv, int dir, 
     Ss = hllc_hydro<DIM>(g, gm1_inv, dir, qL, qR, Fh);
 #pragma unroll
     for (int f = 0; f < NH; f++) F2[(long long)f * N + z] = Fh[f];
-    const double* X = Ss >= 0.0 ? WL : WR;
+    const double* X = nonneg(Ss) ? WL : WR;
     for (int f = NH; f < nv; f++) F2[(long long)f * N + z] = Fh[0] * X[(long long)f * N + z];
 }
 

@@ -109,6 +109,19 @@ __device__ __forceinline__ int wrap(int g, int n) {
 // total energy is formed for the upwind side only, and the star state's energy
 // flux uses fac * e* = (E (S - u) + (S* - u)(S* rho (S - u) + p)) / (S - S*),
 // the same quantity as rho*_K E*_K with e* = E/rho + (S* - u)(S* + p/(rho (S - u))).
+// Sign tests and the wave-speed min / max on bit patterns (integer pipe; FP64
+// compares, min and max issue on the narrow FP64 pipe).  x >= 0 holds for +0
+// and -0 as in IEEE; the min / max order -0 below +0 (IEEE leaves the pick
+// between equal zeros open; the value is the same).
+__device__ __forceinline__ bool nonneg(double x) { return dbits(x) >= 0 || mag2(x) == 0ull; }
+__device__ __forceinline__ bool positive(double x) { return dbits(x) > 0; }
+__device__ __forceinline__ long long ord_bits(double x) {
+    const long long b = dbits(x);
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ double min_d(double a, double b) { return ord_bits(a) <= ord_bits(b) ? a : b; }
+__device__ __forceinline__ double max_d(double a, double b) { return ord_bits(a) >= ord_bits(b) ? a : b; }
+
 template <int DIM>
 __device__ __forceinline__ double hllc_hydro(double g, double gm1_inv, int dir, const double* qL, const double* qR,
                                              double* Fh) {
@@ -117,14 +130,14 @@ __device__ __forceinline__ double hllc_hydro(double g, double gm1_inv, int dir, 
     const double pL = qL[1 + DIM], pR = qR[1 + DIM];
     const double gpL = g * pL, gpR = g * pR;
     const double cL = gpL * rsqrt_nr(gpL * rL), cR = gpR * rsqrt_nr(gpR * rR);
-    const double SL = fmin(unL - cL, unR - cR);
-    const double SR = fmax(unL + cL, unR + cR);
+    const double SL = min_d(unL - cL, unR - cR);
+    const double SR = max_d(unL + cL, unR + cR);
     const double dL = SL - unL, dR = SR - unR;
     const double aL = rL * dL, aR = rR * dR;  // mass fluxes relative to the waves
     const double Ss = (pR - pL + unL * aL - unR * aR) * rcp_nr(aL - aR);
     // region: SL >= 0 -> F_L; else Ss >= 0 -> F*_L; else SR > 0 -> F*_R; else F_R
-    const bool left = (SL >= 0.0) || (Ss >= 0.0);
-    const bool star = (SL < 0.0) && (Ss >= 0.0 || SR > 0.0);
+    const bool left = nonneg(SL) || nonneg(Ss);
+    const bool star = !nonneg(SL) && (nonneg(Ss) || positive(SR));
     const double r = left ? rL : rR, un = left ? unL : unR, p = left ? pL : pR;
     const double S = left ? SL : SR, a = left ? aL : aR, dS = left ? dL : dR;
     const double* q = left ? qL : qR;
@@ -283,7 +296,7 @@ stencil_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __restric
                     }
                     const double Ss = hllc_hydro<DIM>(g, gm1_inv, dir, qL, qR, F);
                     // species: upwind side of the contact, renormalised
-                    const bool lft = Ss >= 0.0;
+                    const bool lft = nonneg(Ss);
                     const int zu = lft ? zl : zr, su = lft ? slf : sr;
                     // right face of the left zone (+h) or left face of the right zone (-h): the
                     // sign flip on the bit pattern keeps one FP64 add per species
