@@ -73,6 +73,7 @@ def lib():
         _lib.orc_avg_to_point.argtypes = [pp, C.c_int, dp, dp]
         _lib.orc_point_to_avg.argtypes = [pp, C.c_int, dp, dp]
         _lib.orc_hllc.argtypes = [pp, C.c_int, dp, dp, dp]
+        _lib.orc_hllc_star.argtypes = [pp, C.c_int, dp, dp, dp, dp, dp]
         _lib.orc_rates.argtypes = [pp, C.c_double, dp, dp, dp, dp]
         _lib.orc_reaction_source.argtypes = [pp, dp, dp]
         _lib.orc_newton_zone.argtypes = [pp, C.c_double, dp, dp, C.c_double, dp, ip]
@@ -180,6 +181,17 @@ class Oracle:
         F = np.empty(self.nvar)
         self.L.orc_hllc(C.byref(self.s), int(direction), _dp(qL), _dp(qR), _dp(F))
         return F
+
+    def hllc_star(self, direction, qL, qR):
+        """Wave speeds (S_L, S*, S_R) and the star states U*_L, U*_R (mass,
+        momenta, energy) of the HLLC fan between two primitive states."""
+        qL = np.ascontiguousarray(qL, dtype=np.float64)
+        qR = np.ascontiguousarray(qR, dtype=np.float64)
+        S = np.empty(3)
+        UsL = np.empty(2 + self.P.dim)
+        UsR = np.empty(2 + self.P.dim)
+        self.L.orc_hllc_star(C.byref(self.s), int(direction), _dp(qL), _dp(qR), _dp(S), _dp(UsL), _dp(UsR))
+        return S, UsL, UsR
 
     def temperature(self, rho, mom, rhoE):
         mom = np.ascontiguousarray(np.atleast_1d(mom), dtype=np.float64)

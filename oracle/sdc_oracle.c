@@ -11,10 +11,15 @@
  *   section 2, after the eq.   zone averages, implicit in the new state,
  *                              integral from iteration (k) at all nodes,
  *                              trapezoid (2 nodes) / Simpson (3 nodes)
- * The spatial operator (PLM + MC limiter + HLLC), the toy networks, the
- * gamma-law EOS and the Newton solve are not specified by the paper; the
- * readings taken here are the ones listed in the design notes of the
- * repository (c1..c20).
+ * The paper does not specify the spatial operator, the networks, the EOS or
+ * the Newton solve.  Readings taken here: method-of-lines PLM with the MC
+ * limiter (or unlimited centred slopes) and Toro's HLLC flux with Davis wave
+ * speeds; interface mass fractions renormalised to sum to one and species
+ * carried by the mass flux of the side upwind of the contact; a gamma-law gas
+ * p = rho T; the alpha-chain and A -> B networks with rates
+ * r_j = a_j rho^(o_j - 1) f_j(T) prod Y^count; all nodes of the first
+ * iterate equal to U^n; the implicit update solved by Newton iteration with
+ * pseudo-transient continuation and a dense partially pivoted LU.
  */
 #include "sdc_oracle.h"
 
@@ -129,8 +134,17 @@ static void cons_to_prim(const orc_problem* P, const double* U, long long N, lon
 /* HLLC approximate Riemann solver (Toro), Davis wave-speed estimates. */
 /* Species flux = X of the side upwind of the contact times mass flux. */
 /* ------------------------------------------------------------------ */
-void orc_hllc(const orc_problem* P, int dir, const double* qL, const double* qR, double* F) {
-    int dim = P->dim, nv = orc_nvar(P);
+
+/* Wave speeds S = {S_L, S*, S_R} and the two star states U*_L, U*_R (mass,
+   momenta, energy: 2 + dim entries each) of the HLLC fan between the
+   primitive states qL and qR.  Each star state follows from the jump
+   conditions across its outer wave with the contact moving at S* and one
+   pressure on both sides of it:
+     rho*_K = rho_K (S_K - u_K) / (S_K - S*),  u*_K = S*, tangential u kept,
+     E*_K = rho*_K (E_K/rho_K + (S* - u_K)(S* + p_K / (rho_K (S_K - u_K)))). */
+void orc_hllc_star(const orc_problem* P, int dir, const double* qL, const double* qR, double* S, double* UsL,
+                   double* UsR) {
+    int dim = P->dim;
     double g = P->gamma;
     double rL = qL[0], rR = qR[0];
     double unL = qL[1 + dir], unR = qR[1 + dir];
@@ -148,6 +162,34 @@ void orc_hllc(const orc_problem* P, int dir, const double* qL, const double* qR,
     double SR = fmax(unL + cL, unR + cR);
     double Ss = (pR - pL + rL * unL * (SL - unL) - rR * unR * (SR - unR)) /
                 (rL * (SL - unL) - rR * (SR - unR));
+    S[0] = SL; S[1] = Ss; S[2] = SR;
+
+    double fac = rL * (SL - unL) / (SL - Ss);
+    UsL[0] = fac;
+    for (int d = 0; d < dim; d++) UsL[1 + d] = fac * (d == dir ? Ss : qL[1 + d]);
+    UsL[1 + dim] = fac * (EL / rL + (Ss - unL) * (Ss + pL / (rL * (SL - unL))));
+    fac = rR * (SR - unR) / (SR - Ss);
+    UsR[0] = fac;
+    for (int d = 0; d < dim; d++) UsR[1 + d] = fac * (d == dir ? Ss : qR[1 + d]);
+    UsR[1 + dim] = fac * (ER / rR + (Ss - unR) * (Ss + pR / (rR * (SR - unR))));
+}
+
+void orc_hllc(const orc_problem* P, int dir, const double* qL, const double* qR, double* F) {
+    int dim = P->dim;
+    double g = P->gamma;
+    double rL = qL[0], rR = qR[0];
+    double unL = qL[1 + dir], unR = qR[1 + dir];
+    double pL = qL[1 + dim], pR = qR[1 + dim];
+    double kL = 0.0, kR = 0.0;
+    for (int d = 0; d < dim; d++) {
+        kL += qL[1 + d] * qL[1 + d];
+        kR += qR[1 + d] * qR[1 + d];
+    }
+    double EL = pL / (g - 1.0) + 0.5 * rL * kL;
+    double ER = pR / (g - 1.0) + 0.5 * rR * kR;
+    double S[3], UsL[8], UsR[8];
+    orc_hllc_star(P, dir, qL, qR, S, UsL, UsR);
+    double SL = S[0], Ss = S[1], SR = S[2];
 
     /* physical fluxes and conserved states of both sides (mass, momenta, energy) */
     double FL[8], FR[8], UL[8], UR[8];
@@ -164,30 +206,21 @@ void orc_hllc(const orc_problem* P, int dir, const double* qL, const double* qR,
     FL[1 + dim] = (EL + pL) * unL;
     FR[1 + dim] = (ER + pR) * unR;
 
+    /* the region of the fan that holds the face: F_L, F*_L = F_L + S_L (U*_L - U_L),
+       F*_R = F_R + S_R (U*_R - U_R), F_R */
     double Fh[8];
     if (SL >= 0.0) {
         for (int f = 0; f < nh; f++) Fh[f] = FL[f];
     } else if (Ss >= 0.0) {
-        double fac = rL * (SL - unL) / (SL - Ss);
-        double Us[8];
-        Us[0] = fac;
-        for (int d = 0; d < dim; d++) Us[1 + d] = fac * (d == dir ? Ss : qL[1 + d]);
-        Us[1 + dim] = fac * (EL / rL + (Ss - unL) * (Ss + pL / (rL * (SL - unL))));
-        for (int f = 0; f < nh; f++) Fh[f] = FL[f] + SL * (Us[f] - UL[f]);
+        for (int f = 0; f < nh; f++) Fh[f] = FL[f] + SL * (UsL[f] - UL[f]);
     } else if (SR > 0.0) {
-        double fac = rR * (SR - unR) / (SR - Ss);
-        double Us[8];
-        Us[0] = fac;
-        for (int d = 0; d < dim; d++) Us[1 + d] = fac * (d == dir ? Ss : qR[1 + d]);
-        Us[1 + dim] = fac * (ER / rR + (Ss - unR) * (Ss + pR / (rR * (SR - unR))));
-        for (int f = 0; f < nh; f++) Fh[f] = FR[f] + SR * (Us[f] - UR[f]);
+        for (int f = 0; f < nh; f++) Fh[f] = FR[f] + SR * (UsR[f] - UR[f]);
     } else {
         for (int f = 0; f < nh; f++) Fh[f] = FR[f];
     }
     for (int f = 0; f < nh; f++) F[f] = Fh[f];
     const double* Xup = (Ss >= 0.0) ? qL : qR;
     for (int s = 0; s < P->nspec; s++) F[2 + dim + s] = Fh[0] * Xup[2 + dim + s];
-    (void)nv;
 }
 
 /* MC limited slope (or the unlimited centred slope) from three values */

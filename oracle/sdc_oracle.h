@@ -101,6 +101,11 @@ void orc_advective(const orc_problem* P, const double* U, double* A);
 /* HLLC flux through one face, primitive states q = [rho, u_0.., p, X_0..] (nvar entries) */
 void orc_hllc(const orc_problem* P, int dir, const double* qL, const double* qR, double* F);
 
+/* the HLLC fan of one face: wave speeds S[3] = {S_L, S*, S_R} and the star
+   states U*_L, U*_R (2 + dim conserved entries: mass, momenta, energy) */
+void orc_hllc_star(const orc_problem* P, int dir, const double* qL, const double* qR, double* S, double* UsL,
+                   double* UsR);
+
 /* reactive source R(w) (n entries) and dR/dw (n*n, row major) at one zone */
 void orc_rates(const orc_problem* P, double rho, const double* mom, const double* w,
                double* R, double* dRdw /* nullable */);

@@ -136,6 +136,99 @@ def test_hllc_resolves_contact():
     assert F[3:] == pytest.approx(1.0 * u * qL[3:], rel=1e-14)
 
 
+def _hllc_states(rng, region, dim):
+    """Two primitive states whose HLLC fan puts the face in `region`:
+    0 = left of S_L (supersonic to the right), 1 = between S_L and S*,
+    2 = between S* and S_R, 3 = right of S_R (supersonic to the left)."""
+    rho = rng.uniform(0.3, 3.0, 2)
+    p = rng.uniform(0.2, 4.0, 2)
+    vel = rng.uniform(-0.5, 0.5, (2, dim))
+    shift = {0: 4.0, 1: 0.3, 2: -0.3, 3: -4.0}[region]
+    vel[:, 0] += shift
+    return rho, vel, p
+
+
+@pytest.mark.parametrize("dim", [1, 3])
+def test_hllc_star_states_satisfy_the_jump_conditions(dim):
+    """The A(U) of Eq. 1 (section 2) through Toro's HLLC fan: each star state
+    satisfies the Rankine-Hugoniot conditions across its outer wave, with the
+    contact moving at S*, tangential velocity carried, and one pressure on both
+    sides of the contact (from the momentum jumps); the two star states together
+    satisfy the integral form of the conservation law over the fan,
+    S_R U_R - S_L U_L - (F_R - F_L) = (S* - S_L) U*_L + (S_R - S*) U*_R; and the
+    flux in each region is the physical flux of that region's state.  A wrong
+    pressure work term in the star energies (on one side or both) breaks the
+    energy jump and the integral condition."""
+    g = 1.4
+    net = W.alpha_chain(4, np.random.default_rng(5))
+    P = W.Problem(dim=dim, n=(4,) + ((4, 4) if dim == 3 else (1, 1)), dx=(0.25,) * 3, gamma=g, net=net)
+    o = O.Oracle(P)
+    rng = np.random.default_rng(11)
+    nh = 2 + dim
+    seen = set()
+    for trial in range(80):
+        region = trial % 4
+        rho, vel, p = _hllc_states(rng, region, dim)
+        X = [rng.dirichlet(np.ones(net.nspec)) for _ in range(2)]
+        for d in range(dim):
+            v = np.roll(vel, d, axis=1)          # normal velocity along direction d
+            qL = np.concatenate([[rho[0]], v[0], [p[0]], X[0]])
+            qR = np.concatenate([[rho[1]], v[1], [p[1]], X[1]])
+            S, UsL, UsR = o.hllc_star(d, qL, qR)
+            SL, Ss, SR = S
+            assert SL < Ss < SR
+            U, F, pk = [], [], []
+            for q in (qL, qR):
+                r, u, pp = q[0], q[1:1 + dim], q[1 + dim]
+                E = pp / (g - 1) + 0.5 * r * np.dot(u, u)
+                U.append(np.concatenate([[r], r * u, [E]]))
+                mom = r * u[d] * u
+                mom[d] += pp
+                F.append(np.concatenate([[r * u[d]], mom, [(E + pp) * u[d]]]))
+            scale = max(np.abs(np.concatenate(U + F)).max(), 1.0) * max(abs(SL), abs(SR))
+            for K, Us, SK in ((0, UsL, SL), (1, UsR, SR)):
+                r, u, pp = (qL, qR)[K][0], (qL, qR)[K][1:1 + dim], (qL, qR)[K][1 + dim]
+                rs = Us[0]
+                us = Us[1:1 + dim] / rs
+                assert us[d] == pytest.approx(Ss, rel=1e-13, abs=1e-13)
+                for t in range(dim):
+                    if t != d:
+                        assert us[t] == pytest.approx(u[t], rel=1e-13, abs=1e-14)
+                # star pressure of side K from its normal-momentum jump
+                ps = SK * rs * Ss - rs * Ss * Ss - SK * r * u[d] + r * u[d] * u[d] + pp
+                pk.append(ps)
+                assert SK * rs - rs * Ss == pytest.approx(SK * r - r * u[d], rel=1e-12, abs=1e-12 * scale)
+                Es = Us[1 + dim]
+                lhs = SK * Es - Ss * (Es + ps)
+                rhs = SK * U[K][1 + dim] - u[d] * (U[K][1 + dim] + pp)
+                assert abs(lhs - rhs) <= 1e-12 * scale, (region, K, lhs, rhs)
+            assert pk[0] == pytest.approx(pk[1], rel=1e-12)
+            integral = SR * U[1] - SL * U[0] - (F[1] - F[0])
+            fan = (Ss - SL) * UsL + (SR - Ss) * UsR
+            assert np.abs(integral - fan).max() <= 1e-12 * scale
+            # the flux in the region that holds the face (x / t = 0)
+            Fo = o.hllc(d, qL, qR)
+            if SL >= 0:
+                expect, got_region = F[0], 0
+            elif Ss >= 0:
+                expect, got_region = None, 1
+            elif SR > 0:
+                expect, got_region = None, 2
+            else:
+                expect, got_region = F[1], 3
+            if expect is None:
+                Us = UsL if got_region == 1 else UsR
+                ps = pk[got_region - 1]
+                expect = Ss * Us.copy()
+                expect[1 + d] += ps
+                expect[1 + dim] += Ss * ps
+            seen.add(got_region)
+            assert np.abs(Fo[:nh] - expect).max() <= 1e-12 * scale
+            Xup = X[0] if Ss >= 0 else X[1]
+            assert np.abs(Fo[nh:] - Fo[0] * Xup).max() <= 1e-15 * abs(Fo[0]) + 1e-300
+    assert seen == {0, 1, 2, 3}
+
+
 def _exact_riemann(left, right, g, xi):
     """Exact solution of the 1D Euler Riemann problem for a gamma-law gas
     (Toro, chapter 4): star pressure by Newton on f_L(p) + f_R(p) + du = 0
@@ -483,6 +576,61 @@ def test_decay_with_heating_matches_quadrature_reference():
     assert errs[-1] < 1e-5
     assert math.log2(errs[0] / errs[1]) == pytest.approx(2.0, abs=0.3)
     assert math.log2(errs[1] / errs[2]) == pytest.approx(2.0, abs=0.3)
+
+
+# ---------------------------------------------------------------- rate law
+def _uniform_chain_run(a, nu, T, rho, X, t_final, nsteps, nspec=7):
+    """Uniform, motionless 1D box with a 7-species chain whose only reactions
+    are the ones with a nonzero prefactor, Q = 0 (so T stays fixed and A = 0)."""
+    nr = nspec - 1
+    net = custom_chain(a=list(a) + [0.0] * (nr - len(a)), nu=list(nu) + [5.0] * (nr - len(nu)), Q=[0.0] * nr)
+    P, U = uniform_1d(net, nx=2, rho=rho, T=T, X=X, M=3, K=4)
+    P.newton_rtol = 1e-14
+    return _run_to(P, U, t_final, nsteps)
+
+
+def test_triple_alpha_rate_law_closed_form():
+    """North-star rate law r_j = a_j rho^(n_j - 1) T^nu_j prod Y, for the
+    three-body reaction 3 A0 -> A1 alone (n_0 = 3) at rho = 2 with no flow
+    and Q = 0: dY0/dt = -3 a rho^2 T^nu Y0^3, so
+    Y0(t) = Y0(0) / sqrt(1 + 6 a rho^2 T^nu Y0(0)^2 t) (Y0 = X0: mass 1), and
+    A1 (mass 3) holds the rest of the mass."""
+    a, nu, T, rho, tf = 2.0, 6.0, 1.1, 2.0, 0.05
+    X0 = 0.9
+    exact = X0 / math.sqrt(1.0 + 6.0 * a * rho ** 2 * T ** nu * X0 ** 2 * tf)
+    errs = []
+    for ns in (64, 128):
+        V = _uniform_chain_run([a], [nu], T, rho, [X0, 1 - X0, 0, 0, 0, 0, 0], tf, ns)
+        x0 = V[3, 0, 0, :] / V[0, 0, 0, :]
+        x1 = V[4, 0, 0, :] / V[0, 0, 0, :]
+        errs.append(np.abs(x0 - exact).max())
+        assert np.abs(x0 + x1 - 1.0).max() <= 1e-14
+    assert exact < 0.5                     # a large change: rho^3 in place of rho^2 would double the rate
+    assert errs[-1] <= 1e-9 * exact
+    assert math.log2(errs[0] / errs[1]) == pytest.approx(4.0, abs=0.5)
+
+
+def test_alpha_capture_rate_law_closed_form():
+    """The two-body capture A1 + A0 -> A2 alone (n_1 = 2) at rho = 2, Q = 0,
+    no flow: with k = a rho T^nu, dY0/dt = dY1/dt = -k Y0 Y1 (Y1 = X1 / 3), so
+    D = Y0 - Y1 stays fixed and Y1(t) = D Y1(0) e^(-kDt) / (Y1(0) + D - Y1(0) e^(-kDt))."""
+    a, nu, T, rho, tf = 8.0, 7.0, 1.05, 2.0, 0.2
+    X = [0.6, 0.4, 0, 0, 0, 0, 0]
+    y0, y1 = X[0], X[1] / 3.0
+    D = y0 - y1
+    k = a * rho * T ** nu
+    e = math.exp(-k * D * tf)
+    y1t = D * y1 * e / (y1 + D - y1 * e)
+    errs = []
+    for ns in (64, 128):
+        V = _uniform_chain_run([0.0, a], [5.0, nu], T, rho, X, tf, ns)
+        Y1 = V[4, 0, 0, :] / V[0, 0, 0, :] / 3.0
+        Y0 = V[3, 0, 0, :] / V[0, 0, 0, :]
+        errs.append(np.abs(Y1 - y1t).max())
+        assert np.abs((Y0 - Y1) - D).max() <= 1e-14
+    assert y1t < 0.5 * y1                  # a large change: rho^2 in place of rho would square k's rho factor
+    assert errs[-1] <= 1e-8 * y1t
+    assert math.log2(errs[0] / errs[1]) == pytest.approx(4.0, abs=0.5)
 
 
 # ---------------------------------------------------------------- Newton
