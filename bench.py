@@ -6,12 +6,17 @@ unit being one zone's node m -> m+1 update in one SDC iteration (advective term,
 right-hand side and implicit reaction solve).  A step is one sdc_step (CUDA
 graph) over the whole box from the same seeded initial state.
 
-Default workload: 64^3 periodic box, 7-species alpha chain, 3 Gauss-Lobatto
-nodes, 3 SDC iterations, FP64.  Inputs are resident in HBM when the timed
-region starts; L2 is flushed (256 MB write) before every timed step.
+Default workload: 256^3 periodic box (16.8M zones), 13-species alpha chain
+(14 x 14 Newton system), 3 Gauss-Lobatto nodes, 4 SDC iterations: the FP64
+path is the headline and the FP32-Jacobian / FP64-residual path of the same
+workload is measured in the same run (the "fp32jac" object), each with its
+error against the FP64 oracle.  Inputs are resident in HBM when the timed
+region starts; the state (2.4 GB) is larger than L2, and L2 is also flushed
+(256 MB write) before every timed step.
 
 Usage:
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|fp32jac]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config box256|box64|batch200]
+                  [--prec both|fp64|fp32jac]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 Under torchrun each rank runs its own box (independent problems, weak scaling).
 """
@@ -56,9 +61,11 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--config", choices=["box64", "box256", "batch200"], default="box64")
+    p.add_argument("--config", choices=["box64", "box256", "batch200"], default="box256")
     p.add_argument("--no-autotune", action="store_true")
-    p.add_argument("--prec", choices=["fp64", "fp32jac"], default="fp64")
+    p.add_argument("--prec", choices=["both", "fp64", "fp32jac"], default="both",
+                   help="both: the FP64 path is the headline, the FP32-Jacobian path of the same workload is "
+                        "measured in the same run")
     p.add_argument("--space-order", type=int, choices=[2, 4], default=2,
                    help="2: PLM/MC/HLLC; 4: the fourth-order finite-volume operators")
     p.add_argument("--limiter", type=int, choices=[0, 1], default=1,
@@ -139,22 +146,42 @@ def nzones(P):
     return sum(p.nzones for p in as_list(P))
 
 
-def newton_flops_per_iter(nspec):
-    """Algorithmic flops of one Newton / pseudo-time iteration of one zone
-    (alpha chain, n = nspec + 1 unknowns, nspec - 1 reactions):
-      state evaluation  9 (n_r) + 3 nspec + 5 n   (rate constants and their T
-                                                  derivative, sources, residual, norm)
-      Jacobian / matrix 14 n_r + n
-      LU, partial pivot 2n^3/3 - n^2/2 - n/6 + n  (multiply-add = 2, n reciprocals)
-      two triangular solves 2 n^2 - n
-      update and tests  3 n
-    The transcendental calls (1 log, n_r exp per evaluation) are not counted."""
-    n, nr = nspec + 1, nspec - 1
-    ev = 9 * nr + 3 * nspec + 5 * n
-    jac = 14 * nr + n
-    lu = 2 * n ** 3 / 3 - n ** 2 / 2 - n / 6 + n
-    sol = 2 * n ** 2 - n
-    return ev, jac + lu + sol, 3 * n
+def newton_flops(nspec):
+    """Algorithmic flops of one zone's implicit reaction update on the alpha
+    chain as the kernels compute it (nspec species, n_r = nspec - 1 reactions,
+    n_c = nspec - 1 chain columns; a reciprocal counts as one flop, a fused
+    multiply-add as two; the transcendental calls, 1 log2 T and n_r exp2 per
+    evaluation, are counted apart):
+      evaluation   11 + 9 n_r + 7 nspec   T, 1/T and the rate constants k_j
+                                          (2 per reaction), Y, the rates and
+                                          their species and energy sums, the
+                                          residual G = w - dt_m R - rhs, its
+                                          scaled norm
+      matrix       2 + 18 + 30 (n_r - 1)  entries of c I - dt_m dR/dw in its
+                                          bordered bidiagonal form
+      elimination  28 (n_c - 1) + 15 + 11 + 7 n_c
+                                          the chain columns with the border
+                                          rows, the 2 x 2 border block,
+                                          back substitution
+      update       nspec + 3              trial state and stop-test scales
+      setup        6 + nspec + 2 n_r      per solve: 1/rho, kinetic energy,
+                                          1/(rho mass_i), a_j rho^(o_j-1), the
+                                          energy scale
+    One iteration is one linear solve: matrix + elimination + update + the
+    evaluation at the trial (whose residual decides the step and whose R is
+    the source at the solution); one solve adds the setup and the evaluation at
+    the start.  Returns (per_solve, per_iter_fp64_part, per_iter_linear_part)."""
+    nr = nspec - 1
+    nc = nspec - 1
+    evaluation = 11 + 9 * nr + 7 * nspec
+    matrix = 2 + 18 + 30 * (nr - 1)
+    elimination = 28 * (nc - 1) + 15 + 11 + 7 * nc
+    update = nspec + 3
+    setup = 6 + nspec + 2 * nr
+    return {"per_solve": setup + evaluation, "per_iter_eval_update": evaluation + update,
+            "per_iter_linear": matrix + elimination, "evaluation": evaluation, "matrix": matrix,
+            "elimination": elimination, "update": update, "setup": setup,
+            "transcendentals_per_evaluation": 1 + nr}
 
 
 def stencil_bytes_per_zone(P, rhs_mode):
@@ -246,89 +273,144 @@ def dist():
     return ws, rank, local
 
 
+def field_names(P):
+    return ["rho"] + ["mom%d" % d for d in range(P.dim)] + ["rhoE"] + ["X%d" % i for i in range(P.net.nspec)]
+
+
+def field_errors(P, g, r):
+    """Error of the GPU state g against the oracle's r (both [nvar][zones]),
+    per field, in the two forms the results are stated in:
+      per_field   |g - r|_inf / |r|_inf for every field, species included
+                  (relative to each species' own largest value, floor 1e-30);
+      per_field_floored
+                  the same with the species measured against
+                  max(|rho X_i|_inf, 1e-6 |rho|_inf), i.e. in units of the mass
+                  below 1e-6 of it."""
+    import numpy as np
+    g = g.reshape(P.nvar, -1)
+    r = r.reshape(P.nvar, -1)
+    d = np.abs(g - r).max(1)
+    own = np.maximum(np.abs(r).max(1), 1e-30)
+    floored = own.copy()
+    floored[2 + P.dim:] = np.maximum(floored[2 + P.dim:], 1e-6 * np.abs(r[0]).max())
+    names = field_names(P)
+    pf = {n: float(x) for n, x in zip(names, d / own)}
+    pff = {n: float(x) for n, x in zip(names, d / floored)}
+    hydro = names[:2 + P.dim]
+    return {"max_rel": max(pf.values()), "max_rel_hydro": max(pf[n] for n in hydro),
+            "max_rel_floored": max(pff.values()), "per_field": pf, "per_field_floored": pff,
+            "norm": "per field |gpu - oracle|_inf / |oracle|_inf (species: relative to their own largest value, "
+                    "floor 1e-30; per_field_floored: relative to max(|rho X_i|_inf, 1e-6 |rho|_inf))"}
+
+
+def bench_config(args, desc, P):
+    """The workload description shared by both arms of the benchmark."""
+    P0 = as_list(P)[0]
+    return {"workload": desc, "zones": nzones(P), "nspec": P0.net.nspec, "n_nodes": P0.n_nodes,
+            "iters": P0.n_iters, "nodes": args.nodes, "space_order": args.space_order, "limiter": args.limiter,
+            "seed": args.seed, "prec": "fp32jac" if args.prec == "fp32jac" else "fp64",
+            "l2": "inputs larger than L2 at 256^3; L2 also flushed before every timed step (256 MB write)",
+            "parallelism": "independent box per GPU" if args.gpus > 1 else "1 GPU"}
+
+
+def oracle_sample(args, P, U):
+    """The bounded sample of the workload that the oracle runs as a CPU
+    baseline: the whole problem when it is small, a 64^3 box with the same
+    network and parameters for the 256^3 box, the first 8 boxes of the batch.
+    Returns (list of (Problem, U) pairs, description)."""
+    if isinstance(P, list):
+        out, off = [], 0
+        for p in P[:8]:
+            out.append((p, U[:, off:off + p.nzones].reshape((p.nvar,) + tuple(reversed(p.n))).copy()))
+            off += p.nzones
+        return out, "one SDC step of each of the first 8 boxes of the batch"
+    if P.nzones > 64 ** 3:
+        Pc, Uc = W.config_box(n=64, nspec=P.net.nspec, n_nodes=P.n_nodes, n_iters=P.n_iters, seed=args.seed, T0=0.5)
+        Pc.nodes, Pc.n_nodes = P.nodes, P.n_nodes
+        Pc.space_order, Pc.limiter = P.space_order, P.limiter
+        return [(Pc, Uc)], "one full SDC step of a 64^3 box with the same network and parameters"
+    return [(P, U)], "one full SDC step of the workload"
+
+
 def run_reference(args):
     """The FP64 CPU oracle, as it stands, on the host cores: each step is one
-    full SDC step of the same workload."""
+    SDC step of a bounded sample of the workload (oracle_sample)."""
     ws, rank, _ = dist()
     if rank != 0:
         return 0
     import oracle as O
     P, U, desc = workload(args.config, args.seed, args.nodes)
-    for p_ in (P if isinstance(P, list) else [P]):
+    for p_ in as_list(P):
         p_.space_order, p_.limiter = args.space_order, args.limiter
     desc += space_desc(args)
-    if args.config == "box256":
-        # bounded sample: a 64^3 box with the same network and parameters
-        P, U = W.config_box(n=64, nspec=13, n_nodes=3, n_iters=4, seed=args.seed, T0=0.5)
-        _set_nodes(P, args.nodes)
-        P.space_order, P.limiter = args.space_order, args.limiter
-        desc += " (sample: 64^3 box, same network)"
-    if isinstance(P, list):
-        # bounded sample: the first 8 boxes of the batch, each its own oracle step
-        Ps = P[:8]
-        Us = []
-        off = 0
-        for p in P:
-            if len(Us) == len(Ps):
-                break
-            Us.append(U[:, off:off + p.nzones].reshape((p.nvar,) + tuple(reversed(p.n))).copy())
-            off += p.nzones
-        orcs = [O.Oracle(p) for p in Ps]
-        dt = min(o.cfl_dt(u) for o, u in zip(orcs, Us))
-        run = lambda: [o.step(u, dt) for o, u in zip(orcs, Us)]
-        P = Ps
-        desc += " (sample: the first 8 boxes)"
-    else:
-        o = O.Oracle(P)
-        dt = o.cfl_dt(U)
-        run = lambda: o.step(U, dt)
+    sample, sdesc = oracle_sample(args, P, U)
+    orcs = [O.Oracle(p) for p, _ in sample]
+    dt = min(o.cfl_dt(u) for o, (_, u) in zip(orcs, sample))
+    run = lambda: [o.step(u, dt) for o, (_, u) in zip(orcs, sample)]
     for _ in range(args.warmup):
         run()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         run()
     el = time.perf_counter() - t0
-    v = units_per_step(P) * args.steps / el
-    P0 = as_list(P)[0]
+    v = units_per_step([p for p, _ in sample]) * args.steps / el
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "zones": nzones(P), "nspec": P0.net.nspec, "nodes": P0.n_nodes,
-                       "iters": P0.n_iters, "seed": args.seed},
+            "config": bench_config(args, desc, P),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d full SDC steps of the workload (or of its sample), OpenMP over zones"
-                                       % args.steps},
+                             "sample": "per step: %s (%d zones), OpenMP over zones"
+                                       % (sdesc, sum(p.nzones for p, _ in sample))},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def cpu_baseline_sampled(P, U, dt, gpu_out, seed, target_s=10.0, max_steps=3):
-    """Large boxes: the oracle as it stands on a bounded sample (whole SDC steps
-    of a 64^3 box with the same network and parameters), and the GPU step's
-    error per field on a contiguous 64^3 block at the hot spot: one step moves
-    information at most 2 zones per advective evaluation, 2 (1 + K (M-1)) zones
-    in all (fourth order: 5 (1 + K (M-1))), so the oracle run on the block's
-    periodic surrounding with that much padding gives the exact result in the
-    block."""
-    import numpy as np
+def cpu_baseline(args, P, U, dt, target_s=10.0, max_steps=3):
+    """The oracle as it stands on the host cores, on the bounded sample of
+    oracle_sample, repeated until about target_s seconds of CPU work."""
     import oracle as O
-    Pc, Uc = W.config_box(n=64, nspec=P.net.nspec, n_nodes=P.n_nodes, n_iters=P.n_iters, seed=seed, T0=0.5)
-    Pc.nodes = P.nodes
-    Pc.space_order, Pc.limiter = P.space_order, P.limiter
-    oc = O.Oracle(Pc)
-    dtc = oc.cfl_dt(Uc)
+    sample, sdesc = oracle_sample(args, P, U)
+    orcs = [O.Oracle(p) for p, _ in sample]
     t0 = time.perf_counter()
     steps = 0
     while steps < 1 or (time.perf_counter() - t0 < target_s and steps < max_steps):
-        oc.step(Uc, dtc)
+        for o, (_, u) in zip(orcs, sample):
+            o.step(u, dt)
         steps += 1
     el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": units_per_step([p for p, _ in sample]) * steps / el, "unit": UNIT, "cores": cores,
+            "kind": "oracle", "sample": "%d x %s, OpenMP over zones" % (steps, sdesc)}
+
+
+def oracle_reference(P, U, dt):
+    """The oracle's result on the part of the workload it can run, and a
+    function that cuts the same part out of a GPU result:
+      a box of at most 64^3 zones: the whole box;
+      a larger box: the contiguous 64^3 block at the hot spot, from the oracle
+        run on the block's periodic surrounding padded by the step's domain of
+        dependence (2 zones per advective evaluation for PLM/HLLC, 1 + K (M-1)
+        evaluations; fourth order 5 or 6);
+      the batch: its 3 smallest boxes, each run alone.
+    Returns (Problem, oracle state [nvar][zones], cut(gpu_out) -> [nvar][zones], description)."""
+    import numpy as np
+    import oracle as O
+    if isinstance(P, list):
+        offs = np.cumsum([0] + [p.nzones for p in P])
+        small = sorted(range(len(P)), key=lambda j: P[j].nzones)[:3]
+        refs = []
+        for j in small:
+            Uj = U[:, offs[j]:offs[j + 1]].reshape((P[j].nvar,) + tuple(reversed(P[j].n))).copy()
+            refs.append(O.Oracle(P[j]).step(Uj, dt)[0].reshape(P[j].nvar, -1))
+        cut = lambda G: np.concatenate([G[:, offs[j]:offs[j + 1]] for j in small], axis=1)
+        return P[0], np.concatenate(refs, axis=1), cut, \
+            "every zone of the %d smallest boxes of the batch, each box run alone in the oracle" % len(small)
+    if P.nzones <= 64 ** 3:
+        Uo, _ = O.Oracle(P).step(U, dt)
+        return P, Uo.reshape(P.nvar, -1), (lambda G: G.reshape(P.nvar, -1)), "every zone of the workload"
     h = 64
-    # per advective evaluation 2 zones (PLM/HLLC), 3 (fourth order, smooth form) or 4
-    # (limited: the zone limiter reads two zones out); the fourth-order implicit
-    # update reaches 2 more through its average <-> centre maps
     reach = 2 if P.space_order == 2 else (6 if P.limiter else 5)
     pad = reach * (1 + P.n_iters * (P.n_nodes - 1))
     c0 = P.n[0] // 2 - h // 2
@@ -338,102 +420,34 @@ def cpu_baseline_sampled(P, U, dt, gpu_out, seed, target_s=10.0, max_steps=3):
                    n_iters=P.n_iters, nodes=P.nodes, space_order=P.space_order, limiter=P.limiter)
     Vb, _ = O.Oracle(Pb).step(Ub, dt)
     Vb = Vb.reshape(P.nvar, h + 2 * pad, h + 2 * pad, h + 2 * pad)[:, pad:pad + h, pad:pad + h, pad:pad + h]
-    g = gpu_out.reshape(P.nvar, P.n[2], P.n[1], P.n[0])[:, c0:c0 + h, c0:c0 + h, c0:c0 + h]
-    scale = np.abs(gpu_out).reshape(P.nvar, -1).max(1)
-    scale[2 + P.dim:] = np.maximum(scale[2 + P.dim:], 1e-6 * scale[0])
-    names = ["rho"] + ["mom%d" % d for d in range(P.dim)] + ["rhoE"] + ["X%d" % i for i in range(P.net.nspec)]
-    errs = {n: float(e) for n, e in zip(names, np.abs(g - Vb).reshape(P.nvar, -1).max(1) / scale)}
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return ({"value": units_per_step(Pc) * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-             "sample": "%d full SDC step(s) of a 64^3 box with the same network and parameters, OpenMP over zones"
-                       % steps},
-            {"max_rel": max(errs.values()), "per_field": errs,
-             "sample": "every zone of the 64^3 block at the hot spot, from the oracle on its %d^3 periodic "
-                       "surrounding (%d zones of padding: the step's domain of dependence)" % (h + 2 * pad, pad)})
+    cut = lambda G: G.reshape(P.nvar, P.n[2], P.n[1], P.n[0])[:, c0:c0 + h, c0:c0 + h, c0:c0 + h].reshape(
+        P.nvar, -1)
+    return P, Vb.reshape(P.nvar, -1), cut, \
+        ("every zone and field of the 64^3 block at the hot spot, from the oracle on its %d^3 periodic "
+         "surrounding (%d zones of padding: the step's domain of dependence)" % (h + 2 * pad, pad))
 
 
-def cpu_baseline_batched(Ps, U, dt, gpu_out, target_s=10.0):
-    """Batched boxes: the oracle as it stands on a bounded sample (boxes taken in
-    order until ~10 s of CPU work), and the GPU step's error on the smallest
-    boxes of the batch, each compared zone by zone with the oracle run on it."""
-    import numpy as np
-    import oracle as O
-    offs = np.cumsum([0] + [p.nzones for p in Ps])
-    box = lambda i, A: A[:, offs[i]:offs[i + 1]].reshape((Ps[i].nvar,) + tuple(reversed(Ps[i].n)))
-    t0 = time.perf_counter()
-    units = 0
-    i = 0
-    while i < len(Ps) and (i == 0 or time.perf_counter() - t0 < target_s):
-        O.Oracle(Ps[i]).step(box(i, U).copy(), dt)
-        units += units_per_step(Ps[i])
-        i += 1
-    el = time.perf_counter() - t0
-    worst = 0.0
-    smallest = sorted(range(len(Ps)), key=lambda j: Ps[j].nzones)[:3]
-    for j in smallest:
-        Uo, _ = O.Oracle(Ps[j]).step(box(j, U).copy(), dt)
-        g = box(j, gpu_out).reshape(Ps[j].nvar, -1)
-        r = Uo.reshape(Ps[j].nvar, -1)
-        scale = np.abs(r).max(1)
-        scale[2 + Ps[j].dim:] = np.maximum(scale[2 + Ps[j].dim:], 1e-6 * scale[0])
-        worst = max(worst, float((np.abs(g - r) / scale[:, None]).max()))
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return ({"value": units / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-             "sample": "one SDC step of each of the first %d boxes, OpenMP over zones" % i},
-            {"max_rel": worst, "per_field": None,
-             "sample": "every zone of the %d smallest boxes, each box run alone in the oracle" % len(smallest)})
+def hist_summary(hist):
+    """Newton iterations per zone solve: the histogram (index = iterations,
+    the last bin counts 63 and more) and its range."""
+    h = [int(x) for x in hist]
+    nz = [i for i, x in enumerate(h) if x]
+    top = max(nz) if nz else 0
+    return {"hist": h[:top + 1], "min_iters": min(nz) if nz else 0, "max_iters": top,
+            "solves": sum(h), "mean_iters": (sum(i * x for i, x in enumerate(h)) / max(sum(h), 1))}
 
 
-def cpu_baseline_and_error(P, U, dt, gpu_out, target_s=10.0, max_steps=4):
-    """The oracle as it stands on the host cores (bounded sample: whole SDC steps
-    of the workload until ~10 s of CPU work), plus the error of the GPU step
-    against it (this leg is the only one that runs the oracle)."""
-    import numpy as np
-    import oracle as O
-    o = O.Oracle(P)
-    t0 = time.perf_counter()
-    Uo, _ = o.step(U, dt)
-    steps = 1
-    while time.perf_counter() - t0 < target_s and steps < max_steps:
-        o.step(U, dt)
-        steps += 1
-    el = time.perf_counter() - t0
-    g = gpu_out.reshape(P.nvar, -1)
-    r = Uo.reshape(P.nvar, -1)
-    rho_max = np.abs(r[0]).max()
-    errs = {}
-    names = ["rho"] + ["mom%d" % d for d in range(P.dim)] + ["rhoE"] + ["X%d" % i for i in range(P.net.nspec)]
-    for f in range(P.nvar):
-        den = np.abs(r[f]).max()
-        if f >= 2 + P.dim:
-            den = max(den, 1e-6 * rho_max)
-        errs[names[f]] = float(np.abs(g[f] - r[f]).max() / max(den, 1e-300))
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return ({"value": units_per_step(P) * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-             "sample": "%d full SDC step(s) of the workload from the initial state, OpenMP over zones" % steps},
-            {"max_rel": max(errs.values()), "per_field": errs})
-
-
-def run_ours(args):
+def measure(args, P, U, prec, ws, barrier, flush, with_e2e=True):
+    """One context at one precision: autotune, warm-up, K timed steps (device
+    time, inputs resident), end to end with host buffers, the per-class
+    profile, the Newton roofline; returns (record, final state of one step
+    from U (numpy), context)."""
     import numpy as np
     import torch
 
-    from paper_1910_12578_gb300 import build as B
     from paper_1910_12578_gb300 import sdc
 
-    ws, rank, local = dist()
-    if ws > 1:
-        import torch.distributed as tdist
-        tdist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    if not os.path.exists(sdc.LIB_PATH):
-        B.build()
-    P, U, desc = workload(args.config, rank_seed(args.seed, rank), args.nodes)
-    for p_ in as_list(P):
-        p_.space_order, p_.limiter = args.space_order, args.limiter
-    desc += space_desc(args)
     P0 = as_list(P)[0]
-    prec = sdc.PREC_FP64 if args.prec == "fp64" else sdc.PREC_FP32_JAC
     ctx = sdc.Context(P, prec=prec)
     U0 = torch.from_numpy(U).cuda()
     Ud = torch.empty_like(U0)
@@ -441,12 +455,7 @@ def run_ours(args):
     tuning = None
     if not args.no_autotune:
         tuning = ctx.autotune(U0, dt).as_dict()
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     units = units_per_step(P)
-
-    def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
 
     # warm-up (also captures the graph)
     for _ in range(max(args.warmup, 1)):
@@ -473,23 +482,27 @@ def run_ours(args):
     value, total_ms = job_value(sum(step_ms), units, args.steps, ws, torch_reduce_max("cuda"))
 
     # ---- end to end through the public API with host buffers (pinned), copies timed
-    Uh = U0.cpu().pin_memory()
-    Uout = torch.empty_like(Uh).pin_memory()
-    e2e_steps = max(3, min(args.steps, 10))
-    Ud.copy_(U0)
-    ctx.step(Ud, dt, stats=False)
-    torch.cuda.synchronize()
-    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    ea.record()
-    for _ in range(e2e_steps):
-        Ud.copy_(Uh, non_blocking=True)
+    e2e = None
+    if with_e2e:
+        Uh = U0.cpu().pin_memory()
+        Uout = torch.empty_like(Uh).pin_memory()
+        e2e_steps = max(3, min(args.steps, 10))
+        Ud.copy_(U0)
         ctx.step(Ud, dt, stats=False)
-        Uout.copy_(Ud, non_blocking=True)
-    eb.record()
-    torch.cuda.synchronize()
-    e2e_value, _ = job_value(ea.elapsed_time(eb) / e2e_steps, units, 1, ws, torch_reduce_max("cuda"))
-    nbytes = U0.numel() * 8
+        torch.cuda.synchronize()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        ea.record()
+        for _ in range(e2e_steps):
+            Ud.copy_(Uh, non_blocking=True)
+            ctx.step(Ud, dt, stats=False)
+            Uout.copy_(Ud, non_blocking=True)
+        eb.record()
+        torch.cuda.synchronize()
+        e2e_value, _ = job_value(ea.elapsed_time(eb) / e2e_steps, units, 1, ws, torch_reduce_max("cuda"))
+        nbytes = U0.numel() * 8
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+        del Uh, Uout
 
     # ---- per-kernel-class times of the same step (eager launches, CUDA events on the context stream)
     Ud.copy_(U0)
@@ -498,33 +511,40 @@ def run_ours(args):
     st2 = ctx.step(Ud, dt, stats=True)
     torch.cuda.synchronize()
     gpu_out = Ud.cpu().numpy()
-    ev_f, lin_f, upd_f = newton_flops_per_iter(P0.net.nspec)
-    iters = st.newton_iters_total
-    newton_ms_launch = pr.ms_newton / max(pr.launches_newton, 1)
+
+    fl = newton_flops(P0.net.nspec)
+    iters, solves = st.newton_iters_total, st.newton_solves
+    nl = max(pr.launches_newton, 1)
+    newton_ms_launch = pr.ms_newton / nl
+    fp64_total = solves * fl["per_solve"] + iters * fl["per_iter_eval_update"]
+    lin_total = iters * fl["per_iter_linear"]
     if prec == sdc.PREC_FP64:
-        fp64_flops = iters * (ev_f + lin_f + upd_f)
-        fp32_flops = 0
+        fp64_total += lin_total
+        fp32_total = 0
     else:
-        fp64_flops = iters * (ev_f + upd_f)
-        fp32_flops = iters * lin_f
-    achieved = fp64_flops / max(pr.launches_newton, 1) / (newton_ms_launch * 1e-3) / 1e12
+        fp32_total = lin_total
+    achieved = fp64_total / nl / (newton_ms_launch * 1e-3) / 1e12
     newton_choice = tuning["newton_choice"] if tuning else 0
-    per_zone = NEWTON_TRAFFIC_PER_ZONE.get((P0.net.nspec, newton_choice, args.prec))
-    roof = {"kernel": "newton_kernel (implicit reaction update)", "bound": "alu",
-            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+    pkey = "fp64" if prec == sdc.PREC_FP64 else "fp32jac"
+    per_zone = NEWTON_TRAFFIC_PER_ZONE.get((P0.net.nspec, newton_choice, pkey))
+    roof = {"kernel": "newton_*_kernel<%d> (implicit reaction update, variant %d)" % (P0.net.nspec, newton_choice),
+            "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS,
             "traffic": per_zone * nzones(P) if per_zone is not None else None,
             "traffic_unit": "bytes per launch (ncu DRAM read + write)",
             "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (recipe unit counts and clock; "
                            "an FMA-chain probe measured 1.256 TFLOP/s)",
-            "flops_per_launch": fp64_flops / max(pr.launches_newton, 1), "ms_per_launch": newton_ms_launch,
-            "newton_iters_per_solve": iters / max(st.newton_solves, 1),
-            "note": "algorithmic flops count a dense pivoted LU per Newton iteration; the alpha chain's kernels "
-                    "solve the same system by an O(n) elimination of its bordered bidiagonal form, so frac is "
-                    "the algorithmic rate over the FP64 peak, not the FP64 pipe's occupancy (ncu: 84-85 %)"}
-    if fp32_flops:
-        roof["fp32_achieved"] = fp32_flops / max(pr.launches_newton, 1) / (newton_ms_launch * 1e-3) / 1e12
+            "fp64_flops_per_launch": fp64_total / nl, "ms_per_launch": newton_ms_launch,
+            "launches_per_step": pr.launches_newton,
+            "newton_iters_per_solve": iters / max(solves, 1),
+            "flops_per_zone": fl,
+            "note": "algorithmic flops of the bordered bidiagonal elimination the kernel runs (not a dense LU): "
+                    "per solve setup + evaluation, per iteration matrix + elimination + update + evaluation"}
+    if fp32_total:
+        roof["fp32_flops_per_launch"] = fp32_total / nl
+        roof["fp32_achieved"] = fp32_total / nl / (newton_ms_launch * 1e-3) / 1e12
         roof["fp32_peak"] = FP32_PEAK_TFLOPS
+        roof["note"] += "; FP32 Jacobian: matrix and elimination in FP32 (fp32_*), the rest in FP64"
     n_st = pr.launches_stencil
     st_bytes = nzones(P) * (stencil_bytes_per_zone(P0, False) * P0.n_iters +
                             stencil_bytes_per_zone(P0, True) * (P0.n_nodes - 2) * P0.n_iters) / max(n_st, 1)
@@ -539,7 +559,47 @@ def run_ours(args):
     st_gbs = st_bytes / (stencil_ms * 1e-3) / 1e9
     roof_st = {"kernel": "stencil_kernel (advective term + fused rhs)", "bound": "hbm", "achieved": st_gbs,
                "peak": hbm_peak, "unit": "GB/s", "frac": st_gbs / hbm_peak, "traffic": None,
-               "bytes_per_launch": st_bytes, "ms_per_launch": stencil_ms}
+               "bytes_per_launch": st_bytes, "ms_per_launch": stencil_ms,
+               "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    rec = {"value": value, "ms_per_step": total_ms / args.steps, "step_ms": step_ms, "clocks": ck, "e2e": e2e,
+           "kernel_variants": tuning, "roofline": roof, "roofline_stencil": roof_st,
+           "profile_ms": {"stencil": pr.ms_stencil, "newton": pr.ms_newton, "other": pr.ms_other,
+                          "launches": [pr.launches_stencil, pr.launches_newton, pr.launches_other]},
+           "newton": {"iters_total": st2.newton_iters_total, "solves": st2.newton_solves, "fails": st2.n_fail,
+                      "iterations_per_solve": hist_summary(st2.hist)},
+           "gpu_launches": ctx.launches_per_step() * args.steps, "dt": dt}
+    return rec, gpu_out, ctx, U0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1910_12578_gb300 import build as B
+    from paper_1910_12578_gb300 import sdc
+
+    ws, rank, local = dist()
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if not os.path.exists(sdc.LIB_PATH):
+        B.build()
+    P, U, desc = workload(args.config, rank_seed(args.seed, rank), args.nodes)
+    for p_ in as_list(P):
+        p_.space_order, p_.limiter = args.space_order, args.limiter
+    desc += space_desc(args)
+    P0 = as_list(P)[0]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    precs = {"both": [sdc.PREC_FP64, sdc.PREC_FP32_JAC], "fp64": [sdc.PREC_FP64],
+             "fp32jac": [sdc.PREC_FP32_JAC]}[args.prec]
+    head, head_out, ctx, U0 = measure(args, P, U, precs[0], ws, barrier, flush)
+    dt = head["dt"]
 
     # ---- one backward (adjoint) step of the same workload, where the network has one
     adjoint = None
@@ -557,12 +617,13 @@ def run_ours(args):
             ab[1].record()
             torch.cuda.synchronize()
             bms = ab[0].elapsed_time(ab[1]) / 2
-            adjoint = {"ms_per_backward_step": bms, "ms_per_forward_step": total_ms / args.steps,
-                       "ratio": bms / (total_ms / args.steps),
+            adjoint = {"ms_per_backward_step": bms, "ms_per_forward_step": head["ms_per_step"],
+                       "ratio": bms / head["ms_per_step"],
                        "note": "recomputes the forward step from its checkpoint, then the reverse sweep; "
                                "gradient of sum(U^{n+1}) with respect to U^n and the rate prefactors"}
         except sdc.SdcError as e:
             adjoint = {"unavailable": str(e)}
+        del gU, gUn
 
     # ---- the Strang-split baseline on the same kernels: its cost, and the coupling
     # error the SDC step removes (both against the coupled step in 8 steps of dt/8)
@@ -591,12 +652,13 @@ def run_ours(args):
         Uref = U0.clone()
         for _ in range(8):
             ctx.step(Uref, dt / 8, stats=False)
+        ref = Uref.cpu().numpy().reshape(P0.nvar, -1)
+        del Uref
         Uc = U0.clone()
         ctx.step(Uc, dt, stats=False)
         Us.copy_(U0)
         sst = ctx.step_strang(Us, dt)
         torch.cuda.synchronize()
-        ref = Uref.cpu().numpy().reshape(P0.nvar, -1)
 
         names = ["rho"] + ["mom%d" % d for d in range(P0.dim)] + ["rhoE"] + \
             ["rhoX%d" % i for i in range(P0.net.nspec)]
@@ -612,52 +674,60 @@ def run_ours(args):
 
         es, fs = field_err(Us)
         ec, fc = field_err(Uc)
-        strang = {"ms_per_step": s_ms, "sdc_ms_per_step": total_ms / args.steps,
+        strang = {"ms_per_step": s_ms, "sdc_ms_per_step": head["ms_per_step"],
                   "error_vs_fine_sdc": es, "sdc_error_vs_fine_sdc": ec,
                   "per_field_inf_l1": {"strang": fs, "sdc": fc},
                   "newton_fails": sst.n_fail,
                   "reference": "the coupled SDC step in 8 steps of dt/8 on the GPU (same kernels); errors are "
-                               "|U - U_ref|_inf / |U_ref|_inf per field (max over fields) and |U - U_ref|_1 / "
-                               "|U_ref|_1 at the benchmark dt"}
+                               "|U - U_ref|_inf / max(|U_ref|_inf, 1e-6 |rho|_inf) per field (max over fields) "
+                               "and |U - U_ref|_1 / |U_ref|_1 at the benchmark dt"}
+        del Us, Uc
+    ctx.close()
+    del ctx, U0
+    torch.cuda.empty_cache()
+
+    # ---- the FP32-Jacobian path of the same workload
+    second, second_out = None, None
+    if len(precs) > 1:
+        second, second_out, ctx2, U02 = measure(args, P, U, precs[1], ws, barrier, flush)
+        ctx2.close()
+        del ctx2, U02
+        torch.cuda.empty_cache()
 
     line = None
     if rank == 0:
-        cpu, err = (None, None)
+        cpu, err, err2 = None, None, None
         if ws == 1 and not args.no_cpu_baseline:
-            if isinstance(P, list):
-                cpu, err = cpu_baseline_batched(P, U, dt, gpu_out)
-            elif P.nzones > 64 ** 3:
-                cpu, err = cpu_baseline_sampled(P, U, dt, gpu_out, args.seed)
-            else:
-                cpu, err = cpu_baseline_and_error(P, U, dt, gpu_out)
-        per_step = ctx.launches_per_step()
+            cpu = cpu_baseline(args, P, U, dt)
+            Pr, ref, cut, rdesc = oracle_reference(P, U, dt)
+            err = field_errors(Pr, cut(head_out.reshape(P0.nvar, -1)), ref)
+            err["sample"] = rdesc
+            if second is not None:
+                err2 = field_errors(Pr, cut(second_out.reshape(P0.nvar, -1)), ref)
+                err2["sample"] = rdesc
+        prec_name = lambda p: "fp64" if p == sdc.PREC_FP64 else "fp32jac"
+        dtype = lambda p: "f64" if p == sdc.PREC_FP64 else "f64 residual/update, f32 Jacobian/LU"
+        cfg = bench_config(args, desc, P)
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == sdc.PREC_FP64 else "f64 residual/update, f32 Jacobian/LU",
-            "data": "synthetic",
-            "config": {"workload": desc, "zones": nzones(P), "nspec": P0.net.nspec, "n_nodes": P0.n_nodes,
-                       "iters": P0.n_iters, "nodes": args.nodes, "space_order": args.space_order,
-                       "limiter": args.limiter, "prec": args.prec, "seed": args.seed,
-                       "kernel_variants": tuning,
-                       "l2": "flushed before every timed step (256 MB write)",
-                       "parallelism": "independent box per GPU" if ws > 1 else "1 GPU"},
-            "clocks": ck,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                    "d2h_bytes_per_step": nbytes},
-            "gpu_launches": per_step * args.steps,
-            "roofline": roof,
-            "roofline_stencil": roof_st,
-            "profile_ms": {"stencil": pr.ms_stencil, "newton": pr.ms_newton, "other": pr.ms_other,
-                           "launches": [pr.launches_stencil, pr.launches_newton, pr.launches_other]},
-            "newton": {"iters_total": st2.newton_iters_total, "solves": st2.newton_solves,
-                       "fails": st2.n_fail},
-            "cpu_baseline": cpu,
-            "oracle_error": err,
-            "adjoint": adjoint,
-            "strang": strang,
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype(precs[0]), "data": "synthetic",
+            "config": cfg, "clocks": head["clocks"], "e2e": head["e2e"],
+            "gpu_launches": head["gpu_launches"] + (second["gpu_launches"] if second else 0),
+            "roofline": head["roofline"], "roofline_stencil": head["roofline_stencil"],
+            "kernel_variants": head["kernel_variants"], "profile_ms": head["profile_ms"],
+            "newton": head["newton"], "cpu_baseline": cpu, "oracle_error": err,
         }
+        if second is not None:
+            line["fp32jac"] = {
+                "prec": prec_name(precs[1]), "dtype": dtype(precs[1]), "value": second["value"],
+                "ms_per_step": second["ms_per_step"], "speedup_vs_fp64": head["ms_per_step"] / second["ms_per_step"],
+                "e2e": second["e2e"], "clocks": second["clocks"], "roofline": second["roofline"],
+                "kernel_variants": second["kernel_variants"], "profile_ms": second["profile_ms"],
+                "newton": second["newton"], "oracle_error": err2,
+                "note": "same workload, steps and warm-up as the headline; gpu_launches counts both runs"}
+        line["adjoint"] = adjoint
+        line["strang"] = strang
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -294,10 +294,12 @@ sdc_status sdc_sizes(const sdc_ctx* ctx, long long* ntot, int* nvar, int* nreact
    (node states, A and R of two iterations, the rhs, box and tile tables, dt,
    statistics) lives in one file-scope device array of SDC_STATIC_SCRATCH_BYTES
    that every GPU loading the library holds until the process exits.
-   - Capacity: (8 + 2(M-1))*nvar + (1 + 2(M-1))*n doubles per zone plus the
-     tables must fit in SDC_STATIC_SCRATCH_BYTES (48 MiB: e.g. 32^3 zones with
-     7 species and 3 nodes); larger problems return SDC_ERR_TOO_LARGE before
-     any work is enqueued; at most SDC_STATIC_MAX_BOXES boxes.
+   - Capacity: (2 + 3(M-1))*nvar + (1 + 2(M-1))*n doubles per zone (n = nspec
+     + 1; each array rounded up to 256 bytes) plus the box and tile tables must
+     fit in SDC_STATIC_SCRATCH_BYTES (48 MiB: e.g. 32^3 zones with 7 species
+     and 3 nodes, 136 doubles per zone); larger problems, and boxes of 2^31
+     zones or more, return SDC_ERR_TOO_LARGE before any work is enqueued; at
+     most SDC_STATIC_MAX_BOXES boxes.
    - The first call on a device looks up the array's device address with
      cudaGetSymbolAddress (that device current); make that first call before
      any stream capture.

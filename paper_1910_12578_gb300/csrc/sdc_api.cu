@@ -1180,8 +1180,16 @@ extern "C" sdc_status sdc_step_static(const sdc_box* boxes, int nbox, const sdc_
             T.n[b][d] = boxes[b].n[d];
             T.idx[b][d] = d < dim ? 1.0 / boxes[b].dx[d] : 0.0;
         }
+        // zone indices inside a box are 32-bit: refuse 2^31 zones or more before
+        // any product can overflow (each factor is below 2^31)
+        const long long n01 = (long long)boxes[b].n[0] * boxes[b].n[1];
+        if (n01 >= (1ll << 31)) return SDC_ERR_TOO_LARGE;
+        const long long nb = n01 * boxes[b].n[2];
+        if (nb >= (1ll << 31)) return SDC_ERR_TOO_LARGE;
         T.off[b] = Ntot;
-        Ntot += (long long)boxes[b].n[0] * boxes[b].n[1] * boxes[b].n[2];
+        Ntot += nb;
+        // one double per zone must fit before the workspace offsets are formed
+        if (Ntot > (long long)(SDC_STATIC_SCRATCH_BYTES / sizeof(double))) return SDC_ERR_TOO_LARGE;
         const long long nt = (long long)((boxes[b].n[0] + T.t[0] - 1) / T.t[0]) *
                              ((boxes[b].n[1] + T.t[1] - 1) / T.t[1]) * ((boxes[b].n[2] + T.t[2] - 1) / T.t[2]);
         if ((long long)T.tile_first[b] + nt > (1ll << 30)) return SDC_ERR_TOO_LARGE;

@@ -4,18 +4,19 @@ import numpy as np
 import oracle as O
 
 
-def rel_err(gpu, orc, nvar, dim, species_floor=1e-6):
-    """Per-field relative infinity-norm error; species fields are taken
+def rel_err(gpu, orc, nvar, dim, species_floor=None):
+    """Per-field relative infinity-norm error |gpu - orc|_inf / |orc|_inf,
+    every field against its own largest oracle value (floor 1e-30), species
+    included.  With species_floor set, species fields are instead taken
     relative to max(|rho X_i|_inf, species_floor * |rho|_inf)."""
     g = np.asarray(gpu).reshape(nvar, -1)
     o = np.asarray(orc).reshape(nvar, -1)
     rho_max = np.abs(o[0]).max()
     out = []
     for f in range(nvar):
-        den = np.abs(o[f]).max()
-        if f >= 2 + dim:
+        den = max(np.abs(o[f]).max(), 1e-30)
+        if f >= 2 + dim and species_floor is not None:
             den = max(den, species_floor * rho_max)
-        den = max(den, 1e-300)
         out.append(np.abs(g[f] - o[f]).max() / den)
     return np.array(out)
 

