@@ -166,6 +166,10 @@ struct sdc_ctx {
     BoxDev* d_boxes = nullptr;
     TileDev* d_tiles = nullptr;
     int ntiles = 0;
+    // the direction-split stencil (3D): tiles of each pass and the primitives buffer
+    TileDev* d_tiles_split[3] = {nullptr, nullptr, nullptr};
+    int ntiles_split[3] = {0, 0, 0};
+    double* prim = nullptr;
     double* d_dt = nullptr;
     double* node_ws[MAXM - 1] = {nullptr};    // node 0 (copy of U^n), nodes 1..M-2
     double* A0 = nullptr;                     // A at node 0 (fixed within a step)
@@ -318,6 +322,17 @@ RhsArgs rhs_args(const sdc_ctx* c, const double* const* Aold, const double* cons
     return ra;
 }
 
+// The second-order advective term of U into A (with the rhs when mode is
+// STENCIL_A_RHS) by the context's stencil variant: a tile shape of
+// stencil_kernel, or the direction-split passes.
+cudaError_t launch_A(const sdc_ctx* c, const double* U, double* A, int mode, const RhsArgs& ra, cudaStream_t st) {
+    if (c->stencil_variant == stencil_split_variant(c->dim, c->nspec))
+        return launch_stencil_split(c->P, c->limiter, c->Ntot, c->d_boxes, c->d_tiles_split, c->ntiles_split, U,
+                                    c->prim, A, mode, ra, st);
+    return launch_stencil(c->P, c->dim, c->limiter, c->Ntot, c->d_boxes, c->d_tiles, c->ntiles, U, A, mode, ra, st,
+                          c->stencil_variant);
+}
+
 // Operators of a step: both (the coupled SDC step), or one of them alone (the
 // sub-problems of the Strang-split step: A = 0, or R = 0 with the implicit
 // update reduced to w = rhs).
@@ -352,9 +367,7 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
             SDC_LAUNCH(prof, CLS_STENCIL, launch_advective4(c->P, c->dim, c->limiter, N, c->d_boxes, c->nbox,
                                                             node[0], c->A0, c->fw, st));
         else
-            SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles,
-                                                         c->ntiles, node[0], c->A0, STENCIL_A, none, st,
-                                                         c->stencil_variant));
+            SDC_LAUNCH(prof, CLS_STENCIL, launch_A(c, node[0], c->A0, STENCIL_A, none, st));
     } else if ((e = cudaMemsetAsync(c->A0, 0, ubytes, st)) != cudaSuccess) {
         return e;
     }
@@ -394,9 +407,7 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
                                                            st>>>(c->nvar, c->dim, N, node[m], Anew[m], ra),
                                              cudaGetLastError()));
             } else {
-                SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles,
-                                                             c->ntiles, node[m], Anew[m], STENCIL_A_RHS, ra, st,
-                                                             c->stencil_variant));
+                SDC_LAUNCH(prof, CLS_STENCIL, launch_A(c, node[m], Anew[m], STENCIL_A_RHS, ra, st));
             }
             if (with_R) {
                 const double* guess = (k == 0) ? node[0] : node[m + 1];
@@ -427,9 +438,7 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
                 SDC_LAUNCH(prof, CLS_STENCIL, launch_advective4(c->P, c->dim, c->limiter, N, c->d_boxes, c->nbox,
                                                                 node[c->M - 1], Anew[c->M - 1], c->fw, st));
             else
-                SDC_LAUNCH(prof, CLS_STENCIL, launch_stencil(c->P, c->dim, c->limiter, N, c->d_boxes, c->d_tiles,
-                                                             c->ntiles, node[c->M - 1], Anew[c->M - 1], STENCIL_A,
-                                                             none, st, c->stencil_variant));
+                SDC_LAUNCH(prof, CLS_STENCIL, launch_A(c, node[c->M - 1], Anew[c->M - 1], STENCIL_A, none, st));
         }
         for (int l = 1; l < c->M; l++) {
             Aold[l] = Anew[l];
@@ -459,7 +468,24 @@ std::vector<TileDev> tile_list(const sdc_ctx* c, int variant) {
     return ht;
 }
 
+// tiles of direction-split pass D of every box
+std::vector<TileDev> split_tile_list(const sdc_ctx* c, int D) {
+    std::vector<TileDev> ht;
+    int tl[3];
+    split_tile_shape(D, tl);
+    for (int b = 0; b < (int)c->boxes.size(); b++)
+        for (int z = 0; z < c->boxes[b].n[2]; z += tl[2])
+            for (int y = 0; y < c->boxes[b].n[1]; y += tl[1])
+                for (int x = 0; x < c->boxes[b].n[0]; x += tl[0]) ht.push_back(TileDev{b, {x, y, z}});
+    return ht;
+}
+
 cudaError_t set_stencil_variant(sdc_ctx* c, int variant) {
+    if (variant == stencil_split_variant(c->dim, c->nspec)) {
+        if (!c->prim) return cudaErrorInvalidValue;  // a context without the split workspace
+        c->stencil_variant = variant;
+        return cudaSuccess;
+    }
     std::vector<TileDev> ht = tile_list(c, variant);
     if ((int)ht.size() > c->tiles_capacity) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemcpy(c->d_tiles, ht.data(), sizeof(TileDev) * ht.size(), cudaMemcpyHostToDevice);
@@ -617,6 +643,7 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     P.topo = topo_used;
     P.gamma = prm->gamma;
     P.gm1 = prm->gamma - 1.0;
+    P.gm1_inv = 1.0 / P.gm1;
     for (int i = 0; i < net->nspec; i++) {
         P.mass[i] = net->mass[i];
         P.inv_mass[i] = 1.0 / net->mass[i];
@@ -648,6 +675,7 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     c->boxes.assign(boxes, boxes + nbox);
     int max_tiles = 0;
     for (int v = 0; v < stencil_variants(dim, net->nspec); v++) {
+        if (v == stencil_split_variant(dim, net->nspec)) continue;
         const int nt = (int)tile_list(c, v).size();
         if (nt > max_tiles) max_tiles = nt;
     }
@@ -679,6 +707,19 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     if ((e = ctx_alloc(c, (void**)&c->A0, ub)) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->R0, rb)) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->rhs, ub)) != cudaSuccess) return fail(e);
+    if (dim == 3 && c->space_order == 2) {
+        // the direction-split stencil: the primitives buffer and the tiles of its passes
+        if ((e = ctx_alloc(c, (void**)&c->prim, ub)) != cudaSuccess) return fail(e);
+        for (int D = 0; D < 3; D++) {
+            std::vector<TileDev> st3 = split_tile_list(c, D);
+            c->ntiles_split[D] = (int)st3.size();
+            if ((e = ctx_alloc(c, (void**)&c->d_tiles_split[D], sizeof(TileDev) * st3.size())) != cudaSuccess)
+                return fail(e);
+            if ((e = cudaMemcpy(c->d_tiles_split[D], st3.data(), sizeof(TileDev) * st3.size(),
+                                cudaMemcpyHostToDevice)) != cudaSuccess)
+                return fail(e);
+        }
+    }
     for (int g = 0; g < 2; g++)
         for (int m = 1; m < c->M; m++) {
             if ((e = ctx_alloc(c, (void**)&c->Ag[g][m], ub)) != cudaSuccess) return fail(e);
@@ -723,8 +764,7 @@ sdc_status sdc_advective_term(sdc_ctx* ctx, const double* U, double* A) {
     }
     RhsArgs none;
     memset(&none, 0, sizeof(none));
-    SDC_TRY(launch_stencil(ctx->P, ctx->dim, ctx->limiter, ctx->Ntot, ctx->d_boxes, ctx->d_tiles, ctx->ntiles, U, A,
-                           STENCIL_A, none, ctx->stream, ctx->stencil_variant));
+    SDC_TRY(launch_A(ctx, U, A, STENCIL_A, none, ctx->stream));
     return SDC_OK;
 }
 
@@ -891,6 +931,9 @@ sdc_status sdc_autotune(sdc_ctx* ctx, const double* U, double dt, sdc_tuning* ou
     float best_st = 0.0f, best_nw = 0.0f;
     int vs = 0, vn = 0;
     for (int v = 0; v < t.stencil_variants && st == SDC_OK; v++) {
+        // the fourth-order operators use no tile shape, and their contexts hold
+        // no workspace for the direction-split passes
+        if (v == stencil_split_variant(ctx->dim, ctx->nspec) && !ctx->prim) continue;
         if (set_stencil_variant(ctx, v) != cudaSuccess) { st = SDC_ERR_CUDA; break; }
         float a, b;
         st = trial(&a, &b);
@@ -924,6 +967,7 @@ sdc_status sdc_set_variants(sdc_ctx* ctx, int stencil_variant, int newton_varian
     if (!ctx || stencil_variant < 0 || stencil_variant >= stencil_variants(ctx->dim, ctx->nspec) ||
         newton_variant < 0 || newton_variant >= newton_variants(ctx->nspec, ctx->P.topo))
         return SDC_ERR_INVALID_ARG;
+    if (stencil_variant == stencil_split_variant(ctx->dim, ctx->nspec) && !ctx->prim) return SDC_ERR_INVALID_ARG;
     SDC_TRY(set_stencil_variant(ctx, stencil_variant));
     ctx->newton_variant = newton_variant;
     drop_graphs(ctx);
@@ -943,6 +987,12 @@ sdc_status sdc_launches_per_step(const sdc_ctx* ctx, int* launches) {
         return SDC_OK;
     }
     *launches = 3 + ctx->K * 2 * (ctx->M - 1) + (ctx->K - 1);
+    if (ctx->stencil_variant == stencil_split_variant(ctx->dim, ctx->nspec)) {
+        // three passes per advective term: A(U^n), the fused rhs at nodes 1..M-2,
+        // and A at the last node for every iteration but the last
+        const int evals = 1 + ctx->K * (ctx->M - 2) + (ctx->K - 1);
+        *launches += 2 * evals;
+    }
     return SDC_OK;
 }
 
@@ -1245,6 +1295,7 @@ extern "C" sdc_status sdc_step_static(const sdc_box* boxes, int nbox, const sdc_
     P.topo = topo;
     P.gamma = prm->gamma;
     P.gm1 = prm->gamma - 1.0;
+    P.gm1_inv = 1.0 / P.gm1;
     for (int i = 0; i < net->nspec; i++) {
         P.mass[i] = net->mass[i];
         P.inv_mass[i] = 1.0 / net->mass[i];

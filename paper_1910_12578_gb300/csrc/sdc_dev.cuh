@@ -28,6 +28,7 @@ enum { ZONE_OK = 0, ZONE_MAXIT = 1, ZONE_NONPHYSICAL = 2, ZONE_SINGULAR = 3 };
 struct NetParams {
     int nspec, nreac, law, topo;
     double gm1;                          // gamma - 1
+    double gm1_inv;                      // 1 / (gamma - 1)
     double gamma;
     double mass[SDCD_MAXS];
     double inv_mass[SDCD_MAXS];

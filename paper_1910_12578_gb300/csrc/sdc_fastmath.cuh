@@ -78,8 +78,10 @@ __device__ __forceinline__ unsigned int mag2(float x) { return (unsigned int)__f
 // from the plain formula by less than 2^-1022 in absolute value.  The plain
 // formula's dl*dr test also reads zero when the product underflows; here only
 // the signs decide.  Everywhere else the two agree exactly.
-__device__ __forceinline__ double mc_half_slope(int limiter, double qm, double q0, double qp) {
-    const double dl = q0 - qm, dr = qp - q0, s = dl + dr;
+// The same from the two one-sided differences dl = q0 - qm and dr = qp - q0
+// (a pass that forms each difference once per face passes them in).
+__device__ __forceinline__ double mc_half_slope_d(int limiter, double dl, double dr) {
+    const double s = dl + dr;
     if (!limiter) return 0.25 * s;
     const long long bl = dbits(dl), br = dbits(dr), bs = dbits(s);
     // magnitudes as bit patterns shifted left by one (mag2)
@@ -90,6 +92,10 @@ __device__ __forceinline__ double mc_half_slope(int limiter, double qm, double q
     unsigned long long lim = al < ar ? al : ar;
     lim = lim < q ? lim : q;
     return bitsd((long long)(lim >> 1) | (bs & SIGN_BIT));
+}
+
+__device__ __forceinline__ double mc_half_slope(int limiter, double qm, double q0, double qp) {
+    return mc_half_slope_d(limiter, q0 - qm, qp - q0);
 }
 
 }  // namespace sdcd

@@ -13,6 +13,8 @@ bool newton_supported(int nspec, int topo);
 bool stencil_supported(int dim, int nspec);
 cudaError_t newton_prepare(int nspec, int topo);  // raise the dynamic shared-memory limit
 int stencil_variants(int dim, int nspec);  // tile shapes available to the autotuner
+int stencil_split_variant(int dim, int nspec);  // the direction-split passes' variant, or -1
+void split_tile_shape(int D, int t[3]);          // zones of one tile of pass D along x, y, z
 void stencil_tile(int dim, int nspec, int variant, int t[3]);
 size_t stencil_smem_bytes(int dim, int nspec, int variant);
 cudaError_t stencil_prepare(int dim, int nspec);  // raise the dynamic shared-memory limit
@@ -38,5 +40,10 @@ cudaError_t launch_reaction_source(const NetParams& P, long long N, int dim, con
 cudaError_t launch_stencil(const NetParams& P, int dim, int limiter, long long Ntot, const BoxDev* boxes,
                            const TileDev* tiles, int ntiles, const double* U, double* A, int mode,
                            const RhsArgs& ra, cudaStream_t st, int variant = 0);
+// the direction-split passes (3D): tiles[D] / ntiles[D] of pass D; prim is a
+// field-major [nvar][Ntot] buffer for the primitives
+cudaError_t launch_stencil_split(const NetParams& P, int limiter, long long Ntot, const BoxDev* boxes,
+                                 const TileDev* const* tiles, const int* ntiles, const double* U, double* prim,
+                                 double* A, int mode, const RhsArgs& ra, cudaStream_t st);
 
 }  // namespace sdcd

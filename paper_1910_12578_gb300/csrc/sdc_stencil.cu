@@ -1,6 +1,7 @@
 // sdc_stencil.cu -- instantiations and launch of the advective-term kernel
 // (paper section 2, Eq. 1) with the fused right-hand side of Eq. sdc:general.
 #include "sdc_launch.h"
+#include "sdc_stencil_split.cuh"
 
 namespace sdcd {
 
@@ -30,7 +31,11 @@ constexpr size_t smem_bytes() {
     return sizeof(double) * (size_t)(2 + DIM + NS) * (G::NC + G::NB);
 }
 
-int stencil_variants(int dim, int nspec) { return (dim == 3 && nspec <= 7) ? 2 : 1; }
+// 3D: the tile shapes, then the direction-split passes (stencil_split_kernel)
+// as the last variant
+int stencil_variants(int dim, int nspec) { return dim == 3 ? (nspec <= 7 ? 3 : 2) : 1; }
+
+int stencil_split_variant(int dim, int nspec) { return dim == 3 ? stencil_variants(dim, nspec) - 1 : -1; }
 
 bool stencil_supported(int dim, int nspec) {
 #define X(d, ns) \
@@ -44,8 +49,11 @@ void stencil_tile(int dim, int nspec, int variant, int t[3]) {
     t[0] = 64; t[1] = 1; t[2] = 1;
 #define X(d, ns)                                                                                   \
     if (dim == d && nspec == ns) {                                                                 \
-        if (variant == 0) { t[0] = Tile<d, ns, 0>::X; t[1] = Tile<d, ns, 0>::Y; t[2] = Tile<d, ns, 0>::Z; } \
-        else { t[0] = Tile<d, ns, 1>::X; t[1] = Tile<d, ns, 1>::Y; t[2] = Tile<d, ns, 1>::Z; }     \
+        if (variant == 1 && variant != stencil_split_variant(d, ns)) {                             \
+            t[0] = Tile<d, ns, 1>::X; t[1] = Tile<d, ns, 1>::Y; t[2] = Tile<d, ns, 1>::Z;          \
+        } else {                                                                                   \
+            t[0] = Tile<d, ns, 0>::X; t[1] = Tile<d, ns, 0>::Y; t[2] = Tile<d, ns, 0>::Z;          \
+        }                                                                                          \
     }
     SDC_STENCIL_CASES(X)
 #undef X
@@ -53,7 +61,7 @@ void stencil_tile(int dim, int nspec, int variant, int t[3]) {
 
 size_t stencil_smem_bytes(int dim, int nspec, int variant) {
 #define X(d, ns) \
-    if (dim == d && nspec == ns) return variant == 0 ? smem_bytes<d, ns, 0>() : smem_bytes<d, ns, 1>();
+    if (dim == d && nspec == ns) return variant == 1 ? smem_bytes<d, ns, 1>() : smem_bytes<d, ns, 0>();
     SDC_STENCIL_CASES(X)
 #undef X
     return 0;
@@ -69,14 +77,93 @@ cudaError_t prepare_one() {
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<d, ns, V>());
 }
 
+// the direction-split passes (3D): x pass (reads U, writes the primitives),
+// y pass, z pass (finishes A, with or without the rhs)
+#define SDC_SPLIT_CASES(X) \
+    X(2)                   \
+    X(3)                   \
+    X(4)                   \
+    X(5)                   \
+    X(7)                   \
+    X(13)
+
+template <int ns, int D, bool FIRST, bool LAST, int MODE>
+cudaError_t prepare_split_one() {
+    return cudaFuncSetAttribute(stencil_split_kernel<ns, D, FIRST, LAST, MODE>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_smem_bytes<ns, D>());
+}
+
+template <int ns>
+cudaError_t prepare_split() {
+    cudaError_t e;
+    if ((e = prepare_split_one<ns, 0, true, false, STENCIL_A>()) != cudaSuccess) return e;
+    if ((e = prepare_split_one<ns, 1, false, false, STENCIL_A>()) != cudaSuccess) return e;
+    if ((e = prepare_split_one<ns, 2, false, true, STENCIL_A>()) != cudaSuccess) return e;
+    return prepare_split_one<ns, 2, false, true, STENCIL_A_RHS>();
+}
+
 cudaError_t stencil_prepare(int dim, int nspec) {
-#define X(d, ns)                                                     \
-    if (dim == d && nspec == ns) {                                   \
-        cudaError_t e = prepare_one<d, ns, 0>();                     \
-        if (e != cudaSuccess || stencil_variants(d, ns) < 2) return e; \
-        return prepare_one<d, ns, 1>();                              \
+    cudaError_t e = cudaErrorInvalidValue;
+#define X(d, ns)                                                          \
+    if (dim == d && nspec == ns) {                                        \
+        e = prepare_one<d, ns, 0>();                                      \
+        if (e == cudaSuccess && stencil_variants(d, ns) > 1 && stencil_split_variant(d, ns) != 1) \
+            e = prepare_one<d, ns, 1>();                                  \
     }
     SDC_STENCIL_CASES(X)
+#undef X
+    if (e != cudaSuccess || dim != 3) return e;
+#define X(ns) \
+    if (nspec == ns) return prepare_split<ns>();
+    SDC_SPLIT_CASES(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+void split_tile_shape(int D, int t[3]) {
+    t[0] = t[1] = t[2] = 1;
+    const int L = D == 0 ? SplitShape<0>::L : (D == 1 ? SplitShape<1>::L : SplitShape<2>::L);
+    const int NL = D == 0 ? SplitShape<0>::NL : (D == 1 ? SplitShape<1>::NL : SplitShape<2>::NL);
+    t[D] = L;
+    t[D == 0 ? 1 : 0] = NL;
+}
+
+template <int ns>
+cudaError_t launch_split(const NetParams& P, int limiter, long long Ntot, const BoxDev* boxes,
+                         const TileDev* const* tiles, const int* ntiles, const double* U, double* prim, double* A,
+                         int mode, const RhsArgs& ra, cudaStream_t st) {
+    RhsArgs none = ra;
+    if (ntiles[0] > 0)
+        stencil_split_kernel<ns, 0, true, false, STENCIL_A>
+            <<<ntiles[0], SplitGeom<0>::THREADS, split_smem_bytes<ns, 0>(), st>>>(P, limiter, Ntot, boxes, tiles[0],
+                                                                                  U, prim, A, none);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (ntiles[1] > 0)
+        stencil_split_kernel<ns, 1, false, false, STENCIL_A>
+            <<<ntiles[1], SplitGeom<1>::THREADS, split_smem_bytes<ns, 1>(), st>>>(P, limiter, Ntot, boxes, tiles[1],
+                                                                                  U, prim, A, none);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ntiles[2] > 0) {
+        if (mode == STENCIL_A_RHS)
+            stencil_split_kernel<ns, 2, false, true, STENCIL_A_RHS>
+                <<<ntiles[2], SplitGeom<2>::THREADS, split_smem_bytes<ns, 2>(), st>>>(P, limiter, Ntot, boxes,
+                                                                                      tiles[2], U, prim, A, ra);
+        else
+            stencil_split_kernel<ns, 2, false, true, STENCIL_A>
+                <<<ntiles[2], SplitGeom<2>::THREADS, split_smem_bytes<ns, 2>(), st>>>(P, limiter, Ntot, boxes,
+                                                                                      tiles[2], U, prim, A, none);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stencil_split(const NetParams& P, int limiter, long long Ntot, const BoxDev* boxes,
+                                 const TileDev* const* tiles, const int* ntiles, const double* U, double* prim,
+                                 double* A, int mode, const RhsArgs& ra, cudaStream_t st) {
+    if (!prim) return cudaErrorInvalidValue;
+#define X(ns) \
+    if (P.nspec == ns) return launch_split<ns>(P, limiter, Ntot, boxes, tiles, ntiles, U, prim, A, mode, ra, st);
+    SDC_SPLIT_CASES(X)
 #undef X
     return cudaErrorInvalidValue;
 }
@@ -101,9 +188,9 @@ cudaError_t launch_stencil(const NetParams& P, int dim, int limiter, long long N
     if (ntiles <= 0) return cudaSuccess;
 #define X(d, ns)                                                                                      \
     if (dim == d && P.nspec == ns) {                                                                  \
-        if (variant == 0 || stencil_variants(d, ns) < 2)                                              \
-            return launch_one<d, ns, 0>(P, limiter, Ntot, boxes, tiles, ntiles, U, A, mode, ra, st);  \
-        return launch_one<d, ns, 1>(P, limiter, Ntot, boxes, tiles, ntiles, U, A, mode, ra, st);      \
+        if (variant == 1 && stencil_split_variant(d, ns) != 1)                                       \
+            return launch_one<d, ns, 1>(P, limiter, Ntot, boxes, tiles, ntiles, U, A, mode, ra, st);  \
+        return launch_one<d, ns, 0>(P, limiter, Ntot, boxes, tiles, ntiles, U, A, mode, ra, st);      \
     }
     SDC_STENCIL_CASES(X)
 #undef X

@@ -183,7 +183,7 @@ stencil_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __restric
     const int ex = min(TX, b.n[0] - t.o[0]);
     const int ey = DIM >= 2 ? min(TY, b.n[1] - t.o[1]) : 1;
     const int ez = DIM >= 3 ? min(TZ, b.n[2] - t.o[2]) : 1;
-    const double g = P.gamma, gm1 = P.gm1, gm1_inv = rcp_nr(P.gm1);
+    const double g = P.gamma, gm1 = P.gm1, gm1_inv = P.gm1_inv;
 
     // ---- stage primitives of the tile and its cross-shaped halo
     for (int s = threadIdx.x; s < G::NC; s += blockDim.x) {

@@ -217,10 +217,11 @@ def config_sod(n: int = 128, dim: int = 1, axis: int = 0, nspec: int = 7, seed: 
 
 
 def batched_boxes(nbox: int = 200, nspec: int = 7, seed: int = 0,
-                  edges=(16, 24, 32, 48, 64)) -> tuple:
+                  edges=(16, 24, 32, 48, 64), T0: float = 1.0) -> tuple:
     """Ragged batch: per box, edges drawn from `edges` per axis, hot-spot
-    amplitude ~ U[1.2, 3]; dx = 1/64; every box periodic on itself.
-    The network is drawn first from the same seed."""
+    amplitude ~ U[1.2, 3] over the background temperature T0; dx = 1/64;
+    every box periodic on itself.  The network is drawn first from the same
+    seed."""
     rng = np.random.default_rng(seed)
     net = alpha_chain(nspec, rng)
     boxes = []
@@ -230,5 +231,5 @@ def batched_boxes(nbox: int = 200, nspec: int = 7, seed: int = 0,
         h = 1.0 / 64
         P = Problem(dim=3, n=tuple(e), dx=(h, h, h), gamma=5.0 / 3.0, net=net,
                     n_nodes=3, n_iters=3)
-        boxes.append((P, hot_spot_state(P, amp), amp))
+        boxes.append((P, hot_spot_state(P, amp, T0=T0), amp))
     return net, boxes

@@ -27,8 +27,17 @@ inside the step), with a floor on how many samples qualify.
 
 Differences: fourth order, (8 (f(h) - f(-h)) - (f(2h) - f(-2h))) / 12h; with
 relative steps 1e-4 (released energy) and 1e-6 (weighted state) both truncation
-and round-off stay far below the 1e-6 tolerance.  The plain central difference
-at h = 1e-6 is also checked, at the 1e-4 its round-off allows."""
+and round-off stay far below the 1e-6 tolerance.
+
+The released energy is also taken in its binding-energy form,
+L_b = dV sum_zones sum_i b_i (rho Y_i(t_f) - rho Y_i(t_0)) with
+sum_i b_i s_ij = Q_j: total energy less the binding energy is conserved, so
+L_b equals L, but it is a sum of the products' masses and does not cancel
+(L is a difference of two sums of rho E, whose round-off, about eps sum |rho E|,
+divided by the step of a difference, caps the plain central difference at h =
+1e-6 near 1e-4).  With L_b the plain central difference at the relative step
+h = 1e-6 agrees with the adjoint to 1e-6, for the rate prefactors and for the
+initial temperature."""
 import copy
 
 import numpy as np
@@ -122,6 +131,20 @@ def released(P, U0, U1):
     return dV * np.sum(U1[4] - U0[4])
 
 
+def binding_weights(P):
+    """dV b_i / mass_i per reactive species field: L_b = sum_i w_i sum_z rho X_i."""
+    dV = P.dx[0] * P.dx[1] * P.dx[2]
+    return dV * P.net.binding() / np.asarray(P.net.mass, dtype=np.float64)
+
+
+def released_binding(P, U0, U1):
+    """The released energy from the binding energies of the species made."""
+    w = binding_weights(P)
+    s = 2 + P.dim
+    d = (U1[s:s + P.net.nspec] - U0[s:s + P.net.nspec]).reshape(P.net.nspec, -1).sum(1)
+    return float(np.sum(w * d))
+
+
 def fd(f, x, h):
     return (8.0 * (f(x + h) - f(x - h)) - (f(x + 2 * h) - f(x - 2 * h))) / (12.0 * h)
 
@@ -182,6 +205,18 @@ class OracleModel:
 def released_loss(P):
     dV = P.dx[0] * P.dx[1] * P.dx[2]
     return lambda U0, U: dV * (U[4] - U0[4]).sum()
+
+
+def binding_loss(P):
+    w = binding_weights(P)
+    s = 2 + P.dim
+
+    def f(U0, U):
+        import torch
+        wt = torch.tensor(w, dtype=torch.float64, device=U.device)
+        d = (U[s:s + P.net.nspec] - U0[s:s + P.net.nspec]).reshape(P.net.nspec, -1).sum(1)
+        return (wt * d).sum()
+    return f
 
 
 def T_gradient(P, U0, gU0):
@@ -317,15 +352,23 @@ def test_rate_gradient_hot_spot(torch_cuda, n, nsteps, limiter, nodes):
     assert L == pytest.approx(released(P, U0, model.run(U0, a)), rel=1e-12)
     d_rel, d_yield = rate_differences(model.run, P, U0, a)
     err_rel, err_y = rate_errors(ga, d_rel, J, d_yield)
-    j0 = int(np.argmax(np.abs(d_rel)))
-    e0 = np.zeros_like(a); e0[j0] = 1.0
-    d_plain = fd_plain(lambda s: released(P, U0, model.run(U0, a + s * e0)), 0.0, H_PLAIN * a[j0])
+    # the binding-energy form: the same quantity, and the plain central
+    # difference at h = 1e-6 for every prefactor
+    Lb, _, gb = model.grad(U0, a, binding_loss(P))
+    d_plain = []
+    for k in range(len(a)):
+        e = np.zeros_like(a); e[k] = 1.0
+        d_plain.append(fd_plain(lambda s: released_binding(P, U0, model.run(U0, a + s * e)), 0.0, H_PLAIN * a[k]))
+    d_plain = np.array(d_plain)
+    err_plain = np.abs(gb - d_plain).max() / np.abs(d_plain).max()
     print("rate gradients vs FD: released", err_rel, "yields (max per row)", err_y.max(axis=1),
-          "plain h=1e-6:", abs(ga[j0] - d_plain) / abs(d_plain))
+          "binding form, plain h=1e-6:", err_plain, "binding vs rho E form", np.abs(gb - ga).max() / np.abs(ga).max())
     assert np.isfinite(ga).all() and np.isfinite(J).all()
     assert err_rel <= TOL
     assert err_y.max() <= TOL
-    assert abs(ga[j0] - d_plain) <= 1e-4 * abs(d_plain)
+    assert Lb == pytest.approx(L, rel=1e-9)
+    assert np.abs(gb - ga).max() <= TOL * np.abs(ga).max()
+    assert err_plain <= TOL
 
 
 @pytest.mark.parametrize("n,nsteps", [(8, 2), (32, 5)])
@@ -351,9 +394,22 @@ def test_temperature_gradient_hot_spot_unlimited(torch_cuda, n, nsteps):
     v = rng.choice([-1.0, 1.0], size=T.shape) * T
     d = fd(lambda s: loss(T + s * v), 0.0, H)
     err_dir = abs(float(np.sum(gT * v)) - d) / abs(d)
-    print("temperature gradient vs FD:", err, "direction", err_dir)
+    # the binding-energy form with the plain central difference at h = 1e-6
+    _, gUb, _ = model.grad(U0, a, binding_loss(P))
+    gTb = T_gradient(P, U0, gUb)
+    loss_b = lambda Tx: released_binding(P, state_from_T(P, Tx), model.run(state_from_T(P, Tx), a))
+    scale_b = np.abs(gTb).max()
+    err_b = []
+    for z in zones:
+        e = np.zeros_like(T); e[z] = 1.0
+        err_b.append(abs(gTb[z] - fd_plain(lambda s: loss_b(T + s * e), 0.0, H_PLAIN * T[z])) / scale_b)
+    d_b = fd_plain(lambda s: loss_b(T + s * v), 0.0, H_PLAIN)
+    err_dir_b = abs(float(np.sum(gTb * v)) - d_b) / abs(d_b)
+    print("temperature gradient vs FD:", err, "direction", err_dir, "binding form, plain h=1e-6:", err_b, err_dir_b)
     assert max(err) <= TOL
     assert err_dir <= TOL
+    assert max(err_b) <= TOL
+    assert err_dir_b <= TOL
 
 
 def _sampled_state_gradient(model, P, U0, a, g, nsamples, seed):

@@ -335,16 +335,20 @@ def test_table_driven_power_law_rate_factor(torch_cuda):
     assert sp[1] == np.inf and sp[2] == 0.0 and sp[3] == 1.0
 
 
-@pytest.mark.parametrize("name", ["box16", "ragged"])
+@pytest.mark.parametrize("name", ["box16", "ragged", "box16_13"])
 def test_kernel_variants_agree_bitwise(torch_cuda, name):
-    """The queue-fed persistent Newton kernels (per lane and per warp) and the
-    8x8x4 tile shape do the same arithmetic per zone and per face as the
-    defaults: identical results."""
+    """The queue-fed persistent Newton kernels (per lane and per warp), the
+    8x8x4 tile shape and the direction-split stencil passes (the last stencil
+    variant) do the same arithmetic per zone and per face as the defaults:
+    identical results."""
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
     P, U = PROBS[name]
     outs = []
-    for sv, nv in ((0, 0), (0, 1), (0, 2), (1, 0), (1, 1), (1, 2)):
+    pairs = ((0, 0), (0, 1), (0, 2), (1, 0), (1, 1), (1, 2), (2, 0), (2, 1))
+    if P.net.nspec == 13:
+        pairs = ((0, 2), (0, 3), (1, 2), (1, 4))   # 8x8x4 tiles or split passes; thread-per-zone Newton
+    for sv, nv in pairs:
         ctx = sdc.Context(P)
         ctx.set_variants(sv, nv)
         Ud = dev(torch, U)
@@ -442,7 +446,7 @@ def test_autotune_keeps_U_and_picks_valid_variants(torch_cuda):
     t = ctx.autotune(Ud, 1e-3)
     torch.cuda.synchronize()
     assert np.array_equal(Ud.cpu().numpy(), U.reshape(Ud.shape))
-    assert 0 <= t.stencil_choice < t.stencil_variants == 2
+    assert 0 <= t.stencil_choice < t.stencil_variants == 3   # 8^3, 8x8x4, direction-split passes
     assert 0 <= t.newton_choice < t.newton_variants == 4   # static grid, lane queue, warp queue, 4-lane groups
     assert all(x > 0 for x in t.as_dict()["ms_newton"])
     o = O.Oracle(P)
@@ -475,8 +479,10 @@ def test_cfl_dt_matches_oracle(torch_cuda):
         assert ctx.cfl_dt(dev(torch, U), 0.5) == pytest.approx(o.cfl_dt(U, 0.5), rel=1e-14)
 
 
-def test_batched_boxes_match_per_box_oracle(torch_cuda):
-    """Ragged boxes in one context: each box equals the oracle run on it alone."""
+@pytest.mark.parametrize("stencil_variant", [0, 2])
+def test_batched_boxes_match_per_box_oracle(torch_cuda, stencil_variant):
+    """Ragged boxes in one context: each box equals the oracle run on it alone
+    (8^3 tiles, or the direction-split passes with partial lines)."""
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
     net, boxes = W.batched_boxes(nbox=4, nspec=7, seed=3, edges=(8, 16, 24))
@@ -486,6 +492,7 @@ def test_batched_boxes_match_per_box_oracle(torch_cuda):
     Ucat = np.concatenate([b[1].reshape(P.nvar, -1) for P, b in zip(Ps, boxes)], axis=1)
     dt = min(O.Oracle(P).cfl_dt(b[1]) for P, b in zip(Ps, boxes))
     ctx = sdc.Context(Ps)
+    ctx.set_variants(stencil_variant, 0)
     Ud = dev(torch, Ucat)
     ctx.step(Ud, dt)
     torch.cuda.synchronize()
@@ -499,13 +506,14 @@ def test_batched_boxes_match_per_box_oracle(torch_cuda):
         off += nz
 
 
-@pytest.mark.parametrize("space_order", [2, 4])
-def test_tiny_boxes_match_per_box_oracle(torch_cuda, space_order):
+@pytest.mark.parametrize("space_order,split", [(2, False), (2, True), (4, False)])
+def test_tiny_boxes_match_per_box_oracle(torch_cuda, space_order, split):
     """Boxes narrower than the tile and than the 2-zone halo (edges 1, 2, 3, 5;
     the periodic halo wraps onto the box itself, several times for the limited
     fourth-order stencil's two zones each side), with seeded flow in every
     direction, in one context: each box equals the oracle run on it alone over
-    two steps."""
+    two steps.  split: the direction-split stencil passes, whose lines are
+    longer than these boxes."""
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
     rng = np.random.default_rng(21)
@@ -525,6 +533,8 @@ def test_tiny_boxes_match_per_box_oracle(torch_cuda, space_order):
         Us.append(U)
     dt = min(O.Oracle(P).cfl_dt(U) for P, U in zip(Ps, Us))
     ctx = sdc.Context(Ps)
+    if split:
+        ctx.set_variants(2, 0)
     Ud = dev(torch, np.concatenate([U.reshape(P.nvar, -1) for P, U in zip(Ps, Us)], axis=1))
     for _ in range(2):
         st = ctx.step(Ud, dt)
