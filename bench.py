@@ -74,6 +74,9 @@ def parse():
     p.add_argument("--nodes", choices=["lobatto", "radau", "radau4"], default="lobatto",
                    help="temporal node set: Gauss-Lobatto (trapezoid/Simpson), node 0 + the Radau IIA points "
                         "1/3, 1, or (radau4) node 0 + the three Radau IIA points of s = 3")
+    p.add_argument("--batch-T0", type=float, default=1.0,
+                   help="background temperature of the batched boxes (1.15: a stiffer batch, 2-21 Newton "
+                        "iterations per zone in its first step)")
     p.add_argument("--seed", type=int, default=None,
                    help="network / box seed (default: 1 for the single boxes, 3 for the batch)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -91,16 +94,16 @@ def space_desc(args):
     return "" if args.limiter else "; unlimited centred slopes"
 
 
-def workload(name, seed, nodes="lobatto"):
+def workload(name, seed, nodes="lobatto", batch_T0=1.0):
     """(problems, initial state, description): a Problem and its U, or for the
     batched workload a list of Problems and the concatenated U."""
     if name == "batch200":
         import numpy as np
-        net, boxes = W.batched_boxes(nbox=200, nspec=7, seed=seed)
+        net, boxes = W.batched_boxes(nbox=200, nspec=7, seed=seed, T0=batch_T0)
         Ps = [b[0] for b in boxes]
         U = np.concatenate([b[1].reshape(b[0].nvar, -1) for b in boxes], axis=1)
         desc = ("200 ragged periodic boxes (edges from {16,24,32,48,64} per axis, dx=1/64), 7-species alpha chain "
-                "(seeded), hot spots 1.2-3x over T0=0.5, 3 Gauss-Lobatto nodes, 3 SDC iterations, CFL 0.5")
+                "(seeded), hot spots 1.2-3x over T0=%g, 3 Gauss-Lobatto nodes, 3 SDC iterations, CFL 0.5" % batch_T0)
         for p in Ps:
             _set_nodes(p, nodes)
         return Ps, U, _nodes_desc(desc, nodes)
@@ -339,7 +342,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle as O
-    P, U, desc = workload(args.config, args.seed, args.nodes)
+    P, U, desc = workload(args.config, args.seed, args.nodes, args.batch_T0)
     for p_ in as_list(P):
         p_.space_order, p_.limiter = args.space_order, args.limiter
     desc += space_desc(args)
@@ -585,7 +588,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if not os.path.exists(sdc.LIB_PATH):
         B.build()
-    P, U, desc = workload(args.config, rank_seed(args.seed, rank), args.nodes)
+    P, U, desc = workload(args.config, rank_seed(args.seed, rank), args.nodes, args.batch_T0)
     for p_ in as_list(P):
         p_.space_order, p_.limiter = args.space_order, args.limiter
     desc += space_desc(args)

@@ -195,7 +195,7 @@ typedef struct {
    measurement.  Waits for the stream.  stats as in sdc_step. */
 sdc_status sdc_step_profile(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats, sdc_profile* prof);
 
-/* Diagnostic: the library's Newton-Raphson reciprocal and square root (used
+/* Diagnostic: the library's refined reciprocal and square root (used
    inside its kernels in place of IEEE division and sqrt) for n positive normal
    doubles x (device arrays), for testing against correctly rounded results. */
 sdc_status sdc_selftest_math(const double* x, long long n, double* rcp_out, double* sqrt_out, void* cuda_stream);

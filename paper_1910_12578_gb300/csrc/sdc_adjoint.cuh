@@ -168,7 +168,7 @@ __device__ __forceinline__ void face_flux_vjp(double gamma, int limiter, int dir
     constexpr int IE = 1 + DIM, IX = 2 + DIM;
     const double gm1 = gamma - 1.0, igm1 = rcp_nr(gm1);
     // ---------------- forward: primitives of the four zones
-    // (reciprocals and square roots by the Newton-Raphson forms of the forward kernel)
+    // (reciprocals and square roots by the refined forms of the forward kernel)
     double q[4][NV], irz[4];
 #pragma unroll
     for (int z = 0; z < 4; z++) {

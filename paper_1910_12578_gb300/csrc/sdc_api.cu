@@ -999,6 +999,7 @@ sdc_status sdc_launches_per_step(const sdc_ctx* ctx, int* launches) {
 sdc_status sdc_set_rates(sdc_ctx* ctx, const double* a) {
     if (!ctx || !a) return SDC_ERR_INVALID_ARG;
     for (int j = 0; j < ctx->P.nreac; j++) ctx->P.a[j] = a[j];
+    set_chain_coefs(ctx->P);  // the chain's prefactors a_j / prod mass
     drop_graphs(ctx);  // the captured graphs hold the old constants
     return SDC_OK;
 }

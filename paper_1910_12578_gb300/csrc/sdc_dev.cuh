@@ -3,8 +3,8 @@
 // their Jacobian, and the dense pivoted LU of the implicit reaction update.
 //
 // Paper: arXiv:1910.12578, section 2 (Eq. 1, Eq. sdc:general).  The network,
-// EOS and Newton globalisation are the readings stated in sdc.h / the design
-// notes: r_j = a_j rho^(o_j-1) f_j(T) prod Y^cnt, p = rho T, e = T/(gamma-1).
+// EOS and Newton globalisation are the readings stated in sdc.h:
+// r_j = a_j rho^(o_j-1) f_j(T) prod Y^cnt, p = rho T, e = T/(gamma-1).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -35,6 +35,9 @@ struct NetParams {
     double a[SDCD_MAXR], nu[SDCD_MAXR], Q[SDCD_MAXR];
     int r0[SDCD_MAXR], c0[SDCD_MAXR], r1[SDCD_MAXR], c1[SDCD_MAXR], prod[SDCD_MAXR];
     int order[SDCD_MAXR];                // sum of reactant multiplicities
+    // alpha chain: a_j / prod_reactants mass (with multiplicity), so that
+    // r_j = (amp_j / rho) f_j(T) prod_reactants (rho X)^count
+    double amp[SDCD_MAXR];
     // alpha chain: reaction j's share of the Newton matrix, per row (E, X_0, the
     // consumed X_j, the product X_{j+1}) and column (E, X_0, X_j); see build_chain
     double kc[SDCD_MAXR][12];
@@ -42,40 +45,46 @@ struct NetParams {
 };
 
 // Coefficients of build_chain from the masses and energies of the alpha chain
-// (j = 0: 3 A_0 -> A_1; j >= 1: A_j + A_0 -> A_{j+1}).  Row i of dR/dw takes
-// rho * (Q_j or mass_i * s_ij) * dr_j/dw; with dr_j/d(rho X_c) = k_j dP_j/dY_c /
-// (rho mass_c) and dr_j/d(rho E) = f'_j(T)/f_j(T) k_j P_j (gamma-1)/rho, the
-// density cancels: entry (i, c) gains  -(Q_j or mass_i s_ij) / mass_c times
-// dt_m k_j dP_j/dY_c, and entry (i, E) gains -(Q_j or mass_i s_ij) times
-// dt_m (gamma-1) dk_j P_j = nu_j dt_m (gamma-1) f k_j P_j (dk_j/dT = nu_j k_j f,
+// (j = 0: 3 A_0 -> A_1; j >= 1: A_j + A_0 -> A_{j+1}), and the prefactors amp.
+// In terms of the unknowns w (rho E, rho X_i) the rates are
+// r_j = kappa_j prod_reactants w^count with kappa_j = (amp_j / rho) f_j(T):
+// the species masses and the density of Y_i = w_i / (rho mass_i) are folded
+// into kappa_j.  Row i of dR/dw takes rho sigma_ij dr_j/dw (sigma_ij = Q_j in
+// the energy row, mass_i s_ij in species row i), so entry (i, c) of
+// M = c I - dt_m dR/dw gains -sigma_ij times dt_m rho kappa_j dP_j/dw_c
+// (P_j = prod w), and entry (i, E) gains -sigma_ij times
+// dt_m (gamma-1) f r_j nu_j (dr_j/d(rho E) = nu_j r_j f (gamma-1)/rho with
 // f = 1/T for the power law, 1/T^2 for the Arrhenius law).  For j = 0 the
-// factor 3 of dP_0/dY_0 = 3 Y_0^2 is folded into the X_0 column's
+// factor 3 of dP_0/dw_0 = 3 w_0^2 is folded into the X_0 column's
 // coefficients, and nu_j into the E column's.
 inline void set_chain_coefs(NetParams& P) {
-    for (int j = 0; j < SDCD_MAXR; j++)
+    for (int j = 0; j < SDCD_MAXR; j++) {
+        P.amp[j] = 0.0;
         for (int e = 0; e < 12; e++) P.kc[j][e] = 0.0;
+    }
     if (P.topo != TOPO_CHAIN) return;
     const double* m = P.mass;
     for (int j = 0; j < P.nreac; j++) {
+        P.amp[j] = j == 0 ? P.a[0] / (m[0] * m[0] * m[0]) : P.a[j] / (m[j] * m[0]);
         double* c = P.kc[j];
-        const double f0 = j == 0 ? 3.0 : 1.0;        // dP/dY_0 = f0 * (Y_0^2 or Y_j)
+        const double f0 = j == 0 ? 3.0 : 1.0;        // dP/dw_0 = f0 * (w_0^2 or w_j)
         const double s0 = j == 0 ? -3.0 : -1.0;      // stoichiometry of A_0
         // row E
         c[0] = P.Q[j];
-        c[1] = f0 * P.Q[j] / m[0];
-        c[2] = j == 0 ? 0.0 : P.Q[j] / m[j];
+        c[1] = f0 * P.Q[j];
+        c[2] = j == 0 ? 0.0 : P.Q[j];
         // row X_0
         c[3] = s0 * m[0];
-        c[4] = f0 * s0;
-        c[5] = j == 0 ? 0.0 : s0 * m[0] / m[j];
+        c[4] = f0 * s0 * m[0];
+        c[5] = j == 0 ? 0.0 : s0 * m[0];
         // row X_j (consumed; none for j = 0)
         c[6] = j == 0 ? 0.0 : -m[j];
-        c[7] = j == 0 ? 0.0 : -m[j] / m[0];
-        c[8] = j == 0 ? 0.0 : -1.0;
+        c[7] = j == 0 ? 0.0 : -m[j];
+        c[8] = j == 0 ? 0.0 : -m[j];
         // row X_{j+1} (made)
         c[9] = m[j + 1];
-        c[10] = f0 * m[j + 1] / m[0];
-        c[11] = j == 0 ? 0.0 : m[j + 1] / m[j];
+        c[10] = f0 * m[j + 1];
+        c[11] = j == 0 ? 0.0 : m[j + 1];
         // the E column's t_E carries dk_j / (k_j f) = nu_j (rate_consts_k)
         c[0] *= P.nu[j];
         c[3] *= P.nu[j];
@@ -303,15 +312,16 @@ struct ChainSys {
     MT dEE, dEA, dAE, dAA;  // M[E][E], M[E][X_0], M[X_0][E], M[X_0][X_0]
 };
 
-// Entries of ChainSys: M = c I - dt_m dR/dw from the rate constants, with the
-// per-reaction coefficients of set_chain_coefs (the density cancels).  With
-// P_j = Y_j Y_0 (P_0 = Y_0^3), reaction j contributes t_E = dt_m (gamma-1) f
-// k_j P_j to the E column (nu_j is in the coefficients; f from rate_consts_k),
-// t_A = dt_m k_j dP_j/dY_0 (without the factor 3 of j = 0) to the X_0 column
-// and t_J = dt_m k_j Y_0 to the X_j column.
+// Entries of ChainSys: M = c I - dt_m dR/dw from kappa_j and w, with the
+// per-reaction coefficients of set_chain_coefs.  With P_j = w_j w_0
+// (P_0 = w_0^3), reaction j contributes t_E = dt_m (gamma-1) f kappa_j P_j to
+// the E column (nu_j is in the coefficients; f from rate_consts_k),
+// t_A = dt_m rho kappa_j dP_j/dw_0 (without the factor 3 of j = 0) to the X_0
+// column and t_J = dt_m rho kappa_j w_0 to the X_j column.  ws = w_1.. (the
+// species part of w), dtr = dt_m rho.
 template <int NS, typename MT>
-__device__ __forceinline__ void build_chain(const NetParams& P, const double* k, double dfac, const double* Y,
-                                            double c, double dtm, ChainSys<NS, MT>& A) {
+__device__ __forceinline__ void build_chain(const NetParams& P, const double* k, double dfac, const double* ws,
+                                            double c, double dtm, double dtr, ChainSys<NS, MT>& A) {
     constexpr int NC = NS - 1;
     constexpr int NR = NS - 1;
 #pragma unroll
@@ -321,8 +331,8 @@ __device__ __forceinline__ void build_chain(const NetParams& P, const double* k,
     }
     A.dEE = A.dAA = (MT)c;
     A.dEA = A.dAE = (MT)0;
-    const MT dt_ = (MT)dtm, dg = (MT)(dtm * P.gm1 * dfac);
-    const MT y0 = (MT)Y[0];
+    const MT dt_ = (MT)dtr, dg = (MT)(dtm * P.gm1 * dfac);
+    const MT y0 = (MT)ws[0];
 #pragma unroll
     for (int j = 0; j < NR; j++) {
         const MT* cf;
@@ -337,7 +347,7 @@ __device__ __forceinline__ void build_chain(const NetParams& P, const double* k,
             A.dAE = fma(-cf[3], tE, A.dAE);   A.dAA = fma(-cf[4], tA, A.dAA);
             A.uE[0] = fma(-cf[9], tE, A.uE[0]); A.uA[0] = fma(-cf[10], tA, A.uA[0]);
         } else {
-            const MT yj = (MT)Y[j];
+            const MT yj = (MT)ws[j];
             const MT t = dt_ * (MT)k[j];
             const MT tE = dg * (MT)k[j] * (yj * y0);
             const MT tA = t * yj, tJ = t * y0;

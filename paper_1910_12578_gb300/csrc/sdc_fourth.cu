@@ -24,7 +24,7 @@
 // Every operator is a sequence of elementwise kernels over field-major arrays,
 // one thread per zone, periodic within each box.  GB300 issues FP64 at 2 lanes
 // per SM per clock, so even these stencils are bound by the FP64 pipe: the
-// kernels divide once per zone (a Newton-Raphson reciprocal) and multiply.
+// kernels divide once per zone (a refined hardware reciprocal) and multiply.
 #include "sdc_fourth_launch.h"
 #include "sdc_launch.h"
 
@@ -324,7 +324,7 @@ __device__ __forceinline__ void cs_zone(double amm, double am, double a0, double
                 fm = a0 + dm;
                 fp = a0 + dp;
             } else {
-                // in (0, 1); the Newton-Raphson reciprocal takes normal d2 only
+                // in (0, 1); the refined reciprocal takes normal d2 only
                 // (2^-1021 <= |d2| < 2^1022), the division the rest
                 const unsigned long long ex = mag2(d2) >> 53;
                 const double sc = (ex >= 2ull && ex < 2045ull) ? cm * rcp_nr(d2) : cm / d2;

@@ -31,10 +31,11 @@ struct ZoneEval {
 // operations of the definition, G = w - dt_m R(w) - rhs_w, and its scaled norm
 // times rho^2, phi = (G_E rho/|rhs_E|)^2 + sum_i G_i^2 (the solve only compares
 // norms of one zone, so the common factor 1/rho^2 of the scaled norm
-// (G_E/|rhs_E|)^2 + sum_i (G_i/rho)^2 is left out).  For the alpha chain only k_j and
-// the factor f of dk_j/dT = nu_j k_j f are formed (the matrix takes nu_j from
-// its coefficients); otherwise k_j and dk_j.  Returns false when T is not
-// positive and finite.
+// (G_E/|rhs_E|)^2 + sum_i (G_i/rho)^2 is left out).  For the alpha chain only
+// kappa_j = (amp_j / rho) f_j(T), whose products with the unknowns are the rates
+// (no Y_i), and the factor f of dkappa_j/dT = nu_j kappa_j f are formed (the
+// matrix takes nu_j from its coefficients); otherwise k_j, dk_j and Y_i.
+// Returns false when T is not positive and finite.
 // The order of doubles as signed integers (negative patterns reversed), for
 // comparisons on the integer pipe; -0 sorts below +0 and a nan above +inf.
 __device__ __forceinline__ long long ordered_bits(double x) {
@@ -58,14 +59,20 @@ __device__ __forceinline__ bool eval_state(const NetParams& P, double rho, doubl
     constexpr int NR = NS - 1;
     const double T = P.gm1 * (w[0] - ke) * inv_rho;
     if (!positive_finite(T)) return false;
-    if constexpr (TOPO == TOPO_CHAIN) rate_consts_k<NR>(P, ak, T, k, dfac);
-    else rate_consts<NR>(P, rho, T, k, dk);
-#pragma unroll
-    for (int i = 0; i < NS; i++) Y[i] = w[1 + i] * ym[i];
     // G = w - dt_m R(w) - rw with R(rho E) = rho RE and R(rho X_i) = rho mass_i S_i,
     // formed as (w - rw) - (dt_m rho) (mass_i S_i): one product fewer per row
     double S[NS], RE;
-    source_sums<NS, TOPO>(P, k, Y, S, RE);
+    if constexpr (TOPO == TOPO_CHAIN) {
+        // kappa_j = ak_j f_j(T) with the masses and density folded in: the rates
+        // are products of the unknowns themselves (no Y_i)
+        rate_consts_k<NR>(P, ak, T, k, dfac);
+        source_sums<NS, TOPO>(P, k, w + 1, S, RE);
+    } else {
+        rate_consts<NR>(P, rho, T, k, dk);
+#pragma unroll
+        for (int i = 0; i < NS; i++) Y[i] = w[1 + i] * ym[i];
+        source_sums<NS, TOPO>(P, k, Y, S, RE);
+    }
     const double dr = dtm * rho;
     G[0] = fma(-dr, RE, w[0] - rw[0]);
 #pragma unroll
@@ -84,8 +91,8 @@ struct ZoneState {
     static constexpr int N = NS + 1;
     static constexpr int NR = NS - 1;
     double rho, inv_rho, ke, wE, phi, h, dfac;
-    double ym[NS], lower[NS], rw[N], w[N], G[N], k[NR], dk[NR], Y[NS];
-    double ak[NR];  // a_j rho^(o_j - 1) (alpha chain)
+    double ym[NS], lower[NS], rw[N], w[N], G[N], k[NR], dk[NR], Y[NS];  // ym, dk, Y: general networks
+    double ak[NR];  // amp_j / rho (alpha chain: k holds kappa_j = ak_j f_j(T))
     int iters, status;
     bool newton, have_k, done;
     bool r_final;   // G holds R at the solution (set by the stop test's last step)
@@ -99,12 +106,13 @@ __device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, 
     S.rho = rho;
     S.inv_rho = rcp_nr(rho);
     S.ke = 0.5 * m2 * S.inv_rho;
-#pragma unroll
-    for (int i = 0; i < NS; i++) S.ym[i] = S.inv_rho * P.inv_mass[i];
     if constexpr (TOPO == TOPO_CHAIN) {
         constexpr int NR = NS - 1;
 #pragma unroll
-        for (int j = 0; j < NR; j++) S.ak[j] = P.a[j] * ipow_small(rho, P.order[j] - 1);
+        for (int j = 0; j < NR; j++) S.ak[j] = P.amp[j] * S.inv_rho;
+    } else {
+#pragma unroll
+        for (int i = 0; i < NS; i++) S.ym[i] = S.inv_rho * P.inv_mass[i];
     }
     S.wE = rho * rcp_nr(fabs(S.rw[0]));  // rho / |rhs_E|
     // a start without a positive temperature is replaced by rhs
@@ -171,7 +179,7 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     if constexpr (TOPO == TOPO_CHAIN) {
         // the chain's sparsity: bordered bidiagonal system, O(n) elimination
         ChainSys<NS, MT> A;
-        build_chain<NS, MT>(P, S.k, S.dfac, S.Y, c, dtm, A);
+        build_chain<NS, MT>(P, S.k, S.dfac, S.w + 1, c, dtm, dtm * S.rho, A);
         solved = chain_solve<NS, MT>(A, dv);
     } else {
         MT M[N][N];
@@ -192,9 +200,7 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     bool ok = true;
 #pragma unroll
     for (int i = 0; i < NS; i++) ok = ok && (ordered_bits(tr[1 + i]) >= ordered_bits(S.lower[i]));
-    // (NS <= 7: with 13 species the extra live arrays of this path cost more in
-    // register spills than the evaluation it saves)
-    if (NS <= 7 && S.newton && ok && newton_step_small<NS, MT>(S, cfg, dv, tr)) {
+    if (S.newton && ok && newton_step_small<NS, MT>(S, cfg, dv, tr)) {
         // The step meets the stop test, so an admissible trial (T positive and
         // finite, R finite) is the solution: only R at the trial is needed, not
         // the residual, its norm or the matrix's factor f.  Otherwise the full
@@ -205,12 +211,13 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
             if constexpr (TOPO == TOPO_CHAIN) {
                 double dff;
                 rate_consts_k<NR>(P, S.ak, T, kf, dff);
+                sources<NS, TOPO>(P, S.rho, kf, tr + 1, Rf);
             } else {
                 rate_consts<NR>(P, S.rho, T, kf, dkf);
-            }
 #pragma unroll
-            for (int i = 0; i < NS; i++) Yf[i] = tr[1 + i] * S.ym[i];
-            sources<NS, TOPO>(P, S.rho, kf, Yf, Rf);
+                for (int i = 0; i < NS; i++) Yf[i] = tr[1 + i] * S.ym[i];
+                sources<NS, TOPO>(P, S.rho, kf, Yf, Rf);
+            }
             bool finite = true;
 #pragma unroll
             for (int r = 0; r < N; r++) finite = finite && (((dbits(Rf[r]) >> 52) & 0x7ff) != 0x7ff);
@@ -253,9 +260,9 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
         } else {
 #pragma unroll
             for (int j = 0; j < NR; j++) S.dk[j] = dkt[j];
-        }
 #pragma unroll
-        for (int i = 0; i < NS; i++) S.Y[i] = Yt[i];
+            for (int i = 0; i < NS; i++) S.Y[i] = Yt[i];
+        }
         S.phi = phit;
         if (S.newton) {
             if (small) {
@@ -280,14 +287,21 @@ __device__ __forceinline__ void zone_source(const ZoneState<NS>& S, const NetPar
 #pragma unroll
         for (int r = 0; r < N; r++) Rout[r] = S.G[r];
     } else if (S.have_k) {
-        sources<NS, TOPO>(P, S.rho, S.k, S.Y, Rout);
+        if constexpr (TOPO == TOPO_CHAIN) sources<NS, TOPO>(P, S.rho, S.k, S.w + 1, Rout);
+        else sources<NS, TOPO>(P, S.rho, S.k, S.Y, Rout);
     } else {
         const double T = P.gm1 * (S.w[0] - S.ke) * S.inv_rho;
         double kf[NR], dkf[NR], Yf[NS];
-        rate_consts<NR>(P, S.rho, T, kf, dkf);
+        if constexpr (TOPO == TOPO_CHAIN) {
+            double dff;
+            rate_consts_k<NR>(P, S.ak, T, kf, dff);
+            sources<NS, TOPO>(P, S.rho, kf, S.w + 1, Rout);
+        } else {
+            rate_consts<NR>(P, S.rho, T, kf, dkf);
 #pragma unroll
-        for (int i = 0; i < NS; i++) Yf[i] = S.w[1 + i] * S.ym[i];
-        sources<NS, TOPO>(P, S.rho, kf, Yf, Rout);
+            for (int i = 0; i < NS; i++) Yf[i] = S.w[1 + i] * S.ym[i];
+            sources<NS, TOPO>(P, S.rho, kf, Yf, Rout);
+        }
     }
 }
 

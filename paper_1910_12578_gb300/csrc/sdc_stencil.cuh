@@ -15,8 +15,7 @@
 // a shared buffer, every face flux once (one face per thread when the tile is
 // a cube), the fluxes reuse the slope buffer, and each thread accumulates the
 // flux difference of its zones.  GB300 runs FP64 at 1/61 of its FP32 rate,
-// so divisions and square roots are Newton-Raphson refinements of hardware
-// approximations and the limiter works on bit patterns (sdc_fastmath.cuh).
+// so divisions and square roots are refinements of hardware approximations and the limiter works on bit patterns (sdc_fastmath.cuh).
 #pragma once
 #include "sdc_dev.cuh"
 #include "sdc_fastmath.cuh"

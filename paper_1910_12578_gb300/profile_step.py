@@ -24,10 +24,10 @@ if ROOT not in sys.path:
 from paper_1910_12578_gb300 import workloads as W  # noqa: E402
 
 
-def workload(name, seed):
+def workload(name, seed, batch_T0=1.0):
     import numpy as np
     if name == "batch200":
-        net, boxes = W.batched_boxes(nbox=200, nspec=7, seed=seed)
+        net, boxes = W.batched_boxes(nbox=200, nspec=7, seed=seed, T0=batch_T0)
         Ps = [b[0] for b in boxes]
         U = np.concatenate([b[1].reshape(b[0].nvar, -1) for b in boxes], axis=1)
         return Ps, U
@@ -51,13 +51,14 @@ def main(argv=None):
     p.add_argument("--limiter", type=int, choices=[0, 1], default=1)
     p.add_argument("--nodes", choices=["lobatto", "radau"], default="lobatto")
     p.add_argument("--backward", action="store_true", help="then one adjoint step (sdc_step_backward)")
+    p.add_argument("--batch-T0", type=float, default=1.0, help="background temperature of the batched boxes")
     a = p.parse_args(argv)
     seed = a.seed if a.seed is not None else (3 if a.config == "batch200" else 1)
 
     import torch
 
     from paper_1910_12578_gb300 import sdc
-    P, U = workload(a.config, seed)
+    P, U = workload(a.config, seed, a.batch_T0)
     for q in (P if isinstance(P, list) else [P]):
         q.space_order, q.nodes, q.limiter = a.space_order, a.nodes, a.limiter
     P0 = P[0] if isinstance(P, list) else P
