@@ -324,15 +324,16 @@ __device__ __forceinline__ void build_chain(const NetParams& P, const double* k,
                                             double c, double dtm, double dtr, ChainSys<NS, MT>& A) {
     constexpr int NC = NS - 1;
     constexpr int NR = NS - 1;
+    const MT cm = to_mt<MT>(c);
 #pragma unroll
     for (int q = 0; q < NC; q++) {
-        A.bd[q] = (MT)c;
+        A.bd[q] = cm;
         A.bs[q] = A.uE[q] = A.uA[q] = A.vE[q] = A.vA[q] = (MT)0;
     }
-    A.dEE = A.dAA = (MT)c;
+    A.dEE = A.dAA = cm;
     A.dEA = A.dAE = (MT)0;
-    const MT dt_ = (MT)dtr, dg = (MT)(dtm * P.gm1 * dfac);
-    const MT y0 = (MT)ws[0];
+    const MT dt_ = to_mt<MT>(dtr), dg = to_mt<MT>(dtm * P.gm1 * dfac);
+    const MT y0 = to_mt<MT>(ws[0]);
 #pragma unroll
     for (int j = 0; j < NR; j++) {
         const MT* cf;
@@ -340,16 +341,17 @@ __device__ __forceinline__ void build_chain(const NetParams& P, const double* k,
         else cf = P.kcf[j];
         if (j == 0) {
             const MT y02 = y0 * y0;
-            const MT t = dt_ * (MT)k[0];
-            const MT tE = dg * (MT)k[0] * (y02 * y0);
+            const MT k0 = to_mt<MT>(k[0]);
+            const MT t = dt_ * k0;
+            const MT tE = dg * k0 * (y02 * y0);
             const MT tA = t * y02;
             A.dEE = fma(-cf[0], tE, A.dEE);   A.dEA = fma(-cf[1], tA, A.dEA);
             A.dAE = fma(-cf[3], tE, A.dAE);   A.dAA = fma(-cf[4], tA, A.dAA);
             A.uE[0] = fma(-cf[9], tE, A.uE[0]); A.uA[0] = fma(-cf[10], tA, A.uA[0]);
         } else {
-            const MT yj = (MT)ws[j];
-            const MT t = dt_ * (MT)k[j];
-            const MT tE = dg * (MT)k[j] * (yj * y0);
+            const MT yj = to_mt<MT>(ws[j]), kj = to_mt<MT>(k[j]);
+            const MT t = dt_ * kj;
+            const MT tE = dg * kj * (yj * y0);
             const MT tA = t * yj, tJ = t * y0;
             A.dEE = fma(-cf[0], tE, A.dEE);   A.dEA = fma(-cf[1], tA, A.dEA);   A.vE[j - 1] = fma(-cf[2], tJ, A.vE[j - 1]);
             A.dAE = fma(-cf[3], tE, A.dAE);   A.dAA = fma(-cf[4], tA, A.dAA);   A.vA[j - 1] = fma(-cf[5], tJ, A.vA[j - 1]);

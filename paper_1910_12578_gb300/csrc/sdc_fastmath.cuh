@@ -61,6 +61,42 @@ __device__ __forceinline__ double sqrt_nr(double x) { return x * rsqrt_nr(x); }
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 __device__ __forceinline__ double bitsd(long long b) { return __longlong_as_double(b); }
 
+// Conversions between double and float on the integer pipe: GB300 issues the
+// conversion instructions on its narrow FP64 pipe, where the FP32-Jacobian
+// Newton spent a fifth of its FP64 issue slots on them.
+// narrow: a double in the normal range of float to float, its mantissa
+// truncated (the Jacobian's inputs, where the rounding does not matter);
+// signed zeros exactly; anything else (tiny, huge, inf, nan) by the conversion
+// instruction.
+__device__ __forceinline__ float narrow(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;  // exponent field of the float
+    if (e <= 0 || e >= 255) {
+        if (((hi << 1) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+        return (float)x;
+    }
+    return __uint_as_float((hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
+// widen: a float to double, exactly (normal floats and zeros on the integer
+// pipe; subnormals, inf and nan by the conversion instruction)
+__device__ __forceinline__ double widen(float x) {
+    const unsigned f = __float_as_uint(x);
+    const unsigned ef = (f >> 23) & 0xffu;
+    if (ef == 0u || ef == 255u) {
+        if ((f << 1) == 0u) return __hiloint2double((int)(f & 0x80000000u), 0);
+        return (double)x;
+    }
+    return __hiloint2double((int)((f & 0x80000000u) | ((ef + 896u) << 20) | ((f >> 3) & 0xfffffu)), (int)(f << 29));
+}
+
+// the working type MT of a Newton matrix: identity for double
+template <typename MT> __device__ __forceinline__ MT to_mt(double x);
+template <> __device__ __forceinline__ double to_mt<double>(double x) { return x; }
+template <> __device__ __forceinline__ float to_mt<float>(double x) { return narrow(x); }
+__device__ __forceinline__ double from_mt(double x) { return x; }
+__device__ __forceinline__ double from_mt(float x) { return widen(x); }
+
 constexpr long long SIGN_BIT = (long long)0x8000000000000000ull;
 constexpr long long ABS_MASK = 0x7FFFFFFFFFFFFFFFll;
 constexpr long long EXP_ONE = 1ll << 52;  // one unit of the exponent field

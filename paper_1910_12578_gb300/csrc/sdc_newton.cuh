@@ -151,7 +151,7 @@ __device__ __forceinline__ bool newton_step_small(const ZoneState<NS>& S, const 
                                                   const double* tr) {
     // |dv_0| <= rtol |tr_0| on the bit patterns (rtol > 0: |rtol tr_0| is the rounded
     // rtol |tr_0|; a nan step fails)
-    bool small = mag2((double)dv[0]) <= mag2(cfg.rtol * tr[0]);
+    bool small = mag2(from_mt(dv[0])) <= mag2(cfg.rtol * tr[0]);
     const double tol_x = cfg.rtol * S.rho;
     if constexpr (sizeof(MT) == 8) {
         // |dv_i| <= tol_x on the integer pipe (mag2 orders like |x|; a nan step fails)
@@ -159,8 +159,11 @@ __device__ __forceinline__ bool newton_step_small(const ZoneState<NS>& S, const 
 #pragma unroll
         for (int i = 0; i < NS; i++) small = small && (mag2((double)dv[1 + i]) <= mt);
     } else {
+        // a float |dv_i| is <= tol_x exactly when it is <= the largest float not
+        // above tol_x; compared on the integer pipe (a nan step fails)
+        const unsigned int mt = mag2(__double2float_rd(tol_x));
 #pragma unroll
-        for (int i = 0; i < NS; i++) small = small && (fabs((double)dv[1 + i]) <= tol_x);
+        for (int i = 0; i < NS; i++) small = small && (mag2(dv[1 + i]) <= mt);
     }
     return small;
 }
@@ -174,7 +177,7 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     const double c = S.newton ? 1.0 : 1.0 + rcp_nr(S.h);
     MT dv[N];
 #pragma unroll
-    for (int r = 0; r < N; r++) dv[r] = (MT)S.G[r];
+    for (int r = 0; r < N; r++) dv[r] = to_mt<MT>(S.G[r]);
     bool solved;
     if constexpr (TOPO == TOPO_CHAIN) {
         // the chain's sparsity: bordered bidiagonal system, O(n) elimination
@@ -193,7 +196,7 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     }
     double tr[N];
 #pragma unroll
-    for (int r = 0; r < N; r++) tr[r] = S.w[r] - (double)dv[r];
+    for (int r = 0; r < N; r++) tr[r] = S.w[r] - from_mt(dv[r]);
     // admissible: every rho X_i at or above its floor (the floor is -inf or a
     // nonzero value, so the two zeros never meet; a nan trial passes here and
     // fails the evaluation below, as it fails this test in plain compares)

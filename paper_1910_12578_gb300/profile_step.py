@@ -32,13 +32,14 @@ def workload(name, seed, batch_T0=1.0):
         U = np.concatenate([b[1].reshape(b[0].nvar, -1) for b in boxes], axis=1)
         return Ps, U
     n, nspec, K = {"box32": (32, 7, 3), "box64": (64, 7, 3), "box128": (128, 7, 3), "box64_13": (64, 13, 4),
-                   "box256": (256, 13, 4)}[name]
+                   "box128_13": (128, 13, 4), "box256": (256, 13, 4)}[name]
     return W.config_box(n=n, nspec=nspec, n_nodes=3, n_iters=K, seed=seed, T0=0.5)
 
 
 def main(argv=None):
     p = argparse.ArgumentParser()
-    p.add_argument("--config", default="box64", choices=["box32", "box64", "box128", "box64_13", "box256", "batch200"])
+    p.add_argument("--config", default="box64", choices=["box32", "box64", "box128", "box64_13", "box128_13", "box256",
+                                                         "batch200"])
     p.add_argument("--seed", type=int, default=None)
     p.add_argument("--prec", choices=["fp64", "fp32jac"], default="fp64")
     p.add_argument("--stencil-variant", type=int, default=0)

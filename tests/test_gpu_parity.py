@@ -687,9 +687,12 @@ def test_full_size_256_13species_sampled(torch_cuda):
     large as itself (the stop test is absolute, 1e-10 of rho) carries the
     rounding of that solve and of the advective terms feeding it relative to
     itself, about the condition number times the unit round-off: the mass
-    fractions are held to 1e-12 in units of max(|rho X_i|, 1e-6 |rho|) and to
-    3e-12 of themselves (1.2e-12 and 1.4e-12 measured, in X5), the other
-    fields to 1e-12."""
+    fractions are held to the tolerance in units of max(|rho X_i|, 1e-6 |rho|),
+    the other fields to the tolerance of themselves, and the mass fractions to
+    the tolerance of themselves where they reach 1e-6 of rho, to three times it
+    for the trace species below (measured in X5: 1.2e-12 and 1.4e-12 in FP64,
+    1.1e-9 with the FP32 Jacobian, whose iterative refinement stops on the same
+    absolute test)."""
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
     P, U = W.config_box(n=256, nspec=13, n_iters=4, seed=1, T0=0.5)
@@ -728,13 +731,13 @@ def test_full_size_256_13species_sampled(torch_cuda):
         torch.cuda.empty_cache()
         assert st.n_fail == 0
         tol = TOL64 if prec == 0 else TOL32
-        tol_self = tol if prec == 1 else 3 * TOL64
+        trace = own < 1e-6 * own[0]
+        tol_self = np.where(trace, 3 * tol, tol)
         Gb = G[:, c0:c0 + h, c0:c0 + h, c0:c0 + h]
         d = np.abs(Gb - Vb).reshape(P.nvar, -1).max(1)
-        assert (d[:5] / own[:5]).max() <= tol, (variant, prec, d / own)
         assert (d[5:] / floored[5:]).max() <= tol, (variant, prec, d / floored)
-        assert (d[5:] / own[5:]).max() <= tol_self, (variant, prec, d / own)
+        assert (d / own <= tol_self).all(), (variant, prec, d / own)
         for (x, y, z), ref in zip(samples, refs):
             got = G[:, z, y, x]
             err = np.abs(got - ref) / np.maximum(own, np.abs(ref))
-            assert err[:5].max() <= tol and err[5:].max() <= tol_self, ((x, y, z), variant, prec, err)
+            assert (err <= tol_self).all(), ((x, y, z), variant, prec, err)
