@@ -43,16 +43,18 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per zone of one Newton launch, from one ncu
-# capture per kernel variant on the 64^3 workload (262,144 zones), keyed by (nspec, Newton variant, prec).
-# The traffic of these kernels grows in proportion to the zones (no re-reads), so a launch over N zones
-# moves N times this.  A variant or precision without a capture reports null.
+# capture per kernel variant and precision, keyed by (nspec, Newton variant, prec).  The 13-species captures
+# ran on a 128^3 box of the 256^3 workload's network (2.1M zones: every array of the launch exceeds L2, so its
+# writes reach DRAM and the traffic grows in proportion to the zones; algorithmic 544 B per zone), so a launch
+# over N zones moves N times this.  The 7-species capture ran on the 64^3 box itself (its writes still sit in
+# the 129 MB L2 when the launch ends).  A variant or precision without a capture reports null.
 NEWTON_TRAFFIC_PER_ZONE = {
-    (7, 1, "fp64"): (44.363264e6 + 4.091392e6) / 262144,    # newton_queue_kernel<7, chain, double>; its writes
-                                                              # stay in the 129 MB L2 at the 64^3 size
-    (13, 3, "fp64"): (70.107904e6 + 71.510016e6) / 262144,  # newton_queue_kernel<13, chain, double> on a 64^3
-                                                              # box of the 256^3 workload's network; its writes
-                                                              # already reach DRAM there, so 256^3 scales by zones
+    (13, 2, "fp64"): (554.7e6 + 530.7e6) / 2097152,      # newton_kernel<13, chain, double>, static grid
+    (13, 2, "fp32jac"): (555.3e6 + 515.7e6) / 2097152,   # newton_kernel<13, chain, float>
+    (7, 0, "fp64"): (44.2e6 + 2.9e6) / 262144,           # newton_kernel<7, chain, double> on the 64^3 box
 }
+# The same for one advective term of the direction-split passes (x, y, z; A only), 128^3 box, 13 species.
+STENCIL_TRAFFIC_PER_ZONE = {13: (302.8e6 + 547.8e6 + 604.2e6 + 257.7e6 + 646.8e6 + 261.5e6) / 2097152}
 
 
 def parse():
@@ -185,6 +187,34 @@ def newton_flops(nspec):
             "per_iter_linear": matrix + elimination, "evaluation": evaluation, "matrix": matrix,
             "elimination": elimination, "update": update, "setup": setup,
             "transcendentals_per_evaluation": 1 + nr}
+
+
+def stencil_flops_per_zone(P, rhs_mode):
+    """Algorithmic FP64 flops of one advective term per zone (PLM / MC / HLLC,
+    3D, nspec species, nvar = 5 + nspec fields; a fused multiply-add counts 2,
+    a refined reciprocal or reciprocal square root 1):
+      primitives            13 + nspec      (once per zone)
+      per direction, per zone:
+        differences         nvar            (one per face and field)
+        half slopes         nvar            (dl + dr; the MC limiting on bit patterns)
+        face flux           87 + 3 nspec    (both face states of the hydro fields,
+                                             the Davis speeds, S*, the upwind flux,
+                                             the star-region correction; the upwind
+                                             mass fractions, their sum, renormalised
+                                             species fluxes)
+        flux difference     3 nvar
+    so 349 + 25 nspec per zone (7 species 524, 13 species 674).  The fused
+    right-hand side of Eq. sdc:general adds per field the A difference (3),
+    the integral's terms (2 per term and a reactive source add per term) and
+    the reactive R term (2)."""
+    ns = P.net.nspec
+    nv = P.nvar
+    f = 13 + ns + 3 * (2 * nv + 87 + 3 * ns + 3 * nv)
+    if rhs_mode:
+        terms = P.n_nodes
+        nw = ns + 1
+        f += nv * (3 + 2 * terms) + nw * (2 + terms)
+    return f
 
 
 def stencil_bytes_per_zone(P, rhs_mode):
@@ -596,10 +626,28 @@ def measure(args, P, U, prec, ws, barrier, flush, with_e2e=True):
         pass
     hbm_peak = hbm_peak or 6800.0
     st_gbs = st_bytes / (stencil_ms * 1e-3) / 1e9
-    roof_st = {"kernel": "stencil_kernel (advective term + fused rhs)", "bound": "hbm", "achieved": st_gbs,
-               "peak": hbm_peak, "unit": "GB/s", "frac": st_gbs / hbm_peak, "traffic": None,
-               "bytes_per_launch": st_bytes, "ms_per_launch": stencil_ms,
-               "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    st_flops = nzones(P) * (stencil_flops_per_zone(P0, False) * P0.n_iters +
+                            stencil_flops_per_zone(P0, True) * (P0.n_nodes - 2) * P0.n_iters) / max(n_st, 1)
+    st_tf = st_flops / (stencil_ms * 1e-3) / 1e12
+    split = (tuning is not None and tuning["stencil_choice"] == tuning["stencil_variants"] - 1 and P0.dim == 3
+             and P0.space_order == 2)
+    if P0.space_order == 4:
+        st_tf = None
+    roof_st = {"kernel": ("stencil_split_kernel x, y, z passes" if split else "stencil_kernel") +
+                         " (advective term, fused rhs at the inner nodes)",
+               "bound": "alu", "achieved": st_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+               "frac": st_tf / FP64_PEAK_TFLOPS if st_tf is not None else None, "traffic": None,
+               "flops_per_launch": st_flops if st_tf is not None else None,
+               "ms_per_launch": stencil_ms,
+               "hbm": {"achieved": st_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": st_gbs / hbm_peak,
+                       "bytes_per_launch": st_bytes, "peak_source": "measured copy bandwidth (hbm_gbs)",
+                       "traffic_A_only": (STENCIL_TRAFFIC_PER_ZONE[P0.net.nspec] * nzones(P)
+                                          if split and P0.net.nspec in STENCIL_TRAFFIC_PER_ZONE else None),
+                       "traffic_note": "ncu DRAM read + write of the three passes of one advective term without "
+                                       "the rhs, 128^3 capture scaled by zones"},
+               "note": "one launch = one advective term (the direction-split variant's three passes); algorithmic "
+                       "FP64 flops per zone from stencil_flops_per_zone; the term is bound by the FP64 pipe, not by "
+                       "HBM (its algorithmic bytes are the hbm object)"}
     rec = {"value": value, "ms_per_step": total_ms / args.steps, "step_ms": step_ms, "clocks": ck, "e2e": e2e,
            "kernel_variants": tuning, "roofline": roof, "roofline_stencil": roof_st,
            "profile_ms": {"stencil": pr.ms_stencil, "newton": pr.ms_newton, "other": pr.ms_other,

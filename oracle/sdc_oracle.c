@@ -974,6 +974,30 @@ static void step_source(const orc_problem* P, const double* U, double* R) {
     else orc_reaction_source(P, U, R);
 }
 
+/* The Newton guess of the node update (the paper does not say how the
+   implicit equation is started).  The explicit predictor: the update of
+   Eq. sdc:general with the unknown R^{m+1,(k+1)} replaced by the previous
+   iterate's R^{m+1,(k)}, that is rhs + dt_m R^{m+1,(k)} in the reactive fields
+   (R(U^n) in the first iteration), with rho and rho u of the rhs.  Where that
+   state has no positive temperature or a mass fraction below -0.01, the guess
+   stays the previous iterate U^{m+1,(k)} (U^n in the first iteration), as G
+   holds it on entry. */
+static void newton_guess(const orc_problem* P, const double* rhs, const double* Rk, double dtm, double* G) {
+    int dim = P->dim, nv = orc_nvar(P), n = P->nspec + 1;
+    long long N = nzones(P);
+#pragma omp parallel for schedule(static)
+    for (long long z = 0; z < N; z++) {
+        double g[64];
+        for (int f = 0; f < nv; f++) g[f] = rhs[f * N + z];
+        for (int r = 0; r < n; r++) g[1 + dim + r] += dtm * Rk[r * N + z];
+        int ok = orc_temperature(P, g[0], g + 1, g[1 + dim]) > 0.0;
+        for (int i = 0; i < P->nspec; i++)
+            if (g[2 + dim + i] < -1e-2 * g[0]) ok = 0;
+        if (ok)
+            for (int f = 0; f < nv; f++) G[f * N + z] = g[f];
+    }
+}
+
 static void step_implicit(const orc_problem* P, const double* rhs, double dtm, double* U, double* R,
                           orc_stats* st) {
     if (P->split_op == ORC_OP_ADVECT) {
@@ -1025,7 +1049,8 @@ int orc_sdc_step_nodes(const orc_problem* P, double* U, double dt, orc_stats* st
                     if (f >= 1 + dim) v -= dtm * Rold[m + 1][(f - 1 - dim) * N + z];
                     rhs[f * N + z] = v + I[f * N + z];
                 }
-            /* Un[m+1] holds U^{m+1,(k)} (the guess) and receives U^{m+1,(k+1)} */
+            /* Un[m+1] holds U^{m+1,(k)}, takes the guess and receives U^{m+1,(k+1)} */
+            if (P->split_op != ORC_OP_ADVECT) newton_guess(P, rhs, Rold[m + 1], dtm, Un[m + 1]);
             step_implicit(P, rhs, dtm, Un[m + 1], Rnew[m + 1], st);
         }
         if (k < K - 1) step_advective(P, Un[M - 1], Anew[M - 1]);

@@ -50,6 +50,36 @@ __global__ void rhs_kernel(int nvar, int dim, long long N, const double* __restr
     }
 }
 
+// The Newton start of the fourth-order implicit update, formed on the zone
+// averages before their centre maps: the explicit predictor
+// rhs + dt_m R^{m+1,(k)} (rho and rho u of the rhs, separate roundings as in
+// the oracle) where it has a positive temperature and no mass fraction below
+// -0.01, the previous iterate elsewhere.  out may be guess.
+__global__ void predict_kernel(NetParams P, int nvar, int dim, long long N, const double* __restrict__ rhs,
+                               const double* __restrict__ Rk, const double* guess, const double* __restrict__ dt,
+                               double dt_frac, double* out) {
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= N) return;
+    const double dtm = (*dt) * dt_frac;
+    const double rho = rhs[z];
+    double m2 = 0.0;
+    for (int d = 0; d < dim; d++) m2 += rhs[(1 + d) * N + z] * rhs[(1 + d) * N + z];
+    const double ir = rcp_nr(rho);
+    const double wE = __dadd_rn(rhs[(1 + dim) * N + z], __dmul_rn(dtm, Rk[z]));
+    const double T = P.gm1 * (wE - 0.5 * m2 * ir) * ir;
+    bool ok = T > 0.0 && T < INFINITY;
+    const int ns = nvar - 2 - dim;
+    for (int i = 0; i < ns; i++)
+        ok = ok && !(__dadd_rn(rhs[(2 + dim + i) * N + z], __dmul_rn(dtm, Rk[(1 + i) * N + z])) < -XMARGIN * rho);
+    if (ok) {
+        for (int f = 0; f <= dim; f++) out[f * N + z] = rhs[f * N + z];
+        for (int r = 0; r <= ns; r++)
+            out[(1 + dim + r) * N + z] = __dadd_rn(rhs[(1 + dim + r) * N + z], __dmul_rn(dtm, Rk[r * N + z]));
+    } else if (out != guess) {
+        for (int f = 0; f < nvar; f++) out[f * N + z] = guess[f * N + z];
+    }
+}
+
 // I = sum_l (q_l dt) (A_l + R_l)
 __global__ void node_integral_kernel(int nvar, int dim, int M, long long N, const double* __restrict__ A,
                                      const double* __restrict__ R, double q0, double q1, double q2, double q3,
@@ -410,17 +440,35 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
                 SDC_LAUNCH(prof, CLS_STENCIL, launch_A(c, node[m], Anew[m], STENCIL_A_RHS, ra, st));
             }
             if (with_R) {
+                // the previous iterate U^{m+1,(k)} (U^n in the first iteration) and
+                // R^{m+1,(k)}: the FP64 Newton starts from the explicit predictor
+                // rhs + dt_m R^{m+1,(k)} where admissible, from that iterate
+                // elsewhere.  The FP32-Jacobian solve starts from the iterate: its
+                // iterative refinement stops on the same absolute step test, and
+                // from the predictor that test passes after one refinement step,
+                // which leaves trace species at about 1e-7 of themselves
                 const double* guess = (k == 0) ? node[0] : node[m + 1];
+                const double* Rpred = c->prec == SDC_PREC_FP64 ? Rold[m + 1] : nullptr;
                 unsigned long long* q = (c->d_queue && qslot < QUEUE_SLOTS) ? c->d_queue + qslot++ : nullptr;
-                if (fourth)
+                if (fourth && !Rpred) {
                     SDC_LAUNCH(prof, CLS_NEWTON, launch_newton4(c->P, c->cfg, c->prec, c->dim, N, c->d_boxes, c->nbox,
                                                                 c->rhs, guess, node[m + 1], Rnew[m + 1], dt_dev,
                                                                 c->tau[m + 1] - c->tau[m], 0.0, nullptr, nullptr,
                                                                 c->d_stats, c->fw, st, c->newton_variant, q,
                                                                 c->persistent_blocks));
-                else
+                } else if (fourth) {
+                    SDC_LAUNCH(prof, CLS_OTHER, (predict_kernel<<<grid_for(N, EW_BLOCK), EW_BLOCK, 0, st>>>(
+                                                     c->P, c->nvar, c->dim, N, c->rhs, Rold[m + 1], guess, dt_dev,
+                                                     c->tau[m + 1] - c->tau[m], node[m + 1]),
+                                                 cudaGetLastError()));
+                    SDC_LAUNCH(prof, CLS_NEWTON, launch_newton4(c->P, c->cfg, c->prec, c->dim, N, c->d_boxes, c->nbox,
+                                                                c->rhs, node[m + 1], node[m + 1], Rnew[m + 1], dt_dev,
+                                                                c->tau[m + 1] - c->tau[m], 0.0, nullptr, nullptr,
+                                                                c->d_stats, c->fw, st, c->newton_variant, q,
+                                                                c->persistent_blocks));
+                } else
                     SDC_LAUNCH(prof, CLS_NEWTON, launch_newton(c->P, c->cfg, c->prec, N, c->dim, c->rhs, guess,
-                                                               node[m + 1], Rnew[m + 1], dt_dev,
+                                                               Rpred, node[m + 1], Rnew[m + 1], dt_dev,
                                                                c->tau[m + 1] - c->tau[m], 0.0, nullptr, nullptr,
                                                                c->d_stats, st, c->newton_variant, q,
                                                                c->persistent_blocks));
@@ -788,7 +836,7 @@ sdc_status sdc_react_newton(sdc_ctx* ctx, const double* rhs, double dt_m, double
                                U_inout, R_out, nullptr, 1.0, dt_m, zone_status, zone_iters, ctx->d_stats, ctx->fw,
                                ctx->stream, ctx->newton_variant, ctx->d_queue, ctx->persistent_blocks));
     else
-        SDC_TRY(launch_newton(ctx->P, ctx->cfg, ctx->prec, ctx->Ntot, ctx->dim, rhs, U_inout, U_inout, R_out,
+        SDC_TRY(launch_newton(ctx->P, ctx->cfg, ctx->prec, ctx->Ntot, ctx->dim, rhs, U_inout, nullptr, U_inout, R_out,
                               nullptr, 1.0, dt_m, zone_status, zone_iters, ctx->d_stats, ctx->stream,
                               ctx->newton_variant, ctx->d_queue, ctx->persistent_blocks));
     if (stats) return read_stats(ctx, stats);
@@ -982,7 +1030,8 @@ sdc_status sdc_launches_per_step(const sdc_ctx* ctx, int* launches) {
         // fourth order: A is a sequence of kernels and is evaluated apart from
         // the rhs at nodes m >= 1; the source and the implicit update add maps
         const int LA = fourth_advective_launches(ctx->dim, ctx->limiter), K = ctx->K, M = ctx->M;
-        *launches = 1 + LA + FOURTH_SOURCE_LAUNCHES + K * (M - 1) * (1 + FOURTH_NEWTON_LAUNCHES) +
+        const int predict = ctx->prec == SDC_PREC_FP64 ? 1 : 0;  // the FP64 Newton start's kernel
+        *launches = 1 + LA + FOURTH_SOURCE_LAUNCHES + K * (M - 1) * (1 + predict + FOURTH_NEWTON_LAUNCHES) +
                     K * (M - 2) * LA + (K - 1) * LA;
         return SDC_OK;
     }

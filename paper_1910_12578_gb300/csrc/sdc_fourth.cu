@@ -598,7 +598,7 @@ cudaError_t launch_newton4(const NetParams& P, const NewtonCfg& cfg, int prec, i
     cudaError_t e;
     lap_pair_kernel<<<fgrid(N), F_BLOCK, 0, st>>>(dim, nv, N, boxes, nbox, rhs, w.rc, guess, w.gc, -1.0 / 24.0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = launch_newton(P, cfg, prec, N, dim, w.rc, w.gc, w.gc, w.Rc, dt_dev, dt_frac, dtm_host, zone_status,
+    if ((e = launch_newton(P, cfg, prec, N, dim, w.rc, w.gc, nullptr, w.gc, w.Rc, dt_dev, dt_frac, dtm_host, zone_status,
                            zone_iters, stats, st, variant, queue, persistent_blocks)) != cudaSuccess)
         return e;
     (void)n;

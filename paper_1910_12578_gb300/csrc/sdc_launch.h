@@ -27,8 +27,10 @@ cudaError_t stencil_prepare(int dim, int nspec);  // raise the dynamic shared-me
 // 13-species group kernel: 4 lanes per zone (0) or 2 (1).
 int newton_variants(int nspec, int topo);
 bool newton_group_case(int nspec, int topo);  // the 13-species chain (a group of lanes per zone)
+// Rpred: R^{m+1,(k)} of the sweep (the start is then the explicit predictor where
+// admissible, the guess elsewhere), or nullptr (the start is the guess)
 cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, long long N, int dim,
-                          const double* rhs, const double* guess, double* Uout, double* Rout,
+                          const double* rhs, const double* guess, const double* Rpred, double* Uout, double* Rout,
                           const double* dt_dev, double dt_frac, double dtm_host, int* zone_status,
                           int* zone_iters, DevStats* stats, cudaStream_t st, int variant = 0,
                           unsigned long long* queue = nullptr, int persistent_blocks = 0);

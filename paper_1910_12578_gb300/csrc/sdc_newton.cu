@@ -8,11 +8,16 @@ namespace sdcd {
 
 constexpr int NEWTON_BLOCK = 128;
 
-// Load zone z into a solver state and evaluate it.
+// Load zone z into a solver state and evaluate it.  The start: with Rpred
+// (R^{m+1,(k)} of the sweep), the explicit predictor rhs + dt_m R^{m+1,(k)}
+// where it has a positive temperature and no mass fraction below -0.01,
+// otherwise (and without Rpred) the guess carried to the density of the rhs.
+// The predictor is formed with separate roundings (no fused multiply-add), as
+// the oracle forms it.
 template <int NS, int TOPO>
 __device__ __forceinline__ void load_zone(ZoneState<NS>& S, const NetParams& P, long long N, int dim, long long z,
-                                          const double* __restrict__ rhs, const double* guess, double dtm,
-                                          double* mom) {
+                                          const double* __restrict__ rhs, const double* guess,
+                                          const double* __restrict__ Rpred, double dtm, double* mom) {
     constexpr int NW = NS + 1;
     const double rho = rhs[z];
     double m2 = 0.0;
@@ -21,11 +26,22 @@ __device__ __forceinline__ void load_zone(ZoneState<NS>& S, const NetParams& P, 
         mom[d] = rhs[(1 + d) * N + z];
         m2 += mom[d] * mom[d];
     }
-    const double scale = rho / guess[z];
 #pragma unroll
-    for (int r = 0; r < NW; r++) {
-        S.rw[r] = rhs[(1 + dim + r) * N + z];
-        S.w[r] = guess[(1 + dim + r) * N + z] * scale;
+    for (int r = 0; r < NW; r++) S.rw[r] = rhs[(1 + dim + r) * N + z];
+    bool pred = false;
+    if (Rpred) {
+#pragma unroll
+        for (int r = 0; r < NW; r++) S.w[r] = __dadd_rn(S.rw[r], __dmul_rn(dtm, Rpred[r * N + z]));
+        const double ir = rcp_nr(rho);
+        pred = positive_finite(P.gm1 * (S.w[0] - 0.5 * m2 * ir) * ir);
+        const double floor_x = -XMARGIN * rho;
+#pragma unroll
+        for (int i = 0; i < NS; i++) pred = pred && !(S.w[1 + i] < floor_x);
+    }
+    if (!pred) {
+        const double scale = rho / guess[z];
+#pragma unroll
+        for (int r = 0; r < NW; r++) S.w[r] = guess[(1 + dim + r) * N + z] * scale;
     }
     zone_init<NS, TOPO>(S, P, rho, m2, dtm);
 }
@@ -53,7 +69,8 @@ __device__ __forceinline__ void store_zone(const ZoneState<NS>& S, const NetPara
 template <int NS, int TOPO, typename MT>
 __global__ void __launch_bounds__(NEWTON_BLOCK)
 newton_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __restrict__ rhs,
-              const double* guess, double* Uout, double* __restrict__ Rout, const double* __restrict__ dt_dev,
+              const double* guess, const double* __restrict__ Rpred, double* Uout, double* __restrict__ Rout,
+              const double* __restrict__ dt_dev,
               double dt_frac, double dtm_host, int* __restrict__ zone_status, int* __restrict__ zone_iters,
               DevStats* __restrict__ stats) {
     __shared__ unsigned int hist[64];
@@ -66,7 +83,7 @@ newton_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __
         const double dtm = dt_dev ? (*dt_dev) * dt_frac : dtm_host;
         ZoneState<NS> S;
         double mom[3];
-        load_zone<NS, TOPO>(S, P, N, dim, z, rhs, guess, dtm, mom);
+        load_zone<NS, TOPO>(S, P, N, dim, z, rhs, guess, Rpred, dtm, mom);
         while (!S.done) zone_iterate<NS, TOPO, MT>(S, P, cfg, dtm);
         store_zone<NS, TOPO>(S, P, N, dim, z, mom, Uout, Rout, zone_status, zone_iters);
         iters = S.iters;
@@ -101,7 +118,8 @@ newton_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __
 template <int NS, int TOPO, typename MT>
 __global__ void __launch_bounds__(NEWTON_BLOCK)
 newton_queue_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __restrict__ rhs,
-                    const double* guess, double* Uout, double* __restrict__ Rout, const double* __restrict__ dt_dev,
+                    const double* guess, const double* __restrict__ Rpred, double* Uout, double* __restrict__ Rout,
+                    const double* __restrict__ dt_dev,
                     double dt_frac, double dtm_host, int* __restrict__ zone_status, int* __restrict__ zone_iters,
                     DevStats* __restrict__ stats, unsigned long long* __restrict__ queue) {
     __shared__ unsigned int hist[64];
@@ -130,7 +148,7 @@ newton_queue_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const doub
                 const long long zi = (long long)(base + __popc(want & ((1u << lane) - 1u)));
                 if (zi < N) {
                     z = zi;
-                    load_zone<NS, TOPO>(S, P, N, dim, z, rhs, guess, dtm, mom);
+                    load_zone<NS, TOPO>(S, P, N, dim, z, rhs, guess, Rpred, dtm, mom);
                 } else {
                     exhausted = true;
                 }
@@ -172,7 +190,8 @@ newton_queue_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const doub
 template <int NS, int TOPO, typename MT>
 __global__ void __launch_bounds__(NEWTON_BLOCK)
 newton_warpqueue_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __restrict__ rhs,
-                        const double* guess, double* Uout, double* __restrict__ Rout,
+                        const double* guess, const double* __restrict__ Rpred, double* Uout,
+                        double* __restrict__ Rout,
                         const double* __restrict__ dt_dev, double dt_frac, double dtm_host,
                         int* __restrict__ zone_status, int* __restrict__ zone_iters, DevStats* __restrict__ stats,
                         unsigned long long* __restrict__ queue) {
@@ -193,7 +212,7 @@ newton_warpqueue_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const 
         if (z < N) {
             ZoneState<NS> S;
             double mom[3];
-            load_zone<NS, TOPO>(S, P, N, dim, z, rhs, guess, dtm, mom);
+            load_zone<NS, TOPO>(S, P, N, dim, z, rhs, guess, Rpred, dtm, mom);
             while (!S.done) zone_iterate<NS, TOPO, MT>(S, P, cfg, dtm);
             store_zone<NS, TOPO>(S, P, N, dim, z, mom, Uout, Rout, zone_status, zone_iters);
             atomicAdd(&hist[S.iters < 63 ? S.iters : 63], 1u);
@@ -227,7 +246,8 @@ constexpr int GROUP_ZONES = 32;
 template <int NS, typename MT, int L>
 __global__ void __launch_bounds__(NEWTON_BLOCK)
 newton_group_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __restrict__ rhs,
-                    const double* guess, double* Uout, double* __restrict__ Rout, const double* __restrict__ dt_dev,
+                    const double* guess, const double* __restrict__ Rpred, double* Uout, double* __restrict__ Rout,
+                    const double* __restrict__ dt_dev,
                     double dt_frac, double dtm_host, int* __restrict__ zone_status, int* __restrict__ zone_iters,
                     DevStats* __restrict__ stats) {
     using Lay = GroupLayout<NS, MT>;
@@ -252,15 +272,37 @@ newton_group_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const doub
             mom[d] = rhs[(1 + d) * N + z];
             m2 += mom[d] * mom[d];
         }
-        const double scale = rho / guess[z];
         double rw_rows[RL];
 #pragma unroll
         for (int t = 0; t < RL; t++) {
             const int row = lane + L * t;
-            rw_rows[t] = 0.0;
-            if (row < NW) {
-                rw_rows[t] = rhs[(1 + dim + row) * N + z];
-                zs[Lay::O_W + row] = guess[(1 + dim + row) * N + z] * scale;
+            rw_rows[t] = row < NW ? rhs[(1 + dim + row) * N + z] : 0.0;
+        }
+        // the start: the explicit predictor where admissible (as load_zone), else the guess
+        bool pred = false;
+        if (Rpred) {
+            const double floor_x = -XMARGIN * rho;
+            bool ok = true;
+#pragma unroll
+            for (int t = 0; t < RL; t++) {
+                const int row = lane + L * t;
+                if (row < NW) {
+                    const double v = __dadd_rn(rw_rows[t], __dmul_rn(dtm, Rpred[row * N + z]));
+                    zs[Lay::O_W + row] = v;
+                    if (row >= 1) ok = ok && !(v < floor_x);
+                }
+            }
+            __syncwarp(mask);
+            const double ir = rcp_nr(rho);
+            ok = ok && positive_finite(P.gm1 * (zs[Lay::O_W] - 0.5 * m2 * ir) * ir);
+            pred = group_all<L>(mask, ok);
+        }
+        if (!pred) {
+            const double scale = rho / guess[z];
+#pragma unroll
+            for (int t = 0; t < RL; t++) {
+                const int row = lane + L * t;
+                if (row < NW) zs[Lay::O_W + row] = guess[(1 + dim + row) * N + z] * scale;
             }
         }
         __syncwarp(mask);
@@ -412,7 +454,7 @@ int newton_persistent_blocks(const NetParams& P, int prec) {
 }
 
 cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, long long N, int dim,
-                          const double* rhs, const double* guess, double* Uout, double* Rout,
+                          const double* rhs, const double* guess, const double* Rpred, double* Uout, double* Rout,
                           const double* dt_dev, double dt_frac, double dtm_host, int* zone_status,
                           int* zone_iters, DevStats* stats, cudaStream_t st, int variant,
                           unsigned long long* queue, int persistent_blocks) {
@@ -421,7 +463,7 @@ cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, lo
         const unsigned ggrid = (unsigned)((N + GROUP_ZONES - 1) / GROUP_ZONES);
 #define SDC_GROUP_LAUNCH(MT, L)                                                                                    \
     newton_group_kernel<13, MT, L><<<ggrid, 32 * L, group_smem<13, MT>(), st>>>(                                   \
-        P, cfg, N, dim, rhs, guess, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, zone_iters, stats)
+        P, cfg, N, dim, rhs, guess, Rpred, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, zone_iters, stats)
         if (variant == 1) {
             if (prec == 0) SDC_GROUP_LAUNCH(double, 2);
             else SDC_GROUP_LAUNCH(float, 2);
@@ -436,7 +478,7 @@ cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, lo
         const unsigned ggrid = (unsigned)((N + GROUP_ZONES - 1) / GROUP_ZONES);
 #define SDC_SMALL_GROUP_LAUNCH(NSV, MT)                                                                            \
     newton_group_kernel<NSV, MT, 4><<<ggrid, 128, group_smem<NSV, MT>(), st>>>(                                      \
-        P, cfg, N, dim, rhs, guess, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, zone_iters, stats)
+        P, cfg, N, dim, rhs, guess, Rpred, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, zone_iters, stats)
         if (P.nspec == 5) {
             if (prec == 0) SDC_SMALL_GROUP_LAUNCH(5, double);
             else SDC_SMALL_GROUP_LAUNCH(5, float);
@@ -457,27 +499,27 @@ cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, lo
         if (q && variant == 2) {                                                                           \
             if (prec == 0)                                                                                 \
                 newton_warpqueue_kernel<ns, tp, double><<<pgrid, NEWTON_BLOCK, 0, st>>>(                   \
-                    P, cfg, N, dim, rhs, guess, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status,        \
+                    P, cfg, N, dim, rhs, guess, Rpred, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, \
                     zone_iters, stats, queue);                                                             \
             else                                                                                           \
                 newton_warpqueue_kernel<ns, tp, float><<<pgrid, NEWTON_BLOCK, 0, st>>>(                    \
-                    P, cfg, N, dim, rhs, guess, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status,        \
+                    P, cfg, N, dim, rhs, guess, Rpred, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, \
                     zone_iters, stats, queue);                                                             \
         } else if (q) {                                                                                    \
             if (prec == 0)                                                                                 \
                 newton_queue_kernel<ns, tp, double><<<pgrid, NEWTON_BLOCK, 0, st>>>(                       \
-                    P, cfg, N, dim, rhs, guess, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status,        \
+                    P, cfg, N, dim, rhs, guess, Rpred, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, \
                     zone_iters, stats, queue);                                                             \
             else                                                                                           \
                 newton_queue_kernel<ns, tp, float><<<pgrid, NEWTON_BLOCK, 0, st>>>(                        \
-                    P, cfg, N, dim, rhs, guess, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status,        \
+                    P, cfg, N, dim, rhs, guess, Rpred, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, \
                     zone_iters, stats, queue);                                                             \
         } else if (prec == 0)                                                                              \
-            newton_kernel<ns, tp, double><<<grid, NEWTON_BLOCK, 0, st>>>(P, cfg, N, dim, rhs, guess, Uout,   \
+            newton_kernel<ns, tp, double><<<grid, NEWTON_BLOCK, 0, st>>>(P, cfg, N, dim, rhs, guess, Rpred, Uout, \
                                                                          Rout, dt_dev, dt_frac, dtm_host,  \
                                                                          zone_status, zone_iters, stats);  \
         else                                                                                               \
-            newton_kernel<ns, tp, float><<<grid, NEWTON_BLOCK, 0, st>>>(P, cfg, N, dim, rhs, guess, Uout,    \
+            newton_kernel<ns, tp, float><<<grid, NEWTON_BLOCK, 0, st>>>(P, cfg, N, dim, rhs, guess, Rpred, Uout, \
                                                                         Rout, dt_dev, dt_frac, dtm_host,   \
                                                                         zone_status, zone_iters, stats);   \
         return cudaGetLastError();                                                                         \

@@ -50,9 +50,29 @@ def rel_err_R(gpu, orc, n, scale):
     return np.array([np.abs(g[r] - o[r]).max() / max(np.abs(o[r]).max(), scale) for r in range(n)])
 
 
-def oracle_sweep_inputs(o, U, dt, k_iters=1, m_target=None):
+def newton_guess(o, rhs, Rk, dtm, prev):
+    """The sweep's Newton start, as the oracle forms it: the explicit predictor
+    rhs + dt_m R^{m+1,(k)} in the reactive fields where it has a positive
+    temperature and no mass fraction below -0.01, the previous iterate prev
+    elsewhere."""
+    P = o.P
+    dim = P.dim
+    g = rhs.copy()
+    g[1 + dim:] = rhs[1 + dim:] + dtm * Rk
+    G = g.reshape(P.nvar, -1)
+    ke = 0.5 * (G[1:1 + dim] ** 2).sum(0) / G[0]
+    ok = (G[1 + dim] - ke) > 0
+    ok &= ~(G[2 + dim:] < -1e-2 * G[0]).any(0)
+    out = prev.reshape(P.nvar, -1).copy()
+    out[:, ok] = G[:, ok]
+    return out.reshape(rhs.shape)
+
+
+def oracle_sweep_inputs(o, U, dt, k_iters=1, m_target=None, predictor=True):
     """Run the oracle sweep in Python from its building blocks and return the
-    (rhs, guess, dt_m) seen by the Newton solve at the last (k, m) visited."""
+    (rhs, guess, dt_m) seen by the Newton solve at the last (k, m) visited.
+    predictor=False: the guess is the previous iterate, the start of the
+    FP32-Jacobian solves (the oracle's own sweep takes the predictor)."""
     P = o.P
     M = P.n_nodes
     dim = P.dim
@@ -73,10 +93,11 @@ def oracle_sweep_inputs(o, U, dt, k_iters=1, m_target=None):
             rhs = Un[m] + dtm * (Anew[m] - Aold[m])
             rhs[1 + dim:] -= dtm * Rold[m + 1]
             rhs = rhs + I
-            last = (rhs.copy(), Un[m + 1].copy(), dtm)
+            guess = newton_guess(o, rhs, Rold[m + 1], dtm, Un[m + 1]) if predictor else Un[m + 1]
+            last = (rhs.copy(), guess.copy(), dtm)
             if m_target is not None and m == m_target and k == k_iters - 1:
                 return last
-            Unew, Rn, zs, zi, st = o.react_newton(rhs, dtm, Un[m + 1])
+            Unew, Rn, zs, zi, st = o.react_newton(rhs, dtm, newton_guess(o, rhs, Rold[m + 1], dtm, Un[m + 1]))
             Un[m + 1] = Unew
             Rnew[m + 1] = Rn
         if k < k_iters - 1:

@@ -662,6 +662,29 @@ def test_newton_matches_bisection_root():
         assert w[0] == pytest.approx(E + Q * (XA - w[1]), rel=1e-13)
 
 
+def test_newton_start_changes_iterations_not_the_root():
+    """The sweep starts each implicit solve from the explicit predictor
+    rhs + dt_m R^{m+1,(k)} (falling back to the previous iterate): on the
+    inputs of a 12^3 hot-spot sweep (second iteration, last node) the solve
+    from the predictor and the solve from the previous iterate reach the same
+    root to the stop test's accuracy, and the predictor needs fewer iterations."""
+    from gpu_util import oracle_sweep_inputs
+    P, U = W.config_box(n=12, nspec=7, seed=1, T0=0.5)
+    o = O.Oracle(P)
+    dt = o.cfl_dt(U)
+    rhs, g_pred, dtm = oracle_sweep_inputs(o, U, dt, k_iters=2, predictor=True)
+    _, g_prev, _ = oracle_sweep_inputs(o, U, dt, k_iters=2, predictor=False)
+    assert not np.array_equal(g_pred, g_prev)
+    Ua, _, za, ia, sa = o.react_newton(rhs, dtm, g_pred)
+    Ub, _, zb, ib, sb = o.react_newton(rhs, dtm, g_prev)
+    assert sa.n_fail == 0 and sb.n_fail == 0
+    a = Ua.reshape(P.nvar, -1)
+    b = Ub.reshape(P.nvar, -1)
+    den = np.maximum(np.abs(b).max(1), 1e-6 * np.abs(b[0]).max())
+    assert (np.abs(a - b).max(1) / den).max() <= 1e-12
+    assert sa.newton_iters_total < sb.newton_iters_total
+
+
 def test_newton_reports_status():
     """maxit = 1 cannot converge: the zone reports ORC_NEWTON_MAXIT."""
     net = W.decay_network(Q=1.0)
