@@ -38,6 +38,9 @@ struct NetParams {
     // alpha chain: a_j / prod_reactants mass (with multiplicity), so that
     // r_j = (amp_j / rho) f_j(T) prod_reactants (rho X)^count
     double amp[SDCD_MAXR];
+    // alpha chain with the power law and every nu_j <= 45: the rate factors of a
+    // state within 2^-32 of a known one in T may be carried to first order
+    int rate_taylor;
     // alpha chain: reaction j's share of the Newton matrix, per row (E, X_0, the
     // consumed X_j, the product X_{j+1}) and column (E, X_0, X_j); see build_chain
     double kc[SDCD_MAXR][12];
@@ -62,7 +65,11 @@ inline void set_chain_coefs(NetParams& P) {
         P.amp[j] = 0.0;
         for (int e = 0; e < 12; e++) P.kc[j][e] = 0.0;
     }
+    P.rate_taylor = 0;
     if (P.topo != TOPO_CHAIN) return;
+    P.rate_taylor = P.law == LAW_POWER;
+    for (int j = 0; j < P.nreac; j++)
+        if (!(P.nu[j] >= 0.0 && P.nu[j] <= 45.0)) P.rate_taylor = 0;
     const double* m = P.mass;
     for (int j = 0; j < P.nreac; j++) {
         P.amp[j] = j == 0 ? P.a[0] / (m[0] * m[0] * m[0]) : P.a[j] / (m[j] * m[0]);

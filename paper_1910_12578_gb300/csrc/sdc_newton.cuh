@@ -212,8 +212,20 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
         if (positive_finite(T)) {
             double kf[NR], dkf[NR], Yf[NS], Rf[N];
             if constexpr (TOPO == TOPO_CHAIN) {
-                double dff;
-                rate_consts_k<NR>(P, S.ak, T, kf, dff);
+                // delta = (T - T_w) / T_w from the energy step (tr_0 - w_0 is exact:
+                // the two lie within a factor of two; dfac = 1 / T_w for the power
+                // law).  Where |delta| <= 2^-32, kappa_j(T) = kappa_j(T_w) (1 + nu_j
+                // delta) to within the rounding of kappa: the next term of
+                // (1 + delta)^nu_j, nu_j (nu_j - 1) delta^2 / 2, is below 2^-55 for
+                // nu_j <= 45 (P.rate_taylor).  Else the rate factors are evaluated.
+                const double delta = P.gm1 * (tr[0] - S.w[0]) * S.inv_rho * S.dfac;
+                if (P.rate_taylor && mag2(delta) <= mag2(0x1p-32)) {
+#pragma unroll
+                    for (int j = 0; j < NR; j++) kf[j] = fma(S.k[j], P.nu[j] * delta, S.k[j]);
+                } else {
+                    double dff;
+                    rate_consts_k<NR>(P, S.ak, T, kf, dff);
+                }
                 sources<NS, TOPO>(P, S.rho, kf, tr + 1, Rf);
             } else {
                 rate_consts<NR>(P, S.rho, T, kf, dkf);
