@@ -45,13 +45,14 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per zone of one Newton launch, from one ncu
 # capture per kernel variant and precision, keyed by (nspec, Newton variant, prec).  The 13-species captures
 # ran on a 128^3 box of the 256^3 workload's network (2.1M zones: every array of the launch exceeds L2, so its
-# writes reach DRAM and the traffic grows in proportion to the zones; algorithmic 544 B per zone), so a launch
+# writes reach DRAM and the traffic grows in proportion to the zones; algorithmic 512 B per zone: the rhs and
+# R^{m+1,(k)} read, the new state and R written), mean over the 8 launches of a step, so a launch
 # over N zones moves N times this.  The 7-species capture ran on the 64^3 box itself (its writes still sit in
 # the 129 MB L2 when the launch ends).  A variant or precision without a capture reports null.
 NEWTON_TRAFFIC_PER_ZONE = {
-    (13, 2, "fp64"): (554.7e6 + 530.7e6) / 2097152,      # newton_kernel<13, chain, double>, static grid
-    (13, 2, "fp32jac"): (555.3e6 + 515.7e6) / 2097152,   # newton_kernel<13, chain, float>
-    (7, 0, "fp64"): (44.2e6 + 2.9e6) / 262144,           # newton_kernel<7, chain, double> on the 64^3 box
+    (13, 2, "fp64"): (538.6e6 + 526.5e6) / 2097152,      # newton_kernel<13, chain, double>, static grid
+    (13, 2, "fp32jac"): (554.2e6 + 556.7e6) / 2097152,   # newton_kernel<13, chain, float>
+    (7, 0, "fp64"): (42.1e6 + 2.3e6) / 262144,           # newton_kernel<7, chain, double> on the 64^3 box
 }
 # The same for one advective term of the direction-split passes (x, y, z; A only), 128^3 box, 13 species.
 STENCIL_TRAFFIC_PER_ZONE = {13: (302.8e6 + 547.8e6 + 604.2e6 + 257.7e6 + 646.8e6 + 261.5e6) / 2097152}

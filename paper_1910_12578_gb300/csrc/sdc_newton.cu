@@ -361,12 +361,23 @@ reaction_source_kernel(NetParams P, long long N, int dim, const double* __restri
         const double m = U[(1 + d) * N + z];
         m2 += m * m;
     }
-    const double inv_rho = 1.0 / rho;
+    const double inv_rho = rcp_nr(rho);
     const double T = P.gm1 * (U[(1 + dim) * N + z] - 0.5 * m2 * inv_rho) * inv_rho;
-    double k[NR], dk[NR], Y[NS], Rz[NW];
-    rate_consts<NR>(P, rho, T, k, dk);
+    double k[NR], Y[NS], Rz[NW];
+    if constexpr (TOPO == TOPO_CHAIN) {
+        // the chain's rates as products of the unknowns: kappa_j = (amp_j / rho) f_j(T)
+        double ak[NR], dfac;
 #pragma unroll
-    for (int i = 0; i < NS; i++) Y[i] = U[(2 + dim + i) * N + z] * (inv_rho * P.inv_mass[i]);
+        for (int j = 0; j < NR; j++) ak[j] = P.amp[j] * inv_rho;
+        rate_consts_k<NR>(P, ak, T, k, dfac);
+#pragma unroll
+        for (int i = 0; i < NS; i++) Y[i] = U[(2 + dim + i) * N + z];
+    } else {
+        double dk[NR];
+        rate_consts<NR>(P, rho, T, k, dk);
+#pragma unroll
+        for (int i = 0; i < NS; i++) Y[i] = U[(2 + dim + i) * N + z] * (inv_rho * P.inv_mass[i]);
+    }
     sources<NS, TOPO>(P, rho, k, Y, Rz);
 #pragma unroll
     for (int r = 0; r < NW; r++) R[r * N + z] = Rz[r];

@@ -31,6 +31,8 @@
 
 namespace sdcd {
 
+__device__ __forceinline__ void prefetch_l2(const double* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 template <int D> struct SplitShape;
 template <> struct SplitShape<0> { static constexpr int L = 32, NL = 8; };
 template <> struct SplitShape<1> { static constexpr int L = 16, NL = 16; };
@@ -104,6 +106,27 @@ stencil_split_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __r
         return b.off + c[0] + (long long)b.n[0] * (c[1] + (long long)b.n[1] * c[2]);
     };
 
+    // the global data of phase 5 (the partial sums of A, and with the rhs the
+    // node state, the previous iterate's A and R), requested into L2 now so
+    // that the end of the tile does not wait on HBM
+    if (!FIRST && tid < G::NO) {
+        int li, p;
+        G::item(tid, L, li, p);
+        if (t.o[G::A] + li < nA && t.o[D] + p < nD) {
+            const long long gi = zone_of(li, p);
+#pragma unroll
+            for (int f = 0; f < NV; f++) prefetch_l2(Aout + f * Ntot + gi);
+            if (LAST && MODE == STENCIL_A_RHS) {
+#pragma unroll
+                for (int f = 0; f < NV; f++) {
+                    prefetch_l2(U + f * Ntot + gi);
+                    prefetch_l2(ra.Aold_m + f * Ntot + gi);
+                }
+#pragma unroll
+                for (int r = 0; r < NV - 1 - DIM; r++) prefetch_l2(ra.Rnext + r * Ntot + gi);
+            }
+        }
+    }
     // ---- 1. stage the primitives of every line and its halo
     {
         int li, j;
