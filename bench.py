@@ -8,15 +8,16 @@ graph) over the whole box from the same seeded initial state.
 
 Default workload: 256^3 periodic box (16.8M zones), 13-species alpha chain
 (14 x 14 Newton system), 3 Gauss-Lobatto nodes, 4 SDC iterations: the FP64
-path is the headline and the FP32-Jacobian / FP64-residual path of the same
-workload is measured in the same run (the "fp32jac" object), each with its
-error against the FP64 oracle.  Inputs are resident in HBM when the timed
+path is the headline; the FP32-Jacobian / FP64-residual path and the
+float-pair Jacobian path of the same workload are measured in the same run (the
+"fp32jac" and "fp32x2jac" objects), each with its error against the FP64
+oracle.  Inputs are resident in HBM when the timed
 region starts; the state (2.4 GB) is larger than L2, and L2 is also flushed
 (256 MB write) before every timed step.
 
 Usage:
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config box256|box64|batch200]
-                  [--prec both|fp64|fp32jac]
+                  [--prec all|both|fp64|fp32jac|fp32x2jac]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 Under torchrun each rank runs its own box (independent problems, weak scaling).
 """
@@ -55,6 +56,7 @@ NEWTON_TRAFFIC_PER_ZONE = {
     (7, 0, "fp64"): (42.1e6 + 2.3e6) / 262144,           # newton_kernel<7, chain, double> on the 64^3 box
 }
 # The same for one advective term of the direction-split passes (x, y, z; A only), 128^3 box, 13 species.
+PREC_NAMES = {0: "fp64", 1: "fp32jac", 2: "fp32x2jac"}   # sdc_precision values
 STENCIL_TRAFFIC_PER_ZONE = {13: (302.8e6 + 547.8e6 + 604.2e6 + 257.7e6 + 646.8e6 + 261.5e6) / 2097152}
 
 
@@ -66,9 +68,10 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--config", choices=["box64", "box256", "batch200"], default="box256")
     p.add_argument("--no-autotune", action="store_true")
-    p.add_argument("--prec", choices=["both", "fp64", "fp32jac"], default="both",
-                   help="both: the FP64 path is the headline, the FP32-Jacobian path of the same workload is "
-                        "measured in the same run")
+    p.add_argument("--prec", choices=["all", "both", "fp64", "fp32jac", "fp32x2jac"], default="all",
+                   help="all: the FP64 path is the headline, the FP32-Jacobian and the float-pair Jacobian paths "
+                        "of the same workload are measured in the same run; both: FP64 and FP32 Jacobian; "
+                        "otherwise that path alone")
     p.add_argument("--space-order", type=int, choices=[2, 4], default=2,
                    help="2: PLM/MC/HLLC; 4: the fourth-order finite-volume operators")
     p.add_argument("--limiter", type=int, choices=[0, 1], default=1,
@@ -342,7 +345,7 @@ def bench_config(args, desc, P):
     P0 = as_list(P)[0]
     return {"workload": desc, "zones": nzones(P), "nspec": P0.net.nspec, "n_nodes": P0.n_nodes,
             "iters": P0.n_iters, "nodes": args.nodes, "space_order": args.space_order, "limiter": args.limiter,
-            "seed": args.seed, "prec": "fp32jac" if args.prec == "fp32jac" else "fp64",
+            "seed": args.seed, "prec": args.prec if args.prec in ("fp32jac", "fp32x2jac") else "fp64",
             "l2": "inputs larger than L2 at 256^3; L2 also flushed before every timed step (256 MB write)",
             "parallelism": "independent box per GPU" if args.gpus > 1 else "1 GPU"}
 
@@ -592,10 +595,10 @@ def measure(args, P, U, prec, ws, barrier, flush, with_e2e=True):
         fp64_total += lin_total
         fp32_total = 0
     else:
-        fp32_total = lin_total
+        fp32_total = lin_total   # in FP32, or in float pairs on the FP32 pipe
     achieved = fp64_total / nl / (newton_ms_launch * 1e-3) / 1e12
     newton_choice = tuning["newton_choice"] if tuning else 0
-    pkey = "fp64" if prec == sdc.PREC_FP64 else "fp32jac"
+    pkey = PREC_NAMES[prec]
     per_zone = NEWTON_TRAFFIC_PER_ZONE.get((P0.net.nspec, newton_choice, pkey))
     roof = {"kernel": "newton_*_kernel<%d> (implicit reaction update, variant %d)" % (P0.net.nspec, newton_choice),
             "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -614,7 +617,12 @@ def measure(args, P, U, prec, ws, barrier, flush, with_e2e=True):
         roof["fp32_flops_per_launch"] = fp32_total / nl
         roof["fp32_achieved"] = fp32_total / nl / (newton_ms_launch * 1e-3) / 1e12
         roof["fp32_peak"] = FP32_PEAK_TFLOPS
-        roof["note"] += "; FP32 Jacobian: matrix and elimination in FP32 (fp32_*), the rest in FP64"
+        if prec == sdc.PREC_FP32_JAC:
+            roof["note"] += "; FP32 Jacobian: matrix and elimination in FP32 (fp32_*), the rest in FP64"
+        else:
+            roof["note"] += ("; float-pair Jacobian: matrix and elimination in double-float arithmetic on the FP32 "
+                             "pipe (fp32_* counts their algorithmic flops, each about 10-15 FP32 instructions), "
+                             "the rest in FP64")
     n_st = pr.launches_stencil
     st_bytes = nzones(P) * (stencil_bytes_per_zone(P0, False) * P0.n_iters +
                             stencil_bytes_per_zone(P0, True) * (P0.n_nodes - 2) * P0.n_iters) / max(n_st, 1)
@@ -684,8 +692,9 @@ def run_ours(args):
         if ws > 1:
             torch.distributed.barrier()
 
-    precs = {"both": [sdc.PREC_FP64, sdc.PREC_FP32_JAC], "fp64": [sdc.PREC_FP64],
-             "fp32jac": [sdc.PREC_FP32_JAC]}[args.prec]
+    precs = {"all": [sdc.PREC_FP64, sdc.PREC_FP32_JAC, sdc.PREC_FP32X2_JAC],
+             "both": [sdc.PREC_FP64, sdc.PREC_FP32_JAC], "fp64": [sdc.PREC_FP64],
+             "fp32jac": [sdc.PREC_FP32_JAC], "fp32x2jac": [sdc.PREC_FP32X2_JAC]}[args.prec]
     head, head_out, ctx, U0 = measure(args, P, U, precs[0], ws, barrier, flush)
     dt = head["dt"]
 
@@ -774,46 +783,48 @@ def run_ours(args):
     del ctx, U0
     torch.cuda.empty_cache()
 
-    # ---- the FP32-Jacobian path of the same workload
-    second, second_out = None, None
-    if len(precs) > 1:
-        second, second_out, ctx2, U02 = measure(args, P, U, precs[1], ws, barrier, flush)
+    # ---- the FP32-Jacobian and float-pair Jacobian paths of the same workload
+    others = []
+    for pr_ in precs[1:]:
+        rec2, out2, ctx2, U02 = measure(args, P, U, pr_, ws, barrier, flush)
+        others.append((pr_, rec2, out2))
         ctx2.close()
         del ctx2, U02
         torch.cuda.empty_cache()
 
     line = None
     if rank == 0:
-        cpu, err, err2 = None, None, None
+        cpu, err = None, None
+        errs = [None] * len(others)
         if ws == 1 and not args.no_cpu_baseline:
             cpu = cpu_baseline(args, P, U, dt)
             Pr, ref, cut, rdesc = oracle_reference(P, U, dt)
             err = field_errors(Pr, cut(head_out.reshape(P0.nvar, -1)), ref)
             err["sample"] = rdesc
-            if second is not None:
-                err2 = field_errors(Pr, cut(second_out.reshape(P0.nvar, -1)), ref)
-                err2["sample"] = rdesc
-        prec_name = lambda p: "fp64" if p == sdc.PREC_FP64 else "fp32jac"
-        dtype = lambda p: "f64" if p == sdc.PREC_FP64 else "f64 residual/update, f32 Jacobian/LU"
+            for i, (_, _, out2) in enumerate(others):
+                errs[i] = field_errors(Pr, cut(out2.reshape(P0.nvar, -1)), ref)
+                errs[i]["sample"] = rdesc
+        dtype = lambda p: {sdc.PREC_FP64: "f64", sdc.PREC_FP32_JAC: "f64 residual/update, f32 Jacobian/LU",
+                           sdc.PREC_FP32X2_JAC: "f64 residual/update, float-pair (2 x f32) Jacobian/LU"}[p]
         cfg = bench_config(args, desc, P)
         line = {
             "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype(precs[0]), "data": "synthetic",
             "config": cfg, "clocks": head["clocks"], "e2e": head["e2e"],
-            "gpu_launches": head["gpu_launches"] + (second["gpu_launches"] if second else 0),
+            "gpu_launches": head["gpu_launches"] + sum(r["gpu_launches"] for _, r, _ in others),
             "roofline": head["roofline"], "roofline_stencil": head["roofline_stencil"],
             "kernel_variants": head["kernel_variants"], "profile_ms": head["profile_ms"],
             "newton": head["newton"], "cpu_baseline": cpu, "oracle_error": err,
         }
-        if second is not None:
-            line["fp32jac"] = {
-                "prec": prec_name(precs[1]), "dtype": dtype(precs[1]), "value": second["value"],
-                "ms_per_step": second["ms_per_step"], "speedup_vs_fp64": head["ms_per_step"] / second["ms_per_step"],
-                "e2e": second["e2e"], "clocks": second["clocks"], "roofline": second["roofline"],
-                "kernel_variants": second["kernel_variants"], "profile_ms": second["profile_ms"],
-                "newton": second["newton"], "oracle_error": err2,
-                "note": "same workload, steps and warm-up as the headline; gpu_launches counts both runs"}
+        for (pr_, rec2, _), err2 in zip(others, errs):
+            line[PREC_NAMES[pr_]] = {
+                "prec": PREC_NAMES[pr_], "dtype": dtype(pr_), "value": rec2["value"],
+                "ms_per_step": rec2["ms_per_step"], "speedup_vs_fp64": head["ms_per_step"] / rec2["ms_per_step"],
+                "e2e": rec2["e2e"], "clocks": rec2["clocks"], "roofline": rec2["roofline"],
+                "kernel_variants": rec2["kernel_variants"], "profile_ms": rec2["profile_ms"],
+                "newton": rec2["newton"], "oracle_error": err2,
+                "note": "same workload, steps and warm-up as the headline; gpu_launches counts every run"}
         line["adjoint"] = adjoint
         line["strang"] = strang
         print(json.dumps(line), flush=True)

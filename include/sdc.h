@@ -54,7 +54,20 @@ typedef enum {
     SDC_ERR_TOO_LARGE = 7      /* the problem does not fit the fixed scratch of sdc_step_static */
 } sdc_status;
 
-typedef enum { SDC_PREC_FP64 = 0, SDC_PREC_FP32_JAC = 1 } sdc_precision;
+/* Precision of the Newton matrix and its elimination (section 2's implicit
+   reaction update; the residual, the rates, the quadrature and the update are
+   FP64 in every mode):
+   SDC_PREC_FP64       FP64 throughout;
+   SDC_PREC_FP32_JAC   the Jacobian build and LU in FP32, so that Newton acts as
+                       iterative refinement of the FP64 residual;
+   SDC_PREC_FP32X2_JAC the Jacobian build and LU in pairs of FP32 values
+                       (double-float arithmetic on the FP32 pipe, about 48
+                       significant bits): Newton's step to about 2^-44 relative.
+                       Alpha-chain networks only (SDC_ERR_INVALID_ARG otherwise),
+                       one zone per thread (Newton variants without lane groups).
+   The FP64 and FP32-pair modes start each node's Newton solve from the explicit
+   predictor rhs + dt_m R^{m+1,(k)}; the FP32 mode from the previous iterate. */
+typedef enum { SDC_PREC_FP64 = 0, SDC_PREC_FP32_JAC = 1, SDC_PREC_FP32X2_JAC = 2 } sdc_precision;
 
 /* rate laws of the network: r_j = a_j rho^(o_j-1) f_j(T) prod_reactants Y^cnt,
    Y_i = X_i / mass_i, o_j = total reactant count */
@@ -215,7 +228,10 @@ sdc_status sdc_selftest_pow(const double* T, const double* nu, long long n, doub
    many Newton iterations do not hold their warp; 2 = the same with a queue of
    32-zone chunks per warp; 3 (5- and 7-species chains) = a group of 4 lanes per
    zone.  13-species chain: 0 / 1 = a group of 4 / 2 lanes per zone; 2, 3, 4 =
-   variants 0, 1, 2 of the smaller networks.  Defaults: 0, 0. */
+   variants 0, 1, 2 of the smaller networks.  Defaults: 0, 0 (SDC_PREC_FP32X2_JAC,
+   which has no lane-group kernels: Newton default 2 for 13 species; variant 3
+   of the smaller chains and 0, 1 of the 13-species chain are refused by
+   sdc_set_variants and skipped by sdc_autotune, whose ms_newton stays 0 there). */
 #define SDC_MAX_VARIANTS 8
 typedef struct {
     int stencil_variants, newton_variants;  /* candidates tried */

@@ -448,7 +448,7 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
                 // from the predictor that test passes after one refinement step,
                 // which leaves trace species at about 1e-7 of themselves
                 const double* guess = (k == 0) ? node[0] : node[m + 1];
-                const double* Rpred = c->prec == SDC_PREC_FP64 ? Rold[m + 1] : nullptr;
+                const double* Rpred = c->prec != SDC_PREC_FP32_JAC ? Rold[m + 1] : nullptr;
                 unsigned long long* q = (c->d_queue && qslot < QUEUE_SLOTS) ? c->d_queue + qslot++ : nullptr;
                 if (fourth && !Rpred) {
                     SDC_LAUNCH(prof, CLS_NEWTON, launch_newton4(c->P, c->cfg, c->prec, c->dim, N, c->d_boxes, c->nbox,
@@ -651,7 +651,7 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     if (!(prm->gamma > 1.0) || prm->n_nodes < 2 || prm->n_nodes > 3 + (prm->node_type == SDC_NODES_RADAU) ||
         prm->n_iters < 1 ||
         prm->newton_maxit < 1 || !(prm->newton_rtol > 0.0) ||
-        (prm->prec != SDC_PREC_FP64 && prm->prec != SDC_PREC_FP32_JAC) ||
+        (prm->prec != SDC_PREC_FP64 && prm->prec != SDC_PREC_FP32_JAC && prm->prec != SDC_PREC_FP32X2_JAC) ||
         (prm->node_type != SDC_NODES_LOBATTO && prm->node_type != SDC_NODES_RADAU) ||
         (prm->space_order != 2 && prm->space_order != 4))
         return SDC_ERR_INVALID_ARG;
@@ -661,6 +661,8 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
         topo_used = TOPO_GENERIC;
         if (!newton_supported(net->nspec, topo_used)) return SDC_ERR_INVALID_ARG;
     }
+    // the float-pair matrix: the alpha chain's bordered form only
+    if (prm->prec == SDC_PREC_FP32X2_JAC && topo_used != TOPO_CHAIN) return SDC_ERR_INVALID_ARG;
     // the per-thread rate arrays hold nspec - 1 reactions
     if (net->nreac > net->nspec - 1) return SDC_ERR_INVALID_ARG;
     if (!stencil_supported(dim, net->nspec)) return SDC_ERR_INVALID_ARG;
@@ -679,6 +681,7 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     c->K = prm->n_iters;
     c->limiter = prm->limiter ? 1 : 0;
     c->prec = prm->prec;
+    c->newton_variant = newton_default_variant(net->nspec, topo_used, prm->prec);
     c->cfg.rtol = prm->newton_rtol;
     c->cfg.maxit = prm->newton_maxit;
     c->space_order = prm->space_order;
@@ -988,12 +991,14 @@ sdc_status sdc_autotune(sdc_ctx* ctx, const double* U, double dt, sdc_tuning* ou
         t.ms_stencil[v] = a;
         if (st == SDC_OK && (v == 0 || a < best_st)) { best_st = a; vs = v; }
     }
+    bool first_nw = true;
     for (int v = 0; v < t.newton_variants && st == SDC_OK; v++) {
+        if (!newton_variant_ok(ctx->nspec, ctx->P.topo, ctx->prec, v)) continue;  // not built for this precision
         ctx->newton_variant = v;
         float a, b;
         st = trial(&a, &b);
         t.ms_newton[v] = b;
-        if (st == SDC_OK && (v == 0 || b < best_nw)) { best_nw = b; vn = v; }
+        if (st == SDC_OK && (first_nw || b < best_nw)) { best_nw = b; vn = v; first_nw = false; }
     }
     cudaFree(scratch);
     if (st != SDC_OK) {
@@ -1013,7 +1018,7 @@ sdc_status sdc_autotune(sdc_ctx* ctx, const double* U, double dt, sdc_tuning* ou
 
 sdc_status sdc_set_variants(sdc_ctx* ctx, int stencil_variant, int newton_variant) {
     if (!ctx || stencil_variant < 0 || stencil_variant >= stencil_variants(ctx->dim, ctx->nspec) ||
-        newton_variant < 0 || newton_variant >= newton_variants(ctx->nspec, ctx->P.topo))
+        !newton_variant_ok(ctx->nspec, ctx->P.topo, ctx->prec, newton_variant))
         return SDC_ERR_INVALID_ARG;
     if (stencil_variant == stencil_split_variant(ctx->dim, ctx->nspec) && !ctx->prim) return SDC_ERR_INVALID_ARG;
     SDC_TRY(set_stencil_variant(ctx, stencil_variant));
@@ -1030,7 +1035,7 @@ sdc_status sdc_launches_per_step(const sdc_ctx* ctx, int* launches) {
         // fourth order: A is a sequence of kernels and is evaluated apart from
         // the rhs at nodes m >= 1; the source and the implicit update add maps
         const int LA = fourth_advective_launches(ctx->dim, ctx->limiter), K = ctx->K, M = ctx->M;
-        const int predict = ctx->prec == SDC_PREC_FP64 ? 1 : 0;  // the FP64 Newton start's kernel
+        const int predict = ctx->prec != SDC_PREC_FP32_JAC ? 1 : 0;  // the predictor start's kernel
         *launches = 1 + LA + FOURTH_SOURCE_LAUNCHES + K * (M - 1) * (1 + predict + FOURTH_NEWTON_LAUNCHES) +
                     K * (M - 2) * LA + (K - 1) * LA;
         return SDC_OK;
@@ -1254,7 +1259,7 @@ extern "C" sdc_status sdc_step_static(const sdc_box* boxes, int nbox, const sdc_
     }
     if (!(prm->gamma > 1.0) || (prm->n_nodes != 2 && prm->n_nodes != 3) || prm->n_iters < 1 ||
         prm->newton_maxit < 1 || !(prm->newton_rtol > 0.0) ||
-        (prm->prec != SDC_PREC_FP64 && prm->prec != SDC_PREC_FP32_JAC) ||
+        (prm->prec != SDC_PREC_FP64 && prm->prec != SDC_PREC_FP32_JAC && prm->prec != SDC_PREC_FP32X2_JAC) ||
         (prm->node_type != SDC_NODES_LOBATTO && prm->node_type != SDC_NODES_RADAU) ||
         (prm->space_order != 2 && prm->space_order != 4))
         return SDC_ERR_INVALID_ARG;
@@ -1264,6 +1269,7 @@ extern "C" sdc_status sdc_step_static(const sdc_box* boxes, int nbox, const sdc_
         topo = TOPO_GENERIC;
         if (!newton_supported(net->nspec, topo)) return SDC_ERR_INVALID_ARG;
     }
+    if (prm->prec == SDC_PREC_FP32X2_JAC && topo != TOPO_CHAIN) return SDC_ERR_INVALID_ARG;
     if (!stencil_supported(dim, net->nspec)) return SDC_ERR_INVALID_ARG;
 
     // tables and sizes (stack only)
@@ -1334,6 +1340,7 @@ extern "C" sdc_status sdc_step_static(const sdc_box* boxes, int nbox, const sdc_
     c.K = prm->n_iters;
     c.limiter = prm->limiter ? 1 : 0;
     c.prec = prm->prec;
+    c.newton_variant = newton_default_variant(net->nspec, topo, prm->prec);
     c.cfg.rtol = prm->newton_rtol;
     c.cfg.maxit = prm->newton_maxit;
     weights(prm->node_type, M, c.tau, c.q);

@@ -36,7 +36,7 @@ struct NetParams {
     int r0[SDCD_MAXR], c0[SDCD_MAXR], r1[SDCD_MAXR], c1[SDCD_MAXR], prod[SDCD_MAXR];
     int order[SDCD_MAXR];                // sum of reactant multiplicities
     // alpha chain: a_j / prod_reactants mass (with multiplicity), so that
-    // r_j = (amp_j / rho) f_j(T) prod_reactants (rho X)^count
+    // rho r_j = amp_j f_j(T) prod_reactants (rho X)^count
     double amp[SDCD_MAXR];
     // alpha chain with the power law and every nu_j <= 45: the rate factors of a
     // state within 2^-32 of a known one in T may be carried to first order
@@ -44,7 +44,11 @@ struct NetParams {
     // alpha chain: reaction j's share of the Newton matrix, per row (E, X_0, the
     // consumed X_j, the product X_{j+1}) and column (E, X_0, X_j); see build_chain
     double kc[SDCD_MAXR][12];
+    // alpha chain: reaction j's coefficients in the sources, mass_i s_ij for
+    // i = X_0, the consumed X_j (none for j = 0) and the product X_{j+1}
+    double rs[SDCD_MAXR][3];
     float kcf[SDCD_MAXR][12];
+    float kcl[SDCD_MAXR][12];  // kc - kcf: the float pair (kcf, kcl) of the FP32-pair matrix
 };
 
 // Coefficients of build_chain from the masses and energies of the alpha chain
@@ -64,6 +68,8 @@ inline void set_chain_coefs(NetParams& P) {
     for (int j = 0; j < SDCD_MAXR; j++) {
         P.amp[j] = 0.0;
         for (int e = 0; e < 12; e++) P.kc[j][e] = 0.0;
+        for (int e = 0; e < 12; e++) P.kcf[j][e] = P.kcl[j][e] = 0.0f;
+        P.rs[j][0] = P.rs[j][1] = P.rs[j][2] = 0.0;
     }
     P.rate_taylor = 0;
     if (P.topo != TOPO_CHAIN) return;
@@ -73,6 +79,9 @@ inline void set_chain_coefs(NetParams& P) {
     const double* m = P.mass;
     for (int j = 0; j < P.nreac; j++) {
         P.amp[j] = j == 0 ? P.a[0] / (m[0] * m[0] * m[0]) : P.a[j] / (m[j] * m[0]);
+        P.rs[j][0] = (j == 0 ? -3.0 : -1.0) * m[0];
+        P.rs[j][1] = j == 0 ? 0.0 : -m[j];
+        P.rs[j][2] = m[j + 1];
         double* c = P.kc[j];
         const double f0 = j == 0 ? 3.0 : 1.0;        // dP/dw_0 = f0 * (w_0^2 or w_j)
         const double s0 = j == 0 ? -3.0 : -1.0;      // stoichiometry of A_0
@@ -97,7 +106,10 @@ inline void set_chain_coefs(NetParams& P) {
         c[3] *= P.nu[j];
         c[6] *= P.nu[j];
         c[9] *= P.nu[j];
-        for (int e = 0; e < 12; e++) P.kcf[j][e] = (float)c[e];
+        for (int e = 0; e < 12; e++) {
+            P.kcf[j][e] = (float)c[e];
+            P.kcl[j][e] = (float)(c[e] - (double)P.kcf[j][e]);
+        }
     }
 }
 
@@ -157,7 +169,7 @@ __device__ __forceinline__ void rate_consts(const NetParams& P, double rho, doub
 // k_j only, and the factor f with dk_j/dT = nu_j k_j f (power law: f = 1/T;
 // Arrhenius: f = 1/T^2): the alpha chain's matrix takes nu_j from its
 // coefficients (set_chain_coefs), so the solve needs no dk_j.
-// ak[j] = a_j rho^(o_j - 1), fixed during one zone's solve (k_j = ak[j] f_j(T)).
+// ak[j]: the prefactor of k_j = ak[j] f_j(T) (the alpha chain's amp_j).
 template <int NR>
 __device__ __forceinline__ void rate_consts_k(const NetParams& P, const double* ak, double T, double* k,
                                               double& dfac) {
@@ -208,6 +220,33 @@ __device__ __forceinline__ void source_sums(const NetParams& P, const double* k,
             if (P.r1[j] >= 0) S[P.r1[j]] -= P.c1[j] * r;
             S[P.prod[j]] += r;
         }
+    }
+}
+
+// The alpha chain's sources from kappa_j = amp_j f_j(T) and the unknowns w_X
+// (rho X_i) themselves: with P_j = w_0^3 (j = 0) or w_j w_0,
+//   R(rho X_i) = sum_j mass_i s_ij kappa_j P_j,   R(rho E) = sum_j Q_j kappa_j P_j
+// (the density and the masses of Y_i = X_i / mass_i folded into kappa_j, the
+// masses of the rows into the coefficients rs).  Rm = [R(rho E), R(rho X_i)].
+template <int NS>
+__device__ __forceinline__ void sources_w(const NetParams& P, const double* k, const double* w, double* Rm) {
+    constexpr int NR = NS - 1;
+    double r[NR];
+#pragma unroll
+    for (int j = 0; j < NR; j++) r[j] = (j == 0) ? k[0] * (w[0] * w[0] * w[0]) : k[j] * (w[j] * w[0]);
+    double RE = P.Q[0] * r[0], S0 = P.rs[0][0] * r[0];
+#pragma unroll
+    for (int j = 1; j < NR; j++) {
+        RE = fma(P.Q[j], r[j], RE);
+        S0 = fma(P.rs[j][0], r[j], S0);
+    }
+    Rm[0] = RE;
+    Rm[1] = S0;
+#pragma unroll
+    for (int i = 1; i < NS; i++) {
+        // made by reaction i - 1, used by reaction i (the last species is not used)
+        const double made = P.rs[i - 1][2] * r[i - 1];
+        Rm[1 + i] = (i < NR) ? fma(P.rs[i][1], r[i], made) : made;
     }
 }
 
@@ -319,16 +358,26 @@ struct ChainSys {
     MT dEE, dEA, dAE, dAA;  // M[E][E], M[E][X_0], M[X_0][E], M[X_0][X_0]
 };
 
-// Entries of ChainSys: M = c I - dt_m dR/dw from kappa_j and w, with the
-// per-reaction coefficients of set_chain_coefs.  With P_j = w_j w_0
-// (P_0 = w_0^3), reaction j contributes t_E = dt_m (gamma-1) f kappa_j P_j to
-// the E column (nu_j is in the coefficients; f from rate_consts_k),
-// t_A = dt_m rho kappa_j dP_j/dw_0 (without the factor 3 of j = 0) to the X_0
-// column and t_J = dt_m rho kappa_j w_0 to the X_j column.  ws = w_1.. (the
-// species part of w), dtr = dt_m rho.
+// Entries of ChainSys: M = c I - dt_m dR/dw from kappa_j = amp_j f_j(T) (the
+// rates of sources_w) and w, with the per-reaction coefficients of
+// set_chain_coefs.  With P_j = w_j w_0 (P_0 = w_0^3), reaction j contributes
+// t_E = dt_m (gamma-1) (f / rho) kappa_j P_j to the E column (dT/d(rho E) =
+// (gamma-1)/rho; nu_j is in the coefficients, f from rate_consts_k),
+// t_A = dt_m kappa_j dP_j/dw_0 (without the factor 3 of j = 0) to the X_0
+// column and t_J = dt_m kappa_j w_0 to the X_j column.  ws = w_1.. (the species
+// part of w), dfac = f / rho.
+
+// reaction j's coefficient e of build_chain in the matrix's working type
+template <typename MT> __device__ __forceinline__ MT chain_coef(const NetParams& P, int j, int e);
+template <> __device__ __forceinline__ double chain_coef<double>(const NetParams& P, int j, int e) { return P.kc[j][e]; }
+template <> __device__ __forceinline__ float chain_coef<float>(const NetParams& P, int j, int e) { return P.kcf[j][e]; }
+template <> __device__ __forceinline__ f2 chain_coef<f2>(const NetParams& P, int j, int e) {
+    return f2(P.kcf[j][e], P.kcl[j][e]);
+}
+
 template <int NS, typename MT>
 __device__ __forceinline__ void build_chain(const NetParams& P, const double* k, double dfac, const double* ws,
-                                            double c, double dtm, double dtr, ChainSys<NS, MT>& A) {
+                                            double c, double dtm, ChainSys<NS, MT>& A) {
     constexpr int NC = NS - 1;
     constexpr int NR = NS - 1;
     const MT cm = to_mt<MT>(c);
@@ -339,35 +388,33 @@ __device__ __forceinline__ void build_chain(const NetParams& P, const double* k,
     }
     A.dEE = A.dAA = cm;
     A.dEA = A.dAE = (MT)0;
-    const MT dt_ = to_mt<MT>(dtr), dg = to_mt<MT>(dtm * P.gm1 * dfac);
+    const MT dt_ = to_mt<MT>(dtm), dg = to_mt<MT>(dtm * P.gm1 * dfac);
     const MT y0 = to_mt<MT>(ws[0]);
 #pragma unroll
     for (int j = 0; j < NR; j++) {
-        const MT* cf;
-        if constexpr (sizeof(MT) == 8) cf = P.kc[j];
-        else cf = P.kcf[j];
+        auto cf = [&](int e) { return chain_coef<MT>(P, j, e); };
         if (j == 0) {
             const MT y02 = y0 * y0;
             const MT k0 = to_mt<MT>(k[0]);
             const MT t = dt_ * k0;
             const MT tE = dg * k0 * (y02 * y0);
             const MT tA = t * y02;
-            A.dEE = fma(-cf[0], tE, A.dEE);   A.dEA = fma(-cf[1], tA, A.dEA);
-            A.dAE = fma(-cf[3], tE, A.dAE);   A.dAA = fma(-cf[4], tA, A.dAA);
-            A.uE[0] = fma(-cf[9], tE, A.uE[0]); A.uA[0] = fma(-cf[10], tA, A.uA[0]);
+            A.dEE = msub(A.dEE, cf(0), tE);     A.dEA = msub(A.dEA, cf(1), tA);
+            A.dAE = msub(A.dAE, cf(3), tE);     A.dAA = msub(A.dAA, cf(4), tA);
+            A.uE[0] = msub(A.uE[0], cf(9), tE); A.uA[0] = msub(A.uA[0], cf(10), tA);
         } else {
             const MT yj = to_mt<MT>(ws[j]), kj = to_mt<MT>(k[j]);
             const MT t = dt_ * kj;
             const MT tE = dg * kj * (yj * y0);
             const MT tA = t * yj, tJ = t * y0;
-            A.dEE = fma(-cf[0], tE, A.dEE);   A.dEA = fma(-cf[1], tA, A.dEA);   A.vE[j - 1] = fma(-cf[2], tJ, A.vE[j - 1]);
-            A.dAE = fma(-cf[3], tE, A.dAE);   A.dAA = fma(-cf[4], tA, A.dAA);   A.vA[j - 1] = fma(-cf[5], tJ, A.vA[j - 1]);
-            A.uE[j - 1] = fma(-cf[6], tE, A.uE[j - 1]);
-            A.uA[j - 1] = fma(-cf[7], tA, A.uA[j - 1]);
-            A.bd[j - 1] = fma(-cf[8], tJ, A.bd[j - 1]);
-            A.uE[j] = fma(-cf[9], tE, A.uE[j]);
-            A.uA[j] = fma(-cf[10], tA, A.uA[j]);
-            A.bs[j] = fma(-cf[11], tJ, A.bs[j]);
+            A.dEE = msub(A.dEE, cf(0), tE);   A.dEA = msub(A.dEA, cf(1), tA);   A.vE[j - 1] = msub(A.vE[j - 1], cf(2), tJ);
+            A.dAE = msub(A.dAE, cf(3), tE);   A.dAA = msub(A.dAA, cf(4), tA);   A.vA[j - 1] = msub(A.vA[j - 1], cf(5), tJ);
+            A.uE[j - 1] = msub(A.uE[j - 1], cf(6), tE);
+            A.uA[j - 1] = msub(A.uA[j - 1], cf(7), tA);
+            A.bd[j - 1] = msub(A.bd[j - 1], cf(8), tJ);
+            A.uE[j] = msub(A.uE[j], cf(9), tE);
+            A.uA[j] = msub(A.uA[j], cf(10), tA);
+            A.bs[j] = msub(A.bs[j], cf(11), tJ);
         }
     }
 }
@@ -403,25 +450,25 @@ __device__ __forceinline__ bool chain_solve(const ChainSys<NS, MT>& A, MT* b) {
             const MT op = sw ? cp : ns_, od = sw ? (MT)0 : nd;
             const MT ouE = sw ? cuE : nuE, ouA = sw ? cuA : nuA, og = sw ? cg : ng;
             ok = ok && (p != (MT)0);
-            const MT ip = (sizeof(MT) == 8) ? (MT)rcp_nr((double)p) : (MT)1 / p;
+            const MT ip = inv_mt(p);
             pip[k] = ip;
             const MT l = op * ip;
-            cp = od - l * e;
-            cuE = ouE - l * quE;
-            cuA = ouA - l * quA;
-            cg = og - l * qg;
+            cp = msub(od, l, e);
+            cuE = msub(ouE, l, quE);
+            cuA = msub(ouA, l, quA);
+            cg = msub(og, l, qg);
         } else {
             p = cp; e = (MT)0; quE = cuE; quA = cuA; qg = cg;
             ok = ok && (p != (MT)0);
-            pip[k] = (sizeof(MT) == 8) ? (MT)rcp_nr((double)p) : (MT)1 / p;
+            pip[k] = inv_mt(p);
         }
         pe[k] = e; puE[k] = quE; puA[k] = quA; pg[k] = qg;
         const MT lE = wE * pip[k], lA = wA * pip[k];
-        dEE -= lE * quE; dEA -= lE * quA; gE -= lE * qg;
-        dAE -= lA * quE; dAA -= lA * quA; gA -= lA * qg;
+        dEE = msub(dEE, lE, quE); dEA = msub(dEA, lE, quA); gE = msub(gE, lE, qg);
+        dAE = msub(dAE, lA, quE); dAA = msub(dAA, lA, quA); gA = msub(gA, lA, qg);
         if (k + 1 < NC) {
-            wE = A.vE[k + 1] - lE * e;
-            wA = A.vA[k + 1] - lA * e;
+            wE = msub(A.vE[k + 1], lE, e);
+            wA = msub(A.vA[k + 1], lA, e);
         }
     }
     // 2 x 2 border block, partial pivoting
@@ -429,19 +476,159 @@ __device__ __forceinline__ bool chain_solve(const ChainSys<NS, MT>& A, MT* b) {
     const MT a = sw ? dAE : dEE, bb = sw ? dAA : dEA, c2 = sw ? dEE : dAE, d2 = sw ? dEA : dAA;
     const MT r1 = sw ? gA : gE, r2 = sw ? gE : gA;
     ok = ok && (a != (MT)0);
-    const MT ia = (sizeof(MT) == 8) ? (MT)rcp_nr((double)a) : (MT)1 / a;
+    const MT ia = inv_mt(a);
     const MT l = c2 * ia;
-    const MT s22 = d2 - l * bb;
+    const MT s22 = msub(d2, l, bb);
     ok = ok && (s22 != (MT)0);
-    const MT xA = (r2 - l * r1) * ((sizeof(MT) == 8) ? (MT)rcp_nr((double)s22) : (MT)1 / s22);
-    const MT xE = (r1 - bb * xA) * ia;
+    const MT xA = msub(r2, l, r1) * inv_mt(s22);
+    const MT xE = msub(r1, bb, xA) * ia;
     b[0] = xE;
     b[1] = xA;
     MT xn = (MT)0;
 #pragma unroll
     for (int k = NC - 1; k >= 0; k--) {
-        const MT x = (pg[k] - pe[k] * xn - puE[k] * xE - puA[k] * xA) * pip[k];
+        const MT x = msub(msub(msub(pg[k], pe[k], xn), puE[k], xE), puA[k], xA) * pip[k];
         b[2 + k] = x;
+        xn = x;
+    }
+    return ok;
+}
+
+// build_chain and chain_solve in one pass, for the float-pair matrix: reaction
+// j's entries are formed when the elimination reaches the column that needs them
+// (the chain row k+1 is complete once reaction k+2 is in, and the border entries
+// at column k come from reaction k+1), so the matrix itself is never held; the
+// border block accumulates reaction terms and elimination updates in whatever
+// order they come (a different rounding order from build_chain + chain_solve,
+// the same pivots and the same algebra).  The right-hand side G (FP64, w order)
+// is converted as it is used; the step d is returned in StepType<MT>.
+// The pivot rows wait for the back substitution in shared memory: field f of
+// column kk at piv[(f NC + kk) stride] (stride = threads of the block), which
+// keeps the solve's live registers to the rows in hand.
+template <int NS, typename MT>
+__device__ __forceinline__ bool chain_build_solve(const NetParams& P, const double* k, double dfac, const double* ws,
+                                                  double c, double dtm, const double* G,
+                                                  typename StepType<MT>::type* d, MT* piv, int stride) {
+    constexpr int NC = NS - 1;
+    constexpr int NR = NS - 1;
+    const MT cm = to_mt<MT>(c);
+    const MT dt_ = to_mt<MT>(dtm), dg = to_mt<MT>(dtm * P.gm1 * dfac);
+    const MT y0 = to_mt<MT>(ws[0]);
+    const MT zero = (MT)0;
+    // border block and border right-hand side
+    MT dEE = cm, dEA = zero, dAE = zero, dAA = cm;
+    MT gE = to_mt<MT>(G[0]), gA = to_mt<MT>(G[1]);
+    // chain rows in the making: row r (complete once reaction r+1 is in) and row r+1
+    MT rbd = cm, ruE, ruA, rbs = zero;       // row r: diagonal, border columns, sub-diagonal
+    MT sbs = zero, suE = zero, suA = zero;   // row r+1: the part reaction r+1 gave
+    MT vEr = zero, vAr = zero;               // border rows at column r (reaction r+1)
+    // reaction j's terms on the rows and columns it touches
+    auto react = [&](int j, MT& uE_prev, MT& uA_prev, MT& bd_prev, MT& vE_prev, MT& vA_prev, MT& uE_j, MT& uA_j,
+                     MT& bs_j) {
+        auto cf = [&](int e) { return chain_coef<MT>(P, j, e); };
+        if (j == 0) {
+            const MT y02 = y0 * y0;
+            const MT k0 = to_mt<MT>(k[0]);
+            const MT tE = dg * k0 * (y02 * y0);
+            const MT tA = dt_ * k0 * y02;
+            dEE = msub(dEE, cf(0), tE); dEA = msub(dEA, cf(1), tA);
+            dAE = msub(dAE, cf(3), tE); dAA = msub(dAA, cf(4), tA);
+            uE_j = (MT)0 - cf(9) * tE; uA_j = (MT)0 - cf(10) * tA;
+            bs_j = zero;
+        } else {
+            const MT yj = to_mt<MT>(ws[j]), kj = to_mt<MT>(k[j]);
+            const MT t = dt_ * kj;
+            const MT tE = dg * kj * (yj * y0);
+            const MT tA = t * yj, tJ = t * y0;
+            dEE = msub(dEE, cf(0), tE); dEA = msub(dEA, cf(1), tA);
+            dAE = msub(dAE, cf(3), tE); dAA = msub(dAA, cf(4), tA);
+            vE_prev = (MT)0 - cf(2) * tJ; vA_prev = (MT)0 - cf(5) * tJ;
+            uE_prev = msub(uE_prev, cf(6), tE);
+            uA_prev = msub(uA_prev, cf(7), tA);
+            bd_prev = msub(bd_prev, cf(8), tJ);
+            uE_j = (MT)0 - cf(9) * tE; uA_j = (MT)0 - cf(10) * tA;
+            bs_j = (MT)0 - cf(11) * tJ;
+        }
+    };
+    {   // reactions 0 and 1: chain row 0 complete, border at column 0, row 1 begun
+        MT du0, du1, du2, du3, du4;
+        react(0, du0, du1, du2, du3, du4, ruE, ruA, rbs);
+        if (NR > 1) react(1, ruE, ruA, rbd, vEr, vAr, suE, suA, sbs);
+    }
+    // pivot rows: 1/p, entry at k+1, border columns, rhs
+    auto pip = [&](int kk) -> MT& { return piv[(0 * NC + kk) * stride]; };
+    auto pe = [&](int kk) -> MT& { return piv[(1 * NC + kk) * stride]; };
+    auto puE = [&](int kk) -> MT& { return piv[(2 * NC + kk) * stride]; };
+    auto puA = [&](int kk) -> MT& { return piv[(3 * NC + kk) * stride]; };
+    auto pg = [&](int kk) -> MT& { return piv[(4 * NC + kk) * stride]; };
+    MT cp = rbd, cuE = ruE, cuA = ruA, cg = to_mt<MT>(G[2]);  // the carried row
+    MT wE = vEr, wA = vAr;  // border rows at the current column
+    // row k+1 (being completed) and the border entries at column k+1
+    MT nbd = cm, nuE = suE, nuA = suA, nbs = sbs, nvE = zero, nvA = zero;
+    bool ok = true;
+#pragma unroll
+    for (int kk = 0; kk < NC; kk++) {
+        MT p, e, quE, quA, qg;
+        if (kk + 1 < NC) {
+            // reaction kk+2 completes row kk+1 and gives the border entries at column kk+1
+            MT tbd = cm, tuE = zero, tuA = zero, tbs = zero;
+            if (kk + 2 < NR) {
+                react(kk + 2, nuE, nuA, nbd, nvE, nvA, tuE, tuA, tbs);
+            }
+            const MT ns_ = nbs, nd = nbd, nu1 = nuE, nu2 = nuA, ng = to_mt<MT>(G[3 + kk]);
+            const bool sw = mag2(ns_) > mag2(cp);
+            p = sw ? ns_ : cp;
+            e = sw ? nd : zero;
+            quE = sw ? nu1 : cuE;
+            quA = sw ? nu2 : cuA;
+            qg = sw ? ng : cg;
+            const MT op = sw ? cp : ns_, od = sw ? zero : nd;
+            const MT ouE = sw ? cuE : nu1, ouA = sw ? cuA : nu2, og = sw ? cg : ng;
+            ok = ok && (p != zero);
+            const MT ip = inv_mt(p);
+            pip(kk) = ip;
+            const MT l = op * ip;
+            cp = msub(od, l, e);
+            cuE = msub(ouE, l, quE);
+            cuA = msub(ouA, l, quA);
+            cg = msub(og, l, qg);
+            pe(kk) = e; puE(kk) = quE; puA(kk) = quA; pg(kk) = qg;
+            const MT lE = wE * ip, lA = wA * ip;
+            dEE = msub(dEE, lE, quE); dEA = msub(dEA, lE, quA); gE = msub(gE, lE, qg);
+            dAE = msub(dAE, lA, quE); dAA = msub(dAA, lA, quA); gA = msub(gA, lA, qg);
+            wE = msub(nvE, lE, e);
+            wA = msub(nvA, lA, e);
+            // row kk+2 becomes the next row
+            nbd = tbd; nuE = tuE; nuA = tuA; nbs = tbs; nvE = zero; nvA = zero;
+        } else {
+            p = cp; e = zero; quE = cuE; quA = cuA; qg = cg;
+            ok = ok && (p != zero);
+            const MT ip = inv_mt(p);
+            pip(kk) = ip;
+            pe(kk) = e; puE(kk) = quE; puA(kk) = quA; pg(kk) = qg;
+            const MT lE = wE * ip, lA = wA * ip;
+            dEE = msub(dEE, lE, quE); dEA = msub(dEA, lE, quA); gE = msub(gE, lE, qg);
+            dAE = msub(dAE, lA, quE); dAA = msub(dAA, lA, quA); gA = msub(gA, lA, qg);
+        }
+    }
+    // 2 x 2 border block, partial pivoting
+    const bool sw = mag2(dAE) > mag2(dEE);
+    const MT a = sw ? dAE : dEE, bb = sw ? dAA : dEA, c2 = sw ? dEE : dAE, d2 = sw ? dEA : dAA;
+    const MT r1 = sw ? gA : gE, r2 = sw ? gE : gA;
+    ok = ok && (a != zero);
+    const MT ia = inv_mt(a);
+    const MT l = c2 * ia;
+    const MT s22 = msub(d2, l, bb);
+    ok = ok && (s22 != zero);
+    const MT xA = msub(r2, l, r1) * inv_mt(s22);
+    const MT xE = msub(r1, bb, xA) * ia;
+    d[0] = step_value(xE);
+    d[1] = step_value(xA);
+    MT xn = zero;
+#pragma unroll
+    for (int kk = NC - 1; kk >= 0; kk--) {
+        const MT x = msub(msub(msub(pg(kk), pe(kk), xn), puE(kk), xE), puA(kk), xA) * pip(kk);
+        d[2 + kk] = step_value(x);
         xn = x;
     }
     return ok;

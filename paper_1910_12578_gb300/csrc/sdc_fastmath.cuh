@@ -90,12 +90,112 @@ __device__ __forceinline__ double widen(float x) {
     return __hiloint2double((int)((f & 0x80000000u) | ((ef + 896u) << 20) | ((f >> 3) & 0xfffffu)), (int)(f << 29));
 }
 
+// ---- float pairs ---------------------------------------------------------
+// The FP32-pair Newton matrix is formed and eliminated on the FP32 pipe in
+// double-float arithmetic: a value is the unevaluated sum hi + lo of two floats
+// with |lo| below an ulp of hi (about 48 significant bits).  The operations are
+// composed from the classical error-free transformations: Knuth's TwoSum
+// (a + b = s + e exactly, six additions), Dekker's Fast2Sum (the same in three
+// when |a| >= |b|) and the exact product through the fused multiply-add
+// (a b = p + e with p = a b rounded and e = fma(a, b, -p)).  The explicitly
+// rounded intrinsics keep the compiler from contracting or reassociating them.
+// Every operation below is within a small multiple of 2^-46 of its operands'
+// magnitude (relative, for products); the solve only forms Newton's step, whose
+// residual and update stay in FP64, so the pair's rounding slows the iteration
+// by about 2^-44 times the matrix's condition number and does not move the root.
+struct f2 {
+    float hi, lo;
+    f2() = default;
+    __device__ __forceinline__ constexpr f2(float h, float l) : hi(h), lo(l) {}
+    __device__ __forceinline__ explicit f2(int v) : hi((float)v), lo(0.0f) {}  // small integers, exactly
+};
+
+// s + e = a + b exactly, given |a| >= |b| (or a = 0)
+__device__ __forceinline__ f2 fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return f2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+// s + e = a + b exactly, any order of magnitude
+__device__ __forceinline__ f2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return f2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+
+__device__ __forceinline__ f2 operator-(f2 x) { return f2(-x.hi, -x.lo); }
+
+__device__ __forceinline__ f2 operator+(f2 x, f2 y) {
+    const f2 s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+
+__device__ __forceinline__ f2 operator-(f2 x, f2 y) { return x + (-y); }
+
+// the product's leading part p and its correction e (x.lo y.lo, below 2^-46 of
+// the product, is left out)
+__device__ __forceinline__ void prod_parts(f2 x, f2 y, float& p, float& e) {
+    p = __fmul_rn(x.hi, y.hi);
+    e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+}
+
+__device__ __forceinline__ f2 operator*(f2 x, f2 y) {
+    float p, e;
+    prod_parts(x, y, p, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ bool operator!=(f2 x, f2 y) { return x.hi != y.hi || x.lo != y.lo; }
+
+// a - x y with one normalisation
+__device__ __forceinline__ f2 msub(f2 a, f2 x, f2 y) {
+    float p, e;
+    prod_parts(x, y, p, e);
+    const f2 s = two_sum(a.hi, -p);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, e)));
+}
+__device__ __forceinline__ double msub(double a, double x, double y) { return fma(-x, y, a); }
+__device__ __forceinline__ float msub(float a, float x, float y) { return fmaf(-x, y, a); }
+
+// 1/x from the hardware reciprocal y of x.hi (within an ulp: |r| <= 2^-22 for
+// r = 1 - x y) and the series 1/x = y (1 + r + r^2 + ...), cut after r^2; x
+// normal and nonzero
+__device__ __forceinline__ f2 inv_mt(f2 x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x.hi));
+    float r = __fmaf_rn(-x.hi, y, 1.0f);
+    r = __fmaf_rn(-x.lo, y, r);
+    return fast_two_sum(y, __fmul_rn(y, __fmaf_rn(r, r, r)));
+}
+__device__ __forceinline__ double inv_mt(double x) { return rcp_nr(x); }
+__device__ __forceinline__ float inv_mt(float x) { return 1.0f / x; }
+
+// |x| ordered on the integer pipe: the leading float decides
+__device__ __forceinline__ unsigned int mag2(f2 x) { return (unsigned int)__float_as_int(x.hi) << 1; }
+
 // the working type MT of a Newton matrix: identity for double
 template <typename MT> __device__ __forceinline__ MT to_mt(double x);
 template <> __device__ __forceinline__ double to_mt<double>(double x) { return x; }
 template <> __device__ __forceinline__ float to_mt<float>(double x) { return narrow(x); }
+// a double as a float pair: hi its leading 24 bits (truncated), lo the leading
+// 24 of the rest (x - hi is exact in FP64: the two share their exponent)
+template <> __device__ __forceinline__ f2 to_mt<f2>(double x) {
+    const float h = narrow(x);
+    return f2(h, narrow(x - widen(h)));
+}
 __device__ __forceinline__ double from_mt(double x) { return x; }
 __device__ __forceinline__ double from_mt(float x) { return widen(x); }
+__device__ __forceinline__ double from_mt(f2 x) { return widen(x.hi) + widen(x.lo); }
+
+// The type in which a solve's step is tested and applied: a float pair is
+// summed into a double once; a float or double step is used as it is.
+template <typename MT> struct StepType { using type = MT; };
+template <> struct StepType<f2> { using type = double; };
+__device__ __forceinline__ double step_value(f2 x) { return from_mt(x); }
+__device__ __forceinline__ double step_value(double x) { return x; }
+__device__ __forceinline__ float step_value(float x) { return x; }
 
 constexpr long long SIGN_BIT = (long long)0x8000000000000000ull;
 constexpr long long ABS_MASK = 0x7FFFFFFFFFFFFFFFll;

@@ -26,6 +26,8 @@ cudaError_t stencil_prepare(int dim, int nspec);  // raise the dynamic shared-me
 // same grid and counter, 32 neighbouring zones per warp at a time.  The
 // 13-species group kernel: 4 lanes per zone (0) or 2 (1).
 int newton_variants(int nspec, int topo);
+bool newton_variant_ok(int nspec, int topo, int prec, int variant);
+int newton_default_variant(int nspec, int topo, int prec);
 bool newton_group_case(int nspec, int topo);  // the 13-species chain (a group of lanes per zone)
 // Rpred: R^{m+1,(k)} of the sweep (the start is then the explicit predictor where
 // admissible, the guess elsewhere), or nullptr (the start is the guess)

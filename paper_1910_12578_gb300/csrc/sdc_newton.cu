@@ -8,6 +8,16 @@ namespace sdcd {
 
 constexpr int NEWTON_BLOCK = 128;
 
+// Resident blocks per SM the one-zone-per-thread kernels ask the register
+// allocator for: the float-pair solve, whose FP32 work is a chain of dependent
+// operations, runs three (168 registers a thread) to hide its latency; the FP64
+// and FP32 solves, bound by the FP64 pipe, keep every register (measured at
+// 256^3, 13 species: float pairs 273 -> 258 ms of Newton per step, FP64 -1 %).
+template <typename MT>
+constexpr int newton_min_blocks() {
+    return std::is_same<MT, f2>::value ? 3 : 1;
+}
+
 // Load zone z into a solver state and evaluate it.  The start: with Rpred
 // (R^{m+1,(k)} of the sweep), the explicit predictor rhs + dt_m R^{m+1,(k)}
 // where it has a positive temperature and no mass fraction below -0.01,
@@ -34,9 +44,10 @@ __device__ __forceinline__ void load_zone(ZoneState<NS>& S, const NetParams& P, 
         for (int r = 0; r < NW; r++) S.w[r] = __dadd_rn(S.rw[r], __dmul_rn(dtm, Rpred[r * N + z]));
         const double ir = rcp_nr(rho);
         pred = positive_finite(P.gm1 * (S.w[0] - 0.5 * m2 * ir) * ir);
-        const double floor_x = -XMARGIN * rho;
+        // rho X_i >= -0.01 rho, compared on the integer pipe
+        const long long floor_x = ordered_bits(-XMARGIN * rho);
 #pragma unroll
-        for (int i = 0; i < NS; i++) pred = pred && !(S.w[1 + i] < floor_x);
+        for (int i = 0; i < NS; i++) pred = pred && (ordered_bits(S.w[1 + i]) >= floor_x);
     }
     if (!pred) {
         const double scale = rho / guess[z];
@@ -67,7 +78,7 @@ __device__ __forceinline__ void store_zone(const ZoneState<NS>& S, const NetPara
 
 // One zone per thread, a static grid over the zones.
 template <int NS, int TOPO, typename MT>
-__global__ void __launch_bounds__(NEWTON_BLOCK)
+__global__ void __launch_bounds__(NEWTON_BLOCK, newton_min_blocks<MT>())
 newton_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __restrict__ rhs,
               const double* guess, const double* __restrict__ Rpred, double* Uout, double* __restrict__ Rout,
               const double* __restrict__ dt_dev,
@@ -116,7 +127,7 @@ newton_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __
 // not hold the other lanes of their warp idle.  Each zone's arithmetic is the
 // same as in newton_kernel, so results agree bit for bit.
 template <int NS, int TOPO, typename MT>
-__global__ void __launch_bounds__(NEWTON_BLOCK)
+__global__ void __launch_bounds__(NEWTON_BLOCK, newton_min_blocks<MT>())
 newton_queue_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __restrict__ rhs,
                     const double* guess, const double* __restrict__ Rpred, double* Uout, double* __restrict__ Rout,
                     const double* __restrict__ dt_dev,
@@ -188,7 +199,7 @@ newton_queue_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const doub
 // warps that draw slow chunks do not hold up the rest of the grid.  Each
 // zone's arithmetic is that of newton_kernel: results agree bit for bit.
 template <int NS, int TOPO, typename MT>
-__global__ void __launch_bounds__(NEWTON_BLOCK)
+__global__ void __launch_bounds__(NEWTON_BLOCK, newton_min_blocks<MT>())
 newton_warpqueue_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __restrict__ rhs,
                         const double* guess, const double* __restrict__ Rpred, double* Uout,
                         double* __restrict__ Rout,
@@ -365,20 +376,19 @@ reaction_source_kernel(NetParams P, long long N, int dim, const double* __restri
     const double T = P.gm1 * (U[(1 + dim) * N + z] - 0.5 * m2 * inv_rho) * inv_rho;
     double k[NR], Y[NS], Rz[NW];
     if constexpr (TOPO == TOPO_CHAIN) {
-        // the chain's rates as products of the unknowns: kappa_j = (amp_j / rho) f_j(T)
-        double ak[NR], dfac;
-#pragma unroll
-        for (int j = 0; j < NR; j++) ak[j] = P.amp[j] * inv_rho;
-        rate_consts_k<NR>(P, ak, T, k, dfac);
+        // the chain's sources as products of the unknowns: kappa_j = amp_j f_j(T)
+        double dfac;
+        rate_consts_k<NR>(P, P.amp, T, k, dfac);
 #pragma unroll
         for (int i = 0; i < NS; i++) Y[i] = U[(2 + dim + i) * N + z];
+        sources_w<NS>(P, k, Y, Rz);
     } else {
         double dk[NR];
         rate_consts<NR>(P, rho, T, k, dk);
 #pragma unroll
         for (int i = 0; i < NS; i++) Y[i] = U[(2 + dim + i) * N + z] * (inv_rho * P.inv_mass[i]);
+        sources<NS, TOPO>(P, rho, k, Y, Rz);
     }
-    sources<NS, TOPO>(P, rho, k, Y, Rz);
 #pragma unroll
     for (int r = 0; r < NW; r++) R[r * N + z] = Rz[r];
 }
@@ -398,8 +408,28 @@ bool newton_group_case(int nspec, int topo) { return nspec == 13 && topo == TOPO
 // the 5- and 7-species chains also have the group kernel, as Newton variant 3
 bool newton_small_group_case(int nspec, int topo) { return topo == TOPO_CHAIN && (nspec == 5 || nspec == 7); }
 
+// the float-pair kernels' dynamic shared memory (above the default 48 KB for 13 species)
+template <int NS>
+cudaError_t pair_prepare() {
+    const int b = (int)pair_pivot_bytes<NS, f2>(NEWTON_BLOCK);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(newton_kernel<NS, TOPO_CHAIN, f2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  b)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(newton_queue_kernel<NS, TOPO_CHAIN, f2>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, b)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(newton_warpqueue_kernel<NS, TOPO_CHAIN, f2>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+}
+
 cudaError_t newton_prepare(int nspec, int topo) {
     cudaError_t e;
+    if (topo == TOPO_CHAIN) {
+        e = nspec == 5 ? pair_prepare<5>() : nspec == 7 ? pair_prepare<7>() : nspec == 13 ? pair_prepare<13>()
+                                                                                           : cudaSuccess;
+        if (e != cudaSuccess) return e;
+    }
     if (newton_small_group_case(nspec, topo)) {
         if (nspec == 5) {
             if ((e = cudaFuncSetAttribute(newton_group_kernel<5, double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -447,21 +477,84 @@ int newton_variants(int nspec, int topo) {
     return newton_small_group_case(nspec, topo) ? 4 : 3;
 }
 
+// Variants a matrix type runs: the float-pair matrix (prec 2) exists for the
+// alpha chain's one-zone-per-thread kernels only (not the lane groups).
+bool newton_variant_ok(int nspec, int topo, int prec, int variant) {
+    if (variant < 0 || variant >= newton_variants(nspec, topo)) return false;
+    if (prec != 2) return true;
+    if (topo != TOPO_CHAIN) return false;
+    if (newton_group_case(nspec, topo)) return variant >= 2;
+    return !(newton_small_group_case(nspec, topo) && variant == 3);
+}
+
+int newton_default_variant(int nspec, int topo, int prec) {
+    for (int v = 0; v < newton_variants(nspec, topo); v++)
+        if (newton_variant_ok(nspec, topo, prec, v)) return v;
+    return 0;
+}
+
+
+template <int NS, int TOPO>
+int queue_blocks_per_sm(int prec) {
+    int per = 0;
+    if (prec == 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, newton_queue_kernel<NS, TOPO, double>, NEWTON_BLOCK, 0);
+    else if (prec == 1)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, newton_queue_kernel<NS, TOPO, float>, NEWTON_BLOCK, 0);
+    else if constexpr (TOPO == TOPO_CHAIN)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, newton_queue_kernel<NS, TOPO, f2>, NEWTON_BLOCK,
+                                                      pair_pivot_bytes<NS, f2>(NEWTON_BLOCK));
+    return per;
+}
+
 int newton_persistent_blocks(const NetParams& P, int prec) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-#define X(ns, tp)                                                                                          \
-    if (P.nspec == ns && P.topo == tp) {                                                                   \
-        if (prec == 0)                                                                                     \
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, newton_queue_kernel<ns, tp, double>, NEWTON_BLOCK, 0); \
-        else                                                                                               \
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, newton_queue_kernel<ns, tp, float>, NEWTON_BLOCK, 0);  \
-    }
+#define X(ns, tp) \
+    if (P.nspec == ns && P.topo == tp) per = queue_blocks_per_sm<ns, tp>(prec);
     SDC_NEWTON_CASES(X)
 #undef X
     if (per < 1) per = 1;
     return sms * per;
+}
+
+// The one-zone-per-thread kernels with matrix type MT: static grid (kind 0),
+// persistent grid with a per-lane (1) or a per-warp (2) work queue.
+template <int NS, int TOPO, typename MT>
+cudaError_t launch_per_zone(int kind, unsigned grid, unsigned pgrid, const NetParams& P, const NewtonCfg& cfg,
+                            long long N, int dim, const double* rhs, const double* guess, const double* Rpred,
+                            double* Uout, double* Rout, const double* dt_dev, double dt_frac, double dtm_host,
+                            int* zone_status, int* zone_iters, DevStats* stats, unsigned long long* queue,
+                            cudaStream_t st) {
+    const size_t sm = pair_pivot_bytes<NS, MT>(NEWTON_BLOCK);
+    if (kind == 2)
+        newton_warpqueue_kernel<NS, TOPO, MT><<<pgrid, NEWTON_BLOCK, sm, st>>>(
+            P, cfg, N, dim, rhs, guess, Rpred, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, zone_iters, stats,
+            queue);
+    else if (kind == 1)
+        newton_queue_kernel<NS, TOPO, MT><<<pgrid, NEWTON_BLOCK, sm, st>>>(
+            P, cfg, N, dim, rhs, guess, Rpred, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, zone_iters, stats,
+            queue);
+    else
+        newton_kernel<NS, TOPO, MT><<<grid, NEWTON_BLOCK, sm, st>>>(P, cfg, N, dim, rhs, guess, Rpred, Uout, Rout,
+                                                                    dt_dev, dt_frac, dtm_host, zone_status,
+                                                                    zone_iters, stats);
+    return cudaGetLastError();
+}
+
+// The float-pair matrix exists for the alpha chain's bordered form only.
+template <int NS, int TOPO>
+cudaError_t launch_per_zone_pair(int kind, unsigned grid, unsigned pgrid, const NetParams& P, const NewtonCfg& cfg,
+                                 long long N, int dim, const double* rhs, const double* guess, const double* Rpred,
+                                 double* Uout, double* Rout, const double* dt_dev, double dt_frac, double dtm_host,
+                                 int* zone_status, int* zone_iters, DevStats* stats, unsigned long long* queue,
+                                 cudaStream_t st) {
+    if constexpr (TOPO == TOPO_CHAIN)
+        return launch_per_zone<NS, TOPO, f2>(kind, grid, pgrid, P, cfg, N, dim, rhs, guess, Rpred, Uout, Rout, dt_dev,
+                                             dt_frac, dtm_host, zone_status, zone_iters, stats, queue, st);
+    else
+        return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, long long N, int dim,
@@ -470,6 +563,7 @@ cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, lo
                           int* zone_iters, DevStats* stats, cudaStream_t st, int variant,
                           unsigned long long* queue, int persistent_blocks) {
     if (N <= 0) return cudaSuccess;
+    if (!newton_variant_ok(P.nspec, P.topo, prec, variant)) return cudaErrorInvalidValue;
     if (newton_group_case(P.nspec, P.topo) && variant < 2) {
         const unsigned ggrid = (unsigned)((N + GROUP_ZONES - 1) / GROUP_ZONES);
 #define SDC_GROUP_LAUNCH(MT, L)                                                                                    \
@@ -505,35 +599,19 @@ cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, lo
     const unsigned grid = (unsigned)((N + NEWTON_BLOCK - 1) / NEWTON_BLOCK);
     const bool q = (variant == 1 || variant == 2) && queue != nullptr && persistent_blocks > 0;
     const unsigned pgrid = q ? (unsigned)(persistent_blocks < (long long)grid ? persistent_blocks : grid) : 0u;
+    const int kind = !q ? 0 : (variant == 2 ? 2 : 1);
 #define X(ns, tp)                                                                                          \
     if (P.nspec == ns && P.topo == tp) {                                                                   \
-        if (q && variant == 2) {                                                                           \
-            if (prec == 0)                                                                                 \
-                newton_warpqueue_kernel<ns, tp, double><<<pgrid, NEWTON_BLOCK, 0, st>>>(                   \
-                    P, cfg, N, dim, rhs, guess, Rpred, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, \
-                    zone_iters, stats, queue);                                                             \
-            else                                                                                           \
-                newton_warpqueue_kernel<ns, tp, float><<<pgrid, NEWTON_BLOCK, 0, st>>>(                    \
-                    P, cfg, N, dim, rhs, guess, Rpred, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, \
-                    zone_iters, stats, queue);                                                             \
-        } else if (q) {                                                                                    \
-            if (prec == 0)                                                                                 \
-                newton_queue_kernel<ns, tp, double><<<pgrid, NEWTON_BLOCK, 0, st>>>(                       \
-                    P, cfg, N, dim, rhs, guess, Rpred, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, \
-                    zone_iters, stats, queue);                                                             \
-            else                                                                                           \
-                newton_queue_kernel<ns, tp, float><<<pgrid, NEWTON_BLOCK, 0, st>>>(                        \
-                    P, cfg, N, dim, rhs, guess, Rpred, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, \
-                    zone_iters, stats, queue);                                                             \
-        } else if (prec == 0)                                                                              \
-            newton_kernel<ns, tp, double><<<grid, NEWTON_BLOCK, 0, st>>>(P, cfg, N, dim, rhs, guess, Rpred, Uout, \
-                                                                         Rout, dt_dev, dt_frac, dtm_host,  \
-                                                                         zone_status, zone_iters, stats);  \
-        else                                                                                               \
-            newton_kernel<ns, tp, float><<<grid, NEWTON_BLOCK, 0, st>>>(P, cfg, N, dim, rhs, guess, Rpred, Uout, \
-                                                                        Rout, dt_dev, dt_frac, dtm_host,   \
-                                                                        zone_status, zone_iters, stats);   \
-        return cudaGetLastError();                                                                         \
+        if (prec == 0)                                                                                     \
+            return launch_per_zone<ns, tp, double>(kind, grid, pgrid, P, cfg, N, dim, rhs, guess, Rpred, Uout, \
+                                                   Rout, dt_dev, dt_frac, dtm_host, zone_status, zone_iters, \
+                                                   stats, queue, st);                                      \
+        if (prec == 1)                                                                                     \
+            return launch_per_zone<ns, tp, float>(kind, grid, pgrid, P, cfg, N, dim, rhs, guess, Rpred, Uout, \
+                                                  Rout, dt_dev, dt_frac, dtm_host, zone_status, zone_iters, \
+                                                  stats, queue, st);                                       \
+        return launch_per_zone_pair<ns, tp>(kind, grid, pgrid, P, cfg, N, dim, rhs, guess, Rpred, Uout, Rout, \
+                                            dt_dev, dt_frac, dtm_host, zone_status, zone_iters, stats, queue, st); \
     }
     SDC_NEWTON_CASES(X)
 #undef X

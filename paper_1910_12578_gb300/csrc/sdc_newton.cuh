@@ -13,13 +13,27 @@
 //   the residual grew by round-off at the root).
 // One thread owns one zone; the matrix lives in registers as MT (double: FP64
 // path; float: FP32 Jacobian / LU with FP64 residual and update, so that Newton
-// acts as iterative refinement): dense with a pivoted LU for a general network,
+// acts as iterative refinement; f2, the alpha chain only: the same with the
+// matrix in float pairs on the FP32 pipe, whose step is accurate to about 2^-44
+// relative, so the iteration keeps the FP64 path's count of steps): dense with a
+// pivoted LU for a general network,
 // in the bordered bidiagonal form of the alpha chain (build_chain, chain_solve)
 // for the chain.
 #pragma once
+#include <type_traits>
+
 #include "sdc_dev.cuh"
 
 namespace sdcd {
+
+// Dynamic shared memory of the one-zone-per-thread kernels: the float-pair
+// solve's pivot rows (pair_pivot_bytes per block; none for the other types).
+extern __shared__ double newton_smem[];
+
+template <int NS, typename MT>
+constexpr size_t pair_pivot_bytes(int block) {
+    return std::is_same<MT, f2>::value ? (size_t)5 * (NS - 1) * sizeof(f2) * (size_t)block : 0;
+}
 
 template <int NS, int TOPO>
 struct ZoneEval {
@@ -32,9 +46,10 @@ struct ZoneEval {
 // times rho^2, phi = (G_E rho/|rhs_E|)^2 + sum_i G_i^2 (the solve only compares
 // norms of one zone, so the common factor 1/rho^2 of the scaled norm
 // (G_E/|rhs_E|)^2 + sum_i (G_i/rho)^2 is left out).  For the alpha chain only
-// kappa_j = (amp_j / rho) f_j(T), whose products with the unknowns are the rates
-// (no Y_i), and the factor f of dkappa_j/dT = nu_j kappa_j f are formed (the
-// matrix takes nu_j from its coefficients); otherwise k_j, dk_j and Y_i.
+// kappa_j = amp_j f_j(T), whose products with the unknowns are the sources
+// (sources_w: no Y_i, no density), and the factor f of dkappa_j/dT =
+// nu_j kappa_j f are formed (the matrix takes nu_j from its coefficients);
+// otherwise k_j, dk_j and Y_i.
 // Returns false when T is not positive and finite.
 // The order of doubles as signed integers (negative patterns reversed), for
 // comparisons on the integer pipe; -0 sorts below +0 and a nan above +inf.
@@ -52,31 +67,34 @@ __device__ __forceinline__ bool positive_finite(double T) {
 
 template <int NS, int TOPO>
 __device__ __forceinline__ bool eval_state(const NetParams& P, double rho, double inv_rho, double ke,
-                                           const double* ym, const double* ak, const double* w, const double* rw,
-                                           double dtm, double wE, double* k, double* dk, double& dfac, double* Y,
-                                           double* G, double& phi) {
+                                           const double* ym, const double* w, const double* rw, double dtm,
+                                           double wE, double* k, double* dk, double& dfac, double* Y, double* G,
+                                           double& phi) {
     constexpr int N = NS + 1;
     constexpr int NR = NS - 1;
     const double T = P.gm1 * (w[0] - ke) * inv_rho;
     if (!positive_finite(T)) return false;
-    // G = w - dt_m R(w) - rw with R(rho E) = rho RE and R(rho X_i) = rho mass_i S_i,
-    // formed as (w - rw) - (dt_m rho) (mass_i S_i): one product fewer per row
-    double S[NS], RE;
+    // G = w - dt_m R(w) - rw, formed as (w - rw) - dt_m R
     if constexpr (TOPO == TOPO_CHAIN) {
-        // kappa_j = ak_j f_j(T) with the masses and density folded in: the rates
-        // are products of the unknowns themselves (no Y_i)
-        rate_consts_k<NR>(P, ak, T, k, dfac);
-        source_sums<NS, TOPO>(P, k, w + 1, S, RE);
+        // kappa_j = amp_j f_j(T) with the masses and density folded in: the
+        // sources are products of the unknowns themselves (no Y_i)
+        double R[N];
+        rate_consts_k<NR>(P, P.amp, T, k, dfac);
+        sources_w<NS>(P, k, w + 1, R);
+#pragma unroll
+        for (int r = 0; r < N; r++) G[r] = fma(-dtm, R[r], w[r] - rw[r]);
     } else {
+        // R(rho E) = rho RE, R(rho X_i) = rho mass_i S_i: (w - rw) - (dt_m rho) (mass_i S_i)
+        double S[NS], RE;
         rate_consts<NR>(P, rho, T, k, dk);
 #pragma unroll
         for (int i = 0; i < NS; i++) Y[i] = w[1 + i] * ym[i];
         source_sums<NS, TOPO>(P, k, Y, S, RE);
-    }
-    const double dr = dtm * rho;
-    G[0] = fma(-dr, RE, w[0] - rw[0]);
+        const double dr = dtm * rho;
+        G[0] = fma(-dr, RE, w[0] - rw[0]);
 #pragma unroll
-    for (int i = 0; i < NS; i++) G[1 + i] = fma(-dr, P.mass[i] * S[i], w[1 + i] - rw[1 + i]);
+        for (int i = 0; i < NS; i++) G[1 + i] = fma(-dr, P.mass[i] * S[i], w[1 + i] - rw[1 + i]);
+    }
     const double gE = G[0] * wE;
     double s = gE * gE;
 #pragma unroll
@@ -92,7 +110,6 @@ struct ZoneState {
     static constexpr int NR = NS - 1;
     double rho, inv_rho, ke, wE, phi, h, dfac;
     double ym[NS], lower[NS], rw[N], w[N], G[N], k[NR], dk[NR], Y[NS];  // ym, dk, Y: general networks
-    double ak[NR];  // amp_j / rho (alpha chain: k holds kappa_j = ak_j f_j(T))
     int iters, status;
     bool newton, have_k, done;
     bool r_final;   // G holds R at the solution (set by the stop test's last step)
@@ -106,11 +123,7 @@ __device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, 
     S.rho = rho;
     S.inv_rho = rcp_nr(rho);
     S.ke = 0.5 * m2 * S.inv_rho;
-    if constexpr (TOPO == TOPO_CHAIN) {
-        constexpr int NR = NS - 1;
-#pragma unroll
-        for (int j = 0; j < NR; j++) S.ak[j] = P.amp[j] * S.inv_rho;
-    } else {
+    if constexpr (TOPO != TOPO_CHAIN) {
 #pragma unroll
         for (int i = 0; i < NS; i++) S.ym[i] = S.inv_rho * P.inv_mass[i];
     }
@@ -123,24 +136,29 @@ __device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, 
             for (int r = 0; r < N; r++) S.w[r] = S.rw[r];
         }
     }
-    // the floor applies when the rhs is physical (every X_i >= -0.01)
+    // the floor applies when the rhs is physical (every X_i >= -0.01), and is
+    // min(0, X_i(rhs), X_i(start)) - 0.01; both are taken in units of rho X_i
+    // (rho > 0): rho X_i(rhs) >= -0.01 rho, and min(0, rw_i, w_i) - 0.01 rho,
+    // compared and selected on the integer pipe
+    const double mr = -XMARGIN * rho;
+    const long long omr = ordered_bits(mr);
     bool physical = true;
 #pragma unroll
-    for (int i = 0; i < NS; i++) physical = physical && (S.rw[1 + i] * S.inv_rho >= -XMARGIN);
+    for (int i = 0; i < NS; i++) physical = physical && (ordered_bits(S.rw[1 + i]) >= omr);
 #pragma unroll
     for (int i = 0; i < NS; i++) {
-        const double x = S.rw[1 + i] * S.inv_rho, xg = S.w[1 + i] * S.inv_rho;
-        double lo = x < 0.0 ? x : 0.0;
-        lo = xg < lo ? xg : lo;
-        S.lower[i] = physical ? (lo - XMARGIN) * rho : -INFINITY;  // as a bound on rho X_i
+        const double x = S.rw[1 + i], xg = S.w[1 + i];
+        double lo = ordered_bits(x) < 0 ? x : 0.0;
+        lo = ordered_bits(xg) < ordered_bits(lo) ? xg : lo;
+        S.lower[i] = physical ? lo + mr : -INFINITY;  // as a bound on rho X_i
     }
     S.iters = 0;
     S.status = ZONE_MAXIT;
     S.newton = true;
     S.r_final = false;
     S.h = PTC_H0;
-    S.have_k = eval_state<NS, TOPO>(P, rho, S.inv_rho, S.ke, S.ym, S.ak, S.w, S.rw, dtm, S.wE, S.k, S.dk, S.dfac, S.Y,
-                                    S.G, S.phi);
+    S.have_k = eval_state<NS, TOPO>(P, rho, S.inv_rho, S.ke, S.ym, S.w, S.rw, dtm, S.wE, S.k, S.dk, S.dfac, S.Y, S.G,
+                                    S.phi);
     S.done = !S.have_k;
     if (!S.have_k) S.status = ZONE_NONPHYSICAL;
 }
@@ -175,19 +193,30 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     constexpr int NR = NS - 1;
     S.iters++;
     const double c = S.newton ? 1.0 : 1.0 + rcp_nr(S.h);
-    MT dv[N];
-#pragma unroll
-    for (int r = 0; r < N; r++) dv[r] = to_mt<MT>(S.G[r]);
+    // the step as tested and applied (a float pair summed into a double once)
+    using ST = typename StepType<MT>::type;
+    ST ds[N];
     bool solved;
-    if constexpr (TOPO == TOPO_CHAIN) {
-        // the chain's sparsity: bordered bidiagonal system, O(n) elimination
-        ChainSys<NS, MT> A;
-        build_chain<NS, MT>(P, S.k, S.dfac, S.w + 1, c, dtm, dtm * S.rho, A);
-        solved = chain_solve<NS, MT>(A, dv);
+    if constexpr (TOPO == TOPO_CHAIN && std::is_same<MT, f2>::value) {
+        // float pairs: the matrix formed as the elimination reaches it
+        solved = chain_build_solve<NS, MT>(P, S.k, S.dfac * S.inv_rho, S.w + 1, c, dtm, S.G, ds,
+                                           reinterpret_cast<f2*>(newton_smem) + threadIdx.x, (int)blockDim.x);
     } else {
-        MT M[N][N];
-        build_matrix<NS, TOPO, MT>(P, S.rho, S.inv_rho, S.ym, S.k, S.dk, S.Y, c, dtm, M);
-        solved = lu_solve<N, MT, MT>(M, dv);
+        MT dv[N];
+#pragma unroll
+        for (int r = 0; r < N; r++) dv[r] = to_mt<MT>(S.G[r]);
+        if constexpr (TOPO == TOPO_CHAIN) {
+            // the chain's sparsity: bordered bidiagonal system, O(n) elimination
+            ChainSys<NS, MT> A;
+            build_chain<NS, MT>(P, S.k, S.dfac * S.inv_rho, S.w + 1, c, dtm, A);
+            solved = chain_solve<NS, MT>(A, dv);
+        } else {
+            MT M[N][N];
+            build_matrix<NS, TOPO, MT>(P, S.rho, S.inv_rho, S.ym, S.k, S.dk, S.Y, c, dtm, M);
+            solved = lu_solve<N, MT, MT>(M, dv);
+        }
+#pragma unroll
+        for (int r = 0; r < N; r++) ds[r] = step_value(dv[r]);
     }
     if (!solved) {
         S.status = ZONE_SINGULAR;
@@ -196,14 +225,14 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     }
     double tr[N];
 #pragma unroll
-    for (int r = 0; r < N; r++) tr[r] = S.w[r] - from_mt(dv[r]);
+    for (int r = 0; r < N; r++) tr[r] = S.w[r] - from_mt(ds[r]);
     // admissible: every rho X_i at or above its floor (the floor is -inf or a
     // nonzero value, so the two zeros never meet; a nan trial passes here and
     // fails the evaluation below, as it fails this test in plain compares)
     bool ok = true;
 #pragma unroll
     for (int i = 0; i < NS; i++) ok = ok && (ordered_bits(tr[1 + i]) >= ordered_bits(S.lower[i]));
-    if (S.newton && ok && newton_step_small<NS, MT>(S, cfg, dv, tr)) {
+    if (S.newton && ok && newton_step_small<NS, ST>(S, cfg, ds, tr)) {
         // The step meets the stop test, so an admissible trial (T positive and
         // finite, R finite) is the solution: only R at the trial is needed, not
         // the residual, its norm or the matrix's factor f.  Otherwise the full
@@ -224,9 +253,9 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
                     for (int j = 0; j < NR; j++) kf[j] = fma(S.k[j], P.nu[j] * delta, S.k[j]);
                 } else {
                     double dff;
-                    rate_consts_k<NR>(P, S.ak, T, kf, dff);
+                    rate_consts_k<NR>(P, P.amp, T, kf, dff);
                 }
-                sources<NS, TOPO>(P, S.rho, kf, tr + 1, Rf);
+                sources_w<NS>(P, kf, tr + 1, Rf);
             } else {
                 rate_consts<NR>(P, S.rho, T, kf, dkf);
 #pragma unroll
@@ -249,11 +278,10 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     double kt[NR], dkt[NR], Yt[NS], Gt[N];
     double phit = 0.0, dfact = 0.0;
     if (ok)
-        ok = eval_state<NS, TOPO>(P, S.rho, S.inv_rho, S.ke, S.ym, S.ak, tr, S.rw, dtm, S.wE, kt, dkt, dfact, Yt, Gt,
-                                  phit);
+        ok = eval_state<NS, TOPO>(P, S.rho, S.inv_rho, S.ke, S.ym, tr, S.rw, dtm, S.wE, kt, dkt, dfact, Yt, Gt, phit);
     // an admissible Newton step that meets the stop test converges even if the
     // residual grew by round-off at the root
-    const bool small = S.newton && ok && newton_step_small<NS, MT>(S, cfg, dv, tr);
+    const bool small = S.newton && ok && newton_step_small<NS, ST>(S, cfg, ds, tr);
     // phit and phi are finite and non-negative where compared: ordered as integers
     if (S.newton && !small && (!ok || ordered_bits(phit) > ordered_bits(S.phi))) {
         S.newton = false;
@@ -302,15 +330,15 @@ __device__ __forceinline__ void zone_source(const ZoneState<NS>& S, const NetPar
 #pragma unroll
         for (int r = 0; r < N; r++) Rout[r] = S.G[r];
     } else if (S.have_k) {
-        if constexpr (TOPO == TOPO_CHAIN) sources<NS, TOPO>(P, S.rho, S.k, S.w + 1, Rout);
+        if constexpr (TOPO == TOPO_CHAIN) sources_w<NS>(P, S.k, S.w + 1, Rout);
         else sources<NS, TOPO>(P, S.rho, S.k, S.Y, Rout);
     } else {
         const double T = P.gm1 * (S.w[0] - S.ke) * S.inv_rho;
         double kf[NR], dkf[NR], Yf[NS];
         if constexpr (TOPO == TOPO_CHAIN) {
             double dff;
-            rate_consts_k<NR>(P, S.ak, T, kf, dff);
-            sources<NS, TOPO>(P, S.rho, kf, S.w + 1, Rout);
+            rate_consts_k<NR>(P, P.amp, T, kf, dff);
+            sources_w<NS>(P, kf, S.w + 1, Rout);
         } else {
             rate_consts<NR>(P, S.rho, T, kf, dkf);
 #pragma unroll

@@ -1,7 +1,7 @@
 """Run SDC steps of a named workload for a profiler (ncu) or a quick timing.
 
     python -m paper_1910_12578_gb300.profile_step --config box64 --stencil-variant 1 --newton-variant 1 \\
-        --warmup 1 --steps 2 [--eager] [--prec fp32jac] [--space-order 4] [--limiter 0] [--nodes radau] \\
+        --warmup 1 --steps 2 [--eager] [--prec fp32jac|fp32x2jac] [--space-order 4] [--limiter 0] [--nodes radau] \\
         [--backward]
 
 Every step starts from the same seeded initial state.  With --eager the kernels
@@ -41,7 +41,7 @@ def main(argv=None):
     p.add_argument("--config", default="box64", choices=["box32", "box64", "box128", "box64_13", "box128_13", "box256",
                                                          "batch200"])
     p.add_argument("--seed", type=int, default=None)
-    p.add_argument("--prec", choices=["fp64", "fp32jac"], default="fp64")
+    p.add_argument("--prec", choices=["fp64", "fp32jac", "fp32x2jac"], default="fp64")
     p.add_argument("--stencil-variant", type=int, default=0)
     p.add_argument("--newton-variant", type=int, default=0)
     p.add_argument("--autotune", action="store_true")
@@ -63,7 +63,8 @@ def main(argv=None):
     for q in (P if isinstance(P, list) else [P]):
         q.space_order, q.nodes, q.limiter = a.space_order, a.nodes, a.limiter
     P0 = P[0] if isinstance(P, list) else P
-    ctx = sdc.Context(P, prec=sdc.PREC_FP64 if a.prec == "fp64" else sdc.PREC_FP32_JAC)
+    ctx = sdc.Context(P, prec={"fp64": sdc.PREC_FP64, "fp32jac": sdc.PREC_FP32_JAC,
+                               "fp32x2jac": sdc.PREC_FP32X2_JAC}[a.prec])
     U0 = torch.from_numpy(U).cuda()
     Ud = torch.empty_like(U0)
     dt = ctx.cfl_dt(U0, P0.cfl)

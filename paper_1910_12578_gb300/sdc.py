@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libsdc.so")
 SDC_OK, SDC_ERR_INVALID_ARG, SDC_ERR_CUDA, SDC_ERR_OOM, SDC_ERR_NEWTON_NOCONV, SDC_ERR_NONPHYSICAL, \
     SDC_ERR_TIMEOUT, SDC_ERR_TOO_LARGE = range(8)
 STATIC_SCRATCH_BYTES = 48 << 20
-PREC_FP64, PREC_FP32_JAC = 0, 1
+PREC_FP64, PREC_FP32_JAC, PREC_FP32X2_JAC = 0, 1, 2
 
 # entry points declared in include/sdc.h
 EXPORTS = ["sdc_init_box", "sdc_advective_term", "sdc_node_integral", "sdc_react_newton", "sdc_step",

@@ -86,12 +86,12 @@ def test_static_step_rejects_problems_beyond_its_scratch(torch_cuda):
     assert torch.equal(Ud, before)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_static_step_matches_allocating_step_on_ragged_boxes(torch_cuda, prec):
     """Several uneven boxes in one call (the tile-to-box map of the static
-    tables: prefix sums of tiles per box, partial tiles, box offsets), in FP64
-    and with the FP32 Jacobian, against sdc_init_box + sdc_step on the same
-    boxes, two calls in a row."""
+    tables: prefix sums of tiles per box, partial tiles, box offsets), in FP64,
+    with the FP32 Jacobian and with the float-pair Jacobian, against
+    sdc_init_box + sdc_step on the same boxes, two calls in a row."""
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
     net = W.alpha_chain(7, np.random.default_rng(3))
