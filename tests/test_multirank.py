@@ -46,3 +46,55 @@ def test_single_rank_needs_no_process_group():
     import bench
     v, t = bench.job_value(20.0, 100, 5, 1)
     assert t == 20.0 and v == pytest.approx(100 * 5 / 0.020)
+
+
+def _rank_step(rank, world, port, out):
+    """One SDC step per rank on that rank's own seeded box (the oracle stands in
+    for the GPU on CPU), no collective but the timing reduction."""
+    import time
+
+    import numpy as np
+
+    import bench
+    import oracle as O
+    from paper_1910_12578_gb300 import workloads as W
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    tdist.init_process_group("gloo", rank=rank, world_size=world)
+    seed = bench.rank_seed(1, rank)
+    P, U = W.config_box(n=8, nspec=7, seed=seed, T0=0.5)
+    o = O.Oracle(P)
+    dt = o.cfl_dt(U)
+    tdist.barrier()
+    t0 = time.perf_counter()
+    V, st = o.step(U, dt)
+    ms = (time.perf_counter() - t0) * 1e3
+    tdist.barrier()
+    v, t = bench.job_value(ms, bench.units_per_step(P), 1, world, bench.torch_reduce_max("cpu"))
+    out[rank] = (seed, float(np.abs(V).sum()), st.newton_solves, v, t, ms, bench.units_per_step(P))
+    tdist.destroy_process_group()
+
+
+def test_two_ranks_each_step_their_own_box():
+    """Each rank's step equals a single-process step of the same seed (nothing
+    couples the ranks' data), the boxes differ, and the job value counts both
+    ranks' units over the slower rank's time."""
+    import numpy as np
+
+    import oracle as O
+    from paper_1910_12578_gb300 import workloads as W
+    world = 2
+    port = _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_rank_step, args=(world, port, out), nprocs=world, join=True)
+    sums = []
+    for rank in range(world):
+        seed, s, solves, v, t, ms, units = out[rank]
+        P, U = W.config_box(n=8, nspec=7, seed=seed, T0=0.5)
+        o = O.Oracle(P)
+        V, _ = o.step(U, o.cfl_dt(U))
+        assert s == float(np.abs(V).sum())
+        assert solves == units
+        assert t == max(out[r][5] for r in range(world))
+        assert v == pytest.approx(units * world / (t * 1e-3))
+        sums.append(s)
+    assert sums[0] != sums[1]
