@@ -388,7 +388,9 @@ __device__ __forceinline__ void build_chain(const NetParams& P, const double* k,
     }
     A.dEE = A.dAA = cm;
     A.dEA = A.dAE = (MT)0;
-    const MT dt_ = to_mt<MT>(dtm), dg = to_mt<MT>(dtm * P.gm1 * dfac);
+    // t_E = t_A c0 with c0 = w_0 (gamma-1) f / rho: for j >= 1, dt_m kappa_j w_j w_0
+    // (gamma-1) f / rho; for j = 0, dt_m kappa_0 w_0^3 (gamma-1) f / rho
+    const MT dt_ = to_mt<MT>(dtm), c0 = to_mt<MT>(ws[0] * (P.gm1 * dfac));
     const MT y0 = to_mt<MT>(ws[0]);
 #pragma unroll
     for (int j = 0; j < NR; j++) {
@@ -397,16 +399,16 @@ __device__ __forceinline__ void build_chain(const NetParams& P, const double* k,
             const MT y02 = y0 * y0;
             const MT k0 = to_mt<MT>(k[0]);
             const MT t = dt_ * k0;
-            const MT tE = dg * k0 * (y02 * y0);
             const MT tA = t * y02;
+            const MT tE = tA * c0;
             A.dEE = msub(A.dEE, cf(0), tE);     A.dEA = msub(A.dEA, cf(1), tA);
             A.dAE = msub(A.dAE, cf(3), tE);     A.dAA = msub(A.dAA, cf(4), tA);
             A.uE[0] = msub(A.uE[0], cf(9), tE); A.uA[0] = msub(A.uA[0], cf(10), tA);
         } else {
             const MT yj = to_mt<MT>(ws[j]), kj = to_mt<MT>(k[j]);
             const MT t = dt_ * kj;
-            const MT tE = dg * kj * (yj * y0);
             const MT tA = t * yj, tJ = t * y0;
+            const MT tE = tA * c0;
             A.dEE = msub(A.dEE, cf(0), tE);   A.dEA = msub(A.dEA, cf(1), tA);   A.vE[j - 1] = msub(A.vE[j - 1], cf(2), tJ);
             A.dAE = msub(A.dAE, cf(3), tE);   A.dAA = msub(A.dAA, cf(4), tA);   A.vA[j - 1] = msub(A.vA[j - 1], cf(5), tJ);
             A.uE[j - 1] = msub(A.uE[j - 1], cf(6), tE);
@@ -512,7 +514,7 @@ __device__ __forceinline__ bool chain_build_solve(const NetParams& P, const doub
     constexpr int NC = NS - 1;
     constexpr int NR = NS - 1;
     const MT cm = to_mt<MT>(c);
-    const MT dt_ = to_mt<MT>(dtm), dg = to_mt<MT>(dtm * P.gm1 * dfac);
+    const MT dt_ = to_mt<MT>(dtm), c0 = to_mt<MT>(ws[0] * (P.gm1 * dfac));  // t_E = t_A c0 (build_chain)
     const MT y0 = to_mt<MT>(ws[0]);
     const MT zero = (MT)0;
     // border block and border right-hand side
@@ -529,8 +531,8 @@ __device__ __forceinline__ bool chain_build_solve(const NetParams& P, const doub
         if (j == 0) {
             const MT y02 = y0 * y0;
             const MT k0 = to_mt<MT>(k[0]);
-            const MT tE = dg * k0 * (y02 * y0);
             const MT tA = dt_ * k0 * y02;
+            const MT tE = tA * c0;
             dEE = msub(dEE, cf(0), tE); dEA = msub(dEA, cf(1), tA);
             dAE = msub(dAE, cf(3), tE); dAA = msub(dAA, cf(4), tA);
             uE_j = (MT)0 - cf(9) * tE; uA_j = (MT)0 - cf(10) * tA;
@@ -538,8 +540,8 @@ __device__ __forceinline__ bool chain_build_solve(const NetParams& P, const doub
         } else {
             const MT yj = to_mt<MT>(ws[j]), kj = to_mt<MT>(k[j]);
             const MT t = dt_ * kj;
-            const MT tE = dg * kj * (yj * y0);
             const MT tA = t * yj, tJ = t * y0;
+            const MT tE = tA * c0;
             dEE = msub(dEE, cf(0), tE); dEA = msub(dEA, cf(1), tA);
             dAE = msub(dAE, cf(3), tE); dAA = msub(dAA, cf(4), tA);
             vE_prev = (MT)0 - cf(2) * tJ; vA_prev = (MT)0 - cf(5) * tJ;

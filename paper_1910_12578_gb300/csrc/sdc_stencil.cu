@@ -28,7 +28,7 @@ template <int NS, int V> struct Tile<3, NS, V> {
 template <int DIM, int NS, int V>
 constexpr size_t smem_bytes() {
     using G = TileGeom<DIM, Tile<DIM, NS, V>::X, Tile<DIM, NS, V>::Y, Tile<DIM, NS, V>::Z>;
-    return sizeof(double) * (size_t)(2 + DIM + NS) * (G::NC + G::NB);
+    return sizeof(double) * ((size_t)(2 + DIM + NS) * (G::NC + G::NB) + G::NB);
 }
 
 // 3D: the tile shapes, then the direction-split passes (stencil_split_kernel)

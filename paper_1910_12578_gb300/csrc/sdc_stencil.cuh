@@ -72,13 +72,14 @@ struct TileGeom {
 };
 
 // CTAs per SM the launch bounds ask for: two where two tiles' shared memory
-// (primitives and the slope / flux buffer) fit in an SM's 228 KB, so that one
+// (primitives, the slope / flux buffer and the per-face species flux factor)
+// fit in an SM's 228 KB, so that one
 // CTA's barrier phases overlap the other's arithmetic; the registers per
 // thread are then capped at 64K / (2 THREADS).
 template <int DIM, int NS, int TX, int TY, int TZ>
 constexpr int stencil_min_blocks() {
     using G = TileGeom<DIM, TX, TY, TZ>;
-    return sizeof(double) * (size_t)(2 + DIM + NS) * (G::NC + G::NB) <= 112 * 1024 ? 2 : 1;
+    return sizeof(double) * ((size_t)(2 + DIM + NS) * (G::NC + G::NB) + G::NB) <= 112 * 1024 ? 2 : 1;
 }
 
 // shared-memory slot of tile-local zone (x, y, z); at most one coordinate
@@ -176,6 +177,7 @@ stencil_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __restric
     extern __shared__ double smem[];
     double* sq = smem;                 // [NV][NC] primitives
     double* sb = smem + NV * G::NC;    // [NV][NB] half slopes, then face fluxes
+    double* sm = sb + NV * G::NB;      // [NB] per face: mass flux / sum of X, times 1/dx
 
     const TileDev t = tiles[blockIdx.x];
     const BoxDev b = boxes[t.box];
@@ -269,6 +271,7 @@ stencil_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __restric
         const int nfaces = T0 * T1 * (dir == 2 ? TZ + 1 : TZ);
         const int S0 = dir == 0 ? TX + 2 : TX, S1 = dir == 1 ? TY + 2 : TY;
         double F[NV];
+        double fmi = 0.0;
         int fi_mine = -1;
         {
             const int fi = threadIdx.x;  // THREADS >= faces of every direction
@@ -308,9 +311,12 @@ stencil_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __restric
                         X[s] = q + bitsd(dbits(h) ^ flip);
                         sum += X[s];
                     }
-                    const double fm = F[0] * rcp_nr(sum);
+                    // species flux F_s = fm X_s, fm = F_rho / sum X: the face keeps X_s and
+                    // fm / dx, and each zone adds fm_lo X_lo / dx - fm_hi X_hi / dx by two
+                    // fused multiply-adds
+                    fmi = F[0] * rcp_nr(sum) * b.idx[dir];
 #pragma unroll
-                    for (int s = 0; s < NS; s++) F[NH + s] = fm * X[s];
+                    for (int s = 0; s < NS; s++) F[NH + s] = X[s];
                 }
             }
         }
@@ -318,6 +324,7 @@ stencil_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __restric
         if (fi_mine >= 0) {
 #pragma unroll
             for (int f = 0; f < NV; f++) sb[f * G::NB + fi_mine] = F[f];
+            sm[fi_mine] = fmi;
         }
         __syncthreads();
         if (own) {
@@ -327,7 +334,13 @@ stencil_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __restric
             const int hi = c[0] + T0 * (c[1] + T1 * c[2]);
             const double idx = b.idx[dir];
 #pragma unroll
-            for (int f = 0; f < NV; f++) A[f] = fma(-(sb[f * G::NB + hi] - sb[f * G::NB + lo]), idx, A[f]);
+            for (int f = 0; f < NH; f++) A[f] = fma(-(sb[f * G::NB + hi] - sb[f * G::NB + lo]), idx, A[f]);
+            const double ml = sm[lo], mh = sm[hi];
+#pragma unroll
+            for (int s = 0; s < NS; s++) {
+                A[NH + s] = fma(ml, sb[(NH + s) * G::NB + lo], A[NH + s]);
+                A[NH + s] = fma(-mh, sb[(NH + s) * G::NB + hi], A[NH + s]);
+            }
         }
         (void)T;
         __syncthreads();

@@ -24,7 +24,9 @@
 //      inside the box);
 //   2. one-sided differences of neighbouring zones, L + 3 per line;
 //   3. half slopes from the two differences of a zone, L + 2 per line;
-//   4. face fluxes, L + 1 per line;
+//   4. face fluxes, L + 1 per line (for the species the upwind X_s and the
+//      factor F_rho / (sum X) / dx_D, so that phase 5 takes each species'
+//      flux difference in two fused multiply-adds);
 //   5. A += -(F_{i+1/2} - F_{i-1/2}) / dx_D for the L zones of every line.
 #pragma once
 #include "sdc_stencil.cuh"
@@ -197,6 +199,7 @@ stencil_split_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __r
     // ---- 4. face fluxes: face m (m = 0..L) between zone positions m-1 and m
     {
         double F[NV];
+        double fmi = 0.0;
         int li = 0, m = 0;
         if (tid < G::NF) G::item(tid, L + 1, li, m);
         const bool act = tid < G::NF && t.o[G::A] + li < nA;
@@ -222,15 +225,17 @@ stencil_split_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __r
                 X[s] = q + bitsd(dbits(hh) ^ flip);
                 sum += X[s];
             }
-            const double fm = F[0] * rcp_nr(sum);
+            // the face keeps X_s and fm / dx (fm = F_rho / sum X), as stencil_kernel
+            fmi = F[0] * rcp_nr(sum) * b.idx[D];
 #pragma unroll
-            for (int s = 0; s < NS; s++) F[NHY + s] = fm * X[s];
+            for (int s = 0; s < NS; s++) F[NHY + s] = X[s];
         }
         __syncthreads();  // every primitive and slope is read: the first buffer takes the fluxes
         if (act) {
             const int sf = G::slot(li, m, L + 1);
 #pragma unroll
             for (int f = 0; f < NV; f++) sq[f * G::NQ + sf] = F[f];
+            sb[sf] = fmi;
         }
     }
     __syncthreads();
@@ -244,9 +249,18 @@ stencil_split_kernel(NetParams P, int limiter, long long Ntot, const BoxDev* __r
     const double idx = b.idx[D];
     double A[NV];
 #pragma unroll
-    for (int f = 0; f < NV; f++) {
+    for (int f = 0; f < NHY; f++) {
         const double prev = FIRST ? 0.0 : Aout[f * Ntot + gi];
         A[f] = fma(-(sq[f * G::NQ + fhi] - sq[f * G::NQ + flo]), idx, prev);
+        Aout[f * Ntot + gi] = A[f];
+    }
+    // species: fm_lo X_lo / dx - fm_hi X_hi / dx, as stencil_kernel
+    const double ml = sb[flo], mh = sb[fhi];
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        const int f = NHY + s;
+        const double prev = FIRST ? 0.0 : Aout[f * Ntot + gi];
+        A[f] = fma(-mh, sq[f * G::NQ + fhi], fma(ml, sq[f * G::NQ + flo], prev));
         Aout[f * Ntot + gi] = A[f];
     }
     if (LAST && MODE == STENCIL_A_RHS) {
