@@ -38,23 +38,30 @@ __device__ __forceinline__ void load_zone(ZoneState<NS>& S, const NetParams& P, 
     }
 #pragma unroll
     for (int r = 0; r < NW; r++) S.rw[r] = rhs[(1 + dim + r) * N + z];
+    // 1/rho, the kinetic energy and the floor -0.01 rho, formed once for the start
+    // test and the solve
+    const double ir = rcp_nr(rho);
+    const double ke = 0.5 * m2 * ir;
+    const double mr = -XMARGIN * rho;
     bool pred = false;
+    double Tw = 0.0;
     if (Rpred) {
 #pragma unroll
         for (int r = 0; r < NW; r++) S.w[r] = __dadd_rn(S.rw[r], __dmul_rn(dtm, Rpred[r * N + z]));
-        const double ir = rcp_nr(rho);
-        pred = positive_finite(P.gm1 * (S.w[0] - 0.5 * m2 * ir) * ir);
+        Tw = P.gm1 * (S.w[0] - ke) * ir;
+        pred = positive_finite(Tw);
         // rho X_i >= -0.01 rho, compared on the integer pipe
-        const long long floor_x = ordered_bits(-XMARGIN * rho);
+        const long long floor_x = ordered_bits(mr);
 #pragma unroll
         for (int i = 0; i < NS; i++) pred = pred && (ordered_bits(S.w[1 + i]) >= floor_x);
     }
     if (!pred) {
+        Tw = 0.0;
         const double scale = rho / guess[z];
 #pragma unroll
         for (int r = 0; r < NW; r++) S.w[r] = guess[(1 + dim + r) * N + z] * scale;
     }
-    zone_init<NS, TOPO>(S, P, rho, m2, dtm);
+    zone_init<NS, TOPO>(S, P, rho, ir, ke, mr, Tw, dtm);
 }
 
 // Store the solution and R of a finished zone.

@@ -65,15 +65,28 @@ __device__ __forceinline__ bool positive_finite(double T) {
     return b > 0 && (b >> 52) < 0x7ff;
 }
 
-template <int NS, int TOPO>
-__device__ __forceinline__ bool eval_state(const NetParams& P, double rho, double inv_rho, double ke,
-                                           const double* ym, const double* w, const double* rw, double dtm,
-                                           double wE, double* k, double* dk, double& dfac, double* Y, double* G,
-                                           double& phi) {
+// The scaled norm phi of a residual G (see eval_state).
+template <int N>
+__device__ __forceinline__ double residual_norm(const double* G, double wE) {
+    const double gE = G[0] * wE;
+    double s = gE * gE;
+#pragma unroll
+    for (int r = 1; r < N; r++) s = fma(G[r], G[r], s);
+    return s;
+}
+
+// eval_at_T: the same at a state whose temperature T is known to be positive
+// and finite (formed by the caller as P.gm1 * (w[0] - ke) * inv_rho).  With
+// PHI false the norm is left for later (have_phi false) where the exponents of
+// G and wE alone show it finite: every |G_r| and |G_0 wE| below 2^500 bounds
+// it by 2^1004 (integer pipe); otherwise it is formed as with PHI.
+template <int NS, int TOPO, bool PHI = true>
+__device__ __forceinline__ bool eval_at_T(const NetParams& P, double rho, double T, const double* ym,
+                                          const double* w, const double* rw, double dtm, double wE, double* k,
+                                          double* dk, double& dfac, double* Y, double* G, double& phi,
+                                          bool* have_phi = nullptr) {
     constexpr int N = NS + 1;
     constexpr int NR = NS - 1;
-    const double T = P.gm1 * (w[0] - ke) * inv_rho;
-    if (!positive_finite(T)) return false;
     // G = w - dt_m R(w) - rw, formed as (w - rw) - dt_m R
     if constexpr (TOPO == TOPO_CHAIN) {
         // kappa_j = amp_j f_j(T) with the masses and density folded in: the
@@ -95,12 +108,32 @@ __device__ __forceinline__ bool eval_state(const NetParams& P, double rho, doubl
 #pragma unroll
         for (int i = 0; i < NS; i++) G[1 + i] = fma(-dr, P.mass[i] * S[i], w[1 + i] - rw[1 + i]);
     }
-    const double gE = G[0] * wE;
-    double s = gE * gE;
+    if constexpr (!PHI) {
+        // biased exponents: |x| < 2^(e - 1022); finite G_r with e <= 1522 are below
+        // 2^500, and G_0 wE is when e(G_0) + e(wE) <= 2544
+        auto bexp = [](double x) { return (int)((dbits(x) >> 52) & 0x7ff); };
+        bool small = bexp(G[0]) + bexp(wE) <= 2544;
 #pragma unroll
-    for (int r = 1; r < N; r++) s = fma(G[r], G[r], s);
+        for (int r = 0; r < N; r++) small = small && bexp(G[r]) <= 1522;
+        if (small) {
+            *have_phi = false;
+            return true;
+        }
+        *have_phi = true;
+    }
+    const double s = residual_norm<N>(G, wE);
     phi = s;
     return (dbits(s) >> 52) < 0x7ff;  // s >= 0: finite (nan and inf have the full exponent)
+}
+
+template <int NS, int TOPO>
+__device__ __forceinline__ bool eval_state(const NetParams& P, double rho, double inv_rho, double ke,
+                                           const double* ym, const double* w, const double* rw, double dtm,
+                                           double wE, double* k, double* dk, double& dfac, double* Y, double* G,
+                                           double& phi) {
+    const double T = P.gm1 * (w[0] - ke) * inv_rho;
+    if (!positive_finite(T)) return false;
+    return eval_at_T<NS, TOPO>(P, rho, T, ym, w, rw, dtm, wE, k, dk, dfac, Y, G, phi);
 }
 
 // Register-resident state of one zone's solve.
@@ -112,35 +145,40 @@ struct ZoneState {
     double ym[NS], lower[NS], rw[N], w[N], G[N], k[NR], dk[NR], Y[NS];  // ym, dk, Y: general networks
     int iters, status;
     bool newton, have_k, done;
+    bool have_phi;  // phi holds the norm of G (at the start it is formed only when a decision needs it)
     bool r_final;   // G holds R at the solution (set by the stop test's last step)
 };
 
 // Set up a zone: rw = reactive part of the rhs, w = the (density-rescaled)
-// guess, m2 = |rho u|^2 of the rhs.  Evaluates the residual at the start.
+// guess; inv_rho = 1/rho, ke = |rho u|^2 / (2 rho) of the rhs, mr = -0.01 rho,
+// Tw = the temperature of w when the caller has formed it and found it
+// positive and finite, else 0.  Evaluates the residual at the start.
 template <int NS, int TOPO>
-__device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, double rho, double m2, double dtm) {
+__device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, double rho, double inv_rho,
+                                          double ke, double mr, double Tw, double dtm) {
     constexpr int N = NS + 1;
     S.rho = rho;
-    S.inv_rho = rcp_nr(rho);
-    S.ke = 0.5 * m2 * S.inv_rho;
+    S.inv_rho = inv_rho;
+    S.ke = ke;
     if constexpr (TOPO != TOPO_CHAIN) {
 #pragma unroll
         for (int i = 0; i < NS; i++) S.ym[i] = S.inv_rho * P.inv_mass[i];
     }
     S.wE = rho * rcp_nr(fabs(S.rw[0]));  // rho / |rhs_E|
     // a start without a positive temperature is replaced by rhs
-    {
-        const double Tg = P.gm1 * (S.w[0] - S.ke) * S.inv_rho;
-        if (!positive_finite(Tg)) {
+    double T = Tw;
+    if (!positive_finite(T)) {
+        T = P.gm1 * (S.w[0] - S.ke) * S.inv_rho;
+        if (!positive_finite(T)) {
 #pragma unroll
             for (int r = 0; r < N; r++) S.w[r] = S.rw[r];
+            T = P.gm1 * (S.w[0] - S.ke) * S.inv_rho;
         }
     }
     // the floor applies when the rhs is physical (every X_i >= -0.01), and is
     // min(0, X_i(rhs), X_i(start)) - 0.01; both are taken in units of rho X_i
     // (rho > 0): rho X_i(rhs) >= -0.01 rho, and min(0, rw_i, w_i) - 0.01 rho,
     // compared and selected on the integer pipe
-    const double mr = -XMARGIN * rho;
     const long long omr = ordered_bits(mr);
     bool physical = true;
 #pragma unroll
@@ -157,8 +195,8 @@ __device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, 
     S.newton = true;
     S.r_final = false;
     S.h = PTC_H0;
-    S.have_k = eval_state<NS, TOPO>(P, rho, S.inv_rho, S.ke, S.ym, S.w, S.rw, dtm, S.wE, S.k, S.dk, S.dfac, S.Y, S.G,
-                                    S.phi);
+    S.have_k = positive_finite(T) && eval_at_T<NS, TOPO, false>(P, rho, T, S.ym, S.w, S.rw, dtm, S.wE, S.k, S.dk,
+                                                                S.dfac, S.Y, S.G, S.phi, &S.have_phi);
     S.done = !S.have_k;
     if (!S.have_k) S.status = ZONE_NONPHYSICAL;
 }
@@ -237,27 +275,41 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
         // finite, R finite) is the solution: only R at the trial is needed, not
         // the residual, its norm or the matrix's factor f.  Otherwise the full
         // evaluation below takes the decision.
-        const double T = P.gm1 * (tr[0] - S.ke) * S.inv_rho;
-        if (positive_finite(T)) {
-            double kf[NR], dkf[NR], Yf[NS], Rf[N];
-            if constexpr (TOPO == TOPO_CHAIN) {
-                // delta = (T - T_w) / T_w from the energy step (tr_0 - w_0 is exact:
-                // the two lie within a factor of two; dfac = 1 / T_w for the power
-                // law).  Where |delta| <= 2^-32, kappa_j(T) = kappa_j(T_w) (1 + nu_j
-                // delta) to within the rounding of kappa: the next term of
-                // (1 + delta)^nu_j, nu_j (nu_j - 1) delta^2 / 2, is below 2^-55 for
-                // nu_j <= 45 (P.rate_taylor).  Else the rate factors are evaluated.
-                const double delta = P.gm1 * (tr[0] - S.w[0]) * S.inv_rho * S.dfac;
-                if (P.rate_taylor && mag2(delta) <= mag2(0x1p-32)) {
+        double kf[NR], dkf[NR], Yf[NS], Rf[N];
+        bool have_rates = false;
+        if constexpr (TOPO == TOPO_CHAIN) {
+            // delta = (T - T_w) / T_w from the energy step (tr_0 - w_0 is exact:
+            // the two lie within a factor of two; dfac = 1 / T_w for the power
+            // law).  Where |delta| <= 2^-32, kappa_j(T) = kappa_j(T_w) (1 + nu_j
+            // delta) to within the rounding of kappa: the next term of
+            // (1 + delta)^nu_j, nu_j (nu_j - 1) delta^2 / 2, is below 2^-55 for
+            // nu_j <= 45 (P.rate_taylor).  There T is positive and finite: T_w is,
+            // and T_w <= 2^1021 (dfac >= 2^-1021, its exponent field >= 2), so T
+            // within 2^-31 of it stays below the overflow threshold.
+            const double delta = P.gm1 * (tr[0] - S.w[0]) * S.inv_rho * S.dfac;
+            if (P.rate_taylor && mag2(delta) <= mag2(0x1p-32) && (dbits(S.dfac) >> 52) >= 2) {
 #pragma unroll
-                    for (int j = 0; j < NR; j++) kf[j] = fma(S.k[j], P.nu[j] * delta, S.k[j]);
-                } else {
+                for (int j = 0; j < NR; j++) kf[j] = fma(S.k[j], P.nu[j] * delta, S.k[j]);
+                have_rates = true;
+            }
+        }
+        if (!have_rates) {
+            // else the rate factors are evaluated at a positive, finite T
+            const double T = P.gm1 * (tr[0] - S.ke) * S.inv_rho;
+            if (positive_finite(T)) {
+                if constexpr (TOPO == TOPO_CHAIN) {
                     double dff;
                     rate_consts_k<NR>(P, P.amp, T, kf, dff);
+                } else {
+                    rate_consts<NR>(P, S.rho, T, kf, dkf);
                 }
+                have_rates = true;
+            }
+        }
+        if (have_rates) {
+            if constexpr (TOPO == TOPO_CHAIN) {
                 sources_w<NS>(P, kf, tr + 1, Rf);
             } else {
-                rate_consts<NR>(P, S.rho, T, kf, dkf);
 #pragma unroll
                 for (int i = 0; i < NS; i++) Yf[i] = tr[1 + i] * S.ym[i];
                 sources<NS, TOPO>(P, S.rho, kf, Yf, Rf);
@@ -282,6 +334,10 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     // an admissible Newton step that meets the stop test converges even if the
     // residual grew by round-off at the root
     const bool small = S.newton && ok && newton_step_small<NS, ST>(S, cfg, ds, tr);
+    if (!S.have_phi) {
+        S.phi = residual_norm<N>(S.G, S.wE);
+        S.have_phi = true;
+    }
     // phit and phi are finite and non-negative where compared: ordered as integers
     if (S.newton && !small && (!ok || ordered_bits(phit) > ordered_bits(S.phi))) {
         S.newton = false;
