@@ -504,9 +504,14 @@ __device__ __forceinline__ bool chain_solve(const ChainSys<NS, MT>& A, MT* b) {
 // order they come (a different rounding order from build_chain + chain_solve,
 // the same pivots and the same algebra).  The right-hand side G (FP64, w order)
 // is converted as it is used; the step d is returned in StepType<MT>.
-// The pivot rows wait for the back substitution in shared memory: field f of
-// column kk at piv[(f NC + kk) stride] (stride = threads of the block), which
-// keeps the solve's live registers to the rows in hand.
+// Each column's record in shared memory (field f of column kk at
+// piv[(f NC + kk) stride], stride = threads of the block) first holds that
+// column's inputs as pairs (kappa_kk, w_kk, the chain rhs G[2 + kk]) and, once
+// the elimination has read them, the pivot row (1/p, entry at kk+1, border
+// columns, rhs) for the back substitution.  The elimination loop over the
+// columns is not unrolled, so that its code, ten FP32 instructions per pair
+// operation, stays in the instruction cache; its per-column inputs come from
+// the records and the network constants from the kernel's parameter space.
 template <int NS, typename MT>
 __device__ __forceinline__ bool chain_build_solve(const NetParams& P, const double* k, double dfac, const double* ws,
                                                   double c, double dtm, const double* G,
@@ -517,6 +522,14 @@ __device__ __forceinline__ bool chain_build_solve(const NetParams& P, const doub
     const MT dt_ = to_mt<MT>(dtm), c0 = to_mt<MT>(ws[0] * (P.gm1 * dfac));  // t_E = t_A c0 (build_chain)
     const MT y0 = to_mt<MT>(ws[0]);
     const MT zero = (MT)0;
+    auto rec = [&](int f, int kk) -> MT& { return piv[(f * NC + kk) * stride]; };
+    // the inputs of every column
+#pragma unroll
+    for (int kk = 0; kk < NC; kk++) {
+        rec(0, kk) = to_mt<MT>(k[kk]);
+        rec(1, kk) = to_mt<MT>(ws[kk]);
+        rec(2, kk) = to_mt<MT>(G[2 + kk]);
+    }
     // border block and border right-hand side
     MT dEE = cm, dEA = zero, dAE = zero, dAA = cm;
     MT gE = to_mt<MT>(G[0]), gA = to_mt<MT>(G[1]);
@@ -524,94 +537,78 @@ __device__ __forceinline__ bool chain_build_solve(const NetParams& P, const doub
     MT rbd = cm, ruE, ruA, rbs = zero;       // row r: diagonal, border columns, sub-diagonal
     MT sbs = zero, suE = zero, suA = zero;   // row r+1: the part reaction r+1 gave
     MT vEr = zero, vAr = zero;               // border rows at column r (reaction r+1)
-    // reaction j's terms on the rows and columns it touches
-    auto react = [&](int j, MT& uE_prev, MT& uA_prev, MT& bd_prev, MT& vE_prev, MT& vA_prev, MT& uE_j, MT& uA_j,
-                     MT& bs_j) {
+    // reaction j >= 1's terms on the rows and columns it touches
+    auto react = [&](int j, MT kj, MT yj, MT& uE_prev, MT& uA_prev, MT& bd_prev, MT& vE_prev, MT& vA_prev, MT& uE_j,
+                     MT& uA_j, MT& bs_j) {
         auto cf = [&](int e) { return chain_coef<MT>(P, j, e); };
-        if (j == 0) {
-            const MT y02 = y0 * y0;
-            const MT k0 = to_mt<MT>(k[0]);
-            const MT tA = dt_ * k0 * y02;
-            const MT tE = tA * c0;
-            dEE = msub(dEE, cf(0), tE); dEA = msub(dEA, cf(1), tA);
-            dAE = msub(dAE, cf(3), tE); dAA = msub(dAA, cf(4), tA);
-            uE_j = (MT)0 - cf(9) * tE; uA_j = (MT)0 - cf(10) * tA;
-            bs_j = zero;
-        } else {
-            const MT yj = to_mt<MT>(ws[j]), kj = to_mt<MT>(k[j]);
-            const MT t = dt_ * kj;
-            const MT tA = t * yj, tJ = t * y0;
-            const MT tE = tA * c0;
-            dEE = msub(dEE, cf(0), tE); dEA = msub(dEA, cf(1), tA);
-            dAE = msub(dAE, cf(3), tE); dAA = msub(dAA, cf(4), tA);
-            vE_prev = (MT)0 - cf(2) * tJ; vA_prev = (MT)0 - cf(5) * tJ;
-            uE_prev = msub(uE_prev, cf(6), tE);
-            uA_prev = msub(uA_prev, cf(7), tA);
-            bd_prev = msub(bd_prev, cf(8), tJ);
-            uE_j = (MT)0 - cf(9) * tE; uA_j = (MT)0 - cf(10) * tA;
-            bs_j = (MT)0 - cf(11) * tJ;
-        }
+        const MT t = dt_ * kj;
+        const MT tA = t * yj, tJ = t * y0;
+        const MT tE = tA * c0;
+        dEE = msub(dEE, cf(0), tE); dEA = msub(dEA, cf(1), tA);
+        dAE = msub(dAE, cf(3), tE); dAA = msub(dAA, cf(4), tA);
+        vE_prev = (MT)0 - cf(2) * tJ; vA_prev = (MT)0 - cf(5) * tJ;
+        uE_prev = msub(uE_prev, cf(6), tE);
+        uA_prev = msub(uA_prev, cf(7), tA);
+        bd_prev = msub(bd_prev, cf(8), tJ);
+        uE_j = (MT)0 - cf(9) * tE; uA_j = (MT)0 - cf(10) * tA;
+        bs_j = (MT)0 - cf(11) * tJ;
     };
     {   // reactions 0 and 1: chain row 0 complete, border at column 0, row 1 begun
-        MT du0, du1, du2, du3, du4;
-        react(0, du0, du1, du2, du3, du4, ruE, ruA, rbs);
-        if (NR > 1) react(1, ruE, ruA, rbd, vEr, vAr, suE, suA, sbs);
+        auto cf = [&](int e) { return chain_coef<MT>(P, 0, e); };
+        const MT y02 = y0 * y0;
+        const MT k0 = rec(0, 0);
+        const MT tA = dt_ * k0 * y02;
+        const MT tE = tA * c0;
+        dEE = msub(dEE, cf(0), tE); dEA = msub(dEA, cf(1), tA);
+        dAE = msub(dAE, cf(3), tE); dAA = msub(dAA, cf(4), tA);
+        ruE = (MT)0 - cf(9) * tE; ruA = (MT)0 - cf(10) * tA;
+        rbs = zero;
+        if (NR > 1) react(1, rec(0, 1), rec(1, 1), ruE, ruA, rbd, vEr, vAr, suE, suA, sbs);
     }
-    // pivot rows: 1/p, entry at k+1, border columns, rhs
-    auto pip = [&](int kk) -> MT& { return piv[(0 * NC + kk) * stride]; };
-    auto pe = [&](int kk) -> MT& { return piv[(1 * NC + kk) * stride]; };
-    auto puE = [&](int kk) -> MT& { return piv[(2 * NC + kk) * stride]; };
-    auto puA = [&](int kk) -> MT& { return piv[(3 * NC + kk) * stride]; };
-    auto pg = [&](int kk) -> MT& { return piv[(4 * NC + kk) * stride]; };
-    MT cp = rbd, cuE = ruE, cuA = ruA, cg = to_mt<MT>(G[2]);  // the carried row
+    MT cp = rbd, cuE = ruE, cuA = ruA, cg = rec(2, 0);  // the carried row
     MT wE = vEr, wA = vAr;  // border rows at the current column
-    // row k+1 (being completed) and the border entries at column k+1
-    MT nbd = cm, nuE = suE, nuA = suA, nbs = sbs, nvE = zero, nvA = zero;
+    // row kk+1 (being completed) and the border entries at column kk+1
+    MT nbd = cm, nuE = suE, nuA = suA, nbs = sbs;
     bool ok = true;
-#pragma unroll
-    for (int kk = 0; kk < NC; kk++) {
-        MT p, e, quE, quA, qg;
-        if (kk + 1 < NC) {
-            // reaction kk+2 completes row kk+1 and gives the border entries at column kk+1
-            MT tbd = cm, tuE = zero, tuA = zero, tbs = zero;
-            if (kk + 2 < NR) {
-                react(kk + 2, nuE, nuA, nbd, nvE, nvA, tuE, tuA, tbs);
-            }
-            const MT ns_ = nbs, nd = nbd, nu1 = nuE, nu2 = nuA, ng = to_mt<MT>(G[3 + kk]);
-            const bool sw = mag2(ns_) > mag2(cp);
-            p = sw ? ns_ : cp;
-            e = sw ? nd : zero;
-            quE = sw ? nu1 : cuE;
-            quA = sw ? nu2 : cuA;
-            qg = sw ? ng : cg;
-            const MT op = sw ? cp : ns_, od = sw ? zero : nd;
-            const MT ouE = sw ? cuE : nu1, ouA = sw ? cuA : nu2, og = sw ? cg : ng;
-            ok = ok && (p != zero);
-            const MT ip = inv_mt(p);
-            pip(kk) = ip;
-            const MT l = op * ip;
-            cp = msub(od, l, e);
-            cuE = msub(ouE, l, quE);
-            cuA = msub(ouA, l, quA);
-            cg = msub(og, l, qg);
-            pe(kk) = e; puE(kk) = quE; puA(kk) = quA; pg(kk) = qg;
-            const MT lE = wE * ip, lA = wA * ip;
-            dEE = msub(dEE, lE, quE); dEA = msub(dEA, lE, quA); gE = msub(gE, lE, qg);
-            dAE = msub(dAE, lA, quE); dAA = msub(dAA, lA, quA); gA = msub(gA, lA, qg);
-            wE = msub(nvE, lE, e);
-            wA = msub(nvA, lA, e);
-            // row kk+2 becomes the next row
-            nbd = tbd; nuE = tuE; nuA = tuA; nbs = tbs; nvE = zero; nvA = zero;
-        } else {
-            p = cp; e = zero; quE = cuE; quA = cuA; qg = cg;
-            ok = ok && (p != zero);
-            const MT ip = inv_mt(p);
-            pip(kk) = ip;
-            pe(kk) = e; puE(kk) = quE; puA(kk) = quA; pg(kk) = qg;
-            const MT lE = wE * ip, lA = wA * ip;
-            dEE = msub(dEE, lE, quE); dEA = msub(dEA, lE, quA); gE = msub(gE, lE, qg);
-            dAE = msub(dAE, lA, quE); dAA = msub(dAA, lA, quA); gA = msub(gA, lA, qg);
-        }
+#pragma unroll 1
+    for (int kk = 0; kk + 1 < NC; kk++) {
+        // reaction kk+2 completes row kk+1 and gives the border entries at column kk+1
+        MT tbd = cm, tuE = zero, tuA = zero, tbs = zero, nvE = zero, nvA = zero;
+        if (kk + 2 < NR) react(kk + 2, rec(0, kk + 2), rec(1, kk + 2), nuE, nuA, nbd, nvE, nvA, tuE, tuA, tbs);
+        const MT ns_ = nbs, nd = nbd, nu1 = nuE, nu2 = nuA, ng = rec(2, kk + 1);
+        const bool sw = mag2(ns_) > mag2(cp);
+        const MT p = sw ? ns_ : cp;
+        const MT e = sw ? nd : zero;
+        const MT quE = sw ? nu1 : cuE;
+        const MT quA = sw ? nu2 : cuA;
+        const MT qg = sw ? ng : cg;
+        const MT op = sw ? cp : ns_, od = sw ? zero : nd;
+        const MT ouE = sw ? cuE : nu1, ouA = sw ? cuA : nu2, og = sw ? cg : ng;
+        ok = ok && (p != zero);
+        const MT ip = inv_mt(p);
+        const MT l = op * ip;
+        cp = msub(od, l, e);
+        cuE = msub(ouE, l, quE);
+        cuA = msub(ouA, l, quA);
+        cg = msub(og, l, qg);
+        rec(0, kk) = ip; rec(1, kk) = e; rec(2, kk) = quE; rec(3, kk) = quA; rec(4, kk) = qg;
+        const MT lE = wE * ip, lA = wA * ip;
+        dEE = msub(dEE, lE, quE); dEA = msub(dEA, lE, quA); gE = msub(gE, lE, qg);
+        dAE = msub(dAE, lA, quE); dAA = msub(dAA, lA, quA); gA = msub(gA, lA, qg);
+        wE = msub(nvE, lE, e);
+        wA = msub(nvA, lA, e);
+        // row kk+2 becomes the next row
+        nbd = tbd; nuE = tuE; nuA = tuA; nbs = tbs;
+    }
+    {   // the last chain column: no row below it
+        constexpr int kk = NC - 1;
+        const MT p = cp;
+        ok = ok && (p != zero);
+        const MT ip = inv_mt(p);
+        rec(0, kk) = ip; rec(1, kk) = zero; rec(2, kk) = cuE; rec(3, kk) = cuA; rec(4, kk) = cg;
+        const MT lE = wE * ip, lA = wA * ip;
+        dEE = msub(dEE, lE, cuE); dEA = msub(dEA, lE, cuA); gE = msub(gE, lE, cg);
+        dAE = msub(dAE, lA, cuE); dAA = msub(dAA, lA, cuA); gA = msub(gA, lA, cg);
     }
     // 2 x 2 border block, partial pivoting
     const bool sw = mag2(dAE) > mag2(dEE);
@@ -629,7 +626,7 @@ __device__ __forceinline__ bool chain_build_solve(const NetParams& P, const doub
     MT xn = zero;
 #pragma unroll
     for (int kk = NC - 1; kk >= 0; kk--) {
-        const MT x = msub(msub(msub(pg(kk), pe(kk), xn), puE(kk), xE), puA(kk), xA) * pip(kk);
+        const MT x = msub(msub(msub(rec(4, kk), rec(1, kk), xn), rec(2, kk), xE), rec(3, kk), xA) * rec(0, kk);
         d[2 + kk] = step_value(x);
         xn = x;
     }

@@ -86,7 +86,7 @@ __device__ __forceinline__ void store_zone(const ZoneState<NS>& S, const NetPara
 // One zone per thread, a static grid over the zones.
 template <int NS, int TOPO, typename MT>
 __global__ void __launch_bounds__(NEWTON_BLOCK, newton_min_blocks<MT>())
-newton_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __restrict__ rhs,
+newton_kernel(const __grid_constant__ NetParams P, NewtonCfg cfg, long long N, int dim, const double* __restrict__ rhs,
               const double* guess, const double* __restrict__ Rpred, double* Uout, double* __restrict__ Rout,
               const double* __restrict__ dt_dev,
               double dt_frac, double dtm_host, int* __restrict__ zone_status, int* __restrict__ zone_iters,
@@ -135,7 +135,7 @@ newton_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __
 // same as in newton_kernel, so results agree bit for bit.
 template <int NS, int TOPO, typename MT>
 __global__ void __launch_bounds__(NEWTON_BLOCK, newton_min_blocks<MT>())
-newton_queue_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __restrict__ rhs,
+newton_queue_kernel(const __grid_constant__ NetParams P, NewtonCfg cfg, long long N, int dim, const double* __restrict__ rhs,
                     const double* guess, const double* __restrict__ Rpred, double* Uout, double* __restrict__ Rout,
                     const double* __restrict__ dt_dev,
                     double dt_frac, double dtm_host, int* __restrict__ zone_status, int* __restrict__ zone_iters,
@@ -207,7 +207,7 @@ newton_queue_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const doub
 // zone's arithmetic is that of newton_kernel: results agree bit for bit.
 template <int NS, int TOPO, typename MT>
 __global__ void __launch_bounds__(NEWTON_BLOCK, newton_min_blocks<MT>())
-newton_warpqueue_kernel(NetParams P, NewtonCfg cfg, long long N, int dim, const double* __restrict__ rhs,
+newton_warpqueue_kernel(const __grid_constant__ NetParams P, NewtonCfg cfg, long long N, int dim, const double* __restrict__ rhs,
                         const double* guess, const double* __restrict__ Rpred, double* Uout,
                         double* __restrict__ Rout,
                         const double* __restrict__ dt_dev, double dt_frac, double dtm_host,
