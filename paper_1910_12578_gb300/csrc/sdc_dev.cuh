@@ -623,12 +623,20 @@ __device__ __forceinline__ bool chain_build_solve(const NetParams& P, const doub
     const MT xE = msub(r1, bb, xA) * ia;
     d[0] = step_value(xE);
     d[1] = step_value(xA);
+    // back substitution, also not unrolled: each column's step (a double) goes to
+    // its record's first field as raw bits, then to d
     MT xn = zero;
-#pragma unroll
+#pragma unroll 1
     for (int kk = NC - 1; kk >= 0; kk--) {
         const MT x = msub(msub(msub(rec(4, kk), rec(1, kk), xn), rec(2, kk), xE), rec(3, kk), xA) * rec(0, kk);
-        d[2 + kk] = step_value(x);
+        const long long b = dbits(step_value(x));
+        rec(0, kk) = MT(__int_as_float((int)b), __int_as_float((int)(b >> 32)));
         xn = x;
+    }
+#pragma unroll
+    for (int kk = 0; kk < NC; kk++) {
+        const MT v = rec(0, kk);
+        d[2 + kk] = bitsd(((long long)__float_as_int(v.lo) << 32) | (long long)(unsigned)__float_as_int(v.hi));
     }
     return ok;
 }

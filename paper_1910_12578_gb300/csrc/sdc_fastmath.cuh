@@ -180,9 +180,27 @@ template <typename MT> __device__ __forceinline__ MT to_mt(double x);
 template <> __device__ __forceinline__ double to_mt<double>(double x) { return x; }
 template <> __device__ __forceinline__ float to_mt<float>(double x) { return narrow(x); }
 // a double as a float pair: hi its leading 24 bits (truncated), lo the leading
-// 24 of the rest (x - hi is exact in FP64: the two share their exponent)
+// 24 of the rest (x - hi is exact in FP64: the two share their exponent).  For
+// x in float's normal range the rest is the 29 mantissa bits below hi's, so lo
+// is formed from them on the integer pipe: their leading one gives lo's
+// exponent, the next 23 bits (truncated) its mantissa, x its sign; a rest of
+// zero gives +0, as x - hi does.  Elsewhere (and where lo would not be a normal
+// float) the FP64 difference and narrow.
 template <> __device__ __forceinline__ f2 to_mt<f2>(double x) {
     const float h = narrow(x);
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int ef = (int)((hi >> 20) & 0x7ffu);
+    const int e = ef - 896;  // exponent field of x as a float
+    const unsigned r = lo & 0x1fffffffu;
+    if (e > 0 && e < 255) {
+        if (r == 0u) return f2(h, 0.0f);
+        const int p = 31 - __clz((int)r);   // leading one of the rest, 0..28
+        const int fe = ef - 948 + p;        // lo's exponent field: r 2^(ef - 1075) = 1.f 2^(ef - 1075 + p)
+        if (fe > 0) {
+            const unsigned m = (p <= 23 ? (r << (23 - p)) : (r >> (p - 23))) & 0x7fffffu;
+            return f2(h, __uint_as_float((hi & 0x80000000u) | ((unsigned)fe << 23) | m));
+        }
+    }
     return f2(h, narrow(x - widen(h)));
 }
 __device__ __forceinline__ double from_mt(double x) { return x; }
