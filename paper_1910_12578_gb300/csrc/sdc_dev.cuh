@@ -451,7 +451,7 @@ __device__ __forceinline__ bool chain_solve(const ChainSys<NS, MT>& A, MT* b) {
             qg = sw ? ng : cg;
             const MT op = sw ? cp : ns_, od = sw ? (MT)0 : nd;
             const MT ouE = sw ? cuE : nuE, ouA = sw ? cuA : nuA, og = sw ? cg : ng;
-            ok = ok && (p != (MT)0);
+            ok = ok && nonzero(p);
             const MT ip = inv_mt(p);
             pip[k] = ip;
             const MT l = op * ip;
@@ -461,7 +461,7 @@ __device__ __forceinline__ bool chain_solve(const ChainSys<NS, MT>& A, MT* b) {
             cg = msub(og, l, qg);
         } else {
             p = cp; e = (MT)0; quE = cuE; quA = cuA; qg = cg;
-            ok = ok && (p != (MT)0);
+            ok = ok && nonzero(p);
             pip[k] = inv_mt(p);
         }
         pe[k] = e; puE[k] = quE; puA[k] = quA; pg[k] = qg;
@@ -477,11 +477,11 @@ __device__ __forceinline__ bool chain_solve(const ChainSys<NS, MT>& A, MT* b) {
     const bool sw = mag2(dAE) > mag2(dEE);
     const MT a = sw ? dAE : dEE, bb = sw ? dAA : dEA, c2 = sw ? dEE : dAE, d2 = sw ? dEA : dAA;
     const MT r1 = sw ? gA : gE, r2 = sw ? gE : gA;
-    ok = ok && (a != (MT)0);
+    ok = ok && nonzero(a);
     const MT ia = inv_mt(a);
     const MT l = c2 * ia;
     const MT s22 = msub(d2, l, bb);
-    ok = ok && (s22 != (MT)0);
+    ok = ok && nonzero(s22);
     const MT xA = msub(r2, l, r1) * inv_mt(s22);
     const MT xE = msub(r1, bb, xA) * ia;
     b[0] = xE;
@@ -584,7 +584,7 @@ __device__ __forceinline__ bool chain_build_solve(const NetParams& P, const doub
         const MT qg = sw ? ng : cg;
         const MT op = sw ? cp : ns_, od = sw ? zero : nd;
         const MT ouE = sw ? cuE : nu1, ouA = sw ? cuA : nu2, og = sw ? cg : ng;
-        ok = ok && (p != zero);
+        ok = ok && nonzero(p);
         const MT ip = inv_mt(p);
         const MT l = op * ip;
         cp = msub(od, l, e);
@@ -603,7 +603,7 @@ __device__ __forceinline__ bool chain_build_solve(const NetParams& P, const doub
     {   // the last chain column: no row below it
         constexpr int kk = NC - 1;
         const MT p = cp;
-        ok = ok && (p != zero);
+        ok = ok && nonzero(p);
         const MT ip = inv_mt(p);
         rec(0, kk) = ip; rec(1, kk) = zero; rec(2, kk) = cuE; rec(3, kk) = cuA; rec(4, kk) = cg;
         const MT lE = wE * ip, lA = wA * ip;
@@ -614,11 +614,11 @@ __device__ __forceinline__ bool chain_build_solve(const NetParams& P, const doub
     const bool sw = mag2(dAE) > mag2(dEE);
     const MT a = sw ? dAE : dEE, bb = sw ? dAA : dEA, c2 = sw ? dEE : dAE, d2 = sw ? dEA : dAA;
     const MT r1 = sw ? gA : gE, r2 = sw ? gE : gA;
-    ok = ok && (a != zero);
+    ok = ok && nonzero(a);
     const MT ia = inv_mt(a);
     const MT l = c2 * ia;
     const MT s22 = msub(d2, l, bb);
-    ok = ok && (s22 != zero);
+    ok = ok && nonzero(s22);
     const MT xA = msub(r2, l, r1) * inv_mt(s22);
     const MT xE = msub(r1, bb, xA) * ia;
     d[0] = step_value(xE);

@@ -172,6 +172,12 @@ __device__ __forceinline__ f2 inv_mt(f2 x) {
 __device__ __forceinline__ double inv_mt(double x) { return rcp_nr(x); }
 __device__ __forceinline__ float inv_mt(float x) { return 1.0f / x; }
 
+// x != 0 (a nan counts as nonzero, as in IEEE compares): for a double on the
+// bit pattern (integer pipe), for float and float pairs on the FP32 pipe
+__device__ __forceinline__ bool nonzero(double x) { return ((unsigned long long)dbits(x) << 1) != 0ull; }
+__device__ __forceinline__ bool nonzero(float x) { return x != 0.0f; }
+__device__ __forceinline__ bool nonzero(f2 x) { return x.hi != 0.0f || x.lo != 0.0f; }
+
 // |x| ordered on the integer pipe: the leading float decides
 __device__ __forceinline__ unsigned int mag2(f2 x) { return (unsigned int)__float_as_int(x.hi) << 1; }
 
