@@ -44,21 +44,19 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per zone of one Newton launch, from one ncu
-# capture per kernel variant and precision, keyed by (nspec, Newton variant, prec).  The 13-species captures
-# ran on a 128^3 box of the 256^3 workload's network (2.1M zones: every array of the launch exceeds L2, so its
-# writes reach DRAM and the traffic grows in proportion to the zones; algorithmic 512 B per zone: the rhs and
-# R^{m+1,(k)} read, the new state and R written), mean over the 8 launches of a step, so a launch
-# over N zones moves N times this.  The 7-species capture ran on the 64^3 box itself (its writes still sit in
-# the 129 MB L2 when the launch ends).  A variant or precision without a capture reports null.
+# capture per kernel variant and precision, keyed by (nspec, Newton variant, prec).  The captures ran on a 128^3
+# box of the 256^3 workload's network (2.1M zones: every array of the launch exceeds L2, so its writes reach
+# DRAM and the traffic grows in proportion to the zones; algorithmic 512 B per zone: the rhs and R^{m+1,(k)}
+# read, the new state and R written), mean over the 8 launches of a step, so a launch over N zones moves N times
+# this.  A variant or precision without a capture of the current kernels reports null.
 NEWTON_TRAFFIC_PER_ZONE = {
-    (13, 2, "fp64"): (538.1e6 + 510.9e6) / 2097152,       # newton_kernel<13, chain, double>, static grid
-    (13, 2, "fp32jac"): (554.1e6 + 523.1e6) / 2097152,    # newton_kernel<13, chain, float>
-    (13, 2, "fp32x2jac"): (556.8e6 + 1280.1e6) / 2097152,  # newton_kernel<13, chain, f2>: its spills reach DRAM
-    (7, 0, "fp64"): (42.1e6 + 2.3e6) / 262144,            # newton_kernel<7, chain, double> on the 64^3 box
+    (13, 2, "fp64"): (538.1e6 + 510.6e6) / 2097152,       # newton_kernel<13, chain, double>, static grid
+    (13, 2, "fp32jac"): (554.6e6 + 520.8e6) / 2097152,    # newton_kernel<13, chain, float>
+    (13, 2, "fp32x2jac"): (542.9e6 + 751.1e6) / 2097152,  # newton_kernel<13, chain, f2>: its spills reach DRAM
 }
 # The same for one advective term of the direction-split passes (x, y, z; A only), 128^3 box, 13 species.
 PREC_NAMES = {0: "fp64", 1: "fp32jac", 2: "fp32x2jac"}   # sdc_precision values
-STENCIL_TRAFFIC_PER_ZONE = {13: (302.8e6 + 547.8e6 + 604.2e6 + 257.7e6 + 646.8e6 + 261.5e6) / 2097152}
+STENCIL_TRAFFIC_PER_ZONE = {13: (302.3e6 + 546.5e6 + 604.3e6 + 259.6e6 + 654.7e6 + 261.8e6) / 2097152}
 
 
 def parse():
