@@ -261,9 +261,12 @@ sdc_status sdc_launches_per_step(const sdc_ctx* ctx, int* launches);
    advective term through its face fluxes with the limiter and HLLC branches of
    the recomputed step fixed.  All pointers are device arrays: U_n, gU_np1, gU_n
    [nvar][Ntot]; g_a [nreac], accumulated (NULL: not formed).  The first call
-   allocates an adjoint workspace in the context.  Supported: the networks of
-   the thread-per-zone kernels (not the 13-species chain): SDC_ERR_INVALID_ARG
-   otherwise.  Deterministic (no floating-point atomics). */
+   allocates an adjoint workspace in the context (for 3 nodes and K
+   iterations about (13 + 2K) nvar + 7 (nspec+1) + 12 nvar + nreac doubles per
+   zone).  Supported: the A -> B network in 1D and 3D and the 5-, 7- and
+   13-species alpha chains in 3D (the chains' transposed solve by the bordered
+   chain elimination, in reversed chain order), second-order operators:
+   SDC_ERR_INVALID_ARG otherwise.  Deterministic (no floating-point atomics). */
 sdc_status sdc_step_backward(sdc_ctx* ctx, const double* U_n, double dt, const double* gU_np1, double* gU_n,
                              double* g_a);
 

@@ -169,6 +169,84 @@ __device__ __forceinline__ void reaction_derivs(const NetParams& P, double rho, 
     }
 }
 
+// ---- the alpha chain: the same VJP without dense matrices
+// With q_j = rho r_j = kappa_j P_j (kappa_j = amp_j f_j(T), P_0 = w_0^3,
+// P_j = w_0 w_j) the sources are R = sum_j sigma_j q_j, sigma_j reaction j's
+// column (Q_j in the energy row, mass_i s_ij in species row i), so for any v
+//   (dR/dw)^T v = sum_j (sigma_j . v) dq_j/dw,   (dR/da_j)^T v = (sigma_j . v) q_j / a_j,
+// where dq_j/dw has at most three nonzero entries (rho E through T, X_0, X_j).
+// The transposed solve (I - dt_m dR/dw)^T lambda = b uses the bordered chain
+// elimination of the forward Newton step: M^T in reversed chain order
+// (X_{n-1} .. X_1) is again lower bidiagonal in the chain, bordered by the
+// energy and alpha rows and columns.
+template <int NS>
+struct ChainDerivs {
+    static constexpr int NR = NS - 1;
+    double q[NR];    // q_j = kappa_j P_j
+    double dE[NR];   // dq_j / d(rho E) = q_j nu_j f (gamma-1) / rho
+    double d0[NR];   // dq_j / dw_0
+    double dj[NR];   // dq_j / dw_j (j >= 1)
+    double fa[NR];   // q_j / a_j = f_j(T) P_j / prod of the reactant masses
+};
+
+// sigma_j . v (v in w order: rho E, rho X_0, ..)
+template <int NS>
+__device__ __forceinline__ double chain_sigma_dot(const NetParams& P, int j, const double* v) {
+    double s = fma(P.Q[j], v[0], P.rs[j][0] * v[1]);
+    if (j >= 1) s = fma(P.rs[j][1], v[1 + j], s);
+    return fma(P.rs[j][2], v[2 + j], s);
+}
+
+// out = (dR/dw)^T v, and sv[j] = sigma_j . v
+template <int NS>
+__device__ __forceinline__ void chain_dRT(const NetParams& P, const ChainDerivs<NS>& D, const double* v, double* out,
+                                          double* sv) {
+    constexpr int N = NS + 1;
+    constexpr int NR = NS - 1;
+#pragma unroll
+    for (int r = 0; r < N; r++) out[r] = 0.0;
+#pragma unroll
+    for (int j = 0; j < NR; j++) {
+        const double sj = chain_sigma_dot<NS>(P, j, v);
+        sv[j] = sj;
+        out[0] = fma(sj, D.dE[j], out[0]);
+        out[1] = fma(sj, D.d0[j], out[1]);
+        if (j >= 1) out[1 + j] = fma(sj, D.dj[j], out[1 + j]);
+    }
+}
+
+// Solve (I - dtm dR/dw)^T lambda = b in place (b, lambda in w order).
+template <int NS>
+__device__ __forceinline__ bool chain_solve_transposed(const NetParams& P, const double* kap, double dfac_rho,
+                                                       const double* ws, double dtm, double* b) {
+    constexpr int NC = NS - 1;
+    ChainSys<NS, double> A, At;
+    build_chain<NS, double>(P, kap, dfac_rho, ws, 1.0, dtm, A);
+    // M^T with the chain reversed: chain position k of At is species X_{NC-k}
+#pragma unroll
+    for (int k = 0; k < NC; k++) {
+        const int o = NC - 1 - k;
+        At.bd[k] = A.bd[o];
+        At.bs[k] = k >= 1 ? A.bs[o + 1] : 0.0;  // M^T[X_{o+1}][X_{o+2}] = M[X_{o+2}][X_{o+1}]
+        At.uE[k] = A.vE[o];
+        At.uA[k] = A.vA[o];
+        At.vE[k] = A.uE[o];
+        At.vA[k] = A.uA[o];
+    }
+    At.dEE = A.dEE; At.dEA = A.dAE; At.dAE = A.dEA; At.dAA = A.dAA;
+    double x[NS + 1];
+    x[0] = b[0];
+    x[1] = b[1];
+#pragma unroll
+    for (int k = 0; k < NC; k++) x[2 + k] = b[2 + NC - 1 - k];
+    const bool ok = chain_solve<NS, double>(At, x);
+    b[0] = x[0];
+    b[1] = x[1];
+#pragma unroll
+    for (int k = 0; k < NC; k++) b[2 + NC - 1 - k] = x[2 + k];
+    return ok;
+}
+
 // Reactive-source VJP at the state U (with Rbar) and, when dtm > 0, the VJP of
 // the implicit update whose root is U: rhsbar = d rhs.  abar_zone[j*N + z] +=.
 template <int NS, int TOPO>
@@ -263,6 +341,102 @@ reaction_vjp_kernel(NetParams P, long long N, int dim, const double* __restrict_
     for (int j = 0; j < NR; j++) abar_zone[j * N + z] += ga[j];
 }
 
+// reaction_vjp_kernel for the alpha chain (any length, 13 species included),
+// from the per-reaction derivatives of ChainDerivs: O(n) work and registers
+// per zone instead of the dense n x n Jacobian and n x (n-1) rate derivatives.
+template <int NS>
+__global__ void __launch_bounds__(ADJ_BLOCK)
+reaction_vjp_chain_kernel(NetParams P, long long N, int dim, const double* __restrict__ U,
+                          const double* __restrict__ Rbar, double* __restrict__ Ubar, double dtm,
+                          double* __restrict__ rhsbar, double* __restrict__ abar_zone) {
+    constexpr int NW = NS + 1;
+    constexpr int NR = NS - 1;
+    const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= N) return;
+    const double rho = U[z];
+    double mom[3] = {0.0, 0.0, 0.0}, m2 = 0.0;
+    for (int d = 0; d < dim; d++) {
+        mom[d] = U[(1 + d) * N + z];
+        m2 += mom[d] * mom[d];
+    }
+    double w[NW];
+#pragma unroll
+    for (int r = 0; r < NW; r++) w[r] = U[(1 + dim + r) * N + z];
+    const double irho = rcp_nr(rho);
+    const double T = P.gm1 * (w[0] - 0.5 * m2 * irho) * irho;
+    // kappa_j = amp_j f_j(T) and f_j(T) alone (unit prefactors), dfac = d ln f_j / dT / nu_j
+    double kap[NR], f[NR], dfac;
+    {
+        double one[NR];
+#pragma unroll
+        for (int j = 0; j < NR; j++) one[j] = 1.0;
+        rate_consts_k<NR>(P, one, T, f, dfac);
+#pragma unroll
+        for (int j = 0; j < NR; j++) kap[j] = P.amp[j] * f[j];
+    }
+    ChainDerivs<NS> D;
+    const double gE = P.gm1 * dfac * irho;  // dT/d(rho E) times dfac
+#pragma unroll
+    for (int j = 0; j < NR; j++) {
+        const double w0 = w[1], wj = w[1 + j];
+        const double Pj = j == 0 ? w0 * w0 * w0 : w0 * wj;
+        D.q[j] = kap[j] * Pj;
+        D.dE[j] = D.q[j] * P.nu[j] * gE;
+        D.d0[j] = j == 0 ? 3.0 * kap[0] * (w0 * w0) : kap[j] * wj;
+        D.dj[j] = j == 0 ? 0.0 : kap[j] * w0;
+        // the reactant masses' product: 1 / prod mass = amp_j / a_j (a_j may be 0)
+        const double mp = j == 0 ? P.mass[0] * P.mass[0] * P.mass[0] : P.mass[j] * P.mass[0];
+        D.fa[j] = f[j] * Pj * rcp_nr(mp);
+    }
+    const double cE_rho = -w[0] * irho + m2 * (irho * irho);  // dT/d(rho) / dT/d(rho E)
+    double ub_rho = Ubar[z], ub_m[3] = {0.0, 0.0, 0.0}, ub_w[NW];
+    for (int d = 0; d < dim; d++) ub_m[d] = Ubar[(1 + d) * N + z];
+#pragma unroll
+    for (int r = 0; r < NW; r++) ub_w[r] = Ubar[(1 + dim + r) * N + z];
+    double ga[NR];
+#pragma unroll
+    for (int j = 0; j < NR; j++) ga[j] = 0.0;
+    if (Rbar) {
+        double rb[NW], t[NW], sv[NR];
+#pragma unroll
+        for (int r = 0; r < NW; r++) rb[r] = Rbar[r * N + z];
+        chain_dRT<NS>(P, D, rb, t, sv);
+#pragma unroll
+        for (int c = 0; c < NW; c++) ub_w[c] += t[c];
+        const double DE = t[0];
+        ub_rho += DE * cE_rho;
+        for (int d = 0; d < dim; d++) ub_m[d] -= DE * mom[d] * irho;
+#pragma unroll
+        for (int j = 0; j < NR; j++) ga[j] += sv[j] * D.fa[j];
+    }
+    if (dtm > 0.0) {
+        double lam[NW];
+#pragma unroll
+        for (int r = 0; r < NW; r++) lam[r] = ub_w[r];
+        if (!chain_solve_transposed<NS>(P, kap, dfac * irho, w + 1, dtm, lam)) {
+            // singular Jacobian at the root: the update is not differentiable here
+#pragma unroll
+            for (int r = 0; r < NW; r++) lam[r] = 0.0;
+        }
+        double t[NW], sv[NR];
+        chain_dRT<NS>(P, D, lam, t, sv);
+        const double DE = t[0];
+        rhsbar[z] = ub_rho + dtm * DE * cE_rho;
+        for (int d = 0; d < dim; d++) rhsbar[(1 + d) * N + z] = ub_m[d] - dtm * DE * mom[d] * irho;
+#pragma unroll
+        for (int r = 0; r < NW; r++) rhsbar[(1 + dim + r) * N + z] = lam[r];
+#pragma unroll
+        for (int j = 0; j < NR; j++) ga[j] += dtm * (sv[j] * D.fa[j]);
+    } else {
+        Ubar[z] = ub_rho;
+        for (int d = 0; d < dim; d++) Ubar[(1 + d) * N + z] = ub_m[d];
+#pragma unroll
+        for (int r = 0; r < NW; r++) Ubar[(1 + dim + r) * N + z] = ub_w[r];
+    }
+#pragma unroll
+    for (int j = 0; j < NR; j++) abar_zone[j * N + z] += ga[j];
+}
+
 // adjoint of rhs_m = U_m + dtm (A_m_new - A_m_old) - dtm R_{m+1}_old + sum_l q_l dt (A_l_old + R_l_old)
 __global__ void rhs_adjoint_kernel(RhsAdjArgs a) {
     // one thread per zone, every field (no 64-bit division per element)
@@ -306,7 +480,8 @@ __global__ void reduce_rows_kernel(long long N, const double* __restrict__ x, do
     X(1, 2, TOPO_GENERIC) \
     X(3, 2, TOPO_GENERIC) \
     X(3, 5, TOPO_CHAIN)   \
-    X(3, 7, TOPO_CHAIN)
+    X(3, 7, TOPO_CHAIN)   \
+    X(3, 13, TOPO_CHAIN)
 
 bool adjoint_supported(int dim, int nspec, int topo) {
 #define X(d, ns, tp) \
@@ -337,13 +512,22 @@ cudaError_t launch_stencil_vjp(const NetParams& P, int dim, int limiter, long lo
     return cudaErrorInvalidValue;
 }
 
+template <int NS, int TOPO>
+static void launch_rvjp(unsigned g, cudaStream_t st, const NetParams& P, long long N, int dim, const double* U,
+                        const double* Rbar, double* Ubar, double dtm, double* rhsbar, double* abar_zone) {
+    if constexpr (TOPO == TOPO_CHAIN)
+        reaction_vjp_chain_kernel<NS><<<g, ADJ_BLOCK, 0, st>>>(P, N, dim, U, Rbar, Ubar, dtm, rhsbar, abar_zone);
+    else
+        reaction_vjp_kernel<NS, TOPO><<<g, ADJ_BLOCK, 0, st>>>(P, N, dim, U, Rbar, Ubar, dtm, rhsbar, abar_zone);
+}
+
 cudaError_t launch_reaction_vjp(const NetParams& P, int dim, long long N, const double* U, const double* Rbar,
                                 double* Ubar, double dtm, double* rhsbar, double* abar_zone, cudaStream_t st) {
     const unsigned g = (unsigned)((N + ADJ_BLOCK - 1) / ADJ_BLOCK);
-#define X(d, ns, tp)                                                                                           \
-    if (dim == d && P.nspec == ns && P.topo == tp) {                                                           \
-        reaction_vjp_kernel<ns, tp><<<g, ADJ_BLOCK, 0, st>>>(P, N, dim, U, Rbar, Ubar, dtm, rhsbar, abar_zone); \
-        return cudaGetLastError();                                                                             \
+#define X(d, ns, tp)                                                                  \
+    if (dim == d && P.nspec == ns && P.topo == tp) {                                  \
+        launch_rvjp<ns, tp>(g, st, P, N, dim, U, Rbar, Ubar, dtm, rhsbar, abar_zone); \
+        return cudaGetLastError();                                                    \
     }
     SDC_ADJ_CASES(X)
 #undef X

@@ -65,9 +65,9 @@ def torch_cuda():
 
 
 # ------------------------------------------------------------------ inputs
-def hot_spot_problem(n, limiter, nodes="lobatto"):
+def hot_spot_problem(n, limiter, nodes="lobatto", nspec=7, n_iters=3):
     """nodes: "lobatto", "radau" (3 nodes) or "radau4" (node 0 and three Radau points)."""
-    P, U = W.config_box(n=n, nspec=7, n_iters=3, seed=1, T0=0.5)
+    P, U = W.config_box(n=n, nspec=nspec, n_iters=n_iters, seed=1, T0=0.5)
     P = copy.deepcopy(P)
     P.limiter = limiter
     P.nodes = "radau" if nodes == "radau4" else nodes
@@ -368,6 +368,42 @@ def test_rate_gradient_hot_spot(torch_cuda, n, nsteps, limiter, nodes):
     assert err_y.max() <= TOL
     assert Lb == pytest.approx(L, rel=1e-9)
     assert np.abs(gb - ga).max() <= TOL * np.abs(ga).max()
+    assert err_plain <= TOL
+
+
+@pytest.mark.parametrize("limiter", [1, 0])
+def test_rate_gradient_13species(torch_cuda, limiter):
+    """The 13-species chain (14 x 14 Newton system; the adjoint's transposed
+    solve by the bordered chain elimination in reversed chain order): dL/da_j
+    of the released energy and of the product yields against GPU finite
+    differences and against the oracle's, 8^3, two steps of the 3-node, 4-iteration
+    scheme; the binding-energy form against the plain central difference at
+    h = 1e-6."""
+    P, U = hot_spot_problem(8, limiter, nspec=13, n_iters=4)
+    dt = O.Oracle(P).cfl_dt(U)
+    model = GpuModel(torch_cuda, P, 2, dt)
+    orc = OracleModel(P, 2, dt)
+    U0 = state_from_T(P, base_T(P))
+    a = np.array(P.net.a, dtype=np.float64)
+    L, ga, J = rate_gradients(model, P, U0, a)
+    assert L == pytest.approx(released(P, U0, model.run(U0, a)), rel=1e-12)
+    d_rel, d_yield = rate_differences(model.run, P, U0, a)
+    err_rel, err_y = rate_errors(ga, d_rel, J, d_yield)
+    o_rel, o_yield = rate_differences(orc.run, P, U0, a)
+    oerr_rel, oerr_y = rate_errors(ga, o_rel, J, o_yield)
+    Lb, _, gb = model.grad(U0, a, binding_loss(P))
+    d_plain = []
+    for k in range(len(a)):
+        e = np.zeros_like(a); e[k] = 1.0
+        d_plain.append(fd_plain(lambda s: released_binding(P, U0, model.run(U0, a + s * e)), 0.0, H_PLAIN * a[k]))
+    d_plain = np.array(d_plain)
+    err_plain = np.abs(gb - d_plain).max() / np.abs(d_plain).max()
+    print("13 species: released", err_rel, "yields", err_y.max(), "oracle FD: released", oerr_rel, "yields",
+          oerr_y.max(), "binding plain h=1e-6", err_plain)
+    assert np.isfinite(ga).all() and np.isfinite(J).all()
+    assert err_rel <= TOL and err_y.max() <= TOL
+    assert oerr_rel <= TOL and oerr_y.max() <= TOL
+    assert Lb == pytest.approx(L, rel=1e-9)
     assert err_plain <= TOL
 
 
