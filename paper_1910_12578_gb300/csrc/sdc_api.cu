@@ -207,6 +207,7 @@ struct sdc_ctx {
     double* Ag[2][MAXM] = {{nullptr}};        // two generations of A at nodes 1..M-1
     double* Rg[2][MAXM] = {{nullptr}};
     double* rhs = nullptr;
+    double* anchor = nullptr;                 // the step's rate anchors (alpha chain; NewtonCfg::anchor)
     DevStats* d_stats = nullptr;
     unsigned long long* d_smax = nullptr;
     std::vector<void*> allocs;
@@ -406,12 +407,15 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
             SDC_LAUNCH(prof, CLS_OTHER, launch_reaction_source4(c->P, c->dim, N, c->d_boxes, c->nbox, node[0], c->R0,
                                                                 c->fw, st));
         else
-            SDC_LAUNCH(prof, CLS_OTHER, launch_reaction_source(c->P, N, c->dim, node[0], c->R0, st));
+            SDC_LAUNCH(prof, CLS_OTHER, launch_reaction_source(c->P, N, c->dim, node[0], c->R0, st, c->anchor));
     } else if ((e = cudaMemsetAsync(c->R0, 0, sizeof(double) * c->nw * N, st)) != cudaSuccess) {
         return e;
     }
     const double* Aold[MAXM] = {c->A0, c->A0, c->A0, c->A0};
     const double* Rold[MAXM] = {c->R0, c->R0, c->R0, c->R0};
+    // the second-order step's Newton solves take the rate anchors R(U^n) just wrote
+    NewtonCfg cfg_a = c->cfg;
+    cfg_a.anchor = with_R ? c->anchor : nullptr;
     for (int k = 0; k < c->K; k++) {
         const int g = k & 1;
         // an operator that is off stays zero: its arrays are all the zeroed node-0 array
@@ -467,7 +471,7 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
                                                                 c->d_stats, c->fw, st, c->newton_variant, q,
                                                                 c->persistent_blocks));
                 } else
-                    SDC_LAUNCH(prof, CLS_NEWTON, launch_newton(c->P, c->cfg, c->prec, N, c->dim, c->rhs, guess,
+                    SDC_LAUNCH(prof, CLS_NEWTON, launch_newton(c->P, cfg_a, c->prec, N, c->dim, c->rhs, guess,
                                                                Rpred, node[m + 1], Rnew[m + 1], dt_dev,
                                                                c->tau[m + 1] - c->tau[m], 0.0, nullptr, nullptr,
                                                                c->d_stats, st, c->newton_variant, q,
@@ -758,6 +762,9 @@ sdc_status sdc_init_box(const sdc_box* boxes, int nbox, const sdc_network* net, 
     if ((e = ctx_alloc(c, (void**)&c->A0, ub)) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->R0, rb)) != cudaSuccess) return fail(e);
     if ((e = ctx_alloc(c, (void**)&c->rhs, ub)) != cudaSuccess) return fail(e);
+    if (c->P.topo == TOPO_CHAIN && c->space_order == 2 &&
+        (e = ctx_alloc(c, (void**)&c->anchor, sizeof(double) * (size_t)(c->P.nreac + 2) * Ntot)) != cudaSuccess)
+        return fail(e);
     if (dim == 3 && c->space_order == 2) {
         // the direction-split stencil: the primitives buffer and the tiles of its passes
         if ((e = ctx_alloc(c, (void**)&c->prim, ub)) != cudaSuccess) return fail(e);

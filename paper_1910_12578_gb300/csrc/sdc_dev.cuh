@@ -117,7 +117,41 @@ inline void set_chain_coefs(NetParams& P) {
 struct NewtonCfg {
     double rtol;
     int maxit;
+    // rate anchors of the step's initial state (alpha chain, power law; nullptr:
+    // none): per zone kappa_j = amp_j T_a^nu_j (rows 0..nreac-1), T_a and 1/T_a
+    // (rows nreac, nreac+1), written by reaction_source_kernel at U^n.  A solve
+    // whose start lies within 2^-20 of T_a in temperature forms its rate
+    // factors from them (rate_consts_anchor) instead of a log2 and nreac exp2.
+    const double* anchor = nullptr;
 };
+
+// kappa_j(T) = kappa_j(T_a) (T / T_a)^nu_j from the zone's anchor, where
+// |delta| = |T / T_a - 1| <= 2^-20 and every nu_j <= 45 (P.rate_taylor):
+// T - T_a is exact (the two lie within a factor of two), delta is formed with
+// the anchor's 1/T_a, ln(1 + delta) = delta - delta^2/2 + delta^3/3 (the next
+// term is below 2^-82), and (1 + delta)^nu_j = exp(y), y = nu_j ln(1 + delta),
+// |y| <= 45 2^-20, by exp(y) - 1 = y + y^2/2 + y^3/6 (the next term is below
+// 2^-62): five FP64 operations per reaction in place of an exp2 and two products,
+// and no log2.  dfac = 1/T as rate_consts_k forms it.  Returns false (nothing
+// formed) where the anchor does not apply, or is not valid (T_a stored as nan).
+template <int NR>
+__device__ __forceinline__ bool rate_consts_anchor(const NetParams& P, double T, const double* anchor, long long N,
+                                                   long long z, double* k, double& dfac) {
+    if (!P.rate_taylor) return false;
+    const double Ta = anchor[(long long)NR * N + z], iTa = anchor[(long long)(NR + 1) * N + z];
+    const double delta = (T - Ta) * iTa;
+    if (!(mag2(delta) <= mag2(0x1p-20))) return false;  // a nan delta fails
+    const double L = fma(delta * delta, fma(delta, 1.0 / 3.0, -0.5), delta);
+#pragma unroll
+    for (int j = 0; j < NR; j++) {
+        const double ka = anchor[(long long)j * N + z];
+        const double y = P.nu[j] * L;
+        const double p = fma(y * y, fma(y, 1.0 / 6.0, 0.5), y);
+        k[j] = fma(ka, p, ka);
+    }
+    dfac = rcp_nr(T);
+    return true;
+}
 
 // Device-side accumulators of the Newton statistics.
 struct DevStats {

@@ -38,8 +38,9 @@ cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, lo
                           unsigned long long* queue = nullptr, int persistent_blocks = 0);
 int newton_persistent_blocks(const NetParams& P, int prec);  // resident blocks x SMs
 
+// anchor: where non-null (alpha chain), the step's rate anchors of NewtonCfg at U
 cudaError_t launch_reaction_source(const NetParams& P, long long N, int dim, const double* U, double* R,
-                                   cudaStream_t st);
+                                   cudaStream_t st, double* anchor = nullptr);
 
 cudaError_t launch_stencil(const NetParams& P, int dim, int limiter, long long Ntot, const BoxDev* boxes,
                            const TileDev* tiles, int ntiles, const double* U, double* A, int mode,

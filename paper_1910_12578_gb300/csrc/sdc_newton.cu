@@ -27,7 +27,8 @@ constexpr int newton_min_blocks() {
 template <int NS, int TOPO>
 __device__ __forceinline__ void load_zone(ZoneState<NS>& S, const NetParams& P, long long N, int dim, long long z,
                                           const double* __restrict__ rhs, const double* guess,
-                                          const double* __restrict__ Rpred, double dtm, double* mom) {
+                                          const double* __restrict__ Rpred, double dtm, double* mom,
+                                          const double* anchor) {
     constexpr int NW = NS + 1;
     const double rho = rhs[z];
     double m2 = 0.0;
@@ -61,7 +62,7 @@ __device__ __forceinline__ void load_zone(ZoneState<NS>& S, const NetParams& P, 
 #pragma unroll
         for (int r = 0; r < NW; r++) S.w[r] = guess[(1 + dim + r) * N + z] * scale;
     }
-    zone_init<NS, TOPO>(S, P, rho, ir, ke, mr, Tw, dtm);
+    zone_init<NS, TOPO>(S, P, rho, ir, ke, mr, Tw, dtm, anchor, N, z);
 }
 
 // Store the solution and R of a finished zone.
@@ -101,7 +102,7 @@ newton_kernel(const __grid_constant__ NetParams P, NewtonCfg cfg, long long N, i
         const double dtm = dt_dev ? (*dt_dev) * dt_frac : dtm_host;
         ZoneState<NS> S;
         double mom[3];
-        load_zone<NS, TOPO>(S, P, N, dim, z, rhs, guess, Rpred, dtm, mom);
+        load_zone<NS, TOPO>(S, P, N, dim, z, rhs, guess, Rpred, dtm, mom, cfg.anchor);
         while (!S.done) zone_iterate<NS, TOPO, MT>(S, P, cfg, dtm);
         store_zone<NS, TOPO>(S, P, N, dim, z, mom, Uout, Rout, zone_status, zone_iters);
         iters = S.iters;
@@ -166,7 +167,7 @@ newton_queue_kernel(const __grid_constant__ NetParams P, NewtonCfg cfg, long lon
                 const long long zi = (long long)(base + __popc(want & ((1u << lane) - 1u)));
                 if (zi < N) {
                     z = zi;
-                    load_zone<NS, TOPO>(S, P, N, dim, z, rhs, guess, Rpred, dtm, mom);
+                    load_zone<NS, TOPO>(S, P, N, dim, z, rhs, guess, Rpred, dtm, mom, cfg.anchor);
                 } else {
                     exhausted = true;
                 }
@@ -230,7 +231,7 @@ newton_warpqueue_kernel(const __grid_constant__ NetParams P, NewtonCfg cfg, long
         if (z < N) {
             ZoneState<NS> S;
             double mom[3];
-            load_zone<NS, TOPO>(S, P, N, dim, z, rhs, guess, Rpred, dtm, mom);
+            load_zone<NS, TOPO>(S, P, N, dim, z, rhs, guess, Rpred, dtm, mom, cfg.anchor);
             while (!S.done) zone_iterate<NS, TOPO, MT>(S, P, cfg, dtm);
             store_zone<NS, TOPO>(S, P, N, dim, z, mom, Uout, Rout, zone_status, zone_iters);
             atomicAdd(&hist[S.iters < 63 ? S.iters : 63], 1u);
@@ -368,7 +369,8 @@ constexpr size_t group_smem() {
 
 template <int NS, int TOPO>
 __global__ void __launch_bounds__(NEWTON_BLOCK)
-reaction_source_kernel(NetParams P, long long N, int dim, const double* __restrict__ U, double* __restrict__ R) {
+reaction_source_kernel(NetParams P, long long N, int dim, const double* __restrict__ U, double* __restrict__ R,
+                       double* __restrict__ anchor) {
     constexpr int NW = NS + 1;
     constexpr int NR = NS - 1;
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -389,6 +391,15 @@ reaction_source_kernel(NetParams P, long long N, int dim, const double* __restri
 #pragma unroll
         for (int i = 0; i < NS; i++) Y[i] = U[(2 + dim + i) * N + z];
         sources_w<NS>(P, k, Y, Rz);
+        if (anchor) {
+            // the step's rate anchors (NewtonCfg): kappa_j, T and 1/T, or a nan T_a
+            // where T is not positive and finite
+            const bool ok = positive_finite(T);
+#pragma unroll
+            for (int j = 0; j < NR; j++) anchor[(long long)j * N + z] = k[j];
+            anchor[(long long)NR * N + z] = ok ? T : __longlong_as_double(0x7ff8000000000000ll);
+            anchor[(long long)(NR + 1) * N + z] = ok ? dfac : 0.0;
+        }
     } else {
         double dk[NR];
         rate_consts<NR>(P, rho, T, k, dk);
@@ -626,16 +637,16 @@ cudaError_t launch_newton(const NetParams& P, const NewtonCfg& cfg, int prec, lo
 }
 
 cudaError_t launch_reaction_source(const NetParams& P, long long N, int dim, const double* U, double* R,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, double* anchor) {
     if (N <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)((N + NEWTON_BLOCK - 1) / NEWTON_BLOCK);
     if (newton_group_case(P.nspec, P.topo)) {
-        reaction_source_kernel<13, TOPO_CHAIN><<<grid, NEWTON_BLOCK, 0, st>>>(P, N, dim, U, R);
+        reaction_source_kernel<13, TOPO_CHAIN><<<grid, NEWTON_BLOCK, 0, st>>>(P, N, dim, U, R, anchor);
         return cudaGetLastError();
     }
 #define X(ns, tp)                                                                              \
     if (P.nspec == ns && P.topo == tp) {                                                       \
-        reaction_source_kernel<ns, tp><<<grid, NEWTON_BLOCK, 0, st>>>(P, N, dim, U, R);        \
+        reaction_source_kernel<ns, tp><<<grid, NEWTON_BLOCK, 0, st>>>(P, N, dim, U, R, anchor); \
         return cudaGetLastError();                                                             \
     }
     SDC_NEWTON_CASES(X)

@@ -80,11 +80,14 @@ __device__ __forceinline__ double residual_norm(const double* G, double wE) {
 // PHI false the norm is left for later (have_phi false) where the exponents of
 // G and wE alone show it finite: every |G_r| and |G_0 wE| below 2^500 bounds
 // it by 2^1004 (integer pipe); otherwise it is formed as with PHI.
+// With anchor (the step's rate anchors, see NewtonCfg) the alpha chain's rate
+// factors come from zone z's anchor where it applies.
 template <int NS, int TOPO, bool PHI = true>
 __device__ __forceinline__ bool eval_at_T(const NetParams& P, double rho, double T, const double* ym,
                                           const double* w, const double* rw, double dtm, double wE, double* k,
                                           double* dk, double& dfac, double* Y, double* G, double& phi,
-                                          bool* have_phi = nullptr) {
+                                          bool* have_phi = nullptr, const double* anchor = nullptr, long long NZ = 0,
+                                          long long z = 0) {
     constexpr int N = NS + 1;
     constexpr int NR = NS - 1;
     // G = w - dt_m R(w) - rw, formed as (w - rw) - dt_m R
@@ -92,7 +95,7 @@ __device__ __forceinline__ bool eval_at_T(const NetParams& P, double rho, double
         // kappa_j = amp_j f_j(T) with the masses and density folded in: the
         // sources are products of the unknowns themselves (no Y_i)
         double R[N];
-        rate_consts_k<NR>(P, P.amp, T, k, dfac);
+        if (!(anchor && rate_consts_anchor<NR>(P, T, anchor, NZ, z, k, dfac))) rate_consts_k<NR>(P, P.amp, T, k, dfac);
         sources_w<NS>(P, k, w + 1, R);
 #pragma unroll
         for (int r = 0; r < N; r++) G[r] = fma(-dtm, R[r], w[r] - rw[r]);
@@ -155,7 +158,8 @@ struct ZoneState {
 // positive and finite, else 0.  Evaluates the residual at the start.
 template <int NS, int TOPO>
 __device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, double rho, double inv_rho,
-                                          double ke, double mr, double Tw, double dtm) {
+                                          double ke, double mr, double Tw, double dtm, const double* anchor = nullptr,
+                                          long long NZ = 0, long long z = 0) {
     constexpr int N = NS + 1;
     S.rho = rho;
     S.inv_rho = inv_rho;
@@ -196,7 +200,7 @@ __device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, 
     S.r_final = false;
     S.h = PTC_H0;
     S.have_k = positive_finite(T) && eval_at_T<NS, TOPO, false>(P, rho, T, S.ym, S.w, S.rw, dtm, S.wE, S.k, S.dk,
-                                                                S.dfac, S.Y, S.G, S.phi, &S.have_phi);
+                                                                S.dfac, S.Y, S.G, S.phi, &S.have_phi, anchor, NZ, z);
     S.done = !S.have_k;
     if (!S.have_k) S.status = ZONE_NONPHYSICAL;
 }
