@@ -820,6 +820,9 @@ def run_ours(args):
             line[PREC_NAMES[pr_]] = {
                 "prec": PREC_NAMES[pr_], "dtype": dtype(pr_), "value": rec2["value"],
                 "ms_per_step": rec2["ms_per_step"], "speedup_vs_fp64": head["ms_per_step"] / rec2["ms_per_step"],
+                # the implicit reaction update alone (eager per-class profile): the part the precision changes
+                "newton_speedup_vs_fp64": (head["profile_ms"]["newton"] / rec2["profile_ms"]["newton"]
+                                           if head.get("profile_ms") and rec2.get("profile_ms") else None),
                 "e2e": rec2["e2e"], "clocks": rec2["clocks"], "roofline": rec2["roofline"],
                 "kernel_variants": rec2["kernel_variants"], "profile_ms": rec2["profile_ms"],
                 "newton": rec2["newton"], "oracle_error": err2,
