@@ -46,13 +46,13 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per zone of one Newton launch, from one ncu
 # capture per kernel variant and precision, keyed by (nspec, Newton variant, prec).  The captures ran on a 128^3
 # box of the 256^3 workload's network (2.1M zones: every array of the launch exceeds L2, so its writes reach
-# DRAM and the traffic grows in proportion to the zones; algorithmic 512 B per zone: the rhs and R^{m+1,(k)}
-# read, the new state and R written), mean over the 8 launches of a step, so a launch over N zones moves N times
-# this.  A variant or precision without a capture of the current kernels reports null.
+# DRAM and the traffic grows in proportion to the zones; algorithmic 624 B per zone: the rhs, R^{m+1,(k)} and
+# the step's rate anchors read, the new state and R written), mean over the 8 launches of a step, so a launch
+# over N zones moves N times this.  A variant or precision without a capture of the current kernels reports null.
 NEWTON_TRAFFIC_PER_ZONE = {
-    (13, 2, "fp64"): (538.1e6 + 510.6e6) / 2097152,       # newton_kernel<13, chain, double>, static grid
-    (13, 2, "fp32jac"): (554.6e6 + 520.8e6) / 2097152,    # newton_kernel<13, chain, float>
-    (13, 2, "fp32x2jac"): (542.9e6 + 751.1e6) / 2097152,  # newton_kernel<13, chain, f2>: its spills reach DRAM
+    (13, 2, "fp64"): (764.6e6 + 516.9e6) / 2097152,       # newton_kernel<13, chain, double>, static grid
+    (13, 2, "fp32jac"): (781.7e6 + 528.7e6) / 2097152,    # newton_kernel<13, chain, float>
+    (13, 2, "fp32x2jac"): (772.0e6 + 792.8e6) / 2097152,  # newton_kernel<13, chain, f2>: its spills reach DRAM
 }
 # The same for one advective term of the direction-split passes (x, y, z; A only), 128^3 box, 13 species.
 PREC_NAMES = {0: "fp64", 1: "fp32jac", 2: "fp32x2jac"}   # sdc_precision values
