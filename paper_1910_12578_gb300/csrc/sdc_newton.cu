@@ -9,13 +9,16 @@ namespace sdcd {
 constexpr int NEWTON_BLOCK = 128;
 
 // Resident blocks per SM the one-zone-per-thread kernels ask the register
-// allocator for: the float-pair solve, whose FP32 work is a chain of dependent
-// operations, runs three (168 registers a thread) to hide its latency; the FP64
-// and FP32 solves, bound by the FP64 pipe, keep every register (measured at
-// 256^3, 13 species: float pairs 273 -> 258 ms of Newton per step, FP64 -1 %).
+// allocator for.  Three (168 registers a thread, twelve warps per SM) for the
+// float-pair solve, whose FP32 work is a chain of dependent operations, and for
+// the FP64 solve, whose FP64 pipe the extra warps keep busier even though its
+// 13-species kernel then spills more (measured at 256^3, 13 species: float
+// pairs 219.7 -> 178.2 ms of Newton per step against two blocks; FP64 217.6 ->
+// 210.1 ms with the rate anchors; 7 species unchanged).  The FP32-Jacobian
+// solve keeps every register.
 template <typename MT>
 constexpr int newton_min_blocks() {
-    return std::is_same<MT, f2>::value ? 3 : 1;
+    return std::is_same<MT, float>::value ? 1 : 3;
 }
 
 // Load zone z into a solver state and evaluate it.  The start: with Rpred
