@@ -9,16 +9,16 @@ namespace sdcd {
 constexpr int NEWTON_BLOCK = 128;
 
 // Resident blocks per SM the one-zone-per-thread kernels ask the register
-// allocator for.  Three (168 registers a thread, twelve warps per SM) for the
-// float-pair solve, whose FP32 work is a chain of dependent operations, and for
-// the FP64 solve, whose FP64 pipe the extra warps keep busier even though its
-// 13-species kernel then spills more (measured at 256^3, 13 species: float
-// pairs 219.7 -> 178.2 ms of Newton per step against two blocks; FP64 217.6 ->
-// 210.1 ms with the rate anchors; 7 species unchanged).  The FP32-Jacobian
-// solve keeps every register.
+// allocator for: three (168 registers a thread, twelve warps per SM) in every
+// precision.  The float-pair solve's FP32 work is a chain of dependent
+// operations, and the FP64 and FP32-Jacobian solves keep their FP64 pipe busier
+// with the extra warps, though their 13-species kernels then spill more.
+// Measured at 256^3, 13 species, Newton per step: float pairs 219.7 (two blocks)
+// -> 178.2 ms; FP64 217.6 (two) -> 210.3 (three) -> 213.0 ms (four); FP32
+// Jacobian 155.3 (two) -> 141.3 ms; 7 species unchanged.
 template <typename MT>
 constexpr int newton_min_blocks() {
-    return std::is_same<MT, float>::value ? 1 : 3;
+    return 3;
 }
 
 // Load zone z into a solver state and evaluate it.  The start: with Rpred
