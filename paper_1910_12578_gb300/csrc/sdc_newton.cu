@@ -40,8 +40,11 @@ __device__ __forceinline__ void load_zone(ZoneState<NS>& S, const NetParams& P, 
         mom[d] = rhs[(1 + d) * N + z];
         m2 += mom[d] * mom[d];
     }
+    double rw[NW];
 #pragma unroll
-    for (int r = 0; r < NW; r++) S.rw[r] = rhs[(1 + dim + r) * N + z];
+    for (int r = 0; r < NW; r++) rw[r] = rhs[(1 + dim + r) * N + z];
+    S.rwp = rhs + (1 + dim) * N + z;
+    S.rws = N;
     // 1/rho, the kinetic energy and the floor -0.01 rho, formed once for the start
     // test and the solve
     const double ir = rcp_nr(rho);
@@ -51,7 +54,7 @@ __device__ __forceinline__ void load_zone(ZoneState<NS>& S, const NetParams& P, 
     double Tw = 0.0;
     if (Rpred) {
 #pragma unroll
-        for (int r = 0; r < NW; r++) S.w[r] = __dadd_rn(S.rw[r], __dmul_rn(dtm, Rpred[r * N + z]));
+        for (int r = 0; r < NW; r++) S.w[r] = __dadd_rn(rw[r], __dmul_rn(dtm, Rpred[r * N + z]));
         Tw = P.gm1 * (S.w[0] - ke) * ir;
         pred = positive_finite(Tw);
         // rho X_i >= -0.01 rho, compared on the integer pipe
@@ -65,7 +68,7 @@ __device__ __forceinline__ void load_zone(ZoneState<NS>& S, const NetParams& P, 
 #pragma unroll
         for (int r = 0; r < NW; r++) S.w[r] = guess[(1 + dim + r) * N + z] * scale;
     }
-    zone_init<NS, TOPO>(S, P, rho, ir, ke, mr, Tw, dtm, anchor, N, z);
+    zone_init<NS, TOPO>(S, P, rw, rho, ir, ke, mr, Tw, dtm, anchor, N, z);
 }
 
 // Store the solution and R of a finished zone.
@@ -104,6 +107,8 @@ newton_kernel(const __grid_constant__ NetParams P, NewtonCfg cfg, long long N, i
     if (active) {
         const double dtm = dt_dev ? (*dt_dev) * dt_frac : dtm_host;
         ZoneState<NS> S;
+        S.lop = newton_floor_smem<NS, MT>();
+        S.los = (int)blockDim.x;
         double mom[3];
         load_zone<NS, TOPO>(S, P, N, dim, z, rhs, guess, Rpred, dtm, mom, cfg.anchor);
         while (!S.done) zone_iterate<NS, TOPO, MT>(S, P, cfg, dtm);
@@ -152,6 +157,8 @@ newton_queue_kernel(const __grid_constant__ NetParams P, NewtonCfg cfg, long lon
     const double dtm = dt_dev ? (*dt_dev) * dt_frac : dtm_host;
     const int lane = threadIdx.x & 31;
     ZoneState<NS> S;
+    S.lop = newton_floor_smem<NS, MT>();
+    S.los = (int)blockDim.x;
     double mom[3];
     long long z = -1;
     bool exhausted = false;
@@ -233,6 +240,8 @@ newton_warpqueue_kernel(const __grid_constant__ NetParams P, NewtonCfg cfg, long
         const long long z = (long long)base + lane;
         if (z < N) {
             ZoneState<NS> S;
+            S.lop = newton_floor_smem<NS, MT>();
+            S.los = (int)blockDim.x;
             double mom[3];
             load_zone<NS, TOPO>(S, P, N, dim, z, rhs, guess, Rpred, dtm, mom, cfg.anchor);
             while (!S.done) zone_iterate<NS, TOPO, MT>(S, P, cfg, dtm);
@@ -432,7 +441,7 @@ bool newton_small_group_case(int nspec, int topo) { return topo == TOPO_CHAIN &&
 // the float-pair kernels' dynamic shared memory (above the default 48 KB for 13 species)
 template <int NS>
 cudaError_t pair_prepare() {
-    const int b = (int)pair_pivot_bytes<NS, f2>(NEWTON_BLOCK);
+    const int b = (int)newton_smem_bytes<NS, f2>(NEWTON_BLOCK);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(newton_kernel<NS, TOPO_CHAIN, f2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   b)) != cudaSuccess)
@@ -519,12 +528,14 @@ template <int NS, int TOPO>
 int queue_blocks_per_sm(int prec) {
     int per = 0;
     if (prec == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, newton_queue_kernel<NS, TOPO, double>, NEWTON_BLOCK, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, newton_queue_kernel<NS, TOPO, double>, NEWTON_BLOCK,
+                                                      newton_smem_bytes<NS, double>(NEWTON_BLOCK));
     else if (prec == 1)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, newton_queue_kernel<NS, TOPO, float>, NEWTON_BLOCK, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, newton_queue_kernel<NS, TOPO, float>, NEWTON_BLOCK,
+                                                      newton_smem_bytes<NS, float>(NEWTON_BLOCK));
     else if constexpr (TOPO == TOPO_CHAIN)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, newton_queue_kernel<NS, TOPO, f2>, NEWTON_BLOCK,
-                                                      pair_pivot_bytes<NS, f2>(NEWTON_BLOCK));
+                                                      newton_smem_bytes<NS, f2>(NEWTON_BLOCK));
     return per;
 }
 
@@ -548,7 +559,7 @@ cudaError_t launch_per_zone(int kind, unsigned grid, unsigned pgrid, const NetPa
                             double* Uout, double* Rout, const double* dt_dev, double dt_frac, double dtm_host,
                             int* zone_status, int* zone_iters, DevStats* stats, unsigned long long* queue,
                             cudaStream_t st) {
-    const size_t sm = pair_pivot_bytes<NS, MT>(NEWTON_BLOCK);
+    const size_t sm = newton_smem_bytes<NS, MT>(NEWTON_BLOCK);
     if (kind == 2)
         newton_warpqueue_kernel<NS, TOPO, MT><<<pgrid, NEWTON_BLOCK, sm, st>>>(
             P, cfg, N, dim, rhs, guess, Rpred, Uout, Rout, dt_dev, dt_frac, dtm_host, zone_status, zone_iters, stats,

@@ -27,12 +27,24 @@
 namespace sdcd {
 
 // Dynamic shared memory of the one-zone-per-thread kernels: the float-pair
-// solve's pivot rows (pair_pivot_bytes per block; none for the other types).
+// solve's pivot rows (pair_pivot_bytes per block; none for the other types),
+// then every thread's composition floors (NS doubles, stride blockDim.x).
 extern __shared__ double newton_smem[];
 
 template <int NS, typename MT>
-constexpr size_t pair_pivot_bytes(int block) {
+__host__ __device__ constexpr size_t pair_pivot_bytes(int block) {
     return std::is_same<MT, f2>::value ? (size_t)5 * (NS - 1) * sizeof(f2) * (size_t)block : 0;
+}
+
+template <int NS, typename MT>
+__host__ __device__ constexpr size_t newton_smem_bytes(int block) {
+    return pair_pivot_bytes<NS, MT>(block) + (size_t)NS * sizeof(double) * (size_t)block;
+}
+
+// this thread's first composition floor (the next at + blockDim.x, ...)
+template <int NS, typename MT>
+__device__ __forceinline__ double* newton_floor_smem() {
+    return newton_smem + pair_pivot_bytes<NS, MT>((int)blockDim.x) / sizeof(double) + threadIdx.x;
 }
 
 template <int NS, int TOPO>
@@ -139,27 +151,35 @@ __device__ __forceinline__ bool eval_state(const NetParams& P, double rho, doubl
     return eval_at_T<NS, TOPO>(P, rho, T, ym, w, rw, dtm, wE, k, dk, dfac, Y, G, phi);
 }
 
-// Register-resident state of one zone's solve.
+// Register-resident state of one zone's solve.  The reactive part of the rhs
+// stays in global memory (rwp, stride rws; needed again only where a trial is
+// evaluated in full) and the composition floors in shared memory (lop, stride
+// los), so that neither holds registers through the solve.
 template <int NS>
 struct ZoneState {
     static constexpr int N = NS + 1;
     static constexpr int NR = NS - 1;
     double rho, inv_rho, ke, wE, phi, h, dfac;
-    double ym[NS], lower[NS], rw[N], w[N], G[N], k[NR], dk[NR], Y[NS];  // ym, dk, Y: general networks
+    double ym[NS], w[N], G[N], k[NR], dk[NR], Y[NS];  // ym, dk, Y: general networks
+    const double* rwp;
+    long long rws;
+    double* lop;
+    int los;
     int iters, status;
     bool newton, have_k, done;
     bool have_phi;  // phi holds the norm of G (at the start it is formed only when a decision needs it)
     bool r_final;   // G holds R at the solution (set by the stop test's last step)
 };
 
-// Set up a zone: rw = reactive part of the rhs, w = the (density-rescaled)
+// Set up a zone: rw = reactive part of the rhs (S.rwp points at it in global
+// memory, S.lop at the zone's floors in shared memory), w = the (density-rescaled)
 // guess; inv_rho = 1/rho, ke = |rho u|^2 / (2 rho) of the rhs, mr = -0.01 rho,
 // Tw = the temperature of w when the caller has formed it and found it
 // positive and finite, else 0.  Evaluates the residual at the start.
 template <int NS, int TOPO>
-__device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, double rho, double inv_rho,
-                                          double ke, double mr, double Tw, double dtm, const double* anchor = nullptr,
-                                          long long NZ = 0, long long z = 0) {
+__device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, const double* rw, double rho,
+                                          double inv_rho, double ke, double mr, double Tw, double dtm,
+                                          const double* anchor = nullptr, long long NZ = 0, long long z = 0) {
     constexpr int N = NS + 1;
     S.rho = rho;
     S.inv_rho = inv_rho;
@@ -168,14 +188,14 @@ __device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, 
 #pragma unroll
         for (int i = 0; i < NS; i++) S.ym[i] = S.inv_rho * P.inv_mass[i];
     }
-    S.wE = rho * rcp_nr(fabs(S.rw[0]));  // rho / |rhs_E|
+    S.wE = rho * rcp_nr(fabs(rw[0]));  // rho / |rhs_E|
     // a start without a positive temperature is replaced by rhs
     double T = Tw;
     if (!positive_finite(T)) {
         T = P.gm1 * (S.w[0] - S.ke) * S.inv_rho;
         if (!positive_finite(T)) {
 #pragma unroll
-            for (int r = 0; r < N; r++) S.w[r] = S.rw[r];
+            for (int r = 0; r < N; r++) S.w[r] = rw[r];
             T = P.gm1 * (S.w[0] - S.ke) * S.inv_rho;
         }
     }
@@ -186,20 +206,20 @@ __device__ __forceinline__ void zone_init(ZoneState<NS>& S, const NetParams& P, 
     const long long omr = ordered_bits(mr);
     bool physical = true;
 #pragma unroll
-    for (int i = 0; i < NS; i++) physical = physical && (ordered_bits(S.rw[1 + i]) >= omr);
+    for (int i = 0; i < NS; i++) physical = physical && (ordered_bits(rw[1 + i]) >= omr);
 #pragma unroll
     for (int i = 0; i < NS; i++) {
-        const double x = S.rw[1 + i], xg = S.w[1 + i];
+        const double x = rw[1 + i], xg = S.w[1 + i];
         double lo = ordered_bits(x) < 0 ? x : 0.0;
         lo = ordered_bits(xg) < ordered_bits(lo) ? xg : lo;
-        S.lower[i] = physical ? lo + mr : -INFINITY;  // as a bound on rho X_i
+        S.lop[i * S.los] = physical ? lo + mr : -INFINITY;  // as a bound on rho X_i
     }
     S.iters = 0;
     S.status = ZONE_MAXIT;
     S.newton = true;
     S.r_final = false;
     S.h = PTC_H0;
-    S.have_k = positive_finite(T) && eval_at_T<NS, TOPO, false>(P, rho, T, S.ym, S.w, S.rw, dtm, S.wE, S.k, S.dk,
+    S.have_k = positive_finite(T) && eval_at_T<NS, TOPO, false>(P, rho, T, S.ym, S.w, rw, dtm, S.wE, S.k, S.dk,
                                                                 S.dfac, S.Y, S.G, S.phi, &S.have_phi, anchor, NZ, z);
     S.done = !S.have_k;
     if (!S.have_k) S.status = ZONE_NONPHYSICAL;
@@ -273,7 +293,7 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     // fails the evaluation below, as it fails this test in plain compares)
     bool ok = true;
 #pragma unroll
-    for (int i = 0; i < NS; i++) ok = ok && (ordered_bits(tr[1 + i]) >= ordered_bits(S.lower[i]));
+    for (int i = 0; i < NS; i++) ok = ok && (ordered_bits(tr[1 + i]) >= ordered_bits(S.lop[i * S.los]));
     if (S.newton && ok && newton_step_small<NS, ST>(S, cfg, ds, tr)) {
         // The step meets the stop test, so an admissible trial (T positive and
         // finite, R finite) is the solution: only R at the trial is needed, not
@@ -333,8 +353,12 @@ __device__ __forceinline__ void zone_iterate(ZoneState<NS>& S, const NetParams& 
     }
     double kt[NR], dkt[NR], Yt[NS], Gt[N];
     double phit = 0.0, dfact = 0.0;
-    if (ok)
-        ok = eval_state<NS, TOPO>(P, S.rho, S.inv_rho, S.ke, S.ym, tr, S.rw, dtm, S.wE, kt, dkt, dfact, Yt, Gt, phit);
+    if (ok) {
+        double rwt[N];
+#pragma unroll
+        for (int r = 0; r < N; r++) rwt[r] = __ldg(S.rwp + r * S.rws);
+        ok = eval_state<NS, TOPO>(P, S.rho, S.inv_rho, S.ke, S.ym, tr, rwt, dtm, S.wE, kt, dkt, dfact, Yt, Gt, phit);
+    }
     // an admissible Newton step that meets the stop test converges even if the
     // residual grew by round-off at the root
     const bool small = S.newton && ok && newton_step_small<NS, ST>(S, cfg, ds, tr);
