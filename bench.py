@@ -50,10 +50,10 @@ L2_FLUSH_BYTES = 256 << 20
 # the step's rate anchors read, the new state and R written), mean over the 8 launches of a step, so a launch
 # over N zones moves N times this.  A variant or precision without a capture of the current kernels reports null.
 NEWTON_TRAFFIC_PER_ZONE = {
-    (13, 2, "fp64"): (775.7e6 + 1036.4e6) / 2097152,      # newton_kernel<13, chain, double>, static grid: its
+    (13, 2, "fp64"): (771.9e6 + 818.0e6) / 2097152,       # newton_kernel<13, chain, double>, static grid: its
                                                           # spills (168 registers) reach DRAM
-    (13, 2, "fp32jac"): (801.6e6 + 1200.4e6) / 2097152,   # newton_kernel<13, chain, float>: the same
-    (13, 2, "fp32x2jac"): (771.7e6 + 792.9e6) / 2097152,  # newton_kernel<13, chain, f2>: the same
+    (13, 2, "fp32jac"): (791.9e6 + 771.1e6) / 2097152,    # newton_kernel<13, chain, float>: the same
+    (13, 2, "fp32x2jac"): (767.9e6 + 577.6e6) / 2097152,  # newton_kernel<13, chain, f2>: the same
 }
 # The same for one advective term of the direction-split passes (x, y, z; A only), 128^3 box, 13 species.
 PREC_NAMES = {0: "fp64", 1: "fp32jac", 2: "fp32x2jac"}   # sdc_precision values
