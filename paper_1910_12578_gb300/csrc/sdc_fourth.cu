@@ -303,45 +303,42 @@ __device__ __forceinline__ double tie_diff(double d, double other, double a, dou
     return d;
 }
 
-// zone limiter of zone a0 (neighbours amm .. app) with face values fm, fp and
-// their deviations dm = fm - a0, dp = fp - a0
-__device__ __forceinline__ void cs_zone(double amm, double am, double a0, double ap, double app, double dm,
-                                        double dp, double& fm, double& fp) {
-    const double e1 = am - a0, e2 = a0 - ap, e3 = amm - a0, e4 = a0 - app;
-    const double t1 = tie_diff(e1, e2, am, a0), t2 = tie_diff(e2, e1, a0, ap);
-    const double t3 = tie_diff(e3, e4, amm, a0), t4 = tie_diff(e4, e3, a0, app);
-    if (!opposite(dp, dm) || !same2(t1, t2) || !same2(t3, t4)) {
-        // extremum: scale both deviations by the limited curvature over the
-        // parabola's; the centred second differences from the differences above
-        // (they enter only through signs and magnitudes, where the limiter is
-        // continuous: a curvature near zero flattens either way)
-        const double d2 = 6.0 * (dm + dp);
-        const double d2c = e1 - e2, d2l = fma(-2.0, e1, e3), d2r = fma(2.0, e2, -e4);
-        if (same2(d2, d2c) && same2(d2, d2l) && same2(d2, d2r)) {
-            const double cm = CS_C * min_mag(d2c, min_mag(d2l, d2r));
-            if (mag2(d2) <= mag2(cm)) {
-                // the parabola's own curvature is the smallest: the deviations stand
-                fm = a0 + dm;
-                fp = a0 + dp;
-            } else {
-                // in (0, 1); the refined reciprocal takes normal d2 only
-                // (2^-1021 <= |d2| < 2^1022), the division the rest
-                const unsigned long long ex = mag2(d2) >> 53;
-                const double sc = (ex >= 2ull && ex < 2045ull) ? cm * rcp_nr(d2) : cm / d2;
-                fm = fma(dm, sc, a0);
-                fp = fma(dp, sc, a0);
-            }
+// Zone limiter of zone a0 (neighbours amm .. app) with face values fm, fp and
+// their deviations dm = fm - a0, dp = fp - a0 (limit4_kernel): an extremum when
+// the deviations do not have opposite signs or the differences e1 = am - a0,
+// e2 = a0 - ap (or e3 = amm - a0, e4 = a0 - app) are not of one sign after the
+// tie rule of tie_diff; there both deviations are scaled by the limited
+// curvature over the parabola's (cs_zone_extremum; the centred second
+// differences come from the differences above: they enter only through signs
+// and magnitudes, where the limiter is continuous, so a curvature near zero
+// flattens either way); elsewhere (dm, dp nonzero) the parabola may not
+// overshoot the far face: |dp| >= 2 |dm| on the bit patterns (2 |dm| is |dm|
+// with the exponent field raised by one; subnormal dm aside) sets fp = a0 - 2 dm,
+// and the same the other way.
+
+// The zone limiter's extremum branch for one (zone, field): the two deviations
+// scaled by the limited curvature over the parabola's (cs_zone); e1..e4 the
+// differences of the extremum tests.
+__device__ __forceinline__ void cs_zone_extremum(double a0, double dm, double dp, double e1, double e2, double e3,
+                                                 double e4, double& fm, double& fp) {
+    const double d2 = 6.0 * (dm + dp);
+    const double d2c = e1 - e2, d2l = fma(-2.0, e1, e3), d2r = fma(2.0, e2, -e4);
+    if (same2(d2, d2c) && same2(d2, d2l) && same2(d2, d2r)) {
+        const double cm = CS_C * min_mag(d2c, min_mag(d2l, d2r));
+        if (mag2(d2) <= mag2(cm)) {
+            fm = a0 + dm;
+            fp = a0 + dp;
         } else {
-            fm = a0;
-            fp = a0;
+            // in (0, 1); the refined reciprocal takes normal d2 only
+            // (2^-1021 <= |d2| < 2^1022), the division the rest
+            const unsigned long long ex = mag2(d2) >> 53;
+            const double sc = (ex >= 2ull && ex < 2045ull) ? cm * rcp_nr(d2) : cm / d2;
+            fm = fma(dm, sc, a0);
+            fp = fma(dp, sc, a0);
         }
     } else {
-        // monotone (dm, dp nonzero): the parabola may not overshoot the far face;
-        // |dp| >= 2 |dm| on the bit patterns (2 |dm| is |dm| with the exponent
-        // field raised by one; subnormal dm aside)
-        constexpr unsigned long long E1 = 1ull << 53;
-        if (mag2(dp) >= mag2(dm) + E1) fp = fma(-2.0, dm, a0);
-        if (mag2(dm) >= mag2(dp) + E1) fm = fma(-2.0, dp, a0);
+        fm = a0;
+        fp = a0;
     }
 }
 
@@ -352,40 +349,114 @@ __device__ __forceinline__ void cs_zone(double amm, double am, double a0, double
 // mass fractions are renormalised: stored first, then read back and scaled.
 // The face tests' differences give the deviations dm, dp when no face limiter
 // fires (fm - a0 = -(a0 - fm) exactly).
-__global__ void limit4_kernel(int dim, int nspec, int dir, long long N, const BoxDev* __restrict__ boxes, int nbox,
-                              const double* __restrict__ Wa, double* __restrict__ WL, double* __restrict__ WR) {
+//
+// The zone limiter's extremum branch (curvatures, their limited minimum and a
+// reciprocal) is taken by a scattered minority of (zone, field) pairs, which
+// would make most warps issue it for a few lanes field after field.  Instead a
+// lane whose field needs it queues the field's inputs in its warp's shared
+// queue; whenever 32 items are waiting, the warp's lanes take one each, and the
+// rest is drained at the end.  The arithmetic per (zone, field) is that of
+// cs_zone, so the results are the same bit for bit.
+constexpr int LIM_Q = 64;   // queue slots per warp (at most 31 waiting + 32 arriving)
+__global__ void __launch_bounds__(F_BLOCK)
+limit4_kernel(int dim, int nspec, int dir, long long N, const BoxDev* __restrict__ boxes, int nbox,
+              const double* __restrict__ Wa, double* __restrict__ WL, double* __restrict__ WR) {
+    __shared__ double qv[F_BLOCK / 32][7][LIM_Q];   // a0, dm, dp, e1, e2, e3, e4
+    __shared__ long long qz[F_BLOCK / 32][2][LIM_Q];  // the owner's zone index z and lower neighbour i1
+    __shared__ int qf[F_BLOCK / 32][LIM_Q];           // the field
     const long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (z >= N) return;
-    const ZoneCoord q = zone_coord(boxes, nbox, z);
-    const Line l = line_of(q, z, dir);
-    const long long i0 = l.at(-2), i1 = l.at(-1), i3 = l.at(1), i4 = l.at(2);
+    const bool act = z < N;
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    long long i0 = z, i1 = z, i3 = z, i4 = z;
+    if (act) {
+        const ZoneCoord q = zone_coord(boxes, nbox, z);
+        const Line l = line_of(q, z, dir);
+        i0 = l.at(-2); i1 = l.at(-1); i3 = l.at(1); i4 = l.at(2);
+    }
     const int nh = 2 + dim, nv = nh + nspec;
-    double sm = 0.0, sp = 0.0;
+    int cnt = 0;  // items waiting in the warp's queue (the same in every lane)
+    auto drain = [&](int n) {
+        // lanes 0..n-1 take items 0..n-1
+        if (lane < n) {
+            double fm, fp;
+            const double a0 = qv[wq][0][lane];
+            cs_zone_extremum(a0, qv[wq][1][lane], qv[wq][2][lane], qv[wq][3][lane], qv[wq][4][lane],
+                             qv[wq][5][lane], qv[wq][6][lane], fm, fp);
+            const long long o = (long long)qf[wq][lane] * N;
+            WL[o + qz[wq][0][lane]] = fp;
+            WR[o + qz[wq][1][lane]] = fm;
+        }
+        __syncwarp();
+    };
     for (int f = 0; f < nv; f++) {
         const long long o = (long long)f * N;
-        const double amm = Wa[o + i0], am = Wa[o + i1], a0 = Wa[o + z], ap = Wa[o + i3], app = Wa[o + i4];
-        double fm = 7.0 / 12.0 * (am + a0) - 1.0 / 12.0 * (amm + ap);
-        double fp = 7.0 / 12.0 * (a0 + ap) - 1.0 / 12.0 * (am + app);
-        // face tests: (af - left)(right - af) < 0 puts af outside its zones' range
-        double lo = a0 - fm;  // -dm
-        if (opposite(fm - am, lo)) {
-            fm = cs_face_limit(amm, am, a0, ap, fm);
-            lo = a0 - fm;
-        }
-        double dp = fp - a0;
-        if (opposite(dp, ap - fp)) {
-            fp = cs_face_limit(am, a0, ap, app, fp);
+        bool ext = false;
+        double a0 = 0.0, dm = 0.0, dp = 0.0, e1 = 0.0, e2 = 0.0, e3 = 0.0, e4 = 0.0;
+        if (act) {
+            const double amm = Wa[o + i0], am = Wa[o + i1], ap = Wa[o + i3], app = Wa[o + i4];
+            a0 = Wa[o + z];
+            double fm = 7.0 / 12.0 * (am + a0) - 1.0 / 12.0 * (amm + ap);
+            double fp = 7.0 / 12.0 * (a0 + ap) - 1.0 / 12.0 * (am + app);
+            // face tests: (af - left)(right - af) < 0 puts af outside its zones' range
+            double lo = a0 - fm;  // -dm
+            if (opposite(fm - am, lo)) {
+                fm = cs_face_limit(amm, am, a0, ap, fm);
+                lo = a0 - fm;
+            }
             dp = fp - a0;
+            if (opposite(dp, ap - fp)) {
+                fp = cs_face_limit(am, a0, ap, app, fp);
+                dp = fp - a0;
+            }
+            dm = -lo;
+            // the zone limiter (cs_zone): the extremum tests, then the monotone
+            // branch here or the extremum branch through the queue
+            e1 = am - a0; e2 = a0 - ap; e3 = amm - a0; e4 = a0 - app;
+            const double t1 = tie_diff(e1, e2, am, a0), t2 = tie_diff(e2, e1, a0, ap);
+            const double t3 = tie_diff(e3, e4, amm, a0), t4 = tie_diff(e4, e3, a0, app);
+            ext = !opposite(dp, dm) || !same2(t1, t2) || !same2(t3, t4);
+            if (!ext) {
+                constexpr unsigned long long E1 = 1ull << 53;
+                if (mag2(dp) >= mag2(dm) + E1) fp = fma(-2.0, dm, a0);
+                if (mag2(dm) >= mag2(dp) + E1) fm = fma(-2.0, dp, a0);
+                WL[o + z] = fp;
+                WR[o + i1] = fm;
+            }
         }
-        cs_zone(amm, am, a0, ap, app, -lo, dp, fm, fp);
-        WL[o + z] = fp;
-        WR[o + i1] = fm;
-        if (f >= nh) {
-            sm += fm;
-            sp += fp;
+        const unsigned b = __ballot_sync(0xffffffffu, ext);
+        if (ext) {
+            const int slot = cnt + __popc(b & lt);
+            qv[wq][0][slot] = a0; qv[wq][1][slot] = dm; qv[wq][2][slot] = dp;
+            qv[wq][3][slot] = e1; qv[wq][4][slot] = e2; qv[wq][5][slot] = e3; qv[wq][6][slot] = e4;
+            qz[wq][0][slot] = z; qz[wq][1][slot] = i1;
+            qf[wq][slot] = f;
+        }
+        cnt += __popc(b);
+        __syncwarp();
+        if (cnt >= 32) {
+            drain(32);
+            // the waiting rest moves to the front
+            const int rest = cnt - 32;
+            if (lane < rest) {
+                for (int v = 0; v < 7; v++) qv[wq][v][lane] = qv[wq][v][32 + lane];
+                qz[wq][0][lane] = qz[wq][0][32 + lane];
+                qz[wq][1][lane] = qz[wq][1][32 + lane];
+                qf[wq][lane] = qf[wq][32 + lane];
+            }
+            __syncwarp();
+            cnt = rest;
         }
     }
-    if (nspec > 0) {
+    if (cnt > 0) drain(cnt);
+    // renormalised mass fractions: the sums in field order, as written
+    if (act && nspec > 0) {
+        double sm = 0.0, sp = 0.0;
+        for (int f = nh; f < nv; f++) {
+            const long long o = (long long)f * N;
+            sm += WR[o + i1];
+            sp += WL[o + z];
+        }
         const double rm = 1.0 / sm, rp = 1.0 / sp;
         for (int f = nh; f < nv; f++) {
             const long long o = (long long)f * N;
