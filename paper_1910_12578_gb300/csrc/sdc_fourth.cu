@@ -317,8 +317,8 @@ __device__ __forceinline__ double tie_diff(double d, double other, double a, dou
 // and the same the other way.
 
 // The zone limiter's extremum branch for one (zone, field): the two deviations
-// scaled by the limited curvature over the parabola's (cs_zone); e1..e4 the
-// differences of the extremum tests.
+// scaled by the limited curvature over the parabola's (the zone limiter above);
+// e1..e4 the differences of the extremum tests.
 __device__ __forceinline__ void cs_zone_extremum(double a0, double dm, double dp, double e1, double e2, double e3,
                                                  double e4, double& fm, double& fp) {
     const double d2 = 6.0 * (dm + dp);
@@ -356,7 +356,8 @@ __device__ __forceinline__ void cs_zone_extremum(double a0, double dm, double dp
 // lane whose field needs it queues the field's inputs in its warp's shared
 // queue; whenever 32 items are waiting, the warp's lanes take one each, and the
 // rest is drained at the end.  The arithmetic per (zone, field) is that of
-// cs_zone, so the results are the same bit for bit.
+// the zone limiter above wherever a lane computes it, so the results do not
+// depend on the queue.
 constexpr int LIM_Q = 64;   // queue slots per warp (at most 31 waiting + 32 arriving)
 __global__ void __launch_bounds__(F_BLOCK)
 limit4_kernel(int dim, int nspec, int dir, long long N, const BoxDev* __restrict__ boxes, int nbox,
@@ -410,7 +411,7 @@ limit4_kernel(int dim, int nspec, int dir, long long N, const BoxDev* __restrict
                 dp = fp - a0;
             }
             dm = -lo;
-            // the zone limiter (cs_zone): the extremum tests, then the monotone
+            // the zone limiter: the extremum tests, then the monotone
             // branch here or the extremum branch through the queue
             e1 = am - a0; e2 = a0 - ap; e3 = amm - a0; e4 = a0 - app;
             const double t1 = tie_diff(e1, e2, am, a0), t2 = tie_diff(e2, e1, a0, ap);
