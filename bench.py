@@ -519,33 +519,33 @@ def measure(args, P, U, prec, ws, barrier, flush, with_e2e=True):
     value, total_ms = job_value(sum(step_ms), units, args.steps, ws, torch_reduce_max("cuda"))
 
     # ---- end to end through the public API with host buffers (pinned), copies timed.  Every step
-    # copies its input state from pinned host memory and its result back; the copies of step i+1's
-    # input and of step i-1's result run on a second stream while step i computes (double-buffered
-    # device staging arrays), as a caller streaming states through the library would.
+    # copies its input state from pinned host memory into one of two device buffers, steps that
+    # buffer in place and copies the result back; the copies of step i+1's input and of step i-1's
+    # result run on a second stream while step i computes, as a caller streaming states through the
+    # library would (the context keeps the step's graph for both buffers).
     e2e = None
     if with_e2e:
         Uh = U0.cpu().pin_memory()
         Uout = [torch.empty_like(Uh).pin_memory() for _ in range(2)]
         Din = [torch.empty_like(U0) for _ in range(2)]
-        Dout = [torch.empty_like(U0) for _ in range(2)]
         e2e_steps = max(3, min(args.steps, 10))
         comp = torch.cuda.current_stream()
         copy = torch.cuda.Stream()
-        Ud.copy_(U0)
-        ctx.step(Ud, dt, stats=False)
+        for b in range(2):   # capture the graph of each buffer outside the timed region
+            Din[b].copy_(U0)
+            ctx.step(Din[b], dt, stats=False)
         torch.cuda.synchronize()
         ev = lambda: torch.cuda.Event()
-        in_ready, in_free, out_ready, out_free = ([ev() for _ in range(2)] for _ in range(4))
+        in_ready, out_ready = ([ev() for _ in range(2)] for _ in range(2))
         ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         ea.record(comp)
         copy.wait_event(ea)
 
         def h2d(i):
+            # on the copy stream after the previous result read from this buffer (stream order)
             b = i % 2
             with torch.cuda.stream(copy):
-                if i >= 2:
-                    copy.wait_event(in_free[b])
                 Din[b].copy_(Uh, non_blocking=True)
                 in_ready[b].record(copy)
 
@@ -555,17 +555,11 @@ def measure(args, P, U, prec, ws, barrier, flush, with_e2e=True):
             if i + 1 < e2e_steps:
                 h2d(i + 1)
             comp.wait_event(in_ready[b])
-            Ud.copy_(Din[b])
-            in_free[b].record(comp)
-            ctx.step(Ud, dt, stats=False)
-            if i >= 2:
-                comp.wait_event(out_free[b])
-            Dout[b].copy_(Ud)
+            ctx.step(Din[b], dt, stats=False)
             out_ready[b].record(comp)
             with torch.cuda.stream(copy):
                 copy.wait_event(out_ready[b])
-                Uout[b].copy_(Dout[b], non_blocking=True)
-                out_free[b].record(copy)
+                Uout[b].copy_(Din[b], non_blocking=True)
         comp.wait_stream(copy)
         eb.record(comp)
         torch.cuda.synchronize()
@@ -573,9 +567,10 @@ def measure(args, P, U, prec, ws, barrier, flush, with_e2e=True):
         nbytes = U0.numel() * 8
         e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "steps": e2e_steps,
-               "note": "per step: host->device copy of the input state (pinned), the step, device->host copy "
-                       "of the result (pinned); copies overlap the neighbouring steps' compute on a second stream"}
-        del Uh, Uout, Din, Dout
+               "note": "per step: host->device copy of the input state (pinned) into one of two device buffers, "
+                       "the step in place on it, device->host copy of the result (pinned); copies overlap the "
+                       "neighbouring steps' compute on a second stream"}
+        del Uh, Uout, Din
 
     # ---- per-kernel-class times of the same step (eager launches, CUDA events on the context stream)
     Ud.copy_(U0)

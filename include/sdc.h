@@ -193,7 +193,9 @@ sdc_status sdc_react_newton(sdc_ctx* ctx, const double* rhs, double dt_m, double
 /* One SDC time step of size dt, in place on U ([nvar][Ntot]): every node starts
    at U^n, then K iterations of the node-to-node sweep of Eq. sdc:general;
    U^{n+1} = U^{M-1,(K)}.  Replays a CUDA graph captured at the first call for
-   this U pointer.  stats: NULL (asynchronous) or filled after a wait;
+   this U pointer (the graphs of the last two U pointers are kept, so a caller
+   that alternates two buffers replays both).  stats: NULL (asynchronous) or
+   filled after a wait;
    returns SDC_ERR_NEWTON_NOCONV when stats is given and some zone failed. */
 sdc_status sdc_step(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats);
 

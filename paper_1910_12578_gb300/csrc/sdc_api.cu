@@ -211,8 +211,11 @@ struct sdc_ctx {
     DevStats* d_stats = nullptr;
     unsigned long long* d_smax = nullptr;
     std::vector<void*> allocs;
-    cudaGraphExec_t gexec = nullptr;
-    double* gU = nullptr;
+    // the step's graphs for the last two U pointers (a caller that alternates two
+    // buffers replays both), and the slot to replace next
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    double* gU[2] = {nullptr, nullptr};
+    int gnext = 0;
     cudaGraphExec_t gexec_strang = nullptr;  // the Strang-split step's graph
     double* gU_strang = nullptr;
     double* d_dt_half = nullptr;             // dt/2 of the split step (next to d_dt)
@@ -502,10 +505,15 @@ cudaError_t enqueue_step(sdc_ctx* c, double* U, cudaStream_t st, Prof* prof = nu
 
 // the captured graphs hold constants and variants: drop them after a change
 void drop_graphs(sdc_ctx* c) {
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    for (int i = 0; i < 2; i++) {
+        if (c->gexec[i]) cudaGraphExecDestroy(c->gexec[i]);
+        c->gexec[i] = nullptr;
+        c->gU[i] = nullptr;
+    }
+    c->gnext = 0;
     if (c->gexec_strang) cudaGraphExecDestroy(c->gexec_strang);
-    c->gexec = c->gexec_strang = nullptr;
-    c->gU = c->gU_strang = nullptr;
+    c->gexec_strang = nullptr;
+    c->gU_strang = nullptr;
 }
 
 // stencil tiles of every box for tile shape `variant`
@@ -855,10 +863,15 @@ sdc_status sdc_react_newton(sdc_ctx* ctx, const double* rhs, double dt_m, double
 
 sdc_status sdc_step(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats) {
     if (!ctx || !U || !(dt > 0.0)) return SDC_ERR_INVALID_ARG;
-    if (!ctx->gexec || ctx->gU != U) {
-        if (ctx->gexec) {
-            cudaGraphExecDestroy(ctx->gexec);
-            ctx->gexec = nullptr;
+    int slot = -1;
+    for (int i = 0; i < 2; i++)
+        if (ctx->gexec[i] && ctx->gU[i] == U) slot = i;
+    if (slot < 0) {
+        slot = ctx->gnext;
+        if (ctx->gexec[slot]) {
+            cudaGraphExecDestroy(ctx->gexec[slot]);
+            ctx->gexec[slot] = nullptr;
+            ctx->gU[slot] = nullptr;
         }
         cudaGraph_t graph = nullptr;
         SDC_TRY(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -868,17 +881,18 @@ sdc_status sdc_step(sdc_ctx* ctx, double* U, double dt, sdc_stats* stats) {
             if (graph) cudaGraphDestroy(graph);
             return cuda_status(e != cudaSuccess ? e : e2);
         }
-        e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+        e = cudaGraphInstantiate(&ctx->gexec[slot], graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
-            ctx->gexec = nullptr;
+            ctx->gexec[slot] = nullptr;
             return cuda_status(e);
         }
-        ctx->gU = U;
+        ctx->gU[slot] = U;
     }
+    ctx->gnext = 1 - slot;  // the other graph is the one replaced next
     set_scalar_kernel<<<1, 1, 0, ctx->stream>>>(ctx->d_dt, dt);
     SDC_TRY(cudaGetLastError());
-    SDC_TRY(cudaGraphLaunch(ctx->gexec, ctx->stream));
+    SDC_TRY(cudaGraphLaunch(ctx->gexec[slot], ctx->stream));
     if (stats) return read_stats(ctx, stats);
     return SDC_OK;
 }

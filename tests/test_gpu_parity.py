@@ -523,6 +523,26 @@ def test_step_is_deterministic(torch_cuda):
     assert np.array_equal(outs[0], outs[1])
 
 
+def test_step_graphs_of_several_buffers(torch_cuda):
+    """One context stepping three buffers in turn (graph hits, and replacements of
+    the least recently used graph) gives each buffer the state that stepping it
+    alone gives, bit for bit."""
+    torch = torch_cuda
+    from paper_1910_12578_gb300 import sdc
+    P, U = PROBS["box16"]
+    ctx = sdc.Context(P)
+    bufs = {k: dev(torch, U) for k in "ABC"}
+    order = "ABAACBCAB"
+    for k in order:
+        ctx.step(bufs[k], 1e-3)
+    for k in "ABC":
+        alone = sdc.Context(P)
+        Ud = dev(torch, U)
+        for _ in range(order.count(k)):
+            alone.step(Ud, 1e-3)
+        assert np.array_equal(bufs[k].cpu().numpy(), Ud.cpu().numpy()), k
+
+
 def test_cfl_dt_matches_oracle(torch_cuda):
     torch = torch_cuda
     from paper_1910_12578_gb300 import sdc
