@@ -528,7 +528,7 @@ def measure(args, P, U, prec, ws, barrier, flush, with_e2e=True):
         Uh = U0.cpu().pin_memory()
         Uout = [torch.empty_like(Uh).pin_memory() for _ in range(2)]
         Din = [torch.empty_like(U0) for _ in range(2)]
-        e2e_steps = max(3, min(args.steps, 10))
+        e2e_steps = max(3, args.steps)
         comp = torch.cuda.current_stream()
         copy = torch.cuda.Stream()
         for b in range(2):   # capture the graph of each buffer outside the timed region
@@ -537,10 +537,6 @@ def measure(args, P, U, prec, ws, barrier, flush, with_e2e=True):
         torch.cuda.synchronize()
         ev = lambda: torch.cuda.Event()
         in_ready, out_ready = ([ev() for _ in range(2)] for _ in range(2))
-        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        ea.record(comp)
-        copy.wait_event(ea)
 
         def h2d(i):
             # on the copy stream after the previous result read from this buffer (stream order)
@@ -549,27 +545,54 @@ def measure(args, P, U, prec, ws, barrier, flush, with_e2e=True):
                 Din[b].copy_(Uh, non_blocking=True)
                 in_ready[b].record(copy)
 
-        h2d(0)
-        for i in range(e2e_steps):
-            b = i % 2
-            if i + 1 < e2e_steps:
-                h2d(i + 1)
-            comp.wait_event(in_ready[b])
-            ctx.step(Din[b], dt, stats=False)
-            out_ready[b].record(comp)
+        def pipeline(n):
+            """n steps, each with its input copied in and its result copied out; the device time"""
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(comp)
+            copy.wait_event(ea)
+            h2d(0)
+            for i in range(n):
+                b = i % 2
+                if i + 1 < n:
+                    h2d(i + 1)
+                comp.wait_event(in_ready[b])
+                ctx.step(Din[b], dt, stats=False)
+                out_ready[b].record(comp)
+                with torch.cuda.stream(copy):
+                    copy.wait_event(out_ready[b])
+                    Uout[b].copy_(Din[b], non_blocking=True)
+            comp.wait_stream(copy)
+            eb.record(comp)
+            torch.cuda.synchronize()
+            return ea.elapsed_time(eb)
+
+        # warm-up: the first copies from and into freshly pinned host buffers take several times
+        # as long as the later ones (about 110 against 12 ms for 2.4 GB at 256^3)
+        pipeline(3)
+        # the copies alone (for the record: the first input and the last result of the timed region
+        # are the copies that no compute hides)
+        h2d_ms = d2h_ms = float("inf")
+        for _ in range(3):   # the fastest of three (single copies vary several-fold on the host side)
+            cev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             with torch.cuda.stream(copy):
-                copy.wait_event(out_ready[b])
-                Uout[b].copy_(Din[b], non_blocking=True)
-        comp.wait_stream(copy)
-        eb.record(comp)
-        torch.cuda.synchronize()
-        e2e_value, _ = job_value(ea.elapsed_time(eb) / e2e_steps, units, 1, ws, torch_reduce_max("cuda"))
+                cev[0].record(copy)
+                Din[0].copy_(Uh, non_blocking=True)
+                cev[1].record(copy)
+                Uout[0].copy_(Din[0], non_blocking=True)
+                cev[2].record(copy)
+            torch.cuda.synchronize()
+            h2d_ms = min(h2d_ms, cev[0].elapsed_time(cev[1]))
+            d2h_ms = min(d2h_ms, cev[1].elapsed_time(cev[2]))
+        barrier()
+        e2e_ms = pipeline(e2e_steps)
+        e2e_value, _ = job_value(e2e_ms / e2e_steps, units, 1, ws, torch_reduce_max("cuda"))
         nbytes = U0.numel() * 8
         e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-               "steps": e2e_steps,
+               "steps": e2e_steps, "h2d_ms": round(h2d_ms, 3), "d2h_ms": round(d2h_ms, 3),
                "note": "per step: host->device copy of the input state (pinned) into one of two device buffers, "
                        "the step in place on it, device->host copy of the result (pinned); copies overlap the "
-                       "neighbouring steps' compute on a second stream"}
+                       "neighbouring steps' compute on a second stream; after 3 untimed steps of the same loop "
+                       "(h2d_ms, d2h_ms: one copy alone, the fastest of three)"}
         del Uh, Uout, Din
 
     # ---- per-kernel-class times of the same step (eager launches, CUDA events on the context stream)
