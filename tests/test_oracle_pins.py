@@ -1057,3 +1057,80 @@ def test_mirror_symmetry():
     scale = np.abs(V).reshape(P.nvar, -1).max(1)[:, None, None, None] + 1e-300
     assert np.abs(V - Vm).max() / 1.0 <= 1e-12 * np.abs(V).max()
     assert np.all(np.abs(V - Vm) <= 1e-12 * scale + 1e-14)
+
+
+@pytest.mark.parametrize("space_order", [2, 4])
+def test_species_advective_terms_sum_to_the_density_term(space_order):
+    """The species ride on the mass flux and their mass fractions sum to one
+    (section 2, Eq. 1), so with the interface mass fractions renormalised the
+    species' face fluxes sum to the mass flux and their advective terms to the
+    density's, on any state.  Here the mass fractions vary strongly from zone to
+    zone, so the MC limiter clips each species' slope differently and the
+    interface values before renormalisation do not sum to one."""
+    rng = np.random.default_rng(11)
+    ns, n = 7, 8
+    net = W.alpha_chain(ns, np.random.default_rng(0))
+    P = W.Problem(dim=3, n=(n, n, n), dx=(1 / n,) * 3, gamma=5 / 3, net=net, space_order=space_order, limiter=1)
+    shape = (n, n, n)
+    rho = rng.uniform(0.5, 2.0, shape)
+    vel = [rng.uniform(-0.5, 0.5, shape) for _ in range(3)]
+    T = rng.uniform(0.5, 2.0, shape)
+    X = rng.uniform(0.0, 1.0, (ns,) + shape) ** 3
+    X /= X.sum(0)
+    U = W.conserved_from(P.gamma, rho, vel, T, list(X))
+    A = O.Oracle(P).advective(U).reshape(P.nvar, -1)
+    assert np.abs(A[5:].sum(0) - A[0]).max() <= 1e-12 * np.abs(A[0]).max()
+
+
+@pytest.mark.parametrize("space_order", [2, 4])
+def test_advective_term_divides_by_each_axis_spacing(space_order):
+    """A state that varies along y alone, on a box whose three spacings differ:
+    the x and z flux differences vanish and the y differences divide by dy, so
+    the advective term is the 1D term of the same profile along x at spacing dy,
+    with the velocity component permuted and no transverse momentum change."""
+    ny, h = 16, 1.0 / 16
+    net = W.decay_network()
+    y = (np.arange(ny) + 0.5) * h
+    rho = 1.0 + 0.3 * np.sin(2 * np.pi * y)
+    v = 0.2 * np.cos(2 * np.pi * y)
+    T = 1.0 + 0.2 * np.sin(4 * np.pi * y)
+    XA = 0.5 + 0.4 * np.sin(2 * np.pi * y + 1.0)
+    P1 = W.Problem(dim=1, n=(ny, 1, 1), dx=(h, 1, 1), gamma=1.4, net=net, space_order=space_order)
+    U1 = W.conserved_from(1.4, rho, [v], T, [XA, 1 - XA])
+    A1 = O.Oracle(P1).advective(U1).reshape(P1.nvar, ny)
+    n = (4, ny, 4)
+    P3 = W.Problem(dim=3, n=n, dx=(3 * h, h, 0.5 * h), gamma=1.4, net=net, space_order=space_order)
+    b = lambda f: np.broadcast_to(f[None, :, None], (n[2], ny, n[0]))   # [z][y][x]
+    z0 = np.zeros((n[2], ny, n[0]))
+    U3 = W.conserved_from(1.4, b(rho), [z0, b(v), z0], b(T), [b(XA), b(1 - XA)])
+    A3 = O.Oracle(P3).advective(U3).reshape(P3.nvar, n[2], ny, n[0])
+    scale = np.abs(A1).max(1) + 1e-300
+    for k in range(n[2]):
+        for i in range(n[0]):
+            col = A3[:, k, :, i]
+            assert np.abs(col[1]).max() == 0.0 and np.abs(col[3]).max() == 0.0
+            got = np.concatenate([col[[0, 2, 4]], col[5:]])
+            assert np.all(np.abs(got - A1).max(1) <= 1e-13 * scale)
+
+
+def test_newton_on_a_linear_network_takes_one_step_and_one_check():
+    """A -> B with Q = 0 leaves rho E and so T unchanged, R is linear in w and the
+    residual G(w) = w - dt R(w) - rhs is affine: Newton's first step from any
+    admissible start lands on the root (to rounding) and the second, of rounding
+    size, meets the stop test.  Two iterations, and the root solves
+    (1 + dt k) X_A = X_A(rhs)."""
+    gamma = 5 / 3
+    net = W.decay_network(Q=0.0)
+    P, _ = uniform_1d(net)
+    o = O.Oracle(P)
+    rng = np.random.default_rng(5)
+    for _ in range(10):
+        XA = rng.uniform(0.2, 1.0)
+        T = rng.uniform(1.0, 3.0)
+        dt = 10 ** rng.uniform(-3, 0)
+        rhs = np.array([T / (gamma - 1), XA, 1 - XA])
+        w, status, it = o.newton_zone(1.0, [0.0], rhs, dt, rhs.copy())
+        assert status == O.NEWTON_OK and it == 2
+        k = 1e3 * math.exp(-10.0 / T)
+        assert w[1] == pytest.approx(XA / (1 + dt * k), rel=1e-13)
+        assert w[2] == pytest.approx(1 - XA / (1 + dt * k), rel=1e-13)
