@@ -70,6 +70,7 @@ def lib():
         _lib.orc_advective.argtypes = [pp, dp, dp]
         _lib.orc_advective_term.argtypes = [pp, dp, dp]
         _lib.orc_reaction_source4.argtypes = [pp, dp, dp]
+        _lib.orc_limited_faces.argtypes = [pp, C.c_int, dp, dp, dp, dp]
         _lib.orc_avg_to_point.argtypes = [pp, C.c_int, dp, dp]
         _lib.orc_point_to_avg.argtypes = [pp, C.c_int, dp, dp]
         _lib.orc_hllc.argtypes = [pp, C.c_int, dp, dp, dp]
@@ -165,6 +166,16 @@ class Oracle:
         out = np.empty_like(F)
         self.L.orc_point_to_avg(C.byref(self.s), int(F.shape[0]), _dp(F), _dp(out))
         return out
+
+    def limited_faces(self, direction, Wa, Wf):
+        """The fourth-order form's limited face states from averaged primitives Wa
+        and face values Wf ([nvar][...]): WL (upper face of each zone) and WR (at
+        zone z: the lower face of zone z+1)."""
+        Wa = np.ascontiguousarray(Wa, dtype=np.float64)
+        Wf = np.ascontiguousarray(Wf, dtype=np.float64)
+        WL, WR = np.empty_like(Wa), np.empty_like(Wa)
+        self.L.orc_limited_faces(C.byref(self.s), int(direction), _dp(Wa), _dp(Wf), _dp(WL), _dp(WR))
+        return WL, WR
 
     def rates(self, rho, mom, w, jac=True):
         mom = np.ascontiguousarray(np.atleast_1d(mom), dtype=np.float64)

@@ -498,6 +498,12 @@ static void limited_face_states(const orc_problem* P, int dir, const double* Wa,
     free(Wfl);
 }
 
+/* limited_face_states on given averaged primitives Wa and face values Wf (a
+   test hook for the limiter's properties) */
+void orc_limited_faces(const orc_problem* P, int dir, const double* Wa, const double* Wf, double* WL, double* WR) {
+    limited_face_states(P, dir, Wa, Wf, WL, WR);
+}
+
 void orc_advective4(const orc_problem* P, const double* U, double* A) {
     int dim = P->dim, nv = orc_nvar(P);
     long long N = nzones(P);

@@ -138,6 +138,10 @@ int orc_sdc_step(const orc_problem* P, double* U, double dt, orc_stats* st);
 void orc_avg_to_point(const orc_problem* P, int nf, const double* avg, double* point);
 void orc_point_to_avg(const orc_problem* P, int nf, const double* point, double* avg);
 void orc_advective4(const orc_problem* P, const double* U, double* A);
+/* the limited left (WL: upper face of zone z) and right (WR at z: lower face of
+   zone z+1) states of direction dir from averaged primitives Wa and face values
+   Wf, all [nvar][N] (the fourth-order form's limiters) */
+void orc_limited_faces(const orc_problem* P, int dir, const double* Wa, const double* Wf, double* WL, double* WR);
 void orc_advective_term(const orc_problem* P, const double* U, double* A);
 void orc_reaction_source4(const orc_problem* P, const double* U, double* R);
 void orc_react_newton4(const orc_problem* P, const double* rhs, double dt_m, double* U_inout, double* R_out,
